@@ -1,0 +1,174 @@
+/*
+ * pfmbem -- periodic fast-multipole BEM for acoustic transmission through a 2D
+ * periodic array of fibers (Kress combined-layer formulation, quasi-periodic
+ * along y), on one NVIDIA GB300 (sm_103a).
+ *
+ * Problem (paper Sec. 2): matrix wavenumber k in Omega_0, fiber wavenumber k1
+ * inside the M fibers of one fundamental block, which repeats with period H
+ * along y (h = (0, H), eq. 3, alpha = exp(i k H sin(theta))).  The incident wave
+ * is exp(i k x.d), d = (cos theta, sin theta).  Unknowns are the double-layer
+ * density phi and the single-layer density varphi on every fiber (eq. 4-5),
+ * discretised as constants on the chords between consecutive boundary nodes
+ * and collocated at the chord midpoints; the linear system is (I - A) Psi = B
+ * of eq. 9 with Psi = (phi_1, varphi_1, ...) interleaved PER ELEMENT:
+ *     Psi[2e] = phi_e,  Psi[2e+1] = varphi_e,   e = 0 .. E-1,
+ * elements numbered fiber by fiber in node order.  Complex numbers are stored
+ * as interleaved (re, im) doubles, so a complex vector of n entries is a
+ * double array of 2n.
+ *
+ * Pointers: every data pointer may address host memory or device memory; the
+ * library asks the CUDA runtime which, and stages host buffers through device
+ * workspace with copies on the handle's stream.  Device buffers must belong to
+ * the current device.  All GPU work is ordered on the stream given at create.
+ *
+ * Errors: every call returns a pfmbem_status; pfmbem_last_error(h) gives a
+ * human-readable reason for the last failure on that handle.  Argument and
+ * geometry errors are detected before any GPU work.  A handle is not
+ * thread-safe; distinct handles are independent.
+ */
+#ifndef PFMBEM_H
+#define PFMBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pfmbem* pfmbem_t;
+
+typedef enum {
+  PFMBEM_OK = 0,
+  PFMBEM_EINVAL = 1,    /* bad argument (null pointer, size, option out of range) */
+  PFMBEM_EGEOM = 2,     /* bad geometry: degenerate element, clockwise fiber, block wider than H */
+  PFMBEM_EWOOD = 3,     /* too close to a Wood anomaly: min_n |kH(1 +- sin theta) - 2 pi n| < 1e-3 (Sec. 2) */
+  PFMBEM_ENOMEM = 4,    /* device allocation failed */
+  PFMBEM_ECUDA = 5,     /* a CUDA runtime call failed */
+  PFMBEM_ENOCONV = 6,   /* GMRES stopped at maxit before reaching tol (best iterate is written) */
+  PFMBEM_ETIMEOUT = 7,  /* reserved for bounded device waits */
+  PFMBEM_ENUMERIC = 8   /* non-finite value detected (overflowing expansion tables, NaN residual) */
+} pfmbem_status;
+
+typedef enum { PFMBEM_SQUARE = 0, PFMBEM_HEXAGON = 1 } pfmbem_lattice;
+typedef enum { PFMBEM_FP64 = 0, PFMBEM_MIXED = 1 } pfmbem_precision;
+
+/* Options; a zero-initialised struct selects every default. */
+typedef struct {
+  int p;            /* expansion order at every level; 0 = per-level rule (below) */
+  int p_min;        /* lower bound of the per-level rule; 0 = 24 */
+  double eta;       /* coupling constant eta of eq. 4 (a real number); 0 = k */
+  int leaf_max;     /* target occupancy of a leaf box; 0 = 40 */
+  int depth;        /* quadtree depth (levels 0..depth); 0 = chosen from leaf_max */
+  int gmres_m;      /* GMRES restart length; 0 = 60 */
+  int precision;    /* pfmbem_precision used by pfmbem_solve; default FP64 */
+  int reserved[8];
+} pfmbem_options;
+
+/* Outcome of a solve. */
+typedef struct {
+  int iters;            /* total inner GMRES iterations (matrix-vector products) */
+  int restarts;         /* GMRES restarts, or FP64 refinement steps in mixed mode */
+  double rel_residual;  /* final true relative residual ||B - (I-A) Psi|| / ||B|| in FP64 */
+  double ms;            /* wall time of the solve in milliseconds */
+  int status;           /* pfmbem_status of the solve */
+} pfmbem_info;
+
+/* Plan summary for inspection and roofline accounting. */
+typedef struct {
+  int E;                  /* elements */
+  int M;                  /* fibers */
+  int depth;              /* quadtree depth */
+  int p[16];              /* expansion order per level 0..depth */
+  int nleaf_nonempty;     /* non-empty leaves */
+  int64_t m2l_pairs;      /* (target box, source box) M2L translations per matvec, all levels */
+  int64_t near_pairs;     /* (target element, source element) pairs of the near field */
+  int64_t near_quad;      /* near-field kernel evaluations (pairs x Gauss nodes) per matvec */
+  int64_t fiber_pairs;    /* same-fiber (k1) element pairs */
+  int64_t fiber_quad;     /* same-fiber kernel evaluations per matvec */
+  int p2m_nodes;          /* Gauss nodes per element in P2M */
+  int lattice_q;          /* directly summed image rows in the lattice sums */
+  double root_x0, root_y0;/* lower-left corner of the root box (side H) */
+  double setup_ms;        /* wall time of pfmbem_create */
+} pfmbem_plan_info;
+
+/* Create a solver for one fundamental block (paper Sec. 2-3).
+ *   M                 number of fibers (>= 1)
+ *   nodes_per_fiber   [M] nodes of each fiber (>= 3), host or device
+ *   nodes_xy          [sum N][2] boundary nodes, counter-clockwise per fiber
+ *                     (outward normal = tangent turned clockwise, Sec. 2),
+ *                     host or device, float64
+ *   H                 period along y (paper H; "period L" elsewhere), > 0;
+ *                     the block's extent along x must not exceed H
+ *   lattice           informational (square / hexagon; the quadtree is square)
+ *   k, k1             matrix and fiber wavenumbers (> 0), k = omega/c_matrix
+ *   rho_ratio         varrho = rho_matrix / rho_fiber of eq. 6 (> 0)
+ *   theta             incidence angle in radians
+ *   opt               options or NULL for defaults
+ *   cuda_stream       cudaStream_t to order all work on (NULL = legacy stream)
+ *   out               receives the handle; the handle owns all device state
+ * Builds the quadtree (Sec. 3.1), self-element integrals, lattice sums
+ * (Sec. 3.3) and translation tables.  Returns EGEOM/EWOOD/EINVAL/ENOMEM/ECUDA. */
+pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nodes_xy,
+                            double H, int lattice, double k, double k1, double rho_ratio,
+                            double theta, const pfmbem_options* opt, void* cuda_stream,
+                            pfmbem_t* out);
+
+/* Release every resource of the handle (NULL is ignored). */
+void pfmbem_destroy(pfmbem_t h);
+
+/* Reason for the last failure on h (never NULL; "" if none). */
+const char* pfmbem_last_error(pfmbem_t h);
+
+/* Plan summary (sizes, orders, pair counts). */
+pfmbem_status pfmbem_plan(pfmbem_t h, pfmbem_plan_info* info);
+
+/* Right-hand side B of eq. 9 (complex [2E]):
+ *   B[2e] = -u_inc(c_e),  B[2e+1] = (2i / (eta (1 + varrho))) du_inc/dnu(c_e). */
+pfmbem_status pfmbem_rhs(pfmbem_t h, double* B);
+
+/* y = (I - A) x, the operator of eq. 9, by the periodic FMM (Sec. 3) plus the
+ * near field and the fiber-local k1 operators; x, y complex [2E]
+ * (x and y must not overlap).  precision: PFMBEM_FP64 or PFMBEM_MIXED. */
+pfmbem_status pfmbem_matvec(pfmbem_t h, const double* x, double* y, int precision);
+
+/* Solve (I - A) Psi = B by restarted GMRES (Sec. 4: "GMRES").
+ *   B     complex [2E] right-hand side, or NULL for the incident-wave B of eq. 9
+ *   psi   complex [2E]; input initial guess if use_guess != 0, output solution
+ *   tol   relative residual target (FP64 true residual)
+ *   maxit maximum matrix-vector products
+ * In mixed precision the inner GMRES uses the mixed matvec and an outer FP64
+ * refinement loop restores FP64 accuracy.  Returns ENOCONV if tol is not met
+ * (psi still holds the best iterate).  info may be NULL. */
+pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_guess,
+                           double tol, int maxit, pfmbem_info* info);
+
+/* Scattered field u^s (eq. 7) at npts points outside the fibers, from the
+ * densities psi: pts [npts][2] float64, u complex [npts]. */
+pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double* pts, double* u);
+
+/* Bragg-order coefficients from the densities psi: for orders n with
+ * |k sin(theta) + 2 pi n / H| < k, R_n (reflected, left of the block) and
+ * T_n (transmitted, right; includes the incident wave for n = 0), plus the
+ * energy sum E = sum (k_x,n / k_x,0)(|R_n|^2 + |T_n|^2).
+ *   max_orders   capacity of orders/R/T; *norders receives the count.
+ *   orders int[max_orders]; R, T complex [max_orders]; all host memory. */
+pfmbem_status pfmbem_coefficients(pfmbem_t h, const double* psi, int max_orders, int* norders,
+                                  int* orders, double* R, double* T, double* energy);
+
+/* Lattice sums S_j = sum_{|m|>=2} alpha^m H_j(k|m|H) e^{i j theta_{-mh}} of
+ * Sec. 3.3 (theta_{-mh} = -pi/2 for m > 0, +pi/2 for m < 0) for
+ * j = -jmax .. jmax, computed as on the root translation: direct rows
+ * 2 <= |m| <= q plus the two spectral tails integrated on the contour of eq. 18.
+ * S complex [2 jmax + 1], index j + jmax. */
+pfmbem_status pfmbem_lattice_sums(pfmbem_t h, int jmax, double* S);
+
+/* Self-element integrals used on the diagonal (flat element at its midpoint):
+ * S_ee and the finite-part T_ee for k (out[0..1]) and k1 (out[2..3]) of every
+ * element; out complex [E][4] in element order. */
+pfmbem_status pfmbem_self_terms(pfmbem_t h, double* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PFMBEM_H */

@@ -1,0 +1,857 @@
+// Host side of the pfmbem library: geometry checks, the periodic quadtree
+// (Sec. 3.1), translation tables (Sec. 3.2), the lattice-sum root operator
+// (Sec. 3.3), the C ABI and the GMRES driver (Sec. 4).
+#include <algorithm>
+#include <chrono>
+#include <complex>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "internal.h"
+
+namespace {
+
+pfmbem_status fail(pfmbem* h, pfmbem_status st, const std::string& msg) {
+  if (h) h->err = msg;
+  return st;
+}
+
+pfmbem_status fail_cuda(pfmbem* h, cudaError_t e, const char* what) {
+  if (h) h->err = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? PFMBEM_ENOMEM : PFMBEM_ECUDA;
+}
+
+#define CK(call)                                            \
+  do {                                                      \
+    cudaError_t _e = (call);                                \
+    if (_e != cudaSuccess) return fail_cuda(h, _e, #call);  \
+  } while (0)
+
+template <class T>
+T* dalloc(pfmbem* h, size_t n) {
+  void* p = nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
+  h->allocs.push_back(p);
+  return static_cast<T*>(p);
+}
+
+template <class T>
+pfmbem_status upload(pfmbem* h, T** dst, const std::vector<T>& src) {
+  *dst = dalloc<T>(h, src.size());
+  if (!*dst) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
+  if (!src.empty()) CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  return PFMBEM_OK;
+}
+
+double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// J_0..J_N and Y_0..Y_N of a real argument x > 0 (Miller for J, forward recurrence for Y).
+void bessel_jy(double x, int N, std::vector<double>& J, std::vector<double>& Y) {
+  J.assign(N + 1, 0.0);
+  Y.assign(N + 1, 0.0);
+  bessel_j_array(x, N, J.data());
+  Y[0] = ::y0(x);
+  if (N >= 1) Y[1] = ::y1(x);
+  for (int n = 1; n < N; ++n) Y[n + 1] = (2.0 * n / x) * Y[n] - Y[n - 1];
+}
+
+inline int morton(int ix, int iy, int D) {
+  int c = 0;
+  for (int b = 0; b < D; ++b) c |= (((ix >> b) & 1) << (2 * b)) | (((iy >> b) & 1) << (2 * b + 1));
+  return c;
+}
+
+// Gauss-Legendre thresholds: rule g meets tolerance tol for a source element
+// whose midpoint is q element lengths away when its Bernstein ellipse
+// parameter 2q + sqrt(4q^2 - 1) >= tol^(-1/(2g)); i.e. q >= (R + 1/R)/4.
+void gl_thresholds(double tol, double* thr) {
+  thr[0] = 1e300;
+  for (int g = 1; g <= PF_GLMAX; ++g) {
+    double R = std::pow(tol, -1.0 / (2.0 * g));
+    thr[g] = (R + 1.0 / R) / 4.0;
+  }
+}
+
+int gl_order_host(double q, const double* thr) {
+  int g = 1;
+  while (g < PF_GLMAX && q < thr[g]) ++g;
+  return g;
+}
+
+double g_thr64[PF_GLMAX + 1], g_thr32[PF_GLMAX + 1];
+int g_gauss_ready_dev = -1;
+
+void ensure_gauss() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (g_gauss_ready_dev == dev) return;
+  std::vector<double> x(PF_GLMAX * PF_GLMAX, 0.0), w(PF_GLMAX * PF_GLMAX, 0.0);
+  for (int g = 1; g <= PF_GLMAX; ++g) gauss_legendre(g, &x[(g - 1) * PF_GLMAX], &w[(g - 1) * PF_GLMAX]);
+  gl_thresholds(1e-14, g_thr64);
+  gl_thresholds(3e-8, g_thr32);
+  k_upload_gauss(x.data(), w.data(), g_thr64, g_thr32);
+  g_gauss_ready_dev = dev;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int j = 2; j <= n; ++j) {
+        double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+        p0 = p1;
+        p1 = p2;
+      }
+      if (n == 1) { p1 = z; p0 = 1.0; }
+      double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (std::fabs(dz) < 1e-16) {
+        // final derivative at the converged node
+        p0 = 1.0; p1 = z;
+        for (int j = 2; j <= n; ++j) {
+          double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+          p0 = p1;
+          p1 = p2;
+        }
+        if (n == 1) { p1 = z; p0 = 1.0; }
+        dp = n * (z * p1 - p0) / (z * z - 1.0);
+        break;
+      }
+    }
+    double p0 = 1.0, p1 = z;
+    for (int j = 2; j <= n; ++j) {
+      double p2 = ((2.0 * j - 1.0) * z * p1 - (j - 1.0) * p0) / j;
+      p0 = p1;
+      p1 = p2;
+    }
+    if (n == 1) { p1 = z; p0 = 1.0; }
+    double dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = -z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+// ============================================================== planning
+static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) {
+  const double t0 = now_ms();
+  const int M = h->M;
+  const double H = h->H, k = h->k;
+  // ---------------------------------------------------- elements (original order)
+  std::vector<int> foff(M + 1, 0);
+  for (int i = 0; i < M; ++i) {
+    if (npf[i] < 3) return fail(h, PFMBEM_EGEOM, "fiber " + std::to_string(i) + " has fewer than 3 nodes");
+    foff[i + 1] = foff[i] + npf[i];
+  }
+  const int E = foff[M];
+  h->E = E;
+  h->hfib_off = foff;
+  std::vector<double2> c(E), t(E), nu(E);
+  std::vector<double> len(E);
+  std::vector<int> fib(E);
+  double xmin = 1e300, xmax = -1e300, ymin = 1e300, ymax = -1e300, hmax = 0, hmin = 1e300;
+  for (int i = 0; i < M; ++i) {
+    double area = 0;
+    const int n = npf[i];
+    h->max_fiber = std::max(h->max_fiber, n);
+    for (int j = 0; j < n; ++j) {
+      const double* a = nodes + 2 * (foff[i] + j);
+      const double* b = nodes + 2 * (foff[i] + (j + 1) % n);
+      if (!std::isfinite(a[0]) || !std::isfinite(a[1])) return fail(h, PFMBEM_EGEOM, "non-finite node");
+      const int e = foff[i] + j;
+      double dx = b[0] - a[0], dy = b[1] - a[1];
+      double L = std::hypot(dx, dy);
+      if (!(L > 0)) return fail(h, PFMBEM_EGEOM, "zero-length element " + std::to_string(e));
+      c[e] = double2{0.5 * (a[0] + b[0]), 0.5 * (a[1] + b[1])};
+      t[e] = double2{dx / L, dy / L};
+      nu[e] = double2{dy / L, -dx / L};
+      len[e] = L;
+      fib[e] = i;
+      area += a[0] * b[1] - a[1] * b[0];
+      xmin = std::min(xmin, a[0]); xmax = std::max(xmax, a[0]);
+      ymin = std::min(ymin, a[1]); ymax = std::max(ymax, a[1]);
+      hmax = std::max(hmax, L);
+      hmin = std::min(hmin, L);
+    }
+    if (!(area > 0)) return fail(h, PFMBEM_EGEOM, "fiber " + std::to_string(i) + " is not counter-clockwise");
+  }
+  if (xmax - xmin > H) return fail(h, PFMBEM_EGEOM, "block wider than the period H along x");
+  if (0.5 * k * hmax > 4.0) return fail(h, PFMBEM_EINVAL, "elements longer than 8/k");
+  // ---------------------------------------------------- root box and wrapping
+  h->x0 = 0.5 * (xmin + xmax) - 0.5 * H;
+  h->y0 = 0.5 * (ymin + ymax) - 0.5 * H;
+  std::vector<int> m0(E);
+  std::vector<double2> cw(E);
+  for (int e = 0; e < E; ++e) {
+    int m = (int)std::floor((c[e].y - h->y0) / H);
+    m0[e] = m;
+    cw[e] = double2{c[e].x, c[e].y - m * H};
+  }
+  // ---------------------------------------------------- depth
+  const int leaf_max = h->opt.leaf_max > 0 ? h->opt.leaf_max : 40;
+  int D = h->opt.depth;
+  auto leaf_of = [&](int e, int Dd) {
+    int n = 1 << Dd;
+    double d = H / n;
+    int ix = (int)std::floor((cw[e].x - h->x0) / d);
+    int iy = (int)std::floor((cw[e].y - h->y0) / d);
+    ix = std::min(std::max(ix, 0), n - 1);
+    iy = std::min(std::max(iy, 0), n - 1);
+    return morton(ix, iy, Dd);
+  };
+  if (D <= 0) {
+    for (D = 2; D < 10; ++D) {
+      std::vector<int> cnt(1 << (2 * D), 0);
+      int mx = 0;
+      for (int e = 0; e < E; ++e) mx = std::max(mx, ++cnt[leaf_of(e, D)]);
+      if (mx <= leaf_max) break;
+    }
+  }
+  if (D < 2 || D > 10) return fail(h, PFMBEM_EINVAL, "depth must be in [2, 10]");
+  h->D = D;
+  // ---------------------------------------------------- sort by leaf Morton key
+  std::vector<int> key(E), perm(E), pos(E);
+  for (int e = 0; e < E; ++e) key[e] = leaf_of(e, D);
+  for (int e = 0; e < E; ++e) perm[e] = e;
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+  for (int s = 0; s < E; ++s) pos[perm[s]] = s;
+  // ---------------------------------------------------- levels
+  const double eta = h->eta;
+  (void)eta;
+  for (int l = 0; l <= D; ++l) {
+    Level& L = h->lev[l];
+    L.nbox = 1 << (2 * l);
+    L.d = H / (1 << l);
+    L.hbegin.assign(L.nbox, 0);
+    L.hend.assign(L.nbox, 0);
+    std::vector<int> cnt(L.nbox, 0);
+    for (int s = 0; s < E; ++s) cnt[key[perm[s]] >> (2 * (D - l))]++;
+    int acc = 0;
+    for (int b = 0; b < L.nbox; ++b) {
+      L.hbegin[b] = acc;
+      acc += cnt[b];
+      L.hend[b] = acc;
+      if (cnt[b] > 0) L.hne.push_back(b);
+    }
+    L.nne = (int)L.hne.size();
+    // expansion order
+    double x = k * L.d * std::sqrt(2.0);
+    int pmin = h->opt.p_min > 0 ? h->opt.p_min : 24;
+    int p = h->opt.p > 0 ? h->opt.p : (int)std::ceil(x + 1.8 * std::pow(10.0, 2.0 / 3.0) * std::cbrt(x));
+    p = std::max(p, h->opt.p > 0 ? 1 : pmin);
+    if (p > PF_PMAX) return fail(h, PFMBEM_EINVAL, "expansion order above the library limit (64); use more levels");
+    L.p = p;
+    L.P = 2 * p + 1;
+    L.sigma = k * L.d / std::sqrt(2.0);
+    L.w.assign(L.P, 1.0);
+    double wn = 1.0;
+    for (int n = 1; n <= p; ++n) {
+      wn *= L.sigma / n;
+      L.w[p + n] = wn;
+      L.w[p - n] = wn;
+    }
+    h->info.p[l] = p;
+  }
+  // ---------------------------------------------------- lists
+  const int nD = 1 << D;
+  {
+    Level& Lf = h->lev[D];
+    std::vector<int> ptr(1, 0), src, img;
+    for (int b : Lf.hne) {
+      int ix = 0, iy = 0;
+      for (int bb = 0; bb < D; ++bb) { ix |= ((b >> (2 * bb)) & 1) << bb; iy |= ((b >> (2 * bb + 1)) & 1) << bb; }
+      for (int dx = -1; dx <= 1; ++dx)
+        for (int dy = -1; dy <= 1; ++dy) {
+          int sx = ix + dx, sy = iy + dy;
+          if (sx < 0 || sx >= nD) continue;
+          int syw = ((sy % nD) + nD) % nD;
+          int m = (sy - syw) / nD;
+          int sb = morton(sx, syw, D);
+          if (Lf.hend[sb] > Lf.hbegin[sb]) { src.push_back(sb); img.push_back(m); }
+        }
+      ptr.push_back((int)src.size());
+    }
+    CK(cudaSuccess);
+    pfmbem_status st;
+    if ((st = upload(h, &h->nl_ptr, ptr)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->nl_src, src)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->nl_img, img)) != PFMBEM_OK) return st;
+    // near-field pair statistics
+    int64_t pairs = 0, quad = 0;
+    for (size_t li = 0; li < Lf.hne.size(); ++li) {
+      int b = Lf.hne[li];
+      for (int s = Lf.hbegin[b]; s < Lf.hend[b]; ++s)
+        for (int e = ptr[li]; e < ptr[li + 1]; ++e) {
+          int sb = src[e];
+          for (int f = Lf.hbegin[sb]; f < Lf.hend[sb]; ++f) {
+            if (f == s && img[e] == 0) continue;
+            int eo = perm[f], so = perm[s];
+            double dx = cw[so].x - cw[eo].x, dy = cw[so].y - (cw[eo].y + img[e] * H);
+            double q = std::hypot(dx, dy) / len[eo];
+            pairs++;
+            quad += gl_order_host(q, g_thr64);
+          }
+        }
+    }
+    h->info.near_pairs = pairs;
+    h->info.near_quad = quad;
+  }
+  int64_t m2l_pairs = 0;
+  for (int l = 1; l <= D; ++l) {
+    Level& L = h->lev[l];
+    const int nl = 1 << l, np = 1 << (l - 1);
+    std::vector<int> ptr(1, 0), src, off, img;
+    for (int b : L.hne) {
+      int ix = 0, iy = 0;
+      for (int bb = 0; bb < l; ++bb) { ix |= ((b >> (2 * bb)) & 1) << bb; iy |= ((b >> (2 * bb + 1)) & 1) << bb; }
+      int px = ix >> 1, py = iy >> 1;
+      for (int pdx = -1; pdx <= 1; ++pdx) {
+        int qx = px + pdx;
+        if (qx < 0 || qx >= np) continue;
+        for (int pdy = -1; pdy <= 1; ++pdy) {
+          int qy = py + pdy;
+          for (int cx = 0; cx < 2; ++cx)
+            for (int cy = 0; cy < 2; ++cy) {
+              int sx = 2 * qx + cx, sy = 2 * qy + cy;
+              int dx = ix - sx, dy = iy - sy;
+              if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
+              int syw = ((sy % nl) + nl) % nl;
+              int m = (sy - syw) / nl;
+              int sb = morton(sx, syw, l);
+              if (L.hend[sb] <= L.hbegin[sb]) continue;
+              src.push_back(sb);
+              off.push_back((dx + 3) * 7 + (dy + 3));
+              img.push_back(m);
+            }
+        }
+      }
+      ptr.push_back((int)src.size());
+    }
+    L.nil = (int64_t)src.size();
+    m2l_pairs += L.nil;
+    pfmbem_status st;
+    if ((st = upload(h, &L.il_ptr, ptr)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.il_src, src)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.il_off, off)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.il_img, img)) != PFMBEM_OK) return st;
+  }
+  h->info.m2l_pairs = m2l_pairs;
+  // fiber-local statistics
+  {
+    int64_t pairs = 0, quad = 0;
+    for (int i = 0; i < M; ++i)
+      for (int e = foff[i]; e < foff[i + 1]; ++e)
+        for (int f = foff[i]; f < foff[i + 1]; ++f) {
+          if (f == e) continue;
+          double q = std::hypot(c[e].x - c[f].x, c[e].y - c[f].y) / len[f];
+          pairs++;
+          quad += gl_order_host(q, g_thr64);
+        }
+    h->info.fiber_pairs = pairs;
+    h->info.fiber_quad = quad;
+  }
+  // P2M Gauss nodes: elements outside the near field are at least one leaf
+  // side minus half an element length away.
+  {
+    double qfar = std::max(1.0, h->lev[D].d / hmax - 1.0);
+    h->g_far = gl_order_host(qfar, g_thr64);
+    h->g_far_f = gl_order_host(qfar, g_thr32);
+  }
+  // ---------------------------------------------------- translation tables
+  for (int l = 0; l <= D; ++l) {
+    Level& L = h->lev[l];
+    const int p = L.p, P = L.P;
+    pfmbem_status st;
+    if ((st = upload(h, &L.w_dev, L.w)) != PFMBEM_OK) return st;
+    std::vector<int> ne(L.hne);
+    if ((st = upload(h, &L.ne, ne)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.box_begin, L.hbegin)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.box_end, L.hend)) != PFMBEM_OK) return st;
+    L.M = dalloc<cplx>(h, (size_t)L.nbox * P);
+    L.L = dalloc<cplx>(h, (size_t)L.nbox * P);
+    if (!L.M || !L.L) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions)");
+    // M2L operators at this level: T[o][l][n] = w_l H^+_{n-l}(k (dx, dy) d) w_n
+    if (l >= 1) {
+      std::vector<cplx> T((size_t)49 * P * P, cplx{0, 0});
+      std::vector<double> J, Y;
+      for (int dx = -3; dx <= 3; ++dx)
+        for (int dy = -3; dy <= 3; ++dy) {
+          if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
+          int o = (dx + 3) * 7 + (dy + 3);
+          double vx = dx * L.d, vy = dy * L.d;
+          double r = std::hypot(vx, vy), th = std::atan2(vy, vx);
+          bessel_jy(k * r, 2 * p, J, Y);
+          for (int a = -p; a <= p; ++a)        // target coefficient l = a
+            for (int n = -p; n <= p; ++n) {    // source coefficient n
+              int j = n - a, aj = std::abs(j);
+              double sg = (j < 0 && (aj & 1)) ? -1.0 : 1.0;
+              double hr = sg * J[aj], hi = sg * Y[aj];
+              double cs = std::cos(j * th), sn = std::sin(j * th);
+              double sc = L.w[a + p] * L.w[n + p];
+              cplx v{sc * (hr * cs - hi * sn), sc * (hr * sn + hi * cs)};
+              if (!std::isfinite(v.re) || !std::isfinite(v.im))
+                return fail(h, PFMBEM_ENUMERIC, "non-finite M2L operator; lower p or change depth");
+              T[((size_t)o * P + (a + p)) * P + (n + p)] = v;
+            }
+        }
+      if ((st = upload(h, &L.m2l, T)) != PFMBEM_OK) return st;
+    }
+    // M2M (children l+1 -> l) and L2L (l -> children)
+    if (l < D) {
+      Level& C = h->lev[l + 1];
+      const int pc = C.p, Pc = C.P;
+      std::vector<cplx> A((size_t)4 * P * Pc), B((size_t)4 * Pc * P);
+      std::vector<double> J, Y;
+      for (int q = 0; q < 4; ++q) {
+        int cx = q & 1, cy = (q >> 1) & 1;
+        double vx = (cx - 0.5) * C.d, vy = (cy - 0.5) * C.d;   // O_child - O_parent
+        double r = std::hypot(vx, vy), th = std::atan2(vy, vx);
+        bessel_jy(k * r, p + pc, J, Y);
+        for (int n = -p; n <= p; ++n)
+          for (int m = -pc; m <= pc; ++m) {
+            // A[n][m] = J^-_{n-m}(k v) w^c_m / w^p_n,  J^-_j = J_j e^{-i j th}
+            int j = n - m, aj = std::abs(j);
+            double Jj = (j < 0 && (aj & 1)) ? -J[aj] : J[aj];
+            double s = C.w[m + pc] / L.w[n + p];
+            A[((size_t)q * P + (n + p)) * Pc + (m + pc)] = cplx{s * Jj * std::cos(j * th), -s * Jj * std::sin(j * th)};
+          }
+        for (int n = -pc; n <= pc; ++n)
+          for (int m = -p; m <= p; ++m) {
+            // B[n][m] = w^c_n J^+_{m-n}(k v) / w^p_m,  J^+_j = J_j e^{i j th}
+            int j = m - n, aj = std::abs(j);
+            double Jj = (j < 0 && (aj & 1)) ? -J[aj] : J[aj];
+            double s = C.w[n + pc] / L.w[m + p];
+            B[((size_t)q * Pc + (n + pc)) * P + (m + p)] = cplx{s * Jj * std::cos(j * th), s * Jj * std::sin(j * th)};
+          }
+      }
+      if ((st = upload(h, &L.m2m, A)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.l2l, B)) != PFMBEM_OK) return st;
+    }
+  }
+  // ---------------------------------------------------- element arrays
+  {
+    std::vector<double2> sc(E), st2(E), snu(E);
+    std::vector<double> sh(E);
+    std::vector<cplx> sph(E);
+    for (int s = 0; s < E; ++s) {
+      int e = perm[s];
+      sc[s] = cw[e];
+      st2[s] = t[e];
+      snu[s] = nu[e];
+      sh[s] = len[e];
+      // alpha^{-m0}
+      double a = -m0[e] * h->beta;
+      sph[s] = cplx{std::cos(a), std::sin(a)};
+    }
+    pfmbem_status st;
+    if ((st = upload(h, &h->s_c, sc)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_t, st2)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_nu, snu)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_h, sh)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_ph, sph)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_perm, perm)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_c, c)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_t, t)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_nu, nu)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_h, len)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_fiber, fib)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->fib_off, foff)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_pos, pos)) != PFMBEM_OK) return st;
+  }
+  h->self4 = dalloc<cplx>(h, (size_t)4 * E);
+  h->dens = dalloc<cplx>(h, (size_t)2 * E);
+  h->U = dalloc<cplx>(h, (size_t)2 * E);
+  h->stage_in = dalloc<cplx>(h, (size_t)2 * E);
+  h->stage_out = dalloc<cplx>(h, (size_t)2 * E);
+  h->dev_rhs = dalloc<cplx>(h, (size_t)2 * E);
+  if (!h->self4 || !h->dens || !h->U || !h->stage_in || !h->stage_out || !h->dev_rhs)
+    return fail(h, PFMBEM_ENOMEM, "device allocation failed (work buffers)");
+  CK(k_self_terms(h));
+  // ---------------------------------------------------- lattice sums + root operator
+  {
+    Level& R = h->lev[0];
+    const int p0 = R.p, P0 = R.P, jmax = 2 * p0;
+    cplx* Sd = dalloc<cplx>(h, jmax + 1);
+    if (!Sd) return fail(h, PFMBEM_ENOMEM, "device allocation failed (lattice sums)");
+    CK(k_lattice_sums(h, jmax, h->lattice_q, Sd));
+    h->lattice_S.resize(jmax + 1);
+    CK(cudaMemcpyAsync(h->lattice_S.data(), Sd, sizeof(cplx) * (jmax + 1), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    std::vector<cplx> Rt((size_t)P0 * P0);
+    for (int a = -p0; a <= p0; ++a)
+      for (int n = -p0; n <= p0; ++n) {
+        cplx s = h->lattice_S[std::abs(n - a)];
+        double sc = R.w[a + p0] * R.w[n + p0];
+        cplx v{sc * s.re, sc * s.im};
+        if (!std::isfinite(v.re) || !std::isfinite(v.im))
+          return fail(h, PFMBEM_ENUMERIC, "non-finite lattice sums");
+        Rt[(size_t)(a + p0) * P0 + (n + p0)] = v;
+      }
+    pfmbem_status st;
+    if ((st = upload(h, &h->root, Rt)) != PFMBEM_OK) return st;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  h->info.E = E;
+  h->info.M = M;
+  h->info.depth = D;
+  h->info.nleaf_nonempty = h->lev[D].nne;
+  h->info.p2m_nodes = h->g_far;
+  h->info.lattice_q = h->lattice_q;
+  h->info.root_x0 = h->x0;
+  h->info.root_y0 = h->y0;
+  h->setup_ms = now_ms() - t0;
+  h->info.setup_ms = h->setup_ms;
+  return PFMBEM_OK;
+}
+
+// ============================================================== staging
+namespace {
+struct InBuf {
+  const cplx* dev = nullptr;
+};
+// Returns a device view of an input vector of n complex numbers.
+pfmbem_status stage_input(pfmbem* h, const double* p, size_t n, cplx* scratch, const cplx** out) {
+  if (is_device_ptr(p)) {
+    *out = reinterpret_cast<const cplx*>(p);
+    return PFMBEM_OK;
+  }
+  CK(cudaMemcpyAsync(scratch, p, n * sizeof(cplx), cudaMemcpyHostToDevice, h->stream));
+  *out = scratch;
+  return PFMBEM_OK;
+}
+}  // namespace
+
+// ============================================================== GMRES
+static pfmbem_status gmres_alloc(pfmbem* h, int m) {
+  GmresWork& g = h->gw;
+  const int n = 2 * h->E;
+  if (g.V && g.m == m) return PFMBEM_OK;
+  if (g.V) return PFMBEM_OK;   // keep the first allocation (restart length fixed per handle)
+  g.n = n;
+  g.m = m;
+  g.V = dalloc<cplx>(h, (size_t)(m + 1) * n);
+  g.w = dalloc<cplx>(h, n);
+  g.r = dalloc<cplx>(h, n);
+  g.x = dalloc<cplx>(h, n);
+  g.b = dalloc<cplx>(h, n);
+  g.d = dalloc<cplx>(h, n);
+  g.hcol = dalloc<cplx>(h, 2 * (m + 2));
+  g.nrm = dalloc<double>(h, 2);
+  if (!g.V || !g.w || !g.r || !g.x || !g.b || !g.d || !g.hcol || !g.nrm) return fail(h, PFMBEM_ENOMEM, "GMRES workspace");
+  if (cudaMallocHost(&g.hhost, sizeof(cplx) * 2 * (m + 2)) != cudaSuccess) return fail(h, PFMBEM_ENOMEM, "pinned host buffer");
+  return PFMBEM_OK;
+}
+
+static inline std::complex<double> toz(cplx a) { return {a.re, a.im}; }
+
+// Restarted GMRES(m) with classical Gram-Schmidt applied twice; A is applied by
+// the FMM matvec in the given precision.  Solves A x = b in place of x (device).
+static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int maxit, int precision,
+                           int* iters_out, int* restarts_out, double* relres_out) {
+  GmresWork& g = h->gw;
+  const int n = g.n, m = g.m;
+  double* hn = reinterpret_cast<double*>(g.hhost);
+  CK(k_norm2(h, b, n, g.nrm));
+  CK(cudaMemcpyAsync(hn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const double bnorm = std::sqrt(hn[0]);
+  if (bnorm == 0) {
+    CK(cudaMemsetAsync(x, 0, sizeof(cplx) * n, h->stream));
+    *iters_out = 0;
+    *relres_out = 0;
+    return PFMBEM_OK;
+  }
+  int iters = 0, restarts = 0;
+  double relres = 1.0;
+  std::vector<std::complex<double>> Hm((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1);
+  while (true) {
+    // r = b - A x
+    CK(k_matvec(h, x, g.w, precision));
+    CK(k_sub(h, b, g.w, g.r, n));
+    CK(k_norm2(h, g.r, n, g.nrm));
+    CK(cudaMemcpyAsync(hn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    double beta = std::sqrt(hn[0]);
+    relres = beta / bnorm;
+    if (!std::isfinite(relres)) return fail(h, PFMBEM_ENUMERIC, "non-finite residual");
+    if (relres <= tol || iters >= maxit) break;
+    CK(k_scale_copy(h, g.r, cplx{1.0 / beta, 0}, g.V, n));
+    std::fill(gvec.begin(), gvec.end(), 0.0);
+    gvec[0] = beta;
+    int j = 0;
+    for (; j < m && iters < maxit; ++j) {
+      cplx* vj = g.V + (size_t)j * n;
+      cplx* vj1 = g.V + (size_t)(j + 1) * n;
+      CK(k_matvec(h, vj, g.w, precision));
+      ++iters;
+      // CGS2
+      CK(k_multidot(h, g.V, j + 1, g.w, n, g.hcol));
+      CK(k_gemv_sub(h, g.V, j + 1, g.hcol, g.w, n));
+      CK(k_multidot(h, g.V, j + 1, g.w, n, g.hcol + (m + 2)));
+      CK(k_gemv_sub(h, g.V, j + 1, g.hcol + (m + 2), g.w, n));
+      CK(k_norm2(h, g.w, n, g.nrm));
+      CK(cudaMemcpyAsync(g.hhost, g.hcol, sizeof(cplx) * 2 * (m + 2), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(hn + 4 * (m + 2) - 2, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      double hnext = std::sqrt(hn[4 * (m + 2) - 2]);
+      for (int i = 0; i <= j; ++i) Hm[(size_t)i * m + j] = toz(g.hhost[i]) + toz(g.hhost[(m + 2) + i]);
+      Hm[(size_t)(j + 1) * m + j] = hnext;
+      if (hnext > 0) CK(k_scale_copy(h, g.w, cplx{1.0 / hnext, 0}, vj1, n));
+      // Givens
+      for (int i = 0; i < j; ++i) {
+        auto a = Hm[(size_t)i * m + j], bb = Hm[(size_t)(i + 1) * m + j];
+        Hm[(size_t)i * m + j] = std::conj(cs[i]) * a + std::conj(sn[i]) * bb;
+        Hm[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      auto a = Hm[(size_t)j * m + j], bb = Hm[(size_t)(j + 1) * m + j];
+      double den = std::sqrt(std::norm(a) + std::norm(bb));
+      if (den == 0) { cs[j] = 1; sn[j] = 0; }
+      else { cs[j] = a / den; sn[j] = bb / den; }
+      Hm[(size_t)j * m + j] = std::conj(cs[j]) * a + std::conj(sn[j]) * bb;
+      Hm[(size_t)(j + 1) * m + j] = 0;
+      auto gj = gvec[j];
+      gvec[j] = std::conj(cs[j]) * gj;
+      gvec[j + 1] = -sn[j] * gj;
+      double est = std::abs(gvec[j + 1]) / bnorm;
+      if (est <= 0.5 * tol || hnext == 0) { ++j; break; }
+    }
+    // back substitution and x += V y
+    std::vector<std::complex<double>> y(j);
+    for (int i = j - 1; i >= 0; --i) {
+      auto s = gvec[i];
+      for (int q = i + 1; q < j; ++q) s -= Hm[(size_t)i * m + q] * y[q];
+      y[i] = s / Hm[(size_t)i * m + i];
+    }
+    for (int i = 0; i < j; ++i) g.hhost[i] = cplx{y[i].real(), y[i].imag()};
+    CK(cudaMemcpyAsync(g.hcol, g.hhost, sizeof(cplx) * j, cudaMemcpyHostToDevice, h->stream));
+    CK(k_gemv_add(h, g.V, j, g.hcol, x, n));
+    ++restarts;
+  }
+  *iters_out = iters;
+  *restarts_out = restarts;
+  *relres_out = relres;
+  return relres <= tol ? PFMBEM_OK : PFMBEM_ENOCONV;
+}
+
+// ============================================================== C ABI
+extern "C" {
+
+pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nodes_xy, double H, int lattice,
+                            double k, double k1, double rho_ratio, double theta, const pfmbem_options* opt,
+                            void* cuda_stream, pfmbem_t* out) {
+  if (!out) return PFMBEM_EINVAL;
+  *out = nullptr;
+  if (M < 1 || !nodes_per_fiber || !nodes_xy) return PFMBEM_EINVAL;
+  if (!(H > 0) || !(k > 0) || !(k1 > 0) || !(rho_ratio > 0) || !std::isfinite(theta)) return PFMBEM_EINVAL;
+  pfmbem* h = new pfmbem();
+  h->M = M;
+  h->H = H;
+  h->lattice = lattice;
+  h->k = k;
+  h->k1 = k1;
+  h->rho = rho_ratio;
+  h->theta = theta;
+  if (opt) h->opt = *opt;
+  h->eta = h->opt.eta != 0 ? h->opt.eta : k;
+  h->beta = k * H * std::sin(theta);
+  h->alpha = cplx{std::cos(h->beta), std::sin(h->beta)};
+  {
+    // c2 = 2 / (i eta (1 + rho)) = -2i / (eta (1 + rho))
+    h->c2re = 0.0;
+    h->c2im = -2.0 / (h->eta * (1.0 + rho_ratio));
+  }
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  // Wood anomalies (Sec. 2): kH(1 +- sin theta) = 2 pi n
+  {
+    double s = std::sin(theta), dmin = 1e300;
+    for (double v : {k * H * (1 + s), k * H * (1 - s)}) {
+      double r = v - 2 * M_PI * std::round(v / (2 * M_PI));
+      dmin = std::min(dmin, std::fabs(r));
+    }
+    if (dmin < 1e-3) {
+      h->err = "incidence within 1e-3 of a Wood anomaly";
+      *out = h;
+      return PFMBEM_EWOOD;
+    }
+  }
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    h->err = "no CUDA device";
+    *out = h;
+    return PFMBEM_ECUDA;
+  }
+  ensure_gauss();
+  // host copies of the inputs
+  std::vector<int> npf(M);
+  if (is_device_ptr(nodes_per_fiber)) {
+    if (cudaMemcpy(npf.data(), nodes_per_fiber, sizeof(int) * M, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      *out = h;
+      return fail_cuda(h, cudaGetLastError(), "copy nodes_per_fiber");
+    }
+  } else {
+    std::memcpy(npf.data(), nodes_per_fiber, sizeof(int) * M);
+  }
+  long long tot = 0;
+  for (int i = 0; i < M; ++i) tot += npf[i] > 0 ? npf[i] : 0;
+  std::vector<double> nodes(2 * tot);
+  if (is_device_ptr(nodes_xy)) {
+    if (cudaMemcpy(nodes.data(), nodes_xy, sizeof(double) * 2 * tot, cudaMemcpyDeviceToHost) != cudaSuccess) {
+      *out = h;
+      return fail_cuda(h, cudaGetLastError(), "copy nodes");
+    }
+  } else {
+    std::memcpy(nodes.data(), nodes_xy, sizeof(double) * 2 * tot);
+  }
+  *out = h;
+  return build_plan(h, npf.data(), nodes.data());
+}
+
+void pfmbem_destroy(pfmbem_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->gw.hhost) cudaFreeHost(h->gw.hhost);
+  delete h;
+}
+
+const char* pfmbem_last_error(pfmbem_t h) { return h ? h->err.c_str() : "null handle"; }
+
+pfmbem_status pfmbem_plan(pfmbem_t h, pfmbem_plan_info* info) {
+  if (!h || !info) return PFMBEM_EINVAL;
+  *info = h->info;
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_rhs(pfmbem_t h, double* B) {
+  if (!h || !B) return PFMBEM_EINVAL;
+  const size_t n = 2 * (size_t)h->E;
+  if (is_device_ptr(B)) {
+    CK(k_rhs(h, reinterpret_cast<cplx*>(B)));
+    return PFMBEM_OK;
+  }
+  CK(k_rhs(h, h->stage_out));
+  CK(cudaMemcpyAsync(B, h->stage_out, n * sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_matvec(pfmbem_t h, const double* x, double* y, int precision) {
+  if (!h || !x || !y) return PFMBEM_EINVAL;
+  if (precision != PFMBEM_FP64 && precision != PFMBEM_MIXED) return fail(h, PFMBEM_EINVAL, "precision");
+  const size_t n = 2 * (size_t)h->E;
+  const cplx* xd;
+  pfmbem_status st = stage_input(h, x, n, h->stage_in, &xd);
+  if (st != PFMBEM_OK) return st;
+  const bool ydev = is_device_ptr(y);
+  cplx* yd = ydev ? reinterpret_cast<cplx*>(y) : h->stage_out;
+  CK(k_matvec(h, xd, yd, precision));
+  if (!ydev) {
+    CK(cudaMemcpyAsync(y, yd, n * sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_guess, double tol, int maxit,
+                           pfmbem_info* info) {
+  if (!h || !psi || !(tol > 0) || maxit < 1) return PFMBEM_EINVAL;
+  const double t0 = now_ms();
+  const int m = h->opt.gmres_m > 0 ? h->opt.gmres_m : 60;
+  if (m > 250) return fail(h, PFMBEM_EINVAL, "gmres_m above 250");
+  pfmbem_status st = gmres_alloc(h, m);
+  if (st != PFMBEM_OK) return st;
+  GmresWork& g = h->gw;
+  const size_t n = 2 * (size_t)h->E;
+  if (B) {
+    const cplx* bd;
+    if ((st = stage_input(h, B, n, g.b, &bd)) != PFMBEM_OK) return st;
+    if (bd != g.b) CK(cudaMemcpyAsync(g.b, bd, n * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    CK(k_rhs(h, g.b));
+  }
+  const bool pdev = is_device_ptr(psi);
+  if (use_guess) {
+    CK(cudaMemcpyAsync(g.x, psi, n * sizeof(cplx), pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  } else {
+    CK(cudaMemsetAsync(g.x, 0, n * sizeof(cplx), h->stream));
+  }
+  int iters = 0, restarts = 0;
+  double relres = 1;
+  st = gmres(h, g.b, g.x, tol, maxit, PFMBEM_FP64, &iters, &restarts, &relres);
+  CK(cudaMemcpyAsync(psi, g.x, n * sizeof(cplx), pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (info) {
+    info->iters = iters;
+    info->restarts = restarts;
+    info->rel_residual = relres;
+    info->ms = now_ms() - t0;
+    info->status = st;
+  }
+  if (st == PFMBEM_ENOCONV) h->err = "GMRES did not reach tol within maxit";
+  return st;
+}
+
+pfmbem_status pfmbem_lattice_sums(pfmbem_t h, int jmax, double* S) {
+  if (!h || !S || jmax < 0 || jmax > 2 * PF_PMAX) return PFMBEM_EINVAL;
+  cplx* Sd = h->stage_out;
+  if ((size_t)(jmax + 1) > 2 * (size_t)h->E) return fail(h, PFMBEM_EINVAL, "jmax too large for the work buffer");
+  CK(k_lattice_sums(h, jmax, h->lattice_q, Sd));
+  std::vector<cplx> tmp(jmax + 1);
+  CK(cudaMemcpyAsync(tmp.data(), Sd, sizeof(cplx) * (jmax + 1), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  std::vector<double> outv(2 * (2 * jmax + 1));
+  for (int j = -jmax; j <= jmax; ++j) {
+    cplx v = tmp[std::abs(j)];
+    outv[2 * (j + jmax)] = v.re;
+    outv[2 * (j + jmax) + 1] = v.im;
+  }
+  if (is_device_ptr(S)) {
+    CK(cudaMemcpy(S, outv.data(), sizeof(double) * outv.size(), cudaMemcpyHostToDevice));
+  } else {
+    std::memcpy(S, outv.data(), sizeof(double) * outv.size());
+  }
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_self_terms(pfmbem_t h, double* out) {
+  if (!h || !out) return PFMBEM_EINVAL;
+  const size_t n = 4 * (size_t)h->E;
+  CK(cudaMemcpyAsync(out, h->self4, n * sizeof(cplx), is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double* pts, double* u) {
+  (void)psi; (void)npts; (void)pts; (void)u;
+  if (!h) return PFMBEM_EINVAL;
+  return fail(h, PFMBEM_EINVAL, "pfmbem_field: not available in this build");
+}
+
+pfmbem_status pfmbem_coefficients(pfmbem_t h, const double* psi, int max_orders, int* norders, int* orders, double* R,
+                                  double* T, double* energy) {
+  (void)psi; (void)max_orders; (void)norders; (void)orders; (void)R; (void)T; (void)energy;
+  if (!h) return PFMBEM_EINVAL;
+  return fail(h, PFMBEM_EINVAL, "pfmbem_coefficients: not available in this build");
+}
+
+}  // extern "C"

@@ -1,0 +1,124 @@
+// Internal state of a pfmbem handle and the kernel launch interface shared by
+// the host planner/driver (host.cpp) and the CUDA kernels (kernels.cu).
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "../../include/pfmbem.h"
+
+// One level of the uniform quadtree (level 0 = root box of side H).
+struct Level {
+  int p = 0, P = 0;          // order and coefficient count 2p+1
+  double d = 0;              // box side
+  double sigma = 0;          // expansion scale k * d / sqrt(2)
+  std::vector<double> w;     // w_n = sigma^|n| / |n|!, n = -p..p (index n + p)
+  double* w_dev = nullptr;   // device copy of w
+  int nbox = 0;              // 4^l boxes (Morton order)
+  std::vector<int> hbegin, hend;   // element range of every box (sorted order)
+  std::vector<int> hne;            // non-empty boxes
+  // device
+  cplx* M = nullptr;         // scaled multipoles [nbox][P]
+  cplx* L = nullptr;         // scaled locals     [nbox][P]
+  int* ne = nullptr;         // non-empty boxes
+  int nne = 0;
+  int* box_begin = nullptr;  // [nbox]
+  int* box_end = nullptr;
+  // M2L interaction lists (CSR over ne), entries: source box, offset id, image m
+  int* il_ptr = nullptr;
+  int* il_src = nullptr;
+  int* il_off = nullptr;
+  int* il_img = nullptr;
+  int64_t nil = 0;
+  cplx* m2l = nullptr;       // [49][P][P]: row = target coefficient, col = source coefficient
+  cplx* m2m = nullptr;       // children (level l+1) -> this level: [4][P][P_child]
+  cplx* l2l = nullptr;       // this level -> children: [4][P_child][P]
+  // FP32 copies for the mixed path
+  cplxf* Mf = nullptr;
+  cplxf* Lf = nullptr;
+  cplxf* m2lf = nullptr;
+  cplxf* m2mf = nullptr;
+  cplxf* l2lf = nullptr;
+};
+
+struct GmresWork {
+  int n = 0, m = 0;
+  cplx* V = nullptr;        // [(m+1)][n]
+  cplx* w = nullptr;        // [n]
+  cplx* r = nullptr;        // [n]
+  cplx* x = nullptr;        // [n]
+  cplx* b = nullptr;        // [n]
+  cplx* d = nullptr;        // [n] correction (refinement)
+  cplx* hcol = nullptr;     // [m+2] device dot results
+  double* nrm = nullptr;    // [2]
+  cplx* hhost = nullptr;    // pinned host mirror of hcol
+};
+
+struct pfmbem {
+  // problem (paper notation)
+  int M = 0, E = 0, lattice = 0;
+  double H = 0, k = 0, k1 = 0, rho = 0, theta = 0, eta = 0, beta = 0;
+  cplx alpha{1, 0};
+  double c2re = 0, c2im = 0;     // c2 = 2 / (i eta (1 + rho))
+  pfmbem_options opt{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  // plan
+  int D = 0;
+  double x0 = 0, y0 = 0;
+  Level lev[PF_MAXLEVEL + 1];
+  int g_far = 4, g_far_f = 2;    // Gauss nodes per element in P2M (FP64 / FP32)
+  int lattice_q = 8;
+  pfmbem_plan_info info{};
+  // elements, tree (sorted) order
+  double2* s_c = nullptr;        // wrapped midpoint
+  double2* s_t = nullptr;        // unit tangent
+  double2* s_nu = nullptr;       // outward normal
+  double* s_h = nullptr;         // length
+  cplx* s_ph = nullptr;          // alpha^{-m0} input phase of the wrapped copy
+  int* s_perm = nullptr;         // sorted -> original
+  // elements, original order
+  double2* o_c = nullptr;        // true midpoint
+  double2* o_t = nullptr;
+  double2* o_nu = nullptr;
+  double* o_h = nullptr;
+  int* o_fiber = nullptr;
+  int* fib_off = nullptr;        // [M + 1]
+  int* o_pos = nullptr;          // original -> sorted
+  cplx* self4 = nullptr;         // [E][4]: S_ee(k), T_ee(k), S_ee(k1), T_ee(k1)
+  std::vector<int> hfib_off;
+  int max_fiber = 0;
+  // near lists over non-empty leaves (CSR): source leaf, image m
+  int* nl_ptr = nullptr;
+  int* nl_src = nullptr;
+  int* nl_img = nullptr;
+  cplx* root = nullptr;          // [P0][P0] periodic root translation
+  cplxf* rootf = nullptr;
+  std::vector<cplx> lattice_S;   // S_j, j = 0..2 p0 (S_-j = S_j)
+  // matvec work
+  cplx* dens = nullptr;          // sorted [E][2] = (phi', varphi')
+  cplx* U = nullptr;             // sorted [E][2] = (U', dU')
+  cplx* stage_in = nullptr;      // [2E] staging for host buffers
+  cplx* stage_out = nullptr;
+  cplx* dev_rhs = nullptr;       // [2E]
+  GmresWork gw;
+  std::vector<void*> allocs;
+  double setup_ms = 0;
+};
+
+// ------------------------------------------------------------ kernel launches
+void k_upload_gauss(const double* x, const double* w, const double* thr64, const double* thr32);
+cudaError_t k_self_terms(pfmbem* h);
+cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev);
+cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);
+cudaError_t k_rhs(pfmbem* h, cplx* B);
+cudaError_t k_field(pfmbem* h, const cplx* psi, int npts, const double2* pts, cplx* u);
+// BLAS-1 style helpers for GMRES (complex128, length n)
+cudaError_t k_multidot(pfmbem* h, const cplx* V, int ncol, const cplx* w, int n, cplx* out);
+cudaError_t k_gemv_sub(pfmbem* h, const cplx* V, int ncol, const cplx* coef, cplx* w, int n);
+cudaError_t k_norm2(pfmbem* h, const cplx* v, int n, double* out);
+cudaError_t k_scale_copy(pfmbem* h, const cplx* src, cplx s, cplx* dst, int n);
+cudaError_t k_axpy(pfmbem* h, cplx a, const cplx* x, cplx* y, int n);   // y += a x
+cudaError_t k_sub(pfmbem* h, const cplx* a, const cplx* b, cplx* out, int n);  // out = a - b
+cudaError_t k_gemv_add(pfmbem* h, const cplx* V, int ncol, const cplx* coef, cplx* y, int n);  // y += V coef

@@ -1,0 +1,710 @@
+// CUDA kernels of the periodic FM-BEM (sm_103a).
+//
+// Operator (paper eq. 9) applied to Psi = (phi_e, varphi_e) per element:
+//   y_2e   = phi_e - V_e + U_e
+//   y_2e+1 = varphi_e + c2 (dU_e - rho dV_e),      c2 = 2 / (i eta (1 + rho))
+// with V = D1 phi - i eta S1 varphi, dV = T1 phi - i eta K1 varphi (same fiber,
+// wavenumber k1, eq. 5) and U = D2b phi - i eta S2b varphi, dU = T2b phi - i eta
+// K2b varphi (all fibers and their images, wavenumber k, eqs. 7-8).  U and dU
+// come from the periodic FMM of Sec. 3 (near field + P2M/M2M/M2L/L2L/L2P +
+// lattice-sum root translation), V and dV from a fiber-local direct sum.
+#include <cstdio>
+
+#include "internal.h"
+
+// Gauss-Legendre rules g = 1..16 on [-1, 1]: node q of rule g at [g-1][q].
+__constant__ double c_glx[PF_GLMAX][PF_GLMAX];
+__constant__ double c_glw[PF_GLMAX][PF_GLMAX];
+__constant__ float c_glxf[PF_GLMAX][PF_GLMAX];
+__constant__ float c_glwf[PF_GLMAX][PF_GLMAX];
+// q-thresholds (distance / element length) above which rule g meets the
+// quadrature tolerance; [0] for the FP64 path, [1] for the FP32 path.
+__constant__ double c_glthr[2][PF_GLMAX + 1];
+
+// Rule size for a source element at distance ratio q = |x - c| / h.
+__device__ __forceinline__ int gl_order(double q, int which) {
+  int g = 1;
+#pragma unroll 1
+  while (g < PF_GLMAX && q < c_glthr[which][g]) ++g;
+  return g;
+}
+
+void k_upload_gauss(const double* x, const double* w, const double* thr64, const double* thr32) {
+  float xf[PF_GLMAX * PF_GLMAX], wf[PF_GLMAX * PF_GLMAX];
+  for (int i = 0; i < PF_GLMAX * PF_GLMAX; ++i) {
+    xf[i] = (float)x[i];
+    wf[i] = (float)w[i];
+  }
+  double thr[2][PF_GLMAX + 1];
+  for (int i = 0; i <= PF_GLMAX; ++i) {
+    thr[0][i] = thr64[i];
+    thr[1][i] = thr32[i];
+  }
+  cudaMemcpyToSymbol(c_glx, x, sizeof(double) * PF_GLMAX * PF_GLMAX);
+  cudaMemcpyToSymbol(c_glw, w, sizeof(double) * PF_GLMAX * PF_GLMAX);
+  cudaMemcpyToSymbol(c_glxf, xf, sizeof(xf));
+  cudaMemcpyToSymbol(c_glwf, wf, sizeof(wf));
+  cudaMemcpyToSymbol(c_glthr, thr, sizeof(thr));
+}
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ cplx cexp_d(cplx z) {
+  double s, c;
+  sincos(z.im, &s, &c);
+  double e = exp(z.re);
+  return cplx{e * c, e * s};
+}
+__device__ __forceinline__ cplx clog_d(cplx z) { return cplx{log(hypot(z.re, z.im)), atan2(z.im, z.re)}; }
+__device__ __forceinline__ cplx csqrt_d(cplx z) {
+  double r = hypot(z.re, z.im);
+  double a = sqrt(fmax(0.0, 0.5 * (r + z.re)));
+  double b = sqrt(fmax(0.0, 0.5 * (r - z.re)));
+  return cplx{a, z.im < 0 ? -b : b};
+}
+__device__ __forceinline__ cplx shfl_down(cplx v, int o) {
+  return cplx{__shfl_down_sync(0xffffffffu, v.re, o), __shfl_down_sync(0xffffffffu, v.im, o)};
+}
+__device__ __forceinline__ cplx warp_sum(cplx v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += shfl_down(v, o);
+  return v;
+}
+__device__ __forceinline__ cplx ipow_phase(cplx alpha, int m) {
+  // alpha^m for m in {-1, 0, 1}
+  if (m == 0) return cplx{1, 0};
+  if (m == 1) return alpha;
+  return cdiv(cplx{1, 0}, alpha);
+}
+
+// ---------------------------------------------------------------- self terms
+// S_ee = (i/2)(1/kappa) I(x), T_ee = (i/2) kappa [I(x) - H1(x)], x = kappa h/2,
+// I(x) = int_0^x H0(t) dt by term-wise integration of the ascending series of
+// J0 and Y0 (Y0 = (2/pi)(ln(t/2) + gamma) J0 + (2/pi) sum (-1)^{m+1} H_m (t/2)^{2m}/(m!)^2).
+__device__ void self_pair(double kap, double h, cplx& S, cplx& T) {
+  const double x = 0.5 * kap * h;
+  const double hx2 = 0.25 * x * x;
+  const double lnh = log(0.5 * x);
+  const double EG = 0.57721566490153286061;
+  double base = x;     // x (x/2)^{2m} / (m!)^2
+  double IJ = 0.0, IYa = 0.0, IYb = 0.0, Hm = 0.0;
+  for (int m = 0; m < 60; ++m) {
+    double term = base / (2 * m + 1);
+    double sg = (m & 1) ? -1.0 : 1.0;
+    IJ += sg * term;
+    IYa += sg * term * (lnh + EG - 1.0 / (2 * m + 1));
+    if (m >= 1) IYb += -sg * Hm * term;
+    if (fabs(term) < 1e-18 * fabs(IJ)) break;
+    base *= hx2 / ((double)(m + 1) * (m + 1));
+    Hm += 1.0 / (m + 1);
+  }
+  const double IY = (2.0 / M_PI) * (IYa + IYb);
+  const double J1 = j1(x), Y1 = y1(x);
+  S = cplx{-IY / (2.0 * kap), IJ / (2.0 * kap)};
+  T = cplx{-0.5 * kap * (IY - Y1), 0.5 * kap * (IJ - J1)};
+}
+
+__global__ void self_terms_kernel(int E, double k, double k1, const double* __restrict__ hlen, cplx* __restrict__ out) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  cplx s, t;
+  self_pair(k, hlen[e], s, t);
+  out[4 * e + 0] = s;
+  out[4 * e + 1] = t;
+  self_pair(k1, hlen[e], s, t);
+  out[4 * e + 2] = s;
+  out[4 * e + 3] = t;
+}
+
+cudaError_t k_self_terms(pfmbem* h) {
+  self_terms_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->k, h->k1, h->o_h, h->self4);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- lattice sums
+// S_j = sum_{2<=|m|<=q} alpha^m H_j(k|m|H) e^{i j theta} + tail_+ + tail_-,
+// tails from the spectral form of the image sums (Sec. 3.3, eq. 17) on the
+// contour t = +-sqrt(u^2 - 2iku) of eq. 18 with u = v^2, where mu = u - ik and
+// dt / mu = du / sqrt(u^2 - 2iku) (the Jacobian), so that
+//   tail_+(n) = (1/(i pi)) int_0^inf (-i/k)^n [w^n + (-k^2/w)^n] e^{iq beta - qH mu}
+//               / (e^{H mu - i beta} - 1) * 2 / sqrt(v^2 - 2ik) dv,   w = mu + sqrt(u^2 - 2iku)
+//   tail_-(n) = the same with beta -> -beta and (-i/k)^n -> (i/k)^n.
+// One block per order j >= 0 (S_-j = S_j); nodes: composite 16-point Gauss on
+// geometrically graded panels [V 2^-(P-1-i)...], given by the host.
+#define LS_PANELS 12
+__global__ void lattice_sum_kernel(int jmax, int q, double k, double H, double beta, double V,
+                                   cplx* __restrict__ out) {
+  const int j = blockIdx.x;
+  __shared__ double red[2][256];
+  cplx acc{0, 0};
+  const int nq = LS_PANELS * 16;
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) {
+    int pnl = t / 16, node = t % 16;
+    double a = (pnl == 0) ? 0.0 : V * ldexp(1.0, pnl - LS_PANELS);
+    double b = V * ldexp(1.0, pnl + 1 - LS_PANELS);
+    double v = 0.5 * (a + b) + 0.5 * (b - a) * c_glx[15][node];
+    double om = 0.5 * (b - a) * c_glw[15][node];
+    double u = v * v;
+    cplx mu{u, -k};
+    cplx sq = csqrt_d(cplx{u, -2.0 * k});            // sqrt(v^2 - 2ik), 4th quadrant
+    cplx s = v * sq;                                 // sqrt(u^2 - 2iku)
+    cplx w = mu + s;
+    cplx F = cdiv(cplx{2.0 * om, 0}, sq);
+    // e^{-qH mu} = e^{-qHu} e^{iqHk}
+    cplx eq = cexp_d(cplx{-q * H * u, q * H * k});
+    cplx base = cdiv(F * eq, cplx{0, M_PI});         // / (i pi)
+    cplx ehu = cexp_d(cplx{H * u, -H * k});         // e^{H mu}
+    cplx dp = ehu * cexp_d(cplx{0, -beta}) - cplx{1, 0};
+    cplx dm = ehu * cexp_d(cplx{0, beta}) - cplx{1, 0};
+    cplx Ap = cdiv(cexp_d(cplx{0, q * beta}), dp);
+    cplx Am = cdiv(cexp_d(cplx{0, -q * beta}), dm);
+    cplx lw = clog_d(w);
+    double lk = log(k);
+    // (-i w / k)^n, (i k / w)^n, (i w / k)^n, (-i k / w)^n in log form
+    cplx l1 = cplx{lw.re - lk, lw.im - 0.5 * M_PI};
+    cplx l2 = cplx{lk - lw.re, 0.5 * M_PI - lw.im};
+    cplx l3 = cplx{lw.re - lk, lw.im + 0.5 * M_PI};
+    cplx l4 = cplx{lk - lw.re, -0.5 * M_PI - lw.im};
+    cplx lbp = clog_d(base * Ap);
+    cplx lbm = clog_d(base * Am);
+    double n = (double)j;
+    acc += cexp_d(n * l1 + lbp) + cexp_d(n * l2 + lbp) + cexp_d(n * l3 + lbm) + cexp_d(n * l4 + lbm);
+  }
+  // direct rows 2 <= |m| <= q
+  for (int m = 2 + threadIdx.x; m <= q; m += blockDim.x) {
+    double x = k * m * H;
+    double Jv[2 * PF_PMAX + 2];
+    bessel_j_array(x, j, Jv);
+    double y0v = ::y0(x), y1v = ::y1(x), Y = y0v;
+    if (j >= 1) {
+      double ym = y0v, yc = y1v;
+      for (int n = 1; n < j; ++n) {
+        double yn = (2.0 * n / x) * yc - ym;
+        ym = yc;
+        yc = yn;
+      }
+      Y = yc;
+    }
+    cplx Hj{Jv[j], Y};
+    // i^j and (-i)^j
+    cplx ij{1, 0};
+    for (int r = 0; r < (j & 3); ++r) ij = mul_i(ij);
+    cplx mij = conj(ij);
+    // alpha^m = e^{i m beta}
+    cplx am = cexp_d(cplx{0, m * beta});
+    acc += Hj * (am * mij + conj(am) * ij);
+  }
+  red[0][threadIdx.x] = acc.re;
+  red[1][threadIdx.x] = acc.im;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      red[0][threadIdx.x] += red[0][threadIdx.x + s];
+      red[1][threadIdx.x] += red[1][threadIdx.x + s];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[j] = cplx{red[0][0], red[1][0]};
+}
+
+// host: upper limit V of the v-integral where every order's integrand has
+// dropped by e^-40 below its peak.
+static double lattice_vmax(int jmax, int q, double k, double H) {
+  double V = sqrt(40.0 / (q * H));
+  for (int n = 0; n <= jmax; n += (jmax > 8 ? jmax / 8 : 1)) {
+    double peak = -1e300, vpk = 0;
+    for (int i = 1; i < 4000; ++i) {
+      double v = 0.005 * i;
+      double u = v * v;
+      double wabs = hypot(u, k) + sqrt(hypot(u * u, 2 * k * u));
+      double f = n * log(wabs / k) - q * H * u;
+      if (f > peak) { peak = f; vpk = v; }
+    }
+    for (double v = vpk; v < 200; v *= 1.01) {
+      double u = v * v;
+      double wabs = hypot(u, k) + sqrt(hypot(u * u, 2 * k * u));
+      double f = n * log(wabs / k) - q * H * u;
+      if (f < peak - 42.0) { if (v > V) V = v; break; }
+    }
+  }
+  return V;
+}
+
+cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev) {
+  double V = lattice_vmax(jmax, q, h->k, h->H);
+  lattice_sum_kernel<<<jmax + 1, 256, 0, h->stream>>>(jmax, q, h->k, h->H, h->beta, V, out_dev);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- pair integrals
+// Element integrals of (i/4)H0(kap|x-y|) (S), its d/dnu_y (D), d/dnu_x (K) and
+// d2/dnu_x dnu_y (T) over the flat element c + s t, |s| <= h/2, by g-point
+// Gauss-Legendre; the factor i/4 is applied by the caller.
+__device__ __forceinline__ void pair4_f64(double kap, double2 x, double2 nx, double2 c, double2 t, double2 ny,
+                                          double h, int g, cplx& S, cplx& D, cplx& K, cplx& T) {
+  const double nn = nx.x * ny.x + nx.y * ny.y;
+#pragma unroll 1
+  for (int q = 0; q < g; ++q) {
+    double s = 0.5 * h * c_glx[g - 1][q];
+    double wq = 0.5 * h * c_glw[g - 1][q];
+    double z1 = x.x - (c.x + s * t.x);
+    double z2 = x.y - (c.y + s * t.y);
+    double r = sqrt(z1 * z1 + z2 * z2);
+    double ir = 1.0 / r;
+    double kr = kap * r;
+    double J0 = j0(kr), Y0 = y0(kr), J1 = j1(kr), Y1 = y1(kr);
+    double zy = (z1 * ny.x + z2 * ny.y) * ir;
+    double zx = (z1 * nx.x + z2 * nx.y) * ir;
+    S += wq * cplx{J0, Y0};
+    D += (wq * kap * zy) * cplx{J1, Y1};
+    K += (-wq * kap * zx) * cplx{J1, Y1};
+    double a = kap * zx * zy;
+    double b = ir * (nn - 2.0 * zx * zy);
+    T += (wq * kap) * cplx{a * J0 + b * J1, a * Y0 + b * Y1};
+  }
+}
+
+// ---------------------------------------------------------------- permute
+__global__ void gather_dens_kernel(int E, const int* __restrict__ perm, const cplx* __restrict__ ph,
+                                   const cplx* __restrict__ x, cplx* __restrict__ dens) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= E) return;
+  int e = perm[s];
+  cplx p = ph[s];
+  dens[2 * s] = p * x[2 * e];
+  dens[2 * s + 1] = p * x[2 * e + 1];
+}
+
+// ---------------------------------------------------------------- P2M (FP64)
+// M_n(O_C) = sum_elements sum_g w_g h/2 [phi' dJ^-_n/dnu_y - i eta varphi' J^-_n](k(y_g - O_C)),
+// J^-_n(v) = J_n(|v|) e^{-i n theta_v}, dJ^-_n/dnu = (k/2)(-nu J^-_{n+1} + conj(nu) J^-_{n-1})
+// with nu = nu_x + i nu_y (Sec. 3.2, the moments of S2b and D2b); stored scaled by 1/w_n.
+__global__ void p2m_f64_kernel(const int* __restrict__ ne, const int* __restrict__ bb, const int* __restrict__ be,
+                               int D, double d, int p, const double* __restrict__ wgt, int g,
+                               double k, double eta, double x0, double y0,
+                               const double2* __restrict__ sc, const double2* __restrict__ st,
+                               const double2* __restrict__ snu, const double* __restrict__ sh,
+                               const cplx* __restrict__ dens, cplx* __restrict__ Mout) {
+  const int box = ne[blockIdx.x];
+  const int P = 2 * p + 1;
+  __shared__ double acc[2 * PF_NCOEF];
+  for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) acc[i] = 0.0;
+  __syncthreads();
+  // box centre from the Morton code
+  int ix = 0, iy = 0;
+  for (int b = 0; b < D; ++b) {
+    ix |= ((box >> (2 * b)) & 1) << b;
+    iy |= ((box >> (2 * b + 1)) & 1) << b;
+  }
+  const double ox = x0 + (ix + 0.5) * d, oy = y0 + (iy + 0.5) * d;
+  const int lb = bb[box], le = be[box];
+  const int npts = (le - lb) * g;
+  for (int t = threadIdx.x; t < npts; t += blockDim.x) {
+    int f = lb + t / g, q = t % g;
+    double2 c = sc[f], tt = st[f], nu = snu[f];
+    double hh = sh[f];
+    double s = 0.5 * hh * c_glx[g - 1][q];
+    double cw = 0.5 * hh * c_glw[g - 1][q];
+    double vx = c.x + s * tt.x - ox, vy = c.y + s * tt.y - oy;
+    double r = sqrt(vx * vx + vy * vy);
+    cplx z = r > 0 ? cplx{vx / r, -vy / r} : cplx{1, 0};   // e^{-i theta}
+    double J[PF_PMAX + 2];
+    bessel_j_array(k * r, p + 1, J);
+    cplx Jm[2 * PF_PMAX + 3];                               // J^-_n, n = -p-1..p+1
+    cplx zp{1, 0};
+    for (int n = 0; n <= p + 1; ++n) {
+      Jm[p + 1 + n] = J[n] * zp;
+      double sg = (n & 1) ? -1.0 : 1.0;
+      Jm[p + 1 - n] = (sg * J[n]) * conj(zp);
+      zp = zp * z;
+    }
+    cplx ph = dens[2 * f], va = dens[2 * f + 1];
+    cplx a = (cw * 0.5 * k) * ph;
+    cplx bcoef = (-eta * cw) * mul_i(va);
+    cplx nuc{nu.x, nu.y};
+    for (int n = -p; n <= p; ++n) {
+      cplx v = a * (conj(nuc) * Jm[p + n] - nuc * Jm[p + n + 2]) + bcoef * Jm[p + n + 1];
+      double iw = 1.0 / wgt[n + p];
+      atomicAdd(&acc[2 * (n + p)], v.re * iw);
+      atomicAdd(&acc[2 * (n + p) + 1], v.im * iw);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < P; i += blockDim.x) Mout[(size_t)box * P + i] = cplx{acc[2 * i], acc[2 * i + 1]};
+}
+
+// ---------------------------------------------------------------- M2M (FP64)
+// M(parent) = sum_children A_q M(child), A_q[n][m] = J^-_{n-m}(k(O_child - O_parent)) w^c_m / w^p_n.
+__global__ void m2m_f64_kernel(const int* __restrict__ ne, int P, int Pc, const cplx* __restrict__ A,
+                               const int* __restrict__ cbb, const int* __restrict__ cbe,
+                               const cplx* __restrict__ Mc, cplx* __restrict__ Mp) {
+  const int box = ne[blockIdx.x];
+  __shared__ cplx sm[PF_NCOEF];
+  cplx acc{0, 0};
+  for (int q = 0; q < 4; ++q) {
+    int ch = 4 * box + q;
+    if (cbb[ch] >= cbe[ch]) continue;   // empty child (uniform across the block)
+    __syncthreads();
+    for (int i = threadIdx.x; i < Pc; i += blockDim.x) sm[i] = Mc[(size_t)ch * Pc + i];
+    __syncthreads();
+    if (threadIdx.x < P) {
+      const cplx* row = A + ((size_t)q * P + threadIdx.x) * Pc;
+      for (int m = 0; m < Pc; ++m) acc += row[m] * sm[m];
+    }
+  }
+  if (threadIdx.x < P) Mp[(size_t)box * P + threadIdx.x] = acc;
+}
+
+// ------------------------------------------------------- L2L + M2L (FP64)
+// L(box) = B_q L(parent) + sum_{(C, o, m) in IL(box)} alpha^m T_o M(C)
+// (Sec. 3.2: M2L with the Toeplitz H^+_{n-l} operators shared by all boxes at
+// the same offset o, and L2L with J^+_{l-n}); at the root, L = R M(root) with
+// the lattice-sum operator R (Sec. 3.3).
+__global__ void local_f64_kernel(const int* __restrict__ ne, int D_unused, int P, int Pp,
+                                 const cplx* __restrict__ B, const cplx* __restrict__ Lp,
+                                 const int* __restrict__ ilp, const int* __restrict__ ils,
+                                 const int* __restrict__ ilo, const int* __restrict__ ilm,
+                                 const cplx* __restrict__ T, const cplx* __restrict__ Mlev,
+                                 const cplx* __restrict__ root, cplx alpha, cplx* __restrict__ Lout) {
+  const int ti = blockIdx.x;
+  const int box = ne[ti];
+  __shared__ cplx sm[PF_NCOEF];
+  cplx acc{0, 0};
+  const int l = threadIdx.x;
+  if (root) {   // level 0
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sm[i] = Mlev[i];
+    __syncthreads();
+    if (l < P)
+      for (int n = 0; n < P; ++n) acc += root[(size_t)l * P + n] * sm[n];
+    if (l < P) Lout[l] = acc;
+    return;
+  }
+  // L2L from the parent
+  {
+    int par = box >> 2, q = box & 3;
+    for (int i = threadIdx.x; i < Pp; i += blockDim.x) sm[i] = Lp[(size_t)par * Pp + i];
+    __syncthreads();
+    if (l < P) {
+      const cplx* row = B + ((size_t)q * P + l) * Pp;
+      for (int m = 0; m < Pp; ++m) acc += row[m] * sm[m];
+    }
+  }
+  // M2L
+  for (int e = ilp[ti]; e < ilp[ti + 1]; ++e) {
+    int src = ils[e], off = ilo[e];
+    cplx ph = ipow_phase(alpha, ilm[e]);
+    __syncthreads();
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sm[i] = ph * Mlev[(size_t)src * P + i];
+    __syncthreads();
+    if (l < P) {
+      const cplx* row = T + ((size_t)off * P + l) * P;
+      for (int n = 0; n < P; ++n) acc += row[n] * sm[n];
+    }
+  }
+  if (l < P) Lout[(size_t)box * P + l] = acc;
+}
+
+// ---------------------------------------------------------------- L2P (FP64)
+// U'(x) = (i/4) sum_l L_l J^+_l(k(x - O_D)),
+// dU'(x) = (i/4)(k/2) sum_l L_l (-conj(nu) J^+_{l+1} + nu J^+_{l-1}).
+__global__ void l2p_f64_kernel(const int* __restrict__ ne, const int* __restrict__ bb, const int* __restrict__ be,
+                               int D, double d, int p, const double* __restrict__ wgt, double k,
+                               double x0, double y0, const double2* __restrict__ sc, const double2* __restrict__ snu,
+                               const cplx* __restrict__ L, cplx* __restrict__ U) {
+  const int box = ne[blockIdx.x];
+  const int P = 2 * p + 1;
+  __shared__ cplx sl[PF_NCOEF];
+  for (int i = threadIdx.x; i < P; i += blockDim.x) sl[i] = (1.0 / wgt[i]) * L[(size_t)box * P + i];
+  __syncthreads();
+  int ix = 0, iy = 0;
+  for (int b = 0; b < D; ++b) {
+    ix |= ((box >> (2 * b)) & 1) << b;
+    iy |= ((box >> (2 * b + 1)) & 1) << b;
+  }
+  const double ox = x0 + (ix + 0.5) * d, oy = y0 + (iy + 0.5) * d;
+  for (int s = bb[box] + threadIdx.x; s < be[box]; s += blockDim.x) {
+    double2 c = sc[s], nu = snu[s];
+    double vx = c.x - ox, vy = c.y - oy;
+    double r = sqrt(vx * vx + vy * vy);
+    cplx z = r > 0 ? cplx{vx / r, vy / r} : cplx{1, 0};    // e^{+i theta}
+    double J[PF_PMAX + 2];
+    bessel_j_array(k * r, p + 1, J);
+    cplx nuc{nu.x, nu.y};
+    cplx u{0, 0}, du{0, 0};
+    // J^+_l = J_l z^l (l >= 0), J^+_{-l} = (-1)^l J_l conj(z)^l
+    cplx zp{1, 0};
+    for (int l = 0; l <= p + 1; ++l) {
+      cplx jp = J[l] * zp;                                 // J^+_l
+      cplx jn = ((l & 1) ? -J[l] : J[l]) * conj(zp);       // J^+_{-l}
+      if (l <= p) {
+        u += sl[p + l] * jp;
+        if (l > 0) u += sl[p - l] * jn;
+      }
+      // coefficient L_m contributes -conj(nu) J^+_{m+1} + nu J^+_{m-1}
+      //   J^+_l appears as J^+_{m+1} for m = l - 1 and as J^+_{m-1} for m = l + 1
+      if (l - 1 >= -p && l - 1 <= p) du -= conj(nuc) * (sl[p + l - 1] * jp);
+      if (l + 1 <= p) du += nuc * (sl[p + l + 1] * jp);
+      if (l > 0) {
+        // J^+_{-l}: as J^+_{m+1} for m = -l - 1, as J^+_{m-1} for m = -l + 1
+        if (-l - 1 >= -p) du -= conj(nuc) * (sl[p - l - 1] * jn);
+        if (-l + 1 <= p) du += nuc * (sl[p - l + 1] * jn);
+      }
+      zp = zp * z;
+    }
+    U[2 * s] = mul_i(0.25 * u);
+    U[2 * s + 1] = mul_i((0.125 * k) * du);
+  }
+}
+
+// ---------------------------------------------------------------- near field (FP64)
+// Direct element integrals over the <= 9 neighbouring leaves (with their
+// periodic images m = -1, 0, 1 and phases alpha^m); the self element is skipped
+// (its integrals are added in the combine step).  One warp per target.
+__global__ void near_f64_kernel(const int* __restrict__ ne, const int* __restrict__ bb, const int* __restrict__ be,
+                                const int* __restrict__ nlp, const int* __restrict__ nls, const int* __restrict__ nlm,
+                                double k, double eta, double H, cplx alpha,
+                                const double2* __restrict__ sc, const double2* __restrict__ st,
+                                const double2* __restrict__ snu, const double* __restrict__ sh,
+                                const cplx* __restrict__ dens, cplx* __restrict__ U) {
+  const int li = blockIdx.x;
+  const int box = ne[li];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int s = bb[box] + warp; s < be[box]; s += nw) {
+    double2 x = sc[s], nx = snu[s];
+    cplx u{0, 0}, du{0, 0};
+    for (int e = nlp[li]; e < nlp[li + 1]; ++e) {
+      int src = nls[e], m = nlm[e];
+      cplx ph = ipow_phase(alpha, m);
+      double shift = m * H;
+      cplx uu{0, 0}, dd{0, 0};
+      for (int f = bb[src] + lane; f < be[src]; f += 32) {
+        if (f == s && m == 0) continue;
+        double2 c = sc[f];
+        c.y += shift;
+        double hh = sh[f];
+        double q = sqrt((x.x - c.x) * (x.x - c.x) + (x.y - c.y) * (x.y - c.y)) / hh;
+        int g = gl_order(q, 0);
+        cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
+        pair4_f64(k, x, nx, c, st[f], snu[f], hh, g, S, Dv, K, T);
+        cplx phi = dens[2 * f], vphi = dens[2 * f + 1];
+        // (i/4)(D phi - i eta S varphi), (i/4)(T phi - i eta K varphi)
+        uu += Dv * phi - eta * mul_i(S * vphi);
+        dd += T * phi - eta * mul_i(K * vphi);
+      }
+      u += ph * uu;
+      du += ph * dd;
+    }
+    u = warp_sum(u);
+    du = warp_sum(du);
+    if (lane == 0) {
+      U[2 * s] += mul_i(0.25 * u);
+      U[2 * s + 1] += mul_i(0.25 * du);
+    }
+  }
+}
+
+// ------------------------------------------------- fiber-local k1 + combine (FP64)
+// V, dV over the target's own fiber (free-space k1 kernel, eq. 5), then eq. 9.
+__global__ void fiber_combine_f64_kernel(int E, const int* __restrict__ fib, const int* __restrict__ foff,
+                                         double k1, double eta, double rho, cplx c2,
+                                         const double2* __restrict__ oc, const double2* __restrict__ ot,
+                                         const double2* __restrict__ onu, const double* __restrict__ oh,
+                                         const int* __restrict__ opos, const cplx* __restrict__ sph,
+                                         const cplx* __restrict__ self4, const cplx* __restrict__ x,
+                                         const cplx* __restrict__ U, cplx* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e >= E) return;
+  const int fb = fib[e];
+  const double2 xe = oc[e], nxe = onu[e];
+  cplx v{0, 0}, dv{0, 0};
+  for (int f = foff[fb] + lane; f < foff[fb + 1]; f += 32) {
+    if (f == e) continue;
+    double2 c = oc[f];
+    double hh = oh[f];
+    double q = sqrt((xe.x - c.x) * (xe.x - c.x) + (xe.y - c.y) * (xe.y - c.y)) / hh;
+    int g = gl_order(q, 0);
+    cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
+    pair4_f64(k1, xe, nxe, c, ot[f], onu[f], hh, g, S, Dv, K, T);
+    cplx phi = x[2 * f], vphi = x[2 * f + 1];
+    v += Dv * phi - eta * mul_i(S * vphi);
+    dv += T * phi - eta * mul_i(K * vphi);
+  }
+  v = warp_sum(v);
+  dv = warp_sum(dv);
+  if (lane == 0) {
+    v = mul_i(0.25 * v);
+    dv = mul_i(0.25 * dv);
+    const cplx phi = x[2 * e], vphi = x[2 * e + 1];
+    const int s = opos[e];
+    const cplx po = cdiv(cplx{1, 0}, sph[s]);   // alpha^{m0}
+    cplx u = po * U[2 * s], du = po * U[2 * s + 1];
+    const cplx Sk = self4[4 * e], Tk = self4[4 * e + 1], Sk1 = self4[4 * e + 2], Tk1 = self4[4 * e + 3];
+    u += -eta * mul_i(Sk * vphi);
+    du += Tk * phi;
+    v += -eta * mul_i(Sk1 * vphi);
+    dv += Tk1 * phi;
+    y[2 * e] = phi - v + u;
+    y[2 * e + 1] = vphi + c2 * (du - rho * dv);
+  }
+}
+
+// ---------------------------------------------------------------- matvec driver
+static inline int round32(int n) { return ((n + 31) / 32) * 32; }
+
+cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision) {
+  (void)precision;
+  cudaStream_t st = h->stream;
+  const int E = h->E, D = h->D;
+  gather_dens_kernel<<<(E + 255) / 256, 256, 0, st>>>(E, h->s_perm, h->s_ph, x, h->dens);
+  Level& leaf = h->lev[D];
+  p2m_f64_kernel<<<leaf.nne, 128, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, D, leaf.d, leaf.p, leaf.w_dev,
+                                            h->g_far, h->k, h->eta, h->x0, h->y0, h->s_c, h->s_t, h->s_nu, h->s_h,
+                                            h->dens, leaf.M);
+  for (int l = D - 1; l >= 0; --l) {
+    Level& a = h->lev[l];
+    Level& c = h->lev[l + 1];
+    m2m_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, c.P, a.m2m, c.box_begin, c.box_end, c.M, a.M);
+  }
+  cplx alpha = h->alpha;
+  {
+    Level& r = h->lev[0];
+    local_f64_kernel<<<1, round32(r.P), 0, st>>>(r.ne, 0, r.P, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                 nullptr, r.M, h->root, alpha, r.L);
+  }
+  for (int l = 1; l <= D; ++l) {
+    Level& a = h->lev[l];
+    Level& pa = h->lev[l - 1];
+    local_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, 0, a.P, pa.P, pa.l2l, pa.L, a.il_ptr, a.il_src, a.il_off,
+                                                     a.il_img, a.m2l, a.M, nullptr, alpha, a.L);
+  }
+  l2p_f64_kernel<<<leaf.nne, 64, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, D, leaf.d, leaf.p, leaf.w_dev, h->k,
+                                          h->x0, h->y0, h->s_c, h->s_nu, leaf.L, h->U);
+  near_f64_kernel<<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nl_ptr, h->nl_src, h->nl_img,
+                                            h->k, h->eta, h->H, alpha, h->s_c, h->s_t, h->s_nu, h->s_h, h->dens, h->U);
+  cplx c2{h->c2re, h->c2im};
+  fiber_combine_f64_kernel<<<(E * 32 + 255) / 256, 256, 0, st>>>(E, h->o_fiber, h->fib_off, h->k1, h->eta, h->rho, c2,
+                                                                 h->o_c, h->o_t, h->o_nu, h->o_h, h->o_pos, h->s_ph,
+                                                                 h->self4, x, h->U, y);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- rhs
+__global__ void rhs_kernel(int E, double k, double dx, double dy, cplx c2, const double2* __restrict__ oc,
+                           const double2* __restrict__ onu, cplx* __restrict__ B) {
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  double2 c = oc[e], nu = onu[e];
+  double ph = k * (c.x * dx + c.y * dy);
+  double s, co;
+  sincos(ph, &s, &co);
+  cplx u{co, s};
+  cplx dn = mul_i((k * (nu.x * dx + nu.y * dy)) * u);
+  B[2 * e] = -u;
+  B[2 * e + 1] = -(c2 * dn);
+}
+
+cudaError_t k_rhs(pfmbem* h, cplx* B) {
+  cplx c2{h->c2re, h->c2im};
+  rhs_kernel<<<(h->E + 255) / 256, 256, 0, h->stream>>>(h->E, h->k, cos(h->theta), sin(h->theta), c2, h->o_c, h->o_nu, B);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- BLAS-1 for GMRES
+// out[c] = sum_t conj(V[c][t]) w[t] for c < ncol (out zeroed by the caller).
+__global__ void multidot_kernel(const cplx* __restrict__ V, int n, const cplx* __restrict__ w, cplx* __restrict__ out) {
+  const int c = blockIdx.y;
+  const cplx* v = V + (size_t)c * n;
+  cplx acc{0, 0};
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) acc += conj(v[t]) * w[t];
+  acc = warp_sum(acc);
+  __shared__ cplx red[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (wid == 0) {
+    acc = lane < (blockDim.x >> 5) ? red[lane] : cplx{0, 0};
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      atomicAdd(&out[c].re, acc.re);
+      atomicAdd(&out[c].im, acc.im);
+    }
+  }
+}
+
+cudaError_t k_multidot(pfmbem* h, const cplx* V, int ncol, const cplx* w, int n, cplx* out) {
+  cudaMemsetAsync(out, 0, sizeof(cplx) * ncol, h->stream);
+  int bx = (n + 255) / 256;
+  if (bx > 64) bx = 64;
+  dim3 grid(bx, ncol);
+  multidot_kernel<<<grid, 256, 0, h->stream>>>(V, n, w, out);
+  return cudaGetLastError();
+}
+
+__global__ void gemv_kernel(const cplx* __restrict__ V, int ncol, int n, const cplx* __restrict__ coef, double sign,
+                            cplx* __restrict__ w) {
+  __shared__ cplx cs[256];
+  for (int i = threadIdx.x; i < ncol; i += blockDim.x) cs[i] = coef[i];
+  __syncthreads();
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) {
+    cplx acc{0, 0};
+    for (int c = 0; c < ncol; ++c) acc += V[(size_t)c * n + t] * cs[c];
+    w[t] += sign * acc;
+  }
+}
+
+cudaError_t k_gemv_sub(pfmbem* h, const cplx* V, int ncol, const cplx* coef, cplx* w, int n) {
+  gemv_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(V, ncol, n, coef, -1.0, w);
+  return cudaGetLastError();
+}
+cudaError_t k_gemv_add(pfmbem* h, const cplx* V, int ncol, const cplx* coef, cplx* y, int n) {
+  gemv_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(V, ncol, n, coef, 1.0, y);
+  return cudaGetLastError();
+}
+
+__global__ void norm2_kernel(const cplx* __restrict__ v, int n, double* __restrict__ out) {
+  double acc = 0;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += gridDim.x * blockDim.x) acc += abs2(v[t]);
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  __shared__ double red[32];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) red[wid] = acc;
+  __syncthreads();
+  if (wid == 0) {
+    acc = lane < (blockDim.x >> 5) ? red[lane] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) atomicAdd(out, acc);
+  }
+}
+
+cudaError_t k_norm2(pfmbem* h, const cplx* v, int n, double* out) {
+  cudaMemsetAsync(out, 0, sizeof(double), h->stream);
+  int bx = (n + 255) / 256;
+  if (bx > 128) bx = 128;
+  norm2_kernel<<<bx, 256, 0, h->stream>>>(v, n, out);
+  return cudaGetLastError();
+}
+
+__global__ void scale_copy_kernel(const cplx* __restrict__ s, cplx a, cplx* __restrict__ d, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) d[t] = a * s[t];
+}
+cudaError_t k_scale_copy(pfmbem* h, const cplx* src, cplx s, cplx* dst, int n) {
+  scale_copy_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(src, s, dst, n);
+  return cudaGetLastError();
+}
+__global__ void axpy_kernel(cplx a, const cplx* __restrict__ x, cplx* __restrict__ y, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) y[t] += a * x[t];
+}
+cudaError_t k_axpy(pfmbem* h, cplx a, const cplx* x, cplx* y, int n) {
+  axpy_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(a, x, y, n);
+  return cudaGetLastError();
+}
+__global__ void sub_kernel(const cplx* __restrict__ a, const cplx* __restrict__ b, cplx* __restrict__ o, int n) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) o[t] = a[t] - b[t];
+}
+cudaError_t k_sub(pfmbem* h, const cplx* a, const cplx* b, cplx* out, int n) {
+  sub_kernel<<<(n + 255) / 256, 256, 0, h->stream>>>(a, b, out, n);
+  return cudaGetLastError();
+}

@@ -1,0 +1,198 @@
+"""ctypes binding of the pfmbem C ABI (include/pfmbem.h).
+
+Argument marshalling only: every computation runs in libpfmbem.so.  Buffers may
+be torch tensors (CPU or CUDA), numpy arrays, or raw integer addresses; complex
+vectors are complex128 (interleaved re/im doubles).  Loading fails loudly when
+the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpfmbem.so")
+
+FP64, MIXED = 0, 1
+STATUS = {0: "OK", 1: "EINVAL", 2: "EGEOM", 3: "EWOOD", 4: "ENOMEM", 5: "ECUDA", 6: "ENOCONV", 7: "ETIMEOUT",
+          8: "ENUMERIC"}
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("p_min", ctypes.c_int), ("eta", ctypes.c_double),
+                ("leaf_max", ctypes.c_int), ("depth", ctypes.c_int), ("gmres_m", ctypes.c_int),
+                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("restarts", ctypes.c_int), ("rel_residual", ctypes.c_double),
+                ("ms", ctypes.c_double), ("status", ctypes.c_int)]
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_int), ("M", ctypes.c_int), ("depth", ctypes.c_int), ("p", ctypes.c_int * 16),
+                ("nleaf_nonempty", ctypes.c_int), ("m2l_pairs", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
+                ("near_quad", ctypes.c_int64), ("fiber_pairs", ctypes.c_int64), ("fiber_quad", ctypes.c_int64),
+                ("p2m_nodes", ctypes.c_int), ("lattice_q", ctypes.c_int), ("root_x0", ctypes.c_double),
+                ("root_y0", ctypes.c_double), ("setup_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpfmbem.so is not built ({LIB_PATH}); run paper_1910_10863_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        sigs = {
+            "pfmbem_create": ([i, vp, vp, d, i, d, d, d, d, vp, vp, vp], i),
+            "pfmbem_destroy": ([vp], None),
+            "pfmbem_last_error": ([vp], ctypes.c_char_p),
+            "pfmbem_plan": ([vp, vp], i),
+            "pfmbem_rhs": ([vp, vp], i),
+            "pfmbem_matvec": ([vp, vp, vp, i], i),
+            "pfmbem_solve": ([vp, vp, vp, i, d, i, vp], i),
+            "pfmbem_field": ([vp, vp, i, vp, vp], i),
+            "pfmbem_coefficients": ([vp, vp, i, vp, vp, vp, vp, vp], i),
+            "pfmbem_lattice_sums": ([vp, i, vp], i),
+            "pfmbem_self_terms": ([vp, vp], i),
+        }
+        for name, (args, res) in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+    return _lib
+
+
+def addr(buf) -> int | None:
+    """Address of a torch tensor, numpy array or integer (None passes NULL)."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):
+        return buf.data_ptr()
+    if isinstance(buf, np.ndarray):
+        return buf.ctypes.data
+    raise TypeError(f"unsupported buffer type {type(buf)}")
+
+
+class PfmbemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _check(h, st):
+    if st != 0:
+        msg = lib().pfmbem_last_error(h).decode() if h else ""
+        raise PfmbemError(st, msg)
+
+
+def pfmbem_create(M, nodes_per_fiber, nodes_xy, H, lattice, k, k1, rho_ratio, theta, opt=None, stream=None):
+    """Returns an opaque handle (int).  nodes_per_fiber int32[M], nodes_xy float64[sum N, 2]."""
+    h = ctypes.c_void_p()
+    st = lib().pfmbem_create(int(M), addr(nodes_per_fiber), addr(nodes_xy), float(H), int(lattice), float(k),
+                             float(k1), float(rho_ratio), float(theta),
+                             ctypes.byref(opt) if opt is not None else None, stream, ctypes.byref(h))
+    if st != 0:
+        msg = lib().pfmbem_last_error(h).decode() if h.value else ""
+        if h.value:
+            lib().pfmbem_destroy(h)
+        raise PfmbemError(st, msg)
+    return h.value
+
+
+def pfmbem_destroy(h):
+    lib().pfmbem_destroy(h)
+
+
+def pfmbem_plan(h) -> PlanInfo:
+    info = PlanInfo()
+    _check(h, lib().pfmbem_plan(h, ctypes.byref(info)))
+    return info
+
+
+def pfmbem_rhs(h, B):
+    _check(h, lib().pfmbem_rhs(h, addr(B)))
+
+
+def pfmbem_matvec(h, x, y, precision=FP64):
+    _check(h, lib().pfmbem_matvec(h, addr(x), addr(y), int(precision)))
+
+
+def pfmbem_solve(h, B, psi, use_guess=False, tol=1e-8, maxit=1000, check=True) -> Info:
+    info = Info()
+    st = lib().pfmbem_solve(h, addr(B), addr(psi), int(bool(use_guess)), float(tol), int(maxit), ctypes.byref(info))
+    if check:
+        _check(h, st)
+    return info
+
+
+def pfmbem_lattice_sums(h, jmax, S):
+    _check(h, lib().pfmbem_lattice_sums(h, int(jmax), addr(S)))
+
+
+def pfmbem_self_terms(h, out):
+    _check(h, lib().pfmbem_self_terms(h, addr(out)))
+
+
+def pfmbem_field(h, psi, pts, u):
+    _check(h, lib().pfmbem_field(h, addr(psi), int(len(pts)), addr(pts), addr(u)))
+
+
+def pfmbem_coefficients(h, psi, max_orders=64):
+    n = ctypes.c_int(0)
+    orders = np.zeros(max_orders, dtype=np.int32)
+    R = np.zeros(max_orders, dtype=np.complex128)
+    T = np.zeros(max_orders, dtype=np.complex128)
+    en = ctypes.c_double(0)
+    _check(h, lib().pfmbem_coefficients(h, addr(psi), max_orders, ctypes.byref(n), addr(orders), addr(R), addr(T),
+                                        ctypes.byref(en)))
+    c = n.value
+    return orders[:c], R[:c], T[:c], en.value
+
+
+class Solver:
+    """Owns one pfmbem handle for a workload (see workloads.Workload)."""
+
+    def __init__(self, w, opt: Options | None = None, stream=None, **kw):
+        if opt is None:
+            opt = Options()
+        for key, val in kw.items():
+            setattr(opt, key, val)
+        self.w = w
+        self._npf = np.ascontiguousarray(w.nodes_per_fiber, dtype=np.int32)
+        self._nodes = np.ascontiguousarray(w.nodes, dtype=np.float64)
+        self.h = pfmbem_create(w.M, self._npf, self._nodes, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta,
+                               opt, stream)
+        self.E = int(self._npf.sum())
+
+    def close(self):
+        if self.h:
+            pfmbem_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def plan(self):
+        return pfmbem_plan(self.h)
+
+    def matvec(self, x, y, precision=FP64):
+        pfmbem_matvec(self.h, x, y, precision)
+
+    def rhs(self, B):
+        pfmbem_rhs(self.h, B)
+
+    def solve(self, psi, B=None, tol=1e-8, maxit=1000, use_guess=False, check=True):
+        return pfmbem_solve(self.h, B, psi, use_guess, tol, maxit, check)
