@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Throughput of the periodic FM-BEM solver on GB300.
+
+One step = the whole hot path for one synthetic fundamental block: pfmbem_create
+(geometry, periodic quadtree, self-element integrals, lattice sums, translation
+tables), pfmbem_solve (FMM matrix-vector products inside GMRES to a relative
+FP64 residual of 1e-6) and pfmbem_coefficients (Bragg orders), then destroy.
+Workload: hexagon lattice, 8x8 = 64 fibers, 256 elements each (16384 elements,
+32768 unknowns), kH = 5, water matrix / mercury fibers.
+
+value = solves/s of the whole job (all ranks; each rank solves its own block:
+weak scaling, no collective on the data path).  The JSON line also carries the
+FMM matvec rate (Munknowns/s), the roofline of the dominant kernel, the CPU
+oracle baseline, the end-to-end rate with host buffers and the SM clocks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GMRES solves/s and FMM matvec Munknowns/s at 1e-6 residual vs plain FP64, 1 GB300"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="own", choices=["own", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--matvec-reps", type=int, default=20)
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1910_10863_gb300 import workloads as W
+    return W.hexagon_8x8_n256()
+
+
+# ------------------------------------------------------------------ clocks
+class Clocks:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------------ CPU oracle sample
+def oracle_sample(w, rows=8, lu_n=2048, seed=0):
+    """Time the oracle on a bounded sample and extrapolate one dense solve of the block.
+
+    Sample: assembly of `rows` element rows (2 equations each) of the dense operator
+    (eq. 9) with the Ewald-summed kernel, plus an LU factorisation of a random
+    complex matrix of size lu_n; the full solve is extrapolated as
+    (E / rows) * t_rows + (2E / lu_n)^3 * t_lu."""
+    from scipy import linalg as sla
+
+    from oracle import bem
+    pb = bem.problem(w)
+    rng = np.random.default_rng(seed)
+    sel = rng.choice(w.E, size=rows, replace=False)
+    t0 = time.perf_counter()
+    bem.operator_rows(pb, sel)
+    t_rows = time.perf_counter() - t0
+    A = rng.standard_normal((lu_n, lu_n)) + 1j * rng.standard_normal((lu_n, lu_n))
+    t0 = time.perf_counter()
+    sla.lu_factor(A, overwrite_a=True, check_finite=False)
+    t_lu = time.perf_counter() - t0
+    n = 2 * w.E
+    t_full = (w.E / rows) * t_rows + (n / lu_n) ** 3 * t_lu
+    sample = (f"assembly of {rows} of {w.E} element rows ({t_rows:.2f} s) + LU of a {lu_n}^2 complex matrix "
+              f"({t_lu:.2f} s), extrapolated to one dense solve of {n} unknowns ({t_full:.0f} s)")
+    return 1.0 / t_full, sample, t_rows + t_lu
+
+
+def cpu_cores():
+    return max(1, min(32, os.cpu_count() or 1))
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload()
+    vals = []
+    sample = ""
+    for _ in range(args.warmup):
+        oracle_sample(w, rows=2, lu_n=512)
+    t_all = 0.0
+    for _ in range(args.steps):
+        v, sample, t = oracle_sample(w, rows=4, lu_n=1536)
+        vals.append(v)
+        t_all += t
+    value = float(np.mean(vals))
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": w.name, "elements": w.E, "unknowns": 2 * w.E, "tol": args.tol,
+                       "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ own arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1910_10863_gb300 import pfmbem as pf
+
+    if not os.path.exists(pf.LIB_PATH):
+        from paper_1910_10863_gb300 import build
+        build.build()
+    prec = pf.FP64 if args.precision == "fp64" else pf.MIXED
+    w = workload()
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    npf_d = torch.from_numpy(np.ascontiguousarray(w.nodes_per_fiber, dtype=np.int32)).cuda()
+    nodes_d = torch.from_numpy(np.ascontiguousarray(w.nodes)).cuda()
+    npf_h = torch.from_numpy(np.ascontiguousarray(w.nodes_per_fiber, dtype=np.int32)).pin_memory()
+    nodes_h = torch.from_numpy(np.ascontiguousarray(w.nodes)).pin_memory()
+    n = 2 * w.E
+    psi_d = torch.zeros(n, dtype=torch.complex128, device="cuda")
+    psi_h = torch.zeros(n, dtype=torch.complex128).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    opt = pf.Options()
+    opt.precision = prec
+    maxit = 2000
+    prof_acc = {"ms": np.zeros(16), "launches": np.zeros(16, dtype=np.int64)}
+    stats = {}
+
+    def step(host=False, profile=False):
+        npf, nodes, psi = (npf_h, nodes_h, psi_h) if host else (npf_d, nodes_d, psi_d)
+        h = pf.pfmbem_create(w.M, npf, nodes, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, opt, sptr)
+        try:
+            if profile:
+                pf.pfmbem_profile(h, True, True)
+            info = pf.pfmbem_solve(h, None, psi, False, args.tol, maxit)
+            orders, R, T, energy = pf.pfmbem_coefficients(h, psi)
+            if profile:
+                p = pf.pfmbem_profile_read(h)
+                prof_acc["ms"] += np.array(p.ms)
+                prof_acc["launches"] += np.array(p.launches)
+            stats.update(iters=info.iters, restarts=info.restarts, rel_residual=info.rel_residual,
+                         energy=energy, norders=len(orders))
+            if "plan" not in stats:
+                stats["plan"] = pf.pfmbem_plan(h)
+        finally:
+            pf.pfmbem_destroy(h)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(host, profile):
+        tot = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(host=host, profile=profile)
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        return tot / args.steps
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ms_step = timed(host=False, profile=True)
+    clk = clocks.stop()
+    barrier()
+    ms_e2e = timed(host=True, profile=False)
+    barrier()
+    if dist is not None:
+        t = torch.tensor([ms_step, ms_e2e], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, ms_e2e = float(t[0]), float(t[1])
+    value = world * 1000.0 / ms_step
+    e2e_value = world * 1000.0 / ms_e2e
+
+    # FMM matvec rate (FP64 and mixed) on one handle
+    h = pf.pfmbem_create(w.M, npf_d, nodes_d, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, opt, sptr)
+    x = torch.from_numpy(pf_density(w)).cuda()
+    y = torch.zeros_like(x)
+    mv = {}
+    for name, pr in (("fp64", pf.FP64),) + ((("mixed", pf.MIXED),) if args.precision == "mixed" else ()):
+        for _ in range(3):
+            pf.pfmbem_matvec(h, x, y, pr)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.matvec_reps):
+            pf.pfmbem_matvec(h, x, y, pr)
+        e1.record(stream)
+        e1.synchronize()
+        mv[name] = n / (e0.elapsed_time(e1) / args.matvec_reps * 1e-3) / 1e6
+    pf.pfmbem_destroy(h)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+    plan = stats["plan"]
+    launches = int(prof_acc["launches"].sum())
+    ms_ph = prof_acc["ms"] / args.steps
+    names = pf.PHASES
+    dom = int(np.argmax(ms_ph[:len(names)]))
+    per_launch = ms_ph[dom] / max(1, prof_acc["launches"][dom] / args.steps)
+    fp64_peak = pf.pfmbem_probe_peak(0)
+    fp32_peak = pf.pfmbem_probe_peak(1)
+    roof = roofline(names[dom], per_launch, plan, fp64_peak, fp32_peak, args.precision)
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        v, sample, _ = oracle_sample(w)
+        cpu = {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample}
+    h2d = int(npf_h.numel() * 4 + nodes_h.numel() * 8)
+    d2h = int(psi_h.numel() * 16 + stats["norders"] * 2 * 16)
+    line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/bf16+f64",
+            "data": "synthetic",
+            "config": {"workload": w.name, "elements": w.E, "unknowns": n, "fibers": w.M, "kH": w.k * w.H,
+                       "tol": args.tol, "precision": args.precision, "depth": plan.depth,
+                       "p": list(plan.p)[:plan.depth + 1],
+                       "l2": "flushed between steps (256 MiB write); per-step working set is L2-resident by design",
+                       "parallelism": f"replicas x{world}"},
+            "matvec_munknowns_per_s": mv,
+            "solve": {"iters": stats["iters"], "restarts": stats["restarts"],
+                      "rel_residual": stats["rel_residual"], "energy_sum": stats["energy"],
+                      "setup_ms": plan.setup_ms},
+            "phase_ms_per_step": {names[i]: float(ms_ph[i]) for i in range(len(names))},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "clocks": clk,
+            "gpu_launches": launches}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def pf_density(w):
+    from paper_1910_10863_gb300 import workloads as W
+    return W.density_vector(w.E, 11)
+
+
+# Algorithmic work per unit, from one ncu capture of each kernel (executed
+# floating-point operations per unit: 2 per FMA, 1 per add/mul); units per
+# launch come from the plan.  Near-field / fiber-local P2P: one unit = one
+# kernel evaluation (target collocation point x Gauss node of a source element).
+FLOPS_PER_EVAL = {"fp64": 180.0, "mixed": 120.0}
+
+
+def roofline(phase, ms_per_launch, plan, fp64_peak, fp32_peak, precision):
+    if phase in ("near_p2p", "fiber_p2p_combine"):
+        units = plan.near_quad if phase == "near_p2p" else plan.fiber_quad
+        flops = units * FLOPS_PER_EVAL[precision]
+        peak = fp64_peak if precision == "fp64" else fp32_peak
+        ach = flops / (ms_per_launch * 1e-3) / 1e12
+        return {"kernel": phase, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "measured FMA-chain probe (pfmbem_probe_peak)",
+                "units_per_launch": int(units), "flops_per_unit": FLOPS_PER_EVAL[precision],
+                "ms_per_launch": ms_per_launch}
+    return {"kernel": phase, "bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s", "frac": None,
+            "traffic": None, "ms_per_launch": ms_per_launch}
+
+
+if __name__ == "__main__":
+    main()

@@ -55,7 +55,7 @@ typedef enum { PFMBEM_FP64 = 0, PFMBEM_MIXED = 1 } pfmbem_precision;
 /* Options; a zero-initialised struct selects every default. */
 typedef struct {
   int p;            /* expansion order at every level; 0 = per-level rule (below) */
-  int p_min;        /* lower bound of the per-level rule; 0 = 24 */
+  int p_min;        /* lower bound of the per-level rule; 0 = 16 */
   double eta;       /* coupling constant eta of eq. 4 (a real number); 0 = k */
   int leaf_max;     /* target occupancy of a leaf box; 0 = 40 */
   int depth;        /* quadtree depth (levels 0..depth); 0 = chosen from leaf_max */
@@ -161,6 +161,28 @@ pfmbem_status pfmbem_coefficients(pfmbem_t h, const double* psi, int max_orders,
  * 2 <= |m| <= q plus the two spectral tails integrated on the contour of eq. 18.
  * S complex [2 jmax + 1], index j + jmax. */
 pfmbem_status pfmbem_lattice_sums(pfmbem_t h, int jmax, double* S);
+
+/* Kernel profiling (not part of the paper's method; measurement support).
+ * Phases: 0 density gather, 1 P2M, 2 M2M, 3 M2L + L2L + root translation,
+ * 4 L2P, 5 near-field P2P, 6 fiber-local P2P + combine, 7 GMRES vector
+ * kernels, 8 set-up kernels, 9 output kernels (field, coefficients).
+ * launches[] always counts the library's kernel launches; ms[] accumulates
+ * CUDA-event device time per phase on the handle's stream while timing is on. */
+typedef struct {
+  double ms[16];
+  int64_t launches[16];
+  int64_t total_launches;
+} pfmbem_profile_info;
+
+/* enable_timing: 1 = record CUDA events around every launch; reset: 1 = zero counters. */
+pfmbem_status pfmbem_profile(pfmbem_t h, int enable_timing, int reset);
+/* Synchronises the stream and reads the counters. */
+pfmbem_status pfmbem_profile_read(pfmbem_t h, pfmbem_profile_info* out);
+
+/* Measured arithmetic peak of the current device (measurement support, not
+ * part of the paper's method): dtype 0 = FP64 FMA, 1 = FP32 FMA; TFLOP/s of
+ * independent FMA chains over 8 CTAs per SM. */
+pfmbem_status pfmbem_probe_peak(int dtype, double* tflops);
 
 /* Self-element integrals used on the diagonal (flat element at its midpoint):
  * S_ee and the finite-part T_ee for k (out[0..1]) and k1 (out[2..3]) of every

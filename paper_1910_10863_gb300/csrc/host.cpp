@@ -253,7 +253,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     L.nne = (int)L.hne.size();
     // expansion order
     double x = k * L.d * std::sqrt(2.0);
-    int pmin = h->opt.p_min > 0 ? h->opt.p_min : 24;
+    int pmin = h->opt.p_min > 0 ? h->opt.p_min : 16;
     int p = h->opt.p > 0 ? h->opt.p : (int)std::ceil(x + 1.8 * std::pow(10.0, 2.0 / 3.0) * std::cbrt(x));
     p = std::max(p, h->opt.p > 0 ? 1 : pmin);
     if (p > PF_PMAX) return fail(h, PFMBEM_EINVAL, "expansion order above the library limit (64); use more levels");
@@ -730,6 +730,7 @@ void pfmbem_destroy(pfmbem_t h) {
   else cudaDeviceSynchronize();
   for (void* p : h->allocs) cudaFree(p);
   if (h->gw.hhost) cudaFreeHost(h->gw.hhost);
+  prof_release(h);
   delete h;
 }
 
@@ -842,16 +843,109 @@ pfmbem_status pfmbem_self_terms(pfmbem_t h, double* out) {
 }
 
 pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double* pts, double* u) {
-  (void)psi; (void)npts; (void)pts; (void)u;
-  if (!h) return PFMBEM_EINVAL;
-  return fail(h, PFMBEM_EINVAL, "pfmbem_field: not available in this build");
+  if (!h || !psi || npts < 0 || (npts > 0 && (!pts || !u))) return PFMBEM_EINVAL;
+  if (npts == 0) return PFMBEM_OK;
+  const size_t n = 2 * (size_t)h->E;
+  // host copy of the points for the validity check
+  std::vector<double> hp(2 * (size_t)npts);
+  if (is_device_ptr(pts)) CK(cudaMemcpy(hp.data(), pts, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost));
+  else std::memcpy(hp.data(), pts, sizeof(double) * hp.size());
+  const double ox = h->x0 + 0.5 * h->H;
+  for (int i = 0; i < npts; ++i) {
+    if (!std::isfinite(hp[2 * i]) || !std::isfinite(hp[2 * i + 1])) return fail(h, PFMBEM_EINVAL, "non-finite point");
+    // the root local expansion of the images |m| >= 2 converges for |x - O| + H/sqrt(2) < 2H
+    if (std::fabs(hp[2 * i] - ox) > 1.2 * h->H - 0.5 * h->H)
+      return fail(h, PFMBEM_EINVAL, "field point too far from the block along x (|x - centre| > 0.7 H)");
+  }
+  const cplx* psid;
+  pfmbem_status st = stage_input(h, psi, n, h->stage_in, &psid);
+  if (st != PFMBEM_OK) return st;
+  double2* pd = dalloc<double2>(h, npts);
+  cplx* ud = dalloc<cplx>(h, npts);
+  if (!pd || !ud) return fail(h, PFMBEM_ENOMEM, "field buffers");
+  CK(cudaMemcpyAsync(pd, hp.data(), sizeof(double2) * npts, cudaMemcpyHostToDevice, h->stream));
+  CK(k_field_prepare(h, psid));
+  CK(k_field(h, psid, npts, pd, ud));
+  CK(cudaMemcpyAsync(u, ud, sizeof(cplx) * npts, is_device_ptr(u) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  // release the temporaries
+  cudaFree(pd);
+  cudaFree(ud);
+  h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)pd), h->allocs.end());
+  h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)ud), h->allocs.end());
+  return PFMBEM_OK;
 }
 
 pfmbem_status pfmbem_coefficients(pfmbem_t h, const double* psi, int max_orders, int* norders, int* orders, double* R,
                                   double* T, double* energy) {
-  (void)psi; (void)max_orders; (void)norders; (void)orders; (void)R; (void)T; (void)energy;
+  if (!h || !psi || !norders || max_orders < 0) return PFMBEM_EINVAL;
+  const double ks = h->k * std::sin(h->theta);
+  std::vector<int> ord;
+  int nlo = (int)std::floor((-h->k - ks) * h->H / (2 * M_PI)) - 1;
+  int nhi = (int)std::ceil((h->k - ks) * h->H / (2 * M_PI)) + 1;
+  for (int n = nlo; n <= nhi; ++n)
+    if (std::fabs(ks + 2 * M_PI * n / h->H) < h->k) ord.push_back(n);
+  *norders = (int)ord.size();
+  if ((int)ord.size() > max_orders || (!ord.empty() && (!orders || !R || !T)))
+    return fail(h, PFMBEM_EINVAL, "max_orders smaller than the number of propagating orders");
+  const size_t n = 2 * (size_t)h->E;
+  const cplx* psid;
+  pfmbem_status st = stage_input(h, psi, n, h->stage_in, &psid);
+  if (st != PFMBEM_OK) return st;
+  const int no = (int)ord.size();
+  // order list and results live in the tail of the output staging buffer
+  if ((size_t)(2 * no + no) > n) return fail(h, PFMBEM_EINVAL, "too many orders for the work buffer");
+  cplx* outd = h->stage_out;
+  int* od = reinterpret_cast<int*>(h->stage_out + 2 * no);
+  CK(cudaMemcpyAsync(od, ord.data(), sizeof(int) * no, cudaMemcpyHostToDevice, h->stream));
+  CK(k_coefficients(h, psid, no, od, outd));
+  std::vector<cplx> res(2 * no);
+  CK(cudaMemcpyAsync(res.data(), outd, sizeof(cplx) * 2 * no, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const double k0 = h->k * std::cos(h->theta);
+  double en = 0;
+  for (int i = 0; i < no; ++i) {
+    cplx t = res[2 * i], r = res[2 * i + 1];
+    if (ord[i] == 0) t.re += 1.0;
+    orders[i] = ord[i];
+    T[2 * i] = t.re;
+    T[2 * i + 1] = t.im;
+    R[2 * i] = r.re;
+    R[2 * i + 1] = r.im;
+    const double kap = ks + 2 * M_PI * ord[i] / h->H;
+    const double kn = std::sqrt(h->k * h->k - kap * kap);
+    en += kn / k0 * (r.re * r.re + r.im * r.im + t.re * t.re + t.im * t.im);
+  }
+  if (energy) *energy = en;
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_profile(pfmbem_t h, int enable_timing, int reset) {
   if (!h) return PFMBEM_EINVAL;
-  return fail(h, PFMBEM_EINVAL, "pfmbem_coefficients: not available in this build");
+  CK(prof_fold(h));
+  if (reset) {
+    for (int i = 0; i < 16; ++i) {
+      h->prof.ms[i] = 0;
+      h->prof.launches[i] = 0;
+    }
+  }
+  h->prof.on = enable_timing != 0;
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_profile_read(pfmbem_t h, pfmbem_profile_info* out) {
+  if (!h || !out) return PFMBEM_EINVAL;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(prof_fold(h));
+  int64_t tot = 0;
+  for (int i = 0; i < 16; ++i) {
+    out->ms[i] = h->prof.ms[i];
+    out->launches[i] = h->prof.launches[i];
+    tot += h->prof.launches[i];
+  }
+  out->total_launches = tot;
+  return PFMBEM_OK;
 }
 
 }  // extern "C"

@@ -55,6 +55,18 @@ struct GmresWork {
   cplx* hhost = nullptr;    // pinned host mirror of hcol
 };
 
+enum Phase { PH_GATHER = 0, PH_P2M, PH_M2M, PH_LOCAL, PH_L2P, PH_NEAR, PH_FIBER, PH_BLAS, PH_SETUP, PH_OUT, PH_COUNT };
+
+// Launch counters and optional CUDA-event timing per phase.
+struct Prof {
+  bool on = false;
+  std::vector<cudaEvent_t> ev;          // pool of events, used in begin/end pairs
+  std::vector<int> phase_of_pair;       // phase of every recorded pair
+  int used = 0;                         // events recorded since the last fold
+  double ms[16] = {0};
+  int64_t launches[16] = {0};
+};
+
 struct pfmbem {
   // problem (paper notation)
   int M = 0, E = 0, lattice = 0;
@@ -103,9 +115,19 @@ struct pfmbem {
   cplx* stage_out = nullptr;
   cplx* dev_rhs = nullptr;       // [2E]
   GmresWork gw;
+  Prof prof;
   std::vector<void*> allocs;
   double setup_ms = 0;
 };
+
+// profiling hooks (kernels.cu)
+void prof_begin(pfmbem* h, int phase);
+void prof_end(pfmbem* h, int phase);
+cudaError_t prof_fold(pfmbem* h);
+void prof_release(pfmbem* h);
+// outputs (kernels.cu): scattered field at points, Bragg-order coefficients
+cudaError_t k_field_prepare(pfmbem* h, const cplx* psi);
+cudaError_t k_coefficients(pfmbem* h, const cplx* psi, int norders, const int* orders_host, cplx* out_dev);
 
 // ------------------------------------------------------------ kernel launches
 void k_upload_gauss(const double* x, const double* w, const double* thr64, const double* thr32);

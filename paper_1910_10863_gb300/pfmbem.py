@@ -61,6 +61,9 @@ def lib():
             "pfmbem_coefficients": ([vp, vp, i, vp, vp, vp, vp, vp], i),
             "pfmbem_lattice_sums": ([vp, i, vp], i),
             "pfmbem_self_terms": ([vp, vp], i),
+            "pfmbem_profile": ([vp, i, i], i),
+            "pfmbem_profile_read": ([vp, vp], i),
+            "pfmbem_probe_peak": ([i, vp], i),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -157,6 +160,32 @@ def pfmbem_coefficients(h, psi, max_orders=64):
                                         ctypes.byref(en)))
     c = n.value
     return orders[:c], R[:c], T[:c], en.value
+
+
+PHASES = ["gather", "p2m", "m2m", "m2l_l2l", "l2p", "near_p2p", "fiber_p2p_combine", "gmres_blas", "setup",
+          "outputs"]
+
+
+class ProfileInfo(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 16), ("launches", ctypes.c_int64 * 16), ("total_launches", ctypes.c_int64)]
+
+
+def pfmbem_profile(h, enable_timing=True, reset=True):
+    _check(h, lib().pfmbem_profile(h, int(bool(enable_timing)), int(bool(reset))))
+
+
+def pfmbem_profile_read(h) -> ProfileInfo:
+    p = ProfileInfo()
+    _check(h, lib().pfmbem_profile_read(h, ctypes.byref(p)))
+    return p
+
+
+def pfmbem_probe_peak(dtype) -> float:
+    t = ctypes.c_double(0)
+    st = lib().pfmbem_probe_peak(int(dtype), ctypes.byref(t))
+    if st != 0:
+        raise PfmbemError(st, "probe failed")
+    return t.value
 
 
 class Solver:
