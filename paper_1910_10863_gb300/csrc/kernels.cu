@@ -277,6 +277,72 @@ cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev) {
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------- lattice sums, allocation-free variant
+// Same kernel as above, but its device results land in a fixed array that lives
+// in this library's device image instead of in memory the caller or a handle
+// allocates.  Every GPU that loads the library holds the array until exit.
+#define PF_NOALLOC_JMAX 128
+static __device__ __align__(256) cplx g_lattice_scratch[PF_NOALLOC_JMAX + 1];
+static cplx* g_lattice_scratch_dev[64];    // device address of the array, per device ordinal
+static bool g_lattice_scratch_ready[64];
+
+__global__ void symmetric_expand_kernel(const cplx* __restrict__ half, int jmax, cplx* __restrict__ full) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i <= 2 * jmax) full[i] = half[abs(i - jmax)];
+}
+
+extern "C" pfmbem_status pfmbem_lattice_sums_noalloc(double k, double H, double theta, int jmax, void* cuda_stream,
+                                                     double* S) {
+  if (!S || !(k > 0) || !(H > 0) || !isfinite(theta)) return PFMBEM_EINVAL;
+  if (jmax < 0 || jmax > PF_NOALLOC_JMAX) return PFMBEM_EINVAL;   // beyond the fixed array
+  {
+    const double s = sin(theta);
+    double dmin = 1e300;
+    for (double v : {k * H * (1 + s), k * H * (1 - s)}) dmin = fmin(dmin, fabs(v - 2 * M_PI * round(v / (2 * M_PI))));
+    if (dmin < 1e-3) return PFMBEM_EWOOD;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PFMBEM_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  if (!g_lattice_scratch_ready[dev]) {
+    // one-time set-up on this device: Gauss rules for the contour integral and
+    // the device address of the fixed array (host code may not use its name)
+    double x[PF_GLMAX * PF_GLMAX] = {0}, w[PF_GLMAX * PF_GLMAX] = {0};
+    for (int g = 1; g <= PF_GLMAX; ++g) gauss_legendre(g, &x[(g - 1) * PF_GLMAX], &w[(g - 1) * PF_GLMAX]);
+    if (cudaMemcpyToSymbol(c_glx, x, sizeof(x)) != cudaSuccess) return PFMBEM_ECUDA;
+    if (cudaMemcpyToSymbol(c_glw, w, sizeof(w)) != cudaSuccess) return PFMBEM_ECUDA;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_lattice_scratch) != cudaSuccess) return PFMBEM_ECUDA;
+    g_lattice_scratch_dev[dev] = static_cast<cplx*>(p);
+    g_lattice_scratch_ready[dev] = true;
+  }
+  cplx* scratch = g_lattice_scratch_dev[dev];
+  const int q = 8;
+  const double beta = k * H * sin(theta);
+  const double V = lattice_vmax(jmax, q, k, H);
+  if (cudaMemsetAsync(scratch, 0, sizeof(cplx) * (jmax + 1), st) != cudaSuccess) return PFMBEM_ECUDA;
+  lattice_sum_kernel<<<jmax + 1, 256, 0, st>>>(jmax, q, k, H, beta, V, scratch);
+  if (cudaGetLastError() != cudaSuccess) return PFMBEM_ECUDA;
+  cudaPointerAttributes a;
+  bool sdev = cudaPointerGetAttributes(&a, S) == cudaSuccess &&
+              (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+  cudaGetLastError();
+  if (sdev) {
+    symmetric_expand_kernel<<<(2 * jmax + 1 + 127) / 128, 128, 0, st>>>(scratch, jmax, reinterpret_cast<cplx*>(S));
+    if (cudaGetLastError() != cudaSuccess) return PFMBEM_ECUDA;
+    return PFMBEM_OK;
+  }
+  cplx half[PF_NOALLOC_JMAX + 1];
+  if (cudaMemcpyAsync(half, scratch, sizeof(cplx) * (jmax + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return PFMBEM_ECUDA;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return PFMBEM_ECUDA;
+  for (int j = -jmax; j <= jmax; ++j) {
+    S[2 * (j + jmax)] = half[abs(j)].re;
+    S[2 * (j + jmax) + 1] = half[abs(j)].im;
+  }
+  return PFMBEM_OK;
+}
+
 // ---------------------------------------------------------------- pair integrals
 // Element integrals of (i/4)H0(kap|x-y|) (S), its d/dnu_y (D), d/dnu_x (K) and
 // d2/dnu_x dnu_y (T) over the flat element c + s t, |s| <= h/2, by g-point

@@ -64,6 +64,7 @@ def lib():
             "pfmbem_profile": ([vp, i, i], i),
             "pfmbem_profile_read": ([vp, vp], i),
             "pfmbem_probe_peak": ([i, vp], i),
+            "pfmbem_lattice_sums_noalloc": ([d, d, d, i, vp, vp], i),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -140,6 +141,13 @@ def pfmbem_solve(h, B, psi, use_guess=False, tol=1e-8, maxit=1000, check=True) -
 
 def pfmbem_lattice_sums(h, jmax, S):
     _check(h, lib().pfmbem_lattice_sums(h, int(jmax), addr(S)))
+
+
+def pfmbem_lattice_sums_noalloc(k, H, theta, jmax, S, stream=None):
+    """Lattice sums without a handle or any device allocation (see include/pfmbem.h)."""
+    st = lib().pfmbem_lattice_sums_noalloc(float(k), float(H), float(theta), int(jmax), stream, addr(S))
+    if st != 0:
+        raise PfmbemError(st, "pfmbem_lattice_sums_noalloc failed")
 
 
 def pfmbem_self_terms(h, out):
