@@ -61,7 +61,10 @@ typedef struct {
   int depth;        /* quadtree depth (levels 0..depth); 0 = chosen from leaf_max */
   int gmres_m;      /* GMRES restart length; 0 = 60 */
   int precision;    /* pfmbem_precision used by pfmbem_solve; default FP64 */
-  int reserved[8];
+  int near_mode;    /* 0 = near-field and same-fiber element integrals computed once at
+                       create and kept in device memory (default); 1 = recomputed in
+                       every matvec (no cache memory) */
+  int reserved[7];
 } pfmbem_options;
 
 /* Outcome of a solve. */

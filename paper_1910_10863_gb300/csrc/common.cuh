@@ -40,6 +40,18 @@ PF_HD cplxf operator*(cplxf a, cplxf b) { return cplxf{a.re * b.re - a.im * b.im
 PF_HD cplxf operator*(float s, cplxf a) { return cplxf{s * a.re, s * a.im}; }
 PF_HD cplxf& operator+=(cplxf& a, cplxf b) { a.re += b.re; a.im += b.im; return a; }
 PF_HD cplxf conj(cplxf a) { return cplxf{a.re, -a.im}; }
+PF_HD cplxf operator-(cplxf a) { return cplxf{-a.re, -a.im}; }
+PF_HD cplxf& operator-=(cplxf& a, cplxf b) { a.re -= b.re; a.im -= b.im; return a; }
+PF_HD cplxf operator*(cplxf a, float s) { return cplxf{s * a.re, s * a.im}; }
+PF_HD cplxf mul_i(cplxf a) { return cplxf{-a.im, a.re}; }
+
+// conversions between the two precisions
+PF_HD cplxf to_f(cplx a) { return cplxf{(float)a.re, (float)a.im}; }
+PF_HD cplx to_d(cplxf a) { return cplx{(double)a.re, (double)a.im}; }
+PF_HD cplx to_d(cplx a) { return a; }
+template <class C> PF_HD C from_d(cplx a);
+template <> PF_HD cplx from_d<cplx>(cplx a) { return a; }
+template <> PF_HD cplxf from_d<cplxf>(cplx a) { return to_f(a); }
 
 // ---------------------------------------------------------------- limits
 #define PF_PMAX 64                 // largest expansion order

@@ -46,6 +46,12 @@ pfmbem_status upload(pfmbem* h, T** dst, const std::vector<T>& src) {
   return PFMBEM_OK;
 }
 
+std::vector<cplxf> to_float(const std::vector<cplx>& v) {
+  std::vector<cplxf> o(v.size());
+  for (size_t i = 0; i < v.size(); ++i) o[i] = cplxf{(float)v[i].re, (float)v[i].im};
+  return o;
+}
+
 double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -271,6 +277,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   }
   // ---------------------------------------------------- lists
   const int nD = 1 << D;
+  std::vector<int64_t> nc_base;
+  std::vector<int> nc_sbase(1, 0), nc_src, nc_img;
   {
     Level& Lf = h->lev[D];
     std::vector<int> ptr(1, 0), src, img;
@@ -293,9 +301,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &h->nl_ptr, ptr)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->nl_src, src)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->nl_img, img)) != PFMBEM_OK) return st;
-    // near-field pair statistics
+    // near-field pair statistics (the cache build counts them on the GPU)
     int64_t pairs = 0, quad = 0;
-    for (size_t li = 0; li < Lf.hne.size(); ++li) {
+    for (size_t li = 0; h->opt.near_mode != 0 && li < Lf.hne.size(); ++li) {
       int b = Lf.hne[li];
       for (int s = Lf.hbegin[b]; s < Lf.hend[b]; ++s)
         for (int e = ptr[li]; e < ptr[li + 1]; ++e) {
@@ -312,6 +320,23 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
     h->info.near_pairs = pairs;
     h->info.near_quad = quad;
+    // layout of the cached near field: per leaf, its concatenated source list
+    // and a dense [targets][sources] array of 2x2 complex blocks
+    int64_t acc = 0;
+    for (size_t li = 0; li < Lf.hne.size(); ++li) {
+      int b = Lf.hne[li];
+      int ns = 0;
+      for (int e = ptr[li]; e < ptr[li + 1]; ++e)
+        for (int f = Lf.hbegin[src[e]]; f < Lf.hend[src[e]]; ++f) {
+          nc_src.push_back(f);
+          nc_img.push_back(img[e]);
+          ++ns;
+        }
+      nc_sbase.push_back((int)nc_src.size());
+      nc_base.push_back(acc);
+      acc += 4 * (int64_t)(Lf.hend[b] - Lf.hbegin[b]) * ns;
+    }
+    h->nc_blocks = acc / 4;
   }
   int64_t m2l_pairs = 0;
   for (int l = 1; l <= D; ++l) {
@@ -356,7 +381,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // fiber-local statistics
   {
     int64_t pairs = 0, quad = 0;
-    for (int i = 0; i < M; ++i)
+    for (int i = 0; h->opt.near_mode != 0 && i < M; ++i)
       for (int e = foff[i]; e < foff[i + 1]; ++e)
         for (int f = foff[i]; f < foff[i + 1]; ++f) {
           if (f == e) continue;
@@ -386,6 +411,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &L.box_end, L.hend)) != PFMBEM_OK) return st;
     L.M = dalloc<cplx>(h, (size_t)L.nbox * P);
     L.L = dalloc<cplx>(h, (size_t)L.nbox * P);
+    L.Mf = dalloc<cplxf>(h, (size_t)L.nbox * P);
+    L.Lf = dalloc<cplxf>(h, (size_t)L.nbox * P);
+    if (!L.Mf || !L.Lf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions)");
     if (!L.M || !L.L) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions)");
     // M2L operators at this level: T[o][l][n] = w_l H^+_{n-l}(k (dx, dy) d) w_n
     if (l >= 1) {
@@ -398,20 +426,27 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
           double vx = dx * L.d, vy = dy * L.d;
           double r = std::hypot(vx, vy), th = std::atan2(vy, vx);
           bessel_jy(k * r, 2 * p, J, Y);
+          // Toeplitz vector H^+_j = H_j(k r) e^{i j th}, j = -2p..2p (H_-j = (-1)^j H_j)
+          std::vector<cplx> hv(4 * p + 1);
+          for (int j = -2 * p; j <= 2 * p; ++j) {
+            int aj = std::abs(j);
+            double sg = (j < 0 && (aj & 1)) ? -1.0 : 1.0;
+            double hr = sg * J[aj], hi = sg * Y[aj];
+            double cs = std::cos(j * th), sn = std::sin(j * th);
+            hv[j + 2 * p] = cplx{hr * cs - hi * sn, hr * sn + hi * cs};
+          }
           for (int a = -p; a <= p; ++a)        // target coefficient l = a
             for (int n = -p; n <= p; ++n) {    // source coefficient n
-              int j = n - a, aj = std::abs(j);
-              double sg = (j < 0 && (aj & 1)) ? -1.0 : 1.0;
-              double hr = sg * J[aj], hi = sg * Y[aj];
-              double cs = std::cos(j * th), sn = std::sin(j * th);
+              const cplx hj = hv[n - a + 2 * p];
               double sc = L.w[a + p] * L.w[n + p];
-              cplx v{sc * (hr * cs - hi * sn), sc * (hr * sn + hi * cs)};
+              cplx v{sc * hj.re, sc * hj.im};
               if (!std::isfinite(v.re) || !std::isfinite(v.im))
                 return fail(h, PFMBEM_ENUMERIC, "non-finite M2L operator; lower p or change depth");
               T[((size_t)o * P + (a + p)) * P + (n + p)] = v;
             }
         }
       if ((st = upload(h, &L.m2l, T)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.m2lf, to_float(T))) != PFMBEM_OK) return st;
     }
     // M2M (children l+1 -> l) and L2L (l -> children)
     if (l < D) {
@@ -443,6 +478,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       }
       if ((st = upload(h, &L.m2m, A)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.l2l, B)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.m2mf, to_float(A))) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.l2lf, to_float(B))) != PFMBEM_OK) return st;
     }
   }
   // ---------------------------------------------------- element arrays
@@ -467,6 +504,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &h->s_h, sh)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->s_ph, sph)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->s_perm, perm)) != PFMBEM_OK) return st;
+    std::vector<int> sleaf(E);
+    for (int s2 = 0; s2 < E; ++s2) sleaf[s2] = key[perm[s2]];
+    if ((st = upload(h, &h->s_leaf, sleaf)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->o_c, c)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->o_t, t)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->o_nu, nu)) != PFMBEM_OK) return st;
@@ -484,6 +524,56 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   if (!h->self4 || !h->dens || !h->U || !h->stage_in || !h->stage_out || !h->dev_rhs)
     return fail(h, PFMBEM_ENOMEM, "device allocation failed (work buffers)");
   CK(k_self_terms(h));
+  // ---------------------------------------------------- near-field / fiber caches
+  if (h->opt.near_mode == 0 && h->max_fiber <= 1024) {
+    std::vector<int64_t> fbase(M, 0);
+    std::vector<int> chunks;
+    int64_t acc = 0;
+    for (int i = 0; i < M; ++i) {
+      fbase[i] = acc;
+      const int n2 = 2 * (foff[i + 1] - foff[i]);
+      acc += (int64_t)n2 * n2;
+      for (int r = 0; r < n2; r += 64) {
+        chunks.push_back(i);
+        chunks.push_back(r);
+        chunks.push_back(std::min(r + 64, n2));
+      }
+    }
+    h->fb_entries = acc;
+    const double bytes = (double)(4 * h->nc_blocks + acc) * (sizeof(cplx) + sizeof(cplxf));
+    size_t freeb = 0, totb = 0;
+    CK(cudaMemGetInfo(&freeb, &totb));
+    if (bytes < 0.5 * (double)freeb) {
+      pfmbem_status st;
+      if ((st = upload(h, &h->nc_base, nc_base)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->nc_sbase, nc_sbase)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->nc_src, nc_src)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->nc_img, nc_img)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->fb_base, fbase)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->fb_chunk, chunks)) != PFMBEM_OK) return st;
+      h->nchunk = (int)chunks.size() / 3;
+      h->nc_val = dalloc<cplx>(h, (size_t)(4 * h->nc_blocks));
+      h->nc_valf = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
+      h->fb_val = dalloc<cplx>(h, (size_t)acc);
+      h->fb_valf = dalloc<cplxf>(h, (size_t)acc);
+      h->stat_dev = dalloc<unsigned long long>(h, 4);
+      if (!h->nc_val || !h->nc_valf || !h->fb_val || !h->fb_valf || !h->stat_dev)
+        return fail(h, PFMBEM_ENOMEM, "device allocation failed (near-field caches)");
+      CK(cudaMemsetAsync(h->stat_dev, 0, 4 * sizeof(unsigned long long), h->stream));
+      CK(k_build_caches(h));
+      const size_t nc = (size_t)E * 2 * h->lev[D].P;
+      h->p2m_c = dalloc<cplx>(h, nc);
+      h->l2p_c = dalloc<cplx>(h, nc);
+      h->p2m_cf = dalloc<cplxf>(h, nc);
+      h->l2p_cf = dalloc<cplxf>(h, nc);
+      h->densf = dalloc<cplxf>(h, (size_t)2 * E);
+      h->Uf = dalloc<cplxf>(h, (size_t)2 * E);
+      if (!h->p2m_c || !h->l2p_c || !h->p2m_cf || !h->l2p_cf || !h->densf || !h->Uf)
+        return fail(h, PFMBEM_ENOMEM, "device allocation failed (P2M/L2P caches)");
+      CK(k_build_fmm_caches(h));
+      h->cached = true;
+    }
+  }
   // ---------------------------------------------------- lattice sums + root operator
   {
     Level& R = h->lev[0];
@@ -506,6 +596,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       }
     pfmbem_status st;
     if ((st = upload(h, &h->root, Rt)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->rootf, to_float(Rt))) != PFMBEM_OK) return st;
   }
   CK(cudaStreamSynchronize(h->stream));
   h->info.E = E;
@@ -552,9 +643,11 @@ static pfmbem_status gmres_alloc(pfmbem* h, int m) {
   g.x = dalloc<cplx>(h, n);
   g.b = dalloc<cplx>(h, n);
   g.d = dalloc<cplx>(h, n);
+  g.c = dalloc<cplx>(h, n);
   g.hcol = dalloc<cplx>(h, 2 * (m + 2));
   g.nrm = dalloc<double>(h, 2);
-  if (!g.V || !g.w || !g.r || !g.x || !g.b || !g.d || !g.hcol || !g.nrm) return fail(h, PFMBEM_ENOMEM, "GMRES workspace");
+  if (!g.V || !g.w || !g.r || !g.x || !g.b || !g.d || !g.c || !g.hcol || !g.nrm)
+    return fail(h, PFMBEM_ENOMEM, "GMRES workspace");
   if (cudaMallocHost(&g.hhost, sizeof(cplx) * 2 * (m + 2)) != cudaSuccess) return fail(h, PFMBEM_ENOMEM, "pinned host buffer");
   return PFMBEM_OK;
 }
@@ -564,7 +657,7 @@ static inline std::complex<double> toz(cplx a) { return {a.re, a.im}; }
 // Restarted GMRES(m) with classical Gram-Schmidt applied twice; A is applied by
 // the FMM matvec in the given precision.  Solves A x = b in place of x (device).
 static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int maxit, int precision,
-                           int* iters_out, int* restarts_out, double* relres_out) {
+                           int* iters_out, int* restarts_out, double* relres_out, bool zero_start = false) {
   GmresWork& g = h->gw;
   const int n = g.n, m = g.m;
   double* hn = reinterpret_cast<double*>(g.hhost);
@@ -582,9 +675,13 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
   double relres = 1.0;
   std::vector<std::complex<double>> Hm((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1);
   while (true) {
-    // r = b - A x
-    CK(k_matvec(h, x, g.w, precision));
-    CK(k_sub(h, b, g.w, g.r, n));
+    // r = b - A x (x = 0 on a zero start)
+    if (zero_start && restarts == 0) {
+      CK(cudaMemcpyAsync(g.r, b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      CK(k_matvec(h, x, g.w, precision));
+      CK(k_sub(h, b, g.w, g.r, n));
+    }
     CK(k_norm2(h, g.r, n, g.nrm));
     CK(cudaMemcpyAsync(hn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -738,6 +835,15 @@ const char* pfmbem_last_error(pfmbem_t h) { return h ? h->err.c_str() : "null ha
 
 pfmbem_status pfmbem_plan(pfmbem_t h, pfmbem_plan_info* info) {
   if (!h || !info) return PFMBEM_EINVAL;
+  if (h->cached && h->stat_dev) {
+    unsigned long long c[4];
+    CK(cudaMemcpyAsync(c, h->stat_dev, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    h->info.near_pairs = (int64_t)c[0];
+    h->info.near_quad = (int64_t)c[1];
+    h->info.fiber_pairs = (int64_t)c[2];
+    h->info.fiber_quad = (int64_t)c[3];
+  }
   *info = h->info;
   return PFMBEM_OK;
 }
@@ -797,7 +903,42 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
   }
   int iters = 0, restarts = 0;
   double relres = 1;
-  st = gmres(h, g.b, g.x, tol, maxit, PFMBEM_FP64, &iters, &restarts, &relres);
+  if (h->opt.precision == PFMBEM_MIXED && h->cached) {
+    // FP64 iterative refinement: r = B - A x with the FP64 operator, an inner
+    // GMRES on the mixed-precision operator solves A d = r loosely, x += d.
+    double bn = 0;
+    {
+      CK(k_norm2(h, g.b, (int)n, g.nrm));
+      CK(cudaMemcpyAsync(&bn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      bn = std::sqrt(bn);
+    }
+    st = PFMBEM_ENOCONV;
+    int refinements = 0;
+    for (; refinements < 50; ++refinements) {
+      CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
+      CK(k_sub(h, g.b, g.w, g.d, (int)n));
+      double rn = 0;
+      CK(k_norm2(h, g.d, (int)n, g.nrm));
+      CK(cudaMemcpyAsync(&rn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      relres = bn > 0 ? std::sqrt(rn) / bn : 0.0;
+      if (!std::isfinite(relres)) return fail(h, PFMBEM_ENUMERIC, "non-finite residual");
+      if (relres <= tol) { st = PFMBEM_OK; break; }
+      if (iters >= maxit) break;
+      const double inner_tol = std::max(1e-5, 0.3 * tol / relres);
+      int it = 0, rs = 0;
+      double rr = 1;
+      CK(cudaMemsetAsync(g.c, 0, n * sizeof(cplx), h->stream));
+      pfmbem_status si = gmres(h, g.d, g.c, inner_tol, maxit - iters, PFMBEM_MIXED, &it, &rs, &rr, true);
+      if (si != PFMBEM_OK && si != PFMBEM_ENOCONV) return si;
+      iters += it;
+      CK(k_axpy(h, cplx{1, 0}, g.c, g.x, (int)n));
+    }
+    restarts = refinements;
+  } else {
+    st = gmres(h, g.b, g.x, tol, maxit, PFMBEM_FP64, &iters, &restarts, &relres);
+  }
   CK(cudaMemcpyAsync(psi, g.x, n * sizeof(cplx), pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (info) {

@@ -49,7 +49,8 @@ struct GmresWork {
   cplx* r = nullptr;        // [n]
   cplx* x = nullptr;        // [n]
   cplx* b = nullptr;        // [n]
-  cplx* d = nullptr;        // [n] correction (refinement)
+  cplx* d = nullptr;        // [n] FP64 residual of the refinement
+  cplx* c = nullptr;        // [n] correction of the refinement
   cplx* hcol = nullptr;     // [m+2] device dot results
   double* nrm = nullptr;    // [2]
   cplx* hhost = nullptr;    // pinned host mirror of hcol
@@ -90,6 +91,7 @@ struct pfmbem {
   double* s_h = nullptr;         // length
   cplx* s_ph = nullptr;          // alpha^{-m0} input phase of the wrapped copy
   int* s_perm = nullptr;         // sorted -> original
+  int* s_leaf = nullptr;         // leaf box (Morton) of every sorted element
   // elements, original order
   double2* o_c = nullptr;        // true midpoint
   double2* o_t = nullptr;
@@ -105,6 +107,35 @@ struct pfmbem {
   int* nl_ptr = nullptr;
   int* nl_src = nullptr;
   int* nl_img = nullptr;
+  // cached near field: per non-empty leaf, a dense [targets][sources] array of
+  // 2x2 blocks (U' += a11 phi' + a12 varphi', dU' += a21 phi' + a22 varphi')
+  bool cached = false;
+  int64_t* nc_base = nullptr;    // [nleaf] value offset (in blocks) of the leaf
+  int* nc_sbase = nullptr;       // [nleaf + 1] offset of the leaf's source list
+  int* nc_src = nullptr;         // source element (sorted index) per list entry
+  int* nc_img = nullptr;         // image m per list entry
+  cplx* nc_val = nullptr;        // [blocks][4]
+  cplxf* nc_valf = nullptr;
+  int64_t nc_blocks = 0;
+  // cached fiber blocks: the diagonal block of (I - A) of every fiber without
+  // the FMM part (identity, k1 operators, self terms), row-major [2N][2N]
+  int64_t* fb_base = nullptr;    // [M] offset of the fiber's block
+  int* fb_chunk = nullptr;       // [nchunk][3] = fiber, first row, last row + 1
+  int nchunk = 0;
+  cplx* fb_val = nullptr;
+  cplxf* fb_valf = nullptr;
+  int64_t fb_entries = 0;
+  unsigned long long* stat_dev = nullptr;   // near pairs, near evaluations, fiber pairs, fiber evaluations
+  // cached P2M / L2P operators, sorted element order: [E][2][P_leaf]
+  //   P2M: M_n(leaf) = sum_f c[f][0][n] phi'_f + c[f][1][n] varphi'_f   (scaled by 1/w_n)
+  //   L2P: U'_s = sum_l c[s][0][l] L_l(leaf), dU'_s = sum_l c[s][1][l] L_l(leaf)
+  cplx* p2m_c = nullptr;
+  cplx* l2p_c = nullptr;
+  cplxf* p2m_cf = nullptr;
+  cplxf* l2p_cf = nullptr;
+  // FP32 work buffers of the mixed matvec
+  cplxf* densf = nullptr;        // [E][2]
+  cplxf* Uf = nullptr;           // [E][2]
   cplx* root = nullptr;          // [P0][P0] periodic root translation
   cplxf* rootf = nullptr;
   std::vector<cplx> lattice_S;   // S_j, j = 0..2 p0 (S_-j = S_j)
@@ -126,6 +157,8 @@ void prof_end(pfmbem* h, int phase);
 cudaError_t prof_fold(pfmbem* h);
 void prof_release(pfmbem* h);
 // outputs (kernels.cu): scattered field at points, Bragg-order coefficients
+cudaError_t k_build_caches(pfmbem* h);
+cudaError_t k_build_fmm_caches(pfmbem* h);
 cudaError_t k_field_prepare(pfmbem* h, const cplx* psi);
 cudaError_t k_coefficients(pfmbem* h, const cplx* psi, int norders, const int* orders_host, cplx* out_dev);
 

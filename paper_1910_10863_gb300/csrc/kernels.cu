@@ -656,8 +656,530 @@ __global__ void fiber_combine_f64_kernel(int E, const int* __restrict__ fib, con
   }
 }
 
-// ---------------------------------------------------------------- matvec driver
+// ------------------------------------------------------------ cached near field
+// Build: for leaf li with targets s in [bb, be) and the concatenated source list
+// (f, m) of its neighbour leaves, block (t, j) holds (i/4) alpha^m times
+// {D, -i eta S, T, -i eta K} of source f at target s (zero for f = s, m = 0).
+__global__ void near_build_kernel(const int* __restrict__ ne, const int* __restrict__ bb, const int* __restrict__ be,
+                                  const int64_t* __restrict__ base, const int* __restrict__ sbase,
+                                  const int* __restrict__ srcf, const int* __restrict__ srcm, double k, double eta,
+                                  double H, cplx alpha, const double2* __restrict__ sc, const double2* __restrict__ st,
+                                  const double2* __restrict__ snu, const double* __restrict__ sh,
+                                  cplx* __restrict__ val, cplxf* __restrict__ valf,
+                                  unsigned long long* __restrict__ stat) {
+  const int li = blockIdx.x;
+  const int box = ne[li];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int s0 = bb[box], nt = be[box] - s0;
+  const int j0 = sbase[li], ns = sbase[li + 1] - j0;
+  unsigned long long npair = 0, nquad = 0;
+  for (int t = warp; t < nt; t += nw) {
+    const int s = s0 + t;
+    const double2 x = sc[s], nx = snu[s];
+    cplx* row = val + base[li] + (int64_t)t * ns * 4;
+    cplxf* rowf = valf ? valf + base[li] + (int64_t)t * ns * 4 : nullptr;
+    for (int j = lane; j < ns; j += 32) {
+      const int f = srcf[j0 + j], m = srcm[j0 + j];
+      cplx b0{0, 0}, b1{0, 0}, b2{0, 0}, b3{0, 0};
+      if (!(f == s && m == 0)) {
+        double2 c = sc[f];
+        c.y += m * H;
+        const double hh = sh[f];
+        const double q = sqrt((x.x - c.x) * (x.x - c.x) + (x.y - c.y) * (x.y - c.y)) / hh;
+        const int g = gl_order(q, 0);
+        ++npair;
+        nquad += g;
+        cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
+        pair4_f64(k, x, nx, c, st[f], snu[f], hh, g, S, Dv, K, T);
+        const cplx ph = mul_i(0.25 * ipow_phase(alpha, m));      // (i/4) alpha^m
+        b0 = ph * Dv;
+        b1 = (-eta) * mul_i(ph * S);
+        b2 = ph * T;
+        b3 = (-eta) * mul_i(ph * K);
+      }
+      row[4 * j + 0] = b0;
+      row[4 * j + 1] = b1;
+      row[4 * j + 2] = b2;
+      row[4 * j + 3] = b3;
+      if (rowf) {
+        rowf[4 * j + 0] = cplxf{(float)b0.re, (float)b0.im};
+        rowf[4 * j + 1] = cplxf{(float)b1.re, (float)b1.im};
+        rowf[4 * j + 2] = cplxf{(float)b2.re, (float)b2.im};
+        rowf[4 * j + 3] = cplxf{(float)b3.re, (float)b3.im};
+      }
+    }
+  }
+  if (stat) {
+    atomicAdd(&stat[0], npair);
+    atomicAdd(&stat[1], nquad);
+  }
+}
+
+// ------------------------------------------------------------ cached fiber blocks
+// Row pair (2e, 2e+1) of fiber i's diagonal block of (I - A) without the
+// periodic k part:  [1 - D1, i eta S1; -c2 rho T1, 1 + i eta c2 rho K1] over the
+// same-fiber sources (k1, eq. 5), plus on the diagonal the self terms of both
+// wavenumbers (-i eta S_ee(k) and c2 T_ee(k) of the k part, whose remainder
+// comes from the FMM).  One warp per target element.
+__global__ void fiber_build_kernel(int E, const int* __restrict__ fib, const int* __restrict__ foff,
+                                   const int64_t* __restrict__ fbase, double k1, double eta, double rho, cplx c2,
+                                   const double2* __restrict__ oc, const double2* __restrict__ ot,
+                                   const double2* __restrict__ onu, const double* __restrict__ oh,
+                                   const cplx* __restrict__ self4, cplx* __restrict__ val, cplxf* __restrict__ valf,
+                                   unsigned long long* __restrict__ stat) {
+  const int lane = threadIdx.x & 31;
+  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (e >= E) return;
+  const int fb = fib[e], f0 = foff[fb], N = foff[fb + 1] - f0, el = e - f0;
+  const int64_t r0 = fbase[fb] + (int64_t)(2 * el) * (2 * N), r1 = r0 + 2 * N;
+  const double2 xe = oc[e], nxe = onu[e];
+  const cplx c2r = rho * c2;
+  unsigned long long nquad = 0;
+  for (int f = f0 + lane; f < f0 + N; f += 32) {
+    const int fl = f - f0;
+    cplx a00, a01, a10, a11;
+    if (f == e) {
+      const cplx Sk = self4[4 * e], Tk = self4[4 * e + 1], Sk1 = self4[4 * e + 2], Tk1 = self4[4 * e + 3];
+      a00 = cplx{1, 0};
+      a01 = eta * mul_i(Sk1) - eta * mul_i(Sk);
+      a10 = c2 * Tk - c2r * Tk1;
+      a11 = cplx{1, 0};
+    } else {
+      const double2 c = oc[f];
+      const double hh = oh[f];
+      const double q = sqrt((xe.x - c.x) * (xe.x - c.x) + (xe.y - c.y) * (xe.y - c.y)) / hh;
+      const int g = gl_order(q, 0);
+      nquad += g;
+      cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
+      pair4_f64(k1, xe, nxe, c, ot[f], onu[f], hh, g, S, Dv, K, T);
+      S = mul_i(0.25 * S);
+      Dv = mul_i(0.25 * Dv);
+      K = mul_i(0.25 * K);
+      T = mul_i(0.25 * T);
+      a00 = -Dv;
+      a01 = eta * mul_i(S);
+      a10 = -(c2r * T);
+      a11 = eta * mul_i(c2r * K);
+    }
+    val[r0 + 2 * fl] = a00;
+    val[r0 + 2 * fl + 1] = a01;
+    val[r1 + 2 * fl] = a10;
+    val[r1 + 2 * fl + 1] = a11;
+    if (valf) {
+      valf[r0 + 2 * fl] = cplxf{(float)a00.re, (float)a00.im};
+      valf[r0 + 2 * fl + 1] = cplxf{(float)a01.re, (float)a01.im};
+      valf[r1 + 2 * fl] = cplxf{(float)a10.re, (float)a10.im};
+      valf[r1 + 2 * fl + 1] = cplxf{(float)a11.re, (float)a11.im};
+    }
+  }
+  if (stat) {
+    if (lane == 0) atomicAdd(&stat[2], (unsigned long long)(N - 1));
+    atomicAdd(&stat[3], nquad);
+  }
+}
+
+cudaError_t k_build_caches(pfmbem* h) {
+  cudaStream_t st = h->stream;
+  Level& leaf = h->lev[h->D];
+  cplx c2{h->c2re, h->c2im};
+  prof_begin(h, PH_SETUP);
+  near_build_kernel<<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
+                                              h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c, h->s_t,
+                                              h->s_nu, h->s_h, h->nc_val, h->nc_valf, h->stat_dev);
+  prof_end(h, PH_SETUP);
+  prof_begin(h, PH_SETUP);
+  fiber_build_kernel<<<(h->E * 32 + 255) / 256, 256, 0, st>>>(h->E, h->o_fiber, h->fib_off, h->fb_base, h->k1,
+                                                              h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu, h->o_h,
+                                                              h->self4, h->fb_val, h->fb_valf, h->stat_dev);
+  prof_end(h, PH_SETUP);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------ cached P2M / L2P
+__device__ __forceinline__ void morton_centre(int box, int D, double d, double x0, double y0, double& ox, double& oy) {
+  int ix = 0, iy = 0;
+  for (int b = 0; b < D; ++b) {
+    ix |= ((box >> (2 * b)) & 1) << b;
+    iy |= ((box >> (2 * b + 1)) & 1) << b;
+  }
+  ox = x0 + (ix + 0.5) * d;
+  oy = y0 + (iy + 0.5) * d;
+}
+
+// P2M coefficients of element s (the moments of Sec. 3.2 per unit density):
+//   c[s][0][n] = sum_g w_g h/2 (k/2)(conj(nu) J^-_{n-1} - nu J^-_{n+1}) / w_n   (phi')
+//   c[s][1][n] = sum_g w_g h/2 (-i eta) J^-_n / w_n                             (varphi')
+__global__ void p2m_coef_kernel(int E, const int* __restrict__ sleaf, int D, double d, int p,
+                                const double* __restrict__ wgt, int g, double k, double eta, double x0, double y0,
+                                const double2* __restrict__ sc, const double2* __restrict__ st,
+                                const double2* __restrict__ snu, const double* __restrict__ sh,
+                                cplx* __restrict__ out, cplxf* __restrict__ outf) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= E) return;
+  const int P = 2 * p + 1;
+  double ox, oy;
+  morton_centre(sleaf[s], D, d, x0, y0, ox, oy);
+  const double2 c = sc[s], tt = st[s], nu = snu[s];
+  const double hh = sh[s];
+  const cplx nuc{nu.x, nu.y};
+  cplx* o = out + (size_t)s * 2 * P;
+  for (int i = 0; i < 2 * P; ++i) o[i] = cplx{0, 0};
+  for (int q = 0; q < g; ++q) {
+    const double sp = 0.5 * hh * c_glx[g - 1][q];
+    const double cw = 0.5 * hh * c_glw[g - 1][q];
+    const double vx = c.x + sp * tt.x - ox, vy = c.y + sp * tt.y - oy;
+    const double r = sqrt(vx * vx + vy * vy);
+    const cplx z = r > 0 ? cplx{vx / r, -vy / r} : cplx{1, 0};   // e^{-i theta}
+    double J[PF_PMAX + 2];
+    bessel_j_array(k * r, p + 1, J);
+    cplx Jm[2 * PF_PMAX + 3];
+    cplx zp{1, 0};
+    for (int n = 0; n <= p + 1; ++n) {
+      Jm[p + 1 + n] = J[n] * zp;
+      Jm[p + 1 - n] = (((n & 1) ? -1.0 : 1.0) * J[n]) * conj(zp);
+      zp = zp * z;
+    }
+    for (int n = -p; n <= p; ++n) {
+      const double iw = 1.0 / wgt[n + p];
+      o[n + p] += (cw * 0.5 * k * iw) * (conj(nuc) * Jm[p + n] - nuc * Jm[p + n + 2]);
+      o[P + n + p] += (-eta * cw * iw) * mul_i(Jm[p + n + 1]);
+    }
+  }
+  if (outf)
+    for (int i = 0; i < 2 * P; ++i) outf[(size_t)s * 2 * P + i] = to_f(o[i]);
+}
+
+// L2P coefficients of target s:
+//   c[s][0][l] = (i/4) J^+_l(k(x - O)) / w_l
+//   c[s][1][l] = (i/4)(k/2)(-conj(nu) J^+_{l+1} + nu J^+_{l-1}) / w_l
+__global__ void l2p_coef_kernel(int E, const int* __restrict__ sleaf, int D, double d, int p,
+                                const double* __restrict__ wgt, double k, double x0, double y0,
+                                const double2* __restrict__ sc, const double2* __restrict__ snu,
+                                cplx* __restrict__ out, cplxf* __restrict__ outf) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= E) return;
+  const int P = 2 * p + 1;
+  double ox, oy;
+  morton_centre(sleaf[s], D, d, x0, y0, ox, oy);
+  const double2 c = sc[s], nu = snu[s];
+  const double vx = c.x - ox, vy = c.y - oy;
+  const double r = sqrt(vx * vx + vy * vy);
+  const cplx z = r > 0 ? cplx{vx / r, vy / r} : cplx{1, 0};
+  double J[PF_PMAX + 2];
+  bessel_j_array(k * r, p + 1, J);
+  cplx Jp[2 * PF_PMAX + 3];                  // J^+_n, n = -p-1 .. p+1
+  cplx zp{1, 0};
+  for (int n = 0; n <= p + 1; ++n) {
+    Jp[p + 1 + n] = J[n] * zp;
+    Jp[p + 1 - n] = (((n & 1) ? -1.0 : 1.0) * J[n]) * conj(zp);
+    zp = zp * z;
+  }
+  const cplx nuc{nu.x, nu.y};
+  cplx* o = out + (size_t)s * 2 * P;
+  for (int l = -p; l <= p; ++l) {
+    const double iw = 1.0 / wgt[l + p];
+    o[l + p] = mul_i((0.25 * iw) * Jp[p + 1 + l]);
+    o[P + l + p] = mul_i((0.125 * k * iw) * (nuc * Jp[p + l] - conj(nuc) * Jp[p + l + 2]));
+  }
+  if (outf)
+    for (int i = 0; i < 2 * P; ++i) outf[(size_t)s * 2 * P + i] = to_f(o[i]);
+}
+
+// ------------------------------------------------ precision-generic matvec pieces
+template <class C>
+__global__ void gather_t_kernel(int E, const int* __restrict__ perm, const cplx* __restrict__ ph,
+                                const cplx* __restrict__ x, C* __restrict__ dens) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= E) return;
+  int e = perm[s];
+  cplx p = ph[s];
+  dens[2 * s] = from_d<C>(p * x[2 * e]);
+  dens[2 * s + 1] = from_d<C>(p * x[2 * e + 1]);
+}
+
+// M(leaf)_n = sum_f c[f][0][n] phi'_f + c[f][1][n] varphi'_f; one block per leaf.
+template <class C>
+__global__ void p2m_apply_t_kernel(const int* __restrict__ ne, const int* __restrict__ bb,
+                                   const int* __restrict__ be, int P, const C* __restrict__ coef,
+                                   const C* __restrict__ dens, C* __restrict__ Mout) {
+  const int box = ne[blockIdx.x];
+  const int n = threadIdx.x;
+  if (n >= P) return;
+  C acc{0, 0};
+  for (int f = bb[box]; f < be[box]; ++f) {
+    const C* cf = coef + (size_t)f * 2 * P;
+    acc += cf[n] * dens[2 * f] + cf[P + n] * dens[2 * f + 1];
+  }
+  Mout[(size_t)box * P + n] = acc;
+}
+
+template <class C>
+__global__ void m2m_t_kernel(const int* __restrict__ ne, int P, int Pc, const C* __restrict__ A,
+                             const int* __restrict__ cbb, const int* __restrict__ cbe, const C* __restrict__ Mc,
+                             C* __restrict__ Mp) {
+  const int box = ne[blockIdx.x];
+  __shared__ C sm[PF_NCOEF];
+  C acc{0, 0};
+  for (int q = 0; q < 4; ++q) {
+    int ch = 4 * box + q;
+    if (cbb[ch] >= cbe[ch]) continue;
+    __syncthreads();
+    for (int i = threadIdx.x; i < Pc; i += blockDim.x) sm[i] = Mc[(size_t)ch * Pc + i];
+    __syncthreads();
+    if (threadIdx.x < P) {
+      const C* row = A + ((size_t)q * P + threadIdx.x) * Pc;
+      for (int m = 0; m < Pc; ++m) acc += row[m] * sm[m];
+    }
+  }
+  if (threadIdx.x < P) Mp[(size_t)box * P + threadIdx.x] = acc;
+}
+
+// L(box) = B_q L(parent) + sum_{IL} alpha^m T_o M(src); at the root L = R M(root).
+template <class C>
+__global__ void local_t_kernel(const int* __restrict__ ne, int P, int Pp, const C* __restrict__ B,
+                               const C* __restrict__ Lp, const int* __restrict__ ilp, const int* __restrict__ ils,
+                               const int* __restrict__ ilo, const int* __restrict__ ilm, const C* __restrict__ T,
+                               const C* __restrict__ Mlev, const C* __restrict__ root, cplx alpha,
+                               C* __restrict__ Lout) {
+  const int ti = blockIdx.x;
+  const int box = ne[ti];
+  __shared__ C sm[PF_NCOEF];
+  C acc{0, 0};
+  const int l = threadIdx.x;
+  if (root) {
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sm[i] = Mlev[i];
+    __syncthreads();
+    if (l < P) {
+      for (int n = 0; n < P; ++n) acc += root[(size_t)l * P + n] * sm[n];
+      Lout[l] = acc;
+    }
+    return;
+  }
+  {
+    int par = box >> 2, q = box & 3;
+    for (int i = threadIdx.x; i < Pp; i += blockDim.x) sm[i] = Lp[(size_t)par * Pp + i];
+    __syncthreads();
+    if (l < P) {
+      const C* row = B + ((size_t)q * P + l) * Pp;
+      for (int m = 0; m < Pp; ++m) acc += row[m] * sm[m];
+    }
+  }
+  for (int e = ilp[ti]; e < ilp[ti + 1]; ++e) {
+    const int src = ils[e], off = ilo[e];
+    const C ph = from_d<C>(ipow_phase(alpha, ilm[e]));
+    __syncthreads();
+    for (int i = threadIdx.x; i < P; i += blockDim.x) sm[i] = ph * Mlev[(size_t)src * P + i];
+    __syncthreads();
+    if (l < P) {
+      const C* row = T + ((size_t)off * P + l) * P;
+      for (int n = 0; n < P; ++n) acc += row[n] * sm[n];
+    }
+  }
+  if (l < P) Lout[(size_t)box * P + l] = acc;
+}
+
+// U'_s = sum_l c[s][0][l] L_l, dU'_s = sum_l c[s][1][l] L_l; one warp per target.
+template <class C>
+__global__ void l2p_apply_t_kernel(const int* __restrict__ ne, const int* __restrict__ bb,
+                                   const int* __restrict__ be, int P, const C* __restrict__ coef,
+                                   const C* __restrict__ L, C* __restrict__ U) {
+  const int box = ne[blockIdx.x];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const C* Lb = L + (size_t)box * P;
+  for (int s = bb[box] + warp; s < be[box]; s += nw) {
+    const C* cs = coef + (size_t)s * 2 * P;
+    C u{0, 0}, du{0, 0};
+    for (int l = lane; l < P; l += 32) {
+      const C Ll = Lb[l];
+      u += cs[l] * Ll;
+      du += cs[P + l] * Ll;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      u.re += __shfl_down_sync(0xffffffffu, u.re, o);
+      u.im += __shfl_down_sync(0xffffffffu, u.im, o);
+      du.re += __shfl_down_sync(0xffffffffu, du.re, o);
+      du.im += __shfl_down_sync(0xffffffffu, du.im, o);
+    }
+    if (lane == 0) {
+      U[2 * s] = u;
+      U[2 * s + 1] = du;
+    }
+  }
+}
+
+template <class C>
+__device__ __forceinline__ C warp_sum_t(C v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.re += __shfl_down_sync(0xffffffffu, v.re, o);
+    v.im += __shfl_down_sync(0xffffffffu, v.im, o);
+  }
+  return v;
+}
+
+template <class C>
+__global__ void near_apply_t_kernel(const int* __restrict__ ne, const int* __restrict__ bb,
+                                    const int* __restrict__ be, const int64_t* __restrict__ base,
+                                    const int* __restrict__ sbase, const int* __restrict__ srcf,
+                                    const C* __restrict__ val, const C* __restrict__ dens, C* __restrict__ U) {
+  const int li = blockIdx.x;
+  const int box = ne[li];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int s0 = bb[box], nt = be[box] - s0;
+  const int j0 = sbase[li], ns = sbase[li + 1] - j0;
+  for (int t = warp; t < nt; t += nw) {
+    const C* row = val + base[li] + (int64_t)t * ns * 4;
+    C u{0, 0}, du{0, 0};
+    for (int j = lane; j < ns; j += 32) {
+      const int f = srcf[j0 + j];
+      const C p = dens[2 * f], v = dens[2 * f + 1];
+      u += row[4 * j] * p + row[4 * j + 1] * v;
+      du += row[4 * j + 2] * p + row[4 * j + 3] * v;
+    }
+    u = warp_sum_t(u);
+    du = warp_sum_t(du);
+    if (lane == 0) {
+      U[2 * (s0 + t)] += u;
+      U[2 * (s0 + t) + 1] += du;
+    }
+  }
+}
+
+template <class C>
+__global__ void fiber_apply_t_kernel(const int* __restrict__ chunk, const int* __restrict__ foff,
+                                     const int64_t* __restrict__ fbase, const C* __restrict__ val,
+                                     const int* __restrict__ opos, const cplx* __restrict__ sph, cplx c2,
+                                     const cplx* __restrict__ x, const C* __restrict__ U, cplx* __restrict__ y) {
+  __shared__ C xs[2 * 1024];
+  const int fb = chunk[3 * blockIdx.x], rb = chunk[3 * blockIdx.x + 1], re = chunk[3 * blockIdx.x + 2];
+  const int f0 = foff[fb], N = foff[fb + 1] - f0, n2 = 2 * N;
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) xs[i] = from_d<C>(x[2 * f0 + i]);
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int r = rb + warp; r < re; r += nw) {
+    const C* row = val + fbase[fb] + (int64_t)r * n2;
+    C acc{0, 0};
+    for (int c = lane; c < n2; c += 32) acc += row[c] * xs[c];
+    acc = warp_sum_t(acc);
+    if (lane == 0) {
+      const int e = f0 + (r >> 1);
+      const int s = opos[e];
+      const cplx po = cdiv(cplx{1, 0}, sph[s]);
+      const cplx u = po * to_d(U[2 * s + (r & 1)]);
+      y[2 * f0 + r] = to_d(acc) + ((r & 1) ? c2 * u : u);
+    }
+  }
+}
+
+// Pointers of one precision for the cached matvec.
+template <class C>
+struct Ops {
+  C* dens;
+  C* U;
+  C* p2m;
+  C* l2p;
+  C* near;
+  C* fiber;
+  C* root;
+  C* M[PF_MAXLEVEL + 1];
+  C* L[PF_MAXLEVEL + 1];
+  C* m2m[PF_MAXLEVEL + 1];
+  C* l2l[PF_MAXLEVEL + 1];
+  C* m2l[PF_MAXLEVEL + 1];
+};
+
+static Ops<cplx> ops64(pfmbem* h) {
+  Ops<cplx> o{};
+  o.dens = h->dens; o.U = h->U; o.p2m = h->p2m_c; o.l2p = h->l2p_c; o.near = h->nc_val; o.fiber = h->fb_val;
+  o.root = h->root;
+  for (int l = 0; l <= h->D; ++l) {
+    o.M[l] = h->lev[l].M; o.L[l] = h->lev[l].L; o.m2m[l] = h->lev[l].m2m; o.l2l[l] = h->lev[l].l2l;
+    o.m2l[l] = h->lev[l].m2l;
+  }
+  return o;
+}
+
+static Ops<cplxf> ops32(pfmbem* h) {
+  Ops<cplxf> o{};
+  o.dens = h->densf; o.U = h->Uf; o.p2m = h->p2m_cf; o.l2p = h->l2p_cf; o.near = h->nc_valf; o.fiber = h->fb_valf;
+  o.root = h->rootf;
+  for (int l = 0; l <= h->D; ++l) {
+    o.M[l] = h->lev[l].Mf; o.L[l] = h->lev[l].Lf; o.m2m[l] = h->lev[l].m2mf; o.l2l[l] = h->lev[l].l2lf;
+    o.m2l[l] = h->lev[l].m2lf;
+  }
+  return o;
+}
+
 static inline int round32(int n) { return ((n + 31) / 32) * 32; }
+
+// The cached matvec: every operator application is plain linear algebra on
+// tables built once at create.
+template <class C>
+static cudaError_t matvec_cached(pfmbem* h, const cplx* x, cplx* y, const Ops<C>& o) {
+  cudaStream_t st = h->stream;
+  const int E = h->E, D = h->D;
+  Level& leaf = h->lev[D];
+  prof_begin(h, PH_GATHER);
+  gather_t_kernel<C><<<(E + 255) / 256, 256, 0, st>>>(E, h->s_perm, h->s_ph, x, o.dens);
+  prof_end(h, PH_GATHER);
+  prof_begin(h, PH_P2M);
+  p2m_apply_t_kernel<C><<<leaf.nne, round32(leaf.P), 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P, o.p2m,
+                                                              o.dens, o.M[D]);
+  prof_end(h, PH_P2M);
+  for (int l = D - 1; l >= 0; --l) {
+    Level& a = h->lev[l];
+    Level& c = h->lev[l + 1];
+    prof_begin(h, PH_M2M);
+    m2m_t_kernel<C><<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, c.P, o.m2m[l], c.box_begin, c.box_end, o.M[l + 1],
+                                                    o.M[l]);
+    prof_end(h, PH_M2M);
+  }
+  {
+    Level& r = h->lev[0];
+    prof_begin(h, PH_LOCAL);
+    local_t_kernel<C><<<1, round32(r.P), 0, st>>>(r.ne, r.P, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                  nullptr, o.M[0], o.root, h->alpha, o.L[0]);
+    prof_end(h, PH_LOCAL);
+  }
+  for (int l = 1; l <= D; ++l) {
+    Level& a = h->lev[l];
+    Level& pa = h->lev[l - 1];
+    prof_begin(h, PH_LOCAL);
+    local_t_kernel<C><<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, pa.P, o.l2l[l - 1], o.L[l - 1], a.il_ptr, a.il_src,
+                                                      a.il_off, a.il_img, o.m2l[l], o.M[l], nullptr, h->alpha,
+                                                      o.L[l]);
+    prof_end(h, PH_LOCAL);
+  }
+  prof_begin(h, PH_L2P);
+  l2p_apply_t_kernel<C><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P, o.l2p, o.L[D], o.U);
+  prof_end(h, PH_L2P);
+  prof_begin(h, PH_NEAR);
+  near_apply_t_kernel<C><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
+                                                   h->nc_src, o.near, o.dens, o.U);
+  prof_end(h, PH_NEAR);
+  cplx c2{h->c2re, h->c2im};
+  prof_begin(h, PH_FIBER);
+  fiber_apply_t_kernel<C><<<h->nchunk, 256, 0, st>>>(h->fb_chunk, h->fib_off, h->fb_base, o.fiber, h->o_pos, h->s_ph,
+                                                     c2, x, o.U, y);
+  prof_end(h, PH_FIBER);
+  return cudaGetLastError();
+}
+
+cudaError_t k_build_fmm_caches(pfmbem* h) {
+  Level& leaf = h->lev[h->D];
+  prof_begin(h, PH_SETUP);
+  p2m_coef_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.w_dev,
+                                                             h->g_far, h->k, h->eta, h->x0, h->y0, h->s_c, h->s_t,
+                                                             h->s_nu, h->s_h, h->p2m_c, h->p2m_cf);
+  prof_end(h, PH_SETUP);
+  prof_begin(h, PH_SETUP);
+  l2p_coef_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.w_dev, h->k,
+                                                             h->x0, h->y0, h->s_c, h->s_nu, h->l2p_c, h->l2p_cf);
+  prof_end(h, PH_SETUP);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- matvec driver
 
 // Gather the densities into tree order and run the upward pass (P2M, M2M)
 // and the periodic root translation.
@@ -691,7 +1213,11 @@ static void upward_f64(pfmbem* h, const cplx* x) {
 }
 
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision) {
-  (void)precision;
+  if (h->cached) {
+    if (precision == PFMBEM_MIXED) return matvec_cached(h, x, y, ops32(h));
+    return matvec_cached(h, x, y, ops64(h));
+  }
+  // on-the-fly path (no cached operators): FP64 element integrals in every product
   cudaStream_t st = h->stream;
   const int E = h->E, D = h->D;
   Level& leaf = h->lev[D];
@@ -709,11 +1235,11 @@ cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision) {
   l2p_f64_kernel<<<leaf.nne, 64, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, D, leaf.d, leaf.p, leaf.w_dev, h->k,
                                           h->x0, h->y0, h->s_c, h->s_nu, leaf.L, h->U);
   prof_end(h, PH_L2P);
+  cplx c2{h->c2re, h->c2im};
   prof_begin(h, PH_NEAR);
   near_f64_kernel<<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nl_ptr, h->nl_src, h->nl_img,
                                             h->k, h->eta, h->H, alpha, h->s_c, h->s_t, h->s_nu, h->s_h, h->dens, h->U);
   prof_end(h, PH_NEAR);
-  cplx c2{h->c2re, h->c2im};
   prof_begin(h, PH_FIBER);
   fiber_combine_f64_kernel<<<(E * 32 + 255) / 256, 256, 0, st>>>(E, h->o_fiber, h->fib_off, h->k1, h->eta, h->rho, c2,
                                                                  h->o_c, h->o_t, h->o_nu, h->o_h, h->o_pos, h->s_ph,

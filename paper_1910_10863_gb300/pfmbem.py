@@ -23,7 +23,7 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "EGEOM", 3: "EWOOD", 4: "ENOMEM", 5: "ECUDA",
 class Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("p_min", ctypes.c_int), ("eta", ctypes.c_double),
                 ("leaf_max", ctypes.c_int), ("depth", ctypes.c_int), ("gmres_m", ctypes.c_int),
-                ("precision", ctypes.c_int), ("reserved", ctypes.c_int * 8)]
+                ("precision", ctypes.c_int), ("near_mode", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class Info(ctypes.Structure):

@@ -125,3 +125,81 @@ def test_invalid_inputs_rejected(pf):
                          math.radians(30))
     assert e.value.status == 3
     del th
+
+
+@pytest.mark.parametrize("make", SMALL)
+def test_matvec_mixed_matches_dense_oracle(pf, make):
+    w = make()
+    s = pf.Solver(w)
+    _, Mo, _ = oracle_system(w)
+    x = W.density_vector(s.E, 4)
+    y = np.zeros_like(x)
+    s.matvec(x, y, pf.MIXED)
+    assert rel(y, Mo @ x) < 2e-6
+
+
+@pytest.mark.parametrize("make", SMALL)
+def test_solve_mixed_refined_matches_dense_lu(pf, make):
+    w = make()
+    s = pf.Solver(w, precision=pf.MIXED)
+    pb, Mo, Bo = oracle_system(w)
+    psi_ref = np.linalg.solve(Mo, Bo)
+    psi = np.zeros(2 * s.E, dtype=np.complex128)
+    info = s.solve(psi, tol=1e-8, maxit=500)
+    assert info.rel_residual <= 1e-8          # FP64 true residual after refinement
+    assert info.restarts >= 1                 # at least one refinement step ran
+    assert rel(psi, psi_ref) < 1e-6
+
+
+def test_matvec_uncached_fp64(pf):
+    w = hexagon_4x4_ragged()
+    s = pf.Solver(w, near_mode=1)
+    _, Mo, _ = oracle_system(w)
+    x = W.density_vector(s.E, 5)
+    y = np.zeros_like(x)
+    s.matvec(x, y)
+    assert rel(y, Mo @ x) < 1e-8
+
+
+@pytest.mark.parametrize("make", SMALL)
+def test_bragg_coefficients_and_field(pf, make):
+    w = make()
+    s = pf.Solver(w)
+    pb, Mo, Bo = oracle_system(w)
+    psi = np.linalg.solve(Mo, Bo)
+    orders, R, T, energy = pf.pfmbem_coefficients(s.h, psi)
+    o_ref, R_ref, T_ref = bem.rayleigh(pb, psi)
+    assert list(orders) == list(o_ref)
+    assert np.max(np.abs(R - R_ref)) < 1e-10 and np.max(np.abs(T - T_ref)) < 1e-10
+    assert abs(energy - bem.energy(pb, o_ref, R_ref, T_ref)) < 1e-10
+    # scattered field at points between the fibers and beside the block
+    el = bem.elements(w.nodes, w.nodes_per_fiber)
+    xmid = 0.5 * (el.a[:, 0].min() + el.a[:, 0].max())
+    pts = np.array([[xmid, el.c[:, 1].min() - 0.02], [el.a[:, 0].max() + 0.05, 0.3],
+                    [el.a[:, 0].min() - 0.05, 0.7], [xmid, el.c[:, 1].max() + 1.37]])
+    u = np.zeros(len(pts), dtype=np.complex128)
+    pf.pfmbem_field(s.h, psi, pts, u)
+    u_ref = bem.potential(pb, psi, pts)
+    assert np.max(np.abs(u - u_ref)) < 1e-8 * np.max(np.abs(u_ref))
+
+
+def test_full_size_hexagon_rows(pf):
+    """hexagon 8x8, 256 elements per fiber (16384 elements): sampled rows of the
+    FP64 and the mixed matvec against rows of the dense oracle operator."""
+    w = W.hexagon_8x8_n256()
+    s = pf.Solver(w)
+    x = W.density_vector(s.E, 6)
+    y64 = np.zeros_like(x)
+    y32 = np.zeros_like(x)
+    s.matvec(x, y64, pf.FP64)
+    s.matvec(x, y32, pf.MIXED)
+    rng = np.random.default_rng(0)
+    rows_e = np.sort(rng.choice(s.E, size=6, replace=False))
+    rows_e[0] = 0                        # first element of the first fiber
+    rows_e[-1] = s.E - 1                 # last element of the last fiber
+    pb = bem.problem(w)
+    Mr = bem.operator_rows(pb, rows_e)
+    ref = Mr @ x
+    idx = np.ravel(np.stack([2 * rows_e, 2 * rows_e + 1], axis=1))
+    assert rel(y64[idx], ref) < 1e-8
+    assert rel(y32[idx], ref) < 2e-6
