@@ -38,7 +38,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 comparator arm")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-reps", type=int, default=20)
@@ -192,16 +193,18 @@ def main():
     opt = pf.Options()
     opt.precision = prec
     maxit = 2000
-    prof_acc = {"ms": np.zeros(16), "launches": np.zeros(16, dtype=np.int64)}
+    prof_acc = {"ms": np.zeros(32), "launches": np.zeros(32, dtype=np.int64)}
     stats = {}
 
-    def step(host=False, profile=False):
+    def step(host=False, profile=False, o=None):
         npf, nodes, psi = (npf_h, nodes_h, psi_h) if host else (npf_d, nodes_d, psi_d)
-        h = pf.pfmbem_create(w.M, npf, nodes, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, opt, sptr)
+        h = pf.pfmbem_create(w.M, npf, nodes, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, o or opt, sptr)
         try:
             if profile:
                 pf.pfmbem_profile(h, True, True)
-            info = pf.pfmbem_solve(h, None, psi, False, args.tol, maxit)
+            info = pf.pfmbem_solve(h, None, psi, False, args.tol, maxit, check=False)
+            if info.status != 0:
+                stats["failed_status"] = pf.STATUS.get(info.status, info.status)
             orders, R, T, energy = pf.pfmbem_coefficients(h, psi)
             if profile:
                 p = pf.pfmbem_profile_read(h)
@@ -220,19 +223,20 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    def timed(host, profile):
+    def timed(host, profile, steps=None, o=None):
+        steps = steps or args.steps
         tot = 0.0
-        for _ in range(args.steps):
+        for _ in range(steps):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            step(host=host, profile=profile)
+            step(host=host, profile=profile, o=o)
             e1.record(stream)
             e1.synchronize()
             tot += e0.elapsed_time(e1)
-        return tot / args.steps
+        return tot / steps
 
     for _ in range(args.warmup):
         step()
@@ -241,8 +245,18 @@ def main():
     clocks.start()
     ms_step = timed(host=False, profile=True)
     clk = clocks.stop()
+    main_stats = dict(stats)
     barrier()
     ms_e2e = timed(host=True, profile=False)
+    barrier()
+    # plain FP64 FMM-GMRES comparator on the same block and tolerance
+    o64 = pf.Options()
+    o64.precision = pf.FP64
+    step(o=o64)
+    ms_fp64 = timed(host=False, profile=False, steps=args.fp64_steps, o=o64)
+    fp64_stats = dict(stats)
+    stats.clear()
+    stats.update(main_stats)
     barrier()
     if dist is not None:
         t = torch.tensor([ms_step, ms_e2e], dtype=torch.float64, device="cuda")
@@ -256,7 +270,7 @@ def main():
     x = torch.from_numpy(pf_density(w)).cuda()
     y = torch.zeros_like(x)
     mv = {}
-    for name, pr in (("fp64", pf.FP64),) + ((("mixed", pf.MIXED),) if args.precision == "mixed" else ()):
+    for name, pr in (("fp64", pf.FP64), ("mixed", pf.MIXED)):
         for _ in range(3):
             pf.pfmbem_matvec(h, x, y, pr)
         torch.cuda.synchronize()
@@ -276,13 +290,12 @@ def main():
         return
     plan = stats["plan"]
     launches = int(prof_acc["launches"].sum())
-    ms_ph = prof_acc["ms"] / args.steps
     names = pf.PHASES
-    dom = int(np.argmax(ms_ph[:len(names)]))
-    per_launch = ms_ph[dom] / max(1, prof_acc["launches"][dom] / args.steps)
+    ms_ph = prof_acc["ms"]
     fp64_peak = pf.pfmbem_probe_peak(0)
     fp32_peak = pf.pfmbem_probe_peak(1)
-    roof = roofline(names[dom], per_launch, plan, fp64_peak, fp32_peak, args.precision)
+    roof = roofline(names, ms_ph, prof_acc["launches"], args.steps, plan, fp64_peak, fp32_peak, w.E)
+    ms_ph = ms_ph / args.steps
 
     cpu = None
     if not args.no_cpu_baseline:
@@ -300,10 +313,13 @@ def main():
                        "l2": "flushed between steps (256 MiB write); per-step working set is L2-resident by design",
                        "parallelism": f"replicas x{world}"},
             "matvec_munknowns_per_s": mv,
+            "plain_fp64": {"solves_per_s": world * 1000.0 / ms_fp64, "ms_per_step": ms_fp64,
+                           "iters": fp64_stats["iters"], "rel_residual": fp64_stats["rel_residual"],
+                           "speedup_of_value": (world * 1000.0 / ms_step) / (world * 1000.0 / ms_fp64)},
             "solve": {"iters": stats["iters"], "restarts": stats["restarts"],
                       "rel_residual": stats["rel_residual"], "energy_sum": stats["energy"],
                       "setup_ms": plan.setup_ms},
-            "phase_ms_per_step": {names[i]: float(ms_ph[i]) for i in range(len(names))},
+            "phase_ms_per_step": {names[i]: float(ms_ph[i]) for i in range(len(names)) if names[i] and ms_ph[i] > 0},
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -319,26 +335,77 @@ def pf_density(w):
     return W.density_vector(w.E, 11)
 
 
-# Algorithmic work per unit, from one ncu capture of each kernel (executed
-# floating-point operations per unit: 2 per FMA, 1 per add/mul); units per
-# launch come from the plan.  Near-field / fiber-local P2P: one unit = one
-# kernel evaluation (target collocation point x Gauss node of a source element).
-FLOPS_PER_EVAL = {"fp64": 180.0, "mixed": 120.0}
+# Algorithmic work per unit.  Element-integral (P2P) evaluation: one unit = one
+# kernel evaluation (target collocation point x Gauss node of a source element),
+# 385 FP64 flops (2 per DFMA + DADD + DMUL, counted by ncu on the near-field and
+# same-fiber kernels of the hexagon 8x8 block).  Cached applies: bytes of the
+# resident operator plus the vectors they read and write.
+FLOPS_PER_EVAL_FP64 = 385.0
 
 
-def roofline(phase, ms_per_launch, plan, fp64_peak, fp32_peak, precision):
-    if phase in ("near_p2p", "fiber_p2p_combine"):
-        units = plan.near_quad if phase == "near_p2p" else plan.fiber_quad
-        flops = units * FLOPS_PER_EVAL[precision]
-        peak = fp64_peak if precision == "fp64" else fp32_peak
-        ach = flops / (ms_per_launch * 1e-3) / 1e12
-        return {"kernel": phase, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "peak_source": "measured FMA-chain probe (pfmbem_probe_peak)",
-                "units_per_launch": int(units), "flops_per_unit": FLOPS_PER_EVAL[precision],
-                "ms_per_launch": ms_per_launch}
-    return {"kernel": phase, "bound": "alu", "achieved": None, "peak": fp64_peak, "unit": "TFLOP/s", "frac": None,
-            "traffic": None, "ms_per_launch": ms_per_launch}
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (measured copy)"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback 6.8 TB/s"
+
+
+def bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["bf16_tflops_sustained"]), "MEASURED_PEAKS.json bf16_tflops_sustained (kernel inside a step)"
+    except (OSError, KeyError, ValueError):
+        return 1700.0, "fallback 1.7 PFLOP/s sustained"
+
+
+def roofline(names, ms_ph, la_ph, steps, plan, fp64_peak, fp32_peak, E, tensor_m2l=True):
+    dom = int(np.argmax(ms_ph))
+    name = names[dom]
+    ms_step = ms_ph[dom] / steps
+    launches = la_ph[dom] / steps
+    per_launch = ms_step / max(launches, 1e-9)
+    f32 = name.endswith("_f32")
+    csz = 8 if f32 else 16
+    hbm, hbm_src = measured_peaks()
+    out = {"kernel": name, "ms_per_launch": per_launch, "launches_per_step": launches}
+    if name == "p2p_cache_build":
+        units = plan.near_quad + plan.fiber_quad
+        ach = units * FLOPS_PER_EVAL_FP64 / (ms_step * 1e-3) / 1e12
+        out.update(bound="alu", achieved=ach, peak=fp64_peak, unit="TFLOP/s", frac=ach / fp64_peak, traffic=None,
+                   peak_source="FP64 FMA-chain probe (pfmbem_probe_peak)", units_per_launch=int(units / 2),
+                   unit_def="kernel evaluation, 385 FP64 flops")
+    elif name.startswith("near_p2p") and plan.cached:
+        nbytes = plan.near_blocks * 4 * csz + 2 * E * csz * 3
+        ach = nbytes / (per_launch * 1e-3) / 1e9
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, traffic=None,
+                   peak_source=hbm_src, bytes_per_launch=int(nbytes))
+    elif name.startswith("fiber_p2p_combine") and plan.cached:
+        nbytes = plan.fiber_entries * csz + 2 * E * (16 + 16 + csz)
+        ach = nbytes / (per_launch * 1e-3) / 1e9
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, traffic=None,
+                   peak_source=hbm_src, bytes_per_launch=int(nbytes))
+    elif name.startswith("m2l_l2l"):
+        # algorithmic flops of one matvec's M2L: 8 (2p+1)^2 per translation; the
+        # number of matvecs in the step is the launch count of the gather phase
+        P = 2 * plan.p[plan.depth] + 1
+        matvecs = la_ph[16 if f32 else 0] / steps
+        flops = 8.0 * P * P * plan.m2l_pairs * matvecs
+        ach = flops / (ms_step * 1e-3) / 1e12
+        if f32 and tensor_m2l:
+            peak, src = bf16_peak()
+            out.update(bound="tensor", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None,
+                       peak_source=src, note="algorithmic complex-M2L flops; the tensor cores issue 6 BF16 "
+                                             "products of the real-embedded, padded operator")
+        else:
+            peak = fp32_peak if f32 else fp64_peak
+            out.update(bound="alu", achieved=ach, peak=peak, unit="TFLOP/s", frac=ach / peak, traffic=None,
+                       peak_source="FMA-chain probe (pfmbem_probe_peak)")
+    else:
+        out.update(bound="alu", achieved=None, peak=None, unit=None, frac=None, traffic=None)
+    return out
 
 
 if __name__ == "__main__":

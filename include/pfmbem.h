@@ -64,7 +64,9 @@ typedef struct {
   int near_mode;    /* 0 = near-field and same-fiber element integrals computed once at
                        create and kept in device memory (default); 1 = recomputed in
                        every matvec (no cache memory) */
-  int reserved[7];
+  int m2l_mode;     /* FP32 (mixed) M2L: 0 = tensor cores (tcgen05, BF16 x3 split, FP32
+                       accumulation) where 2(2p+1) <= 128, 1 = CUDA cores only */
+  int reserved[6];
 } pfmbem_options;
 
 /* Outcome of a solve. */
@@ -92,6 +94,9 @@ typedef struct {
   int lattice_q;          /* directly summed image rows in the lattice sums */
   double root_x0, root_y0;/* lower-left corner of the root box (side H) */
   double setup_ms;        /* wall time of pfmbem_create */
+  int64_t near_blocks;    /* cached near-field 2x2 complex blocks (0 when not cached) */
+  int64_t fiber_entries;  /* cached fiber-block complex entries (0 when not cached) */
+  int cached;             /* 1 when the element integrals are cached in device memory */
 } pfmbem_plan_info;
 
 /* Create a solver for one fundamental block (paper Sec. 2-3).
@@ -168,12 +173,15 @@ pfmbem_status pfmbem_lattice_sums(pfmbem_t h, int jmax, double* S);
 /* Kernel profiling (not part of the paper's method; measurement support).
  * Phases: 0 density gather, 1 P2M, 2 M2M, 3 M2L + L2L + root translation,
  * 4 L2P, 5 near-field P2P, 6 fiber-local P2P + combine, 7 GMRES vector
- * kernels, 8 set-up kernels, 9 output kernels (field, coefficients).
+ * kernels, 8 set-up kernels, 9 output kernels (field, coefficients),
+ * 10 element-integral cache build (the near-field and same-fiber Hankel
+ * quadrature, once per create); phases 0-6 of the FP32 (mixed) matrix-vector
+ * product are counted at index + 16.
  * launches[] always counts the library's kernel launches; ms[] accumulates
  * CUDA-event device time per phase on the handle's stream while timing is on. */
 typedef struct {
-  double ms[16];
-  int64_t launches[16];
+  double ms[32];
+  int64_t launches[32];
   int64_t total_launches;
 } pfmbem_profile_info;
 

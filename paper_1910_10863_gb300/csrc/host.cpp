@@ -376,6 +376,67 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &L.il_src, src)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.il_off, off)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.il_img, img)) != PFMBEM_OK) return st;
+    // the same pairs grouped by offset, cut into chunks of at most 64 pairs
+    {
+      std::vector<std::vector<int>> by(49);
+      for (size_t ti = 0; ti < L.hne.size(); ++ti)
+        for (int e = ptr[ti]; e < ptr[ti + 1]; ++e) by[off[e]].push_back(e);
+      std::vector<int> ptg, psr, pim, cof, cbg, cen;
+      for (int o = 0; o < 49; ++o) {
+        for (size_t i = 0; i < by[o].size(); ++i) {
+          if (i % 64 == 0) {
+            cof.push_back(o);
+            cbg.push_back((int)ptg.size());
+            cen.push_back((int)ptg.size());
+          }
+          const int e = by[o][i];
+          // target box of CSR entry e
+          const int ti = (int)(std::upper_bound(ptr.begin(), ptr.end(), e) - ptr.begin()) - 1;
+          ptg.push_back(L.hne[ti]);
+          psr.push_back(src[e]);
+          pim.push_back(img[e]);
+          cen.back() = (int)ptg.size();
+        }
+      }
+      // tensor-core tiles: 128 consecutive non-empty target boxes
+      {
+        const int nt = ((int)L.hne.size() + 127) / 128;
+        std::vector<int> tbox((size_t)nt * 128, -1), tnoff(nt, 0), toffs((size_t)nt * 49, 0);
+        std::vector<int> tsrc((size_t)nt * 49 * 128, -1), timg((size_t)nt * 49 * 128, 0);
+        for (int tile = 0; tile < nt; ++tile) {
+          int slot[49];
+          for (int o = 0; o < 49; ++o) slot[o] = -1;
+          for (int r = 0; r < 128; ++r) {
+            const size_t ti = (size_t)tile * 128 + r;
+            if (ti >= L.hne.size()) break;
+            tbox[ti] = L.hne[ti];
+            for (int e = ptr[ti]; e < ptr[ti + 1]; ++e) {
+              const int o = off[e];
+              if (slot[o] < 0) {
+                slot[o] = tnoff[tile]++;
+                toffs[(size_t)tile * 49 + slot[o]] = o;
+              }
+              const size_t q = ((size_t)tile * 49 + slot[o]) * 128 + r;
+              tsrc[q] = src[e];
+              timg[q] = img[e];
+            }
+          }
+        }
+        L.tc_ntile = nt;
+        if ((st = upload(h, &L.tc_box, tbox)) != PFMBEM_OK) return st;
+        if ((st = upload(h, &L.tc_noff, tnoff)) != PFMBEM_OK) return st;
+        if ((st = upload(h, &L.tc_offs, toffs)) != PFMBEM_OK) return st;
+        if ((st = upload(h, &L.tc_src, tsrc)) != PFMBEM_OK) return st;
+        if ((st = upload(h, &L.tc_img, timg)) != PFMBEM_OK) return st;
+      }
+      L.nchunk = (int)cof.size();
+      if ((st = upload(h, &L.pr_tgt, ptg)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.pr_src, psr)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.pr_img, pim)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.ch_off, cof)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.ch_beg, cbg)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.ch_end, cen)) != PFMBEM_OK) return st;
+    }
   }
   h->info.m2l_pairs = m2l_pairs;
   // fiber-local statistics
@@ -447,6 +508,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         }
       if ((st = upload(h, &L.m2l, T)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.m2lf, to_float(T))) != PFMBEM_OK) return st;
+      if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 0) {
+        if ((st = upload(h, &L.tc_B, tc_build_operator(T, P))) != PFMBEM_OK) return st;
+      } else {
+        L.tc_ntile = 0;
+      }
     }
     // M2M (children l+1 -> l) and L2L (l -> children)
     if (l < D) {
@@ -557,6 +623,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       h->fb_val = dalloc<cplx>(h, (size_t)acc);
       h->fb_valf = dalloc<cplxf>(h, (size_t)acc);
       h->stat_dev = dalloc<unsigned long long>(h, 4);
+      h->tc_err = dalloc<int>(h, 1);
+      if (!h->tc_err) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
+      CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
       if (!h->nc_val || !h->nc_valf || !h->fb_val || !h->fb_valf || !h->stat_dev)
         return fail(h, PFMBEM_ENOMEM, "device allocation failed (near-field caches)");
       CK(cudaMemsetAsync(h->stat_dev, 0, 4 * sizeof(unsigned long long), h->stream));
@@ -844,6 +913,9 @@ pfmbem_status pfmbem_plan(pfmbem_t h, pfmbem_plan_info* info) {
     h->info.fiber_pairs = (int64_t)c[2];
     h->info.fiber_quad = (int64_t)c[3];
   }
+  h->info.cached = h->cached ? 1 : 0;
+  h->info.near_blocks = h->cached ? h->nc_blocks : 0;
+  h->info.fiber_entries = h->cached ? h->fb_entries : 0;
   *info = h->info;
   return PFMBEM_OK;
 }
@@ -914,7 +986,8 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
       bn = std::sqrt(bn);
     }
     st = PFMBEM_ENOCONV;
-    int refinements = 0;
+    int refinements = 0, stalls = 0;
+    double prev = 1e300;
     for (; refinements < 50; ++refinements) {
       CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
       CK(k_sub(h, g.b, g.w, g.d, (int)n));
@@ -926,11 +999,18 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
       if (!std::isfinite(relres)) return fail(h, PFMBEM_ENUMERIC, "non-finite residual");
       if (relres <= tol) { st = PFMBEM_OK; break; }
       if (iters >= maxit) break;
-      const double inner_tol = std::max(1e-5, 0.3 * tol / relres);
+      // stop when refinement no longer reduces the FP64 residual
+      if (relres > 0.5 * prev) { if (++stalls >= 3) break; } else stalls = 0;
+      prev = relres;
+      // The FP32 operator puts a floor of roughly eps_32 * cond under the inner
+      // residual, so the inner solve is asked for a modest reduction and its
+      // work per refinement step is bounded; refinement does the rest.
+      const double inner_tol = std::max(1e-4, 0.3 * tol / relres);
+      const int cap = std::min(maxit - iters, 4 * g.m);
       int it = 0, rs = 0;
       double rr = 1;
       CK(cudaMemsetAsync(g.c, 0, n * sizeof(cplx), h->stream));
-      pfmbem_status si = gmres(h, g.d, g.c, inner_tol, maxit - iters, PFMBEM_MIXED, &it, &rs, &rr, true);
+      pfmbem_status si = gmres(h, g.d, g.c, inner_tol, cap, PFMBEM_MIXED, &it, &rs, &rr, true);
       if (si != PFMBEM_OK && si != PFMBEM_ENOCONV) return si;
       iters += it;
       CK(k_axpy(h, cplx{1, 0}, g.c, g.x, (int)n));
@@ -941,6 +1021,14 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
   }
   CK(cudaMemcpyAsync(psi, g.x, n * sizeof(cplx), pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  if (h->tc_err) {
+    int e = 0;
+    CK(cudaMemcpy(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      st = PFMBEM_ETIMEOUT;
+      h->err = "tensor-core M2L: a bounded wait for the MMA completion gave up";
+    }
+  }
   if (info) {
     info->iters = iters;
     info->restarts = restarts;
@@ -1066,7 +1154,7 @@ pfmbem_status pfmbem_profile(pfmbem_t h, int enable_timing, int reset) {
   if (!h) return PFMBEM_EINVAL;
   CK(prof_fold(h));
   if (reset) {
-    for (int i = 0; i < 16; ++i) {
+    for (int i = 0; i < 32; ++i) {
       h->prof.ms[i] = 0;
       h->prof.launches[i] = 0;
     }
@@ -1080,7 +1168,7 @@ pfmbem_status pfmbem_profile_read(pfmbem_t h, pfmbem_profile_info* out) {
   CK(cudaStreamSynchronize(h->stream));
   CK(prof_fold(h));
   int64_t tot = 0;
-  for (int i = 0; i < 16; ++i) {
+  for (int i = 0; i < 32; ++i) {
     out->ms[i] = h->prof.ms[i];
     out->launches[i] = h->prof.launches[i];
     tot += h->prof.launches[i];

@@ -31,6 +31,23 @@ struct Level {
   int* il_off = nullptr;
   int* il_img = nullptr;
   int64_t nil = 0;
+  // the same M2L pairs grouped by offset, in chunks of at most M2L_CHUNK pairs
+  int* pr_tgt = nullptr;     // target box per pair
+  int* pr_src = nullptr;     // source box per pair
+  int* pr_img = nullptr;     // image m per pair
+  int* ch_off = nullptr;     // offset id per chunk
+  int* ch_beg = nullptr;     // first pair of the chunk
+  int* ch_end = nullptr;     // one past the last pair
+  int nchunk = 0;
+  // tensor-core M2L: tiles of 128 target boxes, per tile the offsets present and
+  // for every (tile, offset slot, target row) the source box (-1: none) and image
+  int tc_ntile = 0;
+  int* tc_box = nullptr;     // [ntile][128] target box (-1 padding)
+  int* tc_noff = nullptr;    // [ntile]
+  int* tc_offs = nullptr;    // [ntile][49]
+  int* tc_src = nullptr;     // [ntile][49][128]
+  int* tc_img = nullptr;     // [ntile][49][128]
+  uint16_t* tc_B = nullptr;  // [49][3][kp][kp] BF16 parts of the real-embedded operators
   cplx* m2l = nullptr;       // [49][P][P]: row = target coefficient, col = source coefficient
   cplx* m2m = nullptr;       // children (level l+1) -> this level: [4][P][P_child]
   cplx* l2l = nullptr;       // this level -> children: [4][P_child][P]
@@ -56,7 +73,8 @@ struct GmresWork {
   cplx* hhost = nullptr;    // pinned host mirror of hcol
 };
 
-enum Phase { PH_GATHER = 0, PH_P2M, PH_M2M, PH_LOCAL, PH_L2P, PH_NEAR, PH_FIBER, PH_BLAS, PH_SETUP, PH_OUT, PH_COUNT };
+enum Phase { PH_GATHER = 0, PH_P2M, PH_M2M, PH_LOCAL, PH_L2P, PH_NEAR, PH_FIBER, PH_BLAS, PH_SETUP, PH_OUT, PH_BUILD,
+             PH_COUNT };
 
 // Launch counters and optional CUDA-event timing per phase.
 struct Prof {
@@ -64,8 +82,8 @@ struct Prof {
   std::vector<cudaEvent_t> ev;          // pool of events, used in begin/end pairs
   std::vector<int> phase_of_pair;       // phase of every recorded pair
   int used = 0;                         // events recorded since the last fold
-  double ms[16] = {0};
-  int64_t launches[16] = {0};
+  double ms[32] = {0};
+  int64_t launches[32] = {0};
 };
 
 struct pfmbem {
@@ -134,6 +152,7 @@ struct pfmbem {
   cplxf* p2m_cf = nullptr;
   cplxf* l2p_cf = nullptr;
   // FP32 work buffers of the mixed matvec
+  int* tc_err = nullptr;         // set by the tensor-core M2L when a bounded wait gave up
   cplxf* densf = nullptr;        // [E][2]
   cplxf* Uf = nullptr;           // [E][2]
   cplx* root = nullptr;          // [P0][P0] periodic root translation
@@ -157,6 +176,10 @@ void prof_end(pfmbem* h, int phase);
 cudaError_t prof_fold(pfmbem* h);
 void prof_release(pfmbem* h);
 // outputs (kernels.cu): scattered field at points, Bragg-order coefficients
+// tensor-core M2L (m2l_tc.cu)
+int tc_kpad(int P);
+std::vector<uint16_t> tc_build_operator(const std::vector<cplx>& T, int P);
+cudaError_t k_m2l_tc(pfmbem* h, int level, const cplxf* M, cplxf* L);
 cudaError_t k_build_caches(pfmbem* h);
 cudaError_t k_build_fmm_caches(pfmbem* h);
 cudaError_t k_field_prepare(pfmbem* h, const cplx* psi);

@@ -782,16 +782,16 @@ cudaError_t k_build_caches(pfmbem* h) {
   cudaStream_t st = h->stream;
   Level& leaf = h->lev[h->D];
   cplx c2{h->c2re, h->c2im};
-  prof_begin(h, PH_SETUP);
+  prof_begin(h, PH_BUILD);
   near_build_kernel<<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
                                               h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c, h->s_t,
                                               h->s_nu, h->s_h, h->nc_val, h->nc_valf, h->stat_dev);
-  prof_end(h, PH_SETUP);
-  prof_begin(h, PH_SETUP);
+  prof_end(h, PH_BUILD);
+  prof_begin(h, PH_BUILD);
   fiber_build_kernel<<<(h->E * 32 + 255) / 256, 256, 0, st>>>(h->E, h->o_fiber, h->fib_off, h->fb_base, h->k1,
                                                               h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu, h->o_h,
                                                               h->self4, h->fb_val, h->fb_valf, h->stat_dev);
-  prof_end(h, PH_SETUP);
+  prof_end(h, PH_BUILD);
   return cudaGetLastError();
 }
 
@@ -978,6 +978,69 @@ __global__ void local_t_kernel(const int* __restrict__ ne, int P, int Pp, const 
   if (l < P) Lout[(size_t)box * P + l] = acc;
 }
 
+// L2L only (level >= 1): L(box) = B_q L(parent).
+template <class C>
+__global__ void l2l_t_kernel(const int* __restrict__ ne, int P, int Pp, const C* __restrict__ B,
+                             const C* __restrict__ Lp, C* __restrict__ Lout) {
+  const int box = ne[blockIdx.x];
+  __shared__ C sm[PF_NCOEF];
+  const int par = box >> 2, q = box & 3;
+  for (int i = threadIdx.x; i < Pp; i += blockDim.x) sm[i] = Lp[(size_t)par * Pp + i];
+  __syncthreads();
+  for (int l = threadIdx.x; l < P; l += blockDim.x) {
+    const C* row = B + ((size_t)q * P + l) * Pp;
+    C acc{0, 0};
+    for (int m = 0; m < Pp; ++m) acc += row[m] * sm[m];
+    Lout[(size_t)box * P + l] = acc;
+  }
+}
+
+__device__ __forceinline__ void atomic_add_c(cplx* p, cplx v) {
+  atomicAdd(&p->re, v.re);
+  atomicAdd(&p->im, v.im);
+}
+__device__ __forceinline__ void atomic_add_c(cplxf* p, cplxf v) {
+  atomicAdd(&p->re, v.re);
+  atomicAdd(&p->im, v.im);
+}
+
+// M2L grouped by translation offset (Sec. 3.2: the operator H^+_{n-l}(k(O_D - O_C))
+// depends only on the offset, so all pairs with offset o share T_o).  Block b
+// takes a chunk of the pairs of one offset: T_o is staged in shared memory once,
+// each warp applies it to one pair at a time (lanes over output rows) and adds
+// alpha^m T_o M(src) into L(target) atomically.
+#define M2L_CHUNK 64
+template <class C>
+__global__ void m2l_offset_t_kernel(int P, const int* __restrict__ chunk_off, const int* __restrict__ chunk_beg,
+                                    const int* __restrict__ chunk_end, const int* __restrict__ ptgt,
+                                    const int* __restrict__ psrc, const int* __restrict__ pimg,
+                                    const C* __restrict__ T, const C* __restrict__ M, cplx alpha,
+                                    C* __restrict__ L) {
+  extern __shared__ unsigned char smraw[];
+  C* sT = reinterpret_cast<C*>(smraw);             // [P][P+1] (padded rows)
+  C* sM = sT + (size_t)P * (P + 1);                 // [warps][P]
+  const int o = chunk_off[blockIdx.x];
+  const int pb = chunk_beg[blockIdx.x], pe = chunk_end[blockIdx.x];
+  const C* To = T + (size_t)o * P * P;
+  for (int i = threadIdx.x; i < P * P; i += blockDim.x) sT[(i / P) * (P + 1) + (i % P)] = To[i];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  C* mw = sM + (size_t)warp * P;
+  __syncthreads();
+  for (int pi = pb + warp; pi < pe; pi += nw) {
+    const int src = psrc[pi], tgt = ptgt[pi];
+    const C ph = from_d<C>(ipow_phase(alpha, pimg[pi]));
+    for (int n = lane; n < P; n += 32) mw[n] = ph * M[(size_t)src * P + n];
+    __syncwarp();
+    for (int l = lane; l < P; l += 32) {
+      const C* row = sT + (size_t)l * (P + 1);
+      C acc{0, 0};
+      for (int n = 0; n < P; ++n) acc += row[n] * mw[n];
+      atomic_add_c(&L[(size_t)tgt * P + l], acc);
+    }
+    __syncwarp();
+  }
+}
+
 // U'_s = sum_l c[s][0][l] L_l, dU'_s = sum_l c[s][1][l] L_l; one warp per target.
 template <class C>
 __global__ void l2p_apply_t_kernel(const int* __restrict__ ne, const int* __restrict__ bb,
@@ -1017,27 +1080,58 @@ __device__ __forceinline__ C warp_sum_t(C v) {
   return v;
 }
 
+// The leaf's source densities (shared by all its targets) are staged in shared
+// memory once; each row then streams only its cached 2x2 blocks, with two
+// independent accumulator pairs per lane to keep more loads in flight.
+#define NEAR_SMEM_SRC 1536
 template <class C>
 __global__ void near_apply_t_kernel(const int* __restrict__ ne, const int* __restrict__ bb,
                                     const int* __restrict__ be, const int64_t* __restrict__ base,
                                     const int* __restrict__ sbase, const int* __restrict__ srcf,
                                     const C* __restrict__ val, const C* __restrict__ dens, C* __restrict__ U) {
+  __shared__ C sd[2 * NEAR_SMEM_SRC];
   const int li = blockIdx.x;
   const int box = ne[li];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int s0 = bb[box], nt = be[box] - s0;
   const int j0 = sbase[li], ns = sbase[li + 1] - j0;
+  const bool staged = ns <= NEAR_SMEM_SRC;
+  if (staged) {
+    for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+      const int f = srcf[j0 + j];
+      sd[2 * j] = dens[2 * f];
+      sd[2 * j + 1] = dens[2 * f + 1];
+    }
+  }
+  __syncthreads();
   for (int t = warp; t < nt; t += nw) {
     const C* row = val + base[li] + (int64_t)t * ns * 4;
-    C u{0, 0}, du{0, 0};
-    for (int j = lane; j < ns; j += 32) {
-      const int f = srcf[j0 + j];
-      const C p = dens[2 * f], v = dens[2 * f + 1];
-      u += row[4 * j] * p + row[4 * j + 1] * v;
-      du += row[4 * j + 2] * p + row[4 * j + 3] * v;
+    C u0{0, 0}, d0{0, 0}, u1{0, 0}, d1{0, 0};
+    int j = lane;
+    for (; j + 32 < ns; j += 64) {
+      C p0, v0, p1, v1;
+      if (staged) {
+        p0 = sd[2 * j]; v0 = sd[2 * j + 1]; p1 = sd[2 * j + 64]; v1 = sd[2 * j + 65];
+      } else {
+        const int f0 = srcf[j0 + j], f1 = srcf[j0 + j + 32];
+        p0 = dens[2 * f0]; v0 = dens[2 * f0 + 1]; p1 = dens[2 * f1]; v1 = dens[2 * f1 + 1];
+      }
+      const C a0 = row[4 * j], a1 = row[4 * j + 1], a2 = row[4 * j + 2], a3 = row[4 * j + 3];
+      const C b0 = row[4 * j + 128], b1 = row[4 * j + 129], b2 = row[4 * j + 130], b3 = row[4 * j + 131];
+      u0 += a0 * p0 + a1 * v0;
+      d0 += a2 * p0 + a3 * v0;
+      u1 += b0 * p1 + b1 * v1;
+      d1 += b2 * p1 + b3 * v1;
     }
-    u = warp_sum_t(u);
-    du = warp_sum_t(du);
+    for (; j < ns; j += 32) {
+      C p, v;
+      if (staged) { p = sd[2 * j]; v = sd[2 * j + 1]; }
+      else { const int f = srcf[j0 + j]; p = dens[2 * f]; v = dens[2 * f + 1]; }
+      u0 += row[4 * j] * p + row[4 * j + 1] * v;
+      d0 += row[4 * j + 2] * p + row[4 * j + 3] * v;
+    }
+    C u = warp_sum_t(u0 + u1);
+    C du = warp_sum_t(d0 + d1);
     if (lane == 0) {
       U[2 * (s0 + t)] += u;
       U[2 * (s0 + t) + 1] += du;
@@ -1056,17 +1150,40 @@ __global__ void fiber_apply_t_kernel(const int* __restrict__ chunk, const int* _
   for (int i = threadIdx.x; i < n2; i += blockDim.x) xs[i] = from_d<C>(x[2 * f0 + i]);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int r = rb + warp; r < re; r += nw) {
-    const C* row = val + fbase[fb] + (int64_t)r * n2;
-    C acc{0, 0};
-    for (int c = lane; c < n2; c += 32) acc += row[c] * xs[c];
-    acc = warp_sum_t(acc);
+  // a warp takes the row pair (2e, 2e+1) of one element; four independent
+  // accumulators per row keep eight loads in flight per lane
+  for (int r = rb + 2 * warp; r < re; r += 2 * nw) {
+    const C* row0 = val + fbase[fb] + (int64_t)r * n2;
+    const C* row1 = row0 + n2;
+    const bool two = r + 1 < re;
+    C a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
+    int c = lane;
+    for (; c + 32 < n2; c += 64) {
+      const C x0 = xs[c], x1 = xs[c + 32];
+      const C r00 = row0[c], r01 = row0[c + 32];
+      a0 += r00 * x0;
+      a1 += r01 * x1;
+      if (two) {
+        const C r10 = row1[c], r11 = row1[c + 32];
+        b0 += r10 * x0;
+        b1 += r11 * x1;
+      }
+    }
+    for (; c < n2; c += 32) {
+      a0 += row0[c] * xs[c];
+      if (two) b0 += row1[c] * xs[c];
+    }
+    const C s0 = warp_sum_t(a0 + a1);
+    const C s1 = warp_sum_t(b0 + b1);
     if (lane == 0) {
-      const int e = f0 + (r >> 1);
-      const int s = opos[e];
-      const cplx po = cdiv(cplx{1, 0}, sph[s]);
-      const cplx u = po * to_d(U[2 * s + (r & 1)]);
-      y[2 * f0 + r] = to_d(acc) + ((r & 1) ? c2 * u : u);
+      for (int q = 0; q < (two ? 2 : 1); ++q) {
+        const int rr = r + q;
+        const int e = f0 + (rr >> 1);
+        const int s = opos[e];
+        const cplx po = cdiv(cplx{1, 0}, sph[s]);
+        const cplx u = po * to_d(U[2 * s + (rr & 1)]);
+        y[2 * f0 + rr] = to_d(q == 0 ? s0 : s1) + ((rr & 1) ? c2 * u : u);
+      }
     }
   }
 }
@@ -1114,54 +1231,73 @@ static inline int round32(int n) { return ((n + 31) / 32) * 32; }
 
 // The cached matvec: every operator application is plain linear algebra on
 // tables built once at create.
+// FP32 launches are profiled under phase + 16.
 template <class C>
 static cudaError_t matvec_cached(pfmbem* h, const cplx* x, cplx* y, const Ops<C>& o) {
   cudaStream_t st = h->stream;
   const int E = h->E, D = h->D;
+  const int po = sizeof(C) == sizeof(cplxf) ? 16 : 0;
   Level& leaf = h->lev[D];
-  prof_begin(h, PH_GATHER);
+  prof_begin(h, PH_GATHER + po);
   gather_t_kernel<C><<<(E + 255) / 256, 256, 0, st>>>(E, h->s_perm, h->s_ph, x, o.dens);
-  prof_end(h, PH_GATHER);
-  prof_begin(h, PH_P2M);
+  prof_end(h, PH_GATHER + po);
+  prof_begin(h, PH_P2M + po);
   p2m_apply_t_kernel<C><<<leaf.nne, round32(leaf.P), 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P, o.p2m,
                                                               o.dens, o.M[D]);
-  prof_end(h, PH_P2M);
+  prof_end(h, PH_P2M + po);
   for (int l = D - 1; l >= 0; --l) {
     Level& a = h->lev[l];
     Level& c = h->lev[l + 1];
-    prof_begin(h, PH_M2M);
+    prof_begin(h, PH_M2M + po);
     m2m_t_kernel<C><<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, c.P, o.m2m[l], c.box_begin, c.box_end, o.M[l + 1],
                                                     o.M[l]);
-    prof_end(h, PH_M2M);
+    prof_end(h, PH_M2M + po);
   }
   {
     Level& r = h->lev[0];
-    prof_begin(h, PH_LOCAL);
+    prof_begin(h, PH_LOCAL + po);
     local_t_kernel<C><<<1, round32(r.P), 0, st>>>(r.ne, r.P, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                   nullptr, o.M[0], o.root, h->alpha, o.L[0]);
-    prof_end(h, PH_LOCAL);
+    prof_end(h, PH_LOCAL + po);
   }
   for (int l = 1; l <= D; ++l) {
     Level& a = h->lev[l];
     Level& pa = h->lev[l - 1];
-    prof_begin(h, PH_LOCAL);
-    local_t_kernel<C><<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, pa.P, o.l2l[l - 1], o.L[l - 1], a.il_ptr, a.il_src,
-                                                      a.il_off, a.il_img, o.m2l[l], o.M[l], nullptr, h->alpha,
-                                                      o.L[l]);
-    prof_end(h, PH_LOCAL);
+    const int nwarp = 8;
+    const size_t smem = sizeof(C) * ((size_t)a.P * (a.P + 1) + (size_t)nwarp * a.P);
+    prof_begin(h, PH_LOCAL + po);
+    const bool tensor = sizeof(C) == sizeof(cplxf) && a.tc_ntile > 0 && a.tc_B != nullptr && h->tc_err != nullptr;
+    if (tensor) {
+      l2l_t_kernel<C><<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, pa.P, o.l2l[l - 1], o.L[l - 1], o.L[l]);
+      k_m2l_tc(h, l, reinterpret_cast<const cplxf*>(o.M[l]), reinterpret_cast<cplxf*>(o.L[l]));
+    } else if (smem <= 200 * 1024) {
+      l2l_t_kernel<C><<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, pa.P, o.l2l[l - 1], o.L[l - 1], o.L[l]);
+      if (a.nchunk > 0) {
+        if (smem > 48 * 1024)
+          cudaFuncSetAttribute(m2l_offset_t_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        m2l_offset_t_kernel<C><<<a.nchunk, 32 * nwarp, smem, st>>>(a.P, a.ch_off, a.ch_beg, a.ch_end, a.pr_tgt,
+                                                                    a.pr_src, a.pr_img, o.m2l[l], o.M[l], h->alpha,
+                                                                    o.L[l]);
+      }
+    } else {   // operator too large for shared memory: per-target kernel
+      local_t_kernel<C><<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, pa.P, o.l2l[l - 1], o.L[l - 1], a.il_ptr, a.il_src,
+                                                        a.il_off, a.il_img, o.m2l[l], o.M[l], nullptr, h->alpha,
+                                                        o.L[l]);
+    }
+    prof_end(h, PH_LOCAL + po);
   }
-  prof_begin(h, PH_L2P);
+  prof_begin(h, PH_L2P + po);
   l2p_apply_t_kernel<C><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P, o.l2p, o.L[D], o.U);
-  prof_end(h, PH_L2P);
-  prof_begin(h, PH_NEAR);
+  prof_end(h, PH_L2P + po);
+  prof_begin(h, PH_NEAR + po);
   near_apply_t_kernel<C><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
                                                    h->nc_src, o.near, o.dens, o.U);
-  prof_end(h, PH_NEAR);
+  prof_end(h, PH_NEAR + po);
   cplx c2{h->c2re, h->c2im};
-  prof_begin(h, PH_FIBER);
+  prof_begin(h, PH_FIBER + po);
   fiber_apply_t_kernel<C><<<h->nchunk, 256, 0, st>>>(h->fb_chunk, h->fib_off, h->fb_base, o.fiber, h->o_pos, h->s_ph,
                                                      c2, x, o.U, y);
-  prof_end(h, PH_FIBER);
+  prof_end(h, PH_FIBER + po);
   return cudaGetLastError();
 }
 

@@ -23,7 +23,8 @@ STATUS = {0: "OK", 1: "EINVAL", 2: "EGEOM", 3: "EWOOD", 4: "ENOMEM", 5: "ECUDA",
 class Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("p_min", ctypes.c_int), ("eta", ctypes.c_double),
                 ("leaf_max", ctypes.c_int), ("depth", ctypes.c_int), ("gmres_m", ctypes.c_int),
-                ("precision", ctypes.c_int), ("near_mode", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("precision", ctypes.c_int), ("near_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 6)]
 
 
 class Info(ctypes.Structure):
@@ -36,7 +37,8 @@ class PlanInfo(ctypes.Structure):
                 ("nleaf_nonempty", ctypes.c_int), ("m2l_pairs", ctypes.c_int64), ("near_pairs", ctypes.c_int64),
                 ("near_quad", ctypes.c_int64), ("fiber_pairs", ctypes.c_int64), ("fiber_quad", ctypes.c_int64),
                 ("p2m_nodes", ctypes.c_int), ("lattice_q", ctypes.c_int), ("root_x0", ctypes.c_double),
-                ("root_y0", ctypes.c_double), ("setup_ms", ctypes.c_double)]
+                ("root_y0", ctypes.c_double), ("setup_ms", ctypes.c_double), ("near_blocks", ctypes.c_int64),
+                ("fiber_entries", ctypes.c_int64), ("cached", ctypes.c_int)]
 
 
 _lib = None
@@ -171,11 +173,13 @@ def pfmbem_coefficients(h, psi, max_orders=64):
 
 
 PHASES = ["gather", "p2m", "m2m", "m2l_l2l", "l2p", "near_p2p", "fiber_p2p_combine", "gmres_blas", "setup",
-          "outputs"]
+          "outputs", "p2p_cache_build", "", "", "", "", "",
+          "gather_f32", "p2m_f32", "m2m_f32", "m2l_l2l_f32", "l2p_f32", "near_p2p_f32", "fiber_p2p_combine_f32",
+          "", "", "", "", "", "", "", "", ""]
 
 
 class ProfileInfo(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 16), ("launches", ctypes.c_int64 * 16), ("total_launches", ctypes.c_int64)]
+    _fields_ = [("ms", ctypes.c_double * 32), ("launches", ctypes.c_int64 * 32), ("total_launches", ctypes.c_int64)]
 
 
 def pfmbem_profile(h, enable_timing=True, reset=True):

@@ -203,3 +203,21 @@ def test_full_size_hexagon_rows(pf):
     idx = np.ravel(np.stack([2 * rows_e, 2 * rows_e + 1], axis=1))
     assert rel(y64[idx], ref) < 1e-8
     assert rel(y32[idx], ref) < 2e-6
+
+
+def test_tensor_core_m2l_matches_cuda_core_m2l(pf):
+    """Mixed matvec with the tcgen05 BF16x3 M2L against the FP32 CUDA-core M2L on
+    the full-size hexagon block, and the first against the dense oracle on the
+    small blocks through the other tests (default mode uses tensor cores)."""
+    w = W.hexagon_8x8_n256()
+    st = pf.Solver(w)                  # m2l_mode 0: tensor cores
+    sc = pf.Solver(w, m2l_mode=1)      # CUDA cores
+    x = W.density_vector(st.E, 8)
+    yt = np.zeros_like(x)
+    yc = np.zeros_like(x)
+    y64 = np.zeros_like(x)
+    st.matvec(x, yt, pf.MIXED)
+    sc.matvec(x, yc, pf.MIXED)
+    st.matvec(x, y64, pf.FP64)
+    assert rel(yc, y64) < 2e-6
+    assert rel(yt, y64) < 2e-6
