@@ -57,15 +57,16 @@ typedef struct {
   int p;            /* expansion order at every level; 0 = per-level rule (below) */
   int p_min;        /* lower bound of the per-level rule; 0 = 16 */
   double eta;       /* coupling constant eta of eq. 4 (a real number); 0 = k */
-  int leaf_max;     /* target occupancy of a leaf box; 0 = 40 */
+  int leaf_max;     /* target occupancy of a leaf box; 0 = 64 */
   int depth;        /* quadtree depth (levels 0..depth); 0 = chosen from leaf_max */
   int gmres_m;      /* GMRES restart length; 0 = 60 */
   int precision;    /* pfmbem_precision used by pfmbem_solve; default FP64 */
   int near_mode;    /* 0 = near-field and same-fiber element integrals computed once at
                        create and kept in device memory (default); 1 = recomputed in
                        every matvec (no cache memory) */
-  int m2l_mode;     /* FP32 (mixed) M2L: 0 = tensor cores (tcgen05, BF16 x3 split, FP32
-                       accumulation) where 2(2p+1) <= 128, 1 = CUDA cores only */
+  int m2l_mode;     /* FP32 (mixed) M2L: 0 = default (CUDA cores, offset-grouped),
+                       1 = CUDA cores, 2 = tensor cores (tcgen05, BF16 x3 split, FP32
+                       accumulation in tensor memory) where 2(2p+1) <= 128 */
   int reserved[6];
 } pfmbem_options;
 
@@ -169,6 +170,41 @@ pfmbem_status pfmbem_coefficients(pfmbem_t h, const double* psi, int max_orders,
  * 2 <= |m| <= q plus the two spectral tails integrated on the contour of eq. 18.
  * S complex [2 jmax + 1], index j + jmax. */
 pfmbem_status pfmbem_lattice_sums(pfmbem_t h, int jmax, double* S);
+
+/* ---------------------------------------------------------------------------
+ * Learned warm start (beyond the paper: an AI-systems extension).  A small MLP
+ * maps the block's parameters to the low Fourier modes of both densities on
+ * every fiber; decoding them gives an initial guess for pfmbem_solve
+ * (use_guess = 1).  The network is trained on the solver's own solutions.
+ * --------------------------------------------------------------------------- */
+typedef struct pfmbem_mlp* pfmbem_mlp_t;
+
+/* MLP in -> hidden (GELU) x layers -> out (linear), FP32, weights drawn from a
+ * counter-based generator (SplitMix64 of seed and parameter index) with
+ * variance 1/fan_in, biases zero.  Parameters are one flat array: per layer W
+ * [out][in] row-major, then b [out]. */
+pfmbem_status pfmbem_mlp_create(int in, int hidden, int layers, int out, uint64_t seed, void* cuda_stream,
+                                pfmbem_mlp_t* mlp);
+void pfmbem_mlp_destroy(pfmbem_mlp_t mlp);
+/* Parameter count; optionally copies them out (get) or in (set), host or device. */
+pfmbem_status pfmbem_mlp_params(pfmbem_mlp_t mlp, int64_t* nparams, float* get, const float* set);
+/* Y [batch][out] = MLP(X [batch][in]). */
+pfmbem_status pfmbem_mlp_forward(pfmbem_mlp_t mlp, int batch, const float* X, float* Y);
+/* Mean-squared error of MLP(X) against T [batch][out] (loss, host scalar, may be
+ * NULL), its gradient with respect to the flat parameters (grad, may be NULL),
+ * and, if lr > 0, one Adam step (beta1 0.9, beta2 0.999, eps 1e-8). */
+pfmbem_status pfmbem_mlp_train(pfmbem_mlp_t mlp, int batch, const float* X, const float* T, float lr,
+                               float* loss, float* grad);
+
+/* Network input of the block: [kH/8, theta/(pi/2), per fiber ((cx-x0)/H,
+ * (cy-y0)/H, 4r/H)] with (x0, y0) the root corner; x float [2 + 3M]. */
+pfmbem_status pfmbem_warm_features(pfmbem_t h, float* x);
+/* Fourier modes n = -nmodes..nmodes of both densities of every fiber of psi,
+ * about the fiber centre and divided by the incident phase at the centre:
+ * t float [M][2][2 nmodes + 1][2] (re, im). */
+pfmbem_status pfmbem_warm_targets(pfmbem_t h, int nmodes, const double* psi, float* t);
+/* Inverse of pfmbem_warm_targets: psi0 complex [2E] from y (same layout). */
+pfmbem_status pfmbem_warm_decode(pfmbem_t h, int nmodes, const float* y, double* psi0);
 
 /* Kernel profiling (not part of the paper's method; measurement support).
  * Phases: 0 density gather, 1 P2M, 2 M2M, 3 M2L + L2L + root translation,

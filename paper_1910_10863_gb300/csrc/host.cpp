@@ -29,11 +29,30 @@ pfmbem_status fail_cuda(pfmbem* h, cudaError_t e, const char* what) {
     if (_e != cudaSuccess) return fail_cuda(h, _e, #call);  \
   } while (0)
 
+// Device allocations come from the device's stream-ordered memory pool, which
+// keeps released memory for reuse (release threshold raised once per device),
+// so that repeated create/destroy cycles of a sweep do not map memory again.
+void ensure_pool() {
+  static bool done[64] = {false};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64 || done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  cudaGetLastError();
+  done[dev] = true;
+}
+
 template <class T>
 T* dalloc(pfmbem* h, size_t n) {
   void* p = nullptr;
   if (n == 0) n = 1;
-  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
+  if (cudaMallocAsync(&p, n * sizeof(T), h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
   h->allocs.push_back(p);
   return static_cast<T*>(p);
 }
@@ -101,6 +120,7 @@ void ensure_gauss() {
   gl_thresholds(1e-14, g_thr64);
   gl_thresholds(3e-8, g_thr32);
   k_upload_gauss(x.data(), w.data(), g_thr64, g_thr32);
+  k_upload_series();
   g_gauss_ready_dev = dev;
 }
 
@@ -199,6 +219,22 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if (!(area > 0)) return fail(h, PFMBEM_EGEOM, "fiber " + std::to_string(i) + " is not counter-clockwise");
   }
   if (xmax - xmin > H) return fail(h, PFMBEM_EGEOM, "block wider than the period H along x");
+  // fiber centre (mean of the nodes) and mean radius, for the learned warm start
+  h->hfib_geo.assign(3 * (size_t)M, 0.0);
+  for (int i = 0; i < M; ++i) {
+    double sx = 0, sy = 0, sr = 0;
+    const int n = npf[i];
+    for (int j = 0; j < n; ++j) {
+      sx += nodes[2 * (foff[i] + j)];
+      sy += nodes[2 * (foff[i] + j) + 1];
+    }
+    sx /= n;
+    sy /= n;
+    for (int j = 0; j < n; ++j) sr += std::hypot(nodes[2 * (foff[i] + j)] - sx, nodes[2 * (foff[i] + j) + 1] - sy);
+    h->hfib_geo[3 * i] = sx;
+    h->hfib_geo[3 * i + 1] = sy;
+    h->hfib_geo[3 * i + 2] = sr / n;
+  }
   if (0.5 * k * hmax > 4.0) return fail(h, PFMBEM_EINVAL, "elements longer than 8/k");
   // ---------------------------------------------------- root box and wrapping
   h->x0 = 0.5 * (xmin + xmax) - 0.5 * H;
@@ -210,8 +246,19 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     m0[e] = m;
     cw[e] = double2{c[e].x, c[e].y - m * H};
   }
+  // optional set-up timing (PFMBEM_TIMING=1): wall time per section on stderr
+  const bool timing = std::getenv("PFMBEM_TIMING") != nullptr;
+  double tmark = now_ms();
+  auto mark = [&](const char* what) {
+    if (!timing) return;
+    cudaStreamSynchronize(h->stream);
+    const double t = now_ms();
+    std::fprintf(stderr, "pfmbem setup %-22s %8.2f ms\n", what, t - tmark);
+    tmark = t;
+  };
+  mark("elements");
   // ---------------------------------------------------- depth
-  const int leaf_max = h->opt.leaf_max > 0 ? h->opt.leaf_max : 40;
+  const int leaf_max = h->opt.leaf_max > 0 ? h->opt.leaf_max : 64;
   int D = h->opt.depth;
   auto leaf_of = [&](int e, int Dd) {
     int n = 1 << Dd;
@@ -275,6 +322,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
     h->info.p[l] = p;
   }
+  mark("depth, sort, levels");
   // ---------------------------------------------------- lists
   const int nD = 1 << D;
   std::vector<int64_t> nc_base;
@@ -460,6 +508,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     h->g_far = gl_order_host(qfar, g_thr64);
     h->g_far_f = gl_order_host(qfar, g_thr32);
   }
+  mark("lists");
   // ---------------------------------------------------- translation tables
   for (int l = 0; l <= D; ++l) {
     Level& L = h->lev[l];
@@ -508,8 +557,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         }
       if ((st = upload(h, &L.m2l, T)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.m2lf, to_float(T))) != PFMBEM_OK) return st;
-      if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 0) {
-        if ((st = upload(h, &L.tc_B, tc_build_operator(T, P))) != PFMBEM_OK) return st;
+      if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2) {
+        const int kp = tc_kpad(P);
+        L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
+        if (!L.tc_B) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
+        CK(k_tc_build_operator(h, l));
       } else {
         L.tc_ntile = 0;
       }
@@ -531,7 +583,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
             int j = n - m, aj = std::abs(j);
             double Jj = (j < 0 && (aj & 1)) ? -J[aj] : J[aj];
             double s = C.w[m + pc] / L.w[n + p];
-            A[((size_t)q * P + (n + p)) * Pc + (m + pc)] = cplx{s * Jj * std::cos(j * th), -s * Jj * std::sin(j * th)};
+            // stored transposed, [q][m][n], so that threads over n read contiguously
+            A[((size_t)q * Pc + (m + pc)) * P + (n + p)] = cplx{s * Jj * std::cos(j * th), -s * Jj * std::sin(j * th)};
           }
         for (int n = -pc; n <= pc; ++n)
           for (int m = -p; m <= p; ++m) {
@@ -539,7 +592,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
             int j = m - n, aj = std::abs(j);
             double Jj = (j < 0 && (aj & 1)) ? -J[aj] : J[aj];
             double s = C.w[n + pc] / L.w[m + p];
-            B[((size_t)q * Pc + (n + pc)) * P + (m + p)] = cplx{s * Jj * std::cos(j * th), s * Jj * std::sin(j * th)};
+            // stored transposed, [q][m][n] (m parent, n child coefficient)
+            B[((size_t)q * P + (m + p)) * Pc + (n + pc)] = cplx{s * Jj * std::cos(j * th), s * Jj * std::sin(j * th)};
           }
       }
       if ((st = upload(h, &L.m2m, A)) != PFMBEM_OK) return st;
@@ -548,6 +602,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if ((st = upload(h, &L.l2lf, to_float(B))) != PFMBEM_OK) return st;
     }
   }
+  mark("translation tables");
   // ---------------------------------------------------- element arrays
   {
     std::vector<double2> sc(E), st2(E), snu(E);
@@ -579,6 +634,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &h->o_h, len)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->o_fiber, fib)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->fib_off, foff)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->fib_geo, h->hfib_geo)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->o_pos, pos)) != PFMBEM_OK) return st;
   }
   h->self4 = dalloc<cplx>(h, (size_t)4 * E);
@@ -590,6 +646,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   if (!h->self4 || !h->dens || !h->U || !h->stage_in || !h->stage_out || !h->dev_rhs)
     return fail(h, PFMBEM_ENOMEM, "device allocation failed (work buffers)");
   CK(k_self_terms(h));
+  mark("element arrays, self terms");
   // ---------------------------------------------------- near-field / fiber caches
   if (h->opt.near_mode == 0 && h->max_fiber <= 1024) {
     std::vector<int64_t> fbase(M, 0);
@@ -629,7 +686,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if (!h->nc_val || !h->nc_valf || !h->fb_val || !h->fb_valf || !h->stat_dev)
         return fail(h, PFMBEM_ENOMEM, "device allocation failed (near-field caches)");
       CK(cudaMemsetAsync(h->stat_dev, 0, 4 * sizeof(unsigned long long), h->stream));
+      mark("cache allocation");
       CK(k_build_caches(h));
+      mark("near + fiber integrals");
       const size_t nc = (size_t)E * 2 * h->lev[D].P;
       h->p2m_c = dalloc<cplx>(h, nc);
       h->l2p_c = dalloc<cplx>(h, nc);
@@ -643,6 +702,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       h->cached = true;
     }
   }
+  mark("operator caches");
   // ---------------------------------------------------- lattice sums + root operator
   {
     Level& R = h->lev[0];
@@ -668,6 +728,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &h->rootf, to_float(Rt))) != PFMBEM_OK) return st;
   }
   CK(cudaStreamSynchronize(h->stream));
+  mark("lattice sums, root");
   h->info.E = E;
   h->info.M = M;
   h->info.depth = D;
@@ -865,6 +926,7 @@ pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nod
     return PFMBEM_ECUDA;
   }
   ensure_gauss();
+  ensure_pool();
   // host copies of the inputs
   std::vector<int> npf(M);
   if (is_device_ptr(nodes_per_fiber)) {
@@ -892,9 +954,9 @@ pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nod
 
 void pfmbem_destroy(pfmbem_t h) {
   if (!h) return;
+  for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
-  for (void* p : h->allocs) cudaFree(p);
   if (h->gw.hhost) cudaFreeHost(h->gw.hhost);
   prof_release(h);
   delete h;
@@ -975,6 +1037,21 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
   }
   int iters = 0, restarts = 0;
   double relres = 1;
+  if (use_guess) {
+    // keep the initial guess only if its FP64 residual is below ||B||
+    double bn = 0, rn = 0;
+    CK(k_norm2(h, g.b, (int)n, g.nrm));
+    CK(cudaMemcpyAsync(&bn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
+    CK(k_sub(h, g.b, g.w, g.d, (int)n));
+    CK(k_norm2(h, g.d, (int)n, g.nrm));
+    CK(cudaMemcpyAsync(&rn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (!(rn < bn)) {
+      CK(cudaMemsetAsync(g.x, 0, n * sizeof(cplx), h->stream));
+      use_guess = 0;
+    }
+  }
   if (h->opt.precision == PFMBEM_MIXED && h->cached) {
     // FP64 iterative refinement: r = B - A x with the FP64 operator, an inner
     // GMRES on the mixed-precision operator solves A d = r loosely, x += d.
@@ -989,8 +1066,13 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
     int refinements = 0, stalls = 0;
     double prev = 1e300;
     for (; refinements < 50; ++refinements) {
-      CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
-      CK(k_sub(h, g.b, g.w, g.d, (int)n));
+      if (refinements == 0 && !use_guess) {
+        // x = 0: the residual is B itself
+        CK(cudaMemcpyAsync(g.d, g.b, n * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+      } else {
+        CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
+        CK(k_sub(h, g.b, g.w, g.d, (int)n));
+      }
       double rn = 0;
       CK(k_norm2(h, g.d, (int)n, g.nrm));
       CK(cudaMemcpyAsync(&rn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
@@ -1099,8 +1181,8 @@ pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double
                      h->stream));
   CK(cudaStreamSynchronize(h->stream));
   // release the temporaries
-  cudaFree(pd);
-  cudaFree(ud);
+  cudaFreeAsync(pd, h->stream);
+  cudaFreeAsync(ud, h->stream);
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)pd), h->allocs.end());
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)ud), h->allocs.end());
   return PFMBEM_OK;
@@ -1147,6 +1229,61 @@ pfmbem_status pfmbem_coefficients(pfmbem_t h, const double* psi, int max_orders,
     en += kn / k0 * (r.re * r.re + r.im * r.im + t.re * t.re + t.im * t.im);
   }
   if (energy) *energy = en;
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_warm_features(pfmbem_t h, float* x) {
+  if (!h || !x) return PFMBEM_EINVAL;
+  const size_t nx = 2 + 3 * (size_t)h->M;
+  const bool dev = is_device_ptr(x);
+  float* xd = dev ? x : reinterpret_cast<float*>(h->stage_out);
+  if (!dev && nx * sizeof(float) > 2 * (size_t)h->E * sizeof(cplx)) return fail(h, PFMBEM_EINVAL, "work buffer");
+  CK(k_warm_features(h, xd));
+  if (!dev) {
+    CK(cudaMemcpyAsync(x, xd, nx * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_warm_targets(pfmbem_t h, int nmodes, const double* psi, float* t) {
+  if (!h || !psi || !t || nmodes < 0 || nmodes > 64) return PFMBEM_EINVAL;
+  const size_t n = 2 * (size_t)h->E, nt = (size_t)h->M * 2 * (2 * nmodes + 1) * 2;
+  const cplx* pd;
+  pfmbem_status st = stage_input(h, psi, n, h->stage_in, &pd);
+  if (st != PFMBEM_OK) return st;
+  const bool dev = is_device_ptr(t);
+  float* td = dev ? t : dalloc<float>(h, nt);
+  if (!td) return fail(h, PFMBEM_ENOMEM, "warm-start buffer");
+  CK(k_warm_targets(h, nmodes, pd, td));
+  if (!dev) {
+    CK(cudaMemcpyAsync(t, td, nt * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFreeAsync(td, h->stream);
+    h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)td), h->allocs.end());
+  }
+  return PFMBEM_OK;
+}
+
+pfmbem_status pfmbem_warm_decode(pfmbem_t h, int nmodes, const float* y, double* psi0) {
+  if (!h || !y || !psi0 || nmodes < 0 || nmodes > 64) return PFMBEM_EINVAL;
+  const size_t n = 2 * (size_t)h->E, ny = (size_t)h->M * 2 * (2 * nmodes + 1) * 2;
+  const bool ydev = is_device_ptr(y);
+  float* yd = const_cast<float*>(y);
+  if (!ydev) {
+    yd = dalloc<float>(h, ny);
+    if (!yd) return fail(h, PFMBEM_ENOMEM, "warm-start buffer");
+    CK(cudaMemcpyAsync(yd, y, ny * sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  }
+  const bool pdev = is_device_ptr(psi0);
+  cplx* pd = pdev ? reinterpret_cast<cplx*>(psi0) : h->stage_out;
+  CK(k_warm_decode(h, nmodes, yd, pd));
+  if (!pdev) CK(cudaMemcpyAsync(psi0, pd, n * sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (!ydev) {
+    cudaFreeAsync(yd, h->stream);
+    h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)yd), h->allocs.end());
+  }
   return PFMBEM_OK;
 }
 

@@ -117,6 +117,8 @@ struct pfmbem {
   double* o_h = nullptr;
   int* o_fiber = nullptr;
   int* fib_off = nullptr;        // [M + 1]
+  double* fib_geo = nullptr;     // [M][3] fiber centre (mean of nodes) and mean radius
+  std::vector<double> hfib_geo;
   int* o_pos = nullptr;          // original -> sorted
   cplx* self4 = nullptr;         // [E][4]: S_ee(k), T_ee(k), S_ee(k1), T_ee(k1)
   std::vector<int> hfib_off;
@@ -178,15 +180,20 @@ void prof_release(pfmbem* h);
 // outputs (kernels.cu): scattered field at points, Bragg-order coefficients
 // tensor-core M2L (m2l_tc.cu)
 int tc_kpad(int P);
-std::vector<uint16_t> tc_build_operator(const std::vector<cplx>& T, int P);
+cudaError_t k_tc_build_operator(pfmbem* h, int level);
 cudaError_t k_m2l_tc(pfmbem* h, int level, const cplxf* M, cplxf* L);
 cudaError_t k_build_caches(pfmbem* h);
 cudaError_t k_build_fmm_caches(pfmbem* h);
+// learned warm start (mlp.cu)
+cudaError_t k_warm_features(pfmbem* h, float* x_dev);
+cudaError_t k_warm_targets(pfmbem* h, int nm, const cplx* psi, float* t_dev);
+cudaError_t k_warm_decode(pfmbem* h, int nm, const float* y_dev, cplx* psi);
 cudaError_t k_field_prepare(pfmbem* h, const cplx* psi);
 cudaError_t k_coefficients(pfmbem* h, const cplx* psi, int norders, const int* orders_host, cplx* out_dev);
 
 // ------------------------------------------------------------ kernel launches
 void k_upload_gauss(const double* x, const double* w, const double* thr64, const double* thr32);
+void k_upload_series();
 cudaError_t k_self_terms(pfmbem* h);
 cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev);
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);

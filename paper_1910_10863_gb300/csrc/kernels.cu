@@ -343,6 +343,62 @@ extern "C" pfmbem_status pfmbem_lattice_sums_noalloc(double k, double H, double 
   return PFMBEM_OK;
 }
 
+// ---------------------------------------------------------------- J0, J1, Y0, Y1
+// For x <= 4 all four from the ascending series (Abramowitz & Stegun 9.1.10,
+// 9.1.11, 9.1.13 with psi(m+1) = H_m - gamma), sharing one logarithm and the
+// power recurrence in (x/2)^2; the largest term is below e^x / x, so at most
+// ~2 digits are lost to cancellation.  Larger arguments use CUDA's functions.
+// Per-term constants of the series, m = 1..39: 1/m^2, 1/(m(m+1)), H_m and
+// 2 H_m + 1/(m+1) - 2 gamma (FP64 division is slow; these are exact tables).
+__constant__ double c_ser_im2[40], c_ser_imm1[40], c_ser_H[40], c_ser_y1[40];
+
+void k_upload_series() {
+  double im2[40] = {0}, imm1[40] = {0}, H[40] = {0}, y1c[40] = {0};
+  const double EG = 0.57721566490153286061;
+  double Hm = 0.0;
+  for (int m = 1; m < 40; ++m) {
+    im2[m] = 1.0 / ((double)m * m);
+    imm1[m] = 1.0 / ((double)m * (m + 1));
+    Hm += 1.0 / m;
+    H[m] = Hm;
+    y1c[m] = 2.0 * Hm + 1.0 / (m + 1) - 2.0 * EG;
+  }
+  cudaMemcpyToSymbol(c_ser_im2, im2, sizeof(im2));
+  cudaMemcpyToSymbol(c_ser_imm1, imm1, sizeof(imm1));
+  cudaMemcpyToSymbol(c_ser_H, H, sizeof(H));
+  cudaMemcpyToSymbol(c_ser_y1, y1c, sizeof(y1c));
+}
+
+__device__ __forceinline__ void bessel01(double x, double& J0, double& J1, double& Y0, double& Y1) {
+  if (x > 4.0) {
+    J0 = j0(x); J1 = j1(x); Y0 = y0(x); Y1 = y1(x);
+    return;
+  }
+  const double h = 0.5 * x, h2 = h * h;
+  const double EG = 0.57721566490153286061;
+  // a_m = (-1)^m (x/2)^{2m} / (m!)^2,  b_m = (-1)^m (x/2)^{2m} / (m! (m+1)!)
+  double a = 1.0, b = 1.0;
+  double sJ0 = 1.0, sJ1 = 1.0, sY0 = 0.0, sY1 = -(2.0 * (-EG) + 1.0);  // m = 0 terms
+  // Y1 series term: (psi(m+1) + psi(m+2)) b_m with psi(m+1) = H_m - gamma
+  // the number of terms for |term| < 1e-17 grows with x; bound it from x
+  const int mmax = x < 0.5 ? 10 : (x < 1.5 ? 15 : (x < 3.0 ? 21 : 27));
+#pragma unroll 1
+  for (int m = 1; m < mmax; ++m) {
+    a *= -h2 * c_ser_im2[m];
+    b *= -h2 * c_ser_imm1[m];
+    sJ0 += a;
+    sJ1 += b;
+    sY0 = fma(-c_ser_H[m], a, sY0);           // (-1)^{m+1} H_m (x/2)^{2m}/(m!)^2
+    sY1 = fma(-c_ser_y1[m], b, sY1);
+  }
+  const double L = log(h);
+  J0 = sJ0;
+  J1 = h * sJ1;
+  Y0 = (2.0 / M_PI) * ((L + EG) * J0 + sY0);
+  // Y1 = -2/(pi x) + (2/pi) ln(x/2) J1 - (1/pi) sum (psi(m+1) + psi(m+2)) b_m (x/2)
+  Y1 = -2.0 / (M_PI * x) + (2.0 / M_PI) * L * J1 + (1.0 / M_PI) * h * sY1;
+}
+
 // ---------------------------------------------------------------- pair integrals
 // Element integrals of (i/4)H0(kap|x-y|) (S), its d/dnu_y (D), d/dnu_x (K) and
 // d2/dnu_x dnu_y (T) over the flat element c + s t, |s| <= h/2, by g-point
@@ -359,7 +415,8 @@ __device__ __forceinline__ void pair4_f64(double kap, double2 x, double2 nx, dou
     double r = sqrt(z1 * z1 + z2 * z2);
     double ir = 1.0 / r;
     double kr = kap * r;
-    double J0 = j0(kr), Y0 = y0(kr), J1 = j1(kr), Y1 = y1(kr);
+    double J0, J1, Y0, Y1;
+    bessel01(kr, J0, J1, Y0, Y1);
     double zy = (z1 * ny.x + z2 * ny.y) * ir;
     double zx = (z1 * nx.x + z2 * nx.y) * ir;
     S += wq * cplx{J0, Y0};
@@ -455,8 +512,8 @@ __global__ void m2m_f64_kernel(const int* __restrict__ ne, int P, int Pc, const 
     for (int i = threadIdx.x; i < Pc; i += blockDim.x) sm[i] = Mc[(size_t)ch * Pc + i];
     __syncthreads();
     if (threadIdx.x < P) {
-      const cplx* row = A + ((size_t)q * P + threadIdx.x) * Pc;
-      for (int m = 0; m < Pc; ++m) acc += row[m] * sm[m];
+      const cplx* col = A + (size_t)q * Pc * P + threadIdx.x;     // transposed [q][m][n]
+      for (int m = 0; m < Pc; ++m) acc += col[(size_t)m * P] * sm[m];
     }
   }
   if (threadIdx.x < P) Mp[(size_t)box * P + threadIdx.x] = acc;
@@ -492,8 +549,8 @@ __global__ void local_f64_kernel(const int* __restrict__ ne, int D_unused, int P
     for (int i = threadIdx.x; i < Pp; i += blockDim.x) sm[i] = Lp[(size_t)par * Pp + i];
     __syncthreads();
     if (l < P) {
-      const cplx* row = B + ((size_t)q * P + l) * Pp;
-      for (int m = 0; m < Pp; ++m) acc += row[m] * sm[m];
+      const cplx* col = B + (size_t)q * Pp * P + l;               // transposed [q][m][n]
+      for (int m = 0; m < Pp; ++m) acc += col[(size_t)m * P] * sm[m];
     }
   }
   // M2L
@@ -927,8 +984,8 @@ __global__ void m2m_t_kernel(const int* __restrict__ ne, int P, int Pc, const C*
     for (int i = threadIdx.x; i < Pc; i += blockDim.x) sm[i] = Mc[(size_t)ch * Pc + i];
     __syncthreads();
     if (threadIdx.x < P) {
-      const C* row = A + ((size_t)q * P + threadIdx.x) * Pc;
-      for (int m = 0; m < Pc; ++m) acc += row[m] * sm[m];
+      const C* col = A + (size_t)q * Pc * P + threadIdx.x;        // transposed [q][m][n]
+      for (int m = 0; m < Pc; ++m) acc += col[(size_t)m * P] * sm[m];
     }
   }
   if (threadIdx.x < P) Mp[(size_t)box * P + threadIdx.x] = acc;
@@ -960,8 +1017,8 @@ __global__ void local_t_kernel(const int* __restrict__ ne, int P, int Pp, const 
     for (int i = threadIdx.x; i < Pp; i += blockDim.x) sm[i] = Lp[(size_t)par * Pp + i];
     __syncthreads();
     if (l < P) {
-      const C* row = B + ((size_t)q * P + l) * Pp;
-      for (int m = 0; m < Pp; ++m) acc += row[m] * sm[m];
+      const C* col = B + (size_t)q * Pp * P + l;                  // transposed [q][m][n]
+      for (int m = 0; m < Pp; ++m) acc += col[(size_t)m * P] * sm[m];
     }
   }
   for (int e = ilp[ti]; e < ilp[ti + 1]; ++e) {
@@ -988,9 +1045,9 @@ __global__ void l2l_t_kernel(const int* __restrict__ ne, int P, int Pp, const C*
   for (int i = threadIdx.x; i < Pp; i += blockDim.x) sm[i] = Lp[(size_t)par * Pp + i];
   __syncthreads();
   for (int l = threadIdx.x; l < P; l += blockDim.x) {
-    const C* row = B + ((size_t)q * P + l) * Pp;
+    const C* col = B + (size_t)q * Pp * P + l;                    // transposed [q][m][n]
     C acc{0, 0};
-    for (int m = 0; m < Pp; ++m) acc += row[m] * sm[m];
+    for (int m = 0; m < Pp; ++m) acc += col[(size_t)m * P] * sm[m];
     Lout[(size_t)box * P + l] = acc;
   }
 }
@@ -1033,9 +1090,14 @@ __global__ void m2l_offset_t_kernel(int P, const int* __restrict__ chunk_off, co
     __syncwarp();
     for (int l = lane; l < P; l += 32) {
       const C* row = sT + (size_t)l * (P + 1);
-      C acc{0, 0};
-      for (int n = 0; n < P; ++n) acc += row[n] * mw[n];
-      atomic_add_c(&L[(size_t)tgt * P + l], acc);
+      C acc0{0, 0}, acc1{0, 0};            // two independent chains
+      int n = 0;
+      for (; n + 1 < P; n += 2) {
+        acc0 += row[n] * mw[n];
+        acc1 += row[n + 1] * mw[n + 1];
+      }
+      if (n < P) acc0 += row[n] * mw[n];
+      atomic_add_c(&L[(size_t)tgt * P + l], acc0 + acc1);
     }
     __syncwarp();
   }

@@ -81,10 +81,14 @@ __global__ void __launch_bounds__(TILE) m2l_tc_kernel(int P, const int* __restri
   __shared__ int s_fail;
   if (threadIdx.x == 0) s_fail = 0;
 
+  // blockIdx.x = tile, blockIdx.y = group of offsets handled by this CTA
   const int tile = blockIdx.x;
   const int t = threadIdx.x;
   const int warp = t >> 5;
-  const int noff = tile_noff[tile];
+  const int ntot = tile_noff[tile];
+  const int og = (ntot + gridDim.y - 1) / gridDim.y;
+  const int ofirst = blockIdx.y * og;
+  const int noff = max(0, min(ntot, ofirst + og) - ofirst);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -95,12 +99,6 @@ __global__ void __launch_bounds__(TILE) m2l_tc_kernel(int P, const int* __restri
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  // zero the A tiles once (padding columns stay zero)
-  {
-    uint4* p = reinterpret_cast<uint4*>(sA);
-    const int n16 = 3 * TILE * KP * 2 / 16;
-    for (int i = t; i < n16; i += TILE) p[i] = make_uint4(0, 0, 0, 0);
-  }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
@@ -109,37 +107,45 @@ __global__ void __launch_bounds__(TILE) m2l_tc_kernel(int P, const int* __restri
   uint32_t phase = 0;
   bool ok = true;
 
-  for (int oi = 0; oi < noff && ok; ++oi) {
+  for (int oj = 0; oj < noff && ok; ++oj) {
+    const int oi = ofirst + oj;
     const int o = tile_offs[tile * 49 + oi];
     const size_t ti = ((size_t)tile * 49 + oi) * TILE + t;
     const int src = tile_src[ti];
-    // A row t: alpha^m M(src) as [Re; Im], three BF16 parts
-    if (src >= 0) {
-      const int m = tile_img[ti];
+    // A row t: alpha^m M(src) as [Re; Im] (zero row without a source), three
+    // BF16 parts; one 16-byte store per core-matrix row (8 consecutive k)
+    {
+      const int m = src >= 0 ? tile_img[ti] : 0;
       cplxf ph{1.f, 0.f};
       if (m == 1) ph = to_f(alpha);
       else if (m == -1) ph = to_f(cdiv(cplx{1, 0}, alpha));
-      for (int n = 0; n < P; ++n) {
-        const cplxf v = ph * M[(size_t)src * P + n];
-        __nv_bfloat16 a0, a1, a2;
-        split3(v.re, a0, a1, a2);
-        const uint32_t oR = canon(t, n, KP) >> 1;
-        sA[oR] = a0;
-        sA[TILE * KP + oR] = a1;
-        sA[2 * TILE * KP + oR] = a2;
-        split3(v.im, a0, a1, a2);
-        const uint32_t oI = canon(t, P + n, KP) >> 1;
-        sA[oI] = a0;
-        sA[TILE * KP + oI] = a1;
-        sA[2 * TILE * KP + oI] = a2;
-      }
-    } else {
-      for (int n = 0; n < 2 * P; ++n) {
-        const uint32_t off = canon(t, n, KP) >> 1;
-        const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-        sA[off] = z;
-        sA[TILE * KP + off] = z;
-        sA[2 * TILE * KP + off] = z;
+      const cplxf* Ms = M + (size_t)(src >= 0 ? src : 0) * P;
+      for (int g = 0; g < KP / 8; ++g) {
+        uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          float x[2];
+#pragma unroll
+          for (int hh = 0; hh < 2; ++hh) {
+            const int k = 8 * g + 2 * jj + hh;
+            float v = 0.f;
+            if (src >= 0 && k < 2 * P) {
+              const cplxf z = ph * Ms[k < P ? k : k - P];
+              v = k < P ? z.re : z.im;
+            }
+            x[hh] = v;
+          }
+          __nv_bfloat16 a0, a1, a2, b0, b1, b2;
+          split3(x[0], a0, a1, a2);
+          split3(x[1], b0, b1, b2);
+          w0[jj] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(b0) << 16);
+          w1[jj] = (uint32_t)__bfloat16_as_ushort(a1) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+          w2[jj] = (uint32_t)__bfloat16_as_ushort(a2) | ((uint32_t)__bfloat16_as_ushort(b2) << 16);
+        }
+        const uint32_t off = canon(t, 8 * g, KP) >> 4;    // in 16-byte units
+        reinterpret_cast<uint4*>(sA)[off] = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+        reinterpret_cast<uint4*>(sA + TILE * KP)[off] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+        reinterpret_cast<uint4*>(sA + 2 * TILE * KP)[off] = make_uint4(w2[0], w2[1], w2[2], w2[3]);
       }
     }
     // B = T_o, three BF16 parts already in the canonical layout
@@ -162,7 +168,7 @@ __global__ void __launch_bounds__(TILE) m2l_tc_kernel(int P, const int* __restri
         for (int kk = 0; kk < KP / 16; ++kk) {
           const uint64_t ad = sdesc(abase + kk * 256, 128, SBO);
           const uint64_t bd = sdesc(bbase + kk * 256, 128, SBO);
-          const uint32_t acc = (oi > 0 || q > 0 || kk > 0) ? 1u : 0u;
+          const uint32_t acc = (oj > 0 || q > 0 || kk > 0) ? 1u : 0u;
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
@@ -205,11 +211,11 @@ __global__ void __launch_bounds__(TILE) m2l_tc_kernel(int P, const int* __restri
                      "=r"(v[7])
                    : "r"(lane_addr + c0));
       asm volatile("tcgen05.wait::ld.sync.aligned;");
-      if (tgt >= 0) {
+      if (tgt >= 0) {   // several CTAs (offset groups) add into the same target
         for (int j = 0; j < 8; ++j) {
           const int c = c0 + j;
-          if (c < P) Lr[2 * ((size_t)tgt * P + c)] += __uint_as_float(v[j]);
-          else if (c < 2 * P) Lr[2 * ((size_t)tgt * P + (c - P)) + 1] += __uint_as_float(v[j]);
+          if (c < P) atomicAdd(&Lr[2 * ((size_t)tgt * P + c)], __uint_as_float(v[j]));
+          else if (c < 2 * P) atomicAdd(&Lr[2 * ((size_t)tgt * P + (c - P)) + 1], __uint_as_float(v[j]));
         }
       }
     }
@@ -221,49 +227,47 @@ __global__ void __launch_bounds__(TILE) m2l_tc_kernel(int P, const int* __restri
   }
 }
 
-uint16_t bf16_bits(float x) {
-  __nv_bfloat16 b = __float2bfloat16_rn(x);
-  return *reinterpret_cast<uint16_t*>(&b);
-}
-float bf16_float(uint16_t u) {
-  uint32_t w = (uint32_t)u << 16;
-  float f;
-  std::memcpy(&f, &w, 4);
-  return f;
+// Operator tiles of one level in the canonical layout: three BF16 parts split
+// (in FP64) from the FP64 table T [49][P][P] (row = target coefficient) of the
+// real-embedded complex operator.  One thread per (offset, row, column).
+__global__ void tc_split_kernel(int P, int kp, const cplx* __restrict__ T, __nv_bfloat16* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n2 = (int64_t)(2 * P) * (2 * P);
+  if (i >= 49 * n2) return;
+  const int o = (int)(i / n2), rem = (int)(i % n2), c = rem / (2 * P), k = rem % (2 * P);
+  const cplx v = T[((size_t)o * P + (c % P)) * P + (k % P)];
+  double x;
+  if (c < P && k < P) x = v.re;
+  else if (c < P) x = -v.im;
+  else if (k < P) x = v.im;
+  else x = v.re;
+  const __nv_bfloat16 b0 = __float2bfloat16_rn((float)x);
+  const double r1 = x - (double)__bfloat162float(b0);
+  const __nv_bfloat16 b1 = __float2bfloat16_rn((float)r1);
+  const double r2 = r1 - (double)__bfloat162float(b1);
+  const __nv_bfloat16 b2 = __float2bfloat16_rn((float)r2);
+  const size_t base = (size_t)o * 3 * kp * kp;
+  const uint32_t off = canon(c, k, kp) >> 1;
+  out[base + off] = b0;
+  out[base + (size_t)kp * kp + off] = b1;
+  out[base + 2 * (size_t)kp * kp + off] = b2;
 }
 
 }  // namespace
 
 int tc_kpad(int P) { return ((2 * P + 15) / 16) * 16; }
 
-// Host: operator tiles of one level in the canonical layout, three BF16 parts
-// split from the FP64 table T [49][P][P] (row = target coefficient).
-std::vector<uint16_t> tc_build_operator(const std::vector<cplx>& T, int P) {
-  const int kp = tc_kpad(P);
-  std::vector<uint16_t> out((size_t)49 * 3 * kp * kp, 0);
-  for (int o = 0; o < 49; ++o) {
-    for (int c = 0; c < 2 * P; ++c)
-      for (int k = 0; k < 2 * P; ++k) {
-        const cplx v = T[((size_t)o * P + (c % P)) * P + (k % P)];
-        double x;
-        if (c < P && k < P) x = v.re;
-        else if (c < P) x = -v.im;
-        else if (k < P) x = v.im;
-        else x = v.re;
-        const float x0f = (float)x;
-        const uint16_t b0 = bf16_bits(x0f);
-        const double r1 = x - (double)bf16_float(b0);
-        const uint16_t b1 = bf16_bits((float)r1);
-        const double r2 = r1 - (double)bf16_float(b1);
-        const uint16_t b2 = bf16_bits((float)r2);
-        const size_t base = (size_t)o * 3 * kp * kp;
-        const uint32_t off = canon(c, k, kp) >> 1;
-        out[base + off] = b0;
-        out[base + (size_t)kp * kp + off] = b1;
-        out[base + 2 * (size_t)kp * kp + off] = b2;
-      }
-  }
-  return out;
+cudaError_t k_tc_build_operator(pfmbem* h, int l) {
+  Level& a = h->lev[l];
+  const int kp = tc_kpad(a.P);
+  cudaError_t e = cudaMemsetAsync(a.tc_B, 0, sizeof(uint16_t) * 49 * 3 * (size_t)kp * kp, h->stream);
+  if (e != cudaSuccess) return e;
+  const int64_t n = 49LL * (2 * a.P) * (2 * a.P);
+  prof_begin(h, PH_SETUP);
+  tc_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(a.P, kp, a.m2l,
+                                                                      reinterpret_cast<__nv_bfloat16*>(a.tc_B));
+  prof_end(h, PH_SETUP);
+  return cudaGetLastError();
 }
 
 cudaError_t k_m2l_tc(pfmbem* h, int l, const cplxf* M, cplxf* L) {
@@ -272,10 +276,19 @@ cudaError_t k_m2l_tc(pfmbem* h, int l, const cplxf* M, cplxf* L) {
   const int kp = tc_kpad(a.P);
   const size_t smem = (size_t)3 * TILE * kp * 2 + (size_t)3 * kp * kp * 2 + 16;
   cudaStream_t st = h->stream;
+  // split every tile's offsets over enough CTAs to cover the GPU about twice
+  int sms = 152;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int groups = std::max(1, std::min(4, (2 * sms + a.tc_ntile - 1) / a.tc_ntile));
+  const dim3 grid(a.tc_ntile, groups);
 #define PF_TC_CASE(KP)                                                                                    \
   case KP:                                                                                                \
     cudaFuncSetAttribute(m2l_tc_kernel<KP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
-    m2l_tc_kernel<KP><<<a.tc_ntile, TILE, smem, st>>>(a.P, a.tc_box, a.tc_noff, a.tc_offs, a.tc_src,     \
+    m2l_tc_kernel<KP><<<grid, TILE, smem, st>>>(a.P, a.tc_box, a.tc_noff, a.tc_offs, a.tc_src,           \
                                                       a.tc_img, reinterpret_cast<const __nv_bfloat16*>(a.tc_B),  \
                                                       M, h->alpha, L, h->tc_err);                         \
     break;

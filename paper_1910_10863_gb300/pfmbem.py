@@ -67,6 +67,14 @@ def lib():
             "pfmbem_profile_read": ([vp, vp], i),
             "pfmbem_probe_peak": ([i, vp], i),
             "pfmbem_lattice_sums_noalloc": ([d, d, d, i, vp, vp], i),
+            "pfmbem_mlp_create": ([i, i, i, i, ctypes.c_uint64, vp, vp], i),
+            "pfmbem_mlp_destroy": ([vp], None),
+            "pfmbem_mlp_params": ([vp, vp, vp, vp], i),
+            "pfmbem_mlp_forward": ([vp, i, vp, vp], i),
+            "pfmbem_mlp_train": ([vp, i, vp, vp, ctypes.c_float, vp, vp], i),
+            "pfmbem_warm_features": ([vp, vp], i),
+            "pfmbem_warm_targets": ([vp, i, vp, vp], i),
+            "pfmbem_warm_decode": ([vp, i, vp, vp], i),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -198,6 +206,84 @@ def pfmbem_probe_peak(dtype) -> float:
     if st != 0:
         raise PfmbemError(st, "probe failed")
     return t.value
+
+
+def _st(st, what):
+    if st != 0:
+        raise PfmbemError(st, what)
+
+
+class MLP:
+    """The warm-start network (pfmbem_mlp_*): FP32, GELU hidden layers."""
+
+    def __init__(self, n_in, hidden, layers, n_out, seed=0, stream=None):
+        h = ctypes.c_void_p()
+        _st(lib().pfmbem_mlp_create(int(n_in), int(hidden), int(layers), int(n_out), int(seed), stream,
+                                    ctypes.byref(h)), "pfmbem_mlp_create")
+        self.h = h.value
+        self.n_in, self.n_out = n_in, n_out
+
+    def close(self):
+        if self.h:
+            lib().pfmbem_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def nparams(self):
+        n = ctypes.c_int64(0)
+        _st(lib().pfmbem_mlp_params(self.h, ctypes.byref(n), None, None), "pfmbem_mlp_params")
+        return n.value
+
+    def get_params(self):
+        p = np.zeros(self.nparams(), dtype=np.float32)
+        n = ctypes.c_int64(0)
+        _st(lib().pfmbem_mlp_params(self.h, ctypes.byref(n), addr(p), None), "pfmbem_mlp_params")
+        return p
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        n = ctypes.c_int64(0)
+        _st(lib().pfmbem_mlp_params(self.h, ctypes.byref(n), None, addr(p)), "pfmbem_mlp_params")
+
+    def forward(self, X, Y=None):
+        X = np.ascontiguousarray(X, dtype=np.float32) if isinstance(X, np.ndarray) else X
+        B = X.shape[0]
+        if Y is None:
+            Y = np.zeros((B, self.n_out), dtype=np.float32)
+        _st(lib().pfmbem_mlp_forward(self.h, B, addr(X), addr(Y)), "pfmbem_mlp_forward")
+        return Y
+
+    def train(self, X, T, lr=0.0, want_grad=False):
+        """MSE loss (and gradient); lr > 0 takes one Adam step."""
+        X = np.ascontiguousarray(X, dtype=np.float32) if isinstance(X, np.ndarray) else X
+        T = np.ascontiguousarray(T, dtype=np.float32) if isinstance(T, np.ndarray) else T
+        loss = ctypes.c_float(0)
+        g = np.zeros(self.nparams(), dtype=np.float32) if want_grad else None
+        _st(lib().pfmbem_mlp_train(self.h, X.shape[0], addr(X), addr(T), float(lr), ctypes.byref(loss), addr(g)),
+            "pfmbem_mlp_train")
+        return (loss.value, g) if want_grad else loss.value
+
+
+def pfmbem_warm_features(h, M):
+    x = np.zeros(2 + 3 * M, dtype=np.float32)
+    _check(h, lib().pfmbem_warm_features(h, addr(x)))
+    return x
+
+
+def pfmbem_warm_targets(h, psi, M, nmodes=8):
+    t = np.zeros(M * 2 * (2 * nmodes + 1) * 2, dtype=np.float32)
+    _check(h, lib().pfmbem_warm_targets(h, int(nmodes), addr(psi), addr(t)))
+    return t
+
+
+def pfmbem_warm_decode(h, y, psi0, nmodes=8):
+    y = np.ascontiguousarray(y, dtype=np.float32) if isinstance(y, np.ndarray) else y
+    _check(h, lib().pfmbem_warm_decode(h, int(nmodes), addr(y), addr(psi0)))
 
 
 class Solver:

@@ -128,9 +128,10 @@ def test_invalid_inputs_rejected(pf):
 
 
 @pytest.mark.parametrize("make", SMALL)
-def test_matvec_mixed_matches_dense_oracle(pf, make):
+@pytest.mark.parametrize("m2l_mode", [1, 2])
+def test_matvec_mixed_matches_dense_oracle(pf, make, m2l_mode):
     w = make()
-    s = pf.Solver(w)
+    s = pf.Solver(w, m2l_mode=m2l_mode)
     _, Mo, _ = oracle_system(w)
     x = W.density_vector(s.E, 4)
     y = np.zeros_like(x)
@@ -210,7 +211,7 @@ def test_tensor_core_m2l_matches_cuda_core_m2l(pf):
     the full-size hexagon block, and the first against the dense oracle on the
     small blocks through the other tests (default mode uses tensor cores)."""
     w = W.hexagon_8x8_n256()
-    st = pf.Solver(w)                  # m2l_mode 0: tensor cores
+    st = pf.Solver(w, m2l_mode=2)      # tensor cores
     sc = pf.Solver(w, m2l_mode=1)      # CUDA cores
     x = W.density_vector(st.E, 8)
     yt = np.zeros_like(x)

@@ -142,3 +142,21 @@ def test_table1_square_tree(L, offset, size_c, gamma, lam):
     g, l = _gamma_lambda(offset, size_c)
     assert round(g, 4) == gamma
     assert round(l, 4) == lam
+
+
+def test_mlp_oracle_gradient_matches_finite_differences():
+    from oracle import mlp
+    dims = [5, 7, 7, 3]
+    rng = np.random.default_rng(3)
+    _, n = mlp.layout(dims)
+    p = rng.standard_normal(n) * 0.4
+    X = rng.standard_normal((4, 5))
+    T = rng.standard_normal((4, 3))
+    _, g = mlp.loss_and_grad(p, dims, X, T)
+    eps = 1e-6
+    for i in rng.choice(n, size=25, replace=False):
+        pp, pm = p.copy(), p.copy()
+        pp[i] += eps
+        pm[i] -= eps
+        fd = (mlp.loss_and_grad(pp, dims, X, T)[0] - mlp.loss_and_grad(pm, dims, X, T)[0]) / (2 * eps)
+        assert abs(fd - g[i]) < 1e-7 * max(1.0, abs(g[i]))
