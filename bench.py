@@ -196,12 +196,15 @@ def main():
     prof_acc = {"ms": np.zeros(32), "launches": np.zeros(32, dtype=np.int64)}
     stats = {}
 
+    opt_prof = pf.Options()
+    opt_prof.precision = prec
+    opt_prof.profile = 1        # kernel timing from inside pfmbem_create on
+
     def step(host=False, profile=False, o=None):
         npf, nodes, psi = (npf_h, nodes_h, psi_h) if host else (npf_d, nodes_d, psi_d)
-        h = pf.pfmbem_create(w.M, npf, nodes, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, o or opt, sptr)
+        oo = o or (opt_prof if profile else opt)
+        h = pf.pfmbem_create(w.M, npf, nodes, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, oo, sptr)
         try:
-            if profile:
-                pf.pfmbem_profile(h, True, True)
             info = pf.pfmbem_solve(h, None, psi, False, args.tol, maxit, check=False)
             if info.status != 0:
                 stats["failed_status"] = pf.STATUS.get(info.status, info.status)
@@ -294,7 +297,8 @@ def main():
     ms_ph = prof_acc["ms"]
     fp64_peak = pf.pfmbem_probe_peak(0)
     fp32_peak = pf.pfmbem_probe_peak(1)
-    roof = roofline(names, ms_ph, prof_acc["launches"], args.steps, plan, fp64_peak, fp32_peak, w.E)
+    roof = roofline(names, ms_ph, prof_acc["launches"], args.steps, plan, fp64_peak, fp32_peak, w.E,
+                    tensor_m2l=(opt.m2l_mode == 2))
     ms_ph = ms_ph / args.steps
 
     cpu = None
@@ -337,10 +341,11 @@ def pf_density(w):
 
 # Algorithmic work per unit.  Element-integral (P2P) evaluation: one unit = one
 # kernel evaluation (target collocation point x Gauss node of a source element),
-# 385 FP64 flops (2 per DFMA + DADD + DMUL, counted by ncu on the near-field and
-# same-fiber kernels of the hexagon 8x8 block).  Cached applies: bytes of the
-# resident operator plus the vectors they read and write.
-FLOPS_PER_EVAL_FP64 = 385.0
+# 255 FP64 flops (2 per DFMA + DADD + DMUL, counted by ncu on the near-field and
+# same-fiber cache-build kernels of the hexagon 8x8 block, series Hankel
+# evaluation).  Cached applies: bytes of the resident operator plus the vectors
+# they read and write.
+FLOPS_PER_EVAL_FP64 = 255.0
 
 
 def measured_peaks():
@@ -361,7 +366,7 @@ def bf16_peak():
         return 1700.0, "fallback 1.7 PFLOP/s sustained"
 
 
-def roofline(names, ms_ph, la_ph, steps, plan, fp64_peak, fp32_peak, E, tensor_m2l=True):
+def roofline(names, ms_ph, la_ph, steps, plan, fp64_peak, fp32_peak, E, tensor_m2l=False):
     dom = int(np.argmax(ms_ph))
     name = names[dom]
     ms_step = ms_ph[dom] / steps

@@ -67,7 +67,8 @@ typedef struct {
   int m2l_mode;     /* FP32 (mixed) M2L: 0 = default (CUDA cores, offset-grouped),
                        1 = CUDA cores, 2 = tensor cores (tcgen05, BF16 x3 split, FP32
                        accumulation in tensor memory) where 2(2p+1) <= 128 */
-  int reserved[6];
+  int profile;      /* 1 = record per-phase CUDA-event times from create on (see pfmbem_profile) */
+  int reserved[5];
 } pfmbem_options;
 
 /* Outcome of a solve. */
@@ -150,6 +151,16 @@ pfmbem_status pfmbem_matvec(pfmbem_t h, const double* x, double* y, int precisio
  * (psi still holds the best iterate).  info may be NULL. */
 pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_guess,
                            double tol, int maxit, pfmbem_info* info);
+
+/* Solve many blocks together (band-gap sweeps): the incident-wave systems of
+ * ninst handles are solved in lockstep, one unit of GMRES work per instance per
+ * phase, each instance's kernels on its own handle's stream, so that the GPU
+ * overlaps the work of many small blocks.  Each handle uses its own precision:
+ * FP64, or mixed (FP32 operator in the inner GMRES, FP64 residuals for the
+ * refinement).  psis[i] complex [2 E_i] receive the solutions; infos may be
+ * NULL.  Returns the first non-OK instance status (others are still solved). */
+pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* psis, double tol, int maxit,
+                                 pfmbem_info* infos);
 
 /* Scattered field u^s (eq. 7) at npts points outside the fibers, from the
  * densities psi: pts [npts][2] float64, u complex [npts]. */

@@ -650,12 +650,31 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // ---------------------------------------------------- near-field / fiber caches
   if (h->opt.near_mode == 0 && h->max_fiber <= 1024) {
     std::vector<int64_t> fbase(M, 0);
-    std::vector<int> chunks;
+    std::vector<int> chunks, circ(M, 0);
     int64_t acc = 0;
     for (int i = 0; i < M; ++i) {
+      // regular polygon (equal chords, equal turning angles): rotating by one
+      // element maps the fiber onto itself, so its block is circulant and is
+      // stored as the row pair of its first element
+      {
+        const int f0 = foff[i], n = foff[i + 1] - f0;
+        double hm = 0;
+        for (int e = f0; e < f0 + n; ++e) hm += len[e];
+        hm /= n;
+        bool reg = true;
+        double turn0 = 0;
+        for (int q = 0; q < n && reg; ++q) {
+          const int e = f0 + q, e1 = f0 + (q + 1) % n;
+          if (std::fabs(len[e] - hm) > 1e-12 * hm) reg = false;
+          const double turn = std::atan2(t[e].x * t[e1].y - t[e].y * t[e1].x, t[e].x * t[e1].x + t[e].y * t[e1].y);
+          if (q == 0) turn0 = turn;
+          else if (std::fabs(turn - turn0) > 1e-12) reg = false;
+        }
+        circ[i] = reg ? 1 : 0;
+      }
       fbase[i] = acc;
       const int n2 = 2 * (foff[i + 1] - foff[i]);
-      acc += (int64_t)n2 * n2;
+      acc += circ[i] ? (int64_t)2 * n2 : (int64_t)n2 * n2;
       for (int r = 0; r < n2; r += 64) {
         chunks.push_back(i);
         chunks.push_back(r);
@@ -673,6 +692,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if ((st = upload(h, &h->nc_src, nc_src)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->nc_img, nc_img)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->fb_base, fbase)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->fb_circ, circ)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->fb_chunk, chunks)) != PFMBEM_OK) return st;
       h->nchunk = (int)chunks.size() / 3;
       h->nc_val = dalloc<cplx>(h, (size_t)(4 * h->nc_blocks));
@@ -877,8 +897,201 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
   return relres <= tol ? PFMBEM_OK : PFMBEM_ENOCONV;
 }
 
+// ============================================================== batched solve
+// Lockstep iterative refinement over many handles: every instance is a small
+// state machine (outer FP64 residual, then Arnoldi steps of an inner GMRES on
+// the handle's operator precision); each lockstep phase enqueues one unit of
+// work per active instance on that instance's stream, then waits once for all.
+namespace {
+enum BState { B_RESID, B_ARNOLDI, B_DONE };
+struct BInst {
+  pfmbem* h = nullptr;
+  BState state = B_RESID;
+  int prec = PFMBEM_FP64;
+  double bn = 0, relres = 1, prev = 1e300, inner_tol = 1e-4, beta = 0;
+  int iters = 0, refinements = 0, stalls = 0, j = 0;
+  bool zero_x = true;
+  pfmbem_status st = PFMBEM_ENOCONV;
+  std::vector<std::complex<double>> Hm, cs, sn, gv;
+  double t0 = 0;
+};
+}  // namespace
+
+static pfmbem_status batch_enqueue(BInst& b) {
+  pfmbem* h = b.h;
+  GmresWork& g = h->gw;
+  const int n = g.n, m = g.m;
+  if (b.state == B_RESID) {
+    if (b.zero_x) {
+      CK(cudaMemcpyAsync(g.d, g.b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+      CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
+      CK(k_sub(h, g.b, g.w, g.d, n));
+    }
+    CK(k_norm2(h, g.d, n, g.nrm));
+    CK(cudaMemcpyAsync(g.hhost, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  } else if (b.state == B_ARNOLDI) {
+    cplx* vj = g.V + (size_t)b.j * n;
+    CK(k_matvec(h, vj, g.w, b.prec));
+    CK(k_multidot(h, g.V, b.j + 1, g.w, n, g.hcol));
+    CK(k_gemv_sub(h, g.V, b.j + 1, g.hcol, g.w, n));
+    CK(k_multidot(h, g.V, b.j + 1, g.w, n, g.hcol + (m + 2)));
+    CK(k_gemv_sub(h, g.V, b.j + 1, g.hcol + (m + 2), g.w, n));
+    CK(k_norm2(h, g.w, n, g.nrm));
+    CK(cudaMemcpyAsync(g.hhost, g.hcol, sizeof(cplx) * 2 * (m + 2), cudaMemcpyDeviceToHost, h->stream));
+    double* hn = reinterpret_cast<double*>(g.hhost);
+    CK(cudaMemcpyAsync(hn + 4 * (m + 2) - 2, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  }
+  return PFMBEM_OK;
+}
+
+// Finish the inner GMRES of instance b: x += V y; next is the FP64 residual.
+static pfmbem_status batch_finish_inner(BInst& b) {
+  pfmbem* h = b.h;
+  GmresWork& g = h->gw;
+  const int m = g.m, j = b.j;
+  std::vector<std::complex<double>> y(j);
+  for (int i = j - 1; i >= 0; --i) {
+    auto s = b.gv[i];
+    for (int q = i + 1; q < j; ++q) s -= b.Hm[(size_t)i * m + q] * y[q];
+    y[i] = s / b.Hm[(size_t)i * m + i];
+  }
+  // the pinned mirror is free again: this instance's stream has synchronised
+  for (int i = 0; i < j; ++i) g.hhost[i] = cplx{y[i].real(), y[i].imag()};
+  CK(cudaMemcpyAsync(g.hcol, g.hhost, sizeof(cplx) * j, cudaMemcpyHostToDevice, h->stream));
+  CK(k_gemv_add(h, g.V, j, g.hcol, g.x, g.n));
+  b.zero_x = false;
+  b.state = B_RESID;
+  return PFMBEM_OK;
+}
+
+// Host processing after the lockstep wait.
+static pfmbem_status batch_advance(BInst& b, double tol, int maxit) {
+  pfmbem* h = b.h;
+  GmresWork& g = h->gw;
+  const int n = g.n, m = g.m;
+  double* hn = reinterpret_cast<double*>(g.hhost);
+  if (b.state == B_RESID) {
+    const double rn = std::sqrt(hn[0]);
+    if (b.refinements == 0 && b.zero_x) b.bn = rn;
+    b.relres = b.bn > 0 ? rn / b.bn : 0.0;
+    if (!std::isfinite(b.relres)) { b.st = PFMBEM_ENUMERIC; b.state = B_DONE; return PFMBEM_OK; }
+    if (b.relres <= tol) { b.st = PFMBEM_OK; b.state = B_DONE; return PFMBEM_OK; }
+    if (b.iters >= maxit || b.refinements >= 50) { b.st = PFMBEM_ENOCONV; b.state = B_DONE; return PFMBEM_OK; }
+    if (b.relres > 0.5 * b.prev) {
+      if (++b.stalls >= 3) { b.st = PFMBEM_ENOCONV; b.state = B_DONE; return PFMBEM_OK; }
+    } else {
+      b.stalls = 0;
+    }
+    b.prev = b.relres;
+    b.refinements++;
+    // start an inner GMRES on d with V_0 = d / ||d||
+    b.inner_tol = b.prec == PFMBEM_MIXED ? std::max(1e-4, 0.3 * tol / b.relres) : 0.5 * tol / b.relres;
+    b.beta = rn;
+    b.j = 0;
+    std::fill(b.gv.begin(), b.gv.end(), 0.0);
+    b.gv[0] = rn;
+    CK(k_scale_copy(h, g.d, cplx{1.0 / rn, 0}, g.V, n));
+    b.state = B_ARNOLDI;
+    return PFMBEM_OK;
+  }
+  if (b.state == B_ARNOLDI) {
+    const int j = b.j;
+    const double hnext = std::sqrt(hn[4 * (m + 2) - 2]);
+    for (int i = 0; i <= j; ++i) b.Hm[(size_t)i * m + j] = toz(g.hhost[i]) + toz(g.hhost[(m + 2) + i]);
+    b.Hm[(size_t)(j + 1) * m + j] = hnext;
+    if (hnext > 0) CK(k_scale_copy(h, g.w, cplx{1.0 / hnext, 0}, g.V + (size_t)(j + 1) * n, n));
+    for (int i = 0; i < j; ++i) {
+      auto a = b.Hm[(size_t)i * m + j], bb = b.Hm[(size_t)(i + 1) * m + j];
+      b.Hm[(size_t)i * m + j] = std::conj(b.cs[i]) * a + std::conj(b.sn[i]) * bb;
+      b.Hm[(size_t)(i + 1) * m + j] = -b.sn[i] * a + b.cs[i] * bb;
+    }
+    auto a = b.Hm[(size_t)j * m + j], bb = b.Hm[(size_t)(j + 1) * m + j];
+    const double den = std::sqrt(std::norm(a) + std::norm(bb));
+    if (den == 0) { b.cs[j] = 1; b.sn[j] = 0; }
+    else { b.cs[j] = a / den; b.sn[j] = bb / den; }
+    b.Hm[(size_t)j * m + j] = std::conj(b.cs[j]) * a + std::conj(b.sn[j]) * bb;
+    b.Hm[(size_t)(j + 1) * m + j] = 0;
+    const auto gj = b.gv[j];
+    b.gv[j] = std::conj(b.cs[j]) * gj;
+    b.gv[j + 1] = -b.sn[j] * gj;
+    b.iters++;
+    b.j = j + 1;
+    const double est = std::abs(b.gv[j + 1]) / b.beta;
+    if (est <= b.inner_tol || hnext == 0 || b.j >= m || b.iters >= maxit) return batch_finish_inner(b);
+  }
+  return PFMBEM_OK;
+}
+
 // ============================================================== C ABI
 extern "C" {
+
+pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* psis, double tol, int maxit,
+                                 pfmbem_info* infos) {
+  if (ninst < 0 || (ninst > 0 && (!hs || !psis)) || !(tol > 0) || maxit < 1) return PFMBEM_EINVAL;
+  std::vector<BInst> inst(ninst);
+  const double t0 = now_ms();
+  for (int i = 0; i < ninst; ++i) {
+    pfmbem* h = hs[i];
+    if (!h || !psis[i]) return PFMBEM_EINVAL;
+    BInst& b = inst[i];
+    b.h = h;
+    b.prec = (h->opt.precision == PFMBEM_MIXED && h->cached) ? PFMBEM_MIXED : PFMBEM_FP64;
+    const int m = h->opt.gmres_m > 0 ? h->opt.gmres_m : 60;
+    pfmbem_status st = gmres_alloc(h, m);
+    if (st != PFMBEM_OK) return st;
+    GmresWork& g = h->gw;
+    b.Hm.assign((size_t)(g.m + 1) * g.m, 0.0);
+    b.cs.assign(g.m, 0.0);
+    b.sn.assign(g.m, 0.0);
+    b.gv.assign(g.m + 1, 0.0);
+    CK(k_rhs(h, g.b));
+    CK(cudaMemsetAsync(g.x, 0, sizeof(cplx) * g.n, h->stream));
+  }
+  int active = ninst;
+  while (active > 0) {
+    for (auto& b : inst)
+      if (b.state != B_DONE) {
+        pfmbem_status st = batch_enqueue(b);
+        if (st != PFMBEM_OK) return st;
+      }
+    for (auto& b : inst)
+      if (b.state != B_DONE) {
+        pfmbem* h = b.h;
+        CK(cudaStreamSynchronize(h->stream));
+      }
+    active = 0;
+    for (auto& b : inst) {
+      if (b.state == B_DONE) continue;
+      pfmbem_status st = batch_advance(b, tol, maxit);
+      if (st != PFMBEM_OK) return st;
+      if (b.state != B_DONE) ++active;
+    }
+  }
+  pfmbem_status worst = PFMBEM_OK;
+  for (int i = 0; i < ninst; ++i) {
+    BInst& b = inst[i];
+    pfmbem* h = b.h;
+    GmresWork& g = h->gw;
+    const bool pdev = is_device_ptr(psis[i]);
+    CK(cudaMemcpyAsync(psis[i], g.x, sizeof(cplx) * g.n, pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+  }
+  for (int i = 0; i < ninst; ++i) {
+    BInst& b = inst[i];
+    pfmbem* h = b.h;
+    CK(cudaStreamSynchronize(h->stream));
+    if (infos) {
+      infos[i].iters = b.iters;
+      infos[i].restarts = b.refinements;
+      infos[i].rel_residual = b.relres;
+      infos[i].ms = now_ms() - t0;
+      infos[i].status = b.st;
+    }
+    if (b.st != PFMBEM_OK && worst == PFMBEM_OK) worst = b.st;
+  }
+  return worst;
+}
 
 pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nodes_xy, double H, int lattice,
                             double k, double k1, double rho_ratio, double theta, const pfmbem_options* opt,
@@ -927,6 +1140,7 @@ pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nod
   }
   ensure_gauss();
   ensure_pool();
+  h->prof.on = h->opt.profile != 0;
   // host copies of the inputs
   std::vector<int> npf(M);
   if (is_device_ptr(nodes_per_fiber)) {

@@ -140,6 +140,7 @@ struct pfmbem {
   // cached fiber blocks: the diagonal block of (I - A) of every fiber without
   // the FMM part (identity, k1 operators, self terms), row-major [2N][2N]
   int64_t* fb_base = nullptr;    // [M] offset of the fiber's block
+  int* fb_circ = nullptr;        // [M] 1: regular polygon, circulant block stored as its row pair [2][2N]
   int* fb_chunk = nullptr;       // [nchunk][3] = fiber, first row, last row + 1
   int nchunk = 0;
   cplx* fb_val = nullptr;

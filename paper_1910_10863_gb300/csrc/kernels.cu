@@ -783,11 +783,13 @@ __global__ void fiber_build_kernel(int E, const int* __restrict__ fib, const int
                                    const double2* __restrict__ oc, const double2* __restrict__ ot,
                                    const double2* __restrict__ onu, const double* __restrict__ oh,
                                    const cplx* __restrict__ self4, cplx* __restrict__ val, cplxf* __restrict__ valf,
-                                   unsigned long long* __restrict__ stat) {
+                                   unsigned long long* __restrict__ stat, const int* __restrict__ circ) {
   const int lane = threadIdx.x & 31;
   const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (e >= E) return;
   const int fb = fib[e], f0 = foff[fb], N = foff[fb + 1] - f0, el = e - f0;
+  // circulant fiber: only the first element's row pair is stored
+  if (circ[fb] && el != 0) return;
   const int64_t r0 = fbase[fb] + (int64_t)(2 * el) * (2 * N), r1 = r0 + 2 * N;
   const double2 xe = oc[e], nxe = onu[e];
   const cplx c2r = rho * c2;
@@ -847,7 +849,8 @@ cudaError_t k_build_caches(pfmbem* h) {
   prof_begin(h, PH_BUILD);
   fiber_build_kernel<<<(h->E * 32 + 255) / 256, 256, 0, st>>>(h->E, h->o_fiber, h->fib_off, h->fb_base, h->k1,
                                                               h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu, h->o_h,
-                                                              h->self4, h->fb_val, h->fb_valf, h->stat_dev);
+                                                              h->self4, h->fb_val, h->fb_valf, h->stat_dev,
+                                                              h->fb_circ);
   prof_end(h, PH_BUILD);
   return cudaGetLastError();
 }
@@ -1205,23 +1208,31 @@ template <class C>
 __global__ void fiber_apply_t_kernel(const int* __restrict__ chunk, const int* __restrict__ foff,
                                      const int64_t* __restrict__ fbase, const C* __restrict__ val,
                                      const int* __restrict__ opos, const cplx* __restrict__ sph, cplx c2,
-                                     const cplx* __restrict__ x, const C* __restrict__ U, cplx* __restrict__ y) {
+                                     const cplx* __restrict__ x, const C* __restrict__ U, cplx* __restrict__ y,
+                                     const int* __restrict__ circ) {
   __shared__ C xs[2 * 1024];
   const int fb = chunk[3 * blockIdx.x], rb = chunk[3 * blockIdx.x + 1], re = chunk[3 * blockIdx.x + 2];
   const int f0 = foff[fb], N = foff[fb + 1] - f0, n2 = 2 * N;
+  const bool cir = circ[fb] != 0;
   for (int i = threadIdx.x; i < n2; i += blockDim.x) xs[i] = from_d<C>(x[2 * f0 + i]);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   // a warp takes the row pair (2e, 2e+1) of one element; four independent
-  // accumulators per row keep eight loads in flight per lane
+  // accumulators per row keep eight loads in flight per lane.  A circulant
+  // block is read from its generating row pair with x rotated by 2e:
+  // sum_c R[(c - 2e) mod 2N] x[c] = sum_c R[c] x[(c + 2e) mod 2N].
   for (int r = rb + 2 * warp; r < re; r += 2 * nw) {
-    const C* row0 = val + fbase[fb] + (int64_t)r * n2;
+    const C* row0 = val + fbase[fb] + (cir ? 0 : (int64_t)r * n2);
     const C* row1 = row0 + n2;
+    const int sh = cir ? r : 0;
     const bool two = r + 1 < re;
     C a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
     int c = lane;
     for (; c + 32 < n2; c += 64) {
-      const C x0 = xs[c], x1 = xs[c + 32];
+      int i0 = c + sh, i1 = c + 32 + sh;
+      if (i0 >= n2) i0 -= n2;
+      if (i1 >= n2) i1 -= n2;
+      const C x0 = xs[i0], x1 = xs[i1];
       const C r00 = row0[c], r01 = row0[c + 32];
       a0 += r00 * x0;
       a1 += r01 * x1;
@@ -1232,8 +1243,10 @@ __global__ void fiber_apply_t_kernel(const int* __restrict__ chunk, const int* _
       }
     }
     for (; c < n2; c += 32) {
-      a0 += row0[c] * xs[c];
-      if (two) b0 += row1[c] * xs[c];
+      int i0 = c + sh;
+      if (i0 >= n2) i0 -= n2;
+      a0 += row0[c] * xs[i0];
+      if (two) b0 += row1[c] * xs[i0];
     }
     const C s0 = warp_sum_t(a0 + a1);
     const C s1 = warp_sum_t(b0 + b1);
@@ -1358,7 +1371,7 @@ static cudaError_t matvec_cached(pfmbem* h, const cplx* x, cplx* y, const Ops<C>
   cplx c2{h->c2re, h->c2im};
   prof_begin(h, PH_FIBER + po);
   fiber_apply_t_kernel<C><<<h->nchunk, 256, 0, st>>>(h->fb_chunk, h->fib_off, h->fb_base, o.fiber, h->o_pos, h->s_ph,
-                                                     c2, x, o.U, y);
+                                                     c2, x, o.U, y, h->fb_circ);
   prof_end(h, PH_FIBER + po);
   return cudaGetLastError();
 }

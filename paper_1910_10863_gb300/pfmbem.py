@@ -24,7 +24,7 @@ class Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("p_min", ctypes.c_int), ("eta", ctypes.c_double),
                 ("leaf_max", ctypes.c_int), ("depth", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("precision", ctypes.c_int), ("near_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 6)]
+                ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
 
 
 class Info(ctypes.Structure):
@@ -75,6 +75,7 @@ def lib():
             "pfmbem_warm_features": ([vp, vp], i),
             "pfmbem_warm_targets": ([vp, i, vp, vp], i),
             "pfmbem_warm_decode": ([vp, i, vp, vp], i),
+            "pfmbem_solve_batch": ([i, vp, vp, d, i, vp], i),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -147,6 +148,16 @@ def pfmbem_solve(h, B, psi, use_guess=False, tol=1e-8, maxit=1000, check=True) -
     if check:
         _check(h, st)
     return info
+
+
+def pfmbem_solve_batch(handles, psis, tol=1e-6, maxit=2000):
+    """Lockstep solve of many handles; psis are complex128 buffers (host or device)."""
+    n = len(handles)
+    hs = (ctypes.c_void_p * n)(*handles)
+    ps = (ctypes.c_void_p * n)(*[addr(p) for p in psis])
+    infos = (Info * n)()
+    st = lib().pfmbem_solve_batch(n, hs, ps, float(tol), int(maxit), infos)
+    return st, list(infos)
 
 
 def pfmbem_lattice_sums(h, jmax, S):

@@ -58,6 +58,39 @@ def train(X, T, hidden=256, layers=3, epochs=200, batch=256, lr=1e-3, seed=1913,
     return net, hist
 
 
+def main():
+    """Train on --train band-gap-sweep blocks (M = 16) and report the gain on
+    --test held-out blocks drawn from a disjoint seed; one JSON line."""
+    import argparse
+    import json
+    import time
+
+    from . import workloads as W
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--train", type=int, default=8192)
+    ap.add_argument("--test", type=int, default=1024)
+    ap.add_argument("--epochs", type=int, default=100)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    a = ap.parse_args()
+    t0 = time.perf_counter()
+    X, T, _ = generate(W.batch_instances(a.train, seed=1912), tol=a.tol)
+    t1 = time.perf_counter()
+    net, hist = train(X, T, epochs=a.epochs, batch=a.batch, lr=a.lr)
+    t2 = time.perf_counter()
+    rows = evaluate(net, W.batch_instances(a.test, seed=1915), tol=a.tol)
+    t3 = time.perf_counter()
+    iz, iw, r0 = rows[:, 0], rows[:, 1], rows[:, 2]
+    print(json.dumps({
+        "train_blocks": a.train, "test_blocks": a.test, "epochs": a.epochs, "final_loss": hist[-1],
+        "first_loss": hist[0], "mean_iters_zero_start": float(iz.mean()), "mean_iters_warm_start": float(iw.mean()),
+        "median_warm_start_residual": float(np.median(r0)), "fraction_guess_kept": float(np.mean(r0 < 1.0)),
+        "mean_solve_ms_zero": float(rows[:, 5].mean()), "mean_solve_ms_warm": float(rows[:, 6].mean()),
+        "all_converged": bool(np.all(rows[:, 3] <= a.tol) and np.all(rows[:, 4] <= a.tol)),
+        "seconds": {"data": t1 - t0, "train": t2 - t1, "evaluate": t3 - t2}}), flush=True)
+
+
 def evaluate(net, instances, tol=1e-6):
     """Per instance: zero-start and warm-start GMRES iterations and the FP64
     relative residual of the warm start itself."""
@@ -80,3 +113,7 @@ def evaluate(net, instances, tol=1e-6):
         rows.append((iz.iters, iw.iters, res0, iz.rel_residual, iw.rel_residual, iz.ms, iw.ms))
         s.close()
     return np.array(rows)
+
+
+if __name__ == "__main__":
+    main()

@@ -90,6 +90,27 @@ def square_block(nx: int, ny: int, H: float, r_frac: float, n: int, kH: float, t
     return _from_fibers(name or f"square_{nx}x{ny}_n{n}_kH{kH:g}", H, 0, kH, theta, centres, radii, npf, matrix)
 
 
+def round_square_nodes(cx: float, cy: float, r: float, n: int) -> np.ndarray:
+    """Nodes of the round-square scatterer of Sec. 4,
+    (r (3 + 2 sin^2 t) cos t, r (3 + 2 cos^2 t) sin t), at n uniform parameter values."""
+    t = 2.0 * np.pi * np.arange(n) / n
+    return np.stack([cx + r * (3 + 2 * np.sin(t) ** 2) * np.cos(t), cy + r * (3 + 2 * np.cos(t) ** 2) * np.sin(t)],
+                    axis=1)
+
+
+def round_square_block(nx: int, ny: int, H: float, extent_frac: float, n: int, kH: float, theta: float,
+                       name: str | None = None) -> Workload:
+    """Square lattice of round-square scatterers whose half-extent 3r is extent_frac * a."""
+    a = H / ny
+    r = extent_frac * a / 3.0
+    k, k1, rho = _materials(kH, H)
+    centres = [((ix + 0.5) * a, (iy + 0.5) * a) for ix in range(nx) for iy in range(ny)]
+    nodes = np.concatenate([round_square_nodes(c[0], c[1], r, n) for c in centres])
+    return Workload(name=name or f"roundsquare_{nx}x{ny}_n{n}_kH{kH:g}", H=H, lattice=0, k=k, k1=k1, rho_ratio=rho,
+                    theta=theta, nodes_per_fiber=np.full(len(centres), n, dtype=np.int32), nodes=nodes,
+                    centres=np.asarray(centres), radii=np.full(len(centres), 3 * r))
+
+
 def square_2x2_n64():
     """Square lattice, H = 1, 2x2 circles at 0.25/0.75, r = 0.15, 64 elements each, kH = 2, theta = 30 deg."""
     w = square_block(2, 2, 1.0, 0.3, 64, 2.0, math.radians(30.0), name="square_2x2_n64_kH2")

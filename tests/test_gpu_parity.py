@@ -207,9 +207,9 @@ def test_full_size_hexagon_rows(pf):
 
 
 def test_tensor_core_m2l_matches_cuda_core_m2l(pf):
-    """Mixed matvec with the tcgen05 BF16x3 M2L against the FP32 CUDA-core M2L on
-    the full-size hexagon block, and the first against the dense oracle on the
-    small blocks through the other tests (default mode uses tensor cores)."""
+    """Mixed matvec with the tcgen05 BF16x3 M2L against the FP32 CUDA-core M2L and
+    the FP64 matvec on the full-size hexagon block (the small blocks check both
+    M2L engines against the dense oracle in test_matvec_mixed_matches_dense_oracle)."""
     w = W.hexagon_8x8_n256()
     st = pf.Solver(w, m2l_mode=2)      # tensor cores
     sc = pf.Solver(w, m2l_mode=1)      # CUDA cores
@@ -222,3 +222,18 @@ def test_tensor_core_m2l_matches_cuda_core_m2l(pf):
     st.matvec(x, y64, pf.FP64)
     assert rel(yc, y64) < 2e-6
     assert rel(yt, y64) < 2e-6
+
+
+def test_round_square_scatterers_full_fiber_blocks(pf):
+    """Round-square scatterers (Sec. 4) are not regular polygons, so their
+    same-fiber blocks are stored in full (the circles use the circulant form)."""
+    w = W.round_square_block(2, 2, 1.0, 0.35, 40, 2.5, math.radians(20))
+    pb = bem.problem(w)
+    Mo = bem.operator_rows(pb)
+    x = W.density_vector(w.E, 12)
+    s = pf.Solver(w)
+    assert s.plan().fiber_entries == 4 * (2 * 40) ** 2
+    for prec, tol in ((pf.FP64, 1e-8), (pf.MIXED, 2e-6)):
+        y = np.zeros_like(x)
+        s.matvec(x, y, prec)
+        assert rel(y, Mo @ x) < tol

@@ -1,0 +1,76 @@
+"""Learned warm start: network gradients against the FP64 oracle, the Fourier
+feature/target/decode kernels, and what the trained network gains over zero-start
+GMRES on held-out blocks (M = 16 fibers, band-gap-sweep style)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_1910_10863_gb300 import workloads as W
+from tests.gpu_common import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def pf():
+    ensure_built()
+    from paper_1910_10863_gb300 import pfmbem
+    return pfmbem
+
+
+def test_mlp_loss_and_gradient_match_fp64_oracle(pf):
+    dims = [50, 256, 256, 256, 1088]
+    net = pf.MLP(50, 256, 3, 1088, seed=7)
+    rng = np.random.default_rng(0)
+    X = rng.standard_normal((16, 50)).astype(np.float32)
+    T = rng.standard_normal((16, 1088)).astype(np.float32) * 0.1
+    loss, g = net.train(X, T, lr=0.0, want_grad=True)
+    p = net.get_params().astype(np.float64)
+    lo, go = omlp.loss_and_grad(p, dims, X.astype(np.float64), T.astype(np.float64))
+    assert abs(loss - lo) < 1e-5 * abs(lo)
+    assert np.linalg.norm(g - go) < 1e-4 * np.linalg.norm(go)
+    Y = net.forward(X)
+    Yo, _, _ = omlp.forward(p, dims, X)
+    assert np.max(np.abs(Y - Yo)) < 1e-4 * np.max(np.abs(Yo))
+
+
+def test_adam_steps_reduce_the_loss(pf):
+    net = pf.MLP(8, 32, 2, 4, seed=1)
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((64, 8)).astype(np.float32)
+    T = np.tanh(X[:, :4]).astype(np.float32)
+    first = net.train(X, T)
+    for _ in range(200):
+        net.train(X, T, lr=3e-3)
+    assert net.train(X, T) < 0.2 * first
+
+
+def test_warm_targets_and_decode_are_inverse_on_band_limited_densities(pf):
+    w = W.batch_instances(2, seed=5)[0]
+    s = pf.Solver(w)
+    rng = np.random.default_rng(2)
+    nm = 8
+    coef = (rng.standard_normal((w.M, 2, 2 * nm + 1)) + 1j * rng.standard_normal((w.M, 2, 2 * nm + 1))) * 0.5
+    y = np.stack([coef.real, coef.imag], axis=-1).astype(np.float32).ravel()
+    psi = np.zeros(2 * s.E, dtype=np.complex128)
+    pf.pfmbem_warm_decode(s.h, y, psi, nm)
+    t = pf.pfmbem_warm_targets(s.h, psi, w.M, nm)
+    assert np.max(np.abs(t - y)) < 1e-5 * np.max(np.abs(y))
+    x = pf.pfmbem_warm_features(s.h, w.M)
+    assert x.shape == (50,) and abs(x[0] - w.k * w.H / 8) < 1e-6 and abs(x[1] - w.theta / (math.pi / 2)) < 1e-6
+
+
+def test_trained_network_reduces_gmres_iterations_on_held_out_blocks(pf):
+    from paper_1910_10863_gb300 import warmstart as ws
+    train = W.batch_instances(320, seed=101)
+    test = W.batch_instances(24, seed=202)
+    X, T, _ = ws.generate(train)
+    net, hist = ws.train(X, T, epochs=150, batch=64, lr=2e-3, seed=3)
+    assert hist[-1] < 0.5 * hist[0]
+    rows = ws.evaluate(net, test)
+    iz, iw, res0 = rows[:, 0], rows[:, 1], rows[:, 2]
+    assert np.all(rows[:, 3] <= 1e-6) and np.all(rows[:, 4] <= 1e-6)     # both solves converge
+    assert np.median(res0) < 1.0                                         # the guess beats a zero start
+    assert iw.mean() < iz.mean()
