@@ -49,7 +49,7 @@ template <class T>
 T* dalloc(pfmbem* h, size_t n) {
   void* p = nullptr;
   if (n == 0) n = 1;
-  if (cudaMallocAsync(&p, n * sizeof(T), h->stream) != cudaSuccess) {
+  if (cudaMallocAsync(&p, n * sizeof(T), h->astream ? h->astream : h->stream) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
@@ -61,7 +61,9 @@ template <class T>
 pfmbem_status upload(pfmbem* h, T** dst, const std::vector<T>& src) {
   *dst = dalloc<T>(h, src.size());
   if (!*dst) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
-  if (!src.empty()) CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream));
+  if (!src.empty())
+    CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice,
+                       h->astream ? h->astream : h->stream));
   return PFMBEM_OK;
 }
 
@@ -251,7 +253,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   double tmark = now_ms();
   auto mark = [&](const char* what) {
     if (!timing) return;
-    cudaStreamSynchronize(h->stream);
+    cudaStreamSynchronize(h->astream ? h->astream : h->stream);
     const double t = now_ms();
     std::fprintf(stderr, "pfmbem setup %-22s %8.2f ms\n", what, t - tmark);
     tmark = t;
@@ -386,6 +388,193 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
     h->nc_blocks = acc / 4;
   }
+  // fiber-local statistics (the cache build counts them on the GPU)
+  {
+    int64_t pairs = 0, quad = 0;
+    for (int i = 0; h->opt.near_mode != 0 && i < M; ++i)
+      for (int e = foff[i]; e < foff[i + 1]; ++e)
+        for (int f = foff[i]; f < foff[i + 1]; ++f) {
+          if (f == e) continue;
+          double q = std::hypot(c[e].x - c[f].x, c[e].y - c[f].y) / len[f];
+          pairs++;
+          quad += gl_order_host(q, g_thr64);
+        }
+    h->info.fiber_pairs = pairs;
+    h->info.fiber_quad = quad;
+  }
+  // P2M Gauss nodes: elements outside the near field are at least one leaf
+  // side minus half an element length away.
+  {
+    double qfar = std::max(1.0, h->lev[D].d / hmax - 1.0);
+    h->g_far = gl_order_host(qfar, g_thr64);
+    h->g_far_f = gl_order_host(qfar, g_thr32);
+  }
+  // box ranges and expansion weights of every level
+  for (int l = 0; l <= D; ++l) {
+    Level& L = h->lev[l];
+    pfmbem_status st;
+    if ((st = upload(h, &L.w_dev, L.w)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.ne, L.hne)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.box_begin, L.hbegin)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.box_end, L.hend)) != PFMBEM_OK) return st;
+  }
+  mark("near lists");
+  // ---------------------------------------------------- element arrays
+  {
+    std::vector<double2> sc(E), st2(E), snu(E);
+    std::vector<double> sh(E);
+    std::vector<cplx> sph(E);
+    for (int s = 0; s < E; ++s) {
+      int e = perm[s];
+      sc[s] = cw[e];
+      st2[s] = t[e];
+      snu[s] = nu[e];
+      sh[s] = len[e];
+      // alpha^{-m0}
+      double a = -m0[e] * h->beta;
+      sph[s] = cplx{std::cos(a), std::sin(a)};
+    }
+    pfmbem_status st;
+    if ((st = upload(h, &h->s_c, sc)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_t, st2)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_nu, snu)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_h, sh)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_ph, sph)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->s_perm, perm)) != PFMBEM_OK) return st;
+    std::vector<int> sleaf(E);
+    for (int s2 = 0; s2 < E; ++s2) sleaf[s2] = key[perm[s2]];
+    if ((st = upload(h, &h->s_leaf, sleaf)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_c, c)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_t, t)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_nu, nu)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_h, len)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_fiber, fib)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->fib_off, foff)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->fib_geo, h->hfib_geo)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_pos, pos)) != PFMBEM_OK) return st;
+  }
+  h->self4 = dalloc<cplx>(h, (size_t)4 * E);
+  h->dens = dalloc<cplx>(h, (size_t)2 * E);
+  h->U = dalloc<cplx>(h, (size_t)2 * E);
+  h->stage_in = dalloc<cplx>(h, (size_t)2 * E);
+  h->stage_out = dalloc<cplx>(h, (size_t)2 * E);
+  h->dev_rhs = dalloc<cplx>(h, (size_t)2 * E);
+  if (!h->self4 || !h->dens || !h->U || !h->stage_in || !h->stage_out || !h->dev_rhs)
+    return fail(h, PFMBEM_ENOMEM, "device allocation failed (work buffers)");
+  CK(k_self_terms(h));
+  mark("element arrays, self terms");
+  // ---------------------------------------------------- lattice sums + root operator
+  if (!h->side_ev) CK(cudaEventCreateWithFlags(&h->side_ev, cudaEventDisableTiming));
+  {
+    Level& R = h->lev[0];
+    const int p0 = R.p, P0 = R.P, jmax = 2 * p0;
+    cplx* Sd = dalloc<cplx>(h, jmax + 1);
+    if (!Sd) return fail(h, PFMBEM_ENOMEM, "device allocation failed (lattice sums)");
+    CK(k_lattice_sums(h, jmax, h->lattice_q, Sd));
+    h->lattice_S.resize(jmax + 1);
+    CK(cudaMemcpyAsync(h->lattice_S.data(), Sd, sizeof(cplx) * (jmax + 1), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaEventRecord(h->side_ev, h->stream));   // waits for the sums only, not for later work
+    CK(cudaEventSynchronize(h->side_ev));
+    std::vector<cplx> Rt((size_t)P0 * P0);
+    for (int a = -p0; a <= p0; ++a)
+      for (int n = -p0; n <= p0; ++n) {
+        cplx s = h->lattice_S[std::abs(n - a)];
+        double sc = R.w[a + p0] * R.w[n + p0];
+        cplx v{sc * s.re, sc * s.im};
+        if (!std::isfinite(v.re) || !std::isfinite(v.im))
+          return fail(h, PFMBEM_ENUMERIC, "non-finite lattice sums");
+        Rt[(size_t)(a + p0) * P0 + (n + p0)] = v;
+      }
+    pfmbem_status st;
+    if ((st = upload(h, &h->root, Rt)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->rootf, to_float(Rt))) != PFMBEM_OK) return st;
+  }
+  mark("lattice sums, root");
+  // ---------------------------------------------------- near-field / fiber caches
+  // The element integrals of the caches run on the GPU while the host builds
+  // the M2L lists and translation tables on a second stream; the streams join
+  // before the P2M/L2P caches.
+  bool cache = false;
+  if (h->opt.near_mode == 0 && h->max_fiber <= 1024) {
+    std::vector<int64_t> fbase(M, 0);
+    std::vector<int> chunks, circ(M, 0);
+    int64_t acc = 0;
+    for (int i = 0; i < M; ++i) {
+      // regular polygon (equal chords, equal turning angles): rotating by one
+      // element maps the fiber onto itself, so its block is circulant and is
+      // stored as the row pair of its first element
+      {
+        const int f0 = foff[i], n = foff[i + 1] - f0;
+        double hm = 0;
+        for (int e = f0; e < f0 + n; ++e) hm += len[e];
+        hm /= n;
+        bool reg = true;
+        double turn0 = 0;
+        for (int q = 0; q < n && reg; ++q) {
+          const int e = f0 + q, e1 = f0 + (q + 1) % n;
+          if (std::fabs(len[e] - hm) > 1e-12 * hm) reg = false;
+          const double turn = std::atan2(t[e].x * t[e1].y - t[e].y * t[e1].x, t[e].x * t[e1].x + t[e].y * t[e1].y);
+          if (q == 0) turn0 = turn;
+          else if (std::fabs(turn - turn0) > 1e-12) reg = false;
+        }
+        circ[i] = reg ? 1 : 0;
+      }
+      fbase[i] = acc;
+      const int n2 = 2 * (foff[i + 1] - foff[i]);
+      acc += circ[i] ? (int64_t)2 * n2 : (int64_t)n2 * n2;
+      for (int r = 0; r < n2; r += 64) {
+        chunks.push_back(i);
+        chunks.push_back(r);
+        chunks.push_back(std::min(r + 64, n2));
+      }
+    }
+    h->fb_entries = acc;
+    const double bytes = (double)(4 * h->nc_blocks + acc) * (sizeof(cplx) + sizeof(cplxf));
+    size_t freeb = 0, totb = 0;
+    CK(cudaMemGetInfo(&freeb, &totb));
+    if (bytes < 0.5 * (double)freeb) {
+      pfmbem_status st;
+      if ((st = upload(h, &h->nc_base, nc_base)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->nc_sbase, nc_sbase)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->nc_src, nc_src)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->nc_img, nc_img)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->fb_base, fbase)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->fb_circ, circ)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->fb_chunk, chunks)) != PFMBEM_OK) return st;
+      // k tables of the regular-polygon fibers and the wrap shift of every element
+      std::vector<int64_t> kbase(M, -1);
+      int64_t kacc = 0;
+      for (int i = 0; i < M; ++i)
+        if (circ[i]) {
+          kbase[i] = kacc;
+          kacc += foff[i + 1] - foff[i];
+        }
+      std::vector<int> sm0(E);
+      for (int s2 = 0; s2 < E; ++s2) sm0[s2] = m0[perm[s2]];
+      if ((st = upload(h, &h->kt_base, kbase)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->s_m0, sm0)) != PFMBEM_OK) return st;
+      h->kt_val = dalloc<cplx>(h, (size_t)4 * kacc);
+      if (!h->kt_val) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
+      h->nchunk = (int)chunks.size() / 3;
+      h->nc_val = dalloc<cplx>(h, (size_t)(4 * h->nc_blocks));
+      h->nc_valf = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
+      h->fb_val = dalloc<cplx>(h, (size_t)acc);
+      h->fb_valf = dalloc<cplxf>(h, (size_t)acc);
+      h->stat_dev = dalloc<unsigned long long>(h, 4);
+      h->tc_err = dalloc<int>(h, 1);
+      if (!h->tc_err) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
+      CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
+      if (!h->nc_val || !h->nc_valf || !h->fb_val || !h->fb_valf || !h->stat_dev)
+        return fail(h, PFMBEM_ENOMEM, "device allocation failed (near-field caches)");
+      CK(cudaMemsetAsync(h->stat_dev, 0, 4 * sizeof(unsigned long long), h->stream));
+      mark("cache allocation");
+      CK(k_build_caches(h));
+      cache = true;
+    }
+  }
+  if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  if (!h->side_ev) CK(cudaEventCreateWithFlags(&h->side_ev, cudaEventDisableTiming));
+  h->astream = h->side;
   int64_t m2l_pairs = 0;
   for (int l = 1; l <= D; ++l) {
     Level& L = h->lev[l];
@@ -487,38 +676,12 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
   }
   h->info.m2l_pairs = m2l_pairs;
-  // fiber-local statistics
-  {
-    int64_t pairs = 0, quad = 0;
-    for (int i = 0; h->opt.near_mode != 0 && i < M; ++i)
-      for (int e = foff[i]; e < foff[i + 1]; ++e)
-        for (int f = foff[i]; f < foff[i + 1]; ++f) {
-          if (f == e) continue;
-          double q = std::hypot(c[e].x - c[f].x, c[e].y - c[f].y) / len[f];
-          pairs++;
-          quad += gl_order_host(q, g_thr64);
-        }
-    h->info.fiber_pairs = pairs;
-    h->info.fiber_quad = quad;
-  }
-  // P2M Gauss nodes: elements outside the near field are at least one leaf
-  // side minus half an element length away.
-  {
-    double qfar = std::max(1.0, h->lev[D].d / hmax - 1.0);
-    h->g_far = gl_order_host(qfar, g_thr64);
-    h->g_far_f = gl_order_host(qfar, g_thr32);
-  }
-  mark("lists");
+  mark("M2L lists (overlapped)");
   // ---------------------------------------------------- translation tables
   for (int l = 0; l <= D; ++l) {
     Level& L = h->lev[l];
     const int p = L.p, P = L.P;
     pfmbem_status st;
-    if ((st = upload(h, &L.w_dev, L.w)) != PFMBEM_OK) return st;
-    std::vector<int> ne(L.hne);
-    if ((st = upload(h, &L.ne, ne)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &L.box_begin, L.hbegin)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &L.box_end, L.hend)) != PFMBEM_OK) return st;
     L.M = dalloc<cplx>(h, (size_t)L.nbox * P);
     L.L = dalloc<cplx>(h, (size_t)L.nbox * P);
     L.Mf = dalloc<cplxf>(h, (size_t)L.nbox * P);
@@ -561,7 +724,6 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         const int kp = tc_kpad(P);
         L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
         if (!L.tc_B) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
-        CK(k_tc_build_operator(h, l));
       } else {
         L.tc_ntile = 0;
       }
@@ -602,153 +764,29 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if ((st = upload(h, &L.l2lf, to_float(B))) != PFMBEM_OK) return st;
     }
   }
-  mark("translation tables");
-  // ---------------------------------------------------- element arrays
-  {
-    std::vector<double2> sc(E), st2(E), snu(E);
-    std::vector<double> sh(E);
-    std::vector<cplx> sph(E);
-    for (int s = 0; s < E; ++s) {
-      int e = perm[s];
-      sc[s] = cw[e];
-      st2[s] = t[e];
-      snu[s] = nu[e];
-      sh[s] = len[e];
-      // alpha^{-m0}
-      double a = -m0[e] * h->beta;
-      sph[s] = cplx{std::cos(a), std::sin(a)};
-    }
-    pfmbem_status st;
-    if ((st = upload(h, &h->s_c, sc)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->s_t, st2)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->s_nu, snu)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->s_h, sh)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->s_ph, sph)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->s_perm, perm)) != PFMBEM_OK) return st;
-    std::vector<int> sleaf(E);
-    for (int s2 = 0; s2 < E; ++s2) sleaf[s2] = key[perm[s2]];
-    if ((st = upload(h, &h->s_leaf, sleaf)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->o_c, c)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->o_t, t)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->o_nu, nu)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->o_h, len)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->o_fiber, fib)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->fib_off, foff)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->fib_geo, h->hfib_geo)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->o_pos, pos)) != PFMBEM_OK) return st;
+  mark("translation tables (overlapped)");
+  // join: later work on the main stream sees every upload of the second stream
+  CK(cudaEventRecord(h->side_ev, h->side));
+  CK(cudaStreamWaitEvent(h->stream, h->side_ev, 0));
+  h->astream = nullptr;
+  for (int l = 1; l <= D; ++l)
+    if (h->lev[l].tc_B) CK(k_tc_build_operator(h, l));
+  if (cache) {
+    const size_t nc = (size_t)E * 2 * h->lev[D].P;
+    h->p2m_c = dalloc<cplx>(h, nc);
+    h->l2p_c = dalloc<cplx>(h, nc);
+    h->p2m_cf = dalloc<cplxf>(h, nc);
+    h->l2p_cf = dalloc<cplxf>(h, nc);
+    h->densf = dalloc<cplxf>(h, (size_t)2 * E);
+    h->Uf = dalloc<cplxf>(h, (size_t)2 * E);
+    if (!h->p2m_c || !h->l2p_c || !h->p2m_cf || !h->l2p_cf || !h->densf || !h->Uf)
+      return fail(h, PFMBEM_ENOMEM, "device allocation failed (P2M/L2P caches)");
+    CK(k_build_fmm_caches(h));
+    h->cached = true;
   }
-  h->self4 = dalloc<cplx>(h, (size_t)4 * E);
-  h->dens = dalloc<cplx>(h, (size_t)2 * E);
-  h->U = dalloc<cplx>(h, (size_t)2 * E);
-  h->stage_in = dalloc<cplx>(h, (size_t)2 * E);
-  h->stage_out = dalloc<cplx>(h, (size_t)2 * E);
-  h->dev_rhs = dalloc<cplx>(h, (size_t)2 * E);
-  if (!h->self4 || !h->dens || !h->U || !h->stage_in || !h->stage_out || !h->dev_rhs)
-    return fail(h, PFMBEM_ENOMEM, "device allocation failed (work buffers)");
-  CK(k_self_terms(h));
-  mark("element arrays, self terms");
-  // ---------------------------------------------------- near-field / fiber caches
-  if (h->opt.near_mode == 0 && h->max_fiber <= 1024) {
-    std::vector<int64_t> fbase(M, 0);
-    std::vector<int> chunks, circ(M, 0);
-    int64_t acc = 0;
-    for (int i = 0; i < M; ++i) {
-      // regular polygon (equal chords, equal turning angles): rotating by one
-      // element maps the fiber onto itself, so its block is circulant and is
-      // stored as the row pair of its first element
-      {
-        const int f0 = foff[i], n = foff[i + 1] - f0;
-        double hm = 0;
-        for (int e = f0; e < f0 + n; ++e) hm += len[e];
-        hm /= n;
-        bool reg = true;
-        double turn0 = 0;
-        for (int q = 0; q < n && reg; ++q) {
-          const int e = f0 + q, e1 = f0 + (q + 1) % n;
-          if (std::fabs(len[e] - hm) > 1e-12 * hm) reg = false;
-          const double turn = std::atan2(t[e].x * t[e1].y - t[e].y * t[e1].x, t[e].x * t[e1].x + t[e].y * t[e1].y);
-          if (q == 0) turn0 = turn;
-          else if (std::fabs(turn - turn0) > 1e-12) reg = false;
-        }
-        circ[i] = reg ? 1 : 0;
-      }
-      fbase[i] = acc;
-      const int n2 = 2 * (foff[i + 1] - foff[i]);
-      acc += circ[i] ? (int64_t)2 * n2 : (int64_t)n2 * n2;
-      for (int r = 0; r < n2; r += 64) {
-        chunks.push_back(i);
-        chunks.push_back(r);
-        chunks.push_back(std::min(r + 64, n2));
-      }
-    }
-    h->fb_entries = acc;
-    const double bytes = (double)(4 * h->nc_blocks + acc) * (sizeof(cplx) + sizeof(cplxf));
-    size_t freeb = 0, totb = 0;
-    CK(cudaMemGetInfo(&freeb, &totb));
-    if (bytes < 0.5 * (double)freeb) {
-      pfmbem_status st;
-      if ((st = upload(h, &h->nc_base, nc_base)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->nc_sbase, nc_sbase)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->nc_src, nc_src)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->nc_img, nc_img)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->fb_base, fbase)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->fb_circ, circ)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->fb_chunk, chunks)) != PFMBEM_OK) return st;
-      h->nchunk = (int)chunks.size() / 3;
-      h->nc_val = dalloc<cplx>(h, (size_t)(4 * h->nc_blocks));
-      h->nc_valf = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
-      h->fb_val = dalloc<cplx>(h, (size_t)acc);
-      h->fb_valf = dalloc<cplxf>(h, (size_t)acc);
-      h->stat_dev = dalloc<unsigned long long>(h, 4);
-      h->tc_err = dalloc<int>(h, 1);
-      if (!h->tc_err) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
-      CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
-      if (!h->nc_val || !h->nc_valf || !h->fb_val || !h->fb_valf || !h->stat_dev)
-        return fail(h, PFMBEM_ENOMEM, "device allocation failed (near-field caches)");
-      CK(cudaMemsetAsync(h->stat_dev, 0, 4 * sizeof(unsigned long long), h->stream));
-      mark("cache allocation");
-      CK(k_build_caches(h));
-      mark("near + fiber integrals");
-      const size_t nc = (size_t)E * 2 * h->lev[D].P;
-      h->p2m_c = dalloc<cplx>(h, nc);
-      h->l2p_c = dalloc<cplx>(h, nc);
-      h->p2m_cf = dalloc<cplxf>(h, nc);
-      h->l2p_cf = dalloc<cplxf>(h, nc);
-      h->densf = dalloc<cplxf>(h, (size_t)2 * E);
-      h->Uf = dalloc<cplxf>(h, (size_t)2 * E);
-      if (!h->p2m_c || !h->l2p_c || !h->p2m_cf || !h->l2p_cf || !h->densf || !h->Uf)
-        return fail(h, PFMBEM_ENOMEM, "device allocation failed (P2M/L2P caches)");
-      CK(k_build_fmm_caches(h));
-      h->cached = true;
-    }
-  }
-  mark("operator caches");
-  // ---------------------------------------------------- lattice sums + root operator
-  {
-    Level& R = h->lev[0];
-    const int p0 = R.p, P0 = R.P, jmax = 2 * p0;
-    cplx* Sd = dalloc<cplx>(h, jmax + 1);
-    if (!Sd) return fail(h, PFMBEM_ENOMEM, "device allocation failed (lattice sums)");
-    CK(k_lattice_sums(h, jmax, h->lattice_q, Sd));
-    h->lattice_S.resize(jmax + 1);
-    CK(cudaMemcpyAsync(h->lattice_S.data(), Sd, sizeof(cplx) * (jmax + 1), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    std::vector<cplx> Rt((size_t)P0 * P0);
-    for (int a = -p0; a <= p0; ++a)
-      for (int n = -p0; n <= p0; ++n) {
-        cplx s = h->lattice_S[std::abs(n - a)];
-        double sc = R.w[a + p0] * R.w[n + p0];
-        cplx v{sc * s.re, sc * s.im};
-        if (!std::isfinite(v.re) || !std::isfinite(v.im))
-          return fail(h, PFMBEM_ENUMERIC, "non-finite lattice sums");
-        Rt[(size_t)(a + p0) * P0 + (n + p0)] = v;
-      }
-    pfmbem_status st;
-    if ((st = upload(h, &h->root, Rt)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->rootf, to_float(Rt))) != PFMBEM_OK) return st;
-  }
+  mark("near + fiber integrals, P2M/L2P caches");
   CK(cudaStreamSynchronize(h->stream));
-  mark("lattice sums, root");
+  mark("end of set-up");
   h->info.E = E;
   h->info.M = M;
   h->info.depth = D;
@@ -1168,10 +1206,13 @@ pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nod
 
 void pfmbem_destroy(pfmbem_t h) {
   if (!h) return;
+  if (h->side) cudaStreamSynchronize(h->side);
   for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   if (h->gw.hhost) cudaFreeHost(h->gw.hhost);
+  if (h->side_ev) cudaEventDestroy(h->side_ev);
+  if (h->side) cudaStreamDestroy(h->side);
   prof_release(h);
   delete h;
 }

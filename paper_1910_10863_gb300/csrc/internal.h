@@ -94,6 +94,9 @@ struct pfmbem {
   double c2re = 0, c2im = 0;     // c2 = 2 / (i eta (1 + rho))
   pfmbem_options opt{};
   cudaStream_t stream = nullptr;
+  cudaStream_t side = nullptr;   // second stream of the set-up: host planning overlaps the cache build
+  cudaEvent_t side_ev = nullptr;
+  cudaStream_t astream = nullptr;  // stream of allocations and uploads while set-up runs on `side`
   std::string err;
   // plan
   int D = 0;
@@ -142,6 +145,9 @@ struct pfmbem {
   int64_t* fb_base = nullptr;    // [M] offset of the fiber's block
   int* fb_circ = nullptr;        // [M] 1: regular polygon, circulant block stored as its row pair [2][2N]
   int* fb_chunk = nullptr;       // [nchunk][3] = fiber, first row, last row + 1
+  int* s_m0 = nullptr;           // sorted: periods the element was shifted by when wrapped into the root
+  int64_t* kt_base = nullptr;    // [M] first entry of the fiber's k table, -1 when not a regular polygon
+  cplx* kt_val = nullptr;        // [sum N over regular fibers][4]: S, D, K, T at k of (f0, f0 + dl)
   int nchunk = 0;
   cplx* fb_val = nullptr;
   cplxf* fb_valf = nullptr;

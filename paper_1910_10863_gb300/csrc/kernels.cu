@@ -722,6 +722,9 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
                                   const int* __restrict__ srcf, const int* __restrict__ srcm, double k, double eta,
                                   double H, cplx alpha, const double2* __restrict__ sc, const double2* __restrict__ st,
                                   const double2* __restrict__ snu, const double* __restrict__ sh,
+                                  const int* __restrict__ perm, const int* __restrict__ ofib,
+                                  const int* __restrict__ foff, const int* __restrict__ sm0,
+                                  const int64_t* __restrict__ kbase, const cplx* __restrict__ kval,
                                   cplx* __restrict__ val, cplxf* __restrict__ valf,
                                   unsigned long long* __restrict__ stat) {
   const int li = blockIdx.x;
@@ -733,21 +736,38 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
   for (int t = warp; t < nt; t += nw) {
     const int s = s0 + t;
     const double2 x = sc[s], nx = snu[s];
+    // target's fiber; kb >= 0 when the fiber is a regular polygon with a table
+    const int es = perm[s], fs = ofib[es], ms = sm0[s];
+    const int64_t kb = kbase[fs];
+    const int fN = foff[fs + 1] - foff[fs];
     cplx* row = val + base[li] + (int64_t)t * ns * 4;
     cplxf* rowf = valf ? valf + base[li] + (int64_t)t * ns * 4 : nullptr;
     for (int j = lane; j < ns; j += 32) {
       const int f = srcf[j0 + j], m = srcm[j0 + j];
       cplx b0{0, 0}, b1{0, 0}, b2{0, 0}, b3{0, 0};
       if (!(f == s && m == 0)) {
-        double2 c = sc[f];
-        c.y += m * H;
-        const double hh = sh[f];
-        const double q = sqrt((x.x - c.x) * (x.x - c.x) + (x.y - c.y) * (x.y - c.y)) / hh;
-        const int g = gl_order(q, 0);
-        ++npair;
-        nquad += g;
         cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
-        pair4_f64(k, x, nx, c, st[f], snu[f], hh, g, S, Dv, K, T);
+        const int ef = perm[f];
+        // same fiber and, in true coordinates, the same image (the wrapped copies
+        // differ by m + m0_s - m0_f periods): the pair is a rotation of a table entry
+        if (kb >= 0 && ofib[ef] == fs && m + ms - sm0[f] == 0) {
+          int dl = ef - es;
+          if (dl < 0) dl += fN;
+          const cplx* tv = kval + 4 * (kb + dl);
+          S = tv[0];
+          Dv = tv[1];
+          K = tv[2];
+          T = tv[3];
+        } else {
+          double2 c = sc[f];
+          c.y += m * H;
+          const double hh = sh[f];
+          const double q = sqrt((x.x - c.x) * (x.x - c.x) + (x.y - c.y) * (x.y - c.y)) / hh;
+          const int g = gl_order(q, 0);
+          ++npair;
+          nquad += g;
+          pair4_f64(k, x, nx, c, st[f], snu[f], hh, g, S, Dv, K, T);
+        }
         const cplx ph = mul_i(0.25 * ipow_phase(alpha, m));      // (i/4) alpha^m
         b0 = ph * Dv;
         b1 = (-eta) * mul_i(ph * S);
@@ -765,6 +785,46 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
         rowf[4 * j + 3] = cplxf{(float)b3.re, (float)b3.im};
       }
     }
+  }
+  if (stat) {
+    atomicAdd(&stat[0], npair);
+    atomicAdd(&stat[1], nquad);
+  }
+}
+
+// Same-fiber integrals at the matrix wavenumber k of a regular-polygon fiber:
+// S, D, K, T (without the factor i/4) of its first element's midpoint against
+// element f0 + dl, dl = 1..N-1 (dl = 0, the self element, stays zero).  Rotating
+// the fiber by one element maps it onto itself, so element pair (e, e + dl) has
+// the integrals of (f0, f0 + dl) and the near-field build reads them from here.
+// One warp per fiber.
+__global__ void ktab_build_kernel(int M, const int* __restrict__ foff, const int64_t* __restrict__ kbase, double k,
+                                  const double2* __restrict__ oc, const double2* __restrict__ ot,
+                                  const double2* __restrict__ onu, const double* __restrict__ oh,
+                                  cplx* __restrict__ kval, unsigned long long* __restrict__ stat) {
+  const int lane = threadIdx.x & 31;
+  const int fb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (fb >= M || kbase[fb] < 0) return;
+  const int f0 = foff[fb], N = foff[fb + 1] - f0;
+  const double2 xe = oc[f0], nxe = onu[f0];
+  cplx* out = kval + 4 * kbase[fb];
+  unsigned long long npair = 0, nquad = 0;
+  for (int dl = lane; dl < N; dl += 32) {
+    cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
+    if (dl > 0) {
+      const int f = f0 + dl;
+      const double2 c = oc[f];
+      const double hh = oh[f];
+      const double q = sqrt((xe.x - c.x) * (xe.x - c.x) + (xe.y - c.y) * (xe.y - c.y)) / hh;
+      const int g = gl_order(q, 0);
+      ++npair;
+      nquad += g;
+      pair4_f64(k, xe, nxe, c, ot[f], onu[f], hh, g, S, Dv, K, T);
+    }
+    out[4 * dl + 0] = S;
+    out[4 * dl + 1] = Dv;
+    out[4 * dl + 2] = K;
+    out[4 * dl + 3] = T;
   }
   if (stat) {
     atomicAdd(&stat[0], npair);
@@ -842,9 +902,14 @@ cudaError_t k_build_caches(pfmbem* h) {
   Level& leaf = h->lev[h->D];
   cplx c2{h->c2re, h->c2im};
   prof_begin(h, PH_BUILD);
+  ktab_build_kernel<<<(h->M * 32 + 255) / 256, 256, 0, st>>>(h->M, h->fib_off, h->kt_base, h->k, h->o_c, h->o_t,
+                                                             h->o_nu, h->o_h, h->kt_val, h->stat_dev);
+  prof_end(h, PH_BUILD);
+  prof_begin(h, PH_BUILD);
   near_build_kernel<<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
                                               h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c, h->s_t,
-                                              h->s_nu, h->s_h, h->nc_val, h->nc_valf, h->stat_dev);
+                                              h->s_nu, h->s_h, h->s_perm, h->o_fiber, h->fib_off, h->s_m0,
+                                              h->kt_base, h->kt_val, h->nc_val, h->nc_valf, h->stat_dev);
   prof_end(h, PH_BUILD);
   prof_begin(h, PH_BUILD);
   fiber_build_kernel<<<(h->E * 32 + 255) / 256, 256, 0, st>>>(h->E, h->o_fiber, h->fib_off, h->fb_base, h->k1,

@@ -237,3 +237,25 @@ def test_round_square_scatterers_full_fiber_blocks(pf):
         y = np.zeros_like(x)
         s.matvec(x, y, prec)
         assert rel(y, Mo @ x) < tol
+
+
+def test_full_size_square_32x32_rows(pf):
+    """square 32x32, 128 elements per fiber (131072 elements, kH = 20, level-
+    dependent orders up to the root): sampled rows of the FP64 and mixed matvecs
+    against rows of the dense oracle operator."""
+    w = W.square_32x32_n128()
+    s = pf.Solver(w)
+    plan = s.plan()
+    assert plan.p[0] > plan.p[plan.depth]          # orders grow toward the root at kH = 20
+    x = W.density_vector(s.E, 7)
+    y64 = np.zeros_like(x)
+    y32 = np.zeros_like(x)
+    s.matvec(x, y64, pf.FP64)
+    s.matvec(x, y32, pf.MIXED)
+    rng = np.random.default_rng(1)
+    rows_e = np.sort(rng.choice(s.E, size=4, replace=False))
+    pb = bem.problem(w)
+    ref = bem.operator_rows(pb, rows_e) @ x
+    idx = np.ravel(np.stack([2 * rows_e, 2 * rows_e + 1], axis=1))
+    assert rel(y64[idx], ref) < 1e-8
+    assert rel(y32[idx], ref) < 2e-6
