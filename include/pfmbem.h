@@ -68,7 +68,11 @@ typedef struct {
                        1 = CUDA cores, 2 = tensor cores (tcgen05, BF16 x3 split, FP32
                        accumulation in tensor memory) where 2(2p+1) <= 128 */
   int profile;      /* 1 = record per-phase CUDA-event times from create on (see pfmbem_profile) */
-  int reserved[5];
+  int launch;       /* cached matvec: 0 = one cooperative launch per product with a
+                       device-wide barrier between the stages (default; the tensor-core
+                       M2L and devices without cooperative launch use 1); 1 = one kernel
+                       per stage */
+  int reserved[4];
 } pfmbem_options;
 
 /* Outcome of a solve. */
@@ -146,9 +150,12 @@ pfmbem_status pfmbem_matvec(pfmbem_t h, const double* x, double* y, int precisio
  *   psi   complex [2E]; input initial guess if use_guess != 0, output solution
  *   tol   relative residual target (FP64 true residual)
  *   maxit maximum matrix-vector products
- * In mixed precision the inner GMRES uses the mixed matvec and an outer FP64
- * refinement loop restores FP64 accuracy.  Returns ENOCONV if tol is not met
- * (psi still holds the best iterate).  info may be NULL. */
+ * A guess x is first scaled by the gamma minimising ||B - gamma (I - A) x||
+ * (one FP64 matvec) and kept only if that residual is below ||B||; otherwise
+ * the solve starts from zero.  In mixed precision the inner GMRES uses the
+ * mixed matvec and an outer FP64 refinement loop restores FP64 accuracy.
+ * Returns ENOCONV if tol is not met (psi still holds the best iterate).
+ * info may be NULL. */
 pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_guess,
                            double tol, int maxit, pfmbem_info* info);
 

@@ -40,6 +40,7 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
     k_obj = os.path.join(BUILD, "kernels.o")
     t_obj = os.path.join(BUILD, "m2l_tc.o")
     m_obj = os.path.join(BUILD, "mlp.o")
+    f_obj = os.path.join(BUILD, "matvec_fused.o")
     h_obj = os.path.join(BUILD, "host.o")
     nv_flags = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--use_fast_math=false"]
     nv_flags = [f for f in nv_flags if f != "--use_fast_math=false"]
@@ -49,12 +50,13 @@ def build(verbose: bool = False, ptxas_info: bool = False) -> str:
         nv_flags + inc + ["-c", os.path.join(CSRC, "kernels.cu"), "-o", k_obj],
         nv_flags + inc + ["-c", os.path.join(CSRC, "m2l_tc.cu"), "-o", t_obj],
         nv_flags + inc + ["-c", os.path.join(CSRC, "mlp.cu"), "-o", m_obj],
+        nv_flags + inc + ["-c", os.path.join(CSRC, "matvec_fused.cu"), "-o", f_obj],
         ["g++", "-O2", "-fPIC", "-std=c++17", "-Wall", "-Wno-unused-function"] + inc
         + ["-c", os.path.join(CSRC, "host.cpp"), "-o", h_obj],
     ]
     with ThreadPoolExecutor(len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
-    logs.append(_run([nvcc, ARCH, "-shared", "-Xcompiler", "-fPIC", k_obj, t_obj, m_obj, h_obj, "-o", LIB]))
+    logs.append(_run([nvcc, ARCH, "-shared", "-Xcompiler", "-fPIC", k_obj, t_obj, m_obj, f_obj, h_obj, "-o", LIB]))
     if verbose:
         print("\n".join(l for l in logs if l.strip()))
     return "\n".join(logs)

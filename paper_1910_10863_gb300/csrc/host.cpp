@@ -720,6 +720,16 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         }
       if ((st = upload(h, &L.m2l, T)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.m2lf, to_float(T))) != PFMBEM_OK) return st;
+      {
+        // transposed copy for the single-launch matvec: [o][source n][target a]
+        std::vector<cplx> Tt(T.size());
+        for (int o = 0; o < 49; ++o)
+          for (int a2 = 0; a2 < P; ++a2)
+            for (int n2 = 0; n2 < P; ++n2)
+              Tt[((size_t)o * P + n2) * P + a2] = T[((size_t)o * P + a2) * P + n2];
+        if ((st = upload(h, &L.m2lt, Tt)) != PFMBEM_OK) return st;
+        if ((st = upload(h, &L.m2ltf, to_float(Tt))) != PFMBEM_OK) return st;
+      }
       if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2) {
         const int kp = tc_kpad(P);
         L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
@@ -783,6 +793,21 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       return fail(h, PFMBEM_ENOMEM, "device allocation failed (P2M/L2P caches)");
     CK(k_build_fmm_caches(h));
     h->cached = true;
+    // single-launch matvec unless the tensor-core M2L (its own kernel) is on
+    bool tensor = false;
+    for (int l = 1; l <= D; ++l) tensor = tensor || (h->lev[l].tc_B != nullptr && h->lev[l].tc_ntile > 0);
+    if (h->opt.launch == 0 && !tensor) {
+      bool ok = false;
+      CK(k_fused_prepare(h, &ok));
+      if (ok) {
+        h->fz_bar = dalloc<unsigned>(h, 2);
+        h->fz_err = dalloc<int>(h, 1);
+        if (!h->fz_bar || !h->fz_err) return fail(h, PFMBEM_ENOMEM, "device allocation failed (barrier)");
+        CK(cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned), h->stream));
+        CK(cudaMemsetAsync(h->fz_err, 0, sizeof(int), h->stream));
+        h->fused = true;
+      }
+    }
   }
   mark("near + fiber integrals, P2M/L2P caches");
   CK(cudaStreamSynchronize(h->stream));
@@ -1293,16 +1318,27 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
   int iters = 0, restarts = 0;
   double relres = 1;
   if (use_guess) {
-    // keep the initial guess only if its FP64 residual is below ||B||
-    double bn = 0, rn = 0;
-    CK(k_norm2(h, g.b, (int)n, g.nrm));
-    CK(cudaMemcpyAsync(&bn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    // Scale the guess x by the gamma minimising ||B - gamma A x|| (w = A x from
+    // one FP64 matvec, gamma = <w, B> / <w, w>); the scaled guess is kept when
+    // its residual d = B - gamma w is below ||B||, else the solve starts at zero.
+    double nn[2] = {0, 0}, rn = 0;
+    cplx wb{0, 0};
     CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
-    CK(k_sub(h, g.b, g.w, g.d, (int)n));
+    CK(k_norm2(h, g.b, (int)n, g.nrm));
+    CK(k_norm2(h, g.w, (int)n, g.nrm + 1));
+    CK(k_multidot(h, g.w, 1, g.b, (int)n, g.hcol));
+    CK(cudaMemcpyAsync(nn, g.nrm, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&wb, g.hcol, sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    const cplx gam = nn[1] > 0 ? cplx{wb.re / nn[1], wb.im / nn[1]} : cplx{0, 0};
+    CK(k_scale_copy(h, g.x, gam, g.c, (int)n));
+    CK(cudaMemcpyAsync(g.x, g.c, n * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(g.d, g.b, n * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+    CK(k_axpy(h, cplx{-gam.re, -gam.im}, g.w, g.d, (int)n));
     CK(k_norm2(h, g.d, (int)n, g.nrm));
     CK(cudaMemcpyAsync(&rn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    if (!(rn < bn)) {
+    if (!(rn < nn[0])) {
       CK(cudaMemsetAsync(g.x, 0, n * sizeof(cplx), h->stream));
       use_guess = 0;
     }
@@ -1324,6 +1360,8 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
       if (refinements == 0 && !use_guess) {
         // x = 0: the residual is B itself
         CK(cudaMemcpyAsync(g.d, g.b, n * sizeof(cplx), cudaMemcpyDeviceToDevice, h->stream));
+      } else if (refinements == 0) {
+        // the scaled guess: d = B - gamma A x is already in place
       } else {
         CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
         CK(k_sub(h, g.b, g.w, g.d, (int)n));
@@ -1364,6 +1402,14 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
     if (e) {
       st = PFMBEM_ETIMEOUT;
       h->err = "tensor-core M2L: a bounded wait for the MMA completion gave up";
+    }
+  }
+  if (h->fz_err) {
+    int e = 0;
+    CK(cudaMemcpy(&e, h->fz_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+      st = PFMBEM_ETIMEOUT;
+      h->err = "single-launch matvec: a bounded device-wide barrier wait gave up";
     }
   }
   if (info) {

@@ -2,6 +2,7 @@
 // the host planner/driver (host.cpp) and the CUDA kernels (kernels.cu).
 #pragma once
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -49,6 +50,8 @@ struct Level {
   int* tc_img = nullptr;     // [ntile][49][128]
   uint16_t* tc_B = nullptr;  // [49][3][kp][kp] BF16 parts of the real-embedded operators
   cplx* m2l = nullptr;       // [49][P][P]: row = target coefficient, col = source coefficient
+  cplx* m2lt = nullptr;      // the same operators transposed, [49][P source][P target]
+  cplxf* m2ltf = nullptr;
   cplx* m2m = nullptr;       // children (level l+1) -> this level: [4][P][P_child]
   cplx* l2l = nullptr;       // this level -> children: [4][P_child][P]
   // FP32 copies for the mixed path
@@ -74,7 +77,7 @@ struct GmresWork {
 };
 
 enum Phase { PH_GATHER = 0, PH_P2M, PH_M2M, PH_LOCAL, PH_L2P, PH_NEAR, PH_FIBER, PH_BLAS, PH_SETUP, PH_OUT, PH_BUILD,
-             PH_COUNT };
+             PH_FUSED, PH_COUNT };
 
 // Launch counters and optional CUDA-event timing per phase.
 struct Prof {
@@ -164,6 +167,11 @@ struct pfmbem {
   int* tc_err = nullptr;         // set by the tensor-core M2L when a bounded wait gave up
   cplxf* densf = nullptr;        // [E][2]
   cplxf* Uf = nullptr;           // [E][2]
+  // single-launch cached matvec (cooperative grid, device-wide barrier)
+  bool fused = false;
+  int fz_grid64 = 0, fz_grid32 = 0;
+  unsigned* fz_bar = nullptr;    // [2] barrier arrivals and generation
+  int* fz_err = nullptr;         // set when a bounded barrier wait gave up
   cplx* root = nullptr;          // [P0][P0] periodic root translation
   cplxf* rootf = nullptr;
   std::vector<cplx> lattice_S;   // S_j, j = 0..2 p0 (S_-j = S_j)
@@ -190,6 +198,9 @@ int tc_kpad(int P);
 cudaError_t k_tc_build_operator(pfmbem* h, int level);
 cudaError_t k_m2l_tc(pfmbem* h, int level, const cplxf* M, cplxf* L);
 cudaError_t k_build_caches(pfmbem* h);
+// single-launch cached matvec (matvec_fused.cu)
+cudaError_t k_fused_prepare(pfmbem* h, bool* ok);
+cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_build_fmm_caches(pfmbem* h);
 // learned warm start (mlp.cu)
 cudaError_t k_warm_features(pfmbem* h, float* x_dev);

@@ -1489,6 +1489,7 @@ static void upward_f64(pfmbem* h, const cplx* x) {
 }
 
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision) {
+  if (h->cached && h->fused) return k_matvec_fused(h, x, y, precision);
   if (h->cached) {
     if (precision == PFMBEM_MIXED) return matvec_cached(h, x, y, ops32(h));
     return matvec_cached(h, x, y, ops64(h));

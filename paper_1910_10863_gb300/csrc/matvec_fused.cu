@@ -1,0 +1,489 @@
+// The cached matrix-vector product (I - A) x of eq. 9 as ONE cooperative launch.
+//
+// The per-stage path launches some twenty small kernels per product (gather,
+// P2M, one M2M per level, one L2L + M2L per level, L2P, near field, fiber
+// blocks); at the sizes of a fundamental block most of them are latency-bound.
+// Here one grid of co-resident blocks runs the stages back to back and
+// separates them with a device-wide barrier:
+//
+//   A   gather the densities into tree order (alpha^{-m0} phase) and P2M  (warp per leaf)
+//   B_l M2M into level l = D-1 .. 0; at the root also L(0) = R M(0)       (warp per box)
+//   D_l L2L from the parent plus M2L over the interaction list, l = 1..D  (warp per box)
+//   E   L2P + cached near field for every element of a leaf               (block per leaf)
+//   F   cached fiber blocks and the combination of eq. 9                  (block per row chunk)
+//
+// The arithmetic of every stage is that of the per-stage kernels (same tables,
+// same summation order within a box), so both paths agree to rounding.
+//
+// The barrier is a counter plus a generation word in device memory.  The
+// cooperative launch guarantees that every block is resident, so every wait
+// ends; each wait is nevertheless bounded (about one second), after which the
+// block records an error flag and returns, and the host reports
+// PFMBEM_ETIMEOUT instead of a result.
+#include "internal.h"
+
+namespace {
+
+constexpr int FB = 256;          // threads per block
+constexpr int FW = FB / 32;      // warps per block
+constexpr int FSTAGE = 1536;     // near-field source densities staged in shared memory per leaf
+constexpr int FPASS = (PF_NCOEF + 31) / 32;   // lane passes over the coefficients of one box
+
+template <class C>
+struct FusedArgs {
+  int E, D;
+  const int* perm;               // sorted -> original element
+  const cplx* ph;                // alpha^{-m0} of every sorted element
+  const int* opos;               // original -> sorted
+  const cplx* x;                 // input, original order, FP64
+  cplx* y;                       // output, original order, FP64
+  C* dens;                       // sorted (phi', varphi')
+  C* U;                          // sorted (U', dU')
+  int nne[PF_MAXLEVEL + 1];
+  int P[PF_MAXLEVEL + 1];
+  const int* ne[PF_MAXLEVEL + 1];
+  const int* bb[PF_MAXLEVEL + 1];
+  const int* be[PF_MAXLEVEL + 1];
+  const int* ilp[PF_MAXLEVEL + 1];
+  const int* ils[PF_MAXLEVEL + 1];
+  const int* ilo[PF_MAXLEVEL + 1];
+  const int* ilm[PF_MAXLEVEL + 1];
+  const C* m2m[PF_MAXLEVEL + 1];     // at the parent level: [q][m child][n parent]
+  const C* l2l[PF_MAXLEVEL + 1];     // at the parent level: [q][m parent][n child]
+  const C* m2lt[PF_MAXLEVEL + 1];    // [o][n source][l target]
+  C* M[PF_MAXLEVEL + 1];
+  C* L[PF_MAXLEVEL + 1];
+  const C* root;                     // [l][n], lattice-sum translation at the root
+  const C* p2m;                      // [E][2][P_D]
+  const C* l2p;                      // [E][2][P_D]
+  const int64_t* nc_base;
+  const int* nc_sbase;
+  const int* nc_src;
+  const C* nc_val;
+  int nchunk;
+  const int* fb_chunk;
+  const int* foff;
+  const int64_t* fb_base;
+  const C* fb_val;
+  const int* circ;
+  cplx alpha, c2;
+  unsigned* bar;                     // [0] arrivals, [1] generation
+  int* err;
+};
+
+__device__ __forceinline__ cplx phase_m(cplx alpha, int m) {
+  // alpha^m for m in {-1, 0, 1}
+  if (m == 0) return cplx{1, 0};
+  if (m == 1) return alpha;
+  return cdiv(cplx{1, 0}, alpha);
+}
+
+template <class C>
+__device__ __forceinline__ C wsum(C v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.re += __shfl_down_sync(0xffffffffu, v.re, o);
+    v.im += __shfl_down_sync(0xffffffffu, v.im, o);
+  }
+  return v;
+}
+
+// Device-wide barrier with a bounded wait; false when any block gave up.
+__device__ bool grid_barrier(unsigned* bar, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g = *gen;
+    __threadfence();                           // this block's writes before the arrival
+    int ok = 1;
+    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);                  // release the other blocks
+    } else {
+      long long it = 0;
+      while (*gen == g) {
+        if (++it > (1LL << 24)) {              // ~1 s with the sleeps below
+          atomicExch(err, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();                           // other blocks' writes after the release
+    s_ok = ok && *(volatile int*)err == 0;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+template <class C>
+__global__ void __launch_bounds__(FB, 2) matvec_fused_kernel(FusedArgs<C> a) {
+  extern __shared__ unsigned char smraw[];
+  C* sm = reinterpret_cast<C*>(smraw);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * FW + warp, nwarps = gridDim.x * FW;
+  C* wsm = sm + (size_t)warp * PF_NCOEF;       // per-warp scratch (stages A, B, D)
+  const int D = a.D;
+
+  // ------------------------------------------------------------ A: gather + P2M
+  {
+    const int PD = a.P[D];
+    for (int i = gw; i < a.nne[D]; i += nwarps) {
+      const int box = a.ne[D][i], s0 = a.bb[D][box], s1 = a.be[D][box];
+      C acc[FPASS];
+#pragma unroll
+      for (int c = 0; c < FPASS; ++c) acc[c] = C{0, 0};
+      for (int sb = s0; sb < s1; sb += 32) {
+        const int s = sb + lane;
+        C d0{0, 0}, d1{0, 0};
+        if (s < s1) {
+          const int e = a.perm[s];
+          const cplx p = a.ph[s];
+          d0 = from_d<C>(p * a.x[2 * e]);
+          d1 = from_d<C>(p * a.x[2 * e + 1]);
+          a.dens[2 * s] = d0;
+          a.dens[2 * s + 1] = d1;
+        }
+        wsm[2 * lane] = d0;
+        wsm[2 * lane + 1] = d1;
+        __syncwarp();
+        const int cnt = min(32, s1 - sb);
+#pragma unroll
+        for (int c = 0; c < FPASS; ++c) {
+          const int n = 32 * c + lane;
+          if (n < PD) {
+            for (int j = 0; j < cnt; ++j) {
+              const C* cf = a.p2m + (size_t)(sb + j) * 2 * PD;
+              acc[c] += cf[n] * wsm[2 * j] + cf[PD + n] * wsm[2 * j + 1];
+            }
+          }
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int c = 0; c < FPASS; ++c) {
+        const int n = 32 * c + lane;
+        if (n < PD) a.M[D][(size_t)box * PD + n] = acc[c];
+      }
+    }
+  }
+  if (!grid_barrier(a.bar, a.err)) return;
+
+  // ------------------------------------------------------------ B: M2M (+ root)
+  for (int l = D - 1; l >= 0; --l) {
+    const int P = a.P[l], Pc = a.P[l + 1];
+    for (int i = gw; i < a.nne[l]; i += nwarps) {
+      const int box = a.ne[l][i];
+      C acc[FPASS];
+#pragma unroll
+      for (int c = 0; c < FPASS; ++c) acc[c] = C{0, 0};
+      for (int q = 0; q < 4; ++q) {
+        const int ch = 4 * box + q;
+        if (a.bb[l + 1][ch] >= a.be[l + 1][ch]) continue;
+        for (int m = lane; m < Pc; m += 32) wsm[m] = a.M[l + 1][(size_t)ch * Pc + m];
+        __syncwarp();
+        const C* A = a.m2m[l] + (size_t)q * Pc * P;
+#pragma unroll
+        for (int c = 0; c < FPASS; ++c) {
+          const int n = 32 * c + lane;
+          if (n < P)
+            for (int m = 0; m < Pc; ++m) acc[c] += A[(size_t)m * P + n] * wsm[m];
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int c = 0; c < FPASS; ++c) {
+        const int n = 32 * c + lane;
+        if (n < P) a.M[l][(size_t)box * P + n] = acc[c];
+      }
+      if (l == 0) {
+        // root: L(0) = R M(0), the images |m| >= 2 through the lattice sums
+#pragma unroll
+        for (int c = 0; c < FPASS; ++c) {
+          const int n = 32 * c + lane;
+          if (n < P) wsm[n] = acc[c];
+        }
+        __syncwarp();
+        for (int t = lane; t < P; t += 32) {
+          C r{0, 0};
+          for (int n = 0; n < P; ++n) r += a.root[(size_t)t * P + n] * wsm[n];
+          a.L[0][t] = r;
+        }
+        __syncwarp();
+      }
+    }
+    if (!grid_barrier(a.bar, a.err)) return;
+  }
+
+  // ------------------------------------------------------------ D: L2L + M2L
+  for (int l = 1; l <= D; ++l) {
+    const int P = a.P[l], Pp = a.P[l - 1];
+    for (int i = gw; i < a.nne[l]; i += nwarps) {
+      const int box = a.ne[l][i], par = box >> 2, q = box & 3;
+      C acc[FPASS];
+#pragma unroll
+      for (int c = 0; c < FPASS; ++c) acc[c] = C{0, 0};
+      for (int m = lane; m < Pp; m += 32) wsm[m] = a.L[l - 1][(size_t)par * Pp + m];
+      __syncwarp();
+      {
+        const C* B = a.l2l[l - 1] + (size_t)q * Pp * P;
+#pragma unroll
+        for (int c = 0; c < FPASS; ++c) {
+          const int n = 32 * c + lane;
+          if (n < P)
+            for (int m = 0; m < Pp; ++m) acc[c] += B[(size_t)m * P + n] * wsm[m];
+        }
+      }
+      __syncwarp();
+      for (int e = a.ilp[l][i]; e < a.ilp[l][i + 1]; ++e) {
+        const int src = a.ils[l][e];
+        const C* T = a.m2lt[l] + (size_t)a.ilo[l][e] * P * P;
+        const C ph = from_d<C>(phase_m(a.alpha, a.ilm[l][e]));
+        for (int m = lane; m < P; m += 32) wsm[m] = ph * a.M[l][(size_t)src * P + m];
+        __syncwarp();
+#pragma unroll
+        for (int c = 0; c < FPASS; ++c) {
+          const int n = 32 * c + lane;
+          if (n < P)
+            for (int m = 0; m < P; ++m) acc[c] += T[(size_t)m * P + n] * wsm[m];
+        }
+        __syncwarp();
+      }
+#pragma unroll
+      for (int c = 0; c < FPASS; ++c) {
+        const int n = 32 * c + lane;
+        if (n < P) a.L[l][(size_t)box * P + n] = acc[c];
+      }
+    }
+    if (!grid_barrier(a.bar, a.err)) return;
+  }
+
+  // ------------------------------------------------------------ E: L2P + near field
+  {
+    const int PD = a.P[D];
+    C* sd = sm;                                  // [2 * FSTAGE] staged source densities
+    C* sL = sm + 2 * FSTAGE;                     // [PD] the leaf's local expansion
+    for (int li = blockIdx.x; li < a.nne[D]; li += gridDim.x) {
+      const int box = a.ne[D][li];
+      const int s0 = a.bb[D][box], nt = a.be[D][box] - s0;
+      const int j0 = a.nc_sbase[li], ns = a.nc_sbase[li + 1] - j0;
+      const bool staged = ns <= FSTAGE;
+      __syncthreads();                           // the previous leaf is done with the buffers
+      if (staged)
+        for (int j = threadIdx.x; j < ns; j += FB) {
+          const int f = a.nc_src[j0 + j];
+          sd[2 * j] = a.dens[2 * f];
+          sd[2 * j + 1] = a.dens[2 * f + 1];
+        }
+      for (int t = threadIdx.x; t < PD; t += FB) sL[t] = a.L[D][(size_t)box * PD + t];
+      __syncthreads();
+      for (int t = warp; t < nt; t += FW) {
+        const int s = s0 + t;
+        const C* row = a.nc_val + a.nc_base[li] + (int64_t)t * ns * 4;
+        C u0{0, 0}, d0{0, 0}, u1{0, 0}, d1{0, 0};
+        int j = lane;
+        for (; j + 32 < ns; j += 64) {
+          C p0, v0, p1, v1;
+          if (staged) {
+            p0 = sd[2 * j]; v0 = sd[2 * j + 1]; p1 = sd[2 * j + 64]; v1 = sd[2 * j + 65];
+          } else {
+            const int f0 = a.nc_src[j0 + j], f1 = a.nc_src[j0 + j + 32];
+            p0 = a.dens[2 * f0]; v0 = a.dens[2 * f0 + 1]; p1 = a.dens[2 * f1]; v1 = a.dens[2 * f1 + 1];
+          }
+          const C q0 = row[4 * j], q1 = row[4 * j + 1], q2 = row[4 * j + 2], q3 = row[4 * j + 3];
+          const C r0 = row[4 * j + 128], r1 = row[4 * j + 129], r2 = row[4 * j + 130], r3 = row[4 * j + 131];
+          u0 += q0 * p0 + q1 * v0;
+          d0 += q2 * p0 + q3 * v0;
+          u1 += r0 * p1 + r1 * v1;
+          d1 += r2 * p1 + r3 * v1;
+        }
+        for (; j < ns; j += 32) {
+          C p, v;
+          if (staged) { p = sd[2 * j]; v = sd[2 * j + 1]; }
+          else { const int f = a.nc_src[j0 + j]; p = a.dens[2 * f]; v = a.dens[2 * f + 1]; }
+          u0 += row[4 * j] * p + row[4 * j + 1] * v;
+          d0 += row[4 * j + 2] * p + row[4 * j + 3] * v;
+        }
+        // far field of the leaf's local expansion
+        const C* cs = a.l2p + (size_t)s * 2 * PD;
+        C uf{0, 0}, df{0, 0};
+        for (int t2 = lane; t2 < PD; t2 += 32) {
+          uf += cs[t2] * sL[t2];
+          df += cs[PD + t2] * sL[t2];
+        }
+        const C u = wsum(uf + (u0 + u1));
+        const C du = wsum(df + (d0 + d1));
+        if (lane == 0) {
+          a.U[2 * s] = u;
+          a.U[2 * s + 1] = du;
+        }
+      }
+    }
+  }
+  if (!grid_barrier(a.bar, a.err)) return;
+
+  // ------------------------------------------------------------ F: fiber blocks + combine
+  {
+    C* xs = sm;                                  // [2 N] the fiber's input densities
+    for (int b = blockIdx.x; b < a.nchunk; b += gridDim.x) {
+      const int fb = a.fb_chunk[3 * b], rb = a.fb_chunk[3 * b + 1], re = a.fb_chunk[3 * b + 2];
+      const int f0 = a.foff[fb], n2 = 2 * (a.foff[fb + 1] - f0);
+      const bool cir = a.circ[fb] != 0;
+      __syncthreads();
+      for (int i = threadIdx.x; i < n2; i += FB) xs[i] = from_d<C>(a.x[2 * f0 + i]);
+      __syncthreads();
+      // a warp takes the row pair (2e, 2e+1); a circulant block is read from its
+      // generating row pair with x rotated by 2e
+      for (int r = rb + 2 * warp; r < re; r += 2 * FW) {
+        const C* row0 = a.fb_val + a.fb_base[fb] + (cir ? 0 : (int64_t)r * n2);
+        const C* row1 = row0 + n2;
+        const int sh = cir ? r : 0;
+        const bool two = r + 1 < re;
+        C a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
+        int c = lane;
+        for (; c + 32 < n2; c += 64) {
+          int i0 = c + sh, i1 = c + 32 + sh;
+          if (i0 >= n2) i0 -= n2;
+          if (i1 >= n2) i1 -= n2;
+          const C x0 = xs[i0], x1 = xs[i1];
+          a0 += row0[c] * x0;
+          a1 += row0[c + 32] * x1;
+          if (two) {
+            b0 += row1[c] * x0;
+            b1 += row1[c + 32] * x1;
+          }
+        }
+        for (; c < n2; c += 32) {
+          int i0 = c + sh;
+          if (i0 >= n2) i0 -= n2;
+          a0 += row0[c] * xs[i0];
+          if (two) b0 += row1[c] * xs[i0];
+        }
+        const C s0 = wsum(a0 + a1);
+        const C s1 = wsum(b0 + b1);
+        if (lane == 0) {
+          for (int q = 0; q < (two ? 2 : 1); ++q) {
+            const int rr = r + q;
+            const int e = f0 + (rr >> 1);
+            const int s = a.opos[e];
+            const cplx po = cdiv(cplx{1, 0}, a.ph[s]);
+            const cplx u = po * to_d(a.U[2 * s + (rr & 1)]);
+            a.y[2 * f0 + rr] = to_d(q == 0 ? s0 : s1) + ((rr & 1) ? a.c2 * u : u);
+          }
+        }
+      }
+    }
+  }
+}
+
+template <class C>
+size_t fused_smem(int maxfiber) {
+  const size_t a = (size_t)FW * PF_NCOEF;              // stages A, B, D
+  const size_t e = 2 * (size_t)FSTAGE + PF_NCOEF;      // stage E
+  const size_t f = 2 * (size_t)maxfiber;               // stage F
+  return sizeof(C) * std::max(a, std::max(e, f));
+}
+
+template <class C>
+cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
+  FusedArgs<C> a{};
+  a.E = h->E;
+  a.D = h->D;
+  a.perm = h->s_perm;
+  a.ph = h->s_ph;
+  a.opos = h->o_pos;
+  a.x = x;
+  a.y = y;
+  for (int l = 0; l <= h->D; ++l) {
+    const Level& L = h->lev[l];
+    a.nne[l] = L.nne;
+    a.P[l] = L.P;
+    a.ne[l] = L.ne;
+    a.bb[l] = L.box_begin;
+    a.be[l] = L.box_end;
+    a.ilp[l] = L.il_ptr;
+    a.ils[l] = L.il_src;
+    a.ilo[l] = L.il_off;
+    a.ilm[l] = L.il_img;
+    if constexpr (sizeof(C) == sizeof(cplxf)) {
+      a.m2m[l] = L.m2mf; a.l2l[l] = L.l2lf; a.m2lt[l] = L.m2ltf; a.M[l] = L.Mf; a.L[l] = L.Lf;
+    } else {
+      a.m2m[l] = L.m2m; a.l2l[l] = L.l2l; a.m2lt[l] = L.m2lt; a.M[l] = L.M; a.L[l] = L.L;
+    }
+  }
+  if constexpr (sizeof(C) == sizeof(cplxf)) {
+    a.dens = h->densf; a.U = h->Uf; a.root = h->rootf; a.p2m = h->p2m_cf; a.l2p = h->l2p_cf;
+    a.nc_val = h->nc_valf; a.fb_val = h->fb_valf;
+  } else {
+    a.dens = h->dens; a.U = h->U; a.root = h->root; a.p2m = h->p2m_c; a.l2p = h->l2p_c;
+    a.nc_val = h->nc_val; a.fb_val = h->fb_val;
+  }
+  a.nc_base = h->nc_base;
+  a.nc_sbase = h->nc_sbase;
+  a.nc_src = h->nc_src;
+  a.nchunk = h->nchunk;
+  a.fb_chunk = h->fb_chunk;
+  a.foff = h->fib_off;
+  a.fb_base = h->fb_base;
+  a.circ = h->fb_circ;
+  a.alpha = h->alpha;
+  a.c2 = cplx{h->c2re, h->c2im};
+  a.bar = h->fz_bar;
+  a.err = h->fz_err;
+  const int grid = f32 ? h->fz_grid32 : h->fz_grid64;
+  const size_t smem = fused_smem<C>(h->max_fiber);
+  void* args[] = {&a};
+  const int ph = PH_FUSED + (f32 ? 16 : 0);
+  prof_begin(h, ph);
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)matvec_fused_kernel<C>, dim3(grid), dim3(FB), args, smem,
+                                              h->stream);
+  prof_end(h, ph);
+  return e;
+}
+
+template <class C>
+int fused_grid(int maxfiber) {
+  const size_t smem = fused_smem<C>(maxfiber);
+  if (cudaFuncSetAttribute(matvec_fused_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  int dev = 0, nsm = 0, per = 0, coop = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, matvec_fused_kernel<C>, FB, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  // two resident blocks per SM at most: more blocks add barrier traffic and
+  // the stages have no more parallel work than that at these sizes
+  return nsm * std::min(per, 2);
+}
+
+}  // namespace
+
+// Prepares the fused path of a handle (grid sizes, barrier words); returns
+// false when the device cannot run it, in which case the per-stage path is used.
+cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
+  *ok = false;
+  // blocks with work in some stage: warps over boxes (A, B, D), blocks over
+  // leaves (E) and over fiber row chunks (F)
+  int need = std::max(h->lev[h->D].nne, h->nchunk);
+  for (int l = 0; l <= h->D; ++l) need = std::max(need, (h->lev[l].nne + FW - 1) / FW);
+  need = std::max(need, 1);
+  h->fz_grid64 = std::min(fused_grid<cplx>(h->max_fiber), need);
+  h->fz_grid32 = std::min(fused_grid<cplxf>(h->max_fiber), need);
+  if (h->fz_grid64 <= 0 || h->fz_grid32 <= 0) return cudaSuccess;
+  *ok = true;
+  return cudaGetLastError();
+}
+
+cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision) {
+  if (precision == PFMBEM_MIXED) return launch_fused<cplxf>(h, x, y, true);
+  return launch_fused<cplx>(h, x, y, false);
+}

@@ -218,7 +218,9 @@ __global__ void features_kernel(int M, float kH, float th, const double* __restr
 }
 
 // Fourier coefficients of a solution: for fiber i, density d, mode n = -8..8,
-//   c = (1/N_i) sum_e psi_{e,d} e^{-i n t_e} e^{-i k c_i.dir},  t_e = angle of c_e about c_i.
+//   c = (1/N_i) sum_e psi_{e,d} e^{-i n t_e} e^{-i k c_i.dir},
+// t_e = angle of c_e about c_i measured from the incidence direction, so that an
+// isolated circle's response has the same coefficients at every incidence angle.
 // One block per (fiber, density); threads over modes.
 __global__ void targets_kernel(int M, int nm, const int* __restrict__ foff, const double* __restrict__ fc,
                                const double2* __restrict__ oc, double k, double dx, double dy,
@@ -230,7 +232,9 @@ __global__ void targets_kernel(int M, int nm, const int* __restrict__ foff, cons
   const double cx = fc[3 * i], cy = fc[3 * i + 1];
   cplx acc{0, 0};
   for (int e = f0; e < f0 + N; ++e) {
-    const double te = atan2(oc[e].y - cy, oc[e].x - cx);
+    // angle of (c_e - c_i) relative to dir = (dx, dy)
+    const double ux = oc[e].x - cx, uy = oc[e].y - cy;
+    const double te = atan2(uy * dx - ux * dy, ux * dx + uy * dy);
     double s, c;
     sincos(-n * te, &s, &c);
     acc += psi[2 * e + d] * cplx{c, s};
@@ -243,7 +247,7 @@ __global__ void targets_kernel(int M, int nm, const int* __restrict__ foff, cons
   t[o + 1] = (float)acc.im;
 }
 
-// psi0_{e,d} = e^{i k c_i.dir} sum_n c_{i,d,n} e^{i n t_e}; one thread per element.
+// psi0_{e,d} = e^{i k c_i.dir} sum_n c_{i,d,n} e^{i n t_e} (t_e as above); one thread per element.
 __global__ void decode_kernel(int E, int nm, const int* __restrict__ fib, const double* __restrict__ fc,
                               const double2* __restrict__ oc, double k, double dx, double dy,
                               const float* __restrict__ y, cplx* __restrict__ psi) {
@@ -251,7 +255,8 @@ __global__ void decode_kernel(int E, int nm, const int* __restrict__ fib, const 
   if (e >= E) return;
   const int i = fib[e];
   const double cx = fc[3 * i], cy = fc[3 * i + 1];
-  const double te = atan2(oc[e].y - cy, oc[e].x - cx);
+  const double ux = oc[e].x - cx, uy = oc[e].y - cy;
+  const double te = atan2(uy * dx - ux * dy, ux * dx + uy * dy);
   double s, c;
   sincos(k * (cx * dx + cy * dy), &s, &c);
   const cplx ph{c, s};

@@ -24,7 +24,7 @@ class Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("p_min", ctypes.c_int), ("eta", ctypes.c_double),
                 ("leaf_max", ctypes.c_int), ("depth", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("precision", ctypes.c_int), ("near_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int),
-                ("profile", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+                ("profile", ctypes.c_int), ("launch", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
 
 
 class Info(ctypes.Structure):
@@ -192,9 +192,9 @@ def pfmbem_coefficients(h, psi, max_orders=64):
 
 
 PHASES = ["gather", "p2m", "m2m", "m2l_l2l", "l2p", "near_p2p", "fiber_p2p_combine", "gmres_blas", "setup",
-          "outputs", "p2p_cache_build", "", "", "", "", "",
+          "outputs", "p2p_cache_build", "matvec_fused", "", "", "", "",
           "gather_f32", "p2m_f32", "m2m_f32", "m2l_l2l_f32", "l2p_f32", "near_p2p_f32", "fiber_p2p_combine_f32",
-          "", "", "", "", "", "", "", "", ""]
+          "", "", "", "", "matvec_fused_f32", "", "", "", ""]
 
 
 class ProfileInfo(ctypes.Structure):

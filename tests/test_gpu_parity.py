@@ -259,3 +259,20 @@ def test_full_size_square_32x32_rows(pf):
     idx = np.ravel(np.stack([2 * rows_e, 2 * rows_e + 1], axis=1))
     assert rel(y64[idx], ref) < 1e-8
     assert rel(y32[idx], ref) < 2e-6
+
+
+@pytest.mark.parametrize("make", SMALL + [W.hexagon_8x8_n256])
+def test_single_launch_matvec_matches_per_stage_kernels(pf, make):
+    """The cooperative single-launch matvec (default) against the one-kernel-per-
+    stage path on the same cached operators: FP64 to rounding, mixed to the
+    FP32 reordering of the M2L sums."""
+    w = make()
+    sf = pf.Solver(w)
+    ss = pf.Solver(w, launch=1)
+    x = W.density_vector(sf.E, 13)
+    for prec, tol in ((pf.FP64, 1e-12), (pf.MIXED, 1e-5)):
+        yf = np.zeros_like(x)
+        ys = np.zeros_like(x)
+        sf.matvec(x, yf, prec)
+        ss.matvec(x, ys, prec)
+        assert rel(yf, ys) < tol
