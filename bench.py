@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-reps", type=int, default=20)
     ap.add_argument("--workload", default="hexagon_8x8_n256", choices=sorted(WORKLOADS))
+    ap.add_argument("--launch", type=int, default=0, choices=[0, 1],
+                    help="cached matvec: 0 = one cooperative launch per product, 1 = one kernel per stage")
     return ap.parse_args()
 
 
@@ -198,12 +200,14 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     opt = pf.Options()
     opt.precision = prec
+    opt.launch = args.launch
     maxit = 2000
     prof_acc = {"ms": np.zeros(32), "launches": np.zeros(32, dtype=np.int64)}
     stats = {}
 
     opt_prof = pf.Options()
     opt_prof.precision = prec
+    opt_prof.launch = args.launch
     opt_prof.profile = 1        # kernel timing from inside pfmbem_create on
 
     def step(host=False, profile=False, o=None):
@@ -266,6 +270,7 @@ def main():
     # plain FP64 FMM-GMRES comparator on the same block and tolerance
     o64 = pf.Options()
     o64.precision = pf.FP64
+    o64.launch = args.launch
     step(o=o64)
     ms_fp64 = timed(host=False, profile=False, steps=args.fp64_steps, o=o64)
     fp64_stats = dict(stats)
@@ -326,7 +331,8 @@ def main():
                        "tol": args.tol, "precision": args.precision, "depth": plan.depth,
                        "p": list(plan.p)[:plan.depth + 1],
                        "l2": "flushed between steps (256 MiB write); per-step working set is L2-resident by design",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}",
+                       "matvec_launch": "one cooperative kernel" if args.launch == 0 else "one kernel per stage"},
             "matvec_munknowns_per_s": mv,
             "plain_fp64": {"solves_per_s": world * 1000.0 / ms_fp64, "ms_per_step": ms_fp64,
                            "iters": fp64_stats["iters"], "rel_residual": fp64_stats["rel_residual"],

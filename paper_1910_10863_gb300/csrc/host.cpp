@@ -308,7 +308,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     L.nne = (int)L.hne.size();
     // expansion order
     double x = k * L.d * std::sqrt(2.0);
-    int pmin = h->opt.p_min > 0 ? h->opt.p_min : 16;
+    int pmin = h->opt.p_min > 0 ? h->opt.p_min : 15;
     int p = h->opt.p > 0 ? h->opt.p : (int)std::ceil(x + 1.8 * std::pow(10.0, 2.0 / 3.0) * std::cbrt(x));
     p = std::max(p, h->opt.p > 0 ? 1 : pmin);
     if (p > PF_PMAX) return fail(h, PFMBEM_EINVAL, "expansion order above the library limit (64); use more levels");

@@ -27,7 +27,6 @@ namespace {
 constexpr int FB = 256;          // threads per block
 constexpr int FW = FB / 32;      // warps per block
 constexpr int FSTAGE = 1536;     // near-field source densities staged in shared memory per leaf
-constexpr int FPASS = (PF_NCOEF + 31) / 32;   // lane passes over the coefficients of one box
 
 template <class C>
 struct FusedArgs {
@@ -78,6 +77,17 @@ __device__ __forceinline__ cplx phase_m(cplx alpha, int m) {
   return cdiv(cplx{1, 0}, alpha);
 }
 
+// Loads of values written by other blocks earlier in the same launch bypass L1
+// (ld.global.cg), so that no line cached before the barrier is read stale.
+__device__ __forceinline__ cplx ldcg(const cplx* p) {
+  const double2 v = __ldcg(reinterpret_cast<const double2*>(p));
+  return cplx{v.x, v.y};
+}
+__device__ __forceinline__ cplxf ldcg(const cplxf* p) {
+  const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
+  return cplxf{v.x, v.y};
+}
+
 template <class C>
 __device__ __forceinline__ C wsum(C v) {
 #pragma unroll
@@ -120,7 +130,7 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
 }
 
 template <class C>
-__global__ void __launch_bounds__(FB, 2) matvec_fused_kernel(FusedArgs<C> a) {
+__global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   extern __shared__ unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -129,44 +139,34 @@ __global__ void __launch_bounds__(FB, 2) matvec_fused_kernel(FusedArgs<C> a) {
   const int D = a.D;
 
   // ------------------------------------------------------------ A: gather + P2M
+  // Lanes over the coefficients n (one pass per 32); the inner loops are
+  // unrolled so that each lane keeps several independent loads in flight.
   {
     const int PD = a.P[D];
     for (int i = gw; i < a.nne[D]; i += nwarps) {
       const int box = a.ne[D][i], s0 = a.bb[D][box], s1 = a.be[D][box];
-      C acc[FPASS];
-#pragma unroll
-      for (int c = 0; c < FPASS; ++c) acc[c] = C{0, 0};
       for (int sb = s0; sb < s1; sb += 32) {
         const int s = sb + lane;
-        C d0{0, 0}, d1{0, 0};
         if (s < s1) {
           const int e = a.perm[s];
           const cplx p = a.ph[s];
-          d0 = from_d<C>(p * a.x[2 * e]);
-          d1 = from_d<C>(p * a.x[2 * e + 1]);
-          a.dens[2 * s] = d0;
-          a.dens[2 * s + 1] = d1;
+          a.dens[2 * s] = from_d<C>(p * a.x[2 * e]);
+          a.dens[2 * s + 1] = from_d<C>(p * a.x[2 * e + 1]);
         }
-        wsm[2 * lane] = d0;
-        wsm[2 * lane + 1] = d1;
-        __syncwarp();
-        const int cnt = min(32, s1 - sb);
-#pragma unroll
-        for (int c = 0; c < FPASS; ++c) {
-          const int n = 32 * c + lane;
-          if (n < PD) {
-            for (int j = 0; j < cnt; ++j) {
-              const C* cf = a.p2m + (size_t)(sb + j) * 2 * PD;
-              acc[c] += cf[n] * wsm[2 * j] + cf[PD + n] * wsm[2 * j + 1];
-            }
-          }
-        }
-        __syncwarp();
       }
-#pragma unroll
-      for (int c = 0; c < FPASS; ++c) {
-        const int n = 32 * c + lane;
-        if (n < PD) a.M[D][(size_t)box * PD + n] = acc[c];
+      __syncwarp();
+      for (int n0 = 0; n0 < PD; n0 += 32) {
+        const int n = n0 + lane;
+        C acc0{0, 0}, acc1{0, 0};
+        if (n < PD) {
+#pragma unroll 4
+          for (int f = s0; f < s1; ++f) {
+            const C* cf = a.p2m + (size_t)f * 2 * PD;
+            acc0 += cf[n] * a.dens[2 * f];
+            acc1 += cf[PD + n] * a.dens[2 * f + 1];
+          }
+          a.M[D][(size_t)box * PD + n] = acc0 + acc1;
+        }
       }
     }
   }
@@ -177,42 +177,38 @@ __global__ void __launch_bounds__(FB, 2) matvec_fused_kernel(FusedArgs<C> a) {
     const int P = a.P[l], Pc = a.P[l + 1];
     for (int i = gw; i < a.nne[l]; i += nwarps) {
       const int box = a.ne[l][i];
-      C acc[FPASS];
-#pragma unroll
-      for (int c = 0; c < FPASS; ++c) acc[c] = C{0, 0};
-      for (int q = 0; q < 4; ++q) {
-        const int ch = 4 * box + q;
-        if (a.bb[l + 1][ch] >= a.be[l + 1][ch]) continue;
-        for (int m = lane; m < Pc; m += 32) wsm[m] = a.M[l + 1][(size_t)ch * Pc + m];
-        __syncwarp();
-        const C* A = a.m2m[l] + (size_t)q * Pc * P;
-#pragma unroll
-        for (int c = 0; c < FPASS; ++c) {
-          const int n = 32 * c + lane;
-          if (n < P)
-            for (int m = 0; m < Pc; ++m) acc[c] += A[(size_t)m * P + n] * wsm[m];
+      for (int n0 = 0; n0 < P; n0 += 32) {
+        const int n = n0 + lane;
+        C acc0{0, 0}, acc1{0, 0};
+        for (int q = 0; q < 4; ++q) {
+          const int ch = 4 * box + q;
+          if (a.bb[l + 1][ch] >= a.be[l + 1][ch]) continue;
+          __syncwarp();
+          for (int m = lane; m < Pc; m += 32) wsm[m] = ldcg(a.M[l + 1] + (size_t)ch * Pc + m);
+          __syncwarp();
+          if (n < P) {
+            const C* A = a.m2m[l] + (size_t)q * Pc * P + n;
+            int m = 0;
+#pragma unroll 4
+            for (; m + 1 < Pc; m += 2) {
+              acc0 += A[(size_t)m * P] * wsm[m];
+              acc1 += A[(size_t)(m + 1) * P] * wsm[m + 1];
+            }
+            if (m < Pc) acc0 += A[(size_t)m * P] * wsm[m];
+          }
         }
-        __syncwarp();
-      }
-#pragma unroll
-      for (int c = 0; c < FPASS; ++c) {
-        const int n = 32 * c + lane;
-        if (n < P) a.M[l][(size_t)box * P + n] = acc[c];
+        if (n < P) a.M[l][(size_t)box * P + n] = acc0 + acc1;
       }
       if (l == 0) {
         // root: L(0) = R M(0), the images |m| >= 2 through the lattice sums
-#pragma unroll
-        for (int c = 0; c < FPASS; ++c) {
-          const int n = 32 * c + lane;
-          if (n < P) wsm[n] = acc[c];
-        }
+        __syncwarp();
+        for (int m = lane; m < P; m += 32) wsm[m] = ldcg(a.M[0] + m);
         __syncwarp();
         for (int t = lane; t < P; t += 32) {
           C r{0, 0};
-          for (int n = 0; n < P; ++n) r += a.root[(size_t)t * P + n] * wsm[n];
+          for (int m = 0; m < P; ++m) r += a.root[(size_t)t * P + m] * wsm[m];
           a.L[0][t] = r;
         }
-        __syncwarp();
       }
     }
     if (!grid_barrier(a.bar, a.err)) return;
@@ -223,39 +219,41 @@ __global__ void __launch_bounds__(FB, 2) matvec_fused_kernel(FusedArgs<C> a) {
     const int P = a.P[l], Pp = a.P[l - 1];
     for (int i = gw; i < a.nne[l]; i += nwarps) {
       const int box = a.ne[l][i], par = box >> 2, q = box & 3;
-      C acc[FPASS];
-#pragma unroll
-      for (int c = 0; c < FPASS; ++c) acc[c] = C{0, 0};
-      for (int m = lane; m < Pp; m += 32) wsm[m] = a.L[l - 1][(size_t)par * Pp + m];
-      __syncwarp();
-      {
-        const C* B = a.l2l[l - 1] + (size_t)q * Pp * P;
-#pragma unroll
-        for (int c = 0; c < FPASS; ++c) {
-          const int n = 32 * c + lane;
-          if (n < P)
-            for (int m = 0; m < Pp; ++m) acc[c] += B[(size_t)m * P + n] * wsm[m];
-        }
-      }
-      __syncwarp();
-      for (int e = a.ilp[l][i]; e < a.ilp[l][i + 1]; ++e) {
-        const int src = a.ils[l][e];
-        const C* T = a.m2lt[l] + (size_t)a.ilo[l][e] * P * P;
-        const C ph = from_d<C>(phase_m(a.alpha, a.ilm[l][e]));
-        for (int m = lane; m < P; m += 32) wsm[m] = ph * a.M[l][(size_t)src * P + m];
+      const int e0 = a.ilp[l][i], e1 = a.ilp[l][i + 1];
+      for (int n0 = 0; n0 < P; n0 += 32) {
+        const int n = n0 + lane;
+        C acc0{0, 0}, acc1{0, 0};
         __syncwarp();
-#pragma unroll
-        for (int c = 0; c < FPASS; ++c) {
-          const int n = 32 * c + lane;
-          if (n < P)
-            for (int m = 0; m < P; ++m) acc[c] += T[(size_t)m * P + n] * wsm[m];
-        }
+        for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Pp + m);
         __syncwarp();
-      }
-#pragma unroll
-      for (int c = 0; c < FPASS; ++c) {
-        const int n = 32 * c + lane;
-        if (n < P) a.L[l][(size_t)box * P + n] = acc[c];
+        if (n < P) {
+          const C* B = a.l2l[l - 1] + (size_t)q * Pp * P + n;
+          int m = 0;
+#pragma unroll 4
+          for (; m + 1 < Pp; m += 2) {
+            acc0 += B[(size_t)m * P] * wsm[m];
+            acc1 += B[(size_t)(m + 1) * P] * wsm[m + 1];
+          }
+          if (m < Pp) acc0 += B[(size_t)m * P] * wsm[m];
+        }
+        for (int e = e0; e < e1; ++e) {
+          const int src = a.ils[l][e];
+          const C ph = from_d<C>(phase_m(a.alpha, a.ilm[l][e]));
+          __syncwarp();
+          for (int m = lane; m < P; m += 32) wsm[m] = ph * ldcg(a.M[l] + (size_t)src * P + m);
+          __syncwarp();
+          if (n < P) {
+            const C* T = a.m2lt[l] + (size_t)a.ilo[l][e] * P * P + n;
+            int m = 0;
+#pragma unroll 4
+            for (; m + 1 < P; m += 2) {
+              acc0 += T[(size_t)m * P] * wsm[m];
+              acc1 += T[(size_t)(m + 1) * P] * wsm[m + 1];
+            }
+            if (m < P) acc0 += T[(size_t)m * P] * wsm[m];
+          }
+        }
+        if (n < P) a.L[l][(size_t)box * P + n] = acc0 + acc1;
       }
     }
     if (!grid_barrier(a.bar, a.err)) return;
@@ -275,10 +273,10 @@ __global__ void __launch_bounds__(FB, 2) matvec_fused_kernel(FusedArgs<C> a) {
       if (staged)
         for (int j = threadIdx.x; j < ns; j += FB) {
           const int f = a.nc_src[j0 + j];
-          sd[2 * j] = a.dens[2 * f];
-          sd[2 * j + 1] = a.dens[2 * f + 1];
+          sd[2 * j] = ldcg(a.dens + 2 * f);
+          sd[2 * j + 1] = ldcg(a.dens + 2 * f + 1);
         }
-      for (int t = threadIdx.x; t < PD; t += FB) sL[t] = a.L[D][(size_t)box * PD + t];
+      for (int t = threadIdx.x; t < PD; t += FB) sL[t] = ldcg(a.L[D] + (size_t)box * PD + t);
       __syncthreads();
       for (int t = warp; t < nt; t += FW) {
         const int s = s0 + t;
@@ -291,7 +289,8 @@ __global__ void __launch_bounds__(FB, 2) matvec_fused_kernel(FusedArgs<C> a) {
             p0 = sd[2 * j]; v0 = sd[2 * j + 1]; p1 = sd[2 * j + 64]; v1 = sd[2 * j + 65];
           } else {
             const int f0 = a.nc_src[j0 + j], f1 = a.nc_src[j0 + j + 32];
-            p0 = a.dens[2 * f0]; v0 = a.dens[2 * f0 + 1]; p1 = a.dens[2 * f1]; v1 = a.dens[2 * f1 + 1];
+            p0 = ldcg(a.dens + 2 * f0); v0 = ldcg(a.dens + 2 * f0 + 1);
+            p1 = ldcg(a.dens + 2 * f1); v1 = ldcg(a.dens + 2 * f1 + 1);
           }
           const C q0 = row[4 * j], q1 = row[4 * j + 1], q2 = row[4 * j + 2], q3 = row[4 * j + 3];
           const C r0 = row[4 * j + 128], r1 = row[4 * j + 129], r2 = row[4 * j + 130], r3 = row[4 * j + 131];
@@ -303,7 +302,7 @@ __global__ void __launch_bounds__(FB, 2) matvec_fused_kernel(FusedArgs<C> a) {
         for (; j < ns; j += 32) {
           C p, v;
           if (staged) { p = sd[2 * j]; v = sd[2 * j + 1]; }
-          else { const int f = a.nc_src[j0 + j]; p = a.dens[2 * f]; v = a.dens[2 * f + 1]; }
+          else { const int f = a.nc_src[j0 + j]; p = ldcg(a.dens + 2 * f); v = ldcg(a.dens + 2 * f + 1); }
           u0 += row[4 * j] * p + row[4 * j + 1] * v;
           d0 += row[4 * j + 2] * p + row[4 * j + 3] * v;
         }
@@ -370,7 +369,7 @@ __global__ void __launch_bounds__(FB, 2) matvec_fused_kernel(FusedArgs<C> a) {
             const int e = f0 + (rr >> 1);
             const int s = a.opos[e];
             const cplx po = cdiv(cplx{1, 0}, a.ph[s]);
-            const cplx u = po * to_d(a.U[2 * s + (rr & 1)]);
+            const cplx u = po * to_d(ldcg(a.U + 2 * s + (rr & 1)));
             a.y[2 * f0 + rr] = to_d(q == 0 ? s0 : s1) + ((rr & 1) ? a.c2 * u : u);
           }
         }
@@ -460,9 +459,9 @@ int fused_grid(int maxfiber) {
     cudaGetLastError();
     return 0;
   }
-  // two resident blocks per SM at most: more blocks add barrier traffic and
+  // three resident blocks per SM at most: more blocks add barrier traffic and
   // the stages have no more parallel work than that at these sizes
-  return nsm * std::min(per, 2);
+  return nsm * std::min(per, 3);
 }
 
 }  // namespace
