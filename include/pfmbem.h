@@ -218,8 +218,16 @@ pfmbem_status pfmbem_mlp_train(pfmbem_mlp_t mlp, int batch, const float* X, cons
 /* Network input of the block: [kH/8, theta/(pi/2), per fiber ((cx-x0)/H,
  * (cy-y0)/H, 4r/H)] with (x0, y0) the root corner; x float [2 + 3M]. */
 pfmbem_status pfmbem_warm_features(pfmbem_t h, float* x);
+/* Per-fiber network input, one row of 5 + 3K floats per fiber (K <= 32):
+ * [kH/8, theta/(pi/2), 4 r_i/H, (x_i - x_min)/H, (x_max - x_i)/H, then the K
+ * nearest other fibers by distance, each (4 dx/H, 4 dy/H, 4 r_j/H) with dy to
+ * the nearest periodic image, zeros where the block has fewer fibers].  x float
+ * [M][5 + 3K]; a network on these rows maps one fiber's row to that fiber's
+ * 2 x (2 nmodes + 1) complex modes (one row of pfmbem_warm_targets). */
+pfmbem_status pfmbem_warm_features_local(pfmbem_t h, int K, float* x);
 /* Fourier modes n = -nmodes..nmodes of both densities of every fiber of psi,
- * about the fiber centre and divided by the incident phase at the centre:
+ * about the fiber centre, angles measured from the incidence direction, divided
+ * by the incident phase at the centre:
  * t float [M][2][2 nmodes + 1][2] (re, im). */
 pfmbem_status pfmbem_warm_targets(pfmbem_t h, int nmodes, const double* psi, float* t);
 /* Inverse of pfmbem_warm_targets: psi0 complex [2E] from y (same layout). */

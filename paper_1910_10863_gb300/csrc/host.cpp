@@ -1547,6 +1547,22 @@ pfmbem_status pfmbem_warm_features(pfmbem_t h, float* x) {
   return PFMBEM_OK;
 }
 
+pfmbem_status pfmbem_warm_features_local(pfmbem_t h, int K, float* x) {
+  if (!h || !x || K < 0 || K > 32) return PFMBEM_EINVAL;
+  const size_t nx = (size_t)h->M * (5 + 3 * K);
+  const bool dev = is_device_ptr(x);
+  float* xd = dev ? x : dalloc<float>(h, nx);
+  if (!xd) return fail(h, PFMBEM_ENOMEM, "warm-start buffer");
+  CK(k_warm_features_local(h, K, xd));
+  if (!dev) {
+    CK(cudaMemcpyAsync(x, xd, nx * sizeof(float), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    cudaFreeAsync(xd, h->stream);
+    h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)xd), h->allocs.end());
+  }
+  return PFMBEM_OK;
+}
+
 pfmbem_status pfmbem_warm_targets(pfmbem_t h, int nmodes, const double* psi, float* t) {
   if (!h || !psi || !t || nmodes < 0 || nmodes > 64) return PFMBEM_EINVAL;
   const size_t n = 2 * (size_t)h->E, nt = (size_t)h->M * 2 * (2 * nmodes + 1) * 2;

@@ -204,6 +204,7 @@ cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_build_fmm_caches(pfmbem* h);
 // learned warm start (mlp.cu)
 cudaError_t k_warm_features(pfmbem* h, float* x_dev);
+cudaError_t k_warm_features_local(pfmbem* h, int K, float* x_dev);
 cudaError_t k_warm_targets(pfmbem* h, int nm, const cplx* psi, float* t_dev);
 cudaError_t k_warm_decode(pfmbem* h, int nm, const float* y_dev, cplx* psi);
 cudaError_t k_field_prepare(pfmbem* h, const cplx* psi);

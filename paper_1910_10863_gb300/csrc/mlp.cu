@@ -217,6 +217,66 @@ __global__ void features_kernel(int M, float kH, float th, const double* __restr
   }
 }
 
+// Per-fiber network input (one row per fiber, 5 + 3K floats): kH/8,
+// theta/(pi/2), 4 r_i/H, the distances (x_i - x_min)/H and (x_max - x_i)/H to
+// the block's left and right edges, then the K nearest other fibers in order of
+// distance, each as (4 dx/H, 4 dy/H, 4 r_j/H) with dy taken to the nearest
+// periodic image; missing neighbours are zeros.  The row depends on positions
+// only through differences along y, so a model on these rows is equivariant
+// under shifts of the block along the period.  One thread per fiber.
+#define PF_WARM_KMAX 32
+__global__ void features_local_kernel(int M, int K, float kH, float th, const double* __restrict__ fc, double H,
+                                      float* __restrict__ x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const double cx = fc[3 * i], cy = fc[3 * i + 1], ri = fc[3 * i + 2];
+  double xmin = 1e300, xmax = -1e300;
+  for (int j = 0; j < M; ++j) {
+    xmin = fmin(xmin, fc[3 * j] - fc[3 * j + 2]);
+    xmax = fmax(xmax, fc[3 * j] + fc[3 * j + 2]);
+  }
+  double bd[PF_WARM_KMAX];
+  int bj[PF_WARM_KMAX];
+  double bdy[PF_WARM_KMAX];
+  int nb = 0;
+  for (int j = 0; j < M; ++j) {
+    if (j == i) continue;
+    const double dx = fc[3 * j] - cx;
+    double dy = fc[3 * j + 1] - cy;
+    dy -= H * rint(dy / H);
+    const double d2 = dx * dx + dy * dy;
+    // insertion into the K nearest so far
+    int pos = nb < K ? nb : K;
+    while (pos > 0 && bd[pos - 1] > d2) {
+      if (pos < K) { bd[pos] = bd[pos - 1]; bj[pos] = bj[pos - 1]; bdy[pos] = bdy[pos - 1]; }
+      --pos;
+    }
+    if (pos < K) {
+      bd[pos] = d2;
+      bj[pos] = j;
+      bdy[pos] = dy;
+      if (nb < K) ++nb;
+    }
+  }
+  float* o = x + (size_t)i * (5 + 3 * K);
+  o[0] = kH / 8.f;
+  o[1] = th / 1.5707963267948966f;
+  o[2] = (float)(4.0 * ri / H);
+  o[3] = (float)((cx - xmin) / H);
+  o[4] = (float)((xmax - cx) / H);
+  for (int q = 0; q < K; ++q) {
+    float* v = o + 5 + 3 * q;
+    if (q < nb) {
+      const int j = bj[q];
+      v[0] = (float)(4.0 * (fc[3 * j] - cx) / H);
+      v[1] = (float)(4.0 * bdy[q] / H);
+      v[2] = (float)(4.0 * fc[3 * j + 2] / H);
+    } else {
+      v[0] = v[1] = v[2] = 0.f;
+    }
+  }
+}
+
 // Fourier coefficients of a solution: for fiber i, density d, mode n = -8..8,
 //   c = (1/N_i) sum_e psi_{e,d} e^{-i n t_e} e^{-i k c_i.dir},
 // t_e = angle of c_e about c_i measured from the incidence direction, so that an
@@ -404,6 +464,12 @@ pfmbem_status pfmbem_mlp_train(pfmbem_mlp_t m, int B, const float* X, const floa
 cudaError_t k_warm_features(pfmbem* h, float* x_dev) {
   features_kernel<<<(h->M + 127) / 128, 128, 0, h->stream>>>(h->M, (float)(h->k * h->H), (float)h->theta, h->fib_geo,
                                                              h->x0, h->y0, h->H, x_dev);
+  return cudaGetLastError();
+}
+
+cudaError_t k_warm_features_local(pfmbem* h, int K, float* x_dev) {
+  features_local_kernel<<<(h->M + 127) / 128, 128, 0, h->stream>>>(h->M, K, (float)(h->k * h->H), (float)h->theta,
+                                                                   h->fib_geo, h->H, x_dev);
   return cudaGetLastError();
 }
 

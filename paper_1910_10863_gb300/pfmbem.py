@@ -73,6 +73,7 @@ def lib():
             "pfmbem_mlp_forward": ([vp, i, vp, vp], i),
             "pfmbem_mlp_train": ([vp, i, vp, vp, ctypes.c_float, vp, vp], i),
             "pfmbem_warm_features": ([vp, vp], i),
+            "pfmbem_warm_features_local": ([vp, i, vp], i),
             "pfmbem_warm_targets": ([vp, i, vp, vp], i),
             "pfmbem_warm_decode": ([vp, i, vp, vp], i),
             "pfmbem_solve_batch": ([i, vp, vp, d, i, vp], i),
@@ -283,6 +284,12 @@ class MLP:
 def pfmbem_warm_features(h, M):
     x = np.zeros(2 + 3 * M, dtype=np.float32)
     _check(h, lib().pfmbem_warm_features(h, addr(x)))
+    return x
+
+
+def pfmbem_warm_features_local(h, M, K=15):
+    x = np.zeros((M, 5 + 3 * K), dtype=np.float32)
+    _check(h, lib().pfmbem_warm_features_local(h, int(K), addr(x)))
     return x
 
 

@@ -1,10 +1,13 @@
 """Learned GMRES warm start: data, training and evaluation drivers.
 
-The network maps the block's parameters (pfmbem_warm_features: kH, theta and
-every fiber's centre and radius) to the Fourier modes n = -8..8 of both
-densities on every fiber (pfmbem_warm_targets: angles measured from the
+The network maps one fiber's row of pfmbem_warm_features_local (kH, theta, its
+radius, its distances to the block's edges and the relative positions and radii
+of its 15 nearest neighbours) to the Fourier modes n = -8..8 of both densities
+on that fiber (one row of pfmbem_warm_targets: angles measured from the
 incidence direction, coefficients divided by the incident phase at the fiber
-centre).  Training data are solutions produced by the solver itself; forward,
+centre).  The same weights serve every fiber, so a block of M fibers gives M
+training rows and the prediction does not depend on where along the period the
+block sits.  Training data are solutions produced by the solver itself; forward,
 backward and Adam run in the library's kernels (pfmbem_mlp_*).  A prediction is
 decoded (pfmbem_warm_decode) and passed to pfmbem_solve as the initial guess,
 which scales it by the residual-minimising factor and falls back to a zero start
@@ -17,6 +20,8 @@ import numpy as np
 from . import pfmbem as pf
 
 NMODES = 8
+NEIGHBOURS = 15
+NOUT = 2 * (2 * NMODES + 1) * 2          # per fiber: 2 densities x 17 complex modes
 
 
 def solve_instance(w, guess=None, tol=1e-6, maxit=2000, precision=pf.MIXED):
@@ -29,16 +34,23 @@ def solve_instance(w, guess=None, tol=1e-6, maxit=2000, precision=pf.MIXED):
     return psi, info, s
 
 
+def features(s, M):
+    return pf.pfmbem_warm_features_local(s.h, M, NEIGHBOURS)
+
+
 def generate(instances, tol=1e-6):
-    """Features X [n][2+3M], targets T [n][M*2*17*2] and zero-start iteration counts."""
-    X, T, iters = [], [], []
-    for w in instances:
+    """Per-fiber rows: features X [rows][5 + 3K], targets T [rows][2*17*2], the
+    instance index of every row and the zero-start iteration counts."""
+    X, T, inst, iters = [], [], [], []
+    for q, w in enumerate(instances):
         psi, info, s = solve_instance(w, tol=tol)
-        X.append(pf.pfmbem_warm_features(s.h, w.M))
-        T.append(pf.pfmbem_warm_targets(s.h, psi, w.M, NMODES))
+        X.append(features(s, w.M))
+        T.append(pf.pfmbem_warm_targets(s.h, psi, w.M, NMODES).reshape(w.M, NOUT))
+        inst.append(np.full(w.M, q))
         iters.append(info.iters)
         s.close()
-    return np.array(X, dtype=np.float32), np.array(T, dtype=np.float32), np.array(iters)
+    return (np.concatenate(X).astype(np.float32), np.concatenate(T).astype(np.float32), np.concatenate(inst),
+            np.array(iters))
 
 
 def train(X, T, hidden=256, layers=3, epochs=200, batch=256, lr=1e-3, seed=1913, log_every=0, lr_final=0.05,
@@ -77,22 +89,24 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=8192)
     ap.add_argument("--test", type=int, default=1024)
-    ap.add_argument("--epochs", type=int, default=1000)
-    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--epochs", type=int, default=300)
+    ap.add_argument("--batch", type=int, default=512)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--tol", type=float, default=1e-6)
     a = ap.parse_args()
     t0 = time.perf_counter()
-    X, T, _ = generate(W.batch_instances(a.train, seed=1912), tol=a.tol)
-    nv = max(1, a.train // 16)               # validation split of the training blocks
+    X, T, inst, _ = generate(W.batch_instances(a.train, seed=1912), tol=a.tol)
+    nv = max(1, a.train // 16)               # validation split: the first blocks' rows
+    val = inst < nv
     t1 = time.perf_counter()
-    net, hist = train(X[nv:], T[nv:], epochs=a.epochs, batch=a.batch, lr=a.lr, X_val=X[:nv], T_val=T[:nv])
+    net, hist = train(X[~val], T[~val], epochs=a.epochs, batch=a.batch, lr=a.lr, X_val=X[val], T_val=T[val])
     t2 = time.perf_counter()
     rows = evaluate(net, W.batch_instances(a.test, seed=1915), tol=a.tol)
     t3 = time.perf_counter()
     iz, iw, r0 = rows[:, 0], rows[:, 1], rows[:, 2]
     print(json.dumps({
         "train_blocks": a.train - nv, "validation_blocks": nv, "test_blocks": a.test, "epochs": a.epochs,
+        "train_rows": int((~val).sum()), "inputs": int(X.shape[1]), "outputs": int(T.shape[1]),
         "first_loss": hist[0], "final_loss": hist[-1], "final_validation_loss": net.val_hist[-1],
         "mean_iters_zero_start": float(iz.mean()), "mean_iters_warm_start": float(iw.mean()),
         "median_warm_start_residual": float(np.median(r0)),
@@ -128,10 +142,9 @@ def evaluate(net, instances, tol=1e-6):
         proj = np.zeros_like(B)
         pf.pfmbem_warm_decode(s.h, pf.pfmbem_warm_targets(s.h, psi, w.M, NMODES), proj, NMODES)
         t0 = time.perf_counter()
-        x = pf.pfmbem_warm_features(s.h, w.M)
-        y = net.forward(x[None, :])[0]
+        y = net.forward(features(s, w.M))
         psi0 = np.zeros_like(B)
-        pf.pfmbem_warm_decode(s.h, y, psi0, NMODES)
+        pf.pfmbem_warm_decode(s.h, y.ravel(), psi0, NMODES)
         psi_w = psi0.copy()
         iw = s.solve(psi_w, tol=tol, use_guess=True, check=False)
         t1 = time.perf_counter()

@@ -60,14 +60,29 @@ def test_warm_targets_and_decode_are_inverse_on_band_limited_densities(pf):
     assert np.max(np.abs(t - y)) < 1e-5 * np.max(np.abs(y))
     x = pf.pfmbem_warm_features(s.h, w.M)
     assert x.shape == (50,) and abs(x[0] - w.k * w.H / 8) < 1e-6 and abs(x[1] - w.theta / (math.pi / 2)) < 1e-6
+    # per-fiber rows: own radius, the nearest neighbour first, periodic images along y
+    xl = pf.pfmbem_warm_features_local(s.h, w.M, 15)
+    assert xl.shape == (w.M, 50)
+    c, r = w.centres, w.radii
+    for i in range(w.M):
+        assert abs(xl[i, 2] - 4 * r[i] / w.H) < 1e-5
+        d = []
+        for j in range(w.M):
+            if j != i:
+                dy = c[j, 1] - c[i, 1]
+                dy -= w.H * round(dy / w.H)
+                d.append(math.hypot(c[j, 0] - c[i, 0], dy))
+        nb = xl[i, 5:].reshape(15, 3)
+        dist = np.hypot(nb[:, 0], nb[:, 1]) * w.H / 4
+        assert np.all(np.diff(dist) >= -1e-6) and abs(dist[0] - min(d)) < 1e-5
 
 
 def test_trained_network_reduces_gmres_iterations_on_held_out_blocks(pf):
     from paper_1910_10863_gb300 import warmstart as ws
     train = W.batch_instances(320, seed=101)
     test = W.batch_instances(24, seed=202)
-    X, T, _ = ws.generate(train)
-    net, hist = ws.train(X, T, epochs=150, batch=64, lr=2e-3, seed=3)
+    X, T, _, _ = ws.generate(train)
+    net, hist = ws.train(X, T, epochs=60, batch=128, lr=2e-3, seed=3)
     assert hist[-1] < 0.5 * hist[0]
     rows = ws.evaluate(net, test)
     iz, iw, res0 = rows[:, 0], rows[:, 1], rows[:, 2]
