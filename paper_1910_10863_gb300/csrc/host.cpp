@@ -522,10 +522,10 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       fbase[i] = acc;
       const int n2 = 2 * (foff[i + 1] - foff[i]);
       acc += circ[i] ? (int64_t)2 * n2 : (int64_t)n2 * n2;
-      for (int r = 0; r < n2; r += 64) {
+      for (int r = 0; r < n2; r += 32) {
         chunks.push_back(i);
         chunks.push_back(r);
-        chunks.push_back(std::min(r + 64, n2));
+        chunks.push_back(std::min(r + 32, n2));
       }
     }
     h->fb_entries = acc;
@@ -613,7 +613,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &L.il_src, src)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.il_off, off)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.il_img, img)) != PFMBEM_OK) return st;
-    // the same pairs grouped by offset, cut into chunks of at most 64 pairs
+    // the same pairs grouped by offset, cut into chunks of at most 16 pairs
+    // (small chunks spread one level's translations over many blocks)
     {
       std::vector<std::vector<int>> by(49);
       for (size_t ti = 0; ti < L.hne.size(); ++ti)
@@ -621,7 +622,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       std::vector<int> ptg, psr, pim, cof, cbg, cen;
       for (int o = 0; o < 49; ++o) {
         for (size_t i = 0; i < by[o].size(); ++i) {
-          if (i % 64 == 0) {
+          if (i % 16 == 0) {
             cof.push_back(o);
             cbg.push_back((int)ptg.size());
             cen.push_back((int)ptg.size());

@@ -1134,7 +1134,6 @@ __device__ __forceinline__ void atomic_add_c(cplxf* p, cplxf v) {
 // takes a chunk of the pairs of one offset: T_o is staged in shared memory once,
 // each warp applies it to one pair at a time (lanes over output rows) and adds
 // alpha^m T_o M(src) into L(target) atomically.
-#define M2L_CHUNK 64
 template <class C>
 __global__ void m2l_offset_t_kernel(int P, const int* __restrict__ chunk_off, const int* __restrict__ chunk_beg,
                                     const int* __restrict__ chunk_end, const int* __restrict__ ptgt,

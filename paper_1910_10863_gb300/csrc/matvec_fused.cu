@@ -1,19 +1,24 @@
 // The cached matrix-vector product (I - A) x of eq. 9 as ONE cooperative launch.
 //
 // The per-stage path launches some twenty small kernels per product (gather,
-// P2M, one M2M per level, one L2L + M2L per level, L2P, near field, fiber
+// P2M, one M2M per level, L2L and M2L per level, L2P, near field, fiber
 // blocks); at the sizes of a fundamental block most of them are latency-bound.
 // Here one grid of co-resident blocks runs the stages back to back and
 // separates them with a device-wide barrier:
 //
-//   A   gather the densities into tree order (alpha^{-m0} phase) and P2M  (warp per leaf)
+//   A   gather the densities into tree order (alpha^{-m0} phase), P2M,
+//       and clear the local expansions of levels 1..D                     (warp per leaf)
 //   B_l M2M into level l = D-1 .. 0; at the root also L(0) = R M(0)       (warp per box)
-//   D_l L2L from the parent plus M2L over the interaction list, l = 1..D  (warp per box)
+//   D_l L2L from the parent (warp per box) and M2L (block per chunk of
+//       pairs with one translation offset, T_o staged in shared memory),
+//       both added atomically into L(l), l = 1..D
 //   E   L2P + cached near field for every element of a leaf               (block per leaf)
 //   F   cached fiber blocks and the combination of eq. 9                  (block per row chunk)
 //
-// The arithmetic of every stage is that of the per-stage kernels (same tables,
-// same summation order within a box), so both paths agree to rounding.
+// Warp-level items are dealt round-robin over the blocks (item i to block
+// i mod grid), so that a stage with few items still spreads over all SMs: on
+// GB300 the FP64 pipe of one SM sub-partition executes a warp-wide DFMA only
+// every few dozen cycles, and a stage is as slow as its busiest SM.
 //
 // The barrier is a counter plus a generation word in device memory.  The
 // cooperative launch guarantees that every block is resident, so every wait
@@ -27,6 +32,8 @@ namespace {
 constexpr int FB = 256;          // threads per block
 constexpr int FW = FB / 32;      // warps per block
 constexpr int FSTAGE = 1536;     // near-field source densities staged in shared memory per leaf
+constexpr int TSP = 45;          // largest order count P whose M2L operator is staged in shared memory
+constexpr int TSIZE = TSP * (TSP + 1);
 
 template <class C>
 struct FusedArgs {
@@ -39,14 +46,18 @@ struct FusedArgs {
   C* dens;                       // sorted (phi', varphi')
   C* U;                          // sorted (U', dU')
   int nne[PF_MAXLEVEL + 1];
+  int nbox[PF_MAXLEVEL + 1];
   int P[PF_MAXLEVEL + 1];
+  int nch[PF_MAXLEVEL + 1];      // M2L chunks (pairs of one offset) per level
   const int* ne[PF_MAXLEVEL + 1];
   const int* bb[PF_MAXLEVEL + 1];
   const int* be[PF_MAXLEVEL + 1];
-  const int* ilp[PF_MAXLEVEL + 1];
-  const int* ils[PF_MAXLEVEL + 1];
-  const int* ilo[PF_MAXLEVEL + 1];
-  const int* ilm[PF_MAXLEVEL + 1];
+  const int* ch_off[PF_MAXLEVEL + 1];
+  const int* ch_beg[PF_MAXLEVEL + 1];
+  const int* ch_end[PF_MAXLEVEL + 1];
+  const int* pr_tgt[PF_MAXLEVEL + 1];
+  const int* pr_src[PF_MAXLEVEL + 1];
+  const int* pr_img[PF_MAXLEVEL + 1];
   const C* m2m[PF_MAXLEVEL + 1];     // at the parent level: [q][m child][n parent]
   const C* l2l[PF_MAXLEVEL + 1];     // at the parent level: [q][m parent][n child]
   const C* m2lt[PF_MAXLEVEL + 1];    // [o][n source][l target]
@@ -86,6 +97,15 @@ __device__ __forceinline__ cplx ldcg(const cplx* p) {
 __device__ __forceinline__ cplxf ldcg(const cplxf* p) {
   const float2 v = __ldcg(reinterpret_cast<const float2*>(p));
   return cplxf{v.x, v.y};
+}
+
+__device__ __forceinline__ void atomic_add(cplx* p, cplx v) {
+  atomicAdd(&p->re, v.re);
+  atomicAdd(&p->im, v.im);
+}
+__device__ __forceinline__ void atomic_add(cplxf* p, cplxf v) {
+  atomicAdd(&p->re, v.re);
+  atomicAdd(&p->im, v.im);
 }
 
 template <class C>
@@ -129,21 +149,41 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
   return s_ok != 0;
 }
 
+// acc += sum_m A[m * P] * w[m], m < K (A already offset to the output column),
+// two independent accumulators and unrolled loads.
+template <class C>
+__device__ __forceinline__ C colmv(const C* __restrict__ A, int P, const C* w, int K) {
+  C a0{0, 0}, a1{0, 0};
+  int m = 0;
+#pragma unroll 4
+  for (; m + 1 < K; m += 2) {
+    a0 += A[(size_t)m * P] * w[m];
+    a1 += A[(size_t)(m + 1) * P] * w[m + 1];
+  }
+  if (m < K) a0 += A[(size_t)m * P] * w[m];
+  return a0 + a1;
+}
+
 template <class C>
 __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   extern __shared__ unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gw = blockIdx.x * FW + warp, nwarps = gridDim.x * FW;
-  C* wsm = sm + (size_t)warp * PF_NCOEF;       // per-warp scratch (stages A, B, D)
+  const int G = gridDim.x;
+  const int wfirst = blockIdx.x + G * warp, wstride = G * FW;   // round-robin warp items
+  C* wsm = sm + TSIZE + (size_t)warp * PF_NCOEF;                // per-warp scratch
+  C* sT = sm;                                                   // [P][P+1] staged M2L operator
   const int D = a.D;
 
-  // ------------------------------------------------------------ A: gather + P2M
-  // Lanes over the coefficients n (one pass per 32); the inner loops are
-  // unrolled so that each lane keeps several independent loads in flight.
+  // ------------------------------------------------------------ A: gather + P2M, clear L
   {
+    for (int l = 1; l <= D; ++l) {
+      C* Lz = a.L[l];
+      const size_t nz = (size_t)a.nbox[l] * a.P[l];
+      for (size_t t = (size_t)blockIdx.x * FB + threadIdx.x; t < nz; t += (size_t)G * FB) Lz[t] = C{0, 0};
+    }
     const int PD = a.P[D];
-    for (int i = gw; i < a.nne[D]; i += nwarps) {
+    for (int i = wfirst; i < a.nne[D]; i += wstride) {
       const int box = a.ne[D][i], s0 = a.bb[D][box], s1 = a.be[D][box];
       for (int sb = s0; sb < s1; sb += 32) {
         const int s = sb + lane;
@@ -157,8 +197,8 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       __syncwarp();
       for (int n0 = 0; n0 < PD; n0 += 32) {
         const int n = n0 + lane;
-        C acc0{0, 0}, acc1{0, 0};
         if (n < PD) {
+          C acc0{0, 0}, acc1{0, 0};
 #pragma unroll 4
           for (int f = s0; f < s1; ++f) {
             const C* cf = a.p2m + (size_t)f * 2 * PD;
@@ -175,29 +215,20 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   // ------------------------------------------------------------ B: M2M (+ root)
   for (int l = D - 1; l >= 0; --l) {
     const int P = a.P[l], Pc = a.P[l + 1];
-    for (int i = gw; i < a.nne[l]; i += nwarps) {
+    for (int i = wfirst; i < a.nne[l]; i += wstride) {
       const int box = a.ne[l][i];
       for (int n0 = 0; n0 < P; n0 += 32) {
         const int n = n0 + lane;
-        C acc0{0, 0}, acc1{0, 0};
+        C acc{0, 0};
         for (int q = 0; q < 4; ++q) {
           const int ch = 4 * box + q;
           if (a.bb[l + 1][ch] >= a.be[l + 1][ch]) continue;
           __syncwarp();
           for (int m = lane; m < Pc; m += 32) wsm[m] = ldcg(a.M[l + 1] + (size_t)ch * Pc + m);
           __syncwarp();
-          if (n < P) {
-            const C* A = a.m2m[l] + (size_t)q * Pc * P + n;
-            int m = 0;
-#pragma unroll 4
-            for (; m + 1 < Pc; m += 2) {
-              acc0 += A[(size_t)m * P] * wsm[m];
-              acc1 += A[(size_t)(m + 1) * P] * wsm[m + 1];
-            }
-            if (m < Pc) acc0 += A[(size_t)m * P] * wsm[m];
-          }
+          if (n < P) acc += colmv(a.m2m[l] + (size_t)q * Pc * P + n, P, wsm, Pc);
         }
-        if (n < P) a.M[l][(size_t)box * P + n] = acc0 + acc1;
+        if (n < P) a.M[l][(size_t)box * P + n] = acc;
       }
       if (l == 0) {
         // root: L(0) = R M(0), the images |m| >= 2 through the lattice sums
@@ -217,43 +248,48 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   // ------------------------------------------------------------ D: L2L + M2L
   for (int l = 1; l <= D; ++l) {
     const int P = a.P[l], Pp = a.P[l - 1];
-    for (int i = gw; i < a.nne[l]; i += nwarps) {
+    // L2L, one warp per box
+    for (int i = wfirst; i < a.nne[l]; i += wstride) {
       const int box = a.ne[l][i], par = box >> 2, q = box & 3;
-      const int e0 = a.ilp[l][i], e1 = a.ilp[l][i + 1];
-      for (int n0 = 0; n0 < P; n0 += 32) {
-        const int n = n0 + lane;
-        C acc0{0, 0}, acc1{0, 0};
+      __syncwarp();
+      for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Pp + m);
+      __syncwarp();
+      for (int n = lane; n < P; n += 32)
+        atomic_add(a.L[l] + (size_t)box * P + n, colmv(a.l2l[l - 1] + (size_t)q * Pp * P + n, P, wsm, Pp));
+    }
+    // M2L, one block per chunk of pairs that share the translation offset
+    const bool stage = P <= TSP;
+    for (int b = blockIdx.x; b < a.nch[l]; b += G) {
+      const int o = a.ch_off[l][b], pb = a.ch_beg[l][b], pe = a.ch_end[l][b];
+      const C* To = a.m2lt[l] + (size_t)o * P * P;          // [n source][l target]
+      __syncthreads();                                      // sT of the previous chunk is done
+      if (stage)
+        for (int t = threadIdx.x; t < P * P; t += FB) sT[(t % P) * (P + 1) + t / P] = To[t];
+      __syncthreads();
+      for (int pi = pb + warp; pi < pe; pi += FW) {
+        const int src = a.pr_src[l][pi], tgt = a.pr_tgt[l][pi];
+        const C phs = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
         __syncwarp();
-        for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Pp + m);
+        for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * P + m);
         __syncwarp();
-        if (n < P) {
-          const C* B = a.l2l[l - 1] + (size_t)q * Pp * P + n;
-          int m = 0;
-#pragma unroll 4
-          for (; m + 1 < Pp; m += 2) {
-            acc0 += B[(size_t)m * P] * wsm[m];
-            acc1 += B[(size_t)(m + 1) * P] * wsm[m + 1];
-          }
-          if (m < Pp) acc0 += B[(size_t)m * P] * wsm[m];
-        }
-        for (int e = e0; e < e1; ++e) {
-          const int src = a.ils[l][e];
-          const C ph = from_d<C>(phase_m(a.alpha, a.ilm[l][e]));
-          __syncwarp();
-          for (int m = lane; m < P; m += 32) wsm[m] = ph * ldcg(a.M[l] + (size_t)src * P + m);
-          __syncwarp();
-          if (n < P) {
-            const C* T = a.m2lt[l] + (size_t)a.ilo[l][e] * P * P + n;
+        for (int n = lane; n < P; n += 32) {
+          C r;
+          if (stage) {
+            const C* row = sT + (size_t)n * (P + 1);
+            C r0{0, 0}, r1{0, 0};
             int m = 0;
 #pragma unroll 4
             for (; m + 1 < P; m += 2) {
-              acc0 += T[(size_t)m * P] * wsm[m];
-              acc1 += T[(size_t)(m + 1) * P] * wsm[m + 1];
+              r0 += row[m] * wsm[m];
+              r1 += row[m + 1] * wsm[m + 1];
             }
-            if (m < P) acc0 += T[(size_t)m * P] * wsm[m];
+            if (m < P) r0 += row[m] * wsm[m];
+            r = r0 + r1;
+          } else {
+            r = colmv(To + n, P, wsm, P);
           }
+          atomic_add(a.L[l] + (size_t)tgt * P + n, r);
         }
-        if (n < P) a.L[l][(size_t)box * P + n] = acc0 + acc1;
       }
     }
     if (!grid_barrier(a.bar, a.err)) return;
@@ -380,9 +416,9 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
 
 template <class C>
 size_t fused_smem(int maxfiber) {
-  const size_t a = (size_t)FW * PF_NCOEF;              // stages A, B, D
-  const size_t e = 2 * (size_t)FSTAGE + PF_NCOEF;      // stage E
-  const size_t f = 2 * (size_t)maxfiber;               // stage F
+  const size_t a = (size_t)TSIZE + (size_t)FW * PF_NCOEF;   // stages A, B, D
+  const size_t e = 2 * (size_t)FSTAGE + PF_NCOEF;           // stage E
+  const size_t f = 2 * (size_t)maxfiber;                    // stage F
   return sizeof(C) * std::max(a, std::max(e, f));
 }
 
@@ -403,10 +439,14 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
     a.ne[l] = L.ne;
     a.bb[l] = L.box_begin;
     a.be[l] = L.box_end;
-    a.ilp[l] = L.il_ptr;
-    a.ils[l] = L.il_src;
-    a.ilo[l] = L.il_off;
-    a.ilm[l] = L.il_img;
+    a.nbox[l] = L.nbox;
+    a.nch[l] = L.nchunk;
+    a.ch_off[l] = L.ch_off;
+    a.ch_beg[l] = L.ch_beg;
+    a.ch_end[l] = L.ch_end;
+    a.pr_tgt[l] = L.pr_tgt;
+    a.pr_src[l] = L.pr_src;
+    a.pr_img[l] = L.pr_img;
     if constexpr (sizeof(C) == sizeof(cplxf)) {
       a.m2m[l] = L.m2mf; a.l2l[l] = L.l2lf; a.m2lt[l] = L.m2ltf; a.M[l] = L.Mf; a.L[l] = L.Lf;
     } else {
