@@ -1380,8 +1380,12 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
       prev = relres;
       // The FP32 operator puts a floor of roughly eps_32 * cond under the inner
       // residual, so the inner solve is asked for a modest reduction and its
-      // work per refinement step is bounded; refinement does the rest.
-      const double inner_tol = std::max(1e-4, 0.3 * tol / relres);
+      // work per refinement step is bounded; refinement does the rest.  The
+      // first step aims at an absolute residual of 1e-4 ||B|| (a guess that
+      // already sits below ||B|| needs a smaller relative reduction), later
+      // steps at 0.3 tol ||B||.
+      const double target = refinements == 0 ? std::max(1e-4, 0.3 * tol) : 0.3 * tol;
+      const double inner_tol = std::max(1e-4, std::min(0.5, target / relres));
       const int cap = std::min(maxit - iters, 4 * g.m);
       int it = 0, rs = 0;
       double rr = 1;

@@ -1,13 +1,14 @@
 """Learned GMRES warm start: data, training and evaluation drivers.
 
-The network maps one fiber's row of pfmbem_warm_features_local (kH, theta, its
+Two models share the drivers below.  "global" (default): the network maps the
+block's parameters (pfmbem_warm_features: kH, theta and every fiber's centre and
+radius) to the Fourier modes n = -8..8 of both densities on every fiber
+(pfmbem_warm_targets: angles measured from the incidence direction,
+coefficients divided by the incident phase at the fiber centre).  "local": the
+network maps one fiber's row of pfmbem_warm_features_local (kH, theta, its
 radius, its distances to the block's edges and the relative positions and radii
-of its 15 nearest neighbours) to the Fourier modes n = -8..8 of both densities
-on that fiber (one row of pfmbem_warm_targets: angles measured from the
-incidence direction, coefficients divided by the incident phase at the fiber
-centre).  The same weights serve every fiber, so a block of M fibers gives M
-training rows and the prediction does not depend on where along the period the
-block sits.  Training data are solutions produced by the solver itself; forward,
+of its 15 nearest neighbours) to that fiber's modes; the same weights serve
+every fiber, so a block of M fibers gives M training rows.  Training data are solutions produced by the solver itself; forward,
 backward and Adam run in the library's kernels (pfmbem_mlp_*).  A prediction is
 decoded (pfmbem_warm_decode) and passed to pfmbem_solve as the initial guess,
 which scales it by the residual-minimising factor and falls back to a zero start
@@ -22,6 +23,7 @@ from . import pfmbem as pf
 NMODES = 8
 NEIGHBOURS = 15
 NOUT = 2 * (2 * NMODES + 1) * 2          # per fiber: 2 densities x 17 complex modes
+MODEL = "global"
 
 
 def solve_instance(w, guess=None, tol=1e-6, maxit=2000, precision=pf.MIXED):
@@ -34,19 +36,28 @@ def solve_instance(w, guess=None, tol=1e-6, maxit=2000, precision=pf.MIXED):
     return psi, info, s
 
 
-def features(s, M):
-    return pf.pfmbem_warm_features_local(s.h, M, NEIGHBOURS)
+def features(s, M, model=None):
+    """Network input rows of one block: one row (global) or one row per fiber (local)."""
+    if (model or MODEL) == "local":
+        return pf.pfmbem_warm_features_local(s.h, M, NEIGHBOURS)
+    return pf.pfmbem_warm_features(s.h, M)[None, :]
 
 
-def generate(instances, tol=1e-6):
-    """Per-fiber rows: features X [rows][5 + 3K], targets T [rows][2*17*2], the
-    instance index of every row and the zero-start iteration counts."""
+def targets(s, psi, M, model=None):
+    t = pf.pfmbem_warm_targets(s.h, psi, M, NMODES)
+    return t.reshape(M, NOUT) if (model or MODEL) == "local" else t.reshape(1, -1)
+
+
+def generate(instances, tol=1e-6, model=None):
+    """Rows of features X and targets T (one per block, or one per fiber for the
+    local model), the block index of every row and the zero-start iterations."""
     X, T, inst, iters = [], [], [], []
     for q, w in enumerate(instances):
         psi, info, s = solve_instance(w, tol=tol)
-        X.append(features(s, w.M))
-        T.append(pf.pfmbem_warm_targets(s.h, psi, w.M, NMODES).reshape(w.M, NOUT))
-        inst.append(np.full(w.M, q))
+        x = features(s, w.M, model)
+        X.append(x)
+        T.append(targets(s, psi, w.M, model))
+        inst.append(np.full(x.shape[0], q))
         iters.append(info.iters)
         s.close()
     return (np.concatenate(X).astype(np.float32), np.concatenate(T).astype(np.float32), np.concatenate(inst),
@@ -89,23 +100,27 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--train", type=int, default=8192)
     ap.add_argument("--test", type=int, default=1024)
-    ap.add_argument("--epochs", type=int, default=300)
-    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--model", default="global", choices=["global", "local"])
+    ap.add_argument("--epochs", type=int, default=0, help="0: 1000 (global) or 300 (local)")
+    ap.add_argument("--batch", type=int, default=0, help="0: 256 (global) or 512 (local)")
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--tol", type=float, default=1e-6)
     a = ap.parse_args()
+    a.epochs = a.epochs or (1000 if a.model == "global" else 300)
+    a.batch = a.batch or (256 if a.model == "global" else 512)
     t0 = time.perf_counter()
-    X, T, inst, _ = generate(W.batch_instances(a.train, seed=1912), tol=a.tol)
+    X, T, inst, _ = generate(W.batch_instances(a.train, seed=1912), tol=a.tol, model=a.model)
     nv = max(1, a.train // 16)               # validation split: the first blocks' rows
     val = inst < nv
     t1 = time.perf_counter()
     net, hist = train(X[~val], T[~val], epochs=a.epochs, batch=a.batch, lr=a.lr, X_val=X[val], T_val=T[val])
     t2 = time.perf_counter()
-    rows = evaluate(net, W.batch_instances(a.test, seed=1915), tol=a.tol)
+    rows = evaluate(net, W.batch_instances(a.test, seed=1915), tol=a.tol, model=a.model)
     t3 = time.perf_counter()
     iz, iw, r0 = rows[:, 0], rows[:, 1], rows[:, 2]
     print(json.dumps({
-        "train_blocks": a.train - nv, "validation_blocks": nv, "test_blocks": a.test, "epochs": a.epochs,
+        "model": a.model, "train_blocks": a.train - nv, "validation_blocks": nv, "test_blocks": a.test,
+        "epochs": a.epochs,
         "train_rows": int((~val).sum()), "inputs": int(X.shape[1]), "outputs": int(T.shape[1]),
         "first_loss": hist[0], "final_loss": hist[-1], "final_validation_loss": net.val_hist[-1],
         "mean_iters_zero_start": float(iz.mean()), "mean_iters_warm_start": float(iw.mean()),
@@ -124,7 +139,7 @@ def _residual(s, B, psi):
     return float(np.linalg.norm(B - r) / np.linalg.norm(B))
 
 
-def evaluate(net, instances, tol=1e-6):
+def evaluate(net, instances, tol=1e-6, model=None):
     """Per instance: zero-start and warm-start GMRES iterations (columns 0, 1),
     the FP64 relative residual of the decoded prediction (2), the final
     residuals (3, 4), the solve times in ms (5, 6), the residual of the exact
@@ -142,7 +157,7 @@ def evaluate(net, instances, tol=1e-6):
         proj = np.zeros_like(B)
         pf.pfmbem_warm_decode(s.h, pf.pfmbem_warm_targets(s.h, psi, w.M, NMODES), proj, NMODES)
         t0 = time.perf_counter()
-        y = net.forward(features(s, w.M))
+        y = net.forward(features(s, w.M, model))
         psi0 = np.zeros_like(B)
         pf.pfmbem_warm_decode(s.h, y.ravel(), psi0, NMODES)
         psi_w = psi0.copy()

@@ -82,7 +82,7 @@ def test_trained_network_reduces_gmres_iterations_on_held_out_blocks(pf):
     train = W.batch_instances(320, seed=101)
     test = W.batch_instances(24, seed=202)
     X, T, _, _ = ws.generate(train)
-    net, hist = ws.train(X, T, epochs=60, batch=128, lr=2e-3, seed=3)
+    net, hist = ws.train(X, T, epochs=150, batch=64, lr=2e-3, seed=3)
     assert hist[-1] < 0.5 * hist[0]
     rows = ws.evaluate(net, test)
     iz, iw, res0 = rows[:, 0], rows[:, 1], rows[:, 2]
