@@ -529,6 +529,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       }
     }
     h->fb_entries = acc;
+    h->hcirc = circ;
     const double bytes = (double)(4 * h->nc_blocks + acc) * (sizeof(cplx) + sizeof(cplxf));
     size_t freeb = 0, totb = 0;
     CK(cudaMemGetInfo(&freeb, &totb));
@@ -798,6 +799,40 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     bool tensor = false;
     for (int l = 1; l <= D; ++l) tensor = tensor || (h->lev[l].tc_B != nullptr && h->lev[l].tc_ntile > 0);
     if (h->opt.launch == 0 && !tensor) {
+      // fibers applied by FFT (regular polygons with 2^j elements, 8 <= N <= 1024)
+      // and the row chunks of the others
+      std::vector<int> fft, zchunk;
+      std::vector<int64_t> fhb(M, -1);
+      const std::vector<int>& circh = h->hcirc;
+      int64_t fa = 0;
+      for (int i = 0; i < M; ++i) {
+        const int n = foff[i + 1] - foff[i];
+        if (circh[i] && n >= 8 && n <= 1024 && (n & (n - 1)) == 0) {
+          fft.push_back(i);
+          fhb[i] = fa;
+          fa += n;
+        } else {
+          for (int r = 0; r < 2 * n; r += 32) {
+            zchunk.push_back(i);
+            zchunk.push_back(r);
+            zchunk.push_back(std::min(r + 32, 2 * n));
+          }
+        }
+      }
+      pfmbem_status st;
+      h->fz_nfft = (int)fft.size();
+      h->fz_nchunk = (int)zchunk.size() / 3;
+      if ((st = upload(h, &h->fz_fft, fft)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->fz_chunk, zchunk)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->fh_base, fhb)) != PFMBEM_OK) return st;
+      std::vector<cplx> twh(512);
+      for (int j = 0; j < 512; ++j) twh[j] = cplx{std::cos(2.0 * M_PI * j / 1024.0), std::sin(2.0 * M_PI * j / 1024.0)};
+      if ((st = upload(h, &h->tw, twh)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &h->twf, to_float(twh))) != PFMBEM_OK) return st;
+      h->fh_val = dalloc<cplx>(h, (size_t)4 * fa);
+      h->fh_valf = dalloc<cplxf>(h, (size_t)4 * fa);
+      if (!h->fh_val || !h->fh_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber symbols)");
+      CK(k_fiber_symbols(h));
       bool ok = false;
       CK(k_fused_prepare(h, &ok));
       if (ok) {

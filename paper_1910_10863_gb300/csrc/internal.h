@@ -147,6 +147,7 @@ struct pfmbem {
   // the FMM part (identity, k1 operators, self terms), row-major [2N][2N]
   int64_t* fb_base = nullptr;    // [M] offset of the fiber's block
   int* fb_circ = nullptr;        // [M] 1: regular polygon, circulant block stored as its row pair [2][2N]
+  std::vector<int> hcirc;        // host copy of fb_circ
   int* fb_chunk = nullptr;       // [nchunk][3] = fiber, first row, last row + 1
   int* s_m0 = nullptr;           // sorted: periods the element was shifted by when wrapped into the root
   int64_t* kt_base = nullptr;    // [M] first entry of the fiber's k table, -1 when not a regular polygon
@@ -171,6 +172,15 @@ struct pfmbem {
   bool fused = false;
   int fz_grid64 = 0, fz_grid32 = 0;
   unsigned* fz_bar = nullptr;    // [2] barrier arrivals and generation
+  int fz_nfft = 0;               // fibers whose block-circulant block is applied by FFT
+  int* fz_fft = nullptr;         // their indices
+  int64_t* fh_base = nullptr;    // [M] first frequency of the fiber's block symbol (-1: none)
+  cplx* fh_val = nullptr;        // [sum N][4] block symbols B^(r,s)(k)
+  cplxf* fh_valf = nullptr;
+  cplx* tw = nullptr;            // [512] e^{2 pi i j / 1024}
+  cplxf* twf = nullptr;
+  int fz_nchunk = 0;             // row chunks of the other fibers
+  int* fz_chunk = nullptr;
   int* fz_err = nullptr;         // set when a bounded barrier wait gave up
   cplx* root = nullptr;          // [P0][P0] periodic root translation
   cplxf* rootf = nullptr;
@@ -201,6 +211,7 @@ cudaError_t k_build_caches(pfmbem* h);
 // single-launch cached matvec (matvec_fused.cu)
 cudaError_t k_fused_prepare(pfmbem* h, bool* ok);
 cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision);
+cudaError_t k_fiber_symbols(pfmbem* h);
 cudaError_t k_build_fmm_caches(pfmbem* h);
 // learned warm start (mlp.cu)
 cudaError_t k_warm_features(pfmbem* h, float* x_dev);

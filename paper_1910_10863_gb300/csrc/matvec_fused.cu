@@ -13,7 +13,10 @@
 //       pairs with one translation offset, T_o staged in shared memory),
 //       both added atomically into L(l), l = 1..D
 //   E   L2P + cached near field for every element of a leaf               (block per leaf)
-//   F   cached fiber blocks and the combination of eq. 9                  (block per row chunk)
+//   F   fiber blocks and the combination of eq. 9: a regular-polygon fiber
+//       whose element count is a power of two applies its block-circulant
+//       block by FFT (block per fiber), the others by cached rows (block per
+//       chunk of 32 rows)
 //
 // Warp-level items are dealt round-robin over the blocks (item i to block
 // i mod grid), so that a stage with few items still spreads over all SMs: on
@@ -70,8 +73,13 @@ struct FusedArgs {
   const int* nc_sbase;
   const int* nc_src;
   const C* nc_val;
-  int nchunk;
+  int nchunk;                        // direct-row chunks (fibers not applied by FFT)
   const int* fb_chunk;
+  int nfft;                          // fibers applied by FFT
+  const int* fft_fib;
+  const int64_t* fh_base;            // [M] first frequency of the fiber's block symbol
+  const C* fh_val;                   // [sum N][4] block symbol B^(r,s)(k)
+  const C* tw;                       // [512] e^{2 pi i j / 1024}
   const int* foff;
   const int64_t* fb_base;
   const C* fb_val;
@@ -162,6 +170,73 @@ __device__ __forceinline__ C colmv(const C* __restrict__ A, int P, const C* w, i
   }
   if (m < K) a0 += A[(size_t)m * P] * w[m];
   return a0 + a1;
+}
+
+// In-place radix-2 FFTs of nseq sequences of length N = 2^lg (N <= 1024)
+// held one after another in shared memory, by the whole block:
+//   s_q(k) <- sum_j s_q(j) e^{sign 2 pi i j k / N}.
+// Decimation in time: bit-reversed order, then lg butterfly passes whose
+// twiddles come from the table of e^{2 pi i j / 1024}.
+template <class C>
+__device__ void block_fft(C* s, int nseq, int lg, int sign, const C* __restrict__ tw) {
+  const int N = 1 << lg, half_n = N >> 1;
+  __syncthreads();
+  for (int t = threadIdx.x; t < nseq * N; t += blockDim.x) {
+    const int q = t >> lg, j = t & (N - 1);
+    const int k = (int)(__brev((unsigned)j) >> (32 - lg));
+    if (j < k) {
+      C* sq = s + (q << lg);
+      const C v = sq[j];
+      sq[j] = sq[k];
+      sq[k] = v;
+    }
+  }
+  __syncthreads();
+  for (int st = 1; st <= lg; ++st) {
+    const int half = 1 << (st - 1), step = 1024 >> st;
+    for (int t = threadIdx.x; t < nseq * half_n; t += blockDim.x) {
+      const int q = t / half_n, b = t - q * half_n;
+      const int pos = b & (half - 1), i = ((b >> (st - 1)) << st) + pos;
+      C w = tw[pos * step];
+      if (sign < 0) w.im = -w.im;
+      C* sq = s + (q << lg);
+      const C u = sq[i], v = sq[i + half] * w;
+      sq[i] = u + v;
+      sq[i + half] = u - v;
+    }
+    __syncthreads();
+  }
+}
+
+// Block symbol of a block-circulant fiber block.  The stored row pair R_r
+// (r = 0, 1) of the first element gives the blocks b_d^(r,s) = R_r[2d + s]
+// with y_e^(r) = sum_{s,d} b_d^(r,s) x_{(e+d) mod N}^(s); with
+// X(k) = sum_f x_f e^{-2 pi i k f / N} this is Y^(r)(k) = sum_s B^(r,s)(k) X^(s)(k),
+// B^(r,s)(k) = sum_d b_d^(r,s) e^{+2 pi i k d / N}.  One block per fiber.
+__global__ void fiber_symbol_kernel(const int* __restrict__ fib_list, const int* __restrict__ foff,
+                                    const int64_t* __restrict__ fb_base, const cplx* __restrict__ rows,
+                                    const int64_t* __restrict__ fh_base, const cplx* __restrict__ tw,
+                                    cplx* __restrict__ fh, cplxf* __restrict__ fhf) {
+  extern __shared__ unsigned char smraw[];
+  cplx* s = reinterpret_cast<cplx*>(smraw);      // [2][N]
+  const int fb = fib_list[blockIdx.x];
+  const int N = foff[fb + 1] - foff[fb], lg = __ffs(N) - 1;
+  const cplx* R = rows + fb_base[fb];
+  cplx* out = fh + 4 * fh_base[fb];
+  cplxf* outf = fhf + 4 * fh_base[fb];
+  for (int r = 0; r < 2; ++r) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+      const int q = t / N, d = t - q * N;
+      s[t] = R[(size_t)r * 2 * N + 2 * d + q];
+    }
+    block_fft(s, 2, lg, +1, tw);
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+      const int q = t / N, k = t - q * N;
+      out[4 * k + 2 * r + q] = s[t];
+      outf[4 * k + 2 * r + q] = to_f(s[t]);
+    }
+  }
 }
 
 template <class C>
@@ -363,6 +438,34 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   // ------------------------------------------------------------ F: fiber blocks + combine
   {
     C* xs = sm;                                  // [2 N] the fiber's input densities
+    // block-circulant fibers by FFT: y^(r) = IFFT( sum_s B^(r,s) FFT(x^(s)) )
+    for (int b = blockIdx.x; b < a.nfft; b += gridDim.x) {
+      const int fb = a.fft_fib[b];
+      const int f0 = a.foff[fb], N = a.foff[fb + 1] - f0, lg = __ffs(N) - 1;
+      __syncthreads();
+      for (int t = threadIdx.x; t < 2 * N; t += FB) {
+        const int q = t >> lg, f = t & (N - 1);
+        xs[t] = from_d<C>(a.x[2 * (f0 + f) + q]);
+      }
+      block_fft(xs, 2, lg, -1, a.tw);
+      const C* Bh = a.fh_val + 4 * a.fh_base[fb];
+      for (int k = threadIdx.x; k < N; k += FB) {
+        const C x0 = xs[k], x1 = xs[N + k];
+        const C* bk = Bh + 4 * k;
+        xs[k] = bk[0] * x0 + bk[1] * x1;
+        xs[N + k] = bk[2] * x0 + bk[3] * x1;
+      }
+      block_fft(xs, 2, lg, +1, a.tw);
+      const double inv = 1.0 / N;
+      for (int t = threadIdx.x; t < 2 * N; t += FB) {
+        const int rr = t >> lg, e = f0 + (t & (N - 1));
+        const int s = a.opos[e];
+        const cplx po = cdiv(cplx{1, 0}, a.ph[s]);
+        const cplx u = po * to_d(ldcg(a.U + 2 * s + rr));
+        a.y[2 * e + rr] = inv * to_d(xs[t]) + (rr ? a.c2 * u : u);
+      }
+    }
+    // the other fibers from their cached rows
     for (int b = blockIdx.x; b < a.nchunk; b += gridDim.x) {
       const int fb = a.fb_chunk[3 * b], rb = a.fb_chunk[3 * b + 1], re = a.fb_chunk[3 * b + 2];
       const int f0 = a.foff[fb], n2 = 2 * (a.foff[fb + 1] - f0);
@@ -455,16 +558,19 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
   }
   if constexpr (sizeof(C) == sizeof(cplxf)) {
     a.dens = h->densf; a.U = h->Uf; a.root = h->rootf; a.p2m = h->p2m_cf; a.l2p = h->l2p_cf;
-    a.nc_val = h->nc_valf; a.fb_val = h->fb_valf;
+    a.nc_val = h->nc_valf; a.fb_val = h->fb_valf; a.fh_val = h->fh_valf; a.tw = h->twf;
   } else {
     a.dens = h->dens; a.U = h->U; a.root = h->root; a.p2m = h->p2m_c; a.l2p = h->l2p_c;
-    a.nc_val = h->nc_val; a.fb_val = h->fb_val;
+    a.nc_val = h->nc_val; a.fb_val = h->fb_val; a.fh_val = h->fh_val; a.tw = h->tw;
   }
   a.nc_base = h->nc_base;
   a.nc_sbase = h->nc_sbase;
   a.nc_src = h->nc_src;
-  a.nchunk = h->nchunk;
-  a.fb_chunk = h->fb_chunk;
+  a.nchunk = h->fz_nchunk;
+  a.fb_chunk = h->fz_chunk;
+  a.nfft = h->fz_nfft;
+  a.fft_fib = h->fz_fft;
+  a.fh_base = h->fh_base;
   a.foff = h->fib_off;
   a.fb_base = h->fb_base;
   a.circ = h->fb_circ;
@@ -512,13 +618,27 @@ cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
   *ok = false;
   // blocks with work in some stage: warps over boxes (A, B, D), blocks over
   // leaves (E) and over fiber row chunks (F)
-  int need = std::max(h->lev[h->D].nne, h->nchunk);
+  int need = std::max(h->lev[h->D].nne, h->fz_nchunk + h->fz_nfft);
   for (int l = 0; l <= h->D; ++l) need = std::max(need, (h->lev[l].nne + FW - 1) / FW);
   need = std::max(need, 1);
   h->fz_grid64 = std::min(fused_grid<cplx>(h->max_fiber), need);
   h->fz_grid32 = std::min(fused_grid<cplxf>(h->max_fiber), need);
   if (h->fz_grid64 <= 0 || h->fz_grid32 <= 0) return cudaSuccess;
   *ok = true;
+  return cudaGetLastError();
+}
+
+cudaError_t k_fiber_symbols(pfmbem* h) {
+  if (h->fz_nfft == 0) return cudaSuccess;
+  const size_t smem = 2 * (size_t)h->max_fiber * sizeof(cplx);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fiber_symbol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  prof_begin(h, PH_SETUP);
+  fiber_symbol_kernel<<<h->fz_nfft, 256, smem, h->stream>>>(h->fz_fft, h->fib_off, h->fb_base, h->fb_val, h->fh_base,
+                                                            h->tw, h->fh_val, h->fh_valf);
+  prof_end(h, PH_SETUP);
   return cudaGetLastError();
 }
 
