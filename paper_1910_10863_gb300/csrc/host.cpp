@@ -77,16 +77,6 @@ double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
-// J_0..J_N and Y_0..Y_N of a real argument x > 0 (Miller for J, forward recurrence for Y).
-void bessel_jy(double x, int N, std::vector<double>& J, std::vector<double>& Y) {
-  J.assign(N + 1, 0.0);
-  Y.assign(N + 1, 0.0);
-  bessel_j_array(x, N, J.data());
-  Y[0] = ::y0(x);
-  if (N >= 1) Y[1] = ::y1(x);
-  for (int n = 1; n < N; ++n) Y[n + 1] = (2.0 * n / x) * Y[n] - Y[n - 1];
-}
-
 inline int morton(int ix, int iy, int D) {
   int c = 0;
   for (int b = 0; b < D; ++b) c |= (((ix >> b) & 1) << (2 * b)) | (((iy >> b) & 1) << (2 * b + 1));
@@ -461,6 +451,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   h->dev_rhs = dalloc<cplx>(h, (size_t)2 * E);
   if (!h->self4 || !h->dens || !h->U || !h->stage_in || !h->stage_out || !h->dev_rhs)
     return fail(h, PFMBEM_ENOMEM, "device allocation failed (work buffers)");
+  h->tab_err = dalloc<int>(h, 1);
+  if (!h->tab_err) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
+  CK(cudaMemsetAsync(h->tab_err, 0, sizeof(int), h->stream));
   CK(k_self_terms(h));
   mark("element arrays, self terms");
   // ---------------------------------------------------- lattice sums + root operator
@@ -490,6 +483,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &h->rootf, to_float(Rt))) != PFMBEM_OK) return st;
   }
   mark("lattice sums, root");
+  // the second stream starts after everything uploaded so far (level weights)
+  if (!h->pre_ev) CK(cudaEventCreateWithFlags(&h->pre_ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(h->pre_ev, h->stream));
   // ---------------------------------------------------- near-field / fiber caches
   // The element integrals of the caches run on the GPU while the host builds
   // the M2L lists and translation tables on a second stream; the streams join
@@ -575,6 +571,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   }
   if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
   if (!h->side_ev) CK(cudaEventCreateWithFlags(&h->side_ev, cudaEventDisableTiming));
+  CK(cudaStreamWaitEvent(h->side, h->pre_ev, 0));
   h->astream = h->side;
   int64_t m2l_pairs = 0;
   for (int l = 1; l <= D; ++l) {
@@ -682,56 +679,22 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // ---------------------------------------------------- translation tables
   for (int l = 0; l <= D; ++l) {
     Level& L = h->lev[l];
-    const int p = L.p, P = L.P;
-    pfmbem_status st;
+    const int P = L.P;
     L.M = dalloc<cplx>(h, (size_t)L.nbox * P);
     L.L = dalloc<cplx>(h, (size_t)L.nbox * P);
     L.Mf = dalloc<cplxf>(h, (size_t)L.nbox * P);
     L.Lf = dalloc<cplxf>(h, (size_t)L.nbox * P);
     if (!L.Mf || !L.Lf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions)");
     if (!L.M || !L.L) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions)");
-    // M2L operators at this level: T[o][l][n] = w_l H^+_{n-l}(k (dx, dy) d) w_n
+    // M2L operators at this level, T[o][l][n] = w_l H^+_{n-l}(k (dx, dy) d) w_n, and
+    // the M2M / L2L operators to the children, built on the device
     if (l >= 1) {
-      std::vector<cplx> T((size_t)49 * P * P, cplx{0, 0});
-      std::vector<double> J, Y;
-      for (int dx = -3; dx <= 3; ++dx)
-        for (int dy = -3; dy <= 3; ++dy) {
-          if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
-          int o = (dx + 3) * 7 + (dy + 3);
-          double vx = dx * L.d, vy = dy * L.d;
-          double r = std::hypot(vx, vy), th = std::atan2(vy, vx);
-          bessel_jy(k * r, 2 * p, J, Y);
-          // Toeplitz vector H^+_j = H_j(k r) e^{i j th}, j = -2p..2p (H_-j = (-1)^j H_j)
-          std::vector<cplx> hv(4 * p + 1);
-          for (int j = -2 * p; j <= 2 * p; ++j) {
-            int aj = std::abs(j);
-            double sg = (j < 0 && (aj & 1)) ? -1.0 : 1.0;
-            double hr = sg * J[aj], hi = sg * Y[aj];
-            double cs = std::cos(j * th), sn = std::sin(j * th);
-            hv[j + 2 * p] = cplx{hr * cs - hi * sn, hr * sn + hi * cs};
-          }
-          for (int a = -p; a <= p; ++a)        // target coefficient l = a
-            for (int n = -p; n <= p; ++n) {    // source coefficient n
-              const cplx hj = hv[n - a + 2 * p];
-              double sc = L.w[a + p] * L.w[n + p];
-              cplx v{sc * hj.re, sc * hj.im};
-              if (!std::isfinite(v.re) || !std::isfinite(v.im))
-                return fail(h, PFMBEM_ENUMERIC, "non-finite M2L operator; lower p or change depth");
-              T[((size_t)o * P + (a + p)) * P + (n + p)] = v;
-            }
-        }
-      if ((st = upload(h, &L.m2l, T)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.m2lf, to_float(T))) != PFMBEM_OK) return st;
-      {
-        // transposed copy for the single-launch matvec: [o][source n][target a]
-        std::vector<cplx> Tt(T.size());
-        for (int o = 0; o < 49; ++o)
-          for (int a2 = 0; a2 < P; ++a2)
-            for (int n2 = 0; n2 < P; ++n2)
-              Tt[((size_t)o * P + n2) * P + a2] = T[((size_t)o * P + a2) * P + n2];
-        if ((st = upload(h, &L.m2lt, Tt)) != PFMBEM_OK) return st;
-        if ((st = upload(h, &L.m2ltf, to_float(Tt))) != PFMBEM_OK) return st;
-      }
+      const size_t n = (size_t)49 * P * P;
+      L.m2l = dalloc<cplx>(h, n);
+      L.m2lf = dalloc<cplxf>(h, n);
+      L.m2lt = dalloc<cplx>(h, n);
+      L.m2ltf = dalloc<cplxf>(h, n);
+      if (!L.m2l || !L.m2lf || !L.m2lt || !L.m2ltf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (M2L)");
       if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2) {
         const int kp = tc_kpad(P);
         L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
@@ -740,41 +703,15 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         L.tc_ntile = 0;
       }
     }
-    // M2M (children l+1 -> l) and L2L (l -> children)
     if (l < D) {
-      Level& C = h->lev[l + 1];
-      const int pc = C.p, Pc = C.P;
-      std::vector<cplx> A((size_t)4 * P * Pc), B((size_t)4 * Pc * P);
-      std::vector<double> J, Y;
-      for (int q = 0; q < 4; ++q) {
-        int cx = q & 1, cy = (q >> 1) & 1;
-        double vx = (cx - 0.5) * C.d, vy = (cy - 0.5) * C.d;   // O_child - O_parent
-        double r = std::hypot(vx, vy), th = std::atan2(vy, vx);
-        bessel_jy(k * r, p + pc, J, Y);
-        for (int n = -p; n <= p; ++n)
-          for (int m = -pc; m <= pc; ++m) {
-            // A[n][m] = J^-_{n-m}(k v) w^c_m / w^p_n,  J^-_j = J_j e^{-i j th}
-            int j = n - m, aj = std::abs(j);
-            double Jj = (j < 0 && (aj & 1)) ? -J[aj] : J[aj];
-            double s = C.w[m + pc] / L.w[n + p];
-            // stored transposed, [q][m][n], so that threads over n read contiguously
-            A[((size_t)q * Pc + (m + pc)) * P + (n + p)] = cplx{s * Jj * std::cos(j * th), -s * Jj * std::sin(j * th)};
-          }
-        for (int n = -pc; n <= pc; ++n)
-          for (int m = -p; m <= p; ++m) {
-            // B[n][m] = w^c_n J^+_{m-n}(k v) / w^p_m,  J^+_j = J_j e^{i j th}
-            int j = m - n, aj = std::abs(j);
-            double Jj = (j < 0 && (aj & 1)) ? -J[aj] : J[aj];
-            double s = C.w[n + pc] / L.w[m + p];
-            // stored transposed, [q][m][n] (m parent, n child coefficient)
-            B[((size_t)q * P + (m + p)) * Pc + (n + pc)] = cplx{s * Jj * std::cos(j * th), s * Jj * std::sin(j * th)};
-          }
-      }
-      if ((st = upload(h, &L.m2m, A)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.l2l, B)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.m2mf, to_float(A))) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.l2lf, to_float(B))) != PFMBEM_OK) return st;
+      const size_t n = (size_t)4 * P * h->lev[l + 1].P;
+      L.m2m = dalloc<cplx>(h, n);
+      L.m2mf = dalloc<cplxf>(h, n);
+      L.l2l = dalloc<cplx>(h, n);
+      L.l2lf = dalloc<cplxf>(h, n);
+      if (!L.m2m || !L.m2mf || !L.l2l || !L.l2lf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (M2M)");
     }
+    CK(k_level_tables(h, l, h->astream ? h->astream : h->stream));
   }
   mark("translation tables (overlapped)");
   // join: later work on the main stream sees every upload of the second stream
@@ -838,7 +775,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if (ok) {
         h->fz_bar = dalloc<unsigned>(h, 2);
         h->fz_err = dalloc<int>(h, 1);
-        if (!h->fz_bar || !h->fz_err) return fail(h, PFMBEM_ENOMEM, "device allocation failed (barrier)");
+        h->fz_stamp = dalloc<unsigned long long>(h, 32);
+        if (!h->fz_bar || !h->fz_err || !h->fz_stamp)
+          return fail(h, PFMBEM_ENOMEM, "device allocation failed (barrier)");
         CK(cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned), h->stream));
         CK(cudaMemsetAsync(h->fz_err, 0, sizeof(int), h->stream));
         h->fused = true;
@@ -847,6 +786,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   }
   mark("near + fiber integrals, P2M/L2P caches");
   CK(cudaStreamSynchronize(h->stream));
+  {
+    int bad = 0;
+    CK(cudaMemcpy(&bad, h->tab_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (bad) return fail(h, PFMBEM_ENUMERIC, "non-finite M2L operator; lower p or change depth");
+  }
   mark("end of set-up");
   h->info.E = E;
   h->info.M = M;
@@ -1273,6 +1217,7 @@ void pfmbem_destroy(pfmbem_t h) {
   else cudaDeviceSynchronize();
   if (h->gw.hhost) cudaFreeHost(h->gw.hhost);
   if (h->side_ev) cudaEventDestroy(h->side_ev);
+  if (h->pre_ev) cudaEventDestroy(h->pre_ev);
   if (h->side) cudaStreamDestroy(h->side);
   prof_release(h);
   delete h;

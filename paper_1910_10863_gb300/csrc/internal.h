@@ -99,6 +99,7 @@ struct pfmbem {
   cudaStream_t stream = nullptr;
   cudaStream_t side = nullptr;   // second stream of the set-up: host planning overlaps the cache build
   cudaEvent_t side_ev = nullptr;
+  cudaEvent_t pre_ev = nullptr;    // main-stream point the second stream waits for
   cudaStream_t astream = nullptr;  // stream of allocations and uploads while set-up runs on `side`
   std::string err;
   // plan
@@ -166,6 +167,7 @@ struct pfmbem {
   cplxf* l2p_cf = nullptr;
   // FP32 work buffers of the mixed matvec
   int* tc_err = nullptr;         // set by the tensor-core M2L when a bounded wait gave up
+  int* tab_err = nullptr;        // set when a translation table has a non-finite entry
   cplxf* densf = nullptr;        // [E][2]
   cplxf* Uf = nullptr;           // [E][2]
   // single-launch cached matvec (cooperative grid, device-wide barrier)
@@ -182,6 +184,7 @@ struct pfmbem {
   int fz_nchunk = 0;             // row chunks of the other fibers
   int* fz_chunk = nullptr;
   int* fz_err = nullptr;         // set when a bounded barrier wait gave up
+  unsigned long long* fz_stamp = nullptr;   // [32] stage end times (diagnostic)
   cplx* root = nullptr;          // [P0][P0] periodic root translation
   cplxf* rootf = nullptr;
   std::vector<cplx> lattice_S;   // S_j, j = 0..2 p0 (S_-j = S_j)
@@ -225,6 +228,7 @@ cudaError_t k_coefficients(pfmbem* h, const cplx* psi, int norders, const int* o
 void k_upload_gauss(const double* x, const double* w, const double* thr64, const double* thr32);
 void k_upload_series();
 cudaError_t k_self_terms(pfmbem* h);
+cudaError_t k_level_tables(pfmbem* h, int l, cudaStream_t st);
 cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev);
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_rhs(pfmbem* h, cplx* B);

@@ -114,6 +114,116 @@ void prof_release(pfmbem* h) {
   h->prof.ev.clear();
 }
 
+// ---------------------------------------------------------------- translation tables
+// Built on the device from the level's weights w_n (already resident), one
+// block per translation vector; thread 0 evaluates J_0..J_N (Miller) and
+// Y_0..Y_N (CUDA y0/y1 and forward recurrence) of k|v| into shared memory.
+__device__ void bessel_jy_block(double x, int N, double* J, double* Y) {
+  if (threadIdx.x == 0) {
+    bessel_j_array(x, N, J);
+    Y[0] = y0(x);
+    if (N >= 1) Y[1] = y1(x);
+    for (int n = 1; n < N; ++n) Y[n + 1] = (2.0 * n / x) * Y[n] - Y[n - 1];
+  }
+  __syncthreads();
+}
+
+// M2L operators of one level (Sec. 3.2): T[o][a][n] = w_a H^+_{n-a}(k v_o) w_n,
+// H^+_j = H_j(k|v|) e^{i j theta_v}, H_{-j} = (-1)^j H_j, for the offsets
+// v_o = (dx, dy) d, o = (dx + 3) 7 + (dy + 3), max(|dx|, |dy|) >= 2 (the others
+// stay zero).  Also the transposed copy [o][n][a] and FP32 copies.
+__global__ void m2l_table_kernel(int p, double d, double k, const double* __restrict__ w, cplx* __restrict__ T,
+                                 cplxf* __restrict__ Tf, cplx* __restrict__ Tt, cplxf* __restrict__ Ttf,
+                                 int* __restrict__ bad) {
+  const int o = blockIdx.x, dx = o / 7 - 3, dy = o % 7 - 3;
+  if (abs(dx) <= 1 && abs(dy) <= 1) return;
+  __shared__ double J[4 * PF_PMAX + 2], Y[4 * PF_PMAX + 2];
+  __shared__ cplx hv[4 * PF_PMAX + 1];
+  const int P = 2 * p + 1;
+  const double vx = dx * d, vy = dy * d;
+  const double r = sqrt(vx * vx + vy * vy), th = atan2(vy, vx);
+  bessel_jy_block(k * r, 2 * p, J, Y);
+  for (int j = threadIdx.x - 2 * p; j <= 2 * p; j += blockDim.x) {
+    const int aj = abs(j);
+    const double sg = (j < 0 && (aj & 1)) ? -1.0 : 1.0;
+    double sn, cs;
+    sincos(j * th, &sn, &cs);
+    const double hr = sg * J[aj], hi = sg * Y[aj];
+    hv[j + 2 * p] = cplx{hr * cs - hi * sn, hr * sn + hi * cs};
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+    const int a = t / P, n = t % P;                 // a: target coefficient + p, n: source + p
+    const cplx hj = hv[n - a + 2 * p];
+    const double sc = w[a] * w[n];
+    const cplx v{sc * hj.re, sc * hj.im};
+    if (!isfinite(v.re) || !isfinite(v.im)) atomicExch(bad, 1);
+    const size_t i1 = ((size_t)o * P + a) * P + n, i2 = ((size_t)o * P + n) * P + a;
+    T[i1] = v;
+    Tf[i1] = to_f(v);
+    Tt[i2] = v;
+    Ttf[i2] = to_f(v);
+  }
+}
+
+// M2M (children of level l+1 -> level l) and L2L (level l -> children) for the
+// child quadrant q (blockIdx.x), v = O_child - O_parent:
+//   A[q][m][n] = J^-_{n-m}(k v) w^c_m / w^p_n,  J^-_j = J_j e^{-i j theta}
+//   B[q][m][n] = w^c_n J^+_{m-n}(k v) / w^p_m,  J^+_j = J_j e^{+i j theta}
+// (m child and n parent coefficient in A, m parent and n child in B).
+__global__ void m2m_table_kernel(int p, int pc, double dc, double k, const double* __restrict__ wp,
+                                 const double* __restrict__ wc, cplx* __restrict__ A, cplxf* __restrict__ Af,
+                                 cplx* __restrict__ B, cplxf* __restrict__ Bf) {
+  const int q = blockIdx.x, cx = q & 1, cy = (q >> 1) & 1;
+  __shared__ double J[2 * PF_PMAX + 2], Y[2 * PF_PMAX + 2];
+  const int P = 2 * p + 1, Pc = 2 * pc + 1;
+  const double vx = (cx - 0.5) * dc, vy = (cy - 0.5) * dc;
+  const double r = sqrt(vx * vx + vy * vy), th = atan2(vy, vx);
+  bessel_jy_block(k * r, p + pc, J, Y);
+  for (int t = threadIdx.x; t < P * Pc; t += blockDim.x) {
+    {
+      const int m = t / P - pc, n = t % P - p;       // A: [q][m + pc][n + p]
+      const int j = n - m, aj = abs(j);
+      const double Jj = (j < 0 && (aj & 1)) ? -J[aj] : J[aj];
+      const double sc = wc[m + pc] / wp[n + p];
+      double sn, cs;
+      sincos(j * th, &sn, &cs);
+      const cplx v{sc * Jj * cs, -sc * Jj * sn};
+      A[(size_t)q * Pc * P + t] = v;
+      Af[(size_t)q * Pc * P + t] = to_f(v);
+    }
+    {
+      const int m = t / Pc - p, n = t % Pc - pc;     // B: [q][m + p][n + pc]
+      const int j = m - n, aj = abs(j);
+      const double Jj = (j < 0 && (aj & 1)) ? -J[aj] : J[aj];
+      const double sc = wc[n + pc] / wp[m + p];
+      double sn, cs;
+      sincos(j * th, &sn, &cs);
+      const cplx v{sc * Jj * cs, sc * Jj * sn};
+      B[(size_t)q * P * Pc + t] = v;
+      Bf[(size_t)q * P * Pc + t] = to_f(v);
+    }
+  }
+}
+
+cudaError_t k_level_tables(pfmbem* h, int l, cudaStream_t st) {
+  Level& L = h->lev[l];
+  if (l >= 1) {
+    const size_t n = (size_t)49 * L.P * L.P;
+    cudaError_t e = cudaMemsetAsync(L.m2l, 0, n * sizeof(cplx), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.m2lf, 0, n * sizeof(cplxf), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.m2lt, 0, n * sizeof(cplx), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(L.m2ltf, 0, n * sizeof(cplxf), st);
+    if (e != cudaSuccess) return e;
+    m2l_table_kernel<<<49, 256, 0, st>>>(L.p, L.d, h->k, L.w_dev, L.m2l, L.m2lf, L.m2lt, L.m2ltf, h->tab_err);
+  }
+  if (l < h->D) {
+    Level& C = h->lev[l + 1];
+    m2m_table_kernel<<<4, 256, 0, st>>>(L.p, C.p, C.d, h->k, L.w_dev, C.w_dev, L.m2m, L.m2mf, L.l2l, L.l2lf);
+  }
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- self terms
 // S_ee = (i/2)(1/kappa) I(x), T_ee = (i/2) kappa [I(x) - H1(x)], x = kappa h/2,
 // I(x) = int_0^x H0(t) dt by term-wise integration of the ascending series of

@@ -28,6 +28,9 @@
 // ends; each wait is nevertheless bounded (about one second), after which the
 // block records an error flag and returns, and the host reports
 // PFMBEM_ETIMEOUT instead of a result.
+#include <cstdio>
+#include <cstdlib>
+
 #include "internal.h"
 
 namespace {
@@ -87,7 +90,16 @@ struct FusedArgs {
   cplx alpha, c2;
   unsigned* bar;                     // [0] arrivals, [1] generation
   int* err;
+  unsigned long long* stamp;         // optional stage end times (ns), written by block 0
 };
+
+__device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k) {
+  if (stamp && blockIdx.x == 0 && threadIdx.x == 0) {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    stamp[k] = t;
+  }
+}
 
 __device__ __forceinline__ cplx phase_m(cplx alpha, int m) {
   // alpha^m for m in {-1, 0, 1}
@@ -249,6 +261,8 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   C* wsm = sm + TSIZE + (size_t)warp * PF_NCOEF;                // per-warp scratch
   C* sT = sm;                                                   // [P][P+1] staged M2L operator
   const int D = a.D;
+  int ks = 0;
+  stage_stamp(a.stamp, ks++);
 
   // ------------------------------------------------------------ A: gather + P2M, clear L
   {
@@ -286,6 +300,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     }
   }
   if (!grid_barrier(a.bar, a.err)) return;
+  stage_stamp(a.stamp, ks++);
 
   // ------------------------------------------------------------ B: M2M (+ root)
   for (int l = D - 1; l >= 0; --l) {
@@ -318,6 +333,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       }
     }
     if (!grid_barrier(a.bar, a.err)) return;
+    stage_stamp(a.stamp, ks++);
   }
 
   // ------------------------------------------------------------ D: L2L + M2L
@@ -368,6 +384,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       }
     }
     if (!grid_barrier(a.bar, a.err)) return;
+    stage_stamp(a.stamp, ks++);
   }
 
   // ------------------------------------------------------------ E: L2P + near field
@@ -434,6 +451,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     }
   }
   if (!grid_barrier(a.bar, a.err)) return;
+  stage_stamp(a.stamp, ks++);
 
   // ------------------------------------------------------------ F: fiber blocks + combine
   {
@@ -515,6 +533,8 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       }
     }
   }
+  __syncthreads();
+  stage_stamp(a.stamp, ks++);
 }
 
 template <class C>
@@ -578,6 +598,8 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
   a.c2 = cplx{h->c2re, h->c2im};
   a.bar = h->fz_bar;
   a.err = h->fz_err;
+  static const bool stamps = std::getenv("PFMBEM_STAGE_TIMES") != nullptr;
+  a.stamp = stamps ? h->fz_stamp : nullptr;
   const int grid = f32 ? h->fz_grid32 : h->fz_grid64;
   const size_t smem = fused_smem<C>(h->max_fiber);
   void* args[] = {&a};
@@ -586,6 +608,18 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)matvec_fused_kernel<C>, dim3(grid), dim3(FB), args, smem,
                                               h->stream);
   prof_end(h, ph);
+  if (e == cudaSuccess && a.stamp) {
+    // diagnostic (PFMBEM_STAGE_TIMES set): stage durations of this launch on stderr
+    unsigned long long t[32];
+    e = cudaMemcpyAsync(t, a.stamp, sizeof(t), cudaMemcpyDeviceToHost, h->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e == cudaSuccess) {
+      const int n = 2 * h->D + 4;
+      std::fprintf(stderr, "pfmbem fused %s stages (us):", f32 ? "f32" : "f64");
+      for (int i = 1; i < n; ++i) std::fprintf(stderr, " %.1f", 1e-3 * (double)(t[i] - t[i - 1]));
+      std::fprintf(stderr, "  total %.1f\n", 1e-3 * (double)(t[n - 1] - t[0]));
+    }
+  }
   return e;
 }
 
