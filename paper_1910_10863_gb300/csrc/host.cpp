@@ -538,6 +538,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if ((st = upload(h, &h->fb_base, fbase)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->fb_circ, circ)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->fb_chunk, chunks)) != PFMBEM_OK) return st;
+      std::vector<int> rows;
+      for (int i = 0; i < M; ++i)
+        for (int e = foff[i]; e < (circ[i] ? foff[i] + 1 : foff[i + 1]); ++e) rows.push_back(e);
+      h->nfb_rows = (int)rows.size();
+      if ((st = upload(h, &h->fb_rows, rows)) != PFMBEM_OK) return st;
       // k tables of the regular-polygon fibers and the wrap shift of every element
       std::vector<int64_t> kbase(M, -1);
       int64_t kacc = 0;

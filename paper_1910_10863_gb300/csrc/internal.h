@@ -150,6 +150,8 @@ struct pfmbem {
   int* fb_circ = nullptr;        // [M] 1: regular polygon, circulant block stored as its row pair [2][2N]
   std::vector<int> hcirc;        // host copy of fb_circ
   int* fb_chunk = nullptr;       // [nchunk][3] = fiber, first row, last row + 1
+  int* fb_rows = nullptr;        // elements whose row pairs are built (first element of a circulant fiber)
+  int nfb_rows = 0;
   int* s_m0 = nullptr;           // sorted: periods the element was shifted by when wrapped into the root
   int64_t* kt_base = nullptr;    // [M] first entry of the fiber's k table, -1 when not a regular polygon
   cplx* kt_val = nullptr;        // [sum N over regular fibers][4]: S, D, K, T at k of (f0, f0 + dl)

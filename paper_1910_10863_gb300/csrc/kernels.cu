@@ -902,70 +902,44 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
   }
 }
 
-// Same-fiber integrals at the matrix wavenumber k of a regular-polygon fiber:
-// S, D, K, T (without the factor i/4) of its first element's midpoint against
-// element f0 + dl, dl = 1..N-1 (dl = 0, the self element, stays zero).  Rotating
-// the fiber by one element maps it onto itself, so element pair (e, e + dl) has
-// the integrals of (f0, f0 + dl) and the near-field build reads them from here.
-// One warp per fiber.
-__global__ void ktab_build_kernel(int M, const int* __restrict__ foff, const int64_t* __restrict__ kbase, double k,
-                                  const double2* __restrict__ oc, const double2* __restrict__ ot,
-                                  const double2* __restrict__ onu, const double* __restrict__ oh,
-                                  cplx* __restrict__ kval, unsigned long long* __restrict__ stat) {
-  const int lane = threadIdx.x & 31;
-  const int fb = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (fb >= M || kbase[fb] < 0) return;
-  const int f0 = foff[fb], N = foff[fb + 1] - f0;
-  const double2 xe = oc[f0], nxe = onu[f0];
-  cplx* out = kval + 4 * kbase[fb];
-  unsigned long long npair = 0, nquad = 0;
-  for (int dl = lane; dl < N; dl += 32) {
-    cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
-    if (dl > 0) {
-      const int f = f0 + dl;
-      const double2 c = oc[f];
-      const double hh = oh[f];
-      const double q = sqrt((xe.x - c.x) * (xe.x - c.x) + (xe.y - c.y) * (xe.y - c.y)) / hh;
-      const int g = gl_order(q, 0);
-      ++npair;
-      nquad += g;
-      pair4_f64(k, xe, nxe, c, ot[f], onu[f], hh, g, S, Dv, K, T);
-    }
-    out[4 * dl + 0] = S;
-    out[4 * dl + 1] = Dv;
-    out[4 * dl + 2] = K;
-    out[4 * dl + 3] = T;
-  }
-  if (stat) {
-    atomicAdd(&stat[0], npair);
-    atomicAdd(&stat[1], nquad);
-  }
-}
-
 // ------------------------------------------------------------ cached fiber blocks
 // Row pair (2e, 2e+1) of fiber i's diagonal block of (I - A) without the
 // periodic k part:  [1 - D1, i eta S1; -c2 rho T1, 1 + i eta c2 rho K1] over the
 // same-fiber sources (k1, eq. 5), plus on the diagonal the self terms of both
 // wavenumbers (-i eta S_ee(k) and c2 T_ee(k) of the k part, whose remainder
 // comes from the FMM).  One warp per target element.
-__global__ void fiber_build_kernel(int E, const int* __restrict__ fib, const int* __restrict__ foff,
-                                   const int64_t* __restrict__ fbase, double k1, double eta, double rho, cplx c2,
-                                   const double2* __restrict__ oc, const double2* __restrict__ ot,
-                                   const double2* __restrict__ onu, const double* __restrict__ oh,
-                                   const cplx* __restrict__ self4, cplx* __restrict__ val, cplxf* __restrict__ valf,
-                                   unsigned long long* __restrict__ stat, const int* __restrict__ circ) {
-  const int lane = threadIdx.x & 31;
-  const int e = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (e >= E) return;
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// One thread per (row element e, source f) of the same fiber; rows lists the
+// elements whose row pairs are stored (the first element of a circulant fiber,
+// every element of the others).  For a regular-polygon fiber (kbase >= 0) the
+// same thread also writes the fiber's k table: S, D, K, T (without i/4) at the
+// matrix wavenumber k of the first element's midpoint against element f0 + dl,
+// dl = f - f0 (zero for dl = 0).  Rotating the fiber by one element maps it onto
+// itself, so element pair (e, e + dl) has the integrals of (f0, f0 + dl) and the
+// near-field build reads same-fiber pairs from this table.
+__global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __restrict__ fib,
+                                   const int* __restrict__ foff, const int64_t* __restrict__ fbase, double k,
+                                   double k1, double eta, double rho, cplx c2, const double2* __restrict__ oc,
+                                   const double2* __restrict__ ot, const double2* __restrict__ onu,
+                                   const double* __restrict__ oh, const cplx* __restrict__ self4,
+                                   const int64_t* __restrict__ kbase, cplx* __restrict__ kval,
+                                   cplx* __restrict__ val, cplxf* __restrict__ valf,
+                                   unsigned long long* __restrict__ stat) {
+  const int e = rows[blockIdx.x];
   const int fb = fib[e], f0 = foff[fb], N = foff[fb + 1] - f0, el = e - f0;
-  // circulant fiber: only the first element's row pair is stored
-  if (circ[fb] && el != 0) return;
-  const int64_t r0 = fbase[fb] + (int64_t)(2 * el) * (2 * N), r1 = r0 + 2 * N;
-  const double2 xe = oc[e], nxe = onu[e];
-  const cplx c2r = rho * c2;
-  unsigned long long nquad = 0;
-  for (int f = f0 + lane; f < f0 + N; f += 32) {
-    const int fl = f - f0;
+  const int fl = blockIdx.y * blockDim.x + threadIdx.x;
+  unsigned long long kp = 0, kq = 0, fp = 0, fq = 0;
+  if (fl < N) {
+    const int f = f0 + fl;
+    const int64_t r0 = fbase[fb] + (int64_t)(2 * el) * (2 * N), r1 = r0 + 2 * N;
+    const double2 xe = oc[e], nxe = onu[e];
+    const cplx c2r = rho * c2;
+    const int64_t kb = kbase[fb];
     cplx a00, a01, a10, a11;
     if (f == e) {
       const cplx Sk = self4[4 * e], Tk = self4[4 * e + 1], Sk1 = self4[4 * e + 2], Tk1 = self4[4 * e + 3];
@@ -973,14 +947,19 @@ __global__ void fiber_build_kernel(int E, const int* __restrict__ fib, const int
       a01 = eta * mul_i(Sk1) - eta * mul_i(Sk);
       a10 = c2 * Tk - c2r * Tk1;
       a11 = cplx{1, 0};
+      if (kb >= 0) {
+        cplx* tv = kval + 4 * (kb + fl);
+        tv[0] = tv[1] = tv[2] = tv[3] = cplx{0, 0};
+      }
     } else {
-      const double2 c = oc[f];
+      const double2 c = oc[f], tf = ot[f], nf = onu[f];
       const double hh = oh[f];
       const double q = sqrt((xe.x - c.x) * (xe.x - c.x) + (xe.y - c.y) * (xe.y - c.y)) / hh;
       const int g = gl_order(q, 0);
-      nquad += g;
+      fp = 1;
+      fq = g;
       cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
-      pair4_f64(k1, xe, nxe, c, ot[f], onu[f], hh, g, S, Dv, K, T);
+      pair4_f64(k1, xe, nxe, c, tf, nf, hh, g, S, Dv, K, T);
       S = mul_i(0.25 * S);
       Dv = mul_i(0.25 * Dv);
       K = mul_i(0.25 * K);
@@ -989,6 +968,17 @@ __global__ void fiber_build_kernel(int E, const int* __restrict__ fib, const int
       a01 = eta * mul_i(S);
       a10 = -(c2r * T);
       a11 = eta * mul_i(c2r * K);
+      if (kb >= 0) {
+        cplx Sk{0, 0}, Dk{0, 0}, Kk{0, 0}, Tk{0, 0};
+        pair4_f64(k, xe, nxe, c, tf, nf, hh, g, Sk, Dk, Kk, Tk);
+        cplx* tv = kval + 4 * (kb + fl);
+        tv[0] = Sk;
+        tv[1] = Dk;
+        tv[2] = Kk;
+        tv[3] = Tk;
+        kp = 1;
+        kq = g;
+      }
     }
     val[r0 + 2 * fl] = a00;
     val[r0 + 2 * fl + 1] = a01;
@@ -1002,8 +992,16 @@ __global__ void fiber_build_kernel(int E, const int* __restrict__ fib, const int
     }
   }
   if (stat) {
-    if (lane == 0) atomicAdd(&stat[2], (unsigned long long)(N - 1));
-    atomicAdd(&stat[3], nquad);
+    kp = warp_sum_u64(kp);
+    kq = warp_sum_u64(kq);
+    fp = warp_sum_u64(fp);
+    fq = warp_sum_u64(fq);
+    if ((threadIdx.x & 31) == 0) {
+      if (kp) atomicAdd(&stat[0], kp);
+      if (kq) atomicAdd(&stat[1], kq);
+      if (fp) atomicAdd(&stat[2], fp);
+      if (fq) atomicAdd(&stat[3], fq);
+    }
   }
 }
 
@@ -1011,21 +1009,17 @@ cudaError_t k_build_caches(pfmbem* h) {
   cudaStream_t st = h->stream;
   Level& leaf = h->lev[h->D];
   cplx c2{h->c2re, h->c2im};
+  // same-fiber blocks and k tables first: the near-field build reads the k tables
   prof_begin(h, PH_BUILD);
-  ktab_build_kernel<<<(h->M * 32 + 255) / 256, 256, 0, st>>>(h->M, h->fib_off, h->kt_base, h->k, h->o_c, h->o_t,
-                                                             h->o_nu, h->o_h, h->kt_val, h->stat_dev);
+  fiber_build_kernel<<<dim3(h->nfb_rows, (h->max_fiber + 127) / 128), 128, 0, st>>>(
+      h->fb_rows, h->o_fiber, h->fib_off, h->fb_base, h->k, h->k1, h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu,
+      h->o_h, h->self4, h->kt_base, h->kt_val, h->fb_val, h->fb_valf, h->stat_dev);
   prof_end(h, PH_BUILD);
   prof_begin(h, PH_BUILD);
   near_build_kernel<<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
                                               h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c, h->s_t,
                                               h->s_nu, h->s_h, h->s_perm, h->o_fiber, h->fib_off, h->s_m0,
                                               h->kt_base, h->kt_val, h->nc_val, h->nc_valf, h->stat_dev);
-  prof_end(h, PH_BUILD);
-  prof_begin(h, PH_BUILD);
-  fiber_build_kernel<<<(h->E * 32 + 255) / 256, 256, 0, st>>>(h->E, h->o_fiber, h->fib_off, h->fb_base, h->k1,
-                                                              h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu, h->o_h,
-                                                              h->self4, h->fb_val, h->fb_valf, h->stat_dev,
-                                                              h->fb_circ);
   prof_end(h, PH_BUILD);
   return cudaGetLastError();
 }
@@ -1844,7 +1838,9 @@ cudaError_t k_field(pfmbem* h, const cplx* psi, int npts, const double2* pts, cp
 // k_n = sqrt(k^2 - kappa_n^2),
 //   u_n^+- = (i / (2 H k_n)) sum_e int_e [d/dnu_y e^{-i w.y} phi_e - i eta e^{-i w.y} varphi_e] ds,
 // where the element integral of e^{-i w.y} over c + s t is e^{-i w.c} h sinc(w.t h / 2).
-// Block b: order b / 2, side b % 2 (0: transmitted, 1: reflected).
+// Block (b, slice): order b / 2, side b % 2 (0: transmitted, 1: reflected); the
+// blocks of one (order, side) split the elements and add their partial sums
+// into out (zeroed by the caller).
 __global__ void coeff_kernel(int E, double k, double eta, double H, double ks, const int* __restrict__ orders,
                              const double2* __restrict__ oc, const double2* __restrict__ ot,
                              const double2* __restrict__ onu, const double* __restrict__ oh,
@@ -1854,7 +1850,7 @@ __global__ void coeff_kernel(int E, double k, double eta, double H, double ks, c
   const double kn = sqrt(fmax(k * k - kap * kap, 0.0));
   const double wx = side == 0 ? kn : -kn, wy = kap;
   cplx acc{0, 0};
-  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+  for (int e = blockIdx.y * blockDim.x + threadIdx.x; e < E; e += gridDim.y * blockDim.x) {
     const double2 c = oc[e], t = ot[e], nu = onu[e];
     const double hh = oh[e];
     const double a = 0.5 * hh * (wx * t.x + wy * t.y);
@@ -1875,7 +1871,11 @@ __global__ void coeff_kernel(int E, double k, double eta, double H, double ks, c
   if (wid == 0) {
     acc = lane < (blockDim.x >> 5) ? red[lane] : cplx{0, 0};
     acc = warp_sum(acc);
-    if (lane == 0) out[blockIdx.x] = mul_i((1.0 / (2.0 * H * kn)) * acc);
+    if (lane == 0) {
+      const cplx v = mul_i((1.0 / (2.0 * H * kn)) * acc);
+      atomicAdd(&out[blockIdx.x].re, v.re);
+      atomicAdd(&out[blockIdx.x].im, v.im);
+    }
   }
 }
 
@@ -1927,9 +1927,13 @@ extern "C" pfmbem_status pfmbem_probe_peak(int dtype, double* tflops) {
 }
 
 cudaError_t k_coefficients(pfmbem* h, const cplx* psi, int norders, const int* orders_dev, cplx* out_dev) {
+  const int slices = std::min(64, (h->E + 255) / 256);
+  cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(cplx) * 2 * norders, h->stream);
+  if (e != cudaSuccess) return e;
   prof_begin(h, PH_OUT);
-  coeff_kernel<<<2 * norders, 256, 0, h->stream>>>(h->E, h->k, h->eta, h->H, h->k * sin(h->theta), orders_dev,
-                                                   h->o_c, h->o_t, h->o_nu, h->o_h, psi, out_dev);
+  coeff_kernel<<<dim3(2 * norders, slices), 256, 0, h->stream>>>(h->E, h->k, h->eta, h->H, h->k * sin(h->theta),
+                                                                 orders_dev, h->o_c, h->o_t, h->o_nu, h->o_h, psi,
+                                                                 out_dev);
   prof_end(h, PH_OUT);
   return cudaGetLastError();
 }
