@@ -25,7 +25,7 @@
 //
 // The barrier is a counter plus a generation word in device memory.  The
 // cooperative launch guarantees that every block is resident, so every wait
-// ends; each wait is nevertheless bounded (about one second), after which the
+// ends; each wait is nevertheless bounded (one second of %globaltimer), after which the
 // block records an error flag and returns, and the host reports
 // PFMBEM_ETIMEOUT instead of a result.
 #include <cstdio>
@@ -152,14 +152,16 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
       __threadfence();
       atomicAdd(bar + 1, 1u);                  // release the other blocks
     } else {
-      long long it = 0;
+      // spin on the generation word; give up after one second of device time
+      unsigned long long t0, t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
       while (*gen == g) {
-        if (++it > (1LL << 24)) {              // ~1 s with the sleeps below
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > 1000000000ull) {
           atomicExch(err, 1);
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();                           // other blocks' writes after the release
@@ -307,18 +309,31 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     const int P = a.P[l], Pc = a.P[l + 1];
     for (int i = wfirst; i < a.nne[l]; i += wstride) {
       const int box = a.ne[l][i];
-      for (int n0 = 0; n0 < P; n0 += 32) {
-        const int n = n0 + lane;
-        C acc{0, 0};
-        for (int q = 0; q < 4; ++q) {
-          const int ch = 4 * box + q;
-          if (a.bb[l + 1][ch] >= a.be[l + 1][ch]) continue;
-          __syncwarp();
-          for (int m = lane; m < Pc; m += 32) wsm[m] = ldcg(a.M[l + 1] + (size_t)ch * Pc + m);
-          __syncwarp();
-          if (n < P) acc += colmv(a.m2m[l] + (size_t)q * Pc * P + n, P, wsm, Pc);
+      if (4 * Pc <= PF_NCOEF) {
+        // all four children at once (an empty child contributes zeros): the
+        // quadrant operators are stored one after another, so one column walk
+        // over 4 Pc terms applies them all
+        __syncwarp();
+        for (int t = lane; t < 4 * Pc; t += 32) {
+          const int q = t / Pc, ch = 4 * box + q;
+          wsm[t] = a.bb[l + 1][ch] < a.be[l + 1][ch] ? ldcg(a.M[l + 1] + (size_t)ch * Pc + (t - q * Pc)) : C{0, 0};
         }
-        if (n < P) a.M[l][(size_t)box * P + n] = acc;
+        __syncwarp();
+        for (int n = lane; n < P; n += 32) a.M[l][(size_t)box * P + n] = colmv(a.m2m[l] + n, P, wsm, 4 * Pc);
+      } else {
+        for (int n0 = 0; n0 < P; n0 += 32) {
+          const int n = n0 + lane;
+          C acc{0, 0};
+          for (int q = 0; q < 4; ++q) {
+            const int ch = 4 * box + q;
+            if (a.bb[l + 1][ch] >= a.be[l + 1][ch]) continue;
+            __syncwarp();
+            for (int m = lane; m < Pc; m += 32) wsm[m] = ldcg(a.M[l + 1] + (size_t)ch * Pc + m);
+            __syncwarp();
+            if (n < P) acc += colmv(a.m2m[l] + (size_t)q * Pc * P + n, P, wsm, Pc);
+          }
+          if (n < P) a.M[l][(size_t)box * P + n] = acc;
+        }
       }
       if (l == 0) {
         // root: L(0) = R M(0), the images |m| >= 2 through the lattice sums
@@ -357,29 +372,41 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       if (stage)
         for (int t = threadIdx.x; t < P * P; t += FB) sT[(t % P) * (P + 1) + t / P] = To[t];
       __syncthreads();
-      for (int pi = pb + warp; pi < pe; pi += FW) {
-        const int src = a.pr_src[l][pi], tgt = a.pr_tgt[l][pi];
-        const C phs = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
-        __syncwarp();
-        for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * P + m);
-        __syncwarp();
-        for (int n = lane; n < P; n += 32) {
-          C r;
-          if (stage) {
-            const C* row = sT + (size_t)n * (P + 1);
-            C r0{0, 0}, r1{0, 0};
-            int m = 0;
-#pragma unroll 4
-            for (; m + 1 < P; m += 2) {
-              r0 += row[m] * wsm[m];
-              r1 += row[m + 1] * wsm[m + 1];
-            }
-            if (m < P) r0 += row[m] * wsm[m];
-            r = r0 + r1;
-          } else {
-            r = colmv(To + n, P, wsm, P);
+      if (stage) {
+        // two pairs per warp pass, sharing the operator rows read from shared memory
+        for (int pi = pb + 2 * warp; pi < pe; pi += 2 * FW) {
+          const bool two = pi + 1 < pe;
+          const int srcA = a.pr_src[l][pi], tgtA = a.pr_tgt[l][pi];
+          const int srcB = two ? a.pr_src[l][pi + 1] : srcA, tgtB = two ? a.pr_tgt[l][pi + 1] : tgtA;
+          const C phA = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
+          const C phB = two ? from_d<C>(phase_m(a.alpha, a.pr_img[l][pi + 1])) : C{0, 0};
+          __syncwarp();
+          for (int m = lane; m < P; m += 32) {
+            wsm[m] = phA * ldcg(a.M[l] + (size_t)srcA * P + m);
+            wsm[P + m] = phB * ldcg(a.M[l] + (size_t)srcB * P + m);
           }
-          atomic_add(a.L[l] + (size_t)tgt * P + n, r);
+          __syncwarp();
+          for (int n = lane; n < P; n += 32) {
+            const C* row = sT + (size_t)n * (P + 1);
+            C rA{0, 0}, rB{0, 0};
+#pragma unroll 4
+            for (int m = 0; m < P; ++m) {
+              const C t = row[m];
+              rA += t * wsm[m];
+              rB += t * wsm[P + m];
+            }
+            atomic_add(a.L[l] + (size_t)tgtA * P + n, rA);
+            if (two) atomic_add(a.L[l] + (size_t)tgtB * P + n, rB);
+          }
+        }
+      } else {
+        for (int pi = pb + warp; pi < pe; pi += FW) {
+          const int src = a.pr_src[l][pi], tgt = a.pr_tgt[l][pi];
+          const C phs = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
+          __syncwarp();
+          for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * P + m);
+          __syncwarp();
+          for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * P + n, colmv(To + n, P, wsm, P));
         }
       }
     }
