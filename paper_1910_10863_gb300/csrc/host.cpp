@@ -778,6 +778,16 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       bool ok = false;
       CK(k_fused_prepare(h, &ok));
       if (ok) {
+        std::vector<int> sli(E);
+        {
+          const Level& Lf = h->lev[D];
+          for (size_t li = 0; li < Lf.hne.size(); ++li)
+            for (int s2 = Lf.hbegin[Lf.hne[li]]; s2 < Lf.hend[Lf.hne[li]]; ++s2) sli[s2] = (int)li;
+        }
+        if ((st = upload(h, &h->s_li, sli)) != PFMBEM_OK) return st;
+        h->Un = dalloc<cplx>(h, (size_t)2 * E);
+        h->Unf = dalloc<cplxf>(h, (size_t)2 * E);
+        if (!h->Un || !h->Unf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near sums)");
         h->fz_bar = dalloc<unsigned>(h, 2);
         h->fz_err = dalloc<int>(h, 1);
         h->fz_stamp = dalloc<unsigned long long>(h, 32);

@@ -186,6 +186,9 @@ struct pfmbem {
   int fz_nchunk = 0;             // row chunks of the other fibers
   int* fz_chunk = nullptr;
   int* fz_err = nullptr;         // set when a bounded barrier wait gave up
+  int* s_li = nullptr;           // sorted element -> index of its leaf among the non-empty leaves
+  cplx* Un = nullptr;            // [E][2] near-field part of (U', dU'), FP64 and FP32
+  cplxf* Unf = nullptr;
   unsigned long long* fz_stamp = nullptr;   // [32] stage end times (diagnostic)
   cplx* root = nullptr;          // [P0][P0] periodic root translation
   cplxf* rootf = nullptr;

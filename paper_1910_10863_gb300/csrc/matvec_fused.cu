@@ -8,11 +8,13 @@
 //
 //   A   gather the densities into tree order (alpha^{-m0} phase), P2M,
 //       and clear the local expansions of levels 1..D                     (warp per leaf)
-//   B_l M2M into level l = D-1 .. 0; at the root also L(0) = R M(0)       (warp per box)
+//   B_l M2M into level l = D-1 .. 0; at the root also L(0) = R M(0)       (warp per box);
+//       the cached near-field sums of all elements are spread over the
+//       stages of the top three levels, whose few boxes leave most warps idle (warp per element)
 //   D_l L2L from the parent (warp per box) and M2L (block per chunk of
 //       pairs with one translation offset, T_o staged in shared memory),
 //       both added atomically into L(l), l = 1..D
-//   E   L2P + cached near field for every element of a leaf               (block per leaf)
+//   E   L2P plus the near-field sums                                       (warp per element)
 //   F   fiber blocks and the combination of eq. 9: a regular-polygon fiber
 //       whose element count is a power of two applies its block-circulant
 //       block by FFT (block per fiber), the others by cached rows (block per
@@ -37,7 +39,6 @@ namespace {
 
 constexpr int FB = 256;          // threads per block
 constexpr int FW = FB / 32;      // warps per block
-constexpr int FSTAGE = 1536;     // near-field source densities staged in shared memory per leaf
 constexpr int TSP = 45;          // largest order count P whose M2L operator is staged in shared memory
 constexpr int TSIZE = TSP * (TSP + 1);
 
@@ -51,6 +52,8 @@ struct FusedArgs {
   cplx* y;                       // output, original order, FP64
   C* dens;                       // sorted (phi', varphi')
   C* U;                          // sorted (U', dU')
+  C* Un;                         // sorted near-field part of (U', dU')
+  const int* s_li;               // sorted element -> index of its leaf among the non-empty leaves
   int nne[PF_MAXLEVEL + 1];
   int nbox[PF_MAXLEVEL + 1];
   int P[PF_MAXLEVEL + 1];
@@ -253,6 +256,42 @@ __global__ void fiber_symbol_kernel(const int* __restrict__ fib_list, const int*
   }
 }
 
+// Near-field sum of one target (sorted element s) from its leaf's cached
+// [targets][sources] 2x2 blocks; lanes over the sources, two independent
+// accumulator pairs.  Writes (U'_near, dU'_near) of s.
+template <class C>
+__device__ __forceinline__ void near_row(const FusedArgs<C>& a, int s, int lane) {
+  const int D = a.D, li = a.s_li[s];
+  const int t = s - a.bb[D][a.ne[D][li]];
+  const int j0 = a.nc_sbase[li], ns = a.nc_sbase[li + 1] - j0;
+  const C* row = a.nc_val + a.nc_base[li] + (int64_t)t * ns * 4;
+  const int* src = a.nc_src + j0;
+  C u0{0, 0}, d0{0, 0}, u1{0, 0}, d1{0, 0};
+  int j = lane;
+  for (; j + 32 < ns; j += 64) {
+    const int f0 = src[j], f1 = src[j + 32];
+    const C p0 = ldcg(a.dens + 2 * f0), v0 = ldcg(a.dens + 2 * f0 + 1);
+    const C p1 = ldcg(a.dens + 2 * f1), v1 = ldcg(a.dens + 2 * f1 + 1);
+    const C q0 = row[4 * j], q1 = row[4 * j + 1], q2 = row[4 * j + 2], q3 = row[4 * j + 3];
+    const C r0 = row[4 * j + 128], r1 = row[4 * j + 129], r2 = row[4 * j + 130], r3 = row[4 * j + 131];
+    u0 += q0 * p0 + q1 * v0;
+    d0 += q2 * p0 + q3 * v0;
+    u1 += r0 * p1 + r1 * v1;
+    d1 += r2 * p1 + r3 * v1;
+  }
+  for (; j < ns; j += 32) {
+    const int f = src[j];
+    const C p = ldcg(a.dens + 2 * f), v = ldcg(a.dens + 2 * f + 1);
+    u0 += row[4 * j] * p + row[4 * j + 1] * v;
+    d0 += row[4 * j + 2] * p + row[4 * j + 3] * v;
+  }
+  const C u = wsum(u0 + u1), du = wsum(d0 + d1);
+  if (lane == 0) {
+    a.Un[2 * s] = u;
+    a.Un[2 * s + 1] = du;
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   extern __shared__ unsigned char smraw[];
@@ -305,9 +344,21 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   stage_stamp(a.stamp, ks++);
 
   // ------------------------------------------------------------ B: M2M (+ root)
+  const int lnear = min(2, D - 1);                  // levels whose stage also takes near-field rows
   for (int l = D - 1; l >= 0; --l) {
     const int P = a.P[l], Pc = a.P[l + 1];
-    for (int i = wfirst; i < a.nne[l]; i += wstride) {
+    int r0 = 0, r1 = 0;
+    if (l <= lnear) {
+      const int j = lnear - l, nb = lnear + 1;
+      r0 = (int)((int64_t)a.E * j / nb);
+      r1 = (int)((int64_t)a.E * (j + 1) / nb);
+    }
+    const int nitem = a.nne[l] + (r1 - r0);
+    for (int i = wfirst; i < nitem; i += wstride) {
+      if (i >= a.nne[l]) {
+        near_row(a, r0 + (i - a.nne[l]), lane);
+        continue;
+      }
       const int box = a.ne[l][i];
       if (4 * Pc <= PF_NCOEF) {
         // all four children at once (an empty child contributes zeros): the
@@ -417,63 +468,21 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   // ------------------------------------------------------------ E: L2P + near field
   {
     const int PD = a.P[D];
-    C* sd = sm;                                  // [2 * FSTAGE] staged source densities
-    C* sL = sm + 2 * FSTAGE;                     // [PD] the leaf's local expansion
-    for (int li = blockIdx.x; li < a.nne[D]; li += gridDim.x) {
-      const int box = a.ne[D][li];
-      const int s0 = a.bb[D][box], nt = a.be[D][box] - s0;
-      const int j0 = a.nc_sbase[li], ns = a.nc_sbase[li + 1] - j0;
-      const bool staged = ns <= FSTAGE;
-      __syncthreads();                           // the previous leaf is done with the buffers
-      if (staged)
-        for (int j = threadIdx.x; j < ns; j += FB) {
-          const int f = a.nc_src[j0 + j];
-          sd[2 * j] = ldcg(a.dens + 2 * f);
-          sd[2 * j + 1] = ldcg(a.dens + 2 * f + 1);
-        }
-      for (int t = threadIdx.x; t < PD; t += FB) sL[t] = ldcg(a.L[D] + (size_t)box * PD + t);
-      __syncthreads();
-      for (int t = warp; t < nt; t += FW) {
-        const int s = s0 + t;
-        const C* row = a.nc_val + a.nc_base[li] + (int64_t)t * ns * 4;
-        C u0{0, 0}, d0{0, 0}, u1{0, 0}, d1{0, 0};
-        int j = lane;
-        for (; j + 32 < ns; j += 64) {
-          C p0, v0, p1, v1;
-          if (staged) {
-            p0 = sd[2 * j]; v0 = sd[2 * j + 1]; p1 = sd[2 * j + 64]; v1 = sd[2 * j + 65];
-          } else {
-            const int f0 = a.nc_src[j0 + j], f1 = a.nc_src[j0 + j + 32];
-            p0 = ldcg(a.dens + 2 * f0); v0 = ldcg(a.dens + 2 * f0 + 1);
-            p1 = ldcg(a.dens + 2 * f1); v1 = ldcg(a.dens + 2 * f1 + 1);
-          }
-          const C q0 = row[4 * j], q1 = row[4 * j + 1], q2 = row[4 * j + 2], q3 = row[4 * j + 3];
-          const C r0 = row[4 * j + 128], r1 = row[4 * j + 129], r2 = row[4 * j + 130], r3 = row[4 * j + 131];
-          u0 += q0 * p0 + q1 * v0;
-          d0 += q2 * p0 + q3 * v0;
-          u1 += r0 * p1 + r1 * v1;
-          d1 += r2 * p1 + r3 * v1;
-        }
-        for (; j < ns; j += 32) {
-          C p, v;
-          if (staged) { p = sd[2 * j]; v = sd[2 * j + 1]; }
-          else { const int f = a.nc_src[j0 + j]; p = ldcg(a.dens + 2 * f); v = ldcg(a.dens + 2 * f + 1); }
-          u0 += row[4 * j] * p + row[4 * j + 1] * v;
-          d0 += row[4 * j + 2] * p + row[4 * j + 3] * v;
-        }
-        // far field of the leaf's local expansion
-        const C* cs = a.l2p + (size_t)s * 2 * PD;
-        C uf{0, 0}, df{0, 0};
-        for (int t2 = lane; t2 < PD; t2 += 32) {
-          uf += cs[t2] * sL[t2];
-          df += cs[PD + t2] * sL[t2];
-        }
-        const C u = wsum(uf + (u0 + u1));
-        const C du = wsum(df + (d0 + d1));
-        if (lane == 0) {
-          a.U[2 * s] = u;
-          a.U[2 * s + 1] = du;
-        }
+    for (int s = wfirst; s < a.E; s += wstride) {
+      const int box = a.ne[D][a.s_li[s]];
+      const C* Lb = a.L[D] + (size_t)box * PD;
+      const C* cs = a.l2p + (size_t)s * 2 * PD;
+      C uf{0, 0}, df{0, 0};
+      for (int t = lane; t < PD; t += 32) {
+        const C Lt = ldcg(Lb + t);
+        uf += cs[t] * Lt;
+        df += cs[PD + t] * Lt;
+      }
+      uf = wsum(uf);
+      df = wsum(df);
+      if (lane == 0) {
+        a.U[2 * s] = uf + ldcg(a.Un + 2 * s);
+        a.U[2 * s + 1] = df + ldcg(a.Un + 2 * s + 1);
       }
     }
   }
@@ -567,9 +576,8 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
 template <class C>
 size_t fused_smem(int maxfiber) {
   const size_t a = (size_t)TSIZE + (size_t)FW * PF_NCOEF;   // stages A, B, D
-  const size_t e = 2 * (size_t)FSTAGE + PF_NCOEF;           // stage E
   const size_t f = 2 * (size_t)maxfiber;                    // stage F
-  return sizeof(C) * std::max(a, std::max(e, f));
+  return sizeof(C) * std::max(a, f);
 }
 
 template <class C>
@@ -603,10 +611,13 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
       a.m2m[l] = L.m2m; a.l2l[l] = L.l2l; a.m2lt[l] = L.m2lt; a.M[l] = L.M; a.L[l] = L.L;
     }
   }
+  a.s_li = h->s_li;
   if constexpr (sizeof(C) == sizeof(cplxf)) {
+    a.Un = h->Unf;
     a.dens = h->densf; a.U = h->Uf; a.root = h->rootf; a.p2m = h->p2m_cf; a.l2p = h->l2p_cf;
     a.nc_val = h->nc_valf; a.fb_val = h->fb_valf; a.fh_val = h->fh_valf; a.tw = h->twf;
   } else {
+    a.Un = h->Un;
     a.dens = h->dens; a.U = h->U; a.root = h->root; a.p2m = h->p2m_c; a.l2p = h->l2p_c;
     a.nc_val = h->nc_val; a.fb_val = h->fb_val; a.fh_val = h->fh_val; a.tw = h->tw;
   }
