@@ -9,8 +9,8 @@
 //   A   gather the densities into tree order (alpha^{-m0} phase), P2M,
 //       and clear the local expansions of levels 1..D                     (warp per leaf)
 //   B_l M2M into level l = D-1 .. 0; at the root also L(0) = R M(0)       (warp per box);
-//       the cached near-field sums of all elements are spread over the
-//       stages of the top three levels, whose few boxes leave most warps idle (warp per element)
+//       the cached near-field sums of all elements are spread evenly over
+//       these stages, whose few boxes leave most warps idle  (warp per element)
 //   D_l L2L from the parent (warp per box) and M2L (block per chunk of
 //       pairs with one translation offset, T_o staged in shared memory),
 //       both added atomically into L(l), l = 1..D
@@ -344,7 +344,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   stage_stamp(a.stamp, ks++);
 
   // ------------------------------------------------------------ B: M2M (+ root)
-  const int lnear = min(2, D - 1);                  // levels whose stage also takes near-field rows
+  const int lnear = D - 1;                          // levels whose stage also takes near-field rows
   for (int l = D - 1; l >= 0; --l) {
     const int P = a.P[l], Pc = a.P[l + 1];
     int r0 = 0, r1 = 0;
