@@ -252,15 +252,17 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // ---------------------------------------------------- depth
   const int leaf_max = h->opt.leaf_max > 0 ? h->opt.leaf_max : 64;
   int D = h->opt.depth;
-  auto leaf_of = [&](int e, int Dd) {
-    int n = 1 << Dd;
-    double d = H / n;
-    int ix = (int)std::floor((cw[e].x - h->x0) / d);
-    int iy = (int)std::floor((cw[e].y - h->y0) / d);
-    ix = std::min(std::max(ix, 0), n - 1);
-    iy = std::min(std::max(iy, 0), n - 1);
-    return morton(ix, iy, Dd);
-  };
+  // box coordinates of every midpoint at the finest admissible depth (10); the
+  // box at depth D is the same pair shifted right by 10 - D bits
+  std::vector<int> cx10(E), cy10(E);
+  {
+    const double d10 = H / 1024.0;
+    for (int e = 0; e < E; ++e) {
+      cx10[e] = std::min(std::max((int)std::floor((cw[e].x - h->x0) / d10), 0), 1023);
+      cy10[e] = std::min(std::max((int)std::floor((cw[e].y - h->y0) / d10), 0), 1023);
+    }
+  }
+  auto leaf_of = [&](int e, int Dd) { return morton(cx10[e] >> (10 - Dd), cy10[e] >> (10 - Dd), Dd); };
   if (D <= 0) {
     for (D = 2; D < 10; ++D) {
       std::vector<int> cnt(1 << (2 * D), 0);
@@ -271,11 +273,15 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   }
   if (D < 2 || D > 10) return fail(h, PFMBEM_EINVAL, "depth must be in [2, 10]");
   h->D = D;
-  // ---------------------------------------------------- sort by leaf Morton key
+  // ---------------------------------------------------- sort by leaf Morton key (stable counting sort)
   std::vector<int> key(E), perm(E), pos(E);
   for (int e = 0; e < E; ++e) key[e] = leaf_of(e, D);
-  for (int e = 0; e < E; ++e) perm[e] = e;
-  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return key[a] < key[b]; });
+  {
+    std::vector<int> start(((size_t)1 << (2 * D)) + 1, 0);
+    for (int e = 0; e < E; ++e) start[key[e] + 1]++;
+    for (size_t b = 1; b < start.size(); ++b) start[b] += start[b - 1];
+    for (int e = 0; e < E; ++e) perm[start[key[e]]++] = e;
+  }
   for (int s = 0; s < E; ++s) pos[perm[s]] = s;
   // ---------------------------------------------------- levels
   const double eta = h->eta;
@@ -462,25 +468,12 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     Level& R = h->lev[0];
     const int p0 = R.p, P0 = R.P, jmax = 2 * p0;
     cplx* Sd = dalloc<cplx>(h, jmax + 1);
-    if (!Sd) return fail(h, PFMBEM_ENOMEM, "device allocation failed (lattice sums)");
+    h->root = dalloc<cplx>(h, (size_t)P0 * P0);
+    h->rootf = dalloc<cplxf>(h, (size_t)P0 * P0);
+    if (!Sd || !h->root || !h->rootf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (lattice sums)");
     CK(k_lattice_sums(h, jmax, h->lattice_q, Sd));
-    h->lattice_S.resize(jmax + 1);
-    CK(cudaMemcpyAsync(h->lattice_S.data(), Sd, sizeof(cplx) * (jmax + 1), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaEventRecord(h->side_ev, h->stream));   // waits for the sums only, not for later work
-    CK(cudaEventSynchronize(h->side_ev));
-    std::vector<cplx> Rt((size_t)P0 * P0);
-    for (int a = -p0; a <= p0; ++a)
-      for (int n = -p0; n <= p0; ++n) {
-        cplx s = h->lattice_S[std::abs(n - a)];
-        double sc = R.w[a + p0] * R.w[n + p0];
-        cplx v{sc * s.re, sc * s.im};
-        if (!std::isfinite(v.re) || !std::isfinite(v.im))
-          return fail(h, PFMBEM_ENUMERIC, "non-finite lattice sums");
-        Rt[(size_t)(a + p0) * P0 + (n + p0)] = v;
-      }
-    pfmbem_status st;
-    if ((st = upload(h, &h->root, Rt)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->rootf, to_float(Rt))) != PFMBEM_OK) return st;
+    // root translation R[a][n] = w_a S_{|n-a|} w_n, built on the device
+    CK(k_root_operator(h, p0, R.w_dev, Sd));
   }
   mark("lattice sums, root");
   // the second stream starts after everything uploaded so far (level weights)
@@ -640,7 +633,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         }
       }
       // tensor-core tiles: 128 consecutive non-empty target boxes
-      {
+      if (h->opt.m2l_mode == 2) {
         const int nt = ((int)L.hne.size() + 127) / 128;
         std::vector<int> tbox((size_t)nt * 128, -1), tnoff(nt, 0), toffs((size_t)nt * 49, 0);
         std::vector<int> tsrc((size_t)nt * 49 * 128, -1), timg((size_t)nt * 49 * 128, 0);
@@ -682,41 +675,59 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   h->info.m2l_pairs = m2l_pairs;
   mark("M2L lists (overlapped)");
   // ---------------------------------------------------- translation tables
-  for (int l = 0; l <= D; ++l) {
-    Level& L = h->lev[l];
-    const int P = L.P;
-    L.M = dalloc<cplx>(h, (size_t)L.nbox * P);
-    L.L = dalloc<cplx>(h, (size_t)L.nbox * P);
-    L.Mf = dalloc<cplxf>(h, (size_t)L.nbox * P);
-    L.Lf = dalloc<cplxf>(h, (size_t)L.nbox * P);
-    if (!L.Mf || !L.Lf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions)");
-    if (!L.M || !L.L) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions)");
-    // M2L operators at this level, T[o][l][n] = w_l H^+_{n-l}(k (dx, dy) d) w_n, and
-    // the M2M / L2L operators to the children, built on the device
-    if (l >= 1) {
-      const size_t n = (size_t)49 * P * P;
-      L.m2l = dalloc<cplx>(h, n);
-      L.m2lf = dalloc<cplxf>(h, n);
-      L.m2lt = dalloc<cplx>(h, n);
-      L.m2ltf = dalloc<cplxf>(h, n);
-      if (!L.m2l || !L.m2lf || !L.m2lt || !L.m2ltf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (M2L)");
-      if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2) {
-        const int kp = tc_kpad(P);
-        L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
-        if (!L.tc_B) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
-      } else {
-        L.tc_ntile = 0;
+  // One FP64 and one FP32 arena hold every level's expansions and operators
+  // (sub-arrays aligned to 256 bytes); the operators are built on the device.
+  {
+    auto up16 = [](size_t n) { return (n + 15) & ~(size_t)15; };
+    size_t n64 = 0, n32 = 0;
+    for (int l = 0; l <= D; ++l) {
+      const Level& L = h->lev[l];
+      const size_t ex = up16((size_t)L.nbox * L.P);
+      const size_t tm = l >= 1 ? up16((size_t)49 * L.P * L.P) : 0;
+      const size_t mm = l < D ? up16((size_t)4 * L.P * h->lev[l + 1].P) : 0;
+      n64 += 2 * ex + 2 * tm + 2 * mm;
+      n32 += 2 * up16(ex) + 2 * up16(tm) + 2 * up16(mm);
+    }
+    cplx* a64 = dalloc<cplx>(h, n64);
+    cplxf* a32 = dalloc<cplxf>(h, n32);
+    if (!a64 || !a32) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions, tables)");
+    TableLevels tl{};
+    for (int l = 0; l <= D; ++l) {
+      Level& L = h->lev[l];
+      const int P = L.P;
+      const size_t ex = up16((size_t)L.nbox * P);
+      L.M = a64; a64 += ex;
+      L.L = a64; a64 += ex;
+      L.Mf = a32; a32 += ex;
+      L.Lf = a32; a32 += ex;
+      tl.p[l] = L.p;
+      tl.d[l] = L.d;
+      tl.w[l] = L.w_dev;
+      if (l >= 1) {
+        const size_t tm = up16((size_t)49 * P * P);
+        L.m2l = a64; a64 += tm;
+        L.m2lt = a64; a64 += tm;
+        L.m2lf = a32; a32 += tm;
+        L.m2ltf = a32; a32 += tm;
+        tl.T[l] = L.m2l; tl.Tt[l] = L.m2lt; tl.Tf[l] = L.m2lf; tl.Ttf[l] = L.m2ltf;
+        if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2) {
+          const int kp = tc_kpad(P);
+          L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
+          if (!L.tc_B) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
+        } else {
+          L.tc_ntile = 0;
+        }
+      }
+      if (l < D) {
+        const size_t mm = up16((size_t)4 * P * h->lev[l + 1].P);
+        L.m2m = a64; a64 += mm;
+        L.l2l = a64; a64 += mm;
+        L.m2mf = a32; a32 += mm;
+        L.l2lf = a32; a32 += mm;
+        tl.A[l] = L.m2m; tl.B[l] = L.l2l; tl.Af[l] = L.m2mf; tl.Bf[l] = L.l2lf;
       }
     }
-    if (l < D) {
-      const size_t n = (size_t)4 * P * h->lev[l + 1].P;
-      L.m2m = dalloc<cplx>(h, n);
-      L.m2mf = dalloc<cplxf>(h, n);
-      L.l2l = dalloc<cplx>(h, n);
-      L.l2lf = dalloc<cplxf>(h, n);
-      if (!L.m2m || !L.m2mf || !L.l2l || !L.l2lf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (M2M)");
-    }
-    CK(k_level_tables(h, l, h->astream ? h->astream : h->stream));
+    CK(k_tables(h, tl, h->astream ? h->astream : h->stream));
   }
   mark("translation tables (overlapped)");
   // join: later work on the main stream sees every upload of the second stream

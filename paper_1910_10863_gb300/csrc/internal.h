@@ -192,7 +192,6 @@ struct pfmbem {
   unsigned long long* fz_stamp = nullptr;   // [32] stage end times (diagnostic)
   cplx* root = nullptr;          // [P0][P0] periodic root translation
   cplxf* rootf = nullptr;
-  std::vector<cplx> lattice_S;   // S_j, j = 0..2 p0 (S_-j = S_j)
   // matvec work
   cplx* dens = nullptr;          // sorted [E][2] = (phi', varphi')
   cplx* U = nullptr;             // sorted [E][2] = (U', dU')
@@ -233,7 +232,22 @@ cudaError_t k_coefficients(pfmbem* h, const cplx* psi, int norders, const int* o
 void k_upload_gauss(const double* x, const double* w, const double* thr64, const double* thr32);
 void k_upload_series();
 cudaError_t k_self_terms(pfmbem* h);
-cudaError_t k_level_tables(pfmbem* h, int l, cudaStream_t st);
+// translation tables of all levels (kernels.cu)
+struct TableLevels {
+  int p[PF_MAXLEVEL + 1];
+  double d[PF_MAXLEVEL + 1];
+  const double* w[PF_MAXLEVEL + 1];
+  cplx* T[PF_MAXLEVEL + 1];
+  cplxf* Tf[PF_MAXLEVEL + 1];
+  cplx* Tt[PF_MAXLEVEL + 1];
+  cplxf* Ttf[PF_MAXLEVEL + 1];
+  cplx* A[PF_MAXLEVEL + 1];
+  cplxf* Af[PF_MAXLEVEL + 1];
+  cplx* B[PF_MAXLEVEL + 1];
+  cplxf* Bf[PF_MAXLEVEL + 1];
+};
+cudaError_t k_tables(pfmbem* h, const TableLevels& tl, cudaStream_t st);
+cudaError_t k_root_operator(pfmbem* h, int p0, const double* w0, const cplx* S);
 cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev);
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_rhs(pfmbem* h, cplx* B);

@@ -128,19 +128,29 @@ __device__ void bessel_jy_block(double x, int N, double* J, double* Y) {
   __syncthreads();
 }
 
-// M2L operators of one level (Sec. 3.2): T[o][a][n] = w_a H^+_{n-a}(k v_o) w_n,
+// M2L operators of level l = blockIdx.y + 1 (Sec. 3.2): T[o][a][n] = w_a H^+_{n-a}(k v_o) w_n,
 // H^+_j = H_j(k|v|) e^{i j theta_v}, H_{-j} = (-1)^j H_j, for the offsets
-// v_o = (dx, dy) d, o = (dx + 3) 7 + (dy + 3), max(|dx|, |dy|) >= 2 (the others
-// stay zero).  Also the transposed copy [o][n][a] and FP32 copies.
-__global__ void m2l_table_kernel(int p, double d, double k, const double* __restrict__ w, cplx* __restrict__ T,
-                                 cplxf* __restrict__ Tf, cplx* __restrict__ Tt, cplxf* __restrict__ Ttf,
-                                 int* __restrict__ bad) {
-  const int o = blockIdx.x, dx = o / 7 - 3, dy = o % 7 - 3;
-  if (abs(dx) <= 1 && abs(dy) <= 1) return;
+// v_o = (dx, dy) d, o = (dx + 3) 7 + (dy + 3) = blockIdx.x; offsets with
+// max(|dx|, |dy|) <= 1 are never used and are written as zeros.  Also the
+// transposed copy [o][n][a] and FP32 copies.
+__global__ void m2l_tables_kernel(TableLevels tl, double k, int* __restrict__ bad) {
+  const int l = blockIdx.y + 1, o = blockIdx.x, dx = o / 7 - 3, dy = o % 7 - 3;
+  const int p = tl.p[l], P = 2 * p + 1;
+  const double* w = tl.w[l];
+  cplx* T = tl.T[l] + (size_t)o * P * P;
+  cplxf* Tf = tl.Tf[l] + (size_t)o * P * P;
+  cplx* Tt = tl.Tt[l] + (size_t)o * P * P;
+  cplxf* Ttf = tl.Ttf[l] + (size_t)o * P * P;
+  if (abs(dx) <= 1 && abs(dy) <= 1) {
+    for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+      T[t] = Tt[t] = cplx{0, 0};
+      Tf[t] = Ttf[t] = cplxf{0, 0};
+    }
+    return;
+  }
   __shared__ double J[4 * PF_PMAX + 2], Y[4 * PF_PMAX + 2];
   __shared__ cplx hv[4 * PF_PMAX + 1];
-  const int P = 2 * p + 1;
-  const double vx = dx * d, vy = dy * d;
+  const double vx = dx * tl.d[l], vy = dy * tl.d[l];
   const double r = sqrt(vx * vx + vy * vy), th = atan2(vy, vx);
   bessel_jy_block(k * r, 2 * p, J, Y);
   for (int j = threadIdx.x - 2 * p; j <= 2 * p; j += blockDim.x) {
@@ -158,28 +168,32 @@ __global__ void m2l_table_kernel(int p, double d, double k, const double* __rest
     const double sc = w[a] * w[n];
     const cplx v{sc * hj.re, sc * hj.im};
     if (!isfinite(v.re) || !isfinite(v.im)) atomicExch(bad, 1);
-    const size_t i1 = ((size_t)o * P + a) * P + n, i2 = ((size_t)o * P + n) * P + a;
-    T[i1] = v;
-    Tf[i1] = to_f(v);
-    Tt[i2] = v;
-    Ttf[i2] = to_f(v);
+    T[t] = v;
+    Tf[t] = to_f(v);
+    Tt[(size_t)n * P + a] = v;
+    Ttf[(size_t)n * P + a] = to_f(v);
   }
 }
 
-// M2M (children of level l+1 -> level l) and L2L (level l -> children) for the
-// child quadrant q (blockIdx.x), v = O_child - O_parent:
+// M2M (children of level l+1 -> level l) and L2L (level l -> children), l =
+// blockIdx.y, for the child quadrant q = blockIdx.x, v = O_child - O_parent:
 //   A[q][m][n] = J^-_{n-m}(k v) w^c_m / w^p_n,  J^-_j = J_j e^{-i j theta}
 //   B[q][m][n] = w^c_n J^+_{m-n}(k v) / w^p_m,  J^+_j = J_j e^{+i j theta}
 // (m child and n parent coefficient in A, m parent and n child in B).
-__global__ void m2m_table_kernel(int p, int pc, double dc, double k, const double* __restrict__ wp,
-                                 const double* __restrict__ wc, cplx* __restrict__ A, cplxf* __restrict__ Af,
-                                 cplx* __restrict__ B, cplxf* __restrict__ Bf) {
-  const int q = blockIdx.x, cx = q & 1, cy = (q >> 1) & 1;
+__global__ void m2m_tables_kernel(TableLevels tl, double k) {
+  const int l = blockIdx.y, q = blockIdx.x, cx = q & 1, cy = (q >> 1) & 1;
+  const int p = tl.p[l], pc = tl.p[l + 1], P = 2 * p + 1, Pc = 2 * pc + 1;
+  const double* wp = tl.w[l];
+  const double* wc = tl.w[l + 1];
   __shared__ double J[2 * PF_PMAX + 2], Y[2 * PF_PMAX + 2];
-  const int P = 2 * p + 1, Pc = 2 * pc + 1;
+  const double dc = tl.d[l + 1];
   const double vx = (cx - 0.5) * dc, vy = (cy - 0.5) * dc;
   const double r = sqrt(vx * vx + vy * vy), th = atan2(vy, vx);
   bessel_jy_block(k * r, p + pc, J, Y);
+  cplx* A = tl.A[l] + (size_t)q * Pc * P;
+  cplxf* Af = tl.Af[l] + (size_t)q * Pc * P;
+  cplx* B = tl.B[l] + (size_t)q * P * Pc;
+  cplxf* Bf = tl.Bf[l] + (size_t)q * P * Pc;
   for (int t = threadIdx.x; t < P * Pc; t += blockDim.x) {
     {
       const int m = t / P - pc, n = t % P - p;       // A: [q][m + pc][n + p]
@@ -189,8 +203,8 @@ __global__ void m2m_table_kernel(int p, int pc, double dc, double k, const doubl
       double sn, cs;
       sincos(j * th, &sn, &cs);
       const cplx v{sc * Jj * cs, -sc * Jj * sn};
-      A[(size_t)q * Pc * P + t] = v;
-      Af[(size_t)q * Pc * P + t] = to_f(v);
+      A[t] = v;
+      Af[t] = to_f(v);
     }
     {
       const int m = t / Pc - p, n = t % Pc - pc;     // B: [q][m + p][n + pc]
@@ -200,27 +214,40 @@ __global__ void m2m_table_kernel(int p, int pc, double dc, double k, const doubl
       double sn, cs;
       sincos(j * th, &sn, &cs);
       const cplx v{sc * Jj * cs, sc * Jj * sn};
-      B[(size_t)q * P * Pc + t] = v;
-      Bf[(size_t)q * P * Pc + t] = to_f(v);
+      B[t] = v;
+      Bf[t] = to_f(v);
     }
   }
 }
 
-cudaError_t k_level_tables(pfmbem* h, int l, cudaStream_t st) {
-  Level& L = h->lev[l];
-  if (l >= 1) {
-    const size_t n = (size_t)49 * L.P * L.P;
-    cudaError_t e = cudaMemsetAsync(L.m2l, 0, n * sizeof(cplx), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.m2lf, 0, n * sizeof(cplxf), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.m2lt, 0, n * sizeof(cplx), st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(L.m2ltf, 0, n * sizeof(cplxf), st);
-    if (e != cudaSuccess) return e;
-    m2l_table_kernel<<<49, 256, 0, st>>>(L.p, L.d, h->k, L.w_dev, L.m2l, L.m2lf, L.m2lt, L.m2ltf, h->tab_err);
+cudaError_t k_tables(pfmbem* h, const TableLevels& tl, cudaStream_t st) {
+  if (h->D >= 1) {
+    m2l_tables_kernel<<<dim3(49, h->D), 256, 0, st>>>(tl, h->k, h->tab_err);
+    m2m_tables_kernel<<<dim3(4, h->D), 256, 0, st>>>(tl, h->k);
   }
-  if (l < h->D) {
-    Level& C = h->lev[l + 1];
-    m2m_table_kernel<<<4, 256, 0, st>>>(L.p, C.p, C.d, h->k, L.w_dev, C.w_dev, L.m2m, L.m2mf, L.l2l, L.l2lf);
+  return cudaGetLastError();
+}
+
+// Periodic root translation (Sec. 3.3): R[a][n] = w_a S_{|n-a|} w_n, S_{-j} = S_j.
+__global__ void root_operator_kernel(int p0, const double* __restrict__ w, const cplx* __restrict__ S,
+                                     cplx* __restrict__ R, cplxf* __restrict__ Rf, int* __restrict__ bad) {
+  const int P = 2 * p0 + 1;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < P * P; t += gridDim.x * blockDim.x) {
+    const int a = t / P, n = t % P;
+    const cplx sj = S[abs(n - a)];
+    const double sc = w[a] * w[n];
+    const cplx v{sc * sj.re, sc * sj.im};
+    if (!isfinite(v.re) || !isfinite(v.im)) atomicExch(bad, 1);
+    R[t] = v;
+    Rf[t] = to_f(v);
   }
+}
+
+cudaError_t k_root_operator(pfmbem* h, int p0, const double* w0, const cplx* S) {
+  const int P = 2 * p0 + 1;
+  prof_begin(h, PH_SETUP);
+  root_operator_kernel<<<(P * P + 255) / 256, 256, 0, h->stream>>>(p0, w0, S, h->root, h->rootf, h->tab_err);
+  prof_end(h, PH_SETUP);
   return cudaGetLastError();
 }
 
