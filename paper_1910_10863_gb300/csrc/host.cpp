@@ -57,13 +57,39 @@ T* dalloc(pfmbem* h, size_t n) {
   return static_cast<T*>(p);
 }
 
+// Host-to-device copy of a table.  While a batch is open (h->ub_on) the data is
+// appended to one host buffer and the destination pointer is set at the next
+// flush_uploads, which makes one allocation and one copy for the whole batch.
 template <class T>
 pfmbem_status upload(pfmbem* h, T** dst, const std::vector<T>& src) {
+  if (h->ub_on) {
+    const size_t off = (h->ub_buf.size() + 255) & ~(size_t)255;
+    h->ub_buf.resize(off + src.size() * sizeof(T));
+    if (!src.empty()) std::memcpy(h->ub_buf.data() + off, src.data(), src.size() * sizeof(T));
+    h->ub_fix.push_back({reinterpret_cast<void**>(dst), off});
+    *dst = nullptr;
+    return PFMBEM_OK;
+  }
   *dst = dalloc<T>(h, src.size());
   if (!*dst) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
   if (!src.empty())
     CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice,
                        h->astream ? h->astream : h->stream));
+  return PFMBEM_OK;
+}
+
+// Copies the open batch to the device and sets its destination pointers; the
+// batch stays open.
+pfmbem_status flush_uploads(pfmbem* h) {
+  if (h->ub_fix.empty()) return PFMBEM_OK;
+  unsigned char* d = dalloc<unsigned char>(h, std::max<size_t>(h->ub_buf.size(), 1));
+  if (!d) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
+  if (!h->ub_buf.empty())
+    CK(cudaMemcpyAsync(d, h->ub_buf.data(), h->ub_buf.size(), cudaMemcpyHostToDevice,
+                       h->astream ? h->astream : h->stream));
+  for (auto& f : h->ub_fix) *f.first = d + f.second;
+  h->ub_buf.clear();
+  h->ub_fix.clear();
   return PFMBEM_OK;
 }
 
@@ -249,6 +275,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     tmark = t;
   };
   mark("elements");
+  h->ub_on = true;                 // tables below go up in a few batched copies
   // ---------------------------------------------------- depth
   const int leaf_max = h->opt.leaf_max > 0 ? h->opt.leaf_max : 64;
   int D = h->opt.depth;
@@ -457,6 +484,10 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   h->dev_rhs = dalloc<cplx>(h, (size_t)2 * E);
   if (!h->self4 || !h->dens || !h->U || !h->stage_in || !h->stage_out || !h->dev_rhs)
     return fail(h, PFMBEM_ENOMEM, "device allocation failed (work buffers)");
+  {
+    pfmbem_status st;
+    if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
+  }
   h->tab_err = dalloc<int>(h, 1);
   if (!h->tab_err) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
   CK(cudaMemsetAsync(h->tab_err, 0, sizeof(int), h->stream));
@@ -562,6 +593,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if (!h->nc_val || !h->nc_valf || !h->fb_val || !h->fb_valf || !h->stat_dev)
         return fail(h, PFMBEM_ENOMEM, "device allocation failed (near-field caches)");
       CK(cudaMemsetAsync(h->stat_dev, 0, 4 * sizeof(unsigned long long), h->stream));
+      if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
       mark("cache allocation");
       CK(k_build_caches(h));
       cache = true;
@@ -729,6 +761,10 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
     CK(k_tables(h, tl, h->astream ? h->astream : h->stream));
   }
+  {
+    pfmbem_status st;
+    if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
+  }
   mark("translation tables (overlapped)");
   // join: later work on the main stream sees every upload of the second stream
   CK(cudaEventRecord(h->side_ev, h->side));
@@ -782,6 +818,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       for (int j = 0; j < 512; ++j) twh[j] = cplx{std::cos(2.0 * M_PI * j / 1024.0), std::sin(2.0 * M_PI * j / 1024.0)};
       if ((st = upload(h, &h->tw, twh)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->twf, to_float(twh))) != PFMBEM_OK) return st;
+      if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
       h->fh_val = dalloc<cplx>(h, (size_t)4 * fa);
       h->fh_valf = dalloc<cplxf>(h, (size_t)4 * fa);
       if (!h->fh_val || !h->fh_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber symbols)");
@@ -811,6 +848,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
   }
   mark("near + fiber integrals, P2M/L2P caches");
+  {
+    pfmbem_status st;
+    if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
+  }
+  h->ub_on = false;
   CK(cudaStreamSynchronize(h->stream));
   {
     int bad = 0;

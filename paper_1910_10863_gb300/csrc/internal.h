@@ -201,6 +201,10 @@ struct pfmbem {
   GmresWork gw;
   Prof prof;
   std::vector<void*> allocs;
+  // batched table uploads during set-up (host.cpp upload / flush_uploads)
+  bool ub_on = false;
+  std::vector<unsigned char> ub_buf;
+  std::vector<std::pair<void**, size_t>> ub_fix;
   double setup_ms = 0;
 };
 
