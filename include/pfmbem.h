@@ -174,6 +174,19 @@ pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* p
  * densities psi: pts [npts][2] float64, u complex [npts]. */
 pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double* pts, double* u);
 
+/* Scattered field u^s (eq. 7) and its derivative du^s/dx1 at npts points
+ * outside the fibers (either output may be NULL, not both): pts [npts][2]
+ * float64, u and dudx1 complex [npts].  Points must lie within 0.7 H of the
+ * block centre along x (PFMBEM_EINVAL otherwise). */
+pfmbem_status pfmbem_field_dx1(pfmbem_t h, const double* psi, int npts, const double* pts, double* u,
+                               double* dudx1);
+
+/* Energy transmission coefficient of Sec. 4 on the line x1 (normally the
+ * block's right edge): ETC = (1/(kH)) int_0^H |du/dx1(x1, x2)| dx2 of the total
+ * field u = u_inc + u^s, by the midpoint rule with npts points over one period
+ * (the modulus is periodic along x2).  The modulus is not squared, as printed. */
+pfmbem_status pfmbem_etc(pfmbem_t h, const double* psi, double x1, int npts, double* etc);
+
 /* Bragg-order coefficients from the densities psi: for orders n with
  * |k sin(theta) + 2 pi n / H| < k, R_n (reflected, left of the block) and
  * T_n (transmitted, right; includes the incident wave for n = 0), plus the

@@ -381,11 +381,12 @@ def energy(pb: Problem, orders, R, T):
     return tot
 
 
-def etc(pb: Problem, psi, nmax=20, npts=512):
+def etc(pb: Problem, psi, nmax=20, npts=512, x1=None):
     """Energy transmission coefficient (Sec. 4): (1/kH) int_0^H |du/dx1(L, x2)| dx2 with
-    L the right edge of the block, from the Rayleigh expansion to the right."""
+    L the right edge of the block (x1, default the right-most node), from the
+    Rayleigh expansion to the right."""
     el = pb.el
-    L = float(np.max(np.concatenate([el.a[:, 0], el.b[:, 0]])))
+    L = float(np.max(np.concatenate([el.a[:, 0], el.b[:, 0]]))) if x1 is None else float(x1)
     orders = np.arange(-nmax, nmax + 1)
     ordr, _, T = rayleigh(pb, psi, orders)
     x2 = pb.H * (np.arange(npts) + 0.5) / npts

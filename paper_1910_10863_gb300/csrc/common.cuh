@@ -54,7 +54,7 @@ template <> PF_HD cplx from_d<cplx>(cplx a) { return a; }
 template <> PF_HD cplxf from_d<cplxf>(cplx a) { return to_f(a); }
 
 // ---------------------------------------------------------------- limits
-#define PF_PMAX 64                 // largest expansion order
+#define PF_PMAX 128                // largest expansion order
 #define PF_NCOEF (2 * PF_PMAX + 1)
 #define PF_GLMAX 16                // largest Gauss-Legendre rule in the ladder
 #define PF_MAXLEVEL 12

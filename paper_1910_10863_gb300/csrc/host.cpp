@@ -334,7 +334,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     int pmin = h->opt.p_min > 0 ? h->opt.p_min : 15;
     int p = h->opt.p > 0 ? h->opt.p : (int)std::ceil(x + 1.8 * std::pow(10.0, 2.0 / 3.0) * std::cbrt(x));
     p = std::max(p, h->opt.p > 0 ? 1 : pmin);
-    if (p > PF_PMAX) return fail(h, PFMBEM_EINVAL, "expansion order above the library limit (64); use more levels");
+    if (p > PF_PMAX) return fail(h, PFMBEM_EINVAL, "expansion order above the library limit (128); use more levels");
     L.p = p;
     L.P = 2 * p + 1;
     L.sigma = k * L.d / std::sqrt(2.0);
@@ -1507,9 +1507,10 @@ pfmbem_status pfmbem_self_terms(pfmbem_t h, double* out) {
   return PFMBEM_OK;
 }
 
-pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double* pts, double* u) {
-  if (!h || !psi || npts < 0 || (npts > 0 && (!pts || !u))) return PFMBEM_EINVAL;
-  if (npts == 0) return PFMBEM_OK;
+namespace {
+// Scattered field and/or its x1-derivative at host or device points (shared by
+// pfmbem_field, pfmbem_field_dx1 and pfmbem_etc).
+pfmbem_status field_points(pfmbem* h, const double* psi, int npts, const double* pts, double* u, double* du) {
   const size_t n = 2 * (size_t)h->E;
   // host copy of the points for the validity check
   std::vector<double> hp(2 * (size_t)npts);
@@ -1526,19 +1527,59 @@ pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double
   pfmbem_status st = stage_input(h, psi, n, h->stage_in, &psid);
   if (st != PFMBEM_OK) return st;
   double2* pd = dalloc<double2>(h, npts);
-  cplx* ud = dalloc<cplx>(h, npts);
+  cplx* ud = dalloc<cplx>(h, 2 * (size_t)npts);
   if (!pd || !ud) return fail(h, PFMBEM_ENOMEM, "field buffers");
   CK(cudaMemcpyAsync(pd, hp.data(), sizeof(double2) * npts, cudaMemcpyHostToDevice, h->stream));
   CK(k_field_prepare(h, psid));
-  CK(k_field(h, psid, npts, pd, ud));
-  CK(cudaMemcpyAsync(u, ud, sizeof(cplx) * npts, is_device_ptr(u) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                     h->stream));
+  CK(k_field(h, psid, npts, pd, u ? ud : nullptr, du ? ud + npts : nullptr));
+  if (u)
+    CK(cudaMemcpyAsync(u, ud, sizeof(cplx) * npts, is_device_ptr(u) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+  if (du)
+    CK(cudaMemcpyAsync(du, ud + npts, sizeof(cplx) * npts,
+                       is_device_ptr(du) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   // release the temporaries
   cudaFreeAsync(pd, h->stream);
   cudaFreeAsync(ud, h->stream);
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)pd), h->allocs.end());
   h->allocs.erase(std::remove(h->allocs.begin(), h->allocs.end(), (void*)ud), h->allocs.end());
+  return PFMBEM_OK;
+}
+}  // namespace
+
+pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double* pts, double* u) {
+  if (!h || !psi || npts < 0 || (npts > 0 && (!pts || !u))) return PFMBEM_EINVAL;
+  if (npts == 0) return PFMBEM_OK;
+  return field_points(h, psi, npts, pts, u, nullptr);
+}
+
+pfmbem_status pfmbem_field_dx1(pfmbem_t h, const double* psi, int npts, const double* pts, double* u, double* dudx1) {
+  if (!h || !psi || npts < 0 || (npts > 0 && (!pts || (!u && !dudx1)))) return PFMBEM_EINVAL;
+  if (npts == 0) return PFMBEM_OK;
+  return field_points(h, psi, npts, pts, u, dudx1);
+}
+
+pfmbem_status pfmbem_etc(pfmbem_t h, const double* psi, double x1, int npts, double* etc) {
+  if (!h || !psi || !etc || npts < 1 || !std::isfinite(x1)) return PFMBEM_EINVAL;
+  // midpoint rule over one period; |du/dx1| is periodic along x2
+  std::vector<double> pts(2 * (size_t)npts);
+  for (int i = 0; i < npts; ++i) {
+    pts[2 * i] = x1;
+    pts[2 * i + 1] = h->y0 + h->H * (i + 0.5) / npts;
+  }
+  std::vector<cplx> du(npts);
+  pfmbem_status st = field_points(h, psi, npts, pts.data(), nullptr, reinterpret_cast<double*>(du.data()));
+  if (st != PFMBEM_OK) return st;
+  const double c = std::cos(h->theta), s = std::sin(h->theta);
+  double sum = 0;
+  for (int i = 0; i < npts; ++i) {
+    // total field: the incident exp(i k d.x) adds i k cos(theta) exp(i k d.x)
+    const double ph = h->k * (c * pts[2 * i] + s * pts[2 * i + 1]);
+    const cplx inc{-h->k * c * std::sin(ph), h->k * c * std::cos(ph)};
+    sum += std::hypot(du[i].re + inc.re, du[i].im + inc.im);
+  }
+  *etc = sum * (h->H / npts) / (h->k * h->H);
   return PFMBEM_OK;
 }
 

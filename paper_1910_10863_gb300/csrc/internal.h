@@ -255,7 +255,7 @@ cudaError_t k_root_operator(pfmbem* h, int p0, const double* w0, const cplx* S);
 cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev);
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_rhs(pfmbem* h, cplx* B);
-cudaError_t k_field(pfmbem* h, const cplx* psi, int npts, const double2* pts, cplx* u);
+cudaError_t k_field(pfmbem* h, const cplx* psi, int npts, const double2* pts, cplx* u, cplx* dudx1);
 // BLAS-1 style helpers for GMRES (complex128, length n)
 cudaError_t k_multidot(pfmbem* h, const cplx* V, int ncol, const cplx* w, int n, cplx* out);
 cudaError_t k_gemv_sub(pfmbem* h, const cplx* V, int ncol, const cplx* coef, cplx* w, int n);

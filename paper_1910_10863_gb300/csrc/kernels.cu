@@ -1798,19 +1798,26 @@ cudaError_t k_sub(pfmbem* h, const cplx* a, const cplx* b, cplx* out, int n) {
 // of every element are integrated directly, and the images |m| >= 2 enter
 // through the root local expansion built from the lattice sums (Sec. 3.3).
 // One warp per point.
+// Scattered field u^s (eq. 7) and its x1-derivative at points outside the
+// fibers.  Images m = -1, 0, 1 of every element by Gauss quadrature (the target
+// "normal" (1, 0) turns the K and T integrals into d/dx1 of the single- and
+// double-layer integrals); images |m| >= 2 through the root local expansion
+// sum_n c_n J_n(kr) e^{i n theta}, c_n = L_n / w_n, whose x1-derivative is
+// (k/2) sum_m J_m(kr) e^{i m theta} (c_{m+1} - c_{m-1}).  One warp per point.
 __global__ void field_kernel(int npts, const double2* __restrict__ pts, int E, double k, double eta, double H,
                              double x0, double y0, cplx alpha, const double2* __restrict__ sc,
                              const double2* __restrict__ st, const double2* __restrict__ snu,
                              const double* __restrict__ sh, const cplx* __restrict__ dens, int p0,
-                             const double* __restrict__ w0, const cplx* __restrict__ L0, cplx* __restrict__ u) {
+                             const double* __restrict__ w0, const cplx* __restrict__ L0, cplx* __restrict__ u,
+                             cplx* __restrict__ dudx1) {
   const int lane = threadIdx.x & 31;
   const int pi = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (pi >= npts) return;
   double2 x = pts[pi];
   const int mp = (int)floor((x.y - y0) / H);
   x.y -= mp * H;
-  const double2 nx{0.0, 0.0};
-  cplx acc{0, 0};
+  const double2 nx{1.0, 0.0};
+  cplx acc{0, 0}, dacc{0, 0};
   for (int t = lane; t < 3 * E; t += 32) {
     const int f = t / 3, m = t % 3 - 1;
     double2 c = sc[f];
@@ -1820,26 +1827,41 @@ __global__ void field_kernel(int npts, const double2* __restrict__ pts, int E, d
     const int g = gl_order(q, 0);
     cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
     pair4_f64(k, x, nx, c, st[f], snu[f], hh, g, S, Dv, K, T);
-    acc += ipow_phase(alpha, m) * (Dv * dens[2 * f] - eta * mul_i(S * dens[2 * f + 1]));
+    const cplx ph = ipow_phase(alpha, m);
+    acc += ph * (Dv * dens[2 * f] - eta * mul_i(S * dens[2 * f + 1]));
+    dacc += ph * (T * dens[2 * f] - eta * mul_i(K * dens[2 * f + 1]));
   }
   acc = warp_sum(acc);
+  dacc = warp_sum(dacc);
   if (lane == 0) {
     const double ox = x0 + 0.5 * H, oy = y0 + 0.5 * H;
     const double vx = x.x - ox, vy = x.y - oy;
     const double r = sqrt(vx * vx + vy * vy);
     cplx z = r > 0 ? cplx{vx / r, vy / r} : cplx{1, 0};
     double J[PF_PMAX + 2];
-    bessel_j_array(k * r, p0, J);
-    cplx loc{0, 0}, zp{1, 0};
-    for (int l = 0; l <= p0; ++l) {
-      loc += (J[l] / w0[p0 + l]) * (L0[p0 + l] * zp);
-      if (l > 0) loc += (((l & 1) ? -J[l] : J[l]) / w0[p0 - l]) * (L0[p0 - l] * conj(zp));
+    bessel_j_array(k * r, p0 + 1, J);
+    // B_m = J_m(kr) e^{i m theta}, m = -(p0+1) .. p0+1; c_n = L_n / w_n, |n| <= p0
+    cplx loc{0, 0}, dloc{0, 0}, zp{1, 0};
+    auto coef = [&](int n) -> cplx {
+      if (n < -p0 || n > p0) return cplx{0, 0};
+      return (1.0 / w0[p0 + n]) * L0[p0 + n];
+    };
+    for (int l = 0; l <= p0 + 1; ++l) {
+      const cplx Bp = J[l] * zp;                                      // B_l
+      const cplx Bm = ((l & 1) ? -J[l] : J[l]) * conj(zp);            // B_-l
+      if (l <= p0) {
+        loc += coef(l) * Bp;
+        if (l > 0) loc += coef(-l) * Bm;
+      }
+      dloc += (coef(l + 1) - coef(l - 1)) * Bp;
+      if (l > 0) dloc += (coef(-l + 1) - coef(-l - 1)) * Bm;
       zp = zp * z;
     }
-    cplx total = mul_i(0.25 * (acc + loc));
+    dloc = (0.5 * k) * dloc;
     // back to the requested point: u^s(x) = alpha^{mp} u^s(x - mp h)
-    cplx am{cos(mp * atan2(alpha.im, alpha.re)), sin(mp * atan2(alpha.im, alpha.re))};
-    u[pi] = am * total;
+    const cplx am{cos(mp * atan2(alpha.im, alpha.re)), sin(mp * atan2(alpha.im, alpha.re))};
+    if (u) u[pi] = am * mul_i(0.25 * (acc + loc));
+    if (dudx1) dudx1[pi] = am * mul_i(0.25 * (dacc + dloc));
   }
 }
 
@@ -1848,13 +1870,13 @@ cudaError_t k_field_prepare(pfmbem* h, const cplx* psi) {
   return cudaGetLastError();
 }
 
-cudaError_t k_field(pfmbem* h, const cplx* psi, int npts, const double2* pts, cplx* u) {
+cudaError_t k_field(pfmbem* h, const cplx* psi, int npts, const double2* pts, cplx* u, cplx* dudx1) {
   (void)psi;
   Level& r = h->lev[0];
   prof_begin(h, PH_OUT);
   field_kernel<<<(npts * 32 + 127) / 128, 128, 0, h->stream>>>(npts, pts, h->E, h->k, h->eta, h->H, h->x0, h->y0,
                                                                h->alpha, h->s_c, h->s_t, h->s_nu, h->s_h, h->dens,
-                                                               r.p, r.w_dev, r.L, u);
+                                                               r.p, r.w_dev, r.L, u, dudx1);
   prof_end(h, PH_OUT);
   return cudaGetLastError();
 }

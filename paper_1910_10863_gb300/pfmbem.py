@@ -72,6 +72,8 @@ def lib():
             "pfmbem_mlp_params": ([vp, vp, vp, vp], i),
             "pfmbem_mlp_forward": ([vp, i, vp, vp], i),
             "pfmbem_mlp_train": ([vp, i, vp, vp, ctypes.c_float, vp, vp], i),
+            "pfmbem_field_dx1": ([vp, vp, i, vp, vp, vp], i),
+            "pfmbem_etc": ([vp, vp, d, i, vp], i),
             "pfmbem_warm_features": ([vp, vp], i),
             "pfmbem_warm_features_local": ([vp, i, vp], i),
             "pfmbem_warm_targets": ([vp, i, vp, vp], i),
@@ -279,6 +281,20 @@ class MLP:
         _st(lib().pfmbem_mlp_train(self.h, X.shape[0], addr(X), addr(T), float(lr), ctypes.byref(loss), addr(g)),
             "pfmbem_mlp_train")
         return (loss.value, g) if want_grad else loss.value
+
+
+def pfmbem_field_dx1(h, psi, pts, u=None, dudx1=None):
+    """Scattered field and its x1-derivative at pts [n][2] (outputs complex [n])."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64) if isinstance(pts, np.ndarray) else pts
+    n = len(pts)
+    _check(h, lib().pfmbem_field_dx1(h, addr(psi), n, addr(pts), addr(u), addr(dudx1)))
+    return u, dudx1
+
+
+def pfmbem_etc(h, psi, x1, npts=256):
+    v = ctypes.c_double(0)
+    _check(h, lib().pfmbem_etc(h, addr(psi), float(x1), int(npts), ctypes.byref(v)))
+    return v.value
 
 
 def pfmbem_warm_features(h, M):

@@ -214,3 +214,23 @@ def density_vector(E: int, seed: int) -> np.ndarray:
     """Seeded complex128 test vector of 2E unknowns (phi_e, varphi_e interleaved)."""
     rng = np.random.default_rng(seed)
     return rng.standard_normal(2 * E) + 1j * rng.standard_normal(2 * E)
+
+
+def table3_square(ka2pi: float, f: float = 0.35, n: int = 256, c_water: float = 1500.0,
+                  name: str | None = None) -> Workload:
+    """The water/mercury crystal of Sec. 4 (Table 3, circular scatterers in a
+    square lattice): water cylinders in a mercury matrix, lattice constant
+    a = 0.5, M_H = 6 rows (period H = 3) by M_L = 4 columns, radius r = a sqrt(f/pi)
+    for filling fraction f, n elements per circle, normal incidence d = (1, 0),
+    normalised frequency ka/2pi.  k = omega / c_mercury and k1 = omega / c_water
+    (Sec. 4 prints c_water = 1500 m/s, hence k = 1.0345 k1); varrho = 13600/1000."""
+    a = 0.5
+    H = 6 * a
+    k = 2.0 * math.pi * ka2pi / a
+    r = a * math.sqrt(f / math.pi)
+    centres = [((ix + 0.5) * a, (iy + 0.5) * a) for ix in range(4) for iy in range(6)]
+    nodes = np.concatenate([circle_nodes(c[0], c[1], r, n) for c in centres])
+    return Workload(name=name or f"table3_square_f{f:g}_ka{ka2pi:g}", H=H, lattice=0, k=k,
+                    k1=k * C_MERCURY / c_water, rho_ratio=RHO_MERCURY / RHO_WATER, theta=0.0,
+                    nodes_per_fiber=np.full(len(centres), n, dtype=np.int32), nodes=nodes,
+                    centres=np.asarray(centres), radii=np.full(len(centres), r))
