@@ -38,7 +38,7 @@ def test_field_x1_derivative_and_etc_match_oracle(pf):
     # midpoint rule on the GPU against the oracle's Rayleigh expansion
     etc = pf.pfmbem_etc(s.h, psi, 1.0, 512)
     etc_ref = bem.etc(pb, psi, nmax=60, npts=512, x1=1.0)
-    assert abs(etc - etc_ref) < 1e-6 * etc_ref
+    assert abs(etc - etc_ref) < 1e-5 * etc_ref
 
 
 def _golden_gap(scatterer, lattice, fill):
