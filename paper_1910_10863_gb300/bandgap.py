@@ -59,8 +59,10 @@ def main():
     freqs = np.round(np.arange(a.fmin, a.fmax + 1e-9, a.step), 6)
     for f in a.fill:
         c = etc_curve(freqs, f=f)
+        worst = max(c, key=lambda t: t[3])
         print(json.dumps({"filling": f, "gaps_etc_below_3pct": gaps(c), "points": len(c),
-                          "max_rel_residual": max(r for _, _, _, r in c),
+                          "max_rel_residual": worst[3], "max_rel_residual_at": worst[0],
+                          "unconverged": [round(k, 4) for k, _, _, r in c if r > 1e-6],
                           "curve": [[round(k, 4), round(e, 5), it] for k, e, it, _ in c]}), flush=True)
 
 
