@@ -1444,6 +1444,18 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
       CK(k_axpy(h, cplx{1, 0}, g.c, g.x, (int)n));
     }
     restarts = refinements;
+    if (st != PFMBEM_OK && iters < maxit) {
+      // refinement stalled above tol (the FP32 operator's accuracy floor, about
+      // eps_32 times the condition number, lies above it): finish with FP64
+      // GMRES from the current iterate
+      int it = 0, rs = 0;
+      double rr = relres;
+      st = gmres(h, g.b, g.x, tol, maxit - iters, PFMBEM_FP64, &it, &rs, &rr);
+      if (st != PFMBEM_OK && st != PFMBEM_ENOCONV) return st;
+      iters += it;
+      restarts += rs;
+      relres = rr;
+    }
   } else {
     st = gmres(h, g.b, g.x, tol, maxit, PFMBEM_FP64, &iters, &restarts, &relres);
   }
