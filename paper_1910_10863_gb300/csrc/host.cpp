@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "internal.h"
@@ -78,15 +79,61 @@ pfmbem_status upload(pfmbem* h, T** dst, const std::vector<T>& src) {
   return PFMBEM_OK;
 }
 
+// Page-locked staging for the batched set-up copies: one process-wide arena.
+// Every create takes fresh regions from it, so an earlier copy still in flight
+// is never overwritten; the arena is rewound when no create is using it (each
+// create synchronises its stream before it lets go).  When the arena is full
+// the copy goes from pageable memory instead.
+struct PinnedArena {
+  std::mutex mu;
+  unsigned char* buf = nullptr;
+  size_t cap = 0, off = 0;
+  int users = 0;
+};
+PinnedArena g_pin;
+
+void pin_acquire(pfmbem* h) {
+  std::lock_guard<std::mutex> lk(g_pin.mu);
+  g_pin.users++;
+  h->pin_user = true;
+}
+
+void pin_release(pfmbem* h) {
+  if (!h->pin_user) return;
+  std::lock_guard<std::mutex> lk(g_pin.mu);
+  if (--g_pin.users == 0) g_pin.off = 0;
+  h->pin_user = false;
+}
+
 // Copies the open batch to the device and sets its destination pointers; the
 // batch stays open.
 pfmbem_status flush_uploads(pfmbem* h) {
   if (h->ub_fix.empty()) return PFMBEM_OK;
   unsigned char* d = dalloc<unsigned char>(h, std::max<size_t>(h->ub_buf.size(), 1));
   if (!d) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
-  if (!h->ub_buf.empty())
-    CK(cudaMemcpyAsync(d, h->ub_buf.data(), h->ub_buf.size(), cudaMemcpyHostToDevice,
+  const size_t nb = h->ub_buf.size();
+  if (nb) {
+    unsigned char* src = nullptr;
+    {
+      std::lock_guard<std::mutex> lk(g_pin.mu);
+      if (!g_pin.buf) {
+        void* p = nullptr;
+        if (cudaHostAlloc(&p, (size_t)64 << 20, cudaHostAllocDefault) == cudaSuccess) {
+          g_pin.buf = static_cast<unsigned char*>(p);
+          g_pin.cap = (size_t)64 << 20;
+        } else {
+          cudaGetLastError();
+        }
+      }
+      if (h->pin_user && g_pin.buf && g_pin.off + nb <= g_pin.cap) {
+        src = g_pin.buf + g_pin.off;
+        g_pin.off += (nb + 255) & ~(size_t)255;
+      }
+    }
+    if (src) std::memcpy(src, h->ub_buf.data(), nb);
+    CK(cudaMemcpyAsync(d, src ? src : h->ub_buf.data(), nb, cudaMemcpyHostToDevice,
                        h->astream ? h->astream : h->stream));
+  }
   for (auto& f : h->ub_fix) *f.first = d + f.second;
   h->ub_buf.clear();
   h->ub_fix.clear();
@@ -264,32 +311,38 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     m0[e] = m;
     cw[e] = double2{c[e].x, c[e].y - m * H};
   }
-  // optional set-up timing (PFMBEM_TIMING=1): wall time per section on stderr
-  const bool timing = std::getenv("PFMBEM_TIMING") != nullptr;
+  // optional set-up timing on stderr: PFMBEM_TIMING=1 wall time per section
+  // (the stream is synchronised at every mark), =2 host time only (no sync)
+  const char* tenv = std::getenv("PFMBEM_TIMING");
+  const bool timing = tenv != nullptr;
+  const bool tsync = timing && std::strcmp(tenv, "2") != 0;
   double tmark = now_ms();
   auto mark = [&](const char* what) {
     if (!timing) return;
-    cudaStreamSynchronize(h->astream ? h->astream : h->stream);
+    if (tsync) cudaStreamSynchronize(h->astream ? h->astream : h->stream);
     const double t = now_ms();
     std::fprintf(stderr, "pfmbem setup %-22s %8.2f ms\n", what, t - tmark);
     tmark = t;
   };
   mark("elements");
   h->ub_on = true;                 // tables below go up in a few batched copies
+  pin_acquire(h);
   // ---------------------------------------------------- depth
   const int leaf_max = h->opt.leaf_max > 0 ? h->opt.leaf_max : 64;
   int D = h->opt.depth;
   // box coordinates of every midpoint at the finest admissible depth (10); the
   // box at depth D is the same pair shifted right by 10 - D bits
-  std::vector<int> cx10(E), cy10(E);
+  // and its Morton code: the code of the depth-D box is a prefix of it
+  std::vector<int> m10(E);
   {
     const double d10 = H / 1024.0;
     for (int e = 0; e < E; ++e) {
-      cx10[e] = std::min(std::max((int)std::floor((cw[e].x - h->x0) / d10), 0), 1023);
-      cy10[e] = std::min(std::max((int)std::floor((cw[e].y - h->y0) / d10), 0), 1023);
+      const int ix = std::min(std::max((int)std::floor((cw[e].x - h->x0) / d10), 0), 1023);
+      const int iy = std::min(std::max((int)std::floor((cw[e].y - h->y0) / d10), 0), 1023);
+      m10[e] = morton(ix, iy, 10);
     }
   }
-  auto leaf_of = [&](int e, int Dd) { return morton(cx10[e] >> (10 - Dd), cy10[e] >> (10 - Dd), Dd); };
+  auto leaf_of = [&](int e, int Dd) { return m10[e] >> (2 * (10 - Dd)); };
   if (D <= 0) {
     for (D = 2; D < 10; ++D) {
       std::vector<int> cnt(1 << (2 * D), 0);
@@ -854,6 +907,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   }
   h->ub_on = false;
   CK(cudaStreamSynchronize(h->stream));
+  pin_release(h);                  // every staged copy of this create has completed
   {
     int bad = 0;
     CK(cudaMemcpy(&bad, h->tab_err, sizeof(int), cudaMemcpyDeviceToHost));
@@ -1283,6 +1337,7 @@ void pfmbem_destroy(pfmbem_t h) {
   for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
+  pin_release(h);                  // a create that failed part-way
   if (h->gw.hhost) cudaFreeHost(h->gw.hhost);
   if (h->side_ev) cudaEventDestroy(h->side_ev);
   if (h->pre_ev) cudaEventDestroy(h->pre_ev);

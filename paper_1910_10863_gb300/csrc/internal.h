@@ -203,6 +203,7 @@ struct pfmbem {
   std::vector<void*> allocs;
   // batched table uploads during set-up (host.cpp upload / flush_uploads)
   bool ub_on = false;
+  bool pin_user = false;           // holds a share of the process-wide page-locked staging arena
   std::vector<unsigned char> ub_buf;
   std::vector<std::pair<void**, size_t>> ub_fix;
   double setup_ms = 0;

@@ -389,14 +389,16 @@ static double lattice_vmax(int jmax, int q, double k, double H) {
   double V = sqrt(40.0 / (q * H));
   for (int n = 0; n <= jmax; n += (jmax > 8 ? jmax / 8 : 1)) {
     double peak = -1e300, vpk = 0;
-    for (int i = 1; i < 4000; ++i) {
-      double v = 0.005 * i;
+    // the peak of the log-integrand, on a grid of step 0.04 in v (an estimate
+    // low by a little moves the cut-off below out by a little: safe)
+    for (int i = 1; i < 500; ++i) {
+      double v = 0.04 * i;
       double u = v * v;
       double wabs = hypot(u, k) + sqrt(hypot(u * u, 2 * k * u));
       double f = n * log(wabs / k) - q * H * u;
       if (f > peak) { peak = f; vpk = v; }
     }
-    for (double v = vpk; v < 200; v *= 1.01) {
+    for (double v = vpk; v < 200; v *= 1.02) {
       double u = v * v;
       double wabs = hypot(u, k) + sqrt(hypot(u * u, 2 * k * u));
       double f = n * log(wabs / k) - q * H * u;
