@@ -326,6 +326,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   };
   mark("elements");
   h->ub_on = true;                 // tables below go up in a few batched copies
+  h->ub_buf.reserve((size_t)E * 512 + ((size_t)1 << 20));
   pin_acquire(h);
   // ---------------------------------------------------- depth
   const int leaf_max = h->opt.leaf_max > 0 ? h->opt.leaf_max : 64;
@@ -500,15 +501,22 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     std::vector<double2> sc(E), st2(E), snu(E);
     std::vector<double> sh(E);
     std::vector<cplx> sph(E);
+    std::vector<std::pair<int, cplx>> apow;
+    auto alpha_pow = [&](int m) {
+      for (auto& q : apow)
+        if (q.first == m) return q.second;
+      const double a = m * h->beta;
+      apow.push_back({m, cplx{std::cos(a), std::sin(a)}});
+      return apow.back().second;
+    };
     for (int s = 0; s < E; ++s) {
       int e = perm[s];
       sc[s] = cw[e];
       st2[s] = t[e];
       snu[s] = nu[e];
       sh[s] = len[e];
-      // alpha^{-m0}
-      double a = -m0[e] * h->beta;
-      sph[s] = cplx{std::cos(a), std::sin(a)};
+      // alpha^{-m0}; m0 takes a handful of values, so each power is evaluated once
+      sph[s] = alpha_pow(-m0[e]);
     }
     pfmbem_status st;
     if ((st = upload(h, &h->s_c, sc)) != PFMBEM_OK) return st;
@@ -971,8 +979,13 @@ static inline std::complex<double> toz(cplx a) { return {a.re, a.im}; }
 
 // Restarted GMRES(m) with classical Gram-Schmidt applied twice; A is applied by
 // the FMM matvec in the given precision.  Solves A x = b in place of x (device).
+// Restarted GMRES(m) with CGS2 Arnoldi.  With trust_estimate the solve ends as
+// soon as the Arnoldi residual estimate falls below tol/2, without recomputing
+// the true residual (inner solves of the refinement, whose outer loop computes
+// the FP64 residual anyway).
 static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int maxit, int precision,
-                           int* iters_out, int* restarts_out, double* relres_out, bool zero_start = false) {
+                           int* iters_out, int* restarts_out, double* relres_out, bool zero_start = false,
+                           bool trust_estimate = false) {
   GmresWork& g = h->gw;
   const int n = g.n, m = g.m;
   double* hn = reinterpret_cast<double*>(g.hhost);
@@ -988,8 +1001,9 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
   }
   int iters = 0, restarts = 0;
   double relres = 1.0;
+  bool done = false;
   std::vector<std::complex<double>> Hm((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1);
-  while (true) {
+  while (!done) {
     // r = b - A x (x = 0 on a zero start)
     if (zero_start && restarts == 0) {
       CK(cudaMemcpyAsync(g.r, b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, h->stream));
@@ -1042,7 +1056,14 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
       gvec[j] = std::conj(cs[j]) * gj;
       gvec[j + 1] = -sn[j] * gj;
       double est = std::abs(gvec[j + 1]) / bnorm;
-      if (est <= 0.5 * tol || hnext == 0) { ++j; break; }
+      if (est <= 0.5 * tol || hnext == 0) {
+        ++j;
+        if (trust_estimate) {
+          relres = est;
+          done = true;
+        }
+        break;
+      }
     }
     // back substitution and x += V y
     std::vector<std::complex<double>> y(j);
@@ -1493,7 +1514,7 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
       int it = 0, rs = 0;
       double rr = 1;
       CK(cudaMemsetAsync(g.c, 0, n * sizeof(cplx), h->stream));
-      pfmbem_status si = gmres(h, g.d, g.c, inner_tol, cap, PFMBEM_MIXED, &it, &rs, &rr, true);
+      pfmbem_status si = gmres(h, g.d, g.c, inner_tol, cap, PFMBEM_MIXED, &it, &rs, &rr, true, true);
       if (si != PFMBEM_OK && si != PFMBEM_ENOCONV) return si;
       iters += it;
       CK(k_axpy(h, cplx{1, 0}, g.c, g.x, (int)n));
