@@ -225,8 +225,8 @@ def main():
                 prof_acc["launches"] += np.array(p.launches)
             stats.update(iters=info.iters, restarts=info.restarts, rel_residual=info.rel_residual,
                          energy=energy, norders=len(orders))
-            if "plan" not in stats:
-                stats["plan"] = pf.pfmbem_plan(h)
+            if profile or "plan" not in stats:
+                stats["plan"] = pf.pfmbem_plan(h)     # the last profiled (warm) create
         finally:
             pf.pfmbem_destroy(h)
 

@@ -276,3 +276,35 @@ def test_single_launch_matvec_matches_per_stage_kernels(pf, make):
         sf.matvec(x, yf, prec)
         ss.matvec(x, ys, prec)
         assert rel(yf, ys) < tol
+
+
+def _two_fibers_across_the_period():
+    """Two small circles centred 0.03 above the bottom and 0.03 below the top of
+    the period: the root box is [0, 1) in y, so each fiber straddles it and
+    part of its elements are wrapped by one period (phase alpha^-m0)."""
+    nodes = np.concatenate([W.circle_nodes(0.3, 0.03, 0.04, 48), W.circle_nodes(0.7, 0.97, 0.04, 40)])
+    return W.Workload(name="wrapped_pair", H=1.0, lattice=0, k=3.0, k1=3.0 * 1490 / 1450, rho_ratio=1000 / 13600,
+                      theta=0.4, nodes_per_fiber=np.array([48, 40], dtype=np.int32), nodes=nodes)
+
+
+@pytest.mark.parametrize("make", [_two_fibers_across_the_period,
+                                  lambda: W.single_fiber(0.2, 32, 4.0, 4.0 * 1490 / 1450, 1000 / 13600, 0.7,
+                                                         centre=(0.5, 0.5))])
+def test_wrapped_and_single_fiber_blocks(pf, make):
+    """Degenerate and boundary cases of the tree: fibers cut by the root box
+    (elements wrapped into it) and a block of one fiber; both matvec paths and
+    both precisions against the dense oracle."""
+    w = make()
+    pb = bem.problem(w)
+    Mo = bem.operator_rows(pb)
+    x = W.density_vector(w.E, 21)
+    for launch in (0, 1):
+        s = pf.Solver(w, launch=launch)
+        for prec, tol in ((pf.FP64, 1e-8), (pf.MIXED, 2e-6)):
+            y = np.zeros_like(x)
+            s.matvec(x, y, prec)
+            assert rel(y, Mo @ x) < tol, (launch, prec)
+        psi = np.zeros_like(x)
+        info = s.solve(psi, tol=1e-9, maxit=400)
+        assert info.rel_residual <= 1e-9
+        assert rel(psi, np.linalg.solve(Mo, bem.rhs(pb))) < 1e-6
