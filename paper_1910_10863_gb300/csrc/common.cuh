@@ -73,8 +73,9 @@ PF_HD void bessel_j_array(double x, int N, double* out) {
   double big = (double)N > x ? (double)N : x;
   int ns = 2 * (((int)(big + 16.0 + sqrt(40.0 * big))) / 2);   // even start index
   double jp1 = 0.0, j = 1e-250, sum = 0.0;
+  const double tx = 2.0 / x;
   for (int n = ns; n > 0; --n) {
-    double jm1 = (2.0 * n / x) * j - jp1;
+    double jm1 = (n * tx) * j - jp1;
     jp1 = j;
     j = jm1;                       // j = J_{n-1} (unnormalised)
     if (n - 1 <= N) out[n - 1] = j;

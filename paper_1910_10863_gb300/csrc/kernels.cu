@@ -1067,13 +1067,16 @@ __device__ __forceinline__ void morton_centre(int box, int D, double d, double x
 // P2M coefficients of element s (the moments of Sec. 3.2 per unit density):
 //   c[s][0][n] = sum_g w_g h/2 (k/2)(conj(nu) J^-_{n-1} - nu J^-_{n+1}) / w_n   (phi')
 //   c[s][1][n] = sum_g w_g h/2 (-i eta) J^-_n / w_n                             (varphi')
+// One thread per (element s, Gauss node q): the node's share of c[s][.][n] is
+// added atomically into out, which the launcher clears first.
 __global__ void p2m_coef_kernel(int E, const int* __restrict__ sleaf, int D, double d, int p,
                                 const double* __restrict__ wgt, int g, double k, double eta, double x0, double y0,
                                 const double2* __restrict__ sc, const double2* __restrict__ st,
                                 const double2* __restrict__ snu, const double* __restrict__ sh,
-                                cplx* __restrict__ out, cplxf* __restrict__ outf) {
-  const int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= E) return;
+                                cplx* __restrict__ out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= E * g) return;
+  const int s = t / g, q = t - s * g;
   const int P = 2 * p + 1;
   double ox, oy;
   morton_centre(sleaf[s], D, d, x0, y0, ox, oy);
@@ -1081,30 +1084,34 @@ __global__ void p2m_coef_kernel(int E, const int* __restrict__ sleaf, int D, dou
   const double hh = sh[s];
   const cplx nuc{nu.x, nu.y};
   cplx* o = out + (size_t)s * 2 * P;
-  for (int i = 0; i < 2 * P; ++i) o[i] = cplx{0, 0};
-  for (int q = 0; q < g; ++q) {
-    const double sp = 0.5 * hh * c_glx[g - 1][q];
-    const double cw = 0.5 * hh * c_glw[g - 1][q];
-    const double vx = c.x + sp * tt.x - ox, vy = c.y + sp * tt.y - oy;
-    const double r = sqrt(vx * vx + vy * vy);
-    const cplx z = r > 0 ? cplx{vx / r, -vy / r} : cplx{1, 0};   // e^{-i theta}
-    double J[PF_PMAX + 2];
-    bessel_j_array(k * r, p + 1, J);
-    cplx Jm[2 * PF_PMAX + 3];
-    cplx zp{1, 0};
-    for (int n = 0; n <= p + 1; ++n) {
-      Jm[p + 1 + n] = J[n] * zp;
-      Jm[p + 1 - n] = (((n & 1) ? -1.0 : 1.0) * J[n]) * conj(zp);
-      zp = zp * z;
-    }
-    for (int n = -p; n <= p; ++n) {
-      const double iw = 1.0 / wgt[n + p];
-      o[n + p] += (cw * 0.5 * k * iw) * (conj(nuc) * Jm[p + n] - nuc * Jm[p + n + 2]);
-      o[P + n + p] += (-eta * cw * iw) * mul_i(Jm[p + n + 1]);
-    }
+  const double sp = 0.5 * hh * c_glx[g - 1][q];
+  const double cw = 0.5 * hh * c_glw[g - 1][q];
+  const double vx = c.x + sp * tt.x - ox, vy = c.y + sp * tt.y - oy;
+  const double r = sqrt(vx * vx + vy * vy);
+  const cplx z = r > 0 ? cplx{vx / r, -vy / r} : cplx{1, 0};   // e^{-i theta}
+  double J[PF_PMAX + 2];
+  bessel_j_array(k * r, p + 1, J);
+  cplx Jm[2 * PF_PMAX + 3];
+  cplx zp{1, 0};
+  for (int n = 0; n <= p + 1; ++n) {
+    Jm[p + 1 + n] = J[n] * zp;
+    Jm[p + 1 - n] = (((n & 1) ? -1.0 : 1.0) * J[n]) * conj(zp);
+    zp = zp * z;
   }
-  if (outf)
-    for (int i = 0; i < 2 * P; ++i) outf[(size_t)s * 2 * P + i] = to_f(o[i]);
+  for (int n = -p; n <= p; ++n) {
+    const double iw = 1.0 / wgt[n + p];
+    const cplx a = (cw * 0.5 * k * iw) * (conj(nuc) * Jm[p + n] - nuc * Jm[p + n + 2]);
+    const cplx b = (-eta * cw * iw) * mul_i(Jm[p + n + 1]);
+    atomicAdd(&o[n + p].re, a.re);
+    atomicAdd(&o[n + p].im, a.im);
+    atomicAdd(&o[P + n + p].re, b.re);
+    atomicAdd(&o[P + n + p].im, b.im);
+  }
+}
+
+__global__ void to_f32_kernel(size_t n, const cplx* __restrict__ a, cplxf* __restrict__ b) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    b[i] = to_f(a[i]);
 }
 
 // L2P coefficients of target s:
@@ -1575,10 +1582,16 @@ static cudaError_t matvec_cached(pfmbem* h, const cplx* x, cplx* y, const Ops<C>
 
 cudaError_t k_build_fmm_caches(pfmbem* h) {
   Level& leaf = h->lev[h->D];
+  const size_t nc = (size_t)h->E * 2 * leaf.P;
+  cudaError_t e = cudaMemsetAsync(h->p2m_c, 0, nc * sizeof(cplx), h->stream);
+  if (e != cudaSuccess) return e;
   prof_begin(h, PH_SETUP);
-  p2m_coef_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.w_dev,
-                                                             h->g_far, h->k, h->eta, h->x0, h->y0, h->s_c, h->s_t,
-                                                             h->s_nu, h->s_h, h->p2m_c, h->p2m_cf);
+  p2m_coef_kernel<<<(h->E * h->g_far + 127) / 128, 128, 0, h->stream>>>(
+      h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.w_dev, h->g_far, h->k, h->eta, h->x0, h->y0, h->s_c, h->s_t,
+      h->s_nu, h->s_h, h->p2m_c);
+  prof_end(h, PH_SETUP);
+  prof_begin(h, PH_SETUP);
+  to_f32_kernel<<<std::min<size_t>((nc + 255) / 256, 4096), 256, 0, h->stream>>>(nc, h->p2m_c, h->p2m_cf);
   prof_end(h, PH_SETUP);
   prof_begin(h, PH_SETUP);
   l2p_coef_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.w_dev, h->k,
