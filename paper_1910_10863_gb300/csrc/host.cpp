@@ -150,10 +150,20 @@ double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
 
+// Spreads the low 16 bits of v to the even bit positions.
+inline unsigned spread_bits(unsigned v) {
+  v &= 0xFFFFu;
+  v = (v | (v << 8)) & 0x00FF00FFu;
+  v = (v | (v << 4)) & 0x0F0F0F0Fu;
+  v = (v | (v << 2)) & 0x33333333u;
+  v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
+// Morton code of box (ix, iy) at depth D: bit b of ix to bit 2b, of iy to 2b + 1.
 inline int morton(int ix, int iy, int D) {
-  int c = 0;
-  for (int b = 0; b < D; ++b) c |= (((ix >> b) & 1) << (2 * b)) | (((iy >> b) & 1) << (2 * b + 1));
-  return c;
+  const unsigned m = (1u << D) - 1u;
+  return (int)(spread_bits((unsigned)ix & m) | (spread_bits((unsigned)iy & m) << 1));
 }
 
 // Gauss-Legendre thresholds: rule g meets tolerance tol for a source element
