@@ -963,6 +963,38 @@ pfmbem_status stage_input(pfmbem* h, const double* p, size_t n, cplx* scratch, c
 }  // namespace
 
 // ============================================================== GMRES
+// Page-locked mirrors of the Arnoldi columns (2 (m + 2) complex numbers, m <= 250)
+// are recycled between handles: allocating and freeing page-locked memory per
+// solve costs more than the solve's host work.
+namespace {
+std::mutex g_small_mu;
+std::vector<cplx*> g_small_free;
+constexpr size_t kSmallPinned = sizeof(cplx) * 2 * (250 + 2);
+}  // namespace
+
+static cplx* pinned_small_get() {
+  {
+    std::lock_guard<std::mutex> lk(g_small_mu);
+    if (!g_small_free.empty()) {
+      cplx* p = g_small_free.back();
+      g_small_free.pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, kSmallPinned) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<cplx*>(p);
+}
+
+static void pinned_small_put(cplx* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_small_mu);
+  g_small_free.push_back(p);
+}
+
 static pfmbem_status gmres_alloc(pfmbem* h, int m) {
   GmresWork& g = h->gw;
   const int n = 2 * h->E;
@@ -981,7 +1013,8 @@ static pfmbem_status gmres_alloc(pfmbem* h, int m) {
   g.nrm = dalloc<double>(h, 2);
   if (!g.V || !g.w || !g.r || !g.x || !g.b || !g.d || !g.c || !g.hcol || !g.nrm)
     return fail(h, PFMBEM_ENOMEM, "GMRES workspace");
-  if (cudaMallocHost(&g.hhost, sizeof(cplx) * 2 * (m + 2)) != cudaSuccess) return fail(h, PFMBEM_ENOMEM, "pinned host buffer");
+  g.hhost = pinned_small_get();
+  if (!g.hhost) return fail(h, PFMBEM_ENOMEM, "pinned host buffer");
   return PFMBEM_OK;
 }
 
@@ -1369,7 +1402,7 @@ void pfmbem_destroy(pfmbem_t h) {
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
   pin_release(h);                  // a create that failed part-way
-  if (h->gw.hhost) cudaFreeHost(h->gw.hhost);
+  pinned_small_put(h->gw.hhost);
   if (h->side_ev) cudaEventDestroy(h->side_ev);
   if (h->pre_ev) cudaEventDestroy(h->pre_ev);
   if (h->side) cudaStreamDestroy(h->side);
