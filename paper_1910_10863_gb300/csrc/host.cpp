@@ -1267,6 +1267,7 @@ pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* p
     b.h = h;
     b.prec = (h->opt.precision == PFMBEM_MIXED && h->cached) ? PFMBEM_MIXED : PFMBEM_FP64;
     const int m = h->opt.gmres_m > 0 ? h->opt.gmres_m : 60;
+    if (m > 250) return fail(h, PFMBEM_EINVAL, "gmres_m above 250");
     pfmbem_status st = gmres_alloc(h, m);
     if (st != PFMBEM_OK) return st;
     GmresWork& g = h->gw;
