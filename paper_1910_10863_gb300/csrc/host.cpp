@@ -7,7 +7,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "internal.h"
@@ -251,6 +254,167 @@ void gauss_legendre(int n, double* x, double* w) {
 }
 
 // ============================================================== planning
+// Near-field integrals shared by translated copies of a fiber pair.  Fibers
+// whose node lists are translates of each other (to 1e-12 H) form a class; a
+// near-field fiber pair (A, B, m: source shifted by m periods) is keyed by the
+// classes of A and B and the offset between their first nodes.  Keys met at
+// least twice get one table of S, D, K, T over all element pairs, built from
+// the first pair with the key; the near-field build reads every pair of such a
+// key from it.  Nothing happens unless two fibers are congruent.
+static pfmbem_status build_pair_tables(pfmbem* h, const double* nodes, const std::vector<int>& foff,
+                                       const std::vector<int>& fib, const std::vector<int>& m0,
+                                       const std::vector<int>& perm, const std::vector<int>& nc_sbase,
+                                       const std::vector<int>& nc_src, const std::vector<int>& nc_img) {
+  const int M = h->M, D = h->D;
+  const double H = h->H, tol = 1e-12 * H;
+  // ---- classes
+  std::vector<int> cls(M, -1);
+  std::vector<int> rep;                                   // first fiber of each class
+  std::map<std::vector<long long>, std::vector<int>> bucket;
+  const double q = 1e-9 * H;
+  bool repeat = false;
+  for (int i = 0; i < M; ++i) {
+    const int n = foff[i + 1] - foff[i];
+    const double* a = nodes + 2 * foff[i];
+    std::vector<long long> key{n};
+    for (int j : {1, n / 3, (2 * n) / 3})
+      if (j > 0 && j < n) {
+        key.push_back(std::llround((a[2 * j] - a[0]) / q));
+        key.push_back(std::llround((a[2 * j + 1] - a[1]) / q));
+      }
+    auto& cand = bucket[key];
+    for (int c : cand) {
+      const double* r = nodes + 2 * foff[rep[c]];
+      bool same = true;
+      for (int j = 1; j < n && same; ++j)
+        same = std::fabs((a[2 * j] - a[0]) - (r[2 * j] - r[0])) <= tol &&
+               std::fabs((a[2 * j + 1] - a[1]) - (r[2 * j + 1] - r[1])) <= tol;
+      if (same) {
+        cls[i] = c;
+        repeat = true;
+        break;
+      }
+    }
+    if (cls[i] < 0) {
+      cls[i] = (int)rep.size();
+      rep.push_back(i);
+      cand.push_back(cls[i]);
+    }
+  }
+  if (!repeat) return PFMBEM_OK;
+  // ---- near-field fiber pairs (target fiber, source fiber, image shift)
+  const Level& Lf = h->lev[D];
+  std::vector<unsigned long long> pairs;
+  auto pack = [](int A, int B, int m) {
+    return ((unsigned long long)(unsigned)A << 32) | ((unsigned long long)(unsigned)B << 8) | (unsigned)(m + 64);
+  };
+  std::vector<std::pair<int, int>> T;                     // (fiber, m0) of the leaf's targets
+  std::vector<std::array<int, 3>> S;                      // (fiber, m0, m) of its sources
+  for (size_t li = 0; li < Lf.hne.size(); ++li) {
+    const int b = Lf.hne[li];
+    T.clear();
+    S.clear();
+    for (int s2 = Lf.hbegin[b]; s2 < Lf.hend[b]; ++s2) {
+      const int e = perm[s2];
+      if (T.empty() || T.back().first != fib[e] || T.back().second != m0[e]) T.push_back({fib[e], m0[e]});
+    }
+    for (int j = nc_sbase[li]; j < nc_sbase[li + 1]; ++j) {
+      const int e = perm[nc_src[j]];
+      const std::array<int, 3> v{fib[e], m0[e], nc_img[j]};
+      if (!S.empty() && S.back() == v) continue;
+      if (std::find(S.begin(), S.end(), v) == S.end()) S.push_back(v);
+    }
+    for (auto& t : T)
+      for (auto& sv : S) {
+        const int mt = sv[2] + t.second - sv[1];
+        if (sv[0] == t.first && mt == 0) continue;
+        if (mt < -60 || mt > 60) continue;
+        pairs.push_back(pack(t.first, sv[0], mt));
+      }
+  }
+  std::sort(pairs.begin(), pairs.end());
+  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+  // ---- keys: classes and the offset between the first nodes
+  struct Key {
+    int ca, cb;
+    long long dx, dy;
+    bool operator<(const Key& o) const {
+      return std::tie(ca, cb, dx, dy) < std::tie(o.ca, o.cb, o.dx, o.dy);
+    }
+  };
+  std::map<Key, int> kid;
+  std::vector<int> kcount, kA, kB, km;
+  std::vector<int> pair_key(pairs.size());
+  for (size_t i = 0; i < pairs.size(); ++i) {
+    const int A = (int)(pairs[i] >> 32), B = (int)((pairs[i] >> 8) & 0xFFFFFF), mt = (int)(pairs[i] & 0xFF) - 64;
+    const double* a = nodes + 2 * foff[A];
+    const double* bn = nodes + 2 * foff[B];
+    const Key key{cls[A], cls[B], std::llround((bn[0] - a[0]) / q), std::llround((bn[1] + mt * H - a[1]) / q)};
+    auto it = kid.find(key);
+    int id;
+    if (it == kid.end()) {
+      id = (int)kcount.size();
+      kid.emplace(key, id);
+      kcount.push_back(0);
+      kA.push_back(A);
+      kB.push_back(B);
+      km.push_back(mt);
+    } else {
+      id = it->second;
+    }
+    kcount[id]++;
+    pair_key[i] = id;
+  }
+  // ---- tables for the keys met at least twice
+  std::vector<int> tab_of(kcount.size(), -1), tA, tB, tm, tnb;
+  std::vector<int64_t> tstart(1, 0);
+  for (size_t id = 0; id < kcount.size(); ++id)
+    if (kcount[id] >= 2) {
+      tab_of[id] = (int)tA.size();
+      tA.push_back(kA[id]);
+      tB.push_back(kB[id]);
+      tm.push_back(km[id]);
+      const int na = foff[kA[id] + 1] - foff[kA[id]], nb = foff[kB[id] + 1] - foff[kB[id]];
+      tnb.push_back(nb);
+      tstart.push_back(tstart.back() + (int64_t)na * nb);
+    }
+  if (tA.empty()) return PFMBEM_OK;
+  std::vector<int> plp(M + 1, 0), plf, pli, plt;
+  for (size_t i = 0; i < pairs.size(); ++i)
+    if (tab_of[pair_key[i]] >= 0) plp[(pairs[i] >> 32) + 1]++;
+  for (int i = 0; i < M; ++i) plp[i + 1] += plp[i];
+  plf.resize(plp[M]);
+  pli.resize(plp[M]);
+  plt.resize(plp[M]);
+  {
+    std::vector<int> fill(plp.begin(), plp.end() - 1);
+    for (size_t i = 0; i < pairs.size(); ++i) {
+      const int t = tab_of[pair_key[i]];
+      if (t < 0) continue;
+      const int A = (int)(pairs[i] >> 32);
+      const int at = fill[A]++;
+      plf[at] = (int)((pairs[i] >> 8) & 0xFFFFFF);
+      pli[at] = (int)(pairs[i] & 0xFF) - 64;
+      plt[at] = t;
+    }
+  }
+  h->ntab = (int)tA.size();
+  h->tab_entries = tstart.back();
+  pfmbem_status st;
+  if ((st = upload(h, &h->tab_A, tA)) != PFMBEM_OK) return st;
+  if ((st = upload(h, &h->tab_B, tB)) != PFMBEM_OK) return st;
+  if ((st = upload(h, &h->tab_m, tm)) != PFMBEM_OK) return st;
+  if ((st = upload(h, &h->tab_nb, tnb)) != PFMBEM_OK) return st;
+  if ((st = upload(h, &h->tab_start, tstart)) != PFMBEM_OK) return st;
+  if ((st = upload(h, &h->pl_ptr, plp)) != PFMBEM_OK) return st;
+  if ((st = upload(h, &h->pl_fib, plf)) != PFMBEM_OK) return st;
+  if ((st = upload(h, &h->pl_img, pli)) != PFMBEM_OK) return st;
+  if ((st = upload(h, &h->pl_tab, plt)) != PFMBEM_OK) return st;
+  h->tab_val = dalloc<cplx>(h, (size_t)4 * h->tab_entries);
+  if (!h->tab_val) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber-pair tables)");
+  return PFMBEM_OK;
+}
+
 static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) {
   const double t0 = now_ms();
   const int M = h->M;
@@ -650,6 +814,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       for (int s2 = 0; s2 < E; ++s2) sm0[s2] = m0[perm[s2]];
       if ((st = upload(h, &h->kt_base, kbase)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->s_m0, sm0)) != PFMBEM_OK) return st;
+      if ((st = build_pair_tables(h, nodes, foff, fib, m0, perm, nc_sbase, nc_src, nc_img)) != PFMBEM_OK) return st;
       h->kt_val = dalloc<cplx>(h, (size_t)4 * kacc);
       if (!h->kt_val) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
       h->nchunk = (int)chunks.size() / 3;

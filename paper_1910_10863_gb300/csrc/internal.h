@@ -151,6 +151,19 @@ struct pfmbem {
   std::vector<int> hcirc;        // host copy of fb_circ
   int* fb_chunk = nullptr;       // [nchunk][3] = fiber, first row, last row + 1
   int* fb_rows = nullptr;        // elements whose row pairs are built (first element of a circulant fiber)
+  // near-field integrals shared by translated copies of a fiber pair (lattices of identical fibers)
+  int ntab = 0;                  // tables
+  int64_t tab_entries = 0;
+  int* tab_A = nullptr;          // [ntab] representative target fiber
+  int* tab_B = nullptr;          // [ntab] representative source fiber
+  int* tab_m = nullptr;          // [ntab] its image shift (periods)
+  int64_t* tab_start = nullptr;  // [ntab + 1] first entry of every table (4 values each)
+  int* tab_nb = nullptr;         // [ntab] elements of the source fiber
+  cplx* tab_val = nullptr;
+  int* pl_ptr = nullptr;         // [M + 1] per target fiber: (source fiber, image shift) -> table
+  int* pl_fib = nullptr;
+  int* pl_img = nullptr;
+  int* pl_tab = nullptr;
   int nfb_rows = 0;
   int* s_m0 = nullptr;           // sorted: periods the element was shifted by when wrapped into the root
   int64_t* kt_base = nullptr;    // [M] first entry of the fiber's k table, -1 when not a regular polygon

@@ -856,6 +856,63 @@ __global__ void fiber_combine_f64_kernel(int E, const int* __restrict__ fib, con
 // Build: for leaf li with targets s in [bb, be) and the concatenated source list
 // (f, m) of its neighbour leaves, block (t, j) holds (i/4) alpha^m times
 // {D, -i eta S, T, -i eta K} of source f at target s (zero for f = s, m = 0).
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Integrals shared by translated copies of a fiber pair: table t holds S, D, K,
+// T (without i/4) at the matrix wavenumber of every element a of fiber A_t
+// against every element b of fiber B_t shifted by m_t periods, for the pair
+// (A_t, B_t, m_t) that represents the class (true coordinates).  Every fiber
+// pair in the class is a rigid translate of it.  One thread per entry.
+__global__ void pair_table_kernel(int ntab, const int* __restrict__ tA, const int* __restrict__ tB,
+                                  const int* __restrict__ tm, const int64_t* __restrict__ tbase,
+                                  const int64_t* __restrict__ tstart, const int* __restrict__ foff, double k,
+                                  double H, const double2* __restrict__ oc, const double2* __restrict__ ot,
+                                  const double2* __restrict__ onu, const double* __restrict__ oh,
+                                  cplx* __restrict__ tval, unsigned long long* __restrict__ stat) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long np = 0, nq = 0;
+  if (gi < tstart[ntab]) {
+    int lo = 0, hi = ntab - 1;                       // table of entry gi
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tstart[mid] <= gi) lo = mid; else hi = mid - 1;
+    }
+    const int t = lo;
+    const int A = tA[t], B = tB[t];
+    const int nb = foff[B + 1] - foff[B];
+    const int64_t local = gi - tstart[t];
+    const int a = (int)(local / nb), b = (int)(local % nb);
+    const int e = foff[A] + a, f = foff[B] + b;
+    const double2 x = oc[e], nx = onu[e];
+    double2 c = oc[f];
+    c.y += tm[t] * H;
+    const double hh = oh[f];
+    const double q = sqrt((x.x - c.x) * (x.x - c.x) + (x.y - c.y) * (x.y - c.y)) / hh;
+    const int g = gl_order(q, 0);
+    cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
+    pair4_f64(k, x, nx, c, ot[f], onu[f], hh, g, S, Dv, K, T);
+    cplx* tv = tval + 4 * (tbase[t] + local);
+    tv[0] = S;
+    tv[1] = Dv;
+    tv[2] = K;
+    tv[3] = T;
+    np = 1;
+    nq = g;
+  }
+  if (stat) {
+    np = warp_sum_u64(np);
+    nq = warp_sum_u64(nq);
+    if ((threadIdx.x & 31) == 0 && np) {
+      atomicAdd(&stat[0], np);
+      atomicAdd(&stat[1], nq);
+    }
+  }
+}
+
 __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restrict__ bb, const int* __restrict__ be,
                                   const int64_t* __restrict__ base, const int* __restrict__ sbase,
                                   const int* __restrict__ srcf, const int* __restrict__ srcm, double k, double eta,
@@ -864,6 +921,10 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
                                   const int* __restrict__ perm, const int* __restrict__ ofib,
                                   const int* __restrict__ foff, const int* __restrict__ sm0,
                                   const int64_t* __restrict__ kbase, const cplx* __restrict__ kval,
+                                  const int* __restrict__ pl_ptr, const int* __restrict__ pl_fib,
+                                  const int* __restrict__ pl_img, const int* __restrict__ pl_tab,
+                                  const int64_t* __restrict__ tab_base, const int* __restrict__ tab_nb,
+                                  const cplx* __restrict__ tab_val,
                                   cplx* __restrict__ val, cplxf* __restrict__ valf,
                                   unsigned long long* __restrict__ stat) {
   const int li = blockIdx.x;
@@ -889,10 +950,25 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
         const int ef = perm[f];
         // same fiber and, in true coordinates, the same image (the wrapped copies
         // differ by m + m0_s - m0_f periods): the pair is a rotation of a table entry
-        if (kb >= 0 && ofib[ef] == fs && m + ms - sm0[f] == 0) {
+        const int ff = ofib[ef], mt = m + ms - sm0[f];
+        int tab = -1;
+        if (!(ff == fs && mt == 0) && pl_ptr)
+          for (int q = pl_ptr[fs]; q < pl_ptr[fs + 1]; ++q)
+            if (pl_fib[q] == ff && pl_img[q] == mt) {
+              tab = pl_tab[q];
+              break;
+            }
+        if (kb >= 0 && ff == fs && mt == 0) {
           int dl = ef - es;
           if (dl < 0) dl += fN;
           const cplx* tv = kval + 4 * (kb + dl);
+          S = tv[0];
+          Dv = tv[1];
+          K = tv[2];
+          T = tv[3];
+        } else if (tab >= 0) {
+          // a translated copy of a fiber pair whose integrals are tabulated
+          const cplx* tv = tab_val + 4 * (tab_base[tab] + (int64_t)(es - foff[fs]) * tab_nb[tab] + (ef - foff[ff]));
           S = tv[0];
           Dv = tv[1];
           K = tv[2];
@@ -937,12 +1013,6 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
 // same-fiber sources (k1, eq. 5), plus on the diagonal the self terms of both
 // wavenumbers (-i eta S_ee(k) and c2 T_ee(k) of the k part, whose remainder
 // comes from the FMM).  One warp per target element.
-__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
 // One thread per (row element e, source f) of the same fiber; rows lists the
 // elements whose row pairs are stored (the first element of a circulant fiber,
 // every element of the others).  For a regular-polygon fiber (kbase >= 0) the
@@ -1044,11 +1114,20 @@ cudaError_t k_build_caches(pfmbem* h) {
       h->fb_rows, h->o_fiber, h->fib_off, h->fb_base, h->k, h->k1, h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu,
       h->o_h, h->self4, h->kt_base, h->kt_val, h->fb_val, h->fb_valf, h->stat_dev);
   prof_end(h, PH_BUILD);
+  if (h->ntab > 0) {
+    prof_begin(h, PH_BUILD);
+    pair_table_kernel<<<(unsigned)((h->tab_entries + 255) / 256), 256, 0, st>>>(
+        h->ntab, h->tab_A, h->tab_B, h->tab_m, h->tab_start, h->tab_start, h->fib_off, h->k, h->H, h->o_c, h->o_t,
+        h->o_nu, h->o_h, h->tab_val, h->stat_dev);
+    prof_end(h, PH_BUILD);
+  }
   prof_begin(h, PH_BUILD);
   near_build_kernel<<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
                                               h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c, h->s_t,
                                               h->s_nu, h->s_h, h->s_perm, h->o_fiber, h->fib_off, h->s_m0,
-                                              h->kt_base, h->kt_val, h->nc_val, h->nc_valf, h->stat_dev);
+                                              h->kt_base, h->kt_val, h->ntab > 0 ? h->pl_ptr : nullptr, h->pl_fib,
+                                              h->pl_img, h->pl_tab, h->tab_start, h->tab_nb, h->tab_val, h->nc_val,
+                                              h->nc_valf, h->stat_dev);
   prof_end(h, PH_BUILD);
   return cudaGetLastError();
 }
