@@ -263,8 +263,8 @@ void gauss_legendre(int n, double* x, double* w) {
 // key from it.  Nothing happens unless two fibers are congruent.
 static pfmbem_status build_pair_tables(pfmbem* h, const double* nodes, const std::vector<int>& foff,
                                        const std::vector<int>& fib, const std::vector<int>& m0,
-                                       const std::vector<int>& perm, const std::vector<int>& nc_sbase,
-                                       const std::vector<int>& nc_src, const std::vector<int>& nc_img) {
+                                       const std::vector<int>& perm, const std::vector<int>& nl_ptr,
+                                       const std::vector<int>& nl_src, const std::vector<int>& nl_img) {
   const int M = h->M, D = h->D;
   const double H = h->H, tol = 1e-12 * H;
   // ---- classes
@@ -308,21 +308,42 @@ static pfmbem_status build_pair_tables(pfmbem* h, const double* nodes, const std
   auto pack = [](int A, int B, int m) {
     return ((unsigned long long)(unsigned)A << 32) | ((unsigned long long)(unsigned)B << 8) | (unsigned)(m + 64);
   };
+  // distinct (fiber, m0) of every leaf (a leaf's elements of one fiber are
+  // contiguous: the sort by leaf key is stable and the input is fiber-major)
+  std::vector<int> run_ptr(Lf.nbox + 1, 0);
+  std::vector<std::pair<int, int>> runs;
+  {
+    std::vector<int> first(Lf.nbox, -1), count(Lf.nbox, 0);
+    for (int b : Lf.hne) {
+      first[b] = (int)runs.size();
+      for (int s2 = Lf.hbegin[b]; s2 < Lf.hend[b]; ++s2) {
+        const int e = perm[s2];
+        const std::pair<int, int> v{fib[e], m0[e]};
+        bool seen = false;
+        for (int r = first[b]; r < (int)runs.size() && !seen; ++r) seen = runs[r] == v;
+        if (!seen) runs.push_back(v);
+      }
+      count[b] = (int)runs.size() - first[b];
+    }
+    for (int b = 0; b < Lf.nbox; ++b) run_ptr[b + 1] = run_ptr[b] + (first[b] >= 0 ? count[b] : 0);
+    std::vector<std::pair<int, int>> ordered;
+    ordered.reserve(runs.size());
+    for (int b = 0; b < Lf.nbox; ++b)
+      if (first[b] >= 0) ordered.insert(ordered.end(), runs.begin() + first[b], runs.begin() + first[b] + count[b]);
+    runs.swap(ordered);
+  }
   std::vector<std::pair<int, int>> T;                     // (fiber, m0) of the leaf's targets
   std::vector<std::array<int, 3>> S;                      // (fiber, m0, m) of its sources
   for (size_t li = 0; li < Lf.hne.size(); ++li) {
     const int b = Lf.hne[li];
-    T.clear();
+    T.assign(runs.begin() + run_ptr[b], runs.begin() + run_ptr[b + 1]);
     S.clear();
-    for (int s2 = Lf.hbegin[b]; s2 < Lf.hend[b]; ++s2) {
-      const int e = perm[s2];
-      if (T.empty() || T.back().first != fib[e] || T.back().second != m0[e]) T.push_back({fib[e], m0[e]});
-    }
-    for (int j = nc_sbase[li]; j < nc_sbase[li + 1]; ++j) {
-      const int e = perm[nc_src[j]];
-      const std::array<int, 3> v{fib[e], m0[e], nc_img[j]};
-      if (!S.empty() && S.back() == v) continue;
-      if (std::find(S.begin(), S.end(), v) == S.end()) S.push_back(v);
+    for (int j = nl_ptr[li]; j < nl_ptr[li + 1]; ++j) {
+      const int sb = nl_src[j];
+      for (int r = run_ptr[sb]; r < run_ptr[sb + 1]; ++r) {
+        const std::array<int, 3> v{runs[r].first, runs[r].second, nl_img[j]};
+        if (std::find(S.begin(), S.end(), v) == S.end()) S.push_back(v);
+      }
     }
     for (auto& t : T)
       for (auto& sv : S) {
@@ -580,9 +601,12 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   const int nD = 1 << D;
   std::vector<int64_t> nc_base;
   std::vector<int> nc_sbase(1, 0), nc_src, nc_img;
+  std::vector<int> nl_ptr(1, 0), nl_src, nl_img;      // near lists of the leaves: source leaf, image m
   {
     Level& Lf = h->lev[D];
-    std::vector<int> ptr(1, 0), src, img;
+    std::vector<int>& ptr = nl_ptr;
+    std::vector<int>& src = nl_src;
+    std::vector<int>& img = nl_img;
     for (int b : Lf.hne) {
       int ix = 0, iy = 0;
       for (int bb = 0; bb < D; ++bb) { ix |= ((b >> (2 * bb)) & 1) << bb; iy |= ((b >> (2 * bb + 1)) & 1) << bb; }
@@ -814,7 +838,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       for (int s2 = 0; s2 < E; ++s2) sm0[s2] = m0[perm[s2]];
       if ((st = upload(h, &h->kt_base, kbase)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->s_m0, sm0)) != PFMBEM_OK) return st;
-      if ((st = build_pair_tables(h, nodes, foff, fib, m0, perm, nc_sbase, nc_src, nc_img)) != PFMBEM_OK) return st;
+      if ((st = build_pair_tables(h, nodes, foff, fib, m0, perm, nl_ptr, nl_src, nl_img)) != PFMBEM_OK) return st;
       h->kt_val = dalloc<cplx>(h, (size_t)4 * kacc);
       if (!h->kt_val) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
       h->nchunk = (int)chunks.size() / 3;
