@@ -73,7 +73,12 @@ typedef struct {
                        device-wide barrier between the stages (default; the tensor-core
                        M2L and devices without cooperative launch use 1); 1 = one kernel
                        per stage */
-  int reserved[4];
+  int precond;      /* 0 = right block-Jacobi preconditioner over the fibers (default):
+                       each fiber's same-fiber block of (I - A) (both wavenumbers, self
+                       terms) inverted exactly by FFT where the fiber is a regular
+                       polygon with 2^j elements, identity elsewhere; flexible GMRES.
+                       1 = none */
+  int reserved[3];
 } pfmbem_options;
 
 /* Outcome of a solve. */
@@ -146,7 +151,9 @@ pfmbem_status pfmbem_rhs(pfmbem_t h, double* B);
  * (x and y must not overlap).  precision: PFMBEM_FP64 or PFMBEM_MIXED. */
 pfmbem_status pfmbem_matvec(pfmbem_t h, const double* x, double* y, int precision);
 
-/* Solve (I - A) Psi = B by restarted GMRES (Sec. 4: "GMRES").
+/* Solve (I - A) Psi = B by restarted GMRES (Sec. 4: "GMRES"), right-preconditioned
+ * by the fibers' inverse same-fiber blocks unless options.precond = 1 (flexible
+ * GMRES: the preconditioned directions are kept).
  *   B     complex [2E] right-hand side, or NULL for the incident-wave B of eq. 9
  *   psi   complex [2E]; input initial guess if use_guess != 0, output solution
  *   tol   relative residual target (FP64 true residual)

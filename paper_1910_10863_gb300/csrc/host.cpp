@@ -1083,6 +1083,12 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       h->fh_valf = dalloc<cplxf>(h, (size_t)4 * fa);
       if (!h->fh_val || !h->fh_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber symbols)");
       CK(k_fiber_symbols(h));
+      if (h->opt.precond == 0 && h->fz_nfft > 0) {
+        h->pc_val = dalloc<cplx>(h, (size_t)4 * fa);
+        h->pc_valf = dalloc<cplxf>(h, (size_t)4 * fa);
+        if (!h->pc_val || !h->pc_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (preconditioner)");
+        CK(k_precond_symbols(h));
+      }
       bool ok = false;
       CK(k_fused_prepare(h, &ok));
       if (ok) {
@@ -1104,6 +1110,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         CK(cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned), h->stream));
         CK(cudaMemsetAsync(h->fz_err, 0, sizeof(int), h->stream));
         h->fused = true;
+        h->pc = h->pc_val != nullptr;
       }
     }
   }
@@ -1200,7 +1207,8 @@ static pfmbem_status gmres_alloc(pfmbem* h, int m) {
   g.c = dalloc<cplx>(h, n);
   g.hcol = dalloc<cplx>(h, 2 * (m + 2));
   g.nrm = dalloc<double>(h, 2);
-  if (!g.V || !g.w || !g.r || !g.x || !g.b || !g.d || !g.c || !g.hcol || !g.nrm)
+  if (h->pc) g.Z = dalloc<cplx>(h, (size_t)m * n);
+  if (!g.V || !g.w || !g.r || !g.x || !g.b || !g.d || !g.c || !g.hcol || !g.nrm || (h->pc && !g.Z))
     return fail(h, PFMBEM_ENOMEM, "GMRES workspace");
   g.hhost = pinned_small_get();
   if (!g.hhost) return fail(h, PFMBEM_ENOMEM, "pinned host buffer");
@@ -1211,7 +1219,10 @@ static inline std::complex<double> toz(cplx a) { return {a.re, a.im}; }
 
 // Restarted GMRES(m) with classical Gram-Schmidt applied twice; A is applied by
 // the FMM matvec in the given precision.  Solves A x = b in place of x (device).
-// Restarted GMRES(m) with CGS2 Arnoldi.  With trust_estimate the solve ends as
+// Restarted GMRES(m) with CGS2 Arnoldi, flexibly right-preconditioned by the
+// fibers' inverse same-fiber blocks when the handle has them (Sec. 4 solves
+// with a preconditioned GMRES; this is the block-Jacobi choice).  With
+// trust_estimate the solve ends as
 // soon as the Arnoldi residual estimate falls below tol/2, without recomputing
 // the true residual (inner solves of the refinement, whose outer loop computes
 // the FP64 residual anyway).
@@ -1257,7 +1268,14 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
     for (; j < m && iters < maxit; ++j) {
       cplx* vj = g.V + (size_t)j * n;
       cplx* vj1 = g.V + (size_t)(j + 1) * n;
-      CK(k_matvec(h, vj, g.w, precision));
+      if (h->pc) {
+        // flexible right preconditioning: z_j = P^-1 v_j, w = A z_j
+        cplx* zj = g.Z + (size_t)j * n;
+        CK(k_precond_apply(h, vj, zj, precision));
+        CK(k_matvec(h, zj, g.w, precision));
+      } else {
+        CK(k_matvec(h, vj, g.w, precision));
+      }
       ++iters;
       // CGS2
       CK(k_multidot(h, g.V, j + 1, g.w, n, g.hcol));
@@ -1306,7 +1324,7 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
     }
     for (int i = 0; i < j; ++i) g.hhost[i] = cplx{y[i].real(), y[i].imag()};
     CK(cudaMemcpyAsync(g.hcol, g.hhost, sizeof(cplx) * j, cudaMemcpyHostToDevice, h->stream));
-    CK(k_gemv_add(h, g.V, j, g.hcol, x, n));
+    CK(k_gemv_add(h, h->pc ? g.Z : g.V, j, g.hcol, x, n));   // x += Z y (flexible) or V y
     ++restarts;
   }
   *iters_out = iters;

@@ -71,6 +71,7 @@ struct GmresWork {
   cplx* b = nullptr;        // [n]
   cplx* d = nullptr;        // [n] FP64 residual of the refinement
   cplx* c = nullptr;        // [n] correction of the refinement
+  cplx* Z = nullptr;        // [m][n] preconditioned basis (flexible GMRES)
   cplx* hcol = nullptr;     // [m+2] device dot results
   double* nrm = nullptr;    // [2]
   cplx* hhost = nullptr;    // pinned host mirror of hcol
@@ -194,6 +195,9 @@ struct pfmbem {
   int64_t* fh_base = nullptr;    // [M] first frequency of the fiber's block symbol (-1: none)
   cplx* fh_val = nullptr;        // [sum N][4] block symbols B^(r,s)(k)
   cplxf* fh_valf = nullptr;
+  bool pc = false;               // block-Jacobi preconditioner available
+  cplx* pc_val = nullptr;        // [sum N][4] inverse block symbols of the whole same-fiber blocks
+  cplxf* pc_valf = nullptr;
   cplx* tw = nullptr;            // [512] e^{2 pi i j / 1024}
   cplxf* twf = nullptr;
   int fz_nchunk = 0;             // row chunks of the other fibers
@@ -237,6 +241,8 @@ cudaError_t k_build_caches(pfmbem* h);
 cudaError_t k_fused_prepare(pfmbem* h, bool* ok);
 cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_fiber_symbols(pfmbem* h);
+cudaError_t k_precond_symbols(pfmbem* h);
+cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_build_fmm_caches(pfmbem* h);
 // learned warm start (mlp.cu)
 cudaError_t k_warm_features(pfmbem* h, float* x_dev);

@@ -292,6 +292,84 @@ __device__ __forceinline__ void near_row(const FusedArgs<C>& a, int s, int lane)
   }
 }
 
+// Inverse block symbol of a regular-polygon fiber's whole same-fiber block of
+// (I - A): the k1 part with the self terms (symbol fh, built above) plus the
+// same-fiber k part, whose row pair is (i/4) (D, -i eta S) and c2 (i/4) (T,
+// -i eta K) of the fiber's k table (Sec. 2: U, dU restricted to the fiber).
+// The 2x2 symbol is inverted per frequency.  One block per fiber.
+__global__ void precond_symbol_kernel(const int* __restrict__ fib_list, const int* __restrict__ foff,
+                                      const int64_t* __restrict__ kbase, const cplx* __restrict__ kval,
+                                      const int64_t* __restrict__ fh_base, const cplx* __restrict__ fh,
+                                      double eta, cplx c2, const cplx* __restrict__ tw, cplx* __restrict__ pc,
+                                      cplxf* __restrict__ pcf) {
+  extern __shared__ unsigned char smraw[];
+  cplx* sq = reinterpret_cast<cplx*>(smraw);      // [4][N]
+  const int fb = fib_list[blockIdx.x];
+  const int N = foff[fb + 1] - foff[fb], lg = __ffs(N) - 1;
+  const cplx* kv = kval + 4 * kbase[fb];
+  const cplx q4{0.0, 0.25};                       // i/4
+  const cplx mie{0.0, -eta};                      // -i eta
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
+    const cplx S = kv[4 * t], D = kv[4 * t + 1], K = kv[4 * t + 2], T = kv[4 * t + 3];
+    sq[t] = q4 * D;
+    sq[N + t] = q4 * (mie * S);
+    sq[2 * N + t] = c2 * (q4 * T);
+    sq[3 * N + t] = c2 * (q4 * (mie * K));
+  }
+  block_fft(sq, 4, lg, +1, tw);
+  const cplx* B = fh + 4 * fh_base[fb];
+  cplx* out = pc + 4 * fh_base[fb];
+  cplxf* outf = pcf + 4 * fh_base[fb];
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const cplx a = B[4 * k] + sq[k], b = B[4 * k + 1] + sq[N + k];
+    const cplx c = B[4 * k + 2] + sq[2 * N + k], d = B[4 * k + 3] + sq[3 * N + k];
+    const cplx det = a * d - b * c;
+    const cplx id = cdiv(cplx{1, 0}, det);
+    const cplx v[4] = {d * id, -(b * id), -(c * id), a * id};
+    for (int j = 0; j < 4; ++j) {
+      out[4 * k + j] = v[j];
+      outf[4 * k + j] = to_f(v[j]);
+    }
+  }
+}
+
+// y = P^{-1} x (original order, FP64 in and out, arithmetic in C): per fiber,
+// y^(r) = IFFT( sum_s Binv^(r,s) FFT(x^(s)) ) where a symbol exists, y = x
+// elsewhere.  One block per fiber.
+template <class C>
+__global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const int64_t* __restrict__ fh_base,
+                                     const C* __restrict__ pc, const C* __restrict__ tw, const cplx* __restrict__ x,
+                                     cplx* __restrict__ y) {
+  extern __shared__ unsigned char smraw[];
+  C* xs = reinterpret_cast<C*>(smraw);            // [2][N]
+  const int fb = blockIdx.x;
+  const int f0 = foff[fb], N = foff[fb + 1] - f0;
+  const int64_t base = fh_base[fb];
+  if (base < 0) {
+    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) y[2 * f0 + t] = x[2 * f0 + t];
+    return;
+  }
+  const int lg = __ffs(N) - 1;
+  for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+    const int q = t >> lg, f = t & (N - 1);
+    xs[t] = from_d<C>(x[2 * (f0 + f) + q]);
+  }
+  block_fft(xs, 2, lg, -1, tw);
+  const C* Bi = pc + 4 * base;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const C x0 = xs[k], x1 = xs[N + k];
+    const C* bk = Bi + 4 * k;
+    xs[k] = bk[0] * x0 + bk[1] * x1;
+    xs[N + k] = bk[2] * x0 + bk[3] * x1;
+  }
+  block_fft(xs, 2, lg, +1, tw);
+  const double inv = 1.0 / N;
+  for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
+    const int r = t >> lg, e = f0 + (t & (N - 1));
+    y[2 * e + r] = inv * to_d(xs[t]);
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   extern __shared__ unsigned char smraw[];
@@ -711,6 +789,38 @@ cudaError_t k_fiber_symbols(pfmbem* h) {
   fiber_symbol_kernel<<<h->fz_nfft, 256, smem, h->stream>>>(h->fz_fft, h->fib_off, h->fb_base, h->fb_val, h->fh_base,
                                                             h->tw, h->fh_val, h->fh_valf);
   prof_end(h, PH_SETUP);
+  return cudaGetLastError();
+}
+
+cudaError_t k_precond_symbols(pfmbem* h) {
+  if (h->fz_nfft == 0) return cudaSuccess;
+  const size_t smem = 4 * (size_t)h->max_fiber * sizeof(cplx);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(precond_symbol_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  prof_begin(h, PH_SETUP);
+  precond_symbol_kernel<<<h->fz_nfft, 256, smem, h->stream>>>(h->fz_fft, h->fib_off, h->kt_base, h->kt_val,
+                                                              h->fh_base, h->fh_val, h->eta, cplx{h->c2re, h->c2im},
+                                                              h->tw, h->pc_val, h->pc_valf);
+  prof_end(h, PH_SETUP);
+  return cudaGetLastError();
+}
+
+cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision) {
+  const bool f32 = precision == PFMBEM_MIXED;
+  const size_t smem = 2 * (size_t)h->max_fiber * (f32 ? sizeof(cplxf) : sizeof(cplx));
+  prof_begin(h, PH_BLAS);
+  if (f32) {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(precond_apply_kernel<cplxf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    precond_apply_kernel<cplxf><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_valf, h->twf, x, y);
+  } else {
+    if (smem > 48 * 1024)
+      cudaFuncSetAttribute(precond_apply_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    precond_apply_kernel<cplx><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_val, h->tw, x, y);
+  }
+  prof_end(h, PH_BLAS);
   return cudaGetLastError();
 }
 

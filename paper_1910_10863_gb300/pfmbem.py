@@ -24,7 +24,8 @@ class Options(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("p_min", ctypes.c_int), ("eta", ctypes.c_double),
                 ("leaf_max", ctypes.c_int), ("depth", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("precision", ctypes.c_int), ("near_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int),
-                ("profile", ctypes.c_int), ("launch", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+                ("profile", ctypes.c_int), ("launch", ctypes.c_int), ("precond", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class Info(ctypes.Structure):

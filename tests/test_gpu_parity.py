@@ -308,3 +308,35 @@ def test_wrapped_and_single_fiber_blocks(pf, make):
         info = s.solve(psi, tol=1e-9, maxit=400)
         assert info.rel_residual <= 1e-9
         assert rel(psi, np.linalg.solve(Mo, bem.rhs(pb))) < 1e-6
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_block_jacobi_preconditioner_same_solution_fewer_iterations(pf, prec):
+    """The right block-Jacobi preconditioner (inverse same-fiber blocks by FFT)
+    changes the iteration count, not the solution: both solves match dense LU."""
+    w = W.square_2x2_n64()
+    pb, Mo, Bo = oracle_system(w)
+    psi_ref = np.linalg.solve(Mo, Bo)
+    p = pf.FP64 if prec == "fp64" else pf.MIXED
+    res = {}
+    for pc in (0, 1):
+        s = pf.Solver(w, precision=p, precond=pc)
+        psi = np.zeros(2 * s.E, dtype=np.complex128)
+        info = s.solve(psi, tol=1e-8, maxit=500)
+        assert info.rel_residual <= 1e-8
+        assert rel(psi, psi_ref) < 1e-6
+        res[pc] = info.iters
+    assert res[0] < res[1], res
+
+
+def test_block_jacobi_full_size_hexagon(pf):
+    w = W.hexagon_8x8_n256()
+    its = {}
+    for pc in (0, 1):
+        s = pf.Solver(w, precision=pf.MIXED, precond=pc)
+        psi = np.zeros(2 * s.E, dtype=np.complex128)
+        info = s.solve(psi, tol=1e-6)
+        assert info.rel_residual <= 1e-6
+        its[pc] = (info.iters, psi)
+    assert its[0][0] < its[1][0]
+    assert rel(its[0][1], its[1][1]) < 1e-5
