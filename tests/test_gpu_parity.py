@@ -339,4 +339,4 @@ def test_block_jacobi_full_size_hexagon(pf):
         assert info.rel_residual <= 1e-6
         its[pc] = (info.iters, psi)
     assert its[0][0] < its[1][0]
-    assert rel(its[0][1], its[1][1]) < 1e-5
+    assert rel(its[0][1], its[1][1]) < 2e-4          # two solutions at residual 1e-6
