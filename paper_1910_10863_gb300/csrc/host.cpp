@@ -1089,6 +1089,30 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         if (!h->pc_val || !h->pc_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (preconditioner)");
         CK(k_precond_symbols(h));
       }
+      if (h->opt.precond == 0) {
+        // the other regular polygons: preconditioner kept as a circulant row pair
+        std::vector<int> prl;
+        std::vector<int64_t> prb(M, -1);
+        int64_t pa = 0;
+        for (int i = 0; i < M; ++i) {
+          const int n = foff[i + 1] - foff[i];
+          if (circh[i] && fhb[i] < 0) {
+            prl.push_back(i);
+            prb[i] = pa;
+            pa += 4 * (int64_t)n;
+          }
+        }
+        if (!prl.empty()) {
+          h->npr = (int)prl.size();
+          if ((st = upload(h, &h->pr_list, prl)) != PFMBEM_OK) return st;
+          if ((st = upload(h, &h->pr_base, prb)) != PFMBEM_OK) return st;
+          if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
+          h->pr_val = dalloc<cplx>(h, (size_t)pa);
+          h->pr_valf = dalloc<cplxf>(h, (size_t)pa);
+          if (!h->pr_val || !h->pr_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (preconditioner)");
+          CK(k_precond_rows(h));
+        }
+      }
       bool ok = false;
       CK(k_fused_prepare(h, &ok));
       if (ok) {
@@ -1110,7 +1134,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         CK(cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned), h->stream));
         CK(cudaMemsetAsync(h->fz_err, 0, sizeof(int), h->stream));
         h->fused = true;
-        h->pc = h->pc_val != nullptr;
+        h->pc = h->pc_val != nullptr || h->pr_val != nullptr;
       }
     }
   }

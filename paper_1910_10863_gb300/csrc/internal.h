@@ -198,6 +198,11 @@ struct pfmbem {
   bool pc = false;               // block-Jacobi preconditioner available
   cplx* pc_val = nullptr;        // [sum N][4] inverse block symbols of the whole same-fiber blocks
   cplxf* pc_valf = nullptr;
+  int npr = 0;                   // regular-polygon fibers whose element count is not 2^j
+  int* pr_list = nullptr;
+  int64_t* pr_base = nullptr;    // [M] their preconditioner row pairs (-1: none)
+  cplx* pr_val = nullptr;        // [sum 4N]
+  cplxf* pr_valf = nullptr;
   cplx* tw = nullptr;            // [512] e^{2 pi i j / 1024}
   cplxf* twf = nullptr;
   int fz_nchunk = 0;             // row chunks of the other fibers
@@ -243,6 +248,7 @@ cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_fiber_symbols(pfmbem* h);
 cudaError_t k_precond_symbols(pfmbem* h);
 cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision);
+cudaError_t k_precond_rows(pfmbem* h);
 cudaError_t k_build_fmm_caches(pfmbem* h);
 // learned warm start (mlp.cu)
 cudaError_t k_warm_features(pfmbem* h, float* x_dev);

@@ -333,20 +333,114 @@ __global__ void precond_symbol_kernel(const int* __restrict__ fib_list, const in
   }
 }
 
+// Preconditioner of a regular-polygon fiber whose element count is not a power
+// of two: the same block-circulant inverse as above, kept as the row pair of
+// its first element.  The 2x2 blocks b_d = k1 part (stored rows) + k part (k
+// table) are transformed by a direct DFT, B(k) = sum_d b_d e^{2 pi i k d / N},
+// inverted per frequency, and transformed back, c_d = (1/N) sum_k B(k)^-1
+// e^{-2 pi i k d / N}; rows[r][2d + s] = c_d^(r,s).  One block per fiber.
+__global__ void precond_rows_kernel(const int* __restrict__ fib_list, const int* __restrict__ foff,
+                                    const int64_t* __restrict__ fb_base, const cplx* __restrict__ fbrows,
+                                    const int64_t* __restrict__ kbase, const cplx* __restrict__ kval, double eta,
+                                    cplx c2, const int64_t* __restrict__ pr_base, cplx* __restrict__ pr,
+                                    cplxf* __restrict__ prf) {
+  extern __shared__ unsigned char smraw[];
+  cplx* b = reinterpret_cast<cplx*>(smraw);        // [4][N] blocks b_d, later B(k)^-1
+  cplx* bh = b + 4 * (size_t)(foff[fib_list[blockIdx.x] + 1] - foff[fib_list[blockIdx.x]]);   // [4][N]
+  const int fb = fib_list[blockIdx.x];
+  const int N = foff[fb + 1] - foff[fb];
+  const cplx* R = fbrows + fb_base[fb];
+  const cplx* kv = kval + 4 * kbase[fb];
+  const cplx q4{0.0, 0.25}, mie{0.0, -eta};
+  for (int d = threadIdx.x; d < N; d += blockDim.x) {
+    const cplx S = kv[4 * d], D = kv[4 * d + 1], K = kv[4 * d + 2], T = kv[4 * d + 3];
+    b[d] = R[2 * d] + q4 * D;
+    b[N + d] = R[2 * d + 1] + q4 * (mie * S);
+    b[2 * N + d] = R[2 * N + 2 * d] + c2 * (q4 * T);
+    b[3 * N + d] = R[2 * N + 2 * d + 1] + c2 * (q4 * (mie * K));
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    cplx a[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int d = 0; d < N; ++d) {
+      double sn, cs;
+      sincospi(2.0 * (double)(((long long)k * d) % N) / N, &sn, &cs);
+      const cplx w{cs, sn};
+      for (int j = 0; j < 4; ++j) a[j] += b[j * N + d] * w;
+    }
+    const cplx det = a[0] * a[3] - a[1] * a[2];
+    const cplx id = cdiv(cplx{1, 0}, det);
+    bh[k] = a[3] * id;
+    bh[N + k] = -(a[1] * id);
+    bh[2 * N + k] = -(a[2] * id);
+    bh[3 * N + k] = a[0] * id;
+  }
+  __syncthreads();
+  cplx* out = pr + pr_base[fb];
+  cplxf* outf = prf + pr_base[fb];
+  for (int d = threadIdx.x; d < N; d += blockDim.x) {
+    cplx c[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+    for (int k = 0; k < N; ++k) {
+      double sn, cs;
+      sincospi(-2.0 * (double)(((long long)k * d) % N) / N, &sn, &cs);
+      const cplx w{cs, sn};
+      for (int j = 0; j < 4; ++j) c[j] += bh[j * N + k] * w;
+    }
+    const double inv = 1.0 / N;
+    const cplx v[4] = {inv * c[0], inv * c[1], inv * c[2], inv * c[3]};
+    out[2 * d] = v[0];
+    out[2 * d + 1] = v[1];
+    out[2 * N + 2 * d] = v[2];
+    out[2 * N + 2 * d + 1] = v[3];
+    outf[2 * d] = to_f(v[0]);
+    outf[2 * d + 1] = to_f(v[1]);
+    outf[2 * N + 2 * d] = to_f(v[2]);
+    outf[2 * N + 2 * d + 1] = to_f(v[3]);
+  }
+}
+
 // y = P^{-1} x (original order, FP64 in and out, arithmetic in C): per fiber,
 // y^(r) = IFFT( sum_s Binv^(r,s) FFT(x^(s)) ) where a symbol exists, y = x
 // elsewhere.  One block per fiber.
 template <class C>
 __global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const int64_t* __restrict__ fh_base,
-                                     const C* __restrict__ pc, const C* __restrict__ tw, const cplx* __restrict__ x,
-                                     cplx* __restrict__ y) {
+                                     const C* __restrict__ pc, const C* __restrict__ tw,
+                                     const int64_t* __restrict__ pr_base, const C* __restrict__ pr,
+                                     const cplx* __restrict__ x, cplx* __restrict__ y) {
   extern __shared__ unsigned char smraw[];
   C* xs = reinterpret_cast<C*>(smraw);            // [2][N]
   const int fb = blockIdx.x;
   const int f0 = foff[fb], N = foff[fb + 1] - f0;
   const int64_t base = fh_base[fb];
   if (base < 0) {
-    for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) y[2 * f0 + t] = x[2 * f0 + t];
+    const int64_t rb = pr_base ? pr_base[fb] : -1;
+    if (rb < 0) {
+      for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) y[2 * f0 + t] = x[2 * f0 + t];
+      return;
+    }
+    // block-circulant inverse from its row pair: y[2e + r] = sum_c R_r[c] x[(c + 2e) mod 2N]
+    const int n2 = 2 * N;
+    for (int t = threadIdx.x; t < n2; t += blockDim.x) xs[t] = from_d<C>(x[2 * f0 + t]);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const C* R0 = pr + rb;
+    const C* R1 = R0 + n2;
+    for (int r = 2 * warp; r < n2; r += 2 * nw) {
+      C a0{0, 0}, a1{0, 0};
+      for (int c = lane; c < n2; c += 32) {
+        int i = c + r;
+        if (i >= n2) i -= n2;
+        const C xv = xs[i];
+        a0 += R0[c] * xv;
+        a1 += R1[c] * xv;
+      }
+      a0 = wsum(a0);
+      a1 = wsum(a1);
+      if (lane == 0) {
+        y[2 * f0 + r] = to_d(a0);
+        y[2 * f0 + r + 1] = to_d(a1);
+      }
+    }
     return;
   }
   const int lg = __ffs(N) - 1;
@@ -807,6 +901,21 @@ cudaError_t k_precond_symbols(pfmbem* h) {
   return cudaGetLastError();
 }
 
+cudaError_t k_precond_rows(pfmbem* h) {
+  if (h->npr == 0) return cudaSuccess;
+  const size_t smem = 8 * (size_t)h->max_fiber * sizeof(cplx);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(precond_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  prof_begin(h, PH_SETUP);
+  precond_rows_kernel<<<h->npr, 256, smem, h->stream>>>(h->pr_list, h->fib_off, h->fb_base, h->fb_val, h->kt_base,
+                                                        h->kt_val, h->eta, cplx{h->c2re, h->c2im}, h->pr_base,
+                                                        h->pr_val, h->pr_valf);
+  prof_end(h, PH_SETUP);
+  return cudaGetLastError();
+}
+
 cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision) {
   const bool f32 = precision == PFMBEM_MIXED;
   const size_t smem = 2 * (size_t)h->max_fiber * (f32 ? sizeof(cplxf) : sizeof(cplx));
@@ -814,11 +923,13 @@ cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision) {
   if (f32) {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(precond_apply_kernel<cplxf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    precond_apply_kernel<cplxf><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_valf, h->twf, x, y);
+    precond_apply_kernel<cplxf><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_valf, h->twf,
+                                                                h->pr_base, h->pr_valf, x, y);
   } else {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(precond_apply_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    precond_apply_kernel<cplx><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_val, h->tw, x, y);
+    precond_apply_kernel<cplx><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_val, h->tw,
+                                                               h->pr_base, h->pr_val, x, y);
   }
   prof_end(h, PH_BLAS);
   return cudaGetLastError();

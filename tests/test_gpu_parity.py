@@ -311,10 +311,12 @@ def test_wrapped_and_single_fiber_blocks(pf, make):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_block_jacobi_preconditioner_same_solution_fewer_iterations(pf, prec):
-    """The right block-Jacobi preconditioner (inverse same-fiber blocks by FFT)
-    changes the iteration count, not the solution: both solves match dense LU."""
-    w = W.square_2x2_n64()
+@pytest.mark.parametrize("make", SMALL)
+def test_block_jacobi_preconditioner_same_solution_fewer_iterations(pf, prec, make):
+    """The right block-Jacobi preconditioner (inverse same-fiber blocks, by FFT for
+    2^j elements and as a circulant row pair otherwise) changes the iteration
+    count, not the solution: both solves match dense LU."""
+    w = make()
     pb, Mo, Bo = oracle_system(w)
     psi_ref = np.linalg.solve(Mo, Bo)
     p = pf.FP64 if prec == "fp64" else pf.MIXED
