@@ -1392,7 +1392,14 @@ static pfmbem_status batch_enqueue(BInst& b) {
     CK(cudaMemcpyAsync(g.hhost, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   } else if (b.state == B_ARNOLDI) {
     cplx* vj = g.V + (size_t)b.j * n;
-    CK(k_matvec(h, vj, g.w, b.prec));
+    if (h->pc) {
+      // flexible right preconditioning, as in the single solve
+      cplx* zj = g.Z + (size_t)b.j * n;
+      CK(k_precond_apply(h, vj, zj, b.prec));
+      CK(k_matvec(h, zj, g.w, b.prec));
+    } else {
+      CK(k_matvec(h, vj, g.w, b.prec));
+    }
     CK(k_multidot(h, g.V, b.j + 1, g.w, n, g.hcol));
     CK(k_gemv_sub(h, g.V, b.j + 1, g.hcol, g.w, n));
     CK(k_multidot(h, g.V, b.j + 1, g.w, n, g.hcol + (m + 2)));
@@ -1419,7 +1426,7 @@ static pfmbem_status batch_finish_inner(BInst& b) {
   // the pinned mirror is free again: this instance's stream has synchronised
   for (int i = 0; i < j; ++i) g.hhost[i] = cplx{y[i].real(), y[i].imag()};
   CK(cudaMemcpyAsync(g.hcol, g.hhost, sizeof(cplx) * j, cudaMemcpyHostToDevice, h->stream));
-  CK(k_gemv_add(h, g.V, j, g.hcol, g.x, g.n));
+  CK(k_gemv_add(h, h->pc ? g.Z : g.V, j, g.hcol, g.x, g.n));
   b.zero_x = false;
   b.state = B_RESID;
   return PFMBEM_OK;

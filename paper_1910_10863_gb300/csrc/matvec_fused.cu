@@ -345,10 +345,16 @@ __global__ void precond_rows_kernel(const int* __restrict__ fib_list, const int*
                                     cplx c2, const int64_t* __restrict__ pr_base, cplx* __restrict__ pr,
                                     cplxf* __restrict__ prf) {
   extern __shared__ unsigned char smraw[];
-  cplx* b = reinterpret_cast<cplx*>(smraw);        // [4][N] blocks b_d, later B(k)^-1
-  cplx* bh = b + 4 * (size_t)(foff[fib_list[blockIdx.x] + 1] - foff[fib_list[blockIdx.x]]);   // [4][N]
   const int fb = fib_list[blockIdx.x];
   const int N = foff[fb + 1] - foff[fb];
+  cplx* b = reinterpret_cast<cplx*>(smraw);        // [4][N] blocks b_d
+  cplx* bh = b + 4 * (size_t)N;                    // [4][N] B(k)^-1
+  cplx* om = bh + 4 * (size_t)N;                   // [N] e^{2 pi i j / N}
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    double sn, cs;
+    sincospi(2.0 * j / N, &sn, &cs);
+    om[j] = cplx{cs, sn};
+  }
   const cplx* R = fbrows + fb_base[fb];
   const cplx* kv = kval + 4 * kbase[fb];
   const cplx q4{0.0, 0.25}, mie{0.0, -eta};
@@ -362,11 +368,11 @@ __global__ void precond_rows_kernel(const int* __restrict__ fib_list, const int*
   __syncthreads();
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     cplx a[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int d = 0; d < N; ++d) {
-      double sn, cs;
-      sincospi(2.0 * (double)(((long long)k * d) % N) / N, &sn, &cs);
-      const cplx w{cs, sn};
+    for (int d = 0, kd = 0; d < N; ++d) {          // kd = k d mod N
+      const cplx w = om[kd];
       for (int j = 0; j < 4; ++j) a[j] += b[j * N + d] * w;
+      kd += k;
+      if (kd >= N) kd -= N;
     }
     const cplx det = a[0] * a[3] - a[1] * a[2];
     const cplx id = cdiv(cplx{1, 0}, det);
@@ -380,11 +386,11 @@ __global__ void precond_rows_kernel(const int* __restrict__ fib_list, const int*
   cplxf* outf = prf + pr_base[fb];
   for (int d = threadIdx.x; d < N; d += blockDim.x) {
     cplx c[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
-    for (int k = 0; k < N; ++k) {
-      double sn, cs;
-      sincospi(-2.0 * (double)(((long long)k * d) % N) / N, &sn, &cs);
-      const cplx w{cs, sn};
+    for (int k = 0, kd = 0; k < N; ++k) {          // e^{-2 pi i k d / N} = conj(om[k d mod N])
+      const cplx w = conj(om[kd]);
       for (int j = 0; j < 4; ++j) c[j] += bh[j * N + k] * w;
+      kd += d;
+      if (kd >= N) kd -= N;
     }
     const double inv = 1.0 / N;
     const cplx v[4] = {inv * c[0], inv * c[1], inv * c[2], inv * c[3]};
@@ -903,7 +909,7 @@ cudaError_t k_precond_symbols(pfmbem* h) {
 
 cudaError_t k_precond_rows(pfmbem* h) {
   if (h->npr == 0) return cudaSuccess;
-  const size_t smem = 8 * (size_t)h->max_fiber * sizeof(cplx);
+  const size_t smem = 9 * (size_t)h->max_fiber * sizeof(cplx);
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(precond_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
