@@ -842,6 +842,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       h->kt_val = dalloc<cplx>(h, (size_t)4 * kacc);
       if (!h->kt_val) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
       h->nchunk = (int)chunks.size() / 3;
+      // queue of the near pairs integrated directly: every block in the worst case
+      h->nq_cap = (unsigned)std::min<int64_t>(h->nc_blocks, (int64_t)0xFFFFFFFFu);
+      h->nq = dalloc<unsigned long long>(h, std::max<size_t>(h->nq_cap, 1));
+      h->nq_len = dalloc<unsigned>(h, 1);
+      if (!h->nq || !h->nq_len) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near queue)");
       h->nc_val = dalloc<cplx>(h, (size_t)(4 * h->nc_blocks));
       h->nc_valf = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
       h->fb_val = dalloc<cplx>(h, (size_t)acc);
@@ -907,7 +912,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       std::vector<std::vector<int>> by(49);
       for (size_t ti = 0; ti < L.hne.size(); ++ti)
         for (int e = ptr[ti]; e < ptr[ti + 1]; ++e) by[off[e]].push_back(e);
-      std::vector<int> ptg, psr, pim, cof, cbg, cen;
+      std::vector<int> ptg, psr, pim, pof, cof, cbg, cen;
       for (int o = 0; o < 49; ++o) {
         for (size_t i = 0; i < by[o].size(); ++i) {
           if (i % 16 == 0) {
@@ -921,6 +926,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
           ptg.push_back(L.hne[ti]);
           psr.push_back(src[e]);
           pim.push_back(img[e]);
+          pof.push_back(o);
           cen.back() = (int)ptg.size();
         }
       }
@@ -959,6 +965,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if ((st = upload(h, &L.pr_tgt, ptg)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.pr_src, psr)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.pr_img, pim)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.pr_off, pof)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.ch_off, cof)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.ch_beg, cbg)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.ch_end, cen)) != PFMBEM_OK) return st;
@@ -1114,6 +1121,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         }
       }
       bool ok = false;
+      h->rootc = dalloc<cplx>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
+      h->rootcf = dalloc<cplxf>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
+      if (!h->rootc || !h->rootcf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (root operator)");
       CK(k_fused_prepare(h, &ok));
       if (ok) {
         std::vector<int> sli(E);

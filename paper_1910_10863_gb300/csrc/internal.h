@@ -36,6 +36,7 @@ struct Level {
   int* pr_tgt = nullptr;     // target box per pair
   int* pr_src = nullptr;     // source box per pair
   int* pr_img = nullptr;     // image m per pair
+  int* pr_off = nullptr;     // offset id per pair
   int* ch_off = nullptr;     // offset id per chunk
   int* ch_beg = nullptr;     // first pair of the chunk
   int* ch_end = nullptr;     // one past the last pair
@@ -161,6 +162,9 @@ struct pfmbem {
   int64_t* tab_start = nullptr;  // [ntab + 1] first entry of every table (4 values each)
   int* tab_nb = nullptr;         // [ntab] elements of the source fiber
   cplx* tab_val = nullptr;
+  unsigned long long* nq = nullptr;   // near pairs left to integrate directly (leaf, row, column)
+  unsigned* nq_len = nullptr;
+  unsigned nq_cap = 0;
   int* pl_ptr = nullptr;         // [M + 1] per target fiber: (source fiber, image shift) -> table
   int* pl_fib = nullptr;
   int* pl_img = nullptr;
@@ -214,6 +218,8 @@ struct pfmbem {
   unsigned long long* fz_stamp = nullptr;   // [32] stage end times (diagnostic)
   cplx* root = nullptr;          // [P0][P0] periodic root translation
   cplxf* rootf = nullptr;
+  cplx* rootc = nullptr;         // [4 P1][P0] root translation times the level-1 -> root M2M
+  cplxf* rootcf = nullptr;
   // matvec work
   cplx* dens = nullptr;          // sorted [E][2] = (phi', varphi')
   cplx* U = nullptr;             // sorted [E][2] = (U', dU')

@@ -856,6 +856,10 @@ __global__ void fiber_combine_f64_kernel(int E, const int* __restrict__ fib, con
 // Build: for leaf li with targets s in [bb, be) and the concatenated source list
 // (f, m) of its neighbour leaves, block (t, j) holds (i/4) alpha^m times
 // {D, -i eta S, T, -i eta K} of source f at target s (zero for f = s, m = 0).
+// Two launches: near_build_kernel fills every block read from a table (k table
+// of a regular polygon, fiber-pair table) and queues the rest, which
+// near_direct_kernel integrates one pair per thread, so that the Gauss ladder's
+// cost is spread evenly over the GPU instead of over one leaf's warps.
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -926,13 +930,13 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
                                   const int64_t* __restrict__ tab_base, const int* __restrict__ tab_nb,
                                   const cplx* __restrict__ tab_val,
                                   cplx* __restrict__ val, cplxf* __restrict__ valf,
-                                  unsigned long long* __restrict__ stat) {
+                                  unsigned long long* __restrict__ queue, unsigned* __restrict__ qlen,
+                                  unsigned qcap) {
   const int li = blockIdx.x;
   const int box = ne[li];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int s0 = bb[box], nt = be[box] - s0;
   const int j0 = sbase[li], ns = sbase[li + 1] - j0;
-  unsigned long long npair = 0, nquad = 0;
   for (int t = warp; t < nt; t += nw) {
     const int s = s0 + t;
     const double2 x = sc[s], nx = snu[s];
@@ -974,14 +978,11 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
           K = tv[2];
           T = tv[3];
         } else {
-          double2 c = sc[f];
-          c.y += m * H;
-          const double hh = sh[f];
-          const double q = sqrt((x.x - c.x) * (x.x - c.x) + (x.y - c.y) * (x.y - c.y)) / hh;
-          const int g = gl_order(q, 0);
-          ++npair;
-          nquad += g;
-          pair4_f64(k, x, nx, c, st[f], snu[f], hh, g, S, Dv, K, T);
+          // integrated by near_direct_kernel: queue (leaf, target row, source column)
+          const unsigned at = atomicAdd(qlen, 1u);
+          if (at < qcap)
+            queue[at] = ((unsigned long long)li << 40) | ((unsigned long long)t << 24) | (unsigned long long)j;
+          continue;
         }
         const cplx ph = mul_i(0.25 * ipow_phase(alpha, m));      // (i/4) alpha^m
         b0 = ph * Dv;
@@ -1001,9 +1002,51 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
       }
     }
   }
+}
+
+// The near-field pairs that no table covers, one thread each: the element
+// integrals by the Gauss ladder (as above), written into their blocks.
+__global__ void near_direct_kernel(const unsigned long long* __restrict__ queue, const unsigned* __restrict__ qlen,
+                                   unsigned qcap, const int* __restrict__ ne, const int* __restrict__ bb,
+                                   const int64_t* __restrict__ base, const int* __restrict__ sbase,
+                                   const int* __restrict__ srcf, const int* __restrict__ srcm, double k, double eta,
+                                   double H, cplx alpha, const double2* __restrict__ sc,
+                                   const double2* __restrict__ st, const double2* __restrict__ snu,
+                                   const double* __restrict__ sh, cplx* __restrict__ val, cplxf* __restrict__ valf,
+                                   unsigned long long* __restrict__ stat) {
+  const unsigned n = min(*qlen, qcap);
+  unsigned long long npair = 0, nquad = 0;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const unsigned long long w = queue[i];
+    const int li = (int)(w >> 40), t = (int)((w >> 24) & 0xFFFF), j = (int)(w & 0xFFFFFF);
+    const int s = bb[ne[li]] + t;
+    const int j0 = sbase[li], ns = sbase[li + 1] - j0;
+    const int f = srcf[j0 + j], m = srcm[j0 + j];
+    const double2 x = sc[s], nx = snu[s];
+    double2 c = sc[f];
+    c.y += m * H;
+    const double hh = sh[f];
+    const double q = sqrt((x.x - c.x) * (x.x - c.x) + (x.y - c.y) * (x.y - c.y)) / hh;
+    const int g = gl_order(q, 0);
+    ++npair;
+    nquad += g;
+    cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
+    pair4_f64(k, x, nx, c, st[f], snu[f], hh, g, S, Dv, K, T);
+    const cplx ph = mul_i(0.25 * ipow_phase(alpha, m));      // (i/4) alpha^m
+    const cplx b[4] = {ph * Dv, (-eta) * mul_i(ph * S), ph * T, (-eta) * mul_i(ph * K)};
+    const int64_t o = base[li] + ((int64_t)t * ns + j) * 4;
+    for (int q2 = 0; q2 < 4; ++q2) {
+      val[o + q2] = b[q2];
+      if (valf) valf[o + q2] = cplxf{(float)b[q2].re, (float)b[q2].im};
+    }
+  }
   if (stat) {
-    atomicAdd(&stat[0], npair);
-    atomicAdd(&stat[1], nquad);
+    npair = warp_sum_u64(npair);
+    nquad = warp_sum_u64(nquad);
+    if ((threadIdx.x & 31) == 0 && npair) {
+      atomicAdd(&stat[0], npair);
+      atomicAdd(&stat[1], nquad);
+    }
   }
 }
 
@@ -1121,13 +1164,19 @@ cudaError_t k_build_caches(pfmbem* h) {
         h->o_nu, h->o_h, h->tab_val, h->stat_dev);
     prof_end(h, PH_BUILD);
   }
+  cudaMemsetAsync(h->nq_len, 0, sizeof(unsigned), st);
   prof_begin(h, PH_BUILD);
   near_build_kernel<<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
                                               h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c, h->s_t,
                                               h->s_nu, h->s_h, h->s_perm, h->o_fiber, h->fib_off, h->s_m0,
                                               h->kt_base, h->kt_val, h->ntab > 0 ? h->pl_ptr : nullptr, h->pl_fib,
                                               h->pl_img, h->pl_tab, h->tab_start, h->tab_nb, h->tab_val, h->nc_val,
-                                              h->nc_valf, h->stat_dev);
+                                              h->nc_valf, h->nq, h->nq_len, h->nq_cap);
+  prof_end(h, PH_BUILD);
+  prof_begin(h, PH_BUILD);
+  near_direct_kernel<<<1216, 128, 0, st>>>(h->nq, h->nq_len, h->nq_cap, leaf.ne, leaf.box_begin, h->nc_base,
+                                           h->nc_sbase, h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c,
+                                           h->s_t, h->s_nu, h->s_h, h->nc_val, h->nc_valf, h->stat_dev);
   prof_end(h, PH_BUILD);
   return cudaGetLastError();
 }

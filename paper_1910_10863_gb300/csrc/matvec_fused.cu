@@ -6,19 +6,22 @@
 // Here one grid of co-resident blocks runs the stages back to back and
 // separates them with a device-wide barrier:
 //
-//   A   gather the densities into tree order (alpha^{-m0} phase), P2M,
-//       and clear the local expansions of levels 1..D                     (warp per leaf)
-//   B_l M2M into level l = D-1 .. 0; at the root also L(0) = R M(0)       (warp per box);
-//       the cached near-field sums of all elements are spread evenly over
-//       these stages, whose few boxes leave most warps idle  (warp per element)
-//   D_l L2L from the parent (warp per box) and M2L (block per chunk of
-//       pairs with one translation offset, T_o staged in shared memory),
-//       both added atomically into L(l), l = 1..D
-//   E   L2P plus the near-field sums                                       (warp per element)
-//   F   fiber blocks and the combination of eq. 9: a regular-polygon fiber
-//       whose element count is a power of two applies its block-circulant
-//       block by FFT (block per fiber), the others by cached rows (block per
-//       chunk of 32 rows)
+//   A   gather the densities into tree order (alpha^{-m0} phase), P2M and
+//       clear the local expansions of levels 1..D (warp per leaf); at the
+//       same time a share of the blocks applies the same-fiber blocks of
+//       eq. 9 to x and writes them to y: a regular-polygon fiber whose
+//       element count is a power of two by FFT (block per fiber), the others
+//       by cached rows (block per chunk of 32 rows)
+//   B_l M2M into level l = D-1 .. 0 (warp per box, or per output coefficient
+//       where the boxes are few); the root stage forms L(0) directly from the
+//       four level-1 multipoles through the folded operator R T_0.  The
+//       cached near-field sums of all elements are spread evenly over these
+//       stages, whose few boxes leave most warps idle        (warp per element)
+//   D_l L2L from the parent (warp per box or per coefficient) and M2L (warp
+//       per pair, or block per chunk of pairs with one translation offset and
+//       T_o staged in shared memory), both added atomically into L(l)
+//   E   L2P plus the near-field sums, and the combination of eq. 9 added to
+//       the fiber part already in y                           (warp per element)
 //
 // Warp-level items are dealt round-robin over the blocks (item i to block
 // i mod grid), so that a stage with few items still spreads over all SMs: on
@@ -51,7 +54,6 @@ struct FusedArgs {
   const cplx* x;                 // input, original order, FP64
   cplx* y;                       // output, original order, FP64
   C* dens;                       // sorted (phi', varphi')
-  C* U;                          // sorted (U', dU')
   C* Un;                         // sorted near-field part of (U', dU')
   const int* s_li;               // sorted element -> index of its leaf among the non-empty leaves
   int nne[PF_MAXLEVEL + 1];
@@ -67,12 +69,15 @@ struct FusedArgs {
   const int* pr_tgt[PF_MAXLEVEL + 1];
   const int* pr_src[PF_MAXLEVEL + 1];
   const int* pr_img[PF_MAXLEVEL + 1];
+  const int* pr_off[PF_MAXLEVEL + 1];    // translation offset per pair
+  int npair[PF_MAXLEVEL + 1];
   const C* m2m[PF_MAXLEVEL + 1];     // at the parent level: [q][m child][n parent]
   const C* l2l[PF_MAXLEVEL + 1];     // at the parent level: [q][m parent][n child]
   const C* m2lt[PF_MAXLEVEL + 1];    // [o][n source][l target]
   C* M[PF_MAXLEVEL + 1];
   C* L[PF_MAXLEVEL + 1];
   const C* root;                     // [l][n], lattice-sum translation at the root
+  const C* rootc;                    // [u < 4 P_1][l < P_0], R T_0: L(0) from the level-1 multipoles
   const C* p2m;                      // [E][2][P_D]
   const C* l2p;                      // [E][2][P_D]
   const int64_t* nc_base;
@@ -91,6 +96,8 @@ struct FusedArgs {
   const C* fb_val;
   const int* circ;
   cplx alpha, c2;
+  int fblk;                          // blocks applying the same-fiber blocks during stage A (0: all, after P2M)
+  int m2l_warp;                      // M2L one warp per pair (1) or one block per staged chunk (0)
   unsigned* bar;                     // [0] arrivals, [1] generation
   int* err;
   unsigned long long* stamp;         // optional stage end times (ns), written by block 0
@@ -104,11 +111,9 @@ __device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k) {
   }
 }
 
+// alpha^m for m in {-1, 0, 1}; |alpha| = 1, so alpha^{-1} = conj(alpha)
 __device__ __forceinline__ cplx phase_m(cplx alpha, int m) {
-  // alpha^m for m in {-1, 0, 1}
-  if (m == 0) return cplx{1, 0};
-  if (m == 1) return alpha;
-  return cdiv(cplx{1, 0}, alpha);
+  return m == 0 ? cplx{1, 0} : (m > 0 ? alpha : conj(alpha));
 }
 
 // Loads of values written by other blocks earlier in the same launch bypass L1
@@ -254,6 +259,21 @@ __global__ void fiber_symbol_kernel(const int* __restrict__ fib_list, const int*
       outf[4 * k + 2 * r + q] = to_f(s[t]);
     }
   }
+}
+
+// L(0) from the four level-1 multipoles: Rc = R T_0, with R the periodic root
+// translation and T_0 the level-1 -> root M2M, stored [u][l] for the 4 P_1
+// child coefficients u, so that the fused product never forms M(0).  One
+// thread per entry, FP64, with an FP32 copy.
+__global__ void root_fold_kernel(int P0, int K, const cplx* __restrict__ R, const cplx* __restrict__ m2m0,
+                                 cplx* __restrict__ rc, cplxf* __restrict__ rcf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= P0 * K) return;
+  const int u = i / P0, t = i - u * P0;
+  cplx s{0, 0};
+  for (int n = 0; n < P0; ++n) s += R[(size_t)t * P0 + n] * m2m0[(size_t)u * P0 + n];
+  rc[i] = s;
+  rcf[i] = to_f(s);
 }
 
 // Near-field sum of one target (sorted element s) from its leaf's cached
@@ -470,53 +490,145 @@ __global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const 
   }
 }
 
+// Warp items: item i goes to block i mod nb and, within the block, to warp
+// (i / nb + i mod nb) mod FW, so that a stage whose item count is not a
+// multiple of the grid spreads its extra items over all four sub-partitions
+// of the SMs instead of piling them on warp 0.  Returns the first item of
+// warp w of block b; the stride is nb * FW.
+__device__ __forceinline__ int warp_first(int b, int w, int nb) {
+  return b + nb * ((w - b % FW + FW) % FW);
+}
+
+// The same-fiber blocks of eq. 9 (the k1 part with the self terms, and for a
+// regular polygon also the k part) applied to x, written to y in the
+// original element order; block b0 of nb blocks.  A regular-polygon fiber
+// whose element count is a power of two goes by FFT (one block per fiber),
+// y^(r) = IFFT(sum_s B^(r,s) FFT(x^(s))); the others by cached rows (one block
+// per chunk of 32 rows; a circulant block is read from its generating row
+// pair with x rotated by 2e).
+template <class C>
+__device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int warp, int lane) {
+  using R = decltype(C{}.re);
+  for (int b = b0; b < a.nfft; b += nb) {
+    const int fb = a.fft_fib[b];
+    const int f0 = a.foff[fb], N = a.foff[fb + 1] - f0, lg = __ffs(N) - 1;
+    __syncthreads();
+    for (int t = threadIdx.x; t < 2 * N; t += FB) {
+      const int q = t >> lg, f = t & (N - 1);
+      xs[t] = from_d<C>(a.x[2 * (f0 + f) + q]);
+    }
+    block_fft(xs, 2, lg, -1, a.tw);
+    const C* Bh = a.fh_val + 4 * a.fh_base[fb];
+    for (int k = threadIdx.x; k < N; k += FB) {
+      const C x0 = xs[k], x1 = xs[N + k];
+      const C* bk = Bh + 4 * k;
+      xs[k] = bk[0] * x0 + bk[1] * x1;
+      xs[N + k] = bk[2] * x0 + bk[3] * x1;
+    }
+    block_fft(xs, 2, lg, +1, a.tw);
+    const R inv = (R)1 / (R)N;
+    for (int t = threadIdx.x; t < 2 * N; t += FB) {
+      const int rr = t >> lg, e = f0 + (t & (N - 1));
+      a.y[2 * e + rr] = to_d(inv * xs[t]);
+    }
+  }
+  for (int b = b0; b < a.nchunk; b += nb) {
+    const int fb = a.fb_chunk[3 * b], rb = a.fb_chunk[3 * b + 1], re = a.fb_chunk[3 * b + 2];
+    const int f0 = a.foff[fb], n2 = 2 * (a.foff[fb + 1] - f0);
+    const bool cir = a.circ[fb] != 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n2; i += FB) xs[i] = from_d<C>(a.x[2 * f0 + i]);
+    __syncthreads();
+    for (int r = rb + 2 * warp; r < re; r += 2 * FW) {
+      const C* row0 = a.fb_val + a.fb_base[fb] + (cir ? 0 : (int64_t)r * n2);
+      const C* row1 = row0 + n2;
+      const int sh = cir ? r : 0;
+      const bool two = r + 1 < re;
+      C a0{0, 0}, a1{0, 0}, b0v{0, 0}, b1v{0, 0};
+      int c = lane;
+      for (; c + 32 < n2; c += 64) {
+        int i0 = c + sh, i1 = c + 32 + sh;
+        if (i0 >= n2) i0 -= n2;
+        if (i1 >= n2) i1 -= n2;
+        const C x0 = xs[i0], x1 = xs[i1];
+        a0 += row0[c] * x0;
+        a1 += row0[c + 32] * x1;
+        if (two) {
+          b0v += row1[c] * x0;
+          b1v += row1[c + 32] * x1;
+        }
+      }
+      for (; c < n2; c += 32) {
+        int i0 = c + sh;
+        if (i0 >= n2) i0 -= n2;
+        a0 += row0[c] * xs[i0];
+        if (two) b0v += row1[c] * xs[i0];
+      }
+      const C s0 = wsum(a0 + a1);
+      const C s1 = wsum(b0v + b1v);
+      if (lane == 0) {
+        a.y[2 * f0 + r] = to_d(s0);
+        if (two) a.y[2 * f0 + r + 1] = to_d(s1);
+      }
+    }
+  }
+}
+
 template <class C>
 __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   extern __shared__ unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x;
-  const int wfirst = blockIdx.x + G * warp, wstride = G * FW;   // round-robin warp items
+  const int wfirst = warp_first(blockIdx.x, warp, G), wstride = G * FW;
   C* wsm = sm + TSIZE + (size_t)warp * PF_NCOEF;                // per-warp scratch
-  C* sT = sm;                                                   // [P][P+1] staged M2L operator
+  C* sT = sm;                                                   // [P][P] staged M2L operator (row stride P, odd)
   const int D = a.D;
   int ks = 0;
   stage_stamp(a.stamp, ks++);
 
-  // ------------------------------------------------------------ A: gather + P2M, clear L
+  // ------------------------------------------------------------ A: gather + P2M, clear L; fiber part
   {
     for (int l = 1; l <= D; ++l) {
       C* Lz = a.L[l];
       const size_t nz = (size_t)a.nbox[l] * a.P[l];
       for (size_t t = (size_t)blockIdx.x * FB + threadIdx.x; t < nz; t += (size_t)G * FB) Lz[t] = C{0, 0};
     }
-    const int PD = a.P[D];
-    for (int i = wfirst; i < a.nne[D]; i += wstride) {
-      const int box = a.ne[D][i], s0 = a.bb[D][box], s1 = a.be[D][box];
-      for (int sb = s0; sb < s1; sb += 32) {
-        const int s = sb + lane;
-        if (s < s1) {
-          const int e = a.perm[s];
-          const cplx p = a.ph[s];
-          a.dens[2 * s] = from_d<C>(p * a.x[2 * e]);
-          a.dens[2 * s + 1] = from_d<C>(p * a.x[2 * e + 1]);
-        }
-      }
-      __syncwarp();
-      for (int n0 = 0; n0 < PD; n0 += 32) {
-        const int n = n0 + lane;
-        if (n < PD) {
-          C acc0{0, 0}, acc1{0, 0};
-#pragma unroll 4
-          for (int f = s0; f < s1; ++f) {
-            const C* cf = a.p2m + (size_t)f * 2 * PD;
-            acc0 += cf[n] * a.dens[2 * f];
-            acc1 += cf[PD + n] * a.dens[2 * f + 1];
+    // blocks [gA, G) apply the same-fiber blocks while the others run P2M
+    const int gA = G - a.fblk;
+    if (blockIdx.x < gA) {
+      const int PD = a.P[D];
+      for (int i = warp_first(blockIdx.x, warp, gA); i < a.nne[D]; i += gA * FW) {
+        const int box = a.ne[D][i], s0 = a.bb[D][box], s1 = a.be[D][box];
+        for (int sb = s0; sb < s1; sb += 32) {
+          const int s = sb + lane;
+          if (s < s1) {
+            const int e = a.perm[s];
+            const C p = from_d<C>(a.ph[s]);
+            a.dens[2 * s] = p * from_d<C>(a.x[2 * e]);
+            a.dens[2 * s + 1] = p * from_d<C>(a.x[2 * e + 1]);
           }
-          a.M[D][(size_t)box * PD + n] = acc0 + acc1;
+        }
+        __syncwarp();
+        for (int n0 = 0; n0 < PD; n0 += 32) {
+          const int n = n0 + lane;
+          if (n < PD) {
+            C acc0{0, 0}, acc1{0, 0};
+#pragma unroll 4
+            for (int f = s0; f < s1; ++f) {
+              const C* cf = a.p2m + (size_t)f * 2 * PD;
+              acc0 += cf[n] * a.dens[2 * f];
+              acc1 += cf[PD + n] * a.dens[2 * f + 1];
+            }
+            a.M[D][(size_t)box * PD + n] = acc0 + acc1;
+          }
         }
       }
     }
+    if (a.fblk == 0)
+      fiber_part(a, sm, blockIdx.x, G, warp, lane);
+    else if (blockIdx.x >= gA)
+      fiber_part(a, sm, blockIdx.x - gA, a.fblk, warp, lane);
   }
   if (!grid_barrier(a.bar, a.err)) return;
   stage_stamp(a.stamp, ks++);
@@ -531,10 +643,34 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       r0 = (int)((int64_t)a.E * j / nb);
       r1 = (int)((int64_t)a.E * (j + 1) / nb);
     }
-    const int nitem = a.nne[l] + (r1 - r0);
+    // near the top of the tree the boxes are too few to occupy the grid: one
+    // warp per output coefficient, lanes over the 4 Pc child coefficients.  The
+    // root then forms L(0) = (R T_0) [M(1) of its four children] at once.
+    const bool top = (int64_t)a.nne[l] * P <= wstride;
+    const int nbi = top ? a.nne[l] * P : a.nne[l];
+    const int nitem = nbi + (r1 - r0);
     for (int i = wfirst; i < nitem; i += wstride) {
-      if (i >= a.nne[l]) {
-        near_row(a, r0 + (i - a.nne[l]), lane);
+      if (i >= nbi) {
+        near_row(a, r0 + (i - nbi), lane);
+        continue;
+      }
+      if (top) {
+        const int bi = i / P, n = i - bi * P;
+        const int box = a.ne[l][bi];
+        const C* A = (l == 0 ? a.rootc : a.m2m[l]) + n;
+        C acc{0, 0};
+        for (int u = lane; u < 4 * Pc; u += 32) {
+          const int q = u / Pc, ch = 4 * box + q;
+          if (a.bb[l + 1][ch] < a.be[l + 1][ch])
+            acc += A[(size_t)u * P] * ldcg(a.M[l + 1] + (size_t)ch * Pc + (u - q * Pc));
+        }
+        acc = wsum(acc);
+        if (lane == 0) {
+          if (l == 0)
+            a.L[0][n] = acc;
+          else
+            a.M[l][(size_t)box * P + n] = acc;
+        }
         continue;
       }
       const int box = a.ne[l][i];
@@ -566,6 +702,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       }
       if (l == 0) {
         // root: L(0) = R M(0), the images |m| >= 2 through the lattice sums
+        // (only on a grid too small for the coefficient-per-warp form above)
         __syncwarp();
         for (int m = lane; m < P; m += 32) wsm[m] = ldcg(a.M[0] + m);
         __syncwarp();
@@ -583,25 +720,50 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   // ------------------------------------------------------------ D: L2L + M2L
   for (int l = 1; l <= D; ++l) {
     const int P = a.P[l], Pp = a.P[l - 1];
-    // L2L, one warp per box
-    for (int i = wfirst; i < a.nne[l]; i += wstride) {
-      const int box = a.ne[l][i], par = box >> 2, q = box & 3;
+    // L2L: one warp per output coefficient while the boxes are few, else one
+    // warp per box
+    const bool top = (int64_t)a.nne[l] * P <= wstride;
+    const int nl2l = top ? a.nne[l] * P : a.nne[l];
+    // M2L one warp per pair (operator rows through L1/L2), or one block per
+    // chunk of pairs sharing the offset (operator staged in shared memory)
+    const bool wpair = a.m2l_warp || P > TSP;
+    const int nitem = nl2l + (wpair ? a.npair[l] : 0);
+    for (int i = wfirst; i < nitem; i += wstride) {
+      if (i < nl2l) {
+        if (top) {
+          const int bi = i / P, n = i - bi * P;
+          const int box = a.ne[l][bi], par = box >> 2, q = box & 3;
+          const C* A = a.l2l[l - 1] + (size_t)q * Pp * P + n;
+          C acc{0, 0};
+          for (int m = lane; m < Pp; m += 32) acc += A[(size_t)m * P] * ldcg(a.L[l - 1] + (size_t)par * Pp + m);
+          acc = wsum(acc);
+          if (lane == 0) atomic_add(a.L[l] + (size_t)box * P + n, acc);
+        } else {
+          const int box = a.ne[l][i], par = box >> 2, q = box & 3;
+          __syncwarp();
+          for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Pp + m);
+          __syncwarp();
+          for (int n = lane; n < P; n += 32)
+            atomic_add(a.L[l] + (size_t)box * P + n, colmv(a.l2l[l - 1] + (size_t)q * Pp * P + n, P, wsm, Pp));
+        }
+        continue;
+      }
+      const int pi = i - nl2l;
+      const int src = a.pr_src[l][pi], tgt = a.pr_tgt[l][pi];
+      const C phs = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
+      const C* To = a.m2lt[l] + (size_t)a.pr_off[l][pi] * P * P;
       __syncwarp();
-      for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Pp + m);
+      for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * P + m);
       __syncwarp();
-      for (int n = lane; n < P; n += 32)
-        atomic_add(a.L[l] + (size_t)box * P + n, colmv(a.l2l[l - 1] + (size_t)q * Pp * P + n, P, wsm, Pp));
+      for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * P + n, colmv(To + n, P, wsm, P));
     }
-    // M2L, one block per chunk of pairs that share the translation offset
-    const bool stage = P <= TSP;
-    for (int b = blockIdx.x; b < a.nch[l]; b += G) {
-      const int o = a.ch_off[l][b], pb = a.ch_beg[l][b], pe = a.ch_end[l][b];
-      const C* To = a.m2lt[l] + (size_t)o * P * P;          // [n source][l target]
-      __syncthreads();                                      // sT of the previous chunk is done
-      if (stage)
-        for (int t = threadIdx.x; t < P * P; t += FB) sT[(t % P) * (P + 1) + t / P] = To[t];
-      __syncthreads();
-      if (stage) {
+    if (!wpair) {
+      for (int b = blockIdx.x; b < a.nch[l]; b += G) {
+        const int o = a.ch_off[l][b], pb = a.ch_beg[l][b], pe = a.ch_end[l][b];
+        const C* To = a.m2lt[l] + (size_t)o * P * P;          // [n source][l target]
+        __syncthreads();                                      // sT of the previous chunk is done
+        for (int t = threadIdx.x; t < P * P; t += FB) sT[(t % P) * P + t / P] = To[t];
+        __syncthreads();
         // two pairs per warp pass, sharing the operator rows read from shared memory
         for (int pi = pb + 2 * warp; pi < pe; pi += 2 * FW) {
           const bool two = pi + 1 < pe;
@@ -616,7 +778,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
           }
           __syncwarp();
           for (int n = lane; n < P; n += 32) {
-            const C* row = sT + (size_t)n * (P + 1);
+            const C* row = sT + (size_t)n * P;
             C rA{0, 0}, rB{0, 0};
 #pragma unroll 4
             for (int m = 0; m < P; ++m) {
@@ -628,24 +790,16 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
             if (two) atomic_add(a.L[l] + (size_t)tgtB * P + n, rB);
           }
         }
-      } else {
-        for (int pi = pb + warp; pi < pe; pi += FW) {
-          const int src = a.pr_src[l][pi], tgt = a.pr_tgt[l][pi];
-          const C phs = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
-          __syncwarp();
-          for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * P + m);
-          __syncwarp();
-          for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * P + n, colmv(To + n, P, wsm, P));
-        }
       }
     }
     if (!grid_barrier(a.bar, a.err)) return;
     stage_stamp(a.stamp, ks++);
   }
 
-  // ------------------------------------------------------------ E: L2P + near field
+  // ------------------------------------------------------------ E: L2P + near field, combination of eq. 9
   {
     const int PD = a.P[D];
+    const C c2 = from_d<C>(a.c2);
     for (int s = wfirst; s < a.E; s += wstride) {
       const int box = a.ne[D][a.s_li[s]];
       const C* Lb = a.L[D] + (size_t)box * PD;
@@ -659,91 +813,13 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       uf = wsum(uf);
       df = wsum(df);
       if (lane == 0) {
-        a.U[2 * s] = uf + ldcg(a.Un + 2 * s);
-        a.U[2 * s + 1] = df + ldcg(a.Un + 2 * s + 1);
-      }
-    }
-  }
-  if (!grid_barrier(a.bar, a.err)) return;
-  stage_stamp(a.stamp, ks++);
-
-  // ------------------------------------------------------------ F: fiber blocks + combine
-  {
-    C* xs = sm;                                  // [2 N] the fiber's input densities
-    // block-circulant fibers by FFT: y^(r) = IFFT( sum_s B^(r,s) FFT(x^(s)) )
-    for (int b = blockIdx.x; b < a.nfft; b += gridDim.x) {
-      const int fb = a.fft_fib[b];
-      const int f0 = a.foff[fb], N = a.foff[fb + 1] - f0, lg = __ffs(N) - 1;
-      __syncthreads();
-      for (int t = threadIdx.x; t < 2 * N; t += FB) {
-        const int q = t >> lg, f = t & (N - 1);
-        xs[t] = from_d<C>(a.x[2 * (f0 + f) + q]);
-      }
-      block_fft(xs, 2, lg, -1, a.tw);
-      const C* Bh = a.fh_val + 4 * a.fh_base[fb];
-      for (int k = threadIdx.x; k < N; k += FB) {
-        const C x0 = xs[k], x1 = xs[N + k];
-        const C* bk = Bh + 4 * k;
-        xs[k] = bk[0] * x0 + bk[1] * x1;
-        xs[N + k] = bk[2] * x0 + bk[3] * x1;
-      }
-      block_fft(xs, 2, lg, +1, a.tw);
-      const double inv = 1.0 / N;
-      for (int t = threadIdx.x; t < 2 * N; t += FB) {
-        const int rr = t >> lg, e = f0 + (t & (N - 1));
-        const int s = a.opos[e];
-        const cplx po = cdiv(cplx{1, 0}, a.ph[s]);
-        const cplx u = po * to_d(ldcg(a.U + 2 * s + rr));
-        a.y[2 * e + rr] = inv * to_d(xs[t]) + (rr ? a.c2 * u : u);
-      }
-    }
-    // the other fibers from their cached rows
-    for (int b = blockIdx.x; b < a.nchunk; b += gridDim.x) {
-      const int fb = a.fb_chunk[3 * b], rb = a.fb_chunk[3 * b + 1], re = a.fb_chunk[3 * b + 2];
-      const int f0 = a.foff[fb], n2 = 2 * (a.foff[fb + 1] - f0);
-      const bool cir = a.circ[fb] != 0;
-      __syncthreads();
-      for (int i = threadIdx.x; i < n2; i += FB) xs[i] = from_d<C>(a.x[2 * f0 + i]);
-      __syncthreads();
-      // a warp takes the row pair (2e, 2e+1); a circulant block is read from its
-      // generating row pair with x rotated by 2e
-      for (int r = rb + 2 * warp; r < re; r += 2 * FW) {
-        const C* row0 = a.fb_val + a.fb_base[fb] + (cir ? 0 : (int64_t)r * n2);
-        const C* row1 = row0 + n2;
-        const int sh = cir ? r : 0;
-        const bool two = r + 1 < re;
-        C a0{0, 0}, a1{0, 0}, b0{0, 0}, b1{0, 0};
-        int c = lane;
-        for (; c + 32 < n2; c += 64) {
-          int i0 = c + sh, i1 = c + 32 + sh;
-          if (i0 >= n2) i0 -= n2;
-          if (i1 >= n2) i1 -= n2;
-          const C x0 = xs[i0], x1 = xs[i1];
-          a0 += row0[c] * x0;
-          a1 += row0[c + 32] * x1;
-          if (two) {
-            b0 += row1[c] * x0;
-            b1 += row1[c + 32] * x1;
-          }
-        }
-        for (; c < n2; c += 32) {
-          int i0 = c + sh;
-          if (i0 >= n2) i0 -= n2;
-          a0 += row0[c] * xs[i0];
-          if (two) b0 += row1[c] * xs[i0];
-        }
-        const C s0 = wsum(a0 + a1);
-        const C s1 = wsum(b0 + b1);
-        if (lane == 0) {
-          for (int q = 0; q < (two ? 2 : 1); ++q) {
-            const int rr = r + q;
-            const int e = f0 + (rr >> 1);
-            const int s = a.opos[e];
-            const cplx po = cdiv(cplx{1, 0}, a.ph[s]);
-            const cplx u = po * to_d(ldcg(a.U + 2 * s + (rr & 1)));
-            a.y[2 * f0 + rr] = to_d(q == 0 ? s0 : s1) + ((rr & 1) ? a.c2 * u : u);
-          }
-        }
+        // back to the element's true position: times alpha^{m0} = conj(alpha^{-m0})
+        const int e = a.perm[s];
+        const C po = from_d<C>(conj(a.ph[s]));
+        const C u = po * (uf + ldcg(a.Un + 2 * s));
+        const C du = c2 * (po * (df + ldcg(a.Un + 2 * s + 1)));
+        a.y[2 * e] = ldcg(a.y + 2 * e) + to_d(u);
+        a.y[2 * e + 1] = ldcg(a.y + 2 * e + 1) + to_d(du);
       }
     }
   }
@@ -753,8 +829,8 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
 
 template <class C>
 size_t fused_smem(int maxfiber) {
-  const size_t a = (size_t)TSIZE + (size_t)FW * PF_NCOEF;   // stages A, B, D
-  const size_t f = 2 * (size_t)maxfiber;                    // stage F
+  const size_t a = (size_t)TSIZE + (size_t)FW * PF_NCOEF;   // stages B, D
+  const size_t f = 2 * (size_t)maxfiber;                    // fiber part of stage A
   return sizeof(C) * std::max(a, f);
 }
 
@@ -783,6 +859,8 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
     a.pr_tgt[l] = L.pr_tgt;
     a.pr_src[l] = L.pr_src;
     a.pr_img[l] = L.pr_img;
+    a.pr_off[l] = L.pr_off;
+    a.npair[l] = (int)L.nil;
     if constexpr (sizeof(C) == sizeof(cplxf)) {
       a.m2m[l] = L.m2mf; a.l2l[l] = L.l2lf; a.m2lt[l] = L.m2ltf; a.M[l] = L.Mf; a.L[l] = L.Lf;
     } else {
@@ -792,11 +870,11 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
   a.s_li = h->s_li;
   if constexpr (sizeof(C) == sizeof(cplxf)) {
     a.Un = h->Unf;
-    a.dens = h->densf; a.U = h->Uf; a.root = h->rootf; a.p2m = h->p2m_cf; a.l2p = h->l2p_cf;
+    a.dens = h->densf; a.root = h->rootf; a.rootc = h->rootcf; a.p2m = h->p2m_cf; a.l2p = h->l2p_cf;
     a.nc_val = h->nc_valf; a.fb_val = h->fb_valf; a.fh_val = h->fh_valf; a.tw = h->twf;
   } else {
     a.Un = h->Un;
-    a.dens = h->dens; a.U = h->U; a.root = h->root; a.p2m = h->p2m_c; a.l2p = h->l2p_c;
+    a.dens = h->dens; a.root = h->root; a.rootc = h->rootc; a.p2m = h->p2m_c; a.l2p = h->l2p_c;
     a.nc_val = h->nc_val; a.fb_val = h->fb_val; a.fh_val = h->fh_val; a.tw = h->tw;
   }
   a.nc_base = h->nc_base;
@@ -817,6 +895,18 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
   static const bool stamps = std::getenv("PFMBEM_STAGE_TIMES") != nullptr;
   a.stamp = stamps ? h->fz_stamp : nullptr;
   const int grid = f32 ? h->fz_grid32 : h->fz_grid64;
+  // the fiber part's blocks in stage A, in proportion to its block items
+  // against the P2M warp items (one leaf per warp)
+  {
+    const int nf = h->fz_nfft + h->fz_nchunk;
+    const double wa = (double)h->lev[h->D].nne / FW;
+    const int fb = (int)((double)grid * nf / (nf + wa) + 0.5);
+    a.fblk = grid >= 16 ? std::max(1, std::min({fb, nf, grid - grid / 4})) : 0;
+  }
+  // M2L: warp per pair in FP64, whose per-pair cost the FP64 pipe sets; staged
+  // chunks in FP32 (PFMBEM_M2L_WARP=0/1 overrides, for measurement)
+  static const char* mw = std::getenv("PFMBEM_M2L_WARP");
+  a.m2l_warp = mw ? std::atoi(mw) != 0 : !f32;
   const size_t smem = fused_smem<C>(h->max_fiber);
   void* args[] = {&a};
   const int ph = PH_FUSED + (f32 ? 16 : 0);
@@ -830,7 +920,7 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
     e = cudaMemcpyAsync(t, a.stamp, sizeof(t), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) {
-      const int n = 2 * h->D + 4;
+      const int n = 2 * h->D + 3;
       std::fprintf(stderr, "pfmbem fused %s stages (us):", f32 ? "f32" : "f64");
       for (int i = 1; i < n; ++i) std::fprintf(stderr, " %.1f", 1e-3 * (double)(t[i] - t[i - 1]));
       std::fprintf(stderr, "  total %.1f\n", 1e-3 * (double)(t[n - 1] - t[0]));
@@ -874,6 +964,10 @@ cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
   h->fz_grid64 = std::min(fused_grid<cplx>(h->max_fiber), need);
   h->fz_grid32 = std::min(fused_grid<cplxf>(h->max_fiber), need);
   if (h->fz_grid64 <= 0 || h->fz_grid32 <= 0) return cudaSuccess;
+  const int P0 = h->lev[0].P, K = 4 * h->lev[1].P;
+  prof_begin(h, PH_SETUP);
+  root_fold_kernel<<<(P0 * K + 127) / 128, 128, 0, h->stream>>>(P0, K, h->root, h->lev[0].m2m, h->rootc, h->rootcf);
+  prof_end(h, PH_SETUP);
   *ok = true;
   return cudaGetLastError();
 }
