@@ -61,85 +61,102 @@ T* dalloc(pfmbem* h, size_t n) {
   return static_cast<T*>(p);
 }
 
+// Page-locked staging for the batched set-up copies: one process-wide arena,
+// held by one create at a time (pin_acquire to pin_release; that create
+// synchronises its stream before it lets go, so no copy from the arena is in
+// flight when the next create writes into it).  A create that finds the arena
+// held by another, or whose batches outgrow it, stages in pageable memory.
+struct PinnedArena {
+  std::mutex mu;
+  unsigned char* buf = nullptr;
+  size_t cap = 0;
+  pfmbem* owner = nullptr;
+};
+PinnedArena g_pin;
+
+void pin_acquire(pfmbem* h) {
+  std::lock_guard<std::mutex> lk(g_pin.mu);
+  h->pin_user = true;
+  if (!g_pin.buf) {
+    void* p = nullptr;
+    if (cudaHostAlloc(&p, (size_t)64 << 20, cudaHostAllocDefault) == cudaSuccess) {
+      g_pin.buf = static_cast<unsigned char*>(p);
+      g_pin.cap = (size_t)64 << 20;
+    } else {
+      cudaGetLastError();
+    }
+  }
+  if (g_pin.buf && !g_pin.owner) {
+    g_pin.owner = h;
+    h->ub_pin = g_pin.buf;
+    h->ub_pin_cap = g_pin.cap;
+    h->ub_pin_batch = 0;
+    h->ub_len = 0;
+  }
+}
+
+void pin_release(pfmbem* h) {
+  if (!h->pin_user) return;
+  std::lock_guard<std::mutex> lk(g_pin.mu);
+  if (g_pin.owner == h) g_pin.owner = nullptr;
+  h->ub_pin = nullptr;
+  h->pin_user = false;
+}
+
 // Host-to-device copy of a table.  While a batch is open (h->ub_on) the data is
-// appended to one host buffer and the destination pointer is set at the next
-// flush_uploads, which makes one allocation and one copy for the whole batch.
+// appended to the batch (in the page-locked arena when this create holds it)
+// and the destination pointer is set at the next flush_uploads, which makes
+// one allocation and one copy for the whole batch.
 template <class T>
 pfmbem_status upload(pfmbem* h, T** dst, const std::vector<T>& src) {
+  const size_t nb = src.size() * sizeof(T);
   if (h->ub_on) {
+    if (h->ub_pin && !h->ub_spill) {
+      const size_t off = (h->ub_len + 255) & ~(size_t)255;
+      if (h->ub_pin_batch + off + nb <= h->ub_pin_cap) {
+        if (nb) std::memcpy(h->ub_pin + h->ub_pin_batch + off, src.data(), nb);
+        h->ub_len = off + nb;
+        h->ub_fix.push_back({reinterpret_cast<void**>(dst), off});
+        *dst = nullptr;
+        return PFMBEM_OK;
+      }
+      // the arena is full: the open batch continues in pageable memory
+      h->ub_buf.resize(h->ub_len);
+      if (h->ub_len) std::memcpy(h->ub_buf.data(), h->ub_pin + h->ub_pin_batch, h->ub_len);
+      h->ub_len = 0;
+      h->ub_spill = true;
+    }
     const size_t off = (h->ub_buf.size() + 255) & ~(size_t)255;
-    h->ub_buf.resize(off + src.size() * sizeof(T));
-    if (!src.empty()) std::memcpy(h->ub_buf.data() + off, src.data(), src.size() * sizeof(T));
+    h->ub_buf.resize(off + nb);
+    if (nb) std::memcpy(h->ub_buf.data() + off, src.data(), nb);
     h->ub_fix.push_back({reinterpret_cast<void**>(dst), off});
     *dst = nullptr;
     return PFMBEM_OK;
   }
   *dst = dalloc<T>(h, src.size());
   if (!*dst) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
-  if (!src.empty())
-    CK(cudaMemcpyAsync(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice,
-                       h->astream ? h->astream : h->stream));
+  if (nb) CK(cudaMemcpyAsync(*dst, src.data(), nb, cudaMemcpyHostToDevice, h->astream ? h->astream : h->stream));
   return PFMBEM_OK;
-}
-
-// Page-locked staging for the batched set-up copies: one process-wide arena.
-// Every create takes fresh regions from it, so an earlier copy still in flight
-// is never overwritten; the arena is rewound when no create is using it (each
-// create synchronises its stream before it lets go).  When the arena is full
-// the copy goes from pageable memory instead.
-struct PinnedArena {
-  std::mutex mu;
-  unsigned char* buf = nullptr;
-  size_t cap = 0, off = 0;
-  int users = 0;
-};
-PinnedArena g_pin;
-
-void pin_acquire(pfmbem* h) {
-  std::lock_guard<std::mutex> lk(g_pin.mu);
-  g_pin.users++;
-  h->pin_user = true;
-}
-
-void pin_release(pfmbem* h) {
-  if (!h->pin_user) return;
-  std::lock_guard<std::mutex> lk(g_pin.mu);
-  if (--g_pin.users == 0) g_pin.off = 0;
-  h->pin_user = false;
 }
 
 // Copies the open batch to the device and sets its destination pointers; the
 // batch stays open.
 pfmbem_status flush_uploads(pfmbem* h) {
   if (h->ub_fix.empty()) return PFMBEM_OK;
-  unsigned char* d = dalloc<unsigned char>(h, std::max<size_t>(h->ub_buf.size(), 1));
+  cudaStream_t st = h->astream ? h->astream : h->stream;
+  const bool pinned = h->ub_pin && !h->ub_spill;
+  const size_t nb = pinned ? h->ub_len : h->ub_buf.size();
+  unsigned char* d = dalloc<unsigned char>(h, std::max<size_t>(nb, 1));
   if (!d) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
-  const size_t nb = h->ub_buf.size();
-  if (nb) {
-    unsigned char* src = nullptr;
-    {
-      std::lock_guard<std::mutex> lk(g_pin.mu);
-      if (!g_pin.buf) {
-        void* p = nullptr;
-        if (cudaHostAlloc(&p, (size_t)64 << 20, cudaHostAllocDefault) == cudaSuccess) {
-          g_pin.buf = static_cast<unsigned char*>(p);
-          g_pin.cap = (size_t)64 << 20;
-        } else {
-          cudaGetLastError();
-        }
-      }
-      if (h->pin_user && g_pin.buf && g_pin.off + nb <= g_pin.cap) {
-        src = g_pin.buf + g_pin.off;
-        g_pin.off += (nb + 255) & ~(size_t)255;
-      }
-    }
-    if (src) std::memcpy(src, h->ub_buf.data(), nb);
-    CK(cudaMemcpyAsync(d, src ? src : h->ub_buf.data(), nb, cudaMemcpyHostToDevice,
-                       h->astream ? h->astream : h->stream));
-  }
+  if (nb) CK(cudaMemcpyAsync(d, pinned ? h->ub_pin + h->ub_pin_batch : h->ub_buf.data(), nb, cudaMemcpyHostToDevice, st));
   for (auto& f : h->ub_fix) *f.first = d + f.second;
+  if (pinned) {
+    h->ub_pin_batch += (nb + 255) & ~(size_t)255;   // the copy may still be reading the batch
+    h->ub_len = 0;
+  }
   h->ub_buf.clear();
   h->ub_fix.clear();
+  h->ub_spill = false;
   return PFMBEM_OK;
 }
 
@@ -160,6 +177,16 @@ inline unsigned spread_bits(unsigned v) {
   v = (v | (v << 4)) & 0x0F0F0F0Fu;
   v = (v | (v << 2)) & 0x33333333u;
   v = (v | (v << 1)) & 0x55555555u;
+  return v;
+}
+
+// Gathers the even bit positions of v (inverse of spread_bits).
+inline unsigned unspread_bits(unsigned v) {
+  v &= 0x55555555u;
+  v = (v | (v >> 1)) & 0x33333333u;
+  v = (v | (v >> 2)) & 0x0F0F0F0Fu;
+  v = (v | (v >> 4)) & 0x00FF00FFu;
+  v = (v | (v >> 8)) & 0x0000FFFFu;
   return v;
 }
 
@@ -521,7 +548,6 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   };
   mark("elements");
   h->ub_on = true;                 // tables below go up in a few batched copies
-  h->ub_buf.reserve((size_t)E * 512 + ((size_t)1 << 20));
   pin_acquire(h);
   // ---------------------------------------------------- depth
   const int leaf_max = h->opt.leaf_max > 0 ? h->opt.leaf_max : 64;
@@ -531,19 +557,34 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // and its Morton code: the code of the depth-D box is a prefix of it
   std::vector<int> m10(E);
   {
-    const double d10 = H / 1024.0;
+    // (a value below 0 truncates to 0 like its floor clamps to 0)
+    const double r10 = 1024.0 / H;
     for (int e = 0; e < E; ++e) {
-      const int ix = std::min(std::max((int)std::floor((cw[e].x - h->x0) / d10), 0), 1023);
-      const int iy = std::min(std::max((int)std::floor((cw[e].y - h->y0) / d10), 0), 1023);
+      const int ix = std::min(std::max((int)((cw[e].x - h->x0) * r10), 0), 1023);
+      const int iy = std::min(std::max((int)((cw[e].y - h->y0) * r10), 0), 1023);
       m10[e] = morton(ix, iy, 10);
     }
   }
-  auto leaf_of = [&](int e, int Dd) { return m10[e] >> (2 * (10 - Dd)); };
+  // box occupancy at depth 8 in one pass, then at every coarser depth by
+  // summing the four Morton-consecutive children: cnt[l][b], l <= 8
+  constexpr int DH = 8;
+  std::vector<std::vector<int>> cnt(DH + 1);
+  cnt[DH].assign((size_t)1 << (2 * DH), 0);
+  for (int e = 0; e < E; ++e) cnt[DH][m10[e] >> (2 * (10 - DH))]++;
+  for (int l = DH - 1; l >= 0; --l) {
+    cnt[l].resize((size_t)1 << (2 * l));
+    const int* c1 = cnt[l + 1].data();
+    for (size_t b = 0; b < cnt[l].size(); ++b) cnt[l][b] = c1[4 * b] + c1[4 * b + 1] + c1[4 * b + 2] + c1[4 * b + 3];
+  }
   if (D <= 0) {
     for (D = 2; D < 10; ++D) {
-      std::vector<int> cnt(1 << (2 * D), 0);
       int mx = 0;
-      for (int e = 0; e < E; ++e) mx = std::max(mx, ++cnt[leaf_of(e, D)]);
+      if (D <= DH) {
+        for (int v : cnt[D]) mx = std::max(mx, v);
+      } else {
+        std::vector<int> c((size_t)1 << (2 * D), 0);
+        for (int e = 0; e < E; ++e) mx = std::max(mx, ++c[m10[e] >> (2 * (10 - D))]);
+      }
       if (mx <= leaf_max) break;
     }
   }
@@ -551,31 +592,34 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   h->D = D;
   // ---------------------------------------------------- sort by leaf Morton key (stable counting sort)
   std::vector<int> key(E), perm(E), pos(E);
-  for (int e = 0; e < E; ++e) key[e] = leaf_of(e, D);
+  for (int e = 0; e < E; ++e) key[e] = m10[e] >> (2 * (10 - D));
+  if (D > DH) {
+    cnt.resize(D + 1);
+    for (int l = DH + 1; l <= D; ++l) {
+      cnt[l].assign((size_t)1 << (2 * l), 0);
+      for (int e = 0; e < E; ++e) cnt[l][m10[e] >> (2 * (10 - l))]++;
+    }
+  }
   {
     std::vector<int> start(((size_t)1 << (2 * D)) + 1, 0);
-    for (int e = 0; e < E; ++e) start[key[e] + 1]++;
-    for (size_t b = 1; b < start.size(); ++b) start[b] += start[b - 1];
+    for (size_t b = 0; b + 1 < start.size(); ++b) start[b + 1] = start[b] + cnt[D][b];
     for (int e = 0; e < E; ++e) perm[start[key[e]]++] = e;
   }
   for (int s = 0; s < E; ++s) pos[perm[s]] = s;
   // ---------------------------------------------------- levels
-  const double eta = h->eta;
-  (void)eta;
   for (int l = 0; l <= D; ++l) {
     Level& L = h->lev[l];
     L.nbox = 1 << (2 * l);
     L.d = H / (1 << l);
-    L.hbegin.assign(L.nbox, 0);
-    L.hend.assign(L.nbox, 0);
-    std::vector<int> cnt(L.nbox, 0);
-    for (int s = 0; s < E; ++s) cnt[key[perm[s]] >> (2 * (D - l))]++;
+    L.hbegin.resize(L.nbox);
+    L.hend.resize(L.nbox);
+    const int* cl = cnt[l].data();
     int acc = 0;
     for (int b = 0; b < L.nbox; ++b) {
       L.hbegin[b] = acc;
-      acc += cnt[b];
+      acc += cl[b];
       L.hend[b] = acc;
-      if (cnt[b] > 0) L.hne.push_back(b);
+      if (cl[b] > 0) L.hne.push_back(b);
     }
     L.nne = (int)L.hne.size();
     // expansion order
@@ -787,14 +831,19 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         double hm = 0;
         for (int e = f0; e < f0 + n; ++e) hm += len[e];
         hm /= n;
+        // the turn between consecutive unit tangents, as its (sine, cosine)
         bool reg = true;
-        double turn0 = 0;
+        double sn0 = 0, cs0 = 0;
         for (int q = 0; q < n && reg; ++q) {
-          const int e = f0 + q, e1 = f0 + (q + 1) % n;
+          const int e = f0 + q, e1 = q + 1 < n ? e + 1 : f0;
           if (std::fabs(len[e] - hm) > 1e-12 * hm) reg = false;
-          const double turn = std::atan2(t[e].x * t[e1].y - t[e].y * t[e1].x, t[e].x * t[e1].x + t[e].y * t[e1].y);
-          if (q == 0) turn0 = turn;
-          else if (std::fabs(turn - turn0) > 1e-12) reg = false;
+          const double sn = t[e].x * t[e1].y - t[e].y * t[e1].x, cs = t[e].x * t[e1].x + t[e].y * t[e1].y;
+          if (q == 0) {
+            sn0 = sn;
+            cs0 = cs;
+          } else if (std::fabs(sn - sn0) > 1e-12 || std::fabs(cs - cs0) > 1e-12) {
+            reg = false;
+          }
         }
         circ[i] = reg ? 1 : 0;
       }
@@ -869,35 +918,41 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   CK(cudaStreamWaitEvent(h->side, h->pre_ev, 0));
   h->astream = h->side;
   int64_t m2l_pairs = 0;
+  std::vector<unsigned char> occ;
   for (int l = 1; l <= D; ++l) {
     Level& L = h->lev[l];
     const int nl = 1 << l, np = 1 << (l - 1);
-    std::vector<int> ptr(1, 0), src, off, img;
-    for (int b : L.hne) {
-      int ix = 0, iy = 0;
-      for (int bb = 0; bb < l; ++bb) { ix |= ((b >> (2 * bb)) & 1) << bb; iy |= ((b >> (2 * bb + 1)) & 1) << bb; }
-      int px = ix >> 1, py = iy >> 1;
+    const int nne = (int)L.hne.size();
+    // occupancy of the level's boxes on the (x, y) grid
+    occ.assign((size_t)nl * nl, 0);
+    for (int b : L.hne) occ[(size_t)unspread_bits((unsigned)b >> 1) * nl + unspread_bits((unsigned)b)] = 1;
+    std::vector<int> ptr(nne + 1, 0), src, off, img;
+    src.reserve((size_t)27 * nne);
+    off.reserve((size_t)27 * nne);
+    img.reserve((size_t)27 * nne);
+    for (int ti = 0; ti < nne; ++ti) {
+      const int b = L.hne[ti];
+      const int ix = (int)unspread_bits((unsigned)b), iy = (int)unspread_bits((unsigned)b >> 1);
+      const int px = ix >> 1, py = iy >> 1;
       for (int pdx = -1; pdx <= 1; ++pdx) {
-        int qx = px + pdx;
+        const int qx = px + pdx;
         if (qx < 0 || qx >= np) continue;
         for (int pdy = -1; pdy <= 1; ++pdy) {
-          int qy = py + pdy;
+          const int qy = py + pdy;
           for (int cx = 0; cx < 2; ++cx)
             for (int cy = 0; cy < 2; ++cy) {
-              int sx = 2 * qx + cx, sy = 2 * qy + cy;
-              int dx = ix - sx, dy = iy - sy;
-              if (std::abs(dx) <= 1 && std::abs(dy) <= 1) continue;
-              int syw = ((sy % nl) + nl) % nl;
-              int m = (sy - syw) / nl;
-              int sb = morton(sx, syw, l);
-              if (L.hend[sb] <= L.hbegin[sb]) continue;
-              src.push_back(sb);
+              const int sx = 2 * qx + cx, sy = 2 * qy + cy;
+              const int dx = ix - sx, dy = iy - sy;
+              if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+              const int syw = sy & (nl - 1);            // nl is a power of two
+              if (!occ[(size_t)syw * nl + sx]) continue;
+              src.push_back(morton(sx, syw, l));
               off.push_back((dx + 3) * 7 + (dy + 3));
-              img.push_back(m);
+              img.push_back((sy - syw) >> l);
             }
         }
       }
-      ptr.push_back((int)src.size());
+      ptr[ti + 1] = (int)src.size();
     }
     L.nil = (int64_t)src.size();
     m2l_pairs += L.nil;
@@ -909,27 +964,30 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     // the same pairs grouped by offset, cut into chunks of at most 16 pairs
     // (small chunks spread one level's translations over many blocks)
     {
-      std::vector<std::vector<int>> by(49);
-      for (size_t ti = 0; ti < L.hne.size(); ++ti)
-        for (int e = ptr[ti]; e < ptr[ti + 1]; ++e) by[off[e]].push_back(e);
-      std::vector<int> ptg, psr, pim, pof, cof, cbg, cen;
-      for (int o = 0; o < 49; ++o) {
-        for (size_t i = 0; i < by[o].size(); ++i) {
-          if (i % 16 == 0) {
-            cof.push_back(o);
-            cbg.push_back((int)ptg.size());
-            cen.push_back((int)ptg.size());
+      // stable counting sort of the CSR entries by offset
+      const size_t n = src.size();
+      int first[50] = {0};
+      for (size_t e = 0; e < n; ++e) first[off[e] + 1]++;
+      for (int o = 0; o < 49; ++o) first[o + 1] += first[o];
+      std::vector<int> ptg(n), psr(n), pim(n), pof(n), cof, cbg, cen;
+      {
+        int at[49];
+        std::copy(first, first + 49, at);
+        for (int ti = 0; ti < nne; ++ti)
+          for (int e = ptr[ti]; e < ptr[ti + 1]; ++e) {
+            const int q = at[off[e]]++;
+            ptg[q] = L.hne[ti];
+            psr[q] = src[e];
+            pim[q] = img[e];
+            pof[q] = off[e];
           }
-          const int e = by[o][i];
-          // target box of CSR entry e
-          const int ti = (int)(std::upper_bound(ptr.begin(), ptr.end(), e) - ptr.begin()) - 1;
-          ptg.push_back(L.hne[ti]);
-          psr.push_back(src[e]);
-          pim.push_back(img[e]);
-          pof.push_back(o);
-          cen.back() = (int)ptg.size();
-        }
       }
+      for (int o = 0; o < 49; ++o)
+        for (int b0 = first[o]; b0 < first[o + 1]; b0 += 16) {
+          cof.push_back(o);
+          cbg.push_back(b0);
+          cen.push_back(std::min(b0 + 16, first[o + 1]));
+        }
       // tensor-core tiles: 128 consecutive non-empty target boxes
       if (h->opt.m2l_mode == 2) {
         const int nt = ((int)L.hne.size() + 127) / 128;

@@ -3,10 +3,34 @@
 #pragma once
 
 #include <algorithm>
+#include <memory>
+#include <utility>
 #include <string>
 #include <vector>
 
 #include "common.cuh"
+
+// Allocator whose value-less construct leaves the element uninitialised, so
+// that resizing a byte buffer that is about to be overwritten does not first
+// fill it with zeros.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) noexcept {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new (static_cast<void*>(p)) U;
+  }
+  template <class U, class... A>
+  void construct(U* p, A&&... a) {
+    ::new (static_cast<void*>(p)) U(std::forward<A>(a)...);
+  }
+};
 #include "../../include/pfmbem.h"
 
 // One level of the uniform quadtree (level 0 = root box of side H).
@@ -229,10 +253,17 @@ struct pfmbem {
   GmresWork gw;
   Prof prof;
   std::vector<void*> allocs;
-  // batched table uploads during set-up (host.cpp upload / flush_uploads)
+  // batched table uploads during set-up (host.cpp upload / flush_uploads):
+  // the open batch is written straight into the page-locked staging arena
+  // when this create holds it, else (or once it overflows) into ub_buf
   bool ub_on = false;
-  bool pin_user = false;           // holds a share of the process-wide page-locked staging arena
-  std::vector<unsigned char> ub_buf;
+  bool pin_user = false;           // counted among the users of the process-wide arena
+  unsigned char* ub_pin = nullptr; // the arena, while this create holds it
+  size_t ub_pin_cap = 0;
+  size_t ub_pin_batch = 0;         // arena offset of the open batch
+  size_t ub_len = 0;               // bytes of the open batch held in the arena
+  bool ub_spill = false;           // the open batch moved to ub_buf
+  std::vector<unsigned char, NoInitAlloc<unsigned char>> ub_buf;
   std::vector<std::pair<void**, size_t>> ub_fix;
   double setup_ms = 0;
 };
