@@ -46,7 +46,32 @@ def parse():
     ap.add_argument("--workload", default="hexagon_8x8_n256", choices=sorted(WORKLOADS))
     ap.add_argument("--launch", type=int, default=0, choices=[0, 1],
                     help="cached matvec: 0 = one cooperative launch per product, 1 = one kernel per stage")
+    ap.add_argument("--stage-times", action="store_true",
+                    help="diagnostic: print the stage durations of the single-launch matvec (4 FP64 and 4 mixed "
+                         "products of the workload, %%globaltimer read by block 0 after every device-wide "
+                         "barrier) on stderr, then exit; no bench line")
     return ap.parse_args()
+
+
+def stage_times(args):
+    os.environ["PFMBEM_STAGE_TIMES"] = "1"      # read by the library at its first product
+    import torch
+    from paper_1910_10863_gb300 import pfmbem as pf
+    from paper_1910_10863_gb300 import workloads as W
+    if not os.path.exists(pf.LIB_PATH):
+        from paper_1910_10863_gb300 import build
+        build.build()
+    w = workload(args.workload)
+    x = torch.from_numpy(W.density_vector(w.E, 3)).cuda()
+    s = pf.Solver(w)
+    pl = s.plan()
+    print(w.name, "depth", pl.depth, "p", list(pl.p)[:pl.depth + 1], file=sys.stderr, flush=True)
+    for prec in (pf.FP64, pf.MIXED):
+        y = torch.zeros_like(x)
+        for _ in range(4):
+            s.matvec(x, y, prec)
+    torch.cuda.synchronize()
+    s.close()
 
 
 # hexagon 8x8 (16384 elements, kH = 5) is the headline block; the 32x32 square
@@ -61,27 +86,47 @@ def workload(name="hexagon_8x8_n256"):
 
 # ------------------------------------------------------------------ clocks
 class Clocks:
-    """nvidia-smi samples (200 ms) during the timed region."""
+    """nvidia-smi samples every 50 ms, kept for the timed region.
+
+    The sampler starts before the warm-up (nvidia-smi takes a while to come up)
+    and the samples are filtered by their timestamps to the window between
+    mark_start() and mark_stop(); a region shorter than the sampling period keeps
+    the nearest sample on either side of it."""
 
     def __init__(self, index):
         self.index = index
         self.proc = None
         self.path = None
+        self.t0 = self.t1 = None
 
     def start(self):
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
 
+    def wait_first(self, timeout=10.0):
+        t = time.time()
+        while self.proc is not None and time.time() - t < timeout:
+            if os.path.getsize(self.path) > 0 or self.proc.poll() is not None:
+                return
+            time.sleep(0.02)
+
+    def mark_start(self):
+        self.t0 = time.time()
+
+    def mark_stop(self):
+        self.t1 = time.time()
+
     def stop(self):
+        import datetime
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -89,23 +134,30 @@ class Clocks:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        sm, mx, reasons = [], [], set()
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
-            if len(f) < 9:
+            if len(f) < 10:
                 continue
             try:
-                sm.append(float(f[1]))
-                mx.append(float(f[2]))
+                ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[5:9]):
-                if v.lower().startswith("active"):
-                    reasons.add(nm)
         os.unlink(self.path)
+        t0, t1 = self.t0 or 0.0, self.t1 or 1e300
+        keep = [r for r in rows if t0 <= r[0] <= t1]
+        if not keep and rows:
+            before = [r for r in rows if r[0] < t0]
+            after = [r for r in rows if r[0] > t1]
+            keep = ([before[-1]] if before else []) + ([after[0]] if after else [])
+        sm = [r[1] for r in keep]
+        mx = [r[2] for r in keep]
+        reasons = sorted({nm for r in keep for nm, v in zip(names, r[3]) if v.lower().startswith("active")})
         return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "samples": len(sm), "reasons": sorted(reasons)}
+                "samples": len(sm), "in_window": bool(keep) and all(t0 <= r[0] <= t1 for r in keep),
+                "reasons": reasons}
 
 
 # ------------------------------------------------------------------ CPU oracle sample
@@ -175,6 +227,9 @@ def main():
     dist = None
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.stage_times:
+        stage_times(args)
         return
     import torch
     torch.cuda.set_device(local)
@@ -251,12 +306,15 @@ def main():
             tot += e0.elapsed_time(e1)
         return tot / steps
 
-    for _ in range(args.warmup):
-        step()
-    barrier()
     clocks = Clocks(local)
     clocks.start()
+    for _ in range(args.warmup):
+        step()
+    clocks.wait_first()
+    barrier()
+    clocks.mark_start()
     ms_step = timed(host=False, profile=False)
+    clocks.mark_stop()
     clk = clocks.stop()
     main_stats = dict(stats)
     barrier()
@@ -319,7 +377,7 @@ def main():
     fp64_peak = pf.pfmbem_probe_peak(0)
     fp32_peak = pf.pfmbem_probe_peak(1)
     roof = roofline(names, ms_ph, prof_acc["launches"], prof_steps, plan, fp64_peak, fp32_peak, w.E,
-                    tensor_m2l=(opt.m2l_mode == 2))
+                    tensor_m2l=(opt.m2l_mode == 2), workload=w.name)
     ms_ph = ms_ph / prof_steps
 
     cpu = None
@@ -388,7 +446,30 @@ def bf16_peak():
         return 1700.0, "fallback 1.7 PFLOP/s sustained"
 
 
-def roofline(names, ms_ph, la_ph, steps, plan, fp64_peak, fp32_peak, E, tensor_m2l=False):
+# DRAM bytes (read + write) per launch of the single-launch matvec, from one
+# ncu capture of the hexagon 8x8 block (profiles/matvec_fused_hexagon_8x8_n256.md).
+# Valid only while the kernel source is the captured one: keyed by the sha256
+# of matvec_fused.cu, else the line reports traffic null.
+NCU_TRAFFIC = {
+    "sha256": "5c3cc00f642b4b9c1e2144cd358f7376218521368d707ba7f0a282d390879825",
+    ("hexagon_8x8_n256_kH5", "matvec_fused"): 162317312,
+    ("hexagon_8x8_n256_kH5", "matvec_fused_f32"): 79378688,
+}
+
+
+def captured_traffic(workload, kernel):
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_1910_10863_gb300", "csrc", "matvec_fused.cu")
+    try:
+        with open(src, "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != NCU_TRAFFIC["sha256"]:
+                return None
+    except OSError:
+        return None
+    return NCU_TRAFFIC.get((workload, kernel))
+
+
+def roofline(names, ms_ph, la_ph, steps, plan, fp64_peak, fp32_peak, E, tensor_m2l=False, workload=""):
     dom = int(np.argmax(ms_ph))
     name = names[dom]
     ms_step = ms_ph[dom] / steps
@@ -413,8 +494,8 @@ def roofline(names, ms_ph, la_ph, steps, plan, fp64_peak, fp32_peak, E, tensor_m
         nbytes = ((plan.near_blocks * 4 + plan.fiber_entries + 2 * 2 * E * PD) * csz
                   + 2 * 2 * E * 16 + 2 * 2 * 2 * E * csz)
         ach = nbytes / (per_launch * 1e-3) / 1e9
-        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm, traffic=None,
-                   peak_source=hbm_src, bytes_per_launch=int(nbytes))
+        out.update(bound="hbm", achieved=ach, peak=hbm, unit="GB/s", frac=ach / hbm,
+                   traffic=captured_traffic(workload, name), peak_source=hbm_src, bytes_per_launch=int(nbytes))
     elif name.startswith("near_p2p") and plan.cached:
         nbytes = plan.near_blocks * 4 * csz + 2 * E * csz * 3
         ach = nbytes / (per_launch * 1e-3) / 1e9

@@ -463,6 +463,26 @@ static pfmbem_status build_pair_tables(pfmbem* h, const double* nodes, const std
   return PFMBEM_OK;
 }
 
+// Issues the launches of f on set-up stream i, ordered after everything issued
+// so far on the main stream; the main stream waits for them at the join of
+// build_plan (aux_ev).  While f runs, h->stream names stream i, so that the
+// launchers, allocations and profiling events of f go there.
+template <class F>
+static pfmbem_status on_aux(pfmbem* h, int i, F&& f) {
+  if (!h->aux[i]) CK(cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking));
+  if (!h->aux_ev[i]) CK(cudaEventCreateWithFlags(&h->aux_ev[i], cudaEventDisableTiming));
+  if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(h->fork_ev, h->stream));
+  CK(cudaStreamWaitEvent(h->aux[i], h->fork_ev, 0));
+  cudaStream_t main_stream = h->stream;
+  h->stream = h->aux[i];
+  const pfmbem_status st = f();
+  h->stream = main_stream;
+  if (st != PFMBEM_OK) return st;
+  CK(cudaEventRecord(h->aux_ev[i], h->aux[i]));
+  return PFMBEM_OK;
+}
+
 static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) {
   const double t0 = now_ms();
   const int M = h->M;
@@ -799,15 +819,20 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // ---------------------------------------------------- lattice sums + root operator
   if (!h->side_ev) CK(cudaEventCreateWithFlags(&h->side_ev, cudaEventDisableTiming));
   {
-    Level& R = h->lev[0];
-    const int p0 = R.p, P0 = R.P, jmax = 2 * p0;
-    cplx* Sd = dalloc<cplx>(h, jmax + 1);
-    h->root = dalloc<cplx>(h, (size_t)P0 * P0);
-    h->rootf = dalloc<cplxf>(h, (size_t)P0 * P0);
-    if (!Sd || !h->root || !h->rootf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (lattice sums)");
-    CK(k_lattice_sums(h, jmax, h->lattice_q, Sd));
-    // root translation R[a][n] = w_a S_{|n-a|} w_n, built on the device
-    CK(k_root_operator(h, p0, R.w_dev, Sd));
+    // on their own stream: nothing else of the set-up waits for them until the join
+    pfmbem_status st = on_aux(h, 0, [&]() -> pfmbem_status {
+      Level& R = h->lev[0];
+      const int p0 = R.p, P0 = R.P, jmax = 2 * p0;
+      cplx* Sd = dalloc<cplx>(h, jmax + 1);
+      h->root = dalloc<cplx>(h, (size_t)P0 * P0);
+      h->rootf = dalloc<cplxf>(h, (size_t)P0 * P0);
+      if (!Sd || !h->root || !h->rootf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (lattice sums)");
+      CK(k_lattice_sums(h, jmax, h->lattice_q, Sd));
+      // root translation R[a][n] = w_a S_{|n-a|} w_n, built on the device
+      CK(k_root_operator(h, p0, R.w_dev, Sd));
+      return PFMBEM_OK;
+    });
+    if (st != PFMBEM_OK) return st;
   }
   mark("lattice sums, root");
   // the second stream starts after everything uploaded so far (level weights)
@@ -863,6 +888,21 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     CK(cudaMemGetInfo(&freeb, &totb));
     if (bytes < 0.5 * (double)freeb) {
       pfmbem_status st;
+      // P2M/L2P caches (element geometry only) on their own stream
+      st = on_aux(h, 1, [&]() -> pfmbem_status {
+        const size_t nc = (size_t)E * 2 * h->lev[D].P;
+        h->p2m_c = dalloc<cplx>(h, nc);
+        h->l2p_c = dalloc<cplx>(h, nc);
+        h->p2m_cf = dalloc<cplxf>(h, nc);
+        h->l2p_cf = dalloc<cplxf>(h, nc);
+        h->densf = dalloc<cplxf>(h, (size_t)2 * E);
+        h->Uf = dalloc<cplxf>(h, (size_t)2 * E);
+        if (!h->p2m_c || !h->l2p_c || !h->p2m_cf || !h->l2p_cf || !h->densf || !h->Uf)
+          return fail(h, PFMBEM_ENOMEM, "device allocation failed (P2M/L2P caches)");
+        CK(k_build_fmm_caches(h));
+        return PFMBEM_OK;
+      });
+      if (st != PFMBEM_OK) return st;
       if ((st = upload(h, &h->nc_base, nc_base)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->nc_sbase, nc_sbase)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->nc_src, nc_src)) != PFMBEM_OK) return st;
@@ -911,6 +951,75 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       mark("cache allocation");
       CK(k_build_caches(h));
       cache = true;
+      // the fiber symbols and the preconditioner go to the GPU now, ahead of
+      // the host's M2L lists
+      h->cached = true;
+      if (h->opt.launch == 0) {
+        // fibers applied by FFT (regular polygons with 2^j elements, 8 <= N <= 1024)
+        // and the row chunks of the others
+        std::vector<int> fft, zchunk;
+        std::vector<int64_t> fhb(M, -1);
+        const std::vector<int>& circh = h->hcirc;
+        int64_t fa = 0;
+        for (int i = 0; i < M; ++i) {
+          const int n = foff[i + 1] - foff[i];
+          if (circh[i] && n >= 8 && n <= 1024 && (n & (n - 1)) == 0) {
+            fft.push_back(i);
+            fhb[i] = fa;
+            fa += n;
+          } else {
+            for (int r = 0; r < 2 * n; r += 32) {
+              zchunk.push_back(i);
+              zchunk.push_back(r);
+              zchunk.push_back(std::min(r + 32, 2 * n));
+            }
+          }
+        }
+        h->fz_nfft = (int)fft.size();
+        h->fz_nchunk = (int)zchunk.size() / 3;
+        if ((st = upload(h, &h->fz_fft, fft)) != PFMBEM_OK) return st;
+        if ((st = upload(h, &h->fz_chunk, zchunk)) != PFMBEM_OK) return st;
+        if ((st = upload(h, &h->fh_base, fhb)) != PFMBEM_OK) return st;
+        std::vector<cplx> twh(512);
+        for (int j = 0; j < 512; ++j) twh[j] = cplx{std::cos(2.0 * M_PI * j / 1024.0), std::sin(2.0 * M_PI * j / 1024.0)};
+        if ((st = upload(h, &h->tw, twh)) != PFMBEM_OK) return st;
+        if ((st = upload(h, &h->twf, to_float(twh))) != PFMBEM_OK) return st;
+        if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
+        h->fh_val = dalloc<cplx>(h, (size_t)4 * fa);
+        h->fh_valf = dalloc<cplxf>(h, (size_t)4 * fa);
+        if (!h->fh_val || !h->fh_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber symbols)");
+        CK(k_fiber_symbols(h));
+        if (h->opt.precond == 0 && h->fz_nfft > 0) {
+          h->pc_val = dalloc<cplx>(h, (size_t)4 * fa);
+          h->pc_valf = dalloc<cplxf>(h, (size_t)4 * fa);
+          if (!h->pc_val || !h->pc_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (preconditioner)");
+          CK(k_precond_symbols(h));
+        }
+        if (h->opt.precond == 0) {
+          // the other regular polygons: preconditioner kept as a circulant row pair
+          std::vector<int> prl;
+          std::vector<int64_t> prb(M, -1);
+          int64_t pa = 0;
+          for (int i = 0; i < M; ++i) {
+            const int n = foff[i + 1] - foff[i];
+            if (circh[i] && fhb[i] < 0) {
+              prl.push_back(i);
+              prb[i] = pa;
+              pa += 4 * (int64_t)n;
+            }
+          }
+          if (!prl.empty()) {
+            h->npr = (int)prl.size();
+            if ((st = upload(h, &h->pr_list, prl)) != PFMBEM_OK) return st;
+            if ((st = upload(h, &h->pr_base, prb)) != PFMBEM_OK) return st;
+            if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
+            h->pr_val = dalloc<cplx>(h, (size_t)pa);
+            h->pr_valf = dalloc<cplxf>(h, (size_t)pa);
+            if (!h->pr_val || !h->pr_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (preconditioner)");
+            CK(k_precond_rows(h));
+          }
+        }
+      }
     }
   }
   if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
@@ -1094,90 +1203,17 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // join: later work on the main stream sees every upload of the second stream
   CK(cudaEventRecord(h->side_ev, h->side));
   CK(cudaStreamWaitEvent(h->stream, h->side_ev, 0));
+  for (int i = 0; i < 2; ++i)
+    if (h->aux[i]) CK(cudaStreamWaitEvent(h->stream, h->aux_ev[i], 0));
   h->astream = nullptr;
   for (int l = 1; l <= D; ++l)
     if (h->lev[l].tc_B) CK(k_tc_build_operator(h, l));
   if (cache) {
-    const size_t nc = (size_t)E * 2 * h->lev[D].P;
-    h->p2m_c = dalloc<cplx>(h, nc);
-    h->l2p_c = dalloc<cplx>(h, nc);
-    h->p2m_cf = dalloc<cplxf>(h, nc);
-    h->l2p_cf = dalloc<cplxf>(h, nc);
-    h->densf = dalloc<cplxf>(h, (size_t)2 * E);
-    h->Uf = dalloc<cplxf>(h, (size_t)2 * E);
-    if (!h->p2m_c || !h->l2p_c || !h->p2m_cf || !h->l2p_cf || !h->densf || !h->Uf)
-      return fail(h, PFMBEM_ENOMEM, "device allocation failed (P2M/L2P caches)");
-    CK(k_build_fmm_caches(h));
-    h->cached = true;
     // single-launch matvec unless the tensor-core M2L (its own kernel) is on
     bool tensor = false;
     for (int l = 1; l <= D; ++l) tensor = tensor || (h->lev[l].tc_B != nullptr && h->lev[l].tc_ntile > 0);
     if (h->opt.launch == 0 && !tensor) {
-      // fibers applied by FFT (regular polygons with 2^j elements, 8 <= N <= 1024)
-      // and the row chunks of the others
-      std::vector<int> fft, zchunk;
-      std::vector<int64_t> fhb(M, -1);
-      const std::vector<int>& circh = h->hcirc;
-      int64_t fa = 0;
-      for (int i = 0; i < M; ++i) {
-        const int n = foff[i + 1] - foff[i];
-        if (circh[i] && n >= 8 && n <= 1024 && (n & (n - 1)) == 0) {
-          fft.push_back(i);
-          fhb[i] = fa;
-          fa += n;
-        } else {
-          for (int r = 0; r < 2 * n; r += 32) {
-            zchunk.push_back(i);
-            zchunk.push_back(r);
-            zchunk.push_back(std::min(r + 32, 2 * n));
-          }
-        }
-      }
       pfmbem_status st;
-      h->fz_nfft = (int)fft.size();
-      h->fz_nchunk = (int)zchunk.size() / 3;
-      if ((st = upload(h, &h->fz_fft, fft)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->fz_chunk, zchunk)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->fh_base, fhb)) != PFMBEM_OK) return st;
-      std::vector<cplx> twh(512);
-      for (int j = 0; j < 512; ++j) twh[j] = cplx{std::cos(2.0 * M_PI * j / 1024.0), std::sin(2.0 * M_PI * j / 1024.0)};
-      if ((st = upload(h, &h->tw, twh)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->twf, to_float(twh))) != PFMBEM_OK) return st;
-      if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
-      h->fh_val = dalloc<cplx>(h, (size_t)4 * fa);
-      h->fh_valf = dalloc<cplxf>(h, (size_t)4 * fa);
-      if (!h->fh_val || !h->fh_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber symbols)");
-      CK(k_fiber_symbols(h));
-      if (h->opt.precond == 0 && h->fz_nfft > 0) {
-        h->pc_val = dalloc<cplx>(h, (size_t)4 * fa);
-        h->pc_valf = dalloc<cplxf>(h, (size_t)4 * fa);
-        if (!h->pc_val || !h->pc_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (preconditioner)");
-        CK(k_precond_symbols(h));
-      }
-      if (h->opt.precond == 0) {
-        // the other regular polygons: preconditioner kept as a circulant row pair
-        std::vector<int> prl;
-        std::vector<int64_t> prb(M, -1);
-        int64_t pa = 0;
-        for (int i = 0; i < M; ++i) {
-          const int n = foff[i + 1] - foff[i];
-          if (circh[i] && fhb[i] < 0) {
-            prl.push_back(i);
-            prb[i] = pa;
-            pa += 4 * (int64_t)n;
-          }
-        }
-        if (!prl.empty()) {
-          h->npr = (int)prl.size();
-          if ((st = upload(h, &h->pr_list, prl)) != PFMBEM_OK) return st;
-          if ((st = upload(h, &h->pr_base, prb)) != PFMBEM_OK) return st;
-          if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
-          h->pr_val = dalloc<cplx>(h, (size_t)pa);
-          h->pr_valf = dalloc<cplxf>(h, (size_t)pa);
-          if (!h->pr_val || !h->pr_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (preconditioner)");
-          CK(k_precond_rows(h));
-        }
-      }
       bool ok = false;
       h->rootc = dalloc<cplx>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
       h->rootcf = dalloc<cplxf>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
@@ -1705,6 +1741,8 @@ pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nod
 void pfmbem_destroy(pfmbem_t h) {
   if (!h) return;
   if (h->side) cudaStreamSynchronize(h->side);
+  for (int i = 0; i < 2; ++i)
+    if (h->aux[i]) cudaStreamSynchronize(h->aux[i]);
   for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   if (h->stream) cudaStreamSynchronize(h->stream);
   else cudaDeviceSynchronize();
@@ -1713,6 +1751,11 @@ void pfmbem_destroy(pfmbem_t h) {
   if (h->side_ev) cudaEventDestroy(h->side_ev);
   if (h->pre_ev) cudaEventDestroy(h->pre_ev);
   if (h->side) cudaStreamDestroy(h->side);
+  for (int i = 0; i < 2; ++i) {
+    if (h->aux_ev[i]) cudaEventDestroy(h->aux_ev[i]);
+    if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
+  }
+  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
   prof_release(h);
   delete h;
 }

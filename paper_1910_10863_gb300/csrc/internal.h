@@ -126,6 +126,9 @@ struct pfmbem {
   cudaStream_t side = nullptr;   // second stream of the set-up: host planning overlaps the cache build
   cudaEvent_t side_ev = nullptr;
   cudaEvent_t pre_ev = nullptr;    // main-stream point the second stream waits for
+  cudaStream_t aux[2] = {nullptr, nullptr};   // set-up streams: lattice sums / P2M-L2P caches
+  cudaEvent_t aux_ev[2] = {nullptr, nullptr};
+  cudaEvent_t fork_ev = nullptr;
   cudaStream_t astream = nullptr;  // stream of allocations and uploads while set-up runs on `side`
   std::string err;
   // plan

@@ -70,10 +70,8 @@ __device__ __forceinline__ cplx warp_sum(cplx v) {
   return v;
 }
 __device__ __forceinline__ cplx ipow_phase(cplx alpha, int m) {
-  // alpha^m for m in {-1, 0, 1}
-  if (m == 0) return cplx{1, 0};
-  if (m == 1) return alpha;
-  return cdiv(cplx{1, 0}, alpha);
+  // alpha^m for m in {-1, 0, 1}; |alpha| = 1, so alpha^{-1} = conj(alpha)
+  return m == 0 ? cplx{1, 0} : (m > 0 ? alpha : conj(alpha));
 }
 
 // ---------------------------------------------------------------- profiling

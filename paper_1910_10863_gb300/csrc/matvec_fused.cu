@@ -264,16 +264,19 @@ __global__ void fiber_symbol_kernel(const int* __restrict__ fib_list, const int*
 // L(0) from the four level-1 multipoles: Rc = R T_0, with R the periodic root
 // translation and T_0 the level-1 -> root M2M, stored [u][l] for the 4 P_1
 // child coefficients u, so that the fused product never forms M(0).  One
-// thread per entry, FP64, with an FP32 copy.
+// warp per entry (lanes over the P_0 terms), FP64, with an FP32 copy.
 __global__ void root_fold_kernel(int P0, int K, const cplx* __restrict__ R, const cplx* __restrict__ m2m0,
                                  cplx* __restrict__ rc, cplxf* __restrict__ rcf) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (i >= P0 * K) return;
   const int u = i / P0, t = i - u * P0;
   cplx s{0, 0};
-  for (int n = 0; n < P0; ++n) s += R[(size_t)t * P0 + n] * m2m0[(size_t)u * P0 + n];
-  rc[i] = s;
-  rcf[i] = to_f(s);
+  for (int n = lane; n < P0; n += 32) s += R[(size_t)t * P0 + n] * m2m0[(size_t)u * P0 + n];
+  s = wsum(s);
+  if (lane == 0) {
+    rc[i] = s;
+    rcf[i] = to_f(s);
+  }
 }
 
 // Near-field sum of one target (sorted element s) from its leaf's cached
@@ -966,7 +969,7 @@ cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
   if (h->fz_grid64 <= 0 || h->fz_grid32 <= 0) return cudaSuccess;
   const int P0 = h->lev[0].P, K = 4 * h->lev[1].P;
   prof_begin(h, PH_SETUP);
-  root_fold_kernel<<<(P0 * K + 127) / 128, 128, 0, h->stream>>>(P0, K, h->root, h->lev[0].m2m, h->rootc, h->rootcf);
+  root_fold_kernel<<<(P0 * K + 7) / 8, 256, 0, h->stream>>>(P0, K, h->root, h->lev[0].m2m, h->rootc, h->rootcf);
   prof_end(h, PH_SETUP);
   *ok = true;
   return cudaGetLastError();
