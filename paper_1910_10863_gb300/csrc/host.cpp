@@ -722,6 +722,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
           ++ns;
         }
       nc_sbase.push_back((int)nc_src.size());
+      h->nc_maxns = std::max(h->nc_maxns, ns);
+      h->leaf_maxn = std::max(h->leaf_maxn, Lf.hend[b] - Lf.hbegin[b]);
       nc_base.push_back(acc);
       acc += 4 * (int64_t)(Lf.hend[b] - Lf.hbegin[b]) * ns;
     }

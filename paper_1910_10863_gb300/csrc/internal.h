@@ -173,6 +173,8 @@ struct pfmbem {
   cplx* nc_val = nullptr;        // [blocks][4]
   cplxf* nc_valf = nullptr;
   int64_t nc_blocks = 0;
+  int nc_maxns = 0;              // longest source list of a leaf
+  int leaf_maxn = 0;             // most elements in a leaf
   // cached fiber blocks: the diagonal block of (I - A) of every fiber without
   // the FMM part (identity, k1 operators, self terms), row-major [2N][2N]
   int64_t* fb_base = nullptr;    // [M] offset of the fiber's block

@@ -915,11 +915,31 @@ __global__ void pair_table_kernel(int ntab, const int* __restrict__ tA, const in
   }
 }
 
+// Table lookup of one near pair (target fiber fs, source fiber ff, true image
+// shift mt): -2 = the k table of fs (same fiber, same image, regular polygon),
+// >= 0 = a fiber-pair table, -1 = none (integrate).
+__device__ __forceinline__ int near_lookup(int fs, int ff, int mt, int64_t kb, const int* __restrict__ pl_ptr,
+                                           const int* __restrict__ pl_fib, const int* __restrict__ pl_img,
+                                           const int* __restrict__ pl_tab) {
+  if (ff == fs && mt == 0) return kb >= 0 ? -2 : -1;
+  if (pl_ptr)
+    for (int q = pl_ptr[fs]; q < pl_ptr[fs + 1]; ++q)
+      if (pl_fib[q] == ff && pl_img[q] == mt) return pl_tab[q];
+  return -1;
+}
+
+constexpr int NB_RUNS = 8;       // target runs per leaf whose lookups are shared through shared memory
+
+// Phase 1 of the near-field build, one block per leaf.  The leaf's sources and
+// targets are described once in shared memory, and the table of every
+// (target run, source) pair is looked up once: a run is a stretch of targets of
+// one fiber and one wrap shift m0 (the sort by leaf key is stable and the
+// input is fiber-major, so a leaf holds few).  Then every block (t, j) that a
+// table covers is copied and scaled by (i/4) alpha^m; the others are queued for
+// near_direct_kernel.
 __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restrict__ bb, const int* __restrict__ be,
                                   const int64_t* __restrict__ base, const int* __restrict__ sbase,
-                                  const int* __restrict__ srcf, const int* __restrict__ srcm, double k, double eta,
-                                  double H, cplx alpha, const double2* __restrict__ sc, const double2* __restrict__ st,
-                                  const double2* __restrict__ snu, const double* __restrict__ sh,
+                                  const int* __restrict__ srcf, const int* __restrict__ srcm, double eta, cplx alpha,
                                   const int* __restrict__ perm, const int* __restrict__ ofib,
                                   const int* __restrict__ foff, const int* __restrict__ sm0,
                                   const int64_t* __restrict__ kbase, const cplx* __restrict__ kval,
@@ -930,63 +950,111 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
                                   cplx* __restrict__ val, cplxf* __restrict__ valf,
                                   unsigned long long* __restrict__ queue, unsigned* __restrict__ qlen,
                                   unsigned qcap) {
+  extern __shared__ int nbs[];
   const int li = blockIdx.x;
   const int box = ne[li];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int s0 = bb[box], nt = be[box] - s0;
   const int j0 = sbase[li], ns = sbase[li + 1] - j0;
+  int* s_f = nbs;                    // [ns] source element (sorted)
+  int* s_ef = s_f + ns;              // [ns] its original index
+  int* s_ff = s_ef + ns;             // [ns] its fiber
+  int* s_dm = s_ff + ns;             // [ns] image m minus the source's wrap shift m0
+  int* s_m = s_dm + ns;              // [ns] image m
+  int* t_run = s_m + ns;             // [nt] run of the target (-1: beyond NB_RUNS)
+  int* t_es = t_run + nt;            // [nt] original index, fiber and wrap shift of the target
+  int* t_fs = t_es + nt;
+  int* t_ms = t_fs + nt;
+  int* r_fs = t_ms + nt;             // [NB_RUNS] fiber and wrap shift of each run
+  int* r_ms = r_fs + NB_RUNS;
+  int* r_tab = r_ms + NB_RUNS;       // [NB_RUNS][ns] table per (run, source)
+  __shared__ int s_nrun;
+  for (int j = threadIdx.x; j < ns; j += blockDim.x) {
+    const int f = srcf[j0 + j], m = srcm[j0 + j], ef = perm[f];
+    s_f[j] = f;
+    s_ef[j] = ef;
+    s_ff[j] = ofib[ef];
+    s_dm[j] = m - sm0[f];
+    s_m[j] = m;
+  }
+  for (int t = threadIdx.x; t < nt; t += blockDim.x) {
+    const int es = perm[s0 + t];
+    t_es[t] = es;
+    t_fs[t] = ofib[es];
+    t_ms[t] = sm0[s0 + t];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int nr = 0, pf = -1, pm = 0;
+    for (int t = 0; t < nt; ++t) {
+      const int fs = t_fs[t], ms = t_ms[t];
+      if (t == 0 || fs != pf || ms != pm) {
+        if (nr < NB_RUNS) {
+          r_fs[nr] = fs;
+          r_ms[nr] = ms;
+        }
+        ++nr;
+        pf = fs;
+        pm = ms;
+      }
+      t_run[t] = nr - 1 < NB_RUNS ? nr - 1 : -1;
+    }
+    s_nrun = nr < NB_RUNS ? nr : NB_RUNS;
+  }
+  __syncthreads();
+  const int nr = s_nrun;
+  for (int q = threadIdx.x; q < nr * ns; q += blockDim.x) {
+    const int r = q / ns, j = q - r * ns;
+    const int fs = r_fs[r];
+    r_tab[q] = near_lookup(fs, s_ff[j], s_dm[j] + r_ms[r], kbase[fs], pl_ptr, pl_fib, pl_img, pl_tab);
+  }
+  __syncthreads();
+  const cplx q4{0.0, 0.25};
   for (int t = warp; t < nt; t += nw) {
     const int s = s0 + t;
-    const double2 x = sc[s], nx = snu[s];
-    // target's fiber; kb >= 0 when the fiber is a regular polygon with a table
-    const int es = perm[s], fs = ofib[es], ms = sm0[s];
+    const int es = t_es[t], fs = t_fs[t], ms = t_ms[t];
     const int64_t kb = kbase[fs];
-    const int fN = foff[fs + 1] - foff[fs];
+    const int fN = foff[fs + 1] - foff[fs], fo = foff[fs];
+    const int r = t_run[t];
     cplx* row = val + base[li] + (int64_t)t * ns * 4;
     cplxf* rowf = valf ? valf + base[li] + (int64_t)t * ns * 4 : nullptr;
     for (int j = lane; j < ns; j += 32) {
-      const int f = srcf[j0 + j], m = srcm[j0 + j];
+      const int m = s_m[j];
       cplx b0{0, 0}, b1{0, 0}, b2{0, 0}, b3{0, 0};
-      if (!(f == s && m == 0)) {
-        cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
-        const int ef = perm[f];
-        // same fiber and, in true coordinates, the same image (the wrapped copies
-        // differ by m + m0_s - m0_f periods): the pair is a rotation of a table entry
-        const int ff = ofib[ef], mt = m + ms - sm0[f];
-        int tab = -1;
-        if (!(ff == fs && mt == 0) && pl_ptr)
-          for (int q = pl_ptr[fs]; q < pl_ptr[fs + 1]; ++q)
-            if (pl_fib[q] == ff && pl_img[q] == mt) {
-              tab = pl_tab[q];
-              break;
-            }
-        if (kb >= 0 && ff == fs && mt == 0) {
+      if (!(s_f[j] == s && m == 0)) {
+        const int ef = s_ef[j], ff = s_ff[j];
+        const int tab = r >= 0 ? r_tab[r * ns + j]
+                               : near_lookup(fs, ff, s_dm[j] + ms, kb, pl_ptr, pl_fib, pl_img, pl_tab);
+        const cplx* tv;
+        if (tab == -2) {
+          // same fiber and, in true coordinates, the same image: a rotation of the k table
           int dl = ef - es;
           if (dl < 0) dl += fN;
-          const cplx* tv = kval + 4 * (kb + dl);
-          S = tv[0];
-          Dv = tv[1];
-          K = tv[2];
-          T = tv[3];
+          tv = kval + 4 * (kb + dl);
         } else if (tab >= 0) {
           // a translated copy of a fiber pair whose integrals are tabulated
-          const cplx* tv = tab_val + 4 * (tab_base[tab] + (int64_t)(es - foff[fs]) * tab_nb[tab] + (ef - foff[ff]));
-          S = tv[0];
-          Dv = tv[1];
-          K = tv[2];
-          T = tv[3];
+          tv = tab_val + 4 * (tab_base[tab] + (int64_t)(es - fo) * tab_nb[tab] + (ef - foff[ff]));
         } else {
-          // integrated by near_direct_kernel: queue (leaf, target row, source column)
           const unsigned at = atomicAdd(qlen, 1u);
           if (at < qcap)
             queue[at] = ((unsigned long long)li << 40) | ((unsigned long long)t << 24) | (unsigned long long)j;
           continue;
         }
-        const cplx ph = mul_i(0.25 * ipow_phase(alpha, m));      // (i/4) alpha^m
-        b0 = ph * Dv;
-        b1 = (-eta) * mul_i(ph * S);
-        b2 = ph * T;
-        b3 = (-eta) * mul_i(ph * K);
+        const cplx S = tv[0], Dv = tv[1], K = tv[2], T = tv[3];
+        if (m == 0) {
+          // (i/4) {D, -i eta S, T, -i eta K} = {(i/4) D, (eta/4) S, (i/4) T, (eta/4) K}
+          const double e4 = 0.25 * eta;
+          b0 = cplx{-0.25 * Dv.im, 0.25 * Dv.re};
+          b1 = cplx{e4 * S.re, e4 * S.im};
+          b2 = cplx{-0.25 * T.im, 0.25 * T.re};
+          b3 = cplx{e4 * K.re, e4 * K.im};
+        } else {
+          const cplx ph = q4 * ipow_phase(alpha, m);         // (i/4) alpha^m
+          b0 = ph * Dv;
+          b1 = (-eta) * mul_i(ph * S);
+          b2 = ph * T;
+          b3 = (-eta) * mul_i(ph * K);
+        }
       }
       row[4 * j + 0] = b0;
       row[4 * j + 1] = b1;
@@ -1164,12 +1232,21 @@ cudaError_t k_build_caches(pfmbem* h) {
   }
   cudaMemsetAsync(h->nq_len, 0, sizeof(unsigned), st);
   prof_begin(h, PH_BUILD);
-  near_build_kernel<<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
-                                              h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c, h->s_t,
-                                              h->s_nu, h->s_h, h->s_perm, h->o_fiber, h->fib_off, h->s_m0,
-                                              h->kt_base, h->kt_val, h->ntab > 0 ? h->pl_ptr : nullptr, h->pl_fib,
-                                              h->pl_img, h->pl_tab, h->tab_start, h->tab_nb, h->tab_val, h->nc_val,
-                                              h->nc_valf, h->nq, h->nq_len, h->nq_cap);
+  {
+    // per-source arrays, the run and description of every target, the runs and their lookups
+    const size_t smem = sizeof(int) * (5 * (size_t)h->nc_maxns + 4 * (size_t)h->leaf_maxn + 2 * NB_RUNS +
+                                       (size_t)NB_RUNS * h->nc_maxns);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(near_build_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    near_build_kernel<<<leaf.nne, 256, smem, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
+                                                   h->nc_src, h->nc_img, h->eta, h->alpha, h->s_perm, h->o_fiber,
+                                                   h->fib_off, h->s_m0, h->kt_base, h->kt_val,
+                                                   h->ntab > 0 ? h->pl_ptr : nullptr, h->pl_fib, h->pl_img, h->pl_tab,
+                                                   h->tab_start, h->tab_nb, h->tab_val, h->nc_val, h->nc_valf, h->nq,
+                                                   h->nq_len, h->nq_cap);
+  }
   prof_end(h, PH_BUILD);
   prof_begin(h, PH_BUILD);
   near_direct_kernel<<<1216, 128, 0, st>>>(h->nq, h->nq_len, h->nq_cap, leaf.ne, leaf.box_begin, h->nc_base,
