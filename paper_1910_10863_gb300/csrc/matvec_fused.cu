@@ -146,24 +146,39 @@ __device__ __forceinline__ C wsum(C v) {
   return v;
 }
 
-// Device-wide barrier with a bounded wait; false when any block gave up.
+// Device-wide barrier with a bounded wait; false when any block gave up.  The
+// arrival is an acquire-release add at GPU scope (it publishes this block's
+// writes and, for the last arrival, takes in everyone else's); the last
+// arrival resets the counter and advances the generation word with a release
+// add, and the others poll the generation with acquire loads.
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
 __device__ bool grid_barrier(unsigned* bar, int* err) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* gen = bar + 1;
-    const unsigned g = *gen;
-    __threadfence();                           // this block's writes before the arrival
+    const unsigned g = ld_acquire(bar + 1);
     int ok = 1;
-    if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+    if (atom_add_acq_rel(bar, 1u) == gridDim.x - 1) {
       atomicExch(bar, 0u);
-      __threadfence();
-      atomicAdd(bar + 1, 1u);                  // release the other blocks
+      red_add_release(bar + 1, 1u);            // release the other blocks
     } else {
-      // spin on the generation word; give up after one second of device time
+      // poll the generation word; give up after one second of device time
       unsigned long long t0, t;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-      while (*gen == g) {
+      while (ld_acquire(bar + 1) == g) {
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
         if (t - t0 > 1000000000ull) {
           atomicExch(err, 1);
@@ -172,7 +187,6 @@ __device__ bool grid_barrier(unsigned* bar, int* err) {
         }
       }
     }
-    __threadfence();                           // other blocks' writes after the release
     s_ok = ok && *(volatile int*)err == 0;
   }
   __syncthreads();
