@@ -1197,6 +1197,24 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
     CK(k_tables(h, tl, h->astream ? h->astream : h->stream));
   }
+  if (cache && h->opt.launch == 0) {
+    // top operators of the single-launch product, on the second stream once the
+    // root operator (first set-up stream) and the M2M tables are there
+    h->rootc = dalloc<cplx>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
+    h->rootcf = dalloc<cplxf>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
+    if (!h->rootc || !h->rootcf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (root operator)");
+    if (D >= 3) {
+      const size_t P1 = h->lev[1].P, P3 = h->lev[3].P;
+      h->m2m31 = dalloc<cplx>(h, 16 * P3 * P1);
+      h->m2m31f = dalloc<cplxf>(h, 16 * P3 * P1);
+      h->root1 = dalloc<cplx>(h, 16 * P1 * P1);
+      h->root1f = dalloc<cplxf>(h, 16 * P1 * P1);
+      if (!h->m2m31 || !h->m2m31f || !h->root1 || !h->root1f)
+        return fail(h, PFMBEM_ENOMEM, "device allocation failed (top operators)");
+    }
+    if (h->aux[0]) CK(cudaStreamWaitEvent(h->side, h->aux_ev[0], 0));
+    CK(k_top_operators(h, h->side));
+  }
   {
     pfmbem_status st;
     if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
@@ -1217,9 +1235,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if (h->opt.launch == 0 && !tensor) {
       pfmbem_status st;
       bool ok = false;
-      h->rootc = dalloc<cplx>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
-      h->rootcf = dalloc<cplxf>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
-      if (!h->rootc || !h->rootcf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (root operator)");
+      if (!h->rootc) return fail(h, PFMBEM_ENOMEM, "single-launch product without its top operators");
       CK(k_fused_prepare(h, &ok));
       if (ok) {
         std::vector<int> sli(E);

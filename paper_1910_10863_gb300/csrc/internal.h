@@ -249,6 +249,10 @@ struct pfmbem {
   cplxf* rootf = nullptr;
   cplx* rootc = nullptr;         // [4 P1][P0] root translation times the level-1 -> root M2M
   cplxf* rootcf = nullptr;
+  cplx* m2m31 = nullptr;         // [P1][16 P3] level-3 -> level-1 M2M (two M2M steps in one)
+  cplxf* m2m31f = nullptr;
+  cplx* root1 = nullptr;         // [4][P1][4 P1] L(1) of each quadrant from the level-1 multipoles via the root
+  cplxf* root1f = nullptr;
   // matvec work
   cplx* dens = nullptr;          // sorted [E][2] = (phi', varphi')
   cplx* U = nullptr;             // sorted [E][2] = (U', dU')
@@ -286,6 +290,7 @@ cudaError_t k_m2l_tc(pfmbem* h, int level, const cplxf* M, cplxf* L);
 cudaError_t k_build_caches(pfmbem* h);
 // single-launch cached matvec (matvec_fused.cu)
 cudaError_t k_fused_prepare(pfmbem* h, bool* ok);
+cudaError_t k_top_operators(pfmbem* h, cudaStream_t st);
 cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_fiber_symbols(pfmbem* h);
 cudaError_t k_precond_symbols(pfmbem* h);

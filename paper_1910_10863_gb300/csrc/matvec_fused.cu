@@ -78,6 +78,9 @@ struct FusedArgs {
   C* L[PF_MAXLEVEL + 1];
   const C* root;                     // [l][n], lattice-sum translation at the root
   const C* rootc;                    // [u < 4 P_1][l < P_0], R T_0: L(0) from the level-1 multipoles
+  int top3;                          // 1: the level-2 stage also forms M(1), and L(0) is never formed
+  const C* m2m31;                    // [n < P_1][u < 16 P_3], T_1 T_2
+  const C* root1;                    // [q][n < P_1][u < 4 P_1], L2L_q R T_0: L(1) from the level-1 multipoles
   const C* p2m;                      // [E][2][P_D]
   const C* l2p;                      // [E][2][P_D]
   const int64_t* nc_base;
@@ -291,6 +294,41 @@ __global__ void root_fold_kernel(int P0, int K, const cplx* __restrict__ R, cons
     rc[i] = s;
     rcf[i] = to_f(s);
   }
+}
+
+// The top of the tree in one stage each way.  T31 = T_1 T_2 maps the 16
+// level-3 boxes under a level-1 box (index r = 4 q1 + q2, q1 the level-2
+// quadrant, q2 the level-3 one; consecutive in Morton order) to its multipole,
+// stored [n][u = r P_3 + m].  R1 = L2L_q (R T_0) maps the four level-1
+// multipoles straight to the root's contribution to the local expansion of
+// level-1 quadrant q, stored [q][n][u = q' P_1 + m], so that L(0) is never
+// formed.  Both are read with lanes over u, along the multipoles as they lie in
+// memory.  One thread per entry (consecutive threads along u), FP64 sums, with
+// FP32 copies.
+__global__ void m2m31_kernel(int P1, int P2, int P3, const cplx* __restrict__ m2m1, const cplx* __restrict__ m2m2,
+                             cplx* __restrict__ c, cplxf* __restrict__ cf) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int U = 16 * P3;
+  if (i >= U * P1) return;
+  const int n = i / U, u = i - n * U;
+  const int r = u / P3, m = u - r * P3, q1 = r >> 2, q2 = r & 3;
+  cplx s{0, 0};
+  for (int k = 0; k < P2; ++k) s += m2m1[((size_t)q1 * P2 + k) * P1 + n] * m2m2[((size_t)q2 * P3 + m) * P2 + k];
+  c[i] = s;
+  cf[i] = to_f(s);
+}
+
+__global__ void root1_kernel(int P0, int P1, const cplx* __restrict__ l2l0, const cplx* __restrict__ rootc,
+                          cplx* __restrict__ r1, cplxf* __restrict__ r1f) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int U = 4 * P1;
+  if (i >= 4 * P1 * U) return;
+  const int qn = i / U, u = i - qn * U;
+  const int q = qn / P1, n = qn - q * P1;
+  cplx s{0, 0};
+  for (int t = 0; t < P0; ++t) s += l2l0[((size_t)q * P0 + t) * P1 + n] * rootc[(size_t)u * P0 + t];
+  r1[i] = s;
+  r1f[i] = to_f(s);
 }
 
 // Near-field sum of one target (sorted element s) from its leaf's cached
@@ -651,24 +689,39 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   stage_stamp(a.stamp, ks++);
 
   // ------------------------------------------------------------ B: M2M (+ root)
-  const int lnear = D - 1;                          // levels whose stage also takes near-field rows
-  for (int l = D - 1; l >= 0; --l) {
+  // the last B stage: level 2 when it also forms M(1) and L(0), else the root;
+  // the near-field rows are spread evenly over all B stages
+  const int lstop = a.top3 ? 2 : 0, nbst = D - lstop;
+  for (int l = D - 1; l >= lstop; --l) {
     const int P = a.P[l], Pc = a.P[l + 1];
-    int r0 = 0, r1 = 0;
-    if (l <= lnear) {
-      const int j = lnear - l, nb = lnear + 1;
-      r0 = (int)((int64_t)a.E * j / nb);
-      r1 = (int)((int64_t)a.E * (j + 1) / nb);
-    }
+    const int jst = D - 1 - l;
+    const int r0 = (int)((int64_t)a.E * jst / nbst), r1 = (int)((int64_t)a.E * (jst + 1) / nbst);
     // near the top of the tree the boxes are too few to occupy the grid: one
     // warp per output coefficient, lanes over the 4 Pc child coefficients.  The
     // root then forms L(0) = (R T_0) [M(1) of its four children] at once.
     const bool top = (int64_t)a.nne[l] * P <= wstride;
     const int nbi = top ? a.nne[l] * P : a.nne[l];
-    const int nitem = nbi + (r1 - r0);
+    // with top3, the level-2 stage adds M(1) (one warp per coefficient, from the
+    // 16 level-3 boxes below)
+    const int nx = (a.top3 && l == 2) ? a.nne[1] * a.P[1] : 0;
+    const int nitem = nbi + nx + (r1 - r0);
     for (int i = wfirst; i < nitem; i += wstride) {
+      if (i >= nbi + nx) {
+        near_row(a, r0 + (i - nbi - nx), lane);
+        continue;
+      }
       if (i >= nbi) {
-        near_row(a, r0 + (i - nbi), lane);
+        // M(1) of a level-1 box from its 16 level-3 boxes; the multipoles of
+        // empty level-3 boxes are kept at zero, so the sum runs without branches
+        const int k = i - nbi, P1 = a.P[1], U1 = 16 * a.P[3];
+        const int b1 = a.ne[1][k / P1], n = k % P1;
+        const C* A = a.m2m31 + (size_t)n * U1;
+        const C* M3 = a.M[3] + (size_t)b1 * U1;
+        C acc{0, 0};
+#pragma unroll 4
+        for (int u = lane; u < U1; u += 32) acc += A[u] * ldcg(M3 + u);
+        acc = wsum(acc);
+        if (lane == 0) a.M[1][(size_t)b1 * P1 + n] = acc;
         continue;
       }
       if (top) {
@@ -747,7 +800,17 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     const int nitem = nl2l + (wpair ? a.npair[l] : 0);
     for (int i = wfirst; i < nitem; i += wstride) {
       if (i < nl2l) {
-        if (top) {
+        if (top && a.top3 && l == 1) {
+          // the root's part of L(1) straight from the four level-1 multipoles
+          // (those of empty level-1 boxes are kept at zero)
+          const int bi = i / P, n = i - bi * P;
+          const int box = a.ne[1][bi];
+          const C* A = a.root1 + ((size_t)box * P + n) * 4 * P;
+          C acc{0, 0};
+          for (int u = lane; u < 4 * P; u += 32) acc += A[u] * ldcg(a.M[1] + u);
+          acc = wsum(acc);
+          if (lane == 0) atomic_add(a.L[1] + (size_t)box * P + n, acc);
+        } else if (top) {
           const int bi = i / P, n = i - bi * P;
           const int box = a.ne[l][bi], par = box >> 2, q = box & 3;
           const C* A = a.l2l[l - 1] + (size_t)q * Pp * P + n;
@@ -888,10 +951,12 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
   if constexpr (sizeof(C) == sizeof(cplxf)) {
     a.Un = h->Unf;
     a.dens = h->densf; a.root = h->rootf; a.rootc = h->rootcf; a.p2m = h->p2m_cf; a.l2p = h->l2p_cf;
+    a.m2m31 = h->m2m31f; a.root1 = h->root1f;
     a.nc_val = h->nc_valf; a.fb_val = h->fb_valf; a.fh_val = h->fh_valf; a.tw = h->twf;
   } else {
     a.Un = h->Un;
     a.dens = h->dens; a.root = h->root; a.rootc = h->rootc; a.p2m = h->p2m_c; a.l2p = h->l2p_c;
+    a.m2m31 = h->m2m31; a.root1 = h->root1;
     a.nc_val = h->nc_val; a.fb_val = h->fb_val; a.fh_val = h->fh_val; a.tw = h->tw;
   }
   a.nc_base = h->nc_base;
@@ -924,6 +989,13 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
   // chunks in FP32 (PFMBEM_M2L_WARP=0/1 overrides, for measurement)
   static const char* mw = std::getenv("PFMBEM_M2L_WARP");
   a.m2l_warp = mw ? std::atoi(mw) != 0 : !f32;
+  // levels 1 and 0 inside the level-2 stage when the tree has level 3 and the
+  // three levels' coefficients fit one item per warp
+  {
+    const int64_t w = (int64_t)grid * FW;
+    a.top3 = h->m2m31 != nullptr &&
+             (int64_t)h->lev[2].nne * h->lev[2].P + (int64_t)h->lev[1].nne * h->lev[1].P + 4 * h->lev[0].P <= w;
+  }
   const size_t smem = fused_smem<C>(h->max_fiber);
   void* args[] = {&a};
   const int ph = PH_FUSED + (f32 ? 16 : 0);
@@ -937,7 +1009,7 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
     e = cudaMemcpyAsync(t, a.stamp, sizeof(t), cudaMemcpyDeviceToHost, h->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) {
-      const int n = 2 * h->D + 3;
+      const int n = 2 * h->D + 3 - (a.top3 ? 2 : 0);
       std::fprintf(stderr, "pfmbem fused %s stages (us):", f32 ? "f32" : "f64");
       for (int i = 1; i < n; ++i) std::fprintf(stderr, " %.1f", 1e-3 * (double)(t[i] - t[i - 1]));
       std::fprintf(stderr, "  total %.1f\n", 1e-3 * (double)(t[n - 1] - t[0]));
@@ -969,22 +1041,40 @@ int fused_grid(int maxfiber) {
 
 }  // namespace
 
+// The top operators of the fused product on stream st: R T_0 (root fold) and,
+// with level 3 present, T_1 T_2 and R T_0 T_1 T_2; st must be ordered after the
+// root operator and the M2M tables.
+cudaError_t k_top_operators(pfmbem* h, cudaStream_t st) {
+  const int P0 = h->lev[0].P, K = 4 * h->lev[1].P;
+  root_fold_kernel<<<(P0 * K + 7) / 8, 256, 0, st>>>(P0, K, h->root, h->lev[0].m2m, h->rootc, h->rootcf);
+  if (h->m2m31) {
+    const int P1 = h->lev[1].P, P2 = h->lev[2].P, P3 = h->lev[3].P;
+    m2m31_kernel<<<(16 * P3 * P1 + 255) / 256, 256, 0, st>>>(P1, P2, P3, h->lev[1].m2m, h->lev[2].m2m, h->m2m31,
+                                                             h->m2m31f);
+    // the level-1 and level-3 multipoles of empty boxes are never written: keep them zero
+    for (int l : {1, 3}) {
+      const size_t nz = (size_t)h->lev[l].nbox * h->lev[l].P;
+      cudaError_t e = cudaMemsetAsync(h->lev[l].M, 0, nz * sizeof(cplx), st);
+      if (e == cudaSuccess) e = cudaMemsetAsync(h->lev[l].Mf, 0, nz * sizeof(cplxf), st);
+      if (e != cudaSuccess) return e;
+    }
+    root1_kernel<<<(16 * P1 * P1 + 255) / 256, 256, 0, st>>>(P0, P1, h->lev[0].l2l, h->rootc, h->root1, h->root1f);
+  }
+  return cudaGetLastError();
+}
+
 // Prepares the fused path of a handle (grid sizes, barrier words); returns
 // false when the device cannot run it, in which case the per-stage path is used.
 cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
   *ok = false;
   // blocks with work in some stage: warps over boxes (A, B, D), blocks over
-  // leaves (E) and over fiber row chunks (F)
+  // leaves and over fibers or fiber row chunks (fiber part of A)
   int need = std::max(h->lev[h->D].nne, h->fz_nchunk + h->fz_nfft);
   for (int l = 0; l <= h->D; ++l) need = std::max(need, (h->lev[l].nne + FW - 1) / FW);
   need = std::max(need, 1);
   h->fz_grid64 = std::min(fused_grid<cplx>(h->max_fiber), need);
   h->fz_grid32 = std::min(fused_grid<cplxf>(h->max_fiber), need);
   if (h->fz_grid64 <= 0 || h->fz_grid32 <= 0) return cudaSuccess;
-  const int P0 = h->lev[0].P, K = 4 * h->lev[1].P;
-  prof_begin(h, PH_SETUP);
-  root_fold_kernel<<<(P0 * K + 7) / 8, 256, 0, h->stream>>>(P0, K, h->root, h->lev[0].m2m, h->rootc, h->rootcf);
-  prof_end(h, PH_SETUP);
   *ok = true;
   return cudaGetLastError();
 }
