@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <future>
 #include <array>
 #include <map>
 #include <mutex>
@@ -463,6 +464,114 @@ static pfmbem_status build_pair_tables(pfmbem* h, const double* nodes, const std
   return PFMBEM_OK;
 }
 
+// M2L interaction lists of one level (host only, no CUDA calls: it runs on a
+// worker thread while the set-up continues).  Per non-empty target box the
+// sources are the children of the parent's neighbours (y-periodic, image m)
+// that are not neighbours themselves; CSR (ptr, src, off, img), the same pairs
+// grouped by offset in chunks of at most 16 (ptg, psr, pim, pof, cof, cbg,
+// cen) and, for the tensor-core M2L, tiles of 128 target boxes.
+struct M2LLists {
+  std::vector<int> ptr, src, off, img, ptg, psr, pim, pof, cof, cbg, cen, tbox, tnoff, toffs, tsrc, timg;
+  int ntile = 0;
+};
+
+static void build_m2l_lists(const Level& L, int l, bool tc, M2LLists& o) {
+  const int nl = 1 << l, np = 1 << (l - 1);
+  const int nne = (int)L.hne.size();
+  // occupancy of the level's boxes on the (x, y) grid
+  std::vector<unsigned char> occ((size_t)nl * nl, 0);
+  for (int b : L.hne) occ[(size_t)unspread_bits((unsigned)b >> 1) * nl + unspread_bits((unsigned)b)] = 1;
+  std::vector<int>& ptr = o.ptr;
+  std::vector<int>& src = o.src;
+  std::vector<int>& off = o.off;
+  std::vector<int>& img = o.img;
+  ptr.assign(nne + 1, 0);
+  src.reserve((size_t)27 * nne);
+  off.reserve((size_t)27 * nne);
+  img.reserve((size_t)27 * nne);
+  for (int ti = 0; ti < nne; ++ti) {
+    const int b = L.hne[ti];
+    const int ix = (int)unspread_bits((unsigned)b), iy = (int)unspread_bits((unsigned)b >> 1);
+    const int px = ix >> 1, py = iy >> 1;
+    for (int pdx = -1; pdx <= 1; ++pdx) {
+      const int qx = px + pdx;
+      if (qx < 0 || qx >= np) continue;
+      for (int pdy = -1; pdy <= 1; ++pdy) {
+        const int qy = py + pdy;
+        for (int cx = 0; cx < 2; ++cx)
+          for (int cy = 0; cy < 2; ++cy) {
+            const int sx = 2 * qx + cx, sy = 2 * qy + cy;
+            const int dx = ix - sx, dy = iy - sy;
+            if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
+            const int syw = sy & (nl - 1);            // nl is a power of two
+            if (!occ[(size_t)syw * nl + sx]) continue;
+            src.push_back(morton(sx, syw, l));
+            off.push_back((dx + 3) * 7 + (dy + 3));
+            img.push_back((sy - syw) >> l);
+          }
+      }
+    }
+    ptr[ti + 1] = (int)src.size();
+  }
+  // the same pairs grouped by offset (a stable counting sort), cut into chunks
+  // of at most 16 pairs (small chunks spread one level's translations over many blocks)
+  const size_t n = src.size();
+  int first[50] = {0};
+  for (size_t e = 0; e < n; ++e) first[off[e] + 1]++;
+  for (int q = 0; q < 49; ++q) first[q + 1] += first[q];
+  o.ptg.resize(n);
+  o.psr.resize(n);
+  o.pim.resize(n);
+  o.pof.resize(n);
+  {
+    int at[49];
+    std::copy(first, first + 49, at);
+    for (int ti = 0; ti < nne; ++ti)
+      for (int e = ptr[ti]; e < ptr[ti + 1]; ++e) {
+        const int q = at[off[e]]++;
+        o.ptg[q] = L.hne[ti];
+        o.psr[q] = src[e];
+        o.pim[q] = img[e];
+        o.pof[q] = off[e];
+      }
+  }
+  for (int q = 0; q < 49; ++q)
+    for (int b0 = first[q]; b0 < first[q + 1]; b0 += 16) {
+      o.cof.push_back(q);
+      o.cbg.push_back(b0);
+      o.cen.push_back(std::min(b0 + 16, first[q + 1]));
+    }
+  if (tc) {
+    // tensor-core tiles: 128 consecutive non-empty target boxes
+    const int nt = (nne + 127) / 128;
+    o.ntile = nt;
+    o.tbox.assign((size_t)nt * 128, -1);
+    o.tnoff.assign(nt, 0);
+    o.toffs.assign((size_t)nt * 49, 0);
+    o.tsrc.assign((size_t)nt * 49 * 128, -1);
+    o.timg.assign((size_t)nt * 49 * 128, 0);
+    for (int tile = 0; tile < nt; ++tile) {
+      int slot[49];
+      for (int q = 0; q < 49; ++q) slot[q] = -1;
+      for (int r = 0; r < 128; ++r) {
+        const size_t ti = (size_t)tile * 128 + r;
+        if (ti >= L.hne.size()) break;
+        o.tbox[ti] = L.hne[ti];
+        for (int e = ptr[ti]; e < ptr[ti + 1]; ++e) {
+          const int q = off[e];
+          if (slot[q] < 0) {
+            slot[q] = o.tnoff[tile]++;
+            o.toffs[(size_t)tile * 49 + slot[q]] = q;
+          }
+          const size_t qq = ((size_t)tile * 49 + slot[q]) * 128 + r;
+          o.tsrc[qq] = src[e];
+          o.timg[qq] = img[e];
+        }
+      }
+    }
+  }
+}
+
 // Issues the launches of f on set-up stream i, ordered after everything issued
 // so far on the main stream; the main stream waits for them at the join of
 // build_plan (aux_ev).  While f runs, h->stream names stream i, so that the
@@ -661,10 +770,16 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     h->info.p[l] = p;
   }
   mark("depth, sort, levels");
+  // the M2L lists depend on the tree alone: a worker thread builds them while
+  // the set-up below goes on (they are uploaded where the second stream starts)
+  std::vector<M2LLists> m2l(D + 1);
+  std::future<void> m2l_lists = std::async(std::launch::async, [h, D, &m2l]() {
+    for (int l = 1; l <= D; ++l) build_m2l_lists(h->lev[l], l, h->opt.m2l_mode == 2, m2l[l]);
+  });
   // ---------------------------------------------------- lists
   const int nD = 1 << D;
   std::vector<int64_t> nc_base;
-  std::vector<int> nc_sbase(1, 0), nc_src, nc_img;
+  std::vector<int> nc_sbase(1, 0);
   std::vector<int> nl_ptr(1, 0), nl_src, nl_img;      // near lists of the leaves: source leaf, image m
   {
     Level& Lf = h->lev[D];
@@ -710,18 +825,16 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     h->info.near_pairs = pairs;
     h->info.near_quad = quad;
     // layout of the cached near field: per leaf, its concatenated source list
-    // and a dense [targets][sources] array of 2x2 complex blocks
+    // (filled on the device from the leaf's near list) and a dense
+    // [targets][sources] array of 2x2 complex blocks
     int64_t acc = 0;
+    nc_sbase.reserve(Lf.hne.size() + 1);
+    nc_base.reserve(Lf.hne.size());
     for (size_t li = 0; li < Lf.hne.size(); ++li) {
       int b = Lf.hne[li];
       int ns = 0;
-      for (int e = ptr[li]; e < ptr[li + 1]; ++e)
-        for (int f = Lf.hbegin[src[e]]; f < Lf.hend[src[e]]; ++f) {
-          nc_src.push_back(f);
-          nc_img.push_back(img[e]);
-          ++ns;
-        }
-      nc_sbase.push_back((int)nc_src.size());
+      for (int e = ptr[li]; e < ptr[li + 1]; ++e) ns += Lf.hend[src[e]] - Lf.hbegin[src[e]];
+      nc_sbase.push_back(nc_sbase.back() + ns);
       h->nc_maxns = std::max(h->nc_maxns, ns);
       h->leaf_maxn = std::max(h->leaf_maxn, Lf.hend[b] - Lf.hbegin[b]);
       nc_base.push_back(acc);
@@ -762,36 +875,12 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   mark("near lists");
   // ---------------------------------------------------- element arrays
   {
-    std::vector<double2> sc(E), st2(E), snu(E);
-    std::vector<double> sh(E);
-    std::vector<cplx> sph(E);
-    std::vector<std::pair<int, cplx>> apow;
-    auto alpha_pow = [&](int m) {
-      for (auto& q : apow)
-        if (q.first == m) return q.second;
-      const double a = m * h->beta;
-      apow.push_back({m, cplx{std::cos(a), std::sin(a)}});
-      return apow.back().second;
-    };
-    for (int s = 0; s < E; ++s) {
-      int e = perm[s];
-      sc[s] = cw[e];
-      st2[s] = t[e];
-      snu[s] = nu[e];
-      sh[s] = len[e];
-      // alpha^{-m0}; m0 takes a handful of values, so each power is evaluated once
-      sph[s] = alpha_pow(-m0[e]);
-    }
+    // the tree-ordered copies (wrapped midpoints, alpha^{-m0}, leaf keys) are
+    // gathered on the device from the original-order arrays
     pfmbem_status st;
-    if ((st = upload(h, &h->s_c, sc)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->s_t, st2)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->s_nu, snu)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->s_h, sh)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &h->s_ph, sph)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->s_perm, perm)) != PFMBEM_OK) return st;
-    std::vector<int> sleaf(E);
-    for (int s2 = 0; s2 < E; ++s2) sleaf[s2] = key[perm[s2]];
-    if ((st = upload(h, &h->s_leaf, sleaf)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_m0, m0)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->o_key, key)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->o_c, c)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->o_t, t)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->o_nu, nu)) != PFMBEM_OK) return st;
@@ -801,6 +890,15 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &h->fib_geo, h->hfib_geo)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->o_pos, pos)) != PFMBEM_OK) return st;
   }
+  h->s_c = dalloc<double2>(h, (size_t)E);
+  h->s_t = dalloc<double2>(h, (size_t)E);
+  h->s_nu = dalloc<double2>(h, (size_t)E);
+  h->s_h = dalloc<double>(h, (size_t)E);
+  h->s_ph = dalloc<cplx>(h, (size_t)E);
+  h->s_m0 = dalloc<int>(h, (size_t)E);
+  h->s_leaf = dalloc<int>(h, (size_t)E);
+  if (!h->s_c || !h->s_t || !h->s_nu || !h->s_h || !h->s_ph || !h->s_m0 || !h->s_leaf)
+    return fail(h, PFMBEM_ENOMEM, "device allocation failed (element arrays)");
   h->self4 = dalloc<cplx>(h, (size_t)4 * E);
   h->dens = dalloc<cplx>(h, (size_t)2 * E);
   h->U = dalloc<cplx>(h, (size_t)2 * E);
@@ -813,6 +911,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     pfmbem_status st;
     if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
   }
+  CK(k_sort_elements(h));
   h->tab_err = dalloc<int>(h, 1);
   if (!h->tab_err) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
   CK(cudaMemsetAsync(h->tab_err, 0, sizeof(int), h->stream));
@@ -907,8 +1006,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if (st != PFMBEM_OK) return st;
       if ((st = upload(h, &h->nc_base, nc_base)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->nc_sbase, nc_sbase)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->nc_src, nc_src)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->nc_img, nc_img)) != PFMBEM_OK) return st;
+      h->nc_src = dalloc<int>(h, (size_t)std::max(nc_sbase.back(), 1));
+      h->nc_img = dalloc<int>(h, (size_t)std::max(nc_sbase.back(), 1));
+      if (!h->nc_src || !h->nc_img) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near sources)");
       if ((st = upload(h, &h->fb_base, fbase)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->fb_circ, circ)) != PFMBEM_OK) return st;
       if ((st = upload(h, &h->fb_chunk, chunks)) != PFMBEM_OK) return st;
@@ -925,10 +1025,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
           kbase[i] = kacc;
           kacc += foff[i + 1] - foff[i];
         }
-      std::vector<int> sm0(E);
-      for (int s2 = 0; s2 < E; ++s2) sm0[s2] = m0[perm[s2]];
       if ((st = upload(h, &h->kt_base, kbase)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &h->s_m0, sm0)) != PFMBEM_OK) return st;
       if ((st = build_pair_tables(h, nodes, foff, fib, m0, perm, nl_ptr, nl_src, nl_img)) != PFMBEM_OK) return st;
       h->kt_val = dalloc<cplx>(h, (size_t)4 * kacc);
       if (!h->kt_val) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
@@ -1029,116 +1126,33 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   CK(cudaStreamWaitEvent(h->side, h->pre_ev, 0));
   h->astream = h->side;
   int64_t m2l_pairs = 0;
-  std::vector<unsigned char> occ;
+  m2l_lists.wait();
   for (int l = 1; l <= D; ++l) {
     Level& L = h->lev[l];
-    const int nl = 1 << l, np = 1 << (l - 1);
-    const int nne = (int)L.hne.size();
-    // occupancy of the level's boxes on the (x, y) grid
-    occ.assign((size_t)nl * nl, 0);
-    for (int b : L.hne) occ[(size_t)unspread_bits((unsigned)b >> 1) * nl + unspread_bits((unsigned)b)] = 1;
-    std::vector<int> ptr(nne + 1, 0), src, off, img;
-    src.reserve((size_t)27 * nne);
-    off.reserve((size_t)27 * nne);
-    img.reserve((size_t)27 * nne);
-    for (int ti = 0; ti < nne; ++ti) {
-      const int b = L.hne[ti];
-      const int ix = (int)unspread_bits((unsigned)b), iy = (int)unspread_bits((unsigned)b >> 1);
-      const int px = ix >> 1, py = iy >> 1;
-      for (int pdx = -1; pdx <= 1; ++pdx) {
-        const int qx = px + pdx;
-        if (qx < 0 || qx >= np) continue;
-        for (int pdy = -1; pdy <= 1; ++pdy) {
-          const int qy = py + pdy;
-          for (int cx = 0; cx < 2; ++cx)
-            for (int cy = 0; cy < 2; ++cy) {
-              const int sx = 2 * qx + cx, sy = 2 * qy + cy;
-              const int dx = ix - sx, dy = iy - sy;
-              if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
-              const int syw = sy & (nl - 1);            // nl is a power of two
-              if (!occ[(size_t)syw * nl + sx]) continue;
-              src.push_back(morton(sx, syw, l));
-              off.push_back((dx + 3) * 7 + (dy + 3));
-              img.push_back((sy - syw) >> l);
-            }
-        }
-      }
-      ptr[ti + 1] = (int)src.size();
-    }
-    L.nil = (int64_t)src.size();
+    M2LLists& o = m2l[l];
+    L.nil = (int64_t)o.src.size();
     m2l_pairs += L.nil;
     pfmbem_status st;
-    if ((st = upload(h, &L.il_ptr, ptr)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &L.il_src, src)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &L.il_off, off)) != PFMBEM_OK) return st;
-    if ((st = upload(h, &L.il_img, img)) != PFMBEM_OK) return st;
-    // the same pairs grouped by offset, cut into chunks of at most 16 pairs
-    // (small chunks spread one level's translations over many blocks)
-    {
-      // stable counting sort of the CSR entries by offset
-      const size_t n = src.size();
-      int first[50] = {0};
-      for (size_t e = 0; e < n; ++e) first[off[e] + 1]++;
-      for (int o = 0; o < 49; ++o) first[o + 1] += first[o];
-      std::vector<int> ptg(n), psr(n), pim(n), pof(n), cof, cbg, cen;
-      {
-        int at[49];
-        std::copy(first, first + 49, at);
-        for (int ti = 0; ti < nne; ++ti)
-          for (int e = ptr[ti]; e < ptr[ti + 1]; ++e) {
-            const int q = at[off[e]]++;
-            ptg[q] = L.hne[ti];
-            psr[q] = src[e];
-            pim[q] = img[e];
-            pof[q] = off[e];
-          }
-      }
-      for (int o = 0; o < 49; ++o)
-        for (int b0 = first[o]; b0 < first[o + 1]; b0 += 16) {
-          cof.push_back(o);
-          cbg.push_back(b0);
-          cen.push_back(std::min(b0 + 16, first[o + 1]));
-        }
-      // tensor-core tiles: 128 consecutive non-empty target boxes
-      if (h->opt.m2l_mode == 2) {
-        const int nt = ((int)L.hne.size() + 127) / 128;
-        std::vector<int> tbox((size_t)nt * 128, -1), tnoff(nt, 0), toffs((size_t)nt * 49, 0);
-        std::vector<int> tsrc((size_t)nt * 49 * 128, -1), timg((size_t)nt * 49 * 128, 0);
-        for (int tile = 0; tile < nt; ++tile) {
-          int slot[49];
-          for (int o = 0; o < 49; ++o) slot[o] = -1;
-          for (int r = 0; r < 128; ++r) {
-            const size_t ti = (size_t)tile * 128 + r;
-            if (ti >= L.hne.size()) break;
-            tbox[ti] = L.hne[ti];
-            for (int e = ptr[ti]; e < ptr[ti + 1]; ++e) {
-              const int o = off[e];
-              if (slot[o] < 0) {
-                slot[o] = tnoff[tile]++;
-                toffs[(size_t)tile * 49 + slot[o]] = o;
-              }
-              const size_t q = ((size_t)tile * 49 + slot[o]) * 128 + r;
-              tsrc[q] = src[e];
-              timg[q] = img[e];
-            }
-          }
-        }
-        L.tc_ntile = nt;
-        if ((st = upload(h, &L.tc_box, tbox)) != PFMBEM_OK) return st;
-        if ((st = upload(h, &L.tc_noff, tnoff)) != PFMBEM_OK) return st;
-        if ((st = upload(h, &L.tc_offs, toffs)) != PFMBEM_OK) return st;
-        if ((st = upload(h, &L.tc_src, tsrc)) != PFMBEM_OK) return st;
-        if ((st = upload(h, &L.tc_img, timg)) != PFMBEM_OK) return st;
-      }
-      L.nchunk = (int)cof.size();
-      if ((st = upload(h, &L.pr_tgt, ptg)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.pr_src, psr)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.pr_img, pim)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.pr_off, pof)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.ch_off, cof)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.ch_beg, cbg)) != PFMBEM_OK) return st;
-      if ((st = upload(h, &L.ch_end, cen)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.il_ptr, o.ptr)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.il_src, o.src)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.il_off, o.off)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.il_img, o.img)) != PFMBEM_OK) return st;
+    if (h->opt.m2l_mode == 2) {
+      L.tc_ntile = o.ntile;
+      if ((st = upload(h, &L.tc_box, o.tbox)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.tc_noff, o.tnoff)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.tc_offs, o.toffs)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.tc_src, o.tsrc)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.tc_img, o.timg)) != PFMBEM_OK) return st;
     }
+    L.nchunk = (int)o.cof.size();
+    if ((st = upload(h, &L.pr_tgt, o.ptg)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.pr_src, o.psr)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.pr_img, o.pim)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.pr_off, o.pof)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.ch_off, o.cof)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.ch_beg, o.cbg)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &L.ch_end, o.cen)) != PFMBEM_OK) return st;
   }
   h->info.m2l_pairs = m2l_pairs;
   mark("M2L lists (overlapped)");

@@ -156,6 +156,8 @@ struct pfmbem {
   double* fib_geo = nullptr;     // [M][3] fiber centre (mean of nodes) and mean radius
   std::vector<double> hfib_geo;
   int* o_pos = nullptr;          // original -> sorted
+  int* o_m0 = nullptr;           // original order: periods the element is shifted by when wrapped into the root
+  int* o_key = nullptr;          // original order: leaf box (Morton) of the element
   cplx* self4 = nullptr;         // [E][4]: S_ee(k), T_ee(k), S_ee(k1), T_ee(k1)
   std::vector<int> hfib_off;
   int max_fiber = 0;
@@ -288,6 +290,7 @@ int tc_kpad(int P);
 cudaError_t k_tc_build_operator(pfmbem* h, int level);
 cudaError_t k_m2l_tc(pfmbem* h, int level, const cplxf* M, cplxf* L);
 cudaError_t k_build_caches(pfmbem* h);
+cudaError_t k_sort_elements(pfmbem* h);
 // single-launch cached matvec (matvec_fused.cu)
 cudaError_t k_fused_prepare(pfmbem* h, bool* ok);
 cudaError_t k_top_operators(pfmbem* h, cudaStream_t st);

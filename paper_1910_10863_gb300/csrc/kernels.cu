@@ -539,12 +539,14 @@ __device__ __forceinline__ void bessel01(double x, double& J0, double& J1, doubl
 // ---------------------------------------------------------------- pair integrals
 // Element integrals of (i/4)H0(kap|x-y|) (S), its d/dnu_y (D), d/dnu_x (K) and
 // d2/dnu_x dnu_y (T) over the flat element c + s t, |s| <= h/2, by g-point
-// Gauss-Legendre; the factor i/4 is applied by the caller.
+// Gauss-Legendre; the factor i/4 is applied by the caller.  Nodes q0, q0 + qs,
+// ... only (a share of the rule, for callers that split it over lanes).
 __device__ __forceinline__ void pair4_f64(double kap, double2 x, double2 nx, double2 c, double2 t, double2 ny,
-                                          double h, int g, cplx& S, cplx& D, cplx& K, cplx& T) {
+                                          double h, int g, cplx& S, cplx& D, cplx& K, cplx& T, int q0 = 0,
+                                          int qs = 1) {
   const double nn = nx.x * ny.x + nx.y * ny.y;
 #pragma unroll 1
-  for (int q = 0; q < g; ++q) {
+  for (int q = q0; q < g; q += qs) {
     double s = 0.5 * h * c_glx[g - 1][q];
     double wq = 0.5 * h * c_glw[g - 1][q];
     double z1 = x.x - (c.x + s * t.x);
@@ -1121,15 +1123,26 @@ __global__ void near_direct_kernel(const unsigned long long* __restrict__ queue,
 // periodic k part:  [1 - D1, i eta S1; -c2 rho T1, 1 + i eta c2 rho K1] over the
 // same-fiber sources (k1, eq. 5), plus on the diagonal the self terms of both
 // wavenumbers (-i eta S_ee(k) and c2 T_ee(k) of the k part, whose remainder
-// comes from the FMM).  One warp per target element.
-// One thread per (row element e, source f) of the same fiber; rows lists the
-// elements whose row pairs are stored (the first element of a circulant fiber,
-// every element of the others).  For a regular-polygon fiber (kbase >= 0) the
-// same thread also writes the fiber's k table: S, D, K, T (without i/4) at the
-// matrix wavenumber k of the first element's midpoint against element f0 + dl,
+// comes from the FMM).  rows lists the elements whose row pairs are stored (the
+// first element of a circulant fiber, every element of the others).  For a
+// regular-polygon fiber (kbase >= 0) the launch's second plane (blockIdx.z = 1)
+// writes the fiber's k table: S, D, K, T (without i/4) at the matrix
+// wavenumber k of the first element's midpoint against element f0 + dl,
 // dl = f - f0 (zero for dl = 0).  Rotating the fiber by one element maps it onto
 // itself, so element pair (e, e + dl) has the integrals of (f0, f0 + dl) and the
 // near-field build reads same-fiber pairs from this table.
+// FB_SPLIT consecutive lanes share one (row element e, source f) pair and take
+// every FB_SPLIT-th Gauss node; the partial sums meet by shuffles.
+constexpr int FB_SPLIT = 4;
+
+__device__ __forceinline__ void group_sum(cplx& v) {
+#pragma unroll
+  for (int o = 1; o < FB_SPLIT; o <<= 1) {
+    v.re += __shfl_xor_sync(0xffffffffu, v.re, o);
+    v.im += __shfl_xor_sync(0xffffffffu, v.im, o);
+  }
+}
+
 __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __restrict__ fib,
                                    const int* __restrict__ foff, const int64_t* __restrict__ fbase, double k,
                                    double k1, double eta, double rho, cplx c2, const double2* __restrict__ oc,
@@ -1140,76 +1153,130 @@ __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __re
                                    unsigned long long* __restrict__ stat) {
   const int e = rows[blockIdx.x];
   const int fb = fib[e], f0 = foff[fb], N = foff[fb + 1] - f0, el = e - f0;
-  const int fl = blockIdx.y * blockDim.x + threadIdx.x;
-  unsigned long long kp = 0, kq = 0, fp = 0, fq = 0;
-  if (fl < N) {
-    const int f = f0 + fl;
-    const int64_t r0 = fbase[fb] + (int64_t)(2 * el) * (2 * N), r1 = r0 + 2 * N;
-    const double2 xe = oc[e], nxe = onu[e];
-    const cplx c2r = rho * c2;
-    const int64_t kb = kbase[fb];
-    cplx a00, a01, a10, a11;
-    if (f == e) {
-      const cplx Sk = self4[4 * e], Tk = self4[4 * e + 1], Sk1 = self4[4 * e + 2], Tk1 = self4[4 * e + 3];
-      a00 = cplx{1, 0};
-      a01 = eta * mul_i(Sk1) - eta * mul_i(Sk);
-      a10 = c2 * Tk - c2r * Tk1;
-      a11 = cplx{1, 0};
-      if (kb >= 0) {
-        cplx* tv = kval + 4 * (kb + fl);
-        tv[0] = tv[1] = tv[2] = tv[3] = cplx{0, 0};
-      }
-    } else {
-      const double2 c = oc[f], tf = ot[f], nf = onu[f];
-      const double hh = oh[f];
-      const double q = sqrt((xe.x - c.x) * (xe.x - c.x) + (xe.y - c.y) * (xe.y - c.y)) / hh;
-      const int g = gl_order(q, 0);
-      fp = 1;
-      fq = g;
-      cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
-      pair4_f64(k1, xe, nxe, c, tf, nf, hh, g, S, Dv, K, T);
-      S = mul_i(0.25 * S);
-      Dv = mul_i(0.25 * Dv);
-      K = mul_i(0.25 * K);
-      T = mul_i(0.25 * T);
-      a00 = -Dv;
-      a01 = eta * mul_i(S);
-      a10 = -(c2r * T);
-      a11 = eta * mul_i(c2r * K);
-      if (kb >= 0) {
-        cplx Sk{0, 0}, Dk{0, 0}, Kk{0, 0}, Tk{0, 0};
-        pair4_f64(k, xe, nxe, c, tf, nf, hh, g, Sk, Dk, Kk, Tk);
-        cplx* tv = kval + 4 * (kb + fl);
-        tv[0] = Sk;
-        tv[1] = Dk;
-        tv[2] = Kk;
-        tv[3] = Tk;
-        kp = 1;
-        kq = g;
-      }
+  const bool ktab = blockIdx.z == 1;
+  const int64_t kb = kbase[fb];
+  if (ktab && kb < 0) return;                      // uniform over the block
+  const int part = threadIdx.x % FB_SPLIT;
+  const int fl = blockIdx.y * (blockDim.x / FB_SPLIT) + threadIdx.x / FB_SPLIT;
+  const bool lead = part == 0;
+  unsigned long long np = 0, nq = 0;
+  const bool on = fl < N;
+  const int f = f0 + (on ? fl : 0);
+  const bool self = on && f == e;
+  cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
+  const double2 xe = oc[e], nxe = onu[e];
+  if (on && !self) {
+    const double2 c = oc[f], tf = ot[f], nf = onu[f];
+    const double hh = oh[f];
+    const double q = sqrt((xe.x - c.x) * (xe.x - c.x) + (xe.y - c.y) * (xe.y - c.y)) / hh;
+    const int g = gl_order(q, 0);
+    if (lead) {
+      np = 1;
+      nq = g;
     }
-    val[r0 + 2 * fl] = a00;
-    val[r0 + 2 * fl + 1] = a01;
-    val[r1 + 2 * fl] = a10;
-    val[r1 + 2 * fl + 1] = a11;
-    if (valf) {
-      valf[r0 + 2 * fl] = cplxf{(float)a00.re, (float)a00.im};
-      valf[r0 + 2 * fl + 1] = cplxf{(float)a01.re, (float)a01.im};
-      valf[r1 + 2 * fl] = cplxf{(float)a10.re, (float)a10.im};
-      valf[r1 + 2 * fl + 1] = cplxf{(float)a11.re, (float)a11.im};
+    pair4_f64(ktab ? k : k1, xe, nxe, c, tf, nf, hh, g, S, Dv, K, T, part, FB_SPLIT);
+  }
+  group_sum(S);
+  group_sum(Dv);
+  group_sum(K);
+  group_sum(T);
+  if (on && lead) {
+    if (ktab) {
+      cplx* tv = kval + 4 * (kb + fl);
+      tv[0] = S;
+      tv[1] = Dv;
+      tv[2] = K;
+      tv[3] = T;
+    } else {
+      const int64_t r0 = fbase[fb] + (int64_t)(2 * el) * (2 * N), r1 = r0 + 2 * N;
+      const cplx c2r = rho * c2;
+      cplx a00, a01, a10, a11;
+      if (self) {
+        const cplx Sk = self4[4 * e], Tk = self4[4 * e + 1], Sk1 = self4[4 * e + 2], Tk1 = self4[4 * e + 3];
+        a00 = cplx{1, 0};
+        a01 = eta * mul_i(Sk1) - eta * mul_i(Sk);
+        a10 = c2 * Tk - c2r * Tk1;
+        a11 = cplx{1, 0};
+      } else {
+        S = mul_i(0.25 * S);
+        Dv = mul_i(0.25 * Dv);
+        K = mul_i(0.25 * K);
+        T = mul_i(0.25 * T);
+        a00 = -Dv;
+        a01 = eta * mul_i(S);
+        a10 = -(c2r * T);
+        a11 = eta * mul_i(c2r * K);
+      }
+      val[r0 + 2 * fl] = a00;
+      val[r0 + 2 * fl + 1] = a01;
+      val[r1 + 2 * fl] = a10;
+      val[r1 + 2 * fl + 1] = a11;
+      if (valf) {
+        valf[r0 + 2 * fl] = cplxf{(float)a00.re, (float)a00.im};
+        valf[r0 + 2 * fl + 1] = cplxf{(float)a01.re, (float)a01.im};
+        valf[r1 + 2 * fl] = cplxf{(float)a10.re, (float)a10.im};
+        valf[r1 + 2 * fl + 1] = cplxf{(float)a11.re, (float)a11.im};
+      }
     }
   }
   if (stat) {
-    kp = warp_sum_u64(kp);
-    kq = warp_sum_u64(kq);
-    fp = warp_sum_u64(fp);
-    fq = warp_sum_u64(fq);
-    if ((threadIdx.x & 31) == 0) {
-      if (kp) atomicAdd(&stat[0], kp);
-      if (kq) atomicAdd(&stat[1], kq);
-      if (fp) atomicAdd(&stat[2], fp);
-      if (fq) atomicAdd(&stat[3], fq);
+    np = warp_sum_u64(np);
+    nq = warp_sum_u64(nq);
+    if ((threadIdx.x & 31) == 0 && np) {
+      atomicAdd(&stat[ktab ? 0 : 2], np);
+      atomicAdd(&stat[ktab ? 1 : 3], nq);
     }
+  }
+}
+
+// Tree-ordered copies of the element arrays (one thread per sorted element s,
+// original e = perm[s]): midpoint wrapped into the root cell along y (the
+// product and the subtraction rounded separately, as the host does when it
+// builds the tree), tangent, normal, length, the input phase alpha^{-m0}
+// (alpha = e^{i beta}), the wrap shift m0 and the leaf key.
+__global__ void sort_elements_kernel(int E, const int* __restrict__ perm, const double2* __restrict__ oc,
+                                     const double2* __restrict__ ot, const double2* __restrict__ onu,
+                                     const double* __restrict__ oh, const int* __restrict__ om0,
+                                     const int* __restrict__ okey, double H, double beta, double2* __restrict__ sc,
+                                     double2* __restrict__ st, double2* __restrict__ snu, double* __restrict__ sh,
+                                     cplx* __restrict__ sph, int* __restrict__ sm0, int* __restrict__ sleaf) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= E) return;
+  const int e = perm[s], m = om0[e];
+  const double2 c = oc[e];
+  sc[s] = double2{c.x, __dsub_rn(c.y, __dmul_rn((double)m, H))};
+  st[s] = ot[e];
+  snu[s] = onu[e];
+  sh[s] = oh[e];
+  double sn, cs;
+  sincos(__dmul_rn((double)(-m), beta), &sn, &cs);
+  sph[s] = cplx{cs, sn};
+  sm0[s] = m;
+  sleaf[s] = okey[e];
+}
+
+cudaError_t k_sort_elements(pfmbem* h) {
+  sort_elements_kernel<<<(h->E + 255) / 256, 256, 0, h->stream>>>(
+      h->E, h->s_perm, h->o_c, h->o_t, h->o_nu, h->o_h, h->o_m0, h->o_key, h->H, h->beta, h->s_c, h->s_t, h->s_nu,
+      h->s_h, h->s_ph, h->s_m0, h->s_leaf);
+  return cudaGetLastError();
+}
+
+// Concatenated source list of every leaf (sorted element, image m): the
+// elements of the leaf's near-list boxes in list order.  One block per leaf.
+__global__ void near_sources_kernel(const int* __restrict__ nl_ptr, const int* __restrict__ nl_src,
+                                    const int* __restrict__ nl_img, const int* __restrict__ bb,
+                                    const int* __restrict__ be, const int* __restrict__ sbase, int* __restrict__ src,
+                                    int* __restrict__ img) {
+  const int li = blockIdx.x;
+  int o = sbase[li];
+  for (int e = nl_ptr[li]; e < nl_ptr[li + 1]; ++e) {
+    const int sb = nl_src[e], m = nl_img[e], f0 = bb[sb], n = be[sb] - f0;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      src[o + t] = f0 + t;
+      img[o + t] = m;
+    }
+    o += n;
   }
 }
 
@@ -1217,9 +1284,11 @@ cudaError_t k_build_caches(pfmbem* h) {
   cudaStream_t st = h->stream;
   Level& leaf = h->lev[h->D];
   cplx c2{h->c2re, h->c2im};
+  near_sources_kernel<<<leaf.nne, 128, 0, st>>>(h->nl_ptr, h->nl_src, h->nl_img, leaf.box_begin, leaf.box_end,
+                                                h->nc_sbase, h->nc_src, h->nc_img);
   // same-fiber blocks and k tables first: the near-field build reads the k tables
   prof_begin(h, PH_BUILD);
-  fiber_build_kernel<<<dim3(h->nfb_rows, (h->max_fiber + 127) / 128), 128, 0, st>>>(
+  fiber_build_kernel<<<dim3(h->nfb_rows, (h->max_fiber + 128 / FB_SPLIT - 1) / (128 / FB_SPLIT), 2), 128, 0, st>>>(
       h->fb_rows, h->o_fiber, h->fib_off, h->fb_base, h->k, h->k1, h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu,
       h->o_h, h->self4, h->kt_base, h->kt_val, h->fb_val, h->fb_valf, h->stat_dev);
   prof_end(h, PH_BUILD);
