@@ -460,7 +460,8 @@ static pfmbem_status build_pair_tables(pfmbem* h, const double* nodes, const std
   if ((st = upload(h, &h->pl_img, pli)) != PFMBEM_OK) return st;
   if ((st = upload(h, &h->pl_tab, plt)) != PFMBEM_OK) return st;
   h->tab_val = dalloc<cplx>(h, (size_t)4 * h->tab_entries);
-  if (!h->tab_val) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber-pair tables)");
+  h->tab_valf = dalloc<cplxf>(h, (size_t)4 * h->tab_entries);
+  if (!h->tab_val || !h->tab_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber-pair tables)");
   return PFMBEM_OK;
 }
 
@@ -1028,6 +1029,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if ((st = upload(h, &h->kt_base, kbase)) != PFMBEM_OK) return st;
       if ((st = build_pair_tables(h, nodes, foff, fib, m0, perm, nl_ptr, nl_src, nl_img)) != PFMBEM_OK) return st;
       h->kt_val = dalloc<cplx>(h, (size_t)4 * kacc);
+      h->kt_sval = dalloc<cplx>(h, (size_t)4 * kacc);
+      h->kt_svalf = dalloc<cplxf>(h, (size_t)4 * kacc);
+      if (!h->kt_sval || !h->kt_svalf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
       if (!h->kt_val) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
       h->nchunk = (int)chunks.size() / 3;
       // queue of the near pairs integrated directly: every block in the worst case

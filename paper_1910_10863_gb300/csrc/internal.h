@@ -192,7 +192,8 @@ struct pfmbem {
   int* tab_m = nullptr;          // [ntab] its image shift (periods)
   int64_t* tab_start = nullptr;  // [ntab + 1] first entry of every table (4 values each)
   int* tab_nb = nullptr;         // [ntab] elements of the source fiber
-  cplx* tab_val = nullptr;
+  cplx* tab_val = nullptr;       // as near-field blocks: (i/4) D, (eta/4) S, (i/4) T, (eta/4) K
+  cplxf* tab_valf = nullptr;
   unsigned long long* nq = nullptr;   // near pairs left to integrate directly (leaf, row, column)
   unsigned* nq_len = nullptr;
   unsigned nq_cap = 0;
@@ -204,6 +205,8 @@ struct pfmbem {
   int* s_m0 = nullptr;           // sorted: periods the element was shifted by when wrapped into the root
   int64_t* kt_base = nullptr;    // [M] first entry of the fiber's k table, -1 when not a regular polygon
   cplx* kt_val = nullptr;        // [sum N over regular fibers][4]: S, D, K, T at k of (f0, f0 + dl)
+  cplx* kt_sval = nullptr;       // the same as near-field blocks: (i/4) D, (eta/4) S, (i/4) T, (eta/4) K
+  cplxf* kt_svalf = nullptr;
   int nchunk = 0;
   cplx* fb_val = nullptr;
   cplxf* fb_valf = nullptr;

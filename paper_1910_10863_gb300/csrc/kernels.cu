@@ -567,6 +567,19 @@ __device__ __forceinline__ void pair4_f64(double kap, double2 x, double2 nx, dou
   }
 }
 
+// A near-field block from S, D, K, T (without i/4) at the matrix wavenumber:
+// (i/4) {D, -i eta S, T, -i eta K} = {(i/4) D, (eta/4) S, (i/4) T, (eta/4) K},
+// the form in which the tables keep them (FP64 and FP32).
+__device__ __forceinline__ void near_block_form(double eta, cplx S, cplx D, cplx K, cplx T, cplx* o, cplxf* of) {
+  const double e4 = 0.25 * eta;
+  const cplx b[4] = {cplx{-0.25 * D.im, 0.25 * D.re}, cplx{e4 * S.re, e4 * S.im}, cplx{-0.25 * T.im, 0.25 * T.re},
+                     cplx{e4 * K.re, e4 * K.im}};
+  for (int q = 0; q < 4; ++q) {
+    o[q] = b[q];
+    of[q] = cplxf{(float)b[q].re, (float)b[q].im};
+  }
+}
+
 // ---------------------------------------------------------------- permute
 __global__ void gather_dens_kernel(int E, const int* __restrict__ perm, const cplx* __restrict__ ph,
                                    const cplx* __restrict__ x, cplx* __restrict__ dens) {
@@ -875,8 +888,9 @@ __global__ void pair_table_kernel(int ntab, const int* __restrict__ tA, const in
                                   const int* __restrict__ tm, const int64_t* __restrict__ tbase,
                                   const int64_t* __restrict__ tstart, const int* __restrict__ foff, double k,
                                   double H, const double2* __restrict__ oc, const double2* __restrict__ ot,
-                                  const double2* __restrict__ onu, const double* __restrict__ oh,
-                                  cplx* __restrict__ tval, unsigned long long* __restrict__ stat) {
+                                  const double2* __restrict__ onu, const double* __restrict__ oh, double eta,
+                                  cplx* __restrict__ tval, cplxf* __restrict__ tvalf,
+                                  unsigned long long* __restrict__ stat) {
   const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long np = 0, nq = 0;
   if (gi < tstart[ntab]) {
@@ -899,11 +913,7 @@ __global__ void pair_table_kernel(int ntab, const int* __restrict__ tA, const in
     const int g = gl_order(q, 0);
     cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
     pair4_f64(k, x, nx, c, ot[f], onu[f], hh, g, S, Dv, K, T);
-    cplx* tv = tval + 4 * (tbase[t] + local);
-    tv[0] = S;
-    tv[1] = Dv;
-    tv[2] = K;
-    tv[3] = T;
+    near_block_form(eta, S, Dv, K, T, tval + 4 * (tbase[t] + local), tvalf + 4 * (tbase[t] + local));
     np = 1;
     nq = g;
   }
@@ -945,13 +955,13 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
                                   const int* __restrict__ perm, const int* __restrict__ ofib,
                                   const int* __restrict__ foff, const int* __restrict__ sm0,
                                   const int64_t* __restrict__ kbase, const cplx* __restrict__ kval,
-                                  const int* __restrict__ pl_ptr, const int* __restrict__ pl_fib,
-                                  const int* __restrict__ pl_img, const int* __restrict__ pl_tab,
-                                  const int64_t* __restrict__ tab_base, const int* __restrict__ tab_nb,
-                                  const cplx* __restrict__ tab_val,
-                                  cplx* __restrict__ val, cplxf* __restrict__ valf,
-                                  unsigned long long* __restrict__ queue, unsigned* __restrict__ qlen,
-                                  unsigned qcap) {
+                                  const cplxf* __restrict__ kvalf, const int* __restrict__ pl_ptr,
+                                  const int* __restrict__ pl_fib, const int* __restrict__ pl_img,
+                                  const int* __restrict__ pl_tab, const int64_t* __restrict__ tab_base,
+                                  const int* __restrict__ tab_nb, const cplx* __restrict__ tab_val,
+                                  const cplxf* __restrict__ tab_valf, cplx* __restrict__ val,
+                                  cplxf* __restrict__ valf, unsigned long long* __restrict__ queue,
+                                  unsigned* __restrict__ qlen, unsigned qcap) {
   extern __shared__ int nbs[];
   const int li = blockIdx.x;
   const int box = ne[li];
@@ -1011,7 +1021,6 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
     r_tab[q] = near_lookup(fs, s_ff[j], s_dm[j] + r_ms[r], kbase[fs], pl_ptr, pl_fib, pl_img, pl_tab);
   }
   __syncthreads();
-  const cplx q4{0.0, 0.25};
   for (int t = warp; t < nt; t += nw) {
     const int s = s0 + t;
     const int es = t_es[t], fs = t_fs[t], ms = t_ms[t];
@@ -1020,53 +1029,49 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
     const int r = t_run[t];
     cplx* row = val + base[li] + (int64_t)t * ns * 4;
     cplxf* rowf = valf ? valf + base[li] + (int64_t)t * ns * 4 : nullptr;
-    for (int j = lane; j < ns; j += 32) {
+    // four lanes per source j, one complex value each, so that a warp writes
+    // 8 whole blocks (512 contiguous bytes in FP64) per store
+    const int q = lane & 3;
+    for (int j = lane >> 2; j < ns; j += 8) {
       const int m = s_m[j];
-      cplx b0{0, 0}, b1{0, 0}, b2{0, 0}, b3{0, 0};
-      if (!(s_f[j] == s && m == 0)) {
-        const int ef = s_ef[j], ff = s_ff[j];
-        const int tab = r >= 0 ? r_tab[r * ns + j]
-                               : near_lookup(fs, ff, s_dm[j] + ms, kb, pl_ptr, pl_fib, pl_img, pl_tab);
-        const cplx* tv;
-        if (tab == -2) {
-          // same fiber and, in true coordinates, the same image: a rotation of the k table
-          int dl = ef - es;
-          if (dl < 0) dl += fN;
-          tv = kval + 4 * (kb + dl);
-        } else if (tab >= 0) {
-          // a translated copy of a fiber pair whose integrals are tabulated
-          tv = tab_val + 4 * (tab_base[tab] + (int64_t)(es - fo) * tab_nb[tab] + (ef - foff[ff]));
-        } else {
-          const unsigned at = atomicAdd(qlen, 1u);
-          if (at < qcap)
-            queue[at] = ((unsigned long long)li << 40) | ((unsigned long long)t << 24) | (unsigned long long)j;
-          continue;
-        }
-        const cplx S = tv[0], Dv = tv[1], K = tv[2], T = tv[3];
-        if (m == 0) {
-          // (i/4) {D, -i eta S, T, -i eta K} = {(i/4) D, (eta/4) S, (i/4) T, (eta/4) K}
-          const double e4 = 0.25 * eta;
-          b0 = cplx{-0.25 * Dv.im, 0.25 * Dv.re};
-          b1 = cplx{e4 * S.re, e4 * S.im};
-          b2 = cplx{-0.25 * T.im, 0.25 * T.re};
-          b3 = cplx{e4 * K.re, e4 * K.im};
-        } else {
-          const cplx ph = q4 * ipow_phase(alpha, m);         // (i/4) alpha^m
-          b0 = ph * Dv;
-          b1 = (-eta) * mul_i(ph * S);
-          b2 = ph * T;
-          b3 = (-eta) * mul_i(ph * K);
-        }
+      if (s_f[j] == s && m == 0) {
+        row[4 * j + q] = cplx{0, 0};
+        if (rowf) rowf[4 * j + q] = cplxf{0.f, 0.f};
+        continue;
       }
-      row[4 * j + 0] = b0;
-      row[4 * j + 1] = b1;
-      row[4 * j + 2] = b2;
-      row[4 * j + 3] = b3;
-      if (rowf) {
-        rowf[4 * j + 0] = cplxf{(float)b0.re, (float)b0.im};
-        rowf[4 * j + 1] = cplxf{(float)b1.re, (float)b1.im};
-        rowf[4 * j + 2] = cplxf{(float)b2.re, (float)b2.im};
-        rowf[4 * j + 3] = cplxf{(float)b3.re, (float)b3.im};
+      const int ef = s_ef[j], ff = s_ff[j];
+      const int tab = r >= 0 ? r_tab[r * ns + j] : near_lookup(fs, ff, s_dm[j] + ms, kb, pl_ptr, pl_fib, pl_img, pl_tab);
+      int64_t at;
+      const cplx* tv;
+      const cplxf* tvf;
+      if (tab == -2) {
+        // same fiber and, in true coordinates, the same image: a rotation of the k table
+        int dl = ef - es;
+        if (dl < 0) dl += fN;
+        at = 4 * (kb + dl);
+        tv = kval;
+        tvf = kvalf;
+      } else if (tab >= 0) {
+        // a translated copy of a fiber pair whose integrals are tabulated
+        at = 4 * (tab_base[tab] + (int64_t)(es - fo) * tab_nb[tab] + (ef - foff[ff]));
+        tv = tab_val;
+        tvf = tab_valf;
+      } else {
+        if (q == 0) {
+          const unsigned at2 = atomicAdd(qlen, 1u);
+          if (at2 < qcap)
+            queue[at2] = ((unsigned long long)li << 40) | ((unsigned long long)t << 24) | (unsigned long long)j;
+        }
+        continue;
+      }
+      // the tables hold the blocks of image 0; image m adds the factor alpha^m
+      if (m == 0) {
+        row[4 * j + q] = tv[at + q];
+        if (rowf) rowf[4 * j + q] = tvf[at + q];
+      } else {
+        const cplx b = ipow_phase(alpha, m) * tv[at + q];
+        row[4 * j + q] = b;
+        if (rowf) rowf[4 * j + q] = cplxf{(float)b.re, (float)b.im};
       }
     }
   }
@@ -1149,6 +1154,7 @@ __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __re
                                    const double2* __restrict__ ot, const double2* __restrict__ onu,
                                    const double* __restrict__ oh, const cplx* __restrict__ self4,
                                    const int64_t* __restrict__ kbase, cplx* __restrict__ kval,
+                                   cplx* __restrict__ ksval, cplxf* __restrict__ ksvalf,
                                    cplx* __restrict__ val, cplxf* __restrict__ valf,
                                    unsigned long long* __restrict__ stat) {
   const int e = rows[blockIdx.x];
@@ -1187,6 +1193,7 @@ __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __re
       tv[1] = Dv;
       tv[2] = K;
       tv[3] = T;
+      near_block_form(eta, S, Dv, K, T, ksval + 4 * (kb + fl), ksvalf + 4 * (kb + fl));
     } else {
       const int64_t r0 = fbase[fb] + (int64_t)(2 * el) * (2 * N), r1 = r0 + 2 * N;
       const cplx c2r = rho * c2;
@@ -1290,13 +1297,13 @@ cudaError_t k_build_caches(pfmbem* h) {
   prof_begin(h, PH_BUILD);
   fiber_build_kernel<<<dim3(h->nfb_rows, (h->max_fiber + 128 / FB_SPLIT - 1) / (128 / FB_SPLIT), 2), 128, 0, st>>>(
       h->fb_rows, h->o_fiber, h->fib_off, h->fb_base, h->k, h->k1, h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu,
-      h->o_h, h->self4, h->kt_base, h->kt_val, h->fb_val, h->fb_valf, h->stat_dev);
+      h->o_h, h->self4, h->kt_base, h->kt_val, h->kt_sval, h->kt_svalf, h->fb_val, h->fb_valf, h->stat_dev);
   prof_end(h, PH_BUILD);
   if (h->ntab > 0) {
     prof_begin(h, PH_BUILD);
     pair_table_kernel<<<(unsigned)((h->tab_entries + 255) / 256), 256, 0, st>>>(
         h->ntab, h->tab_A, h->tab_B, h->tab_m, h->tab_start, h->tab_start, h->fib_off, h->k, h->H, h->o_c, h->o_t,
-        h->o_nu, h->o_h, h->tab_val, h->stat_dev);
+        h->o_nu, h->o_h, h->eta, h->tab_val, h->tab_valf, h->stat_dev);
     prof_end(h, PH_BUILD);
   }
   cudaMemsetAsync(h->nq_len, 0, sizeof(unsigned), st);
@@ -1311,10 +1318,10 @@ cudaError_t k_build_caches(pfmbem* h) {
     }
     near_build_kernel<<<leaf.nne, 256, smem, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
                                                    h->nc_src, h->nc_img, h->eta, h->alpha, h->s_perm, h->o_fiber,
-                                                   h->fib_off, h->s_m0, h->kt_base, h->kt_val,
+                                                   h->fib_off, h->s_m0, h->kt_base, h->kt_sval, h->kt_svalf,
                                                    h->ntab > 0 ? h->pl_ptr : nullptr, h->pl_fib, h->pl_img, h->pl_tab,
-                                                   h->tab_start, h->tab_nb, h->tab_val, h->nc_val, h->nc_valf, h->nq,
-                                                   h->nq_len, h->nq_cap);
+                                                   h->tab_start, h->tab_nb, h->tab_val, h->tab_valf, h->nc_val,
+                                                   h->nc_valf, h->nq, h->nq_len, h->nq_cap);
   }
   prof_end(h, PH_BUILD);
   prof_begin(h, PH_BUILD);
