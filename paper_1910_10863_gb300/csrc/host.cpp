@@ -1267,11 +1267,13 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         h->Unf = dalloc<cplxf>(h, (size_t)2 * E);
         if (!h->Un || !h->Unf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near sums)");
         h->fz_bar = dalloc<unsigned>(h, 2);
+        h->arn_bar = dalloc<unsigned>(h, 2);
         h->fz_err = dalloc<int>(h, 1);
         h->fz_stamp = dalloc<unsigned long long>(h, 32);
-        if (!h->fz_bar || !h->fz_err || !h->fz_stamp)
+        if (!h->fz_bar || !h->arn_bar || !h->fz_err || !h->fz_stamp)
           return fail(h, PFMBEM_ENOMEM, "device allocation failed (barrier)");
         CK(cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned), h->stream));
+        CK(cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->stream));
         CK(cudaMemsetAsync(h->fz_err, 0, sizeof(int), h->stream));
         h->fused = true;
         h->pc = h->pc_val != nullptr || h->pr_val != nullptr;
@@ -1374,12 +1376,81 @@ static pfmbem_status gmres_alloc(pfmbem* h, int m) {
   if (h->pc) g.Z = dalloc<cplx>(h, (size_t)m * n);
   if (!g.V || !g.w || !g.r || !g.x || !g.b || !g.d || !g.c || !g.hcol || !g.nrm || (h->pc && !g.Z))
     return fail(h, PFMBEM_ENOMEM, "GMRES workspace");
+  if (h->arn_grid > 0) {
+    g.H = dalloc<cplx>(h, (size_t)(m + 1) * m);
+    g.cs = dalloc<cplx>(h, m);
+    g.sn = dalloc<cplx>(h, m);
+    g.gv = dalloc<cplx>(h, m + 1);
+    g.acc = dalloc<cplx>(h, 2 * (2 * (size_t)(m + 1) + 1));
+    g.y = dalloc<cplx>(h, m);
+    g.ctl = dalloc<double>(h, 4);
+    g.ictl = dalloc<int>(h, 4);
+    if (!g.H || !g.cs || !g.sn || !g.gv || !g.acc || !g.y || !g.ctl || !g.ictl)
+      return fail(h, PFMBEM_ENOMEM, "GMRES workspace");
+  }
   g.hhost = pinned_small_get();
   if (!g.hhost) return fail(h, PFMBEM_ENOMEM, "pinned host buffer");
   return PFMBEM_OK;
 }
 
 static inline std::complex<double> toz(cplx a) { return {a.re, a.im}; }
+
+// Arnoldi steps enqueued per host check of the device-side GMRES cycle.
+constexpr int kArnBatch = 4;
+
+// One restart cycle of GMRES with the Arnoldi steps on the device (single-launch
+// products): from V_0 = r / beta, the steps run as (preconditioner,) product
+// and arnoldi step, kArnBatch at a time, and the host reads back only the done
+// flag, the step count and the estimate after each batch.  Steps queued after
+// the cycle finished return at once.  On return x += Z y (or V y), *steps and
+// *est are the cycle's step count and residual estimate, *reason its end
+// (1 estimate below thr, 2 breakdown, 3 restart length or maxit).
+static pfmbem_status gmres_cycle_device(pfmbem* h, cplx* x, double beta, double bnorm, double thr, int max_steps,
+                                        int precision, int* steps, double* est, int* reason) {
+  GmresWork& g = h->gw;
+  const int n = g.n, m = g.m;
+  cplx* hh = g.hhost;
+  double* hctl = reinterpret_cast<double*>(hh + 256);
+  int* hictl = reinterpret_cast<int*>(hh + 260);
+  CK(cudaMemsetAsync(g.gv, 0, sizeof(cplx) * (m + 1), h->stream));
+  CK(cudaMemsetAsync(g.acc, 0, sizeof(cplx) * 2 * (2 * (size_t)(m + 1) + 1), h->stream));
+  CK(cudaMemsetAsync(g.ictl, 0, sizeof(int) * 4, h->stream));
+  hh[0] = cplx{beta, 0};
+  hctl[0] = 1.0;
+  hctl[1] = bnorm;
+  hctl[2] = thr;
+  CK(cudaMemcpyAsync(g.gv, hh, sizeof(cplx), cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(g.ctl, hctl, 3 * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  const int limit = std::min(m, max_steps);
+  int j = 0, done_steps = 0;
+  *reason = 0;
+  // z_0 = P^-1 v_0 here; every later z_{j+1} comes out of the Arnoldi step j
+  if (h->pc) CK(k_precond_apply(h, g.V, g.Z, precision));
+  while (j < limit) {
+    const int nb = std::min(kArnBatch, limit - j);
+    for (int i = 0; i < nb; ++i, ++j) {
+      const cplx* zj = (h->pc ? g.Z : g.V) + (size_t)j * n;
+      CK(k_matvec_fused(h, zj, g.w, precision, g.ictl));
+      CK(k_arnoldi_step(h, j, precision));
+    }
+    CK(cudaMemcpyAsync(hictl, g.ictl, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(hctl + 3, g.ctl, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    done_steps = hictl[1];
+    if (hictl[0]) {
+      *reason = hictl[2];
+      break;
+    }
+  }
+  if (*reason == 0) *reason = 3;
+  *steps = done_steps;
+  *est = hctl[3];
+  if (done_steps > 0) {
+    CK(k_arnoldi_solve(h, g.y));
+    CK(k_gemv_add(h, h->pc ? g.Z : g.V, done_steps, g.y, x, n));   // x += Z y (flexible) or V y
+  }
+  return PFMBEM_OK;
+}
 
 // Restarted GMRES(m) with classical Gram-Schmidt applied twice; A is applied by
 // the FMM matvec in the given precision.  Solves A x = b in place of x (device).
@@ -1426,6 +1497,20 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
     if (!std::isfinite(relres)) return fail(h, PFMBEM_ENUMERIC, "non-finite residual");
     if (relres <= tol || iters >= maxit) break;
     CK(k_scale_copy(h, g.r, cplx{1.0 / beta, 0}, g.V, n));
+    if (h->arn_grid > 0 && h->fused && h->cached && m < 256) {
+      int steps = 0, reason = 0;
+      double est = 1;
+      pfmbem_status sc = gmres_cycle_device(h, x, beta, bnorm, 0.5 * tol, maxit - iters, precision, &steps, &est,
+                                            &reason);
+      if (sc != PFMBEM_OK) return sc;
+      iters += steps;
+      ++restarts;
+      if (reason != 3 && trust_estimate) {
+        relres = est;
+        done = true;
+      }
+      continue;
+    }
     std::fill(gvec.begin(), gvec.end(), 0.0);
     gvec[0] = beta;
     int j = 0;

@@ -100,6 +100,15 @@ struct GmresWork {
   cplx* hcol = nullptr;     // [m+2] device dot results
   double* nrm = nullptr;    // [2]
   cplx* hhost = nullptr;    // pinned host mirror of hcol
+  // device-side GMRES cycle (single-launch products only)
+  cplx* H = nullptr;        // [(m+1)][m] rotated Hessenberg matrix
+  cplx* cs = nullptr;       // [m] Givens rotations
+  cplx* sn = nullptr;
+  cplx* gv = nullptr;       // [m+1] rotated right-hand side
+  cplx* acc = nullptr;      // [2][2 (m+1) + 1] CGS2 sums by step parity
+  cplx* y = nullptr;        // [m] least-squares solution of the cycle
+  double* ctl = nullptr;    // [4] estimate, ||b||, threshold
+  int* ictl = nullptr;      // [4] done, steps completed, reason
 };
 
 enum Phase { PH_GATHER = 0, PH_P2M, PH_M2M, PH_LOCAL, PH_L2P, PH_NEAR, PH_FIBER, PH_BLAS, PH_SETUP, PH_OUT, PH_BUILD,
@@ -227,6 +236,8 @@ struct pfmbem {
   // single-launch cached matvec (cooperative grid, device-wide barrier)
   bool fused = false;
   int fz_grid64 = 0, fz_grid32 = 0;
+  int arn_grid = 0;              // blocks of the device-side GMRES step (0: host-side steps)
+  unsigned* arn_bar = nullptr;   // [2] its barrier words
   unsigned* fz_bar = nullptr;    // [2] barrier arrivals and generation
   int fz_nfft = 0;               // fibers whose block-circulant block is applied by FFT
   int* fz_fft = nullptr;         // their indices
@@ -297,10 +308,12 @@ cudaError_t k_sort_elements(pfmbem* h);
 // single-launch cached matvec (matvec_fused.cu)
 cudaError_t k_fused_prepare(pfmbem* h, bool* ok);
 cudaError_t k_top_operators(pfmbem* h, cudaStream_t st);
-cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision);
+cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done = nullptr);
+cudaError_t k_arnoldi_step(pfmbem* h, int j, int precision);
+cudaError_t k_arnoldi_solve(pfmbem* h, cplx* y);
 cudaError_t k_fiber_symbols(pfmbem* h);
 cudaError_t k_precond_symbols(pfmbem* h);
-cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision);
+cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done = nullptr);
 cudaError_t k_precond_rows(pfmbem* h);
 cudaError_t k_build_fmm_caches(pfmbem* h);
 // learned warm start (mlp.cu)

@@ -104,6 +104,7 @@ struct FusedArgs {
   unsigned* bar;                     // [0] arrivals, [1] generation
   int* err;
   unsigned long long* stamp;         // optional stage end times (ns), written by block 0
+  const int* done;                   // optional: the product is skipped when *done != 0
 };
 
 __device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k) {
@@ -484,13 +485,9 @@ __global__ void precond_rows_kernel(const int* __restrict__ fib_list, const int*
 // y^(r) = IFFT( sum_s Binv^(r,s) FFT(x^(s)) ) where a symbol exists, y = x
 // elsewhere.  One block per fiber.
 template <class C>
-__global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const int64_t* __restrict__ fh_base,
-                                     const C* __restrict__ pc, const C* __restrict__ tw,
-                                     const int64_t* __restrict__ pr_base, const C* __restrict__ pr,
-                                     const cplx* __restrict__ x, cplx* __restrict__ y) {
-  extern __shared__ unsigned char smraw[];
-  C* xs = reinterpret_cast<C*>(smraw);            // [2][N]
-  const int fb = blockIdx.x;
+__device__ void precond_fiber(int fb, const int* __restrict__ foff, const int64_t* __restrict__ fh_base,
+                              const C* __restrict__ pc, const C* __restrict__ tw, const int64_t* __restrict__ pr_base,
+                              const C* __restrict__ pr, const cplx* __restrict__ x, cplx* __restrict__ y, C* xs) {
   const int f0 = foff[fb], N = foff[fb + 1] - f0;
   const int64_t base = fh_base[fb];
   if (base < 0) {
@@ -542,6 +539,217 @@ __global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const 
   for (int t = threadIdx.x; t < 2 * N; t += blockDim.x) {
     const int r = t >> lg, e = f0 + (t & (N - 1));
     y[2 * e + r] = inv * to_d(xs[t]);
+  }
+}
+
+// y = P^-1 x, one block per fiber (see precond_fiber).
+template <class C>
+__global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const int64_t* __restrict__ fh_base,
+                                     const C* __restrict__ pc, const C* __restrict__ tw,
+                                     const int64_t* __restrict__ pr_base, const C* __restrict__ pr,
+                                     const cplx* __restrict__ x, cplx* __restrict__ y, const int* done) {
+  if (done && *(volatile const int*)done != 0) return;
+  extern __shared__ unsigned char smraw[];
+  precond_fiber<C>(blockIdx.x, foff, fh_base, pc, tw, pr_base, pr, x, y, reinterpret_cast<C*>(smraw));
+}
+
+// ------------------------------------------------------------ device-side GMRES step
+// One Arnoldi step of GMRES after w = A z_j, as one cooperative launch:
+// classical Gram-Schmidt applied twice (h1 = V^H w, w -= V h1, h2 = V^H w,
+// w -= V h2), v_{j+1} = w / ||w||, and then, by one thread, the Givens rotations
+// of the new Hessenberg column h1 + h2 (+ ||w|| below the diagonal), the
+// rotated right-hand side g and the residual estimate |g_{j+1}| / ||b||.  The
+// step raises the cycle's done flag when the estimate reaches the threshold,
+// on breakdown (||w|| = 0) or at the restart length; every kernel of the
+// cycle queued after that returns at once.  All FP64.  Each block owns one
+// contiguous slice of the n entries; the dot products go one warp per basis
+// column over the slice and meet by atomic adds.  The sums of step j live in
+// accumulator set j mod 2, and step j clears the other set for step j + 1.
+struct ArnArgs {
+  int n, m, j;
+  cplx* V;                           // [(m+1)][n] orthonormal basis
+  cplx* w;                           // [n] A z_j on entry
+  cplx* H;                           // [(m+1)][m] Hessenberg matrix, rotated into triangular form
+  cplx* cs;                          // [m] Givens rotations
+  cplx* sn;
+  cplx* g;                           // [m+1] rotated right-hand side (beta e_1 at the cycle start)
+  cplx* acc;                         // [2][2 (m+1) + 1] CGS2 sums h1, h2 and ||w||^2, by step parity
+  double* ctl;                       // [0] estimate (out), [1] ||b||, [2] threshold
+  int* ictl;                         // [0] done, [1] steps completed in the cycle, [2] reason (1 est, 2 breakdown, 3 restart)
+  unsigned* bar;
+  int* err;
+  // with the block-Jacobi preconditioner, z_{j+1} = P^-1 v_{j+1} fiber by fiber
+  cplx* Zn;                          // [n] z_{j+1}, or null (no preconditioner)
+  int M;
+  const int* foff;
+  const int64_t* fh_base;
+  const void* pc;                    // inverse symbols (FFT fibers), in the precision of the products
+  const void* tw;
+  const int64_t* pr_base;            // circulant inverse row pairs (the other regular polygons)
+  const void* pr;
+};
+
+constexpr int ARN_MAXC = 256;        // columns of the basis the kernel can hold (restart length <= 250)
+
+__device__ __forceinline__ void arn_dots(const ArnArgs& a, int nc, int t0, int t1, cplx* out, int warp, int lane) {
+  for (int c = warp; c < nc; c += FW) {
+    const cplx* v = a.V + (size_t)c * a.n;
+    cplx s{0, 0};
+#pragma unroll 4
+    for (int t = t0 + lane; t < t1; t += 32) s += conj(v[t]) * a.w[t];
+    s = wsum(s);
+    if (lane == 0) atomic_add(out + c, s);
+  }
+}
+
+template <class C>
+__global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
+  if (*(volatile const int*)a.ictl != 0) return;
+  extern __shared__ unsigned char smraw[];
+  __shared__ cplx sh[ARN_MAXC];
+  __shared__ double red[FW];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int G = gridDim.x, b = blockIdx.x;
+  const int t0 = (int)((int64_t)a.n * b / G), t1 = (int)((int64_t)a.n * (b + 1) / G);
+  const int nc = a.j + 1, S = 2 * (a.m + 1) + 1;
+  cplx* h1 = a.acc + (size_t)(a.j & 1) * S;
+  cplx* h2 = h1 + (a.m + 1);
+  double* nrm = reinterpret_cast<double*>(h2 + (a.m + 1));
+  if (b == 0) {
+    cplx* other = a.acc + (size_t)((a.j + 1) & 1) * S;
+    for (int i = threadIdx.x; i < S; i += FB) other[i] = cplx{0, 0};
+  }
+  // h1 = V^H w
+  arn_dots(a, nc, t0, t1, h1, warp, lane);
+  if (!grid_barrier(a.bar, a.err)) return;
+  // w -= V h1; h2 = V^H w
+  for (int i = threadIdx.x; i < nc; i += FB) sh[i] = ldcg(h1 + i);
+  __syncthreads();
+  for (int t = t0 + threadIdx.x; t < t1; t += FB) {
+    cplx v = a.w[t];
+#pragma unroll 4
+    for (int c = 0; c < nc; ++c) v -= a.V[(size_t)c * a.n + t] * sh[c];
+    a.w[t] = v;
+  }
+  __syncthreads();
+  arn_dots(a, nc, t0, t1, h2, warp, lane);
+  if (!grid_barrier(a.bar, a.err)) return;
+  // w -= V h2; ||w||^2
+  for (int i = threadIdx.x; i < nc; i += FB) sh[i] = ldcg(h2 + i);
+  __syncthreads();
+  double part = 0;
+  for (int t = t0 + threadIdx.x; t < t1; t += FB) {
+    cplx v = a.w[t];
+#pragma unroll 4
+    for (int c = 0; c < nc; ++c) v -= a.V[(size_t)c * a.n + t] * sh[c];
+    a.w[t] = v;
+    part += v.re * v.re + v.im * v.im;
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
+  if (lane == 0) red[warp] = part;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0;
+    for (int i = 0; i < FW; ++i) tot += red[i];
+    atomicAdd(nrm, tot);
+  }
+  if (!grid_barrier(a.bar, a.err)) return;
+  // v_{j+1} = w / ||w|| and, with the preconditioner, z_{j+1} = P^-1 v_{j+1}
+  // (one block per fiber: a fiber's block of P^-1 reads only its own entries)
+  const double hn = sqrt(*(volatile double*)nrm);
+  const double inv = hn > 0 ? 1.0 / hn : 0.0;
+  cplx* vn = a.V + (size_t)(a.j + 1) * a.n;
+  if (a.Zn) {
+    for (int fb = b; fb < a.M; fb += G) {
+      __syncthreads();
+      for (int t = 2 * a.foff[fb] + threadIdx.x; t < 2 * a.foff[fb + 1]; t += FB) vn[t] = inv * a.w[t];
+      __syncthreads();
+      precond_fiber<C>(fb, a.foff, a.fh_base, static_cast<const C*>(a.pc), static_cast<const C*>(a.tw), a.pr_base,
+                       static_cast<const C*>(a.pr), vn, a.Zn, reinterpret_cast<C*>(smraw));
+    }
+  } else {
+    for (int t = t0 + threadIdx.x; t < t1; t += FB) vn[t] = inv * a.w[t];
+  }
+  if (b == G - 1) {
+    // the new column of H and its Givens rotations (by the last block, which
+    // has no fiber to precondition when the fibers are fewer than the blocks);
+    // the operands are staged in shared memory first, so that the serial part
+    // runs without global-memory latency
+    const int j = a.j, m = a.m;
+    cplx* col = sh;                                   // [j + 2]
+    __shared__ cplx rot[2 * ARN_MAXC];                // cs, sn of the earlier steps
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += FB) col[i] = ldcg(h1 + i) + ldcg(h2 + i);
+    for (int i = threadIdx.x; i < j; i += FB) {
+      rot[i] = a.cs[i];
+      rot[ARN_MAXC + i] = a.sn[i];
+    }
+    if (threadIdx.x == 0) col[j + 1] = cplx{hn, 0};
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < j; ++i) {
+        const cplx x0 = col[i], x1 = col[i + 1], c = rot[i], sn = rot[ARN_MAXC + i];
+        col[i] = conj(c) * x0 + conj(sn) * x1;
+        col[i + 1] = (-sn) * x0 + c * x1;
+      }
+      const cplx x0 = col[j], x1 = col[j + 1];
+      const double den = sqrt(x0.re * x0.re + x0.im * x0.im + x1.re * x1.re + x1.im * x1.im);
+      cplx c{1, 0}, sn{0, 0};
+      if (den != 0) {
+        c = (1.0 / den) * x0;
+        sn = (1.0 / den) * x1;
+      }
+      a.cs[j] = c;
+      a.sn[j] = sn;
+      col[j] = conj(c) * x0 + conj(sn) * x1;
+      col[j + 1] = cplx{0, 0};
+      const cplx gj = a.g[j];
+      a.g[j] = conj(c) * gj;
+      const cplx gn = (-sn) * gj;
+      a.g[j + 1] = gn;
+      const double est = sqrt(gn.re * gn.re + gn.im * gn.im) / a.ctl[1];
+      a.ctl[0] = est;
+      a.ictl[1] = j + 1;
+      const int reason = est <= a.ctl[2] ? 1 : (hn == 0 ? 2 : (j + 1 == m ? 3 : 0));
+      if (reason) {
+        a.ictl[2] = reason;
+        a.ictl[0] = 1;
+      }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += FB) a.H[(size_t)i * m + j] = col[i];
+  }
+}
+
+// y = R^{-1} g over the steps completed in the cycle (R: the rotated H) by
+// back substitution: R (up to 32 steps) is staged in shared memory by the
+// block, then one thread solves.
+__global__ void arnoldi_solve_kernel(const cplx* __restrict__ H, const cplx* __restrict__ g, int m,
+                                     const int* __restrict__ ictl, cplx* __restrict__ y) {
+  constexpr int RS = 32;
+  __shared__ cplx R[RS * RS], gs[RS];
+  const int jf = ictl[1];
+  const bool staged = jf <= RS;
+  if (staged) {
+    for (int t = threadIdx.x; t < jf * jf; t += blockDim.x) {
+      const int i = t / jf, q = t - i * jf;
+      R[i * RS + q] = H[(size_t)i * m + q];
+    }
+    for (int t = threadIdx.x; t < jf; t += blockDim.x) gs[t] = g[t];
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  cplx ys[RS];
+  for (int i = jf - 1; i >= 0; --i) {
+    cplx v = staged ? gs[i] : g[i];
+    if (staged) {
+      for (int q = i + 1; q < jf; ++q) v -= R[i * RS + q] * ys[q];
+      ys[i] = cdiv(v, R[i * RS + i]);
+      y[i] = ys[i];
+    } else {
+      for (int q = i + 1; q < jf; ++q) v -= H[(size_t)i * m + q] * y[q];
+      y[i] = cdiv(v, H[(size_t)i * m + i]);
+    }
   }
 }
 
@@ -631,6 +839,8 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
 
 template <class C>
 __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
+  // a GMRES cycle that has already converged skips the products queued after it
+  if (a.done && *(volatile const int*)a.done != 0) return;
   extern __shared__ unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -915,8 +1125,9 @@ size_t fused_smem(int maxfiber) {
 }
 
 template <class C>
-cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32) {
+cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int* done) {
   FusedArgs<C> a{};
+  a.done = done;
   a.E = h->E;
   a.D = h->D;
   a.perm = h->s_perm;
@@ -1075,6 +1286,24 @@ cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
   h->fz_grid64 = std::min(fused_grid<cplx>(h->max_fiber), need);
   h->fz_grid32 = std::min(fused_grid<cplxf>(h->max_fiber), need);
   if (h->fz_grid64 <= 0 || h->fz_grid32 <= 0) return cudaSuccess;
+  {
+    // device-side GMRES steps: one block per SM (the steps are short; fewer
+    // blocks keep the device-wide barriers cheap)
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = 2 * (size_t)h->max_fiber * sizeof(cplx);
+    int per32 = 0;
+    if (smem > 48 * 1024) {
+      cudaFuncSetAttribute(arnoldi_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(arnoldi_kernel<cplxf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, arnoldi_kernel<cplx>, FB, smem) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, arnoldi_kernel<cplxf>, FB, smem) == cudaSuccess &&
+        per >= 1 && per32 >= 1)
+      h->arn_grid = nsm;
+    cudaGetLastError();
+  }
   *ok = true;
   return cudaGetLastError();
 }
@@ -1123,7 +1352,7 @@ cudaError_t k_precond_rows(pfmbem* h) {
   return cudaGetLastError();
 }
 
-cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision) {
+cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done) {
   const bool f32 = precision == PFMBEM_MIXED;
   const size_t smem = 2 * (size_t)h->max_fiber * (f32 ? sizeof(cplxf) : sizeof(cplx));
   prof_begin(h, PH_BLAS);
@@ -1131,18 +1360,71 @@ cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision) {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(precond_apply_kernel<cplxf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     precond_apply_kernel<cplxf><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_valf, h->twf,
-                                                                h->pr_base, h->pr_valf, x, y);
+                                                                h->pr_base, h->pr_valf, x, y, done);
   } else {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(precond_apply_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     precond_apply_kernel<cplx><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_val, h->tw,
-                                                               h->pr_base, h->pr_val, x, y);
+                                                               h->pr_base, h->pr_val, x, y, done);
   }
   prof_end(h, PH_BLAS);
   return cudaGetLastError();
 }
 
-cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision) {
-  if (precision == PFMBEM_MIXED) return launch_fused<cplxf>(h, x, y, true);
-  return launch_fused<cplx>(h, x, y, false);
+// One Arnoldi step of the device-side GMRES cycle (see arnoldi_kernel); with
+// the preconditioner it also writes z_{j+1} = P^-1 v_{j+1} (in the precision of
+// the products).
+cudaError_t k_arnoldi_step(pfmbem* h, int j, int precision) {
+  GmresWork& g = h->gw;
+  const bool f32 = precision == PFMBEM_MIXED;
+  ArnArgs a{};
+  if (h->pc && j + 1 < g.m) {
+    a.Zn = g.Z + (size_t)(j + 1) * g.n;
+    a.M = h->M;
+    a.foff = h->fib_off;
+    a.fh_base = h->fh_base;
+    a.pc = f32 ? (const void*)h->pc_valf : (const void*)h->pc_val;
+    a.tw = f32 ? (const void*)h->twf : (const void*)h->tw;
+    a.pr_base = h->pr_base;
+    a.pr = f32 ? (const void*)h->pr_valf : (const void*)h->pr_val;
+  }
+  a.n = g.n;
+  a.m = g.m;
+  a.j = j;
+  a.V = g.V;
+  a.w = g.w;
+  a.H = g.H;
+  a.cs = g.cs;
+  a.sn = g.sn;
+  a.g = g.gv;
+  a.acc = g.acc;
+  a.ctl = g.ctl;
+  a.ictl = g.ictl;
+  a.bar = h->arn_bar;
+  a.err = h->fz_err;
+  void* args[] = {&a};
+  const size_t smem = a.Zn ? 2 * (size_t)h->max_fiber * (f32 ? sizeof(cplxf) : sizeof(cplx)) : 0;
+  const void* fn = f32 ? (const void*)arnoldi_kernel<cplxf> : (const void*)arnoldi_kernel<cplx>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  prof_begin(h, PH_BLAS);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(h->arn_grid), dim3(FB), args, smem, h->stream);
+  prof_end(h, PH_BLAS);
+  return e;
+}
+
+// y = R^{-1} g for the cycle's completed steps (device), for x += Z y.
+cudaError_t k_arnoldi_solve(pfmbem* h, cplx* y) {
+  GmresWork& g = h->gw;
+  prof_begin(h, PH_BLAS);
+  arnoldi_solve_kernel<<<1, 256, 0, h->stream>>>(g.H, g.gv, g.m, g.ictl, y);
+  prof_end(h, PH_BLAS);
+  return cudaGetLastError();
+}
+
+cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done) {
+  if (precision == PFMBEM_MIXED) return launch_fused<cplxf>(h, x, y, true, done);
+  return launch_fused<cplx>(h, x, y, false, done);
 }
