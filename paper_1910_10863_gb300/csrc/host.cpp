@@ -620,7 +620,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if (!std::isfinite(a[0]) || !std::isfinite(a[1])) return fail(h, PFMBEM_EGEOM, "non-finite node");
       const int e = foff[i] + j;
       double dx = b[0] - a[0], dy = b[1] - a[1];
-      double L = std::hypot(dx, dy);
+      double L = std::sqrt(dx * dx + dy * dy);      // node coordinates are O(H): no overflow concern
       if (!(L > 0)) return fail(h, PFMBEM_EGEOM, "zero-length element " + std::to_string(e));
       c[e] = double2{0.5 * (a[0] + b[0]), 0.5 * (a[1] + b[1])};
       t[e] = double2{dx / L, dy / L};
@@ -647,7 +647,10 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
     sx /= n;
     sy /= n;
-    for (int j = 0; j < n; ++j) sr += std::hypot(nodes[2 * (foff[i] + j)] - sx, nodes[2 * (foff[i] + j) + 1] - sy);
+    for (int j = 0; j < n; ++j) {
+      const double dx = nodes[2 * (foff[i] + j)] - sx, dy = nodes[2 * (foff[i] + j) + 1] - sy;
+      sr += std::sqrt(dx * dx + dy * dy);
+    }
     h->hfib_geo[3 * i] = sx;
     h->hfib_geo[3 * i + 1] = sy;
     h->hfib_geo[3 * i + 2] = sr / n;
@@ -869,6 +872,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     Level& L = h->lev[l];
     pfmbem_status st;
     if ((st = upload(h, &L.w_dev, L.w)) != PFMBEM_OK) return st;
+    {
+      std::vector<double> iw(L.w.size());
+      for (size_t i = 0; i < iw.size(); ++i) iw[i] = 1.0 / L.w[i];
+      if ((st = upload(h, &L.iw_dev, iw)) != PFMBEM_OK) return st;
+    }
     if ((st = upload(h, &L.ne, L.hne)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.box_begin, L.hbegin)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.box_end, L.hend)) != PFMBEM_OK) return st;
@@ -940,6 +948,67 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // the second stream starts after everything uploaded so far (level weights)
   if (!h->pre_ev) CK(cudaEventCreateWithFlags(&h->pre_ev, cudaEventDisableTiming));
   CK(cudaEventRecord(h->pre_ev, h->stream));
+  // ---------------------------------------------------- translation tables
+  // One FP64 and one FP32 arena hold every level's expansions and operators
+  // (sub-arrays aligned to 256 bytes); the operators are built on the device,
+  // on the second stream as soon as the level weights are up.
+  if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  CK(cudaStreamWaitEvent(h->side, h->pre_ev, 0));
+  h->astream = h->side;
+  {
+    auto up16 = [](size_t n) { return (n + 15) & ~(size_t)15; };
+    size_t n64 = 0, n32 = 0;
+    for (int l = 0; l <= D; ++l) {
+      const Level& L = h->lev[l];
+      const size_t ex = up16((size_t)L.nbox * L.P);
+      const size_t tm = l >= 1 ? up16((size_t)49 * L.P * L.P) : 0;
+      const size_t mm = l < D ? up16((size_t)4 * L.P * h->lev[l + 1].P) : 0;
+      n64 += 2 * ex + 2 * tm + 2 * mm;
+      n32 += 2 * up16(ex) + 2 * up16(tm) + 2 * up16(mm);
+    }
+    cplx* a64 = dalloc<cplx>(h, n64);
+    cplxf* a32 = dalloc<cplxf>(h, n32);
+    if (!a64 || !a32) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions, tables)");
+    TableLevels tl{};
+    for (int l = 0; l <= D; ++l) {
+      Level& L = h->lev[l];
+      const int P = L.P;
+      const size_t ex = up16((size_t)L.nbox * P);
+      L.M = a64; a64 += ex;
+      L.L = a64; a64 += ex;
+      L.Mf = a32; a32 += ex;
+      L.Lf = a32; a32 += ex;
+      tl.p[l] = L.p;
+      tl.d[l] = L.d;
+      tl.w[l] = L.w_dev;
+      if (l >= 1) {
+        const size_t tm = up16((size_t)49 * P * P);
+        L.m2l = a64; a64 += tm;
+        L.m2lt = a64; a64 += tm;
+        L.m2lf = a32; a32 += tm;
+        L.m2ltf = a32; a32 += tm;
+        tl.T[l] = L.m2l; tl.Tt[l] = L.m2lt; tl.Tf[l] = L.m2lf; tl.Ttf[l] = L.m2ltf;
+        if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2) {
+          const int kp = tc_kpad(P);
+          L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
+          if (!L.tc_B) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
+        } else {
+          L.tc_ntile = 0;
+        }
+      }
+      if (l < D) {
+        const size_t mm = up16((size_t)4 * P * h->lev[l + 1].P);
+        L.m2m = a64; a64 += mm;
+        L.l2l = a64; a64 += mm;
+        L.m2mf = a32; a32 += mm;
+        L.l2lf = a32; a32 += mm;
+        tl.A[l] = L.m2m; tl.B[l] = L.l2l; tl.Af[l] = L.m2mf; tl.Bf[l] = L.l2lf;
+      }
+    }
+    CK(k_tables(h, tl, h->astream ? h->astream : h->stream));
+  }
+  h->astream = nullptr;
+
   // ---------------------------------------------------- near-field / fiber caches
   // The element integrals of the caches run on the GPU while the host builds
   // the M2L lists and translation tables on a second stream; the streams join
@@ -1160,61 +1229,6 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   }
   h->info.m2l_pairs = m2l_pairs;
   mark("M2L lists (overlapped)");
-  // ---------------------------------------------------- translation tables
-  // One FP64 and one FP32 arena hold every level's expansions and operators
-  // (sub-arrays aligned to 256 bytes); the operators are built on the device.
-  {
-    auto up16 = [](size_t n) { return (n + 15) & ~(size_t)15; };
-    size_t n64 = 0, n32 = 0;
-    for (int l = 0; l <= D; ++l) {
-      const Level& L = h->lev[l];
-      const size_t ex = up16((size_t)L.nbox * L.P);
-      const size_t tm = l >= 1 ? up16((size_t)49 * L.P * L.P) : 0;
-      const size_t mm = l < D ? up16((size_t)4 * L.P * h->lev[l + 1].P) : 0;
-      n64 += 2 * ex + 2 * tm + 2 * mm;
-      n32 += 2 * up16(ex) + 2 * up16(tm) + 2 * up16(mm);
-    }
-    cplx* a64 = dalloc<cplx>(h, n64);
-    cplxf* a32 = dalloc<cplxf>(h, n32);
-    if (!a64 || !a32) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions, tables)");
-    TableLevels tl{};
-    for (int l = 0; l <= D; ++l) {
-      Level& L = h->lev[l];
-      const int P = L.P;
-      const size_t ex = up16((size_t)L.nbox * P);
-      L.M = a64; a64 += ex;
-      L.L = a64; a64 += ex;
-      L.Mf = a32; a32 += ex;
-      L.Lf = a32; a32 += ex;
-      tl.p[l] = L.p;
-      tl.d[l] = L.d;
-      tl.w[l] = L.w_dev;
-      if (l >= 1) {
-        const size_t tm = up16((size_t)49 * P * P);
-        L.m2l = a64; a64 += tm;
-        L.m2lt = a64; a64 += tm;
-        L.m2lf = a32; a32 += tm;
-        L.m2ltf = a32; a32 += tm;
-        tl.T[l] = L.m2l; tl.Tt[l] = L.m2lt; tl.Tf[l] = L.m2lf; tl.Ttf[l] = L.m2ltf;
-        if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2) {
-          const int kp = tc_kpad(P);
-          L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
-          if (!L.tc_B) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
-        } else {
-          L.tc_ntile = 0;
-        }
-      }
-      if (l < D) {
-        const size_t mm = up16((size_t)4 * P * h->lev[l + 1].P);
-        L.m2m = a64; a64 += mm;
-        L.l2l = a64; a64 += mm;
-        L.m2mf = a32; a32 += mm;
-        L.l2lf = a32; a32 += mm;
-        tl.A[l] = L.m2m; tl.B[l] = L.l2l; tl.Af[l] = L.m2mf; tl.Bf[l] = L.l2lf;
-      }
-    }
-    CK(k_tables(h, tl, h->astream ? h->astream : h->stream));
-  }
   if (cache && h->opt.launch == 0) {
     // top operators of the single-launch product, on the second stream once the
     // root operator (first set-up stream) and the M2M tables are there

@@ -40,6 +40,7 @@ struct Level {
   double sigma = 0;          // expansion scale k * d / sqrt(2)
   std::vector<double> w;     // w_n = sigma^|n| / |n|!, n = -p..p (index n + p)
   double* w_dev = nullptr;   // device copy of w
+  double* iw_dev = nullptr;  // 1 / w_n (device)
   int nbox = 0;              // 4^l boxes (Morton order)
   std::vector<int> hbegin, hend;   // element range of every box (sorted order)
   std::vector<int> hne;            // non-empty boxes

@@ -1349,7 +1349,7 @@ __device__ __forceinline__ void morton_centre(int box, int D, double d, double x
 // One thread per (element s, Gauss node q): the node's share of c[s][.][n] is
 // added atomically into out, which the launcher clears first.
 __global__ void p2m_coef_kernel(int E, const int* __restrict__ sleaf, int D, double d, int p,
-                                const double* __restrict__ wgt, int g, double k, double eta, double x0, double y0,
+                                const double* __restrict__ iwgt, int g, double k, double eta, double x0, double y0,
                                 const double2* __restrict__ sc, const double2* __restrict__ st,
                                 const double2* __restrict__ snu, const double* __restrict__ sh,
                                 cplx* __restrict__ out) {
@@ -1378,7 +1378,7 @@ __global__ void p2m_coef_kernel(int E, const int* __restrict__ sleaf, int D, dou
     zp = zp * z;
   }
   for (int n = -p; n <= p; ++n) {
-    const double iw = 1.0 / wgt[n + p];
+    const double iw = iwgt[n + p];
     const cplx a = (cw * 0.5 * k * iw) * (conj(nuc) * Jm[p + n] - nuc * Jm[p + n + 2]);
     const cplx b = (-eta * cw * iw) * mul_i(Jm[p + n + 1]);
     atomicAdd(&o[n + p].re, a.re);
@@ -1397,7 +1397,7 @@ __global__ void to_f32_kernel(size_t n, const cplx* __restrict__ a, cplxf* __res
 //   c[s][0][l] = (i/4) J^+_l(k(x - O)) / w_l
 //   c[s][1][l] = (i/4)(k/2)(-conj(nu) J^+_{l+1} + nu J^+_{l-1}) / w_l
 __global__ void l2p_coef_kernel(int E, const int* __restrict__ sleaf, int D, double d, int p,
-                                const double* __restrict__ wgt, double k, double x0, double y0,
+                                const double* __restrict__ iwgt, double k, double x0, double y0,
                                 const double2* __restrict__ sc, const double2* __restrict__ snu,
                                 cplx* __restrict__ out, cplxf* __restrict__ outf) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1421,7 +1421,7 @@ __global__ void l2p_coef_kernel(int E, const int* __restrict__ sleaf, int D, dou
   const cplx nuc{nu.x, nu.y};
   cplx* o = out + (size_t)s * 2 * P;
   for (int l = -p; l <= p; ++l) {
-    const double iw = 1.0 / wgt[l + p];
+    const double iw = iwgt[l + p];
     o[l + p] = mul_i((0.25 * iw) * Jp[p + 1 + l]);
     o[P + l + p] = mul_i((0.125 * k * iw) * (nuc * Jp[p + l] - conj(nuc) * Jp[p + l + 2]));
   }
@@ -1866,14 +1866,14 @@ cudaError_t k_build_fmm_caches(pfmbem* h) {
   if (e != cudaSuccess) return e;
   prof_begin(h, PH_SETUP);
   p2m_coef_kernel<<<(h->E * h->g_far + 127) / 128, 128, 0, h->stream>>>(
-      h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.w_dev, h->g_far, h->k, h->eta, h->x0, h->y0, h->s_c, h->s_t,
+      h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.iw_dev, h->g_far, h->k, h->eta, h->x0, h->y0, h->s_c, h->s_t,
       h->s_nu, h->s_h, h->p2m_c);
   prof_end(h, PH_SETUP);
   prof_begin(h, PH_SETUP);
   to_f32_kernel<<<std::min<size_t>((nc + 255) / 256, 4096), 256, 0, h->stream>>>(nc, h->p2m_c, h->p2m_cf);
   prof_end(h, PH_SETUP);
   prof_begin(h, PH_SETUP);
-  l2p_coef_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.w_dev, h->k,
+  l2p_coef_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.iw_dev, h->k,
                                                              h->x0, h->y0, h->s_c, h->s_nu, h->l2p_c, h->l2p_cf);
   prof_end(h, PH_SETUP);
   return cudaGetLastError();
