@@ -1245,9 +1245,13 @@ int fused_grid(int maxfiber) {
     cudaGetLastError();
     return 0;
   }
-  // three resident blocks per SM at most: more blocks add barrier traffic and
-  // the stages have no more parallel work than that at these sizes
-  return nsm * std::min(per, 3);
+  // resident blocks per SM: three for the FP64 product, whose stages are bound
+  // by the FP64 pipes of all sub-partitions; two for the FP32 product, whose
+  // stages are short and pay less for a barrier over fewer blocks
+  // (PFMBEM_FUSED_BLOCKS_PER_SM overrides, for measurement)
+  static const char* bps = std::getenv("PFMBEM_FUSED_BLOCKS_PER_SM");
+  const int cap = bps ? std::max(1, std::atoi(bps)) : (sizeof(C) == sizeof(cplx) ? 3 : 2);
+  return nsm * std::min(per, cap);
 }
 
 }  // namespace
