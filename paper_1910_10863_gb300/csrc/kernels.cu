@@ -1393,7 +1393,7 @@ __global__ void to_f32_kernel(size_t n, const cplx* __restrict__ a, cplxf* __res
     b[i] = to_f(a[i]);
 }
 
-// L2P coefficients of target s:
+// L2P coefficients of target s (stored coefficient-major: [2][P][E]):
 //   c[s][0][l] = (i/4) J^+_l(k(x - O)) / w_l
 //   c[s][1][l] = (i/4)(k/2)(-conj(nu) J^+_{l+1} + nu J^+_{l-1}) / w_l
 __global__ void l2p_coef_kernel(int E, const int* __restrict__ sleaf, int D, double d, int p,
@@ -1419,14 +1419,19 @@ __global__ void l2p_coef_kernel(int E, const int* __restrict__ sleaf, int D, dou
     zp = zp * z;
   }
   const cplx nuc{nu.x, nu.y};
-  cplx* o = out + (size_t)s * 2 * P;
+  // coefficient-major: entry (q, l) of element s at (q P + l) E + s
   for (int l = -p; l <= p; ++l) {
     const double iw = iwgt[l + p];
-    o[l + p] = mul_i((0.25 * iw) * Jp[p + 1 + l]);
-    o[P + l + p] = mul_i((0.125 * k * iw) * (nuc * Jp[p + l] - conj(nuc) * Jp[p + l + 2]));
+    const cplx v = mul_i((0.25 * iw) * Jp[p + 1 + l]);
+    const cplx dv = mul_i((0.125 * k * iw) * (nuc * Jp[p + l] - conj(nuc) * Jp[p + l + 2]));
+    const size_t i0 = (size_t)(l + p) * E + s, i1 = (size_t)(P + l + p) * E + s;
+    out[i0] = v;
+    out[i1] = dv;
+    if (outf) {
+      outf[i0] = to_f(v);
+      outf[i1] = to_f(dv);
+    }
   }
-  if (outf)
-    for (int i = 0; i < 2 * P; ++i) outf[(size_t)s * 2 * P + i] = to_f(o[i]);
 }
 
 // ------------------------------------------------ precision-generic matvec pieces
@@ -1592,18 +1597,19 @@ __global__ void m2l_offset_t_kernel(int P, const int* __restrict__ chunk_off, co
 // U'_s = sum_l c[s][0][l] L_l, dU'_s = sum_l c[s][1][l] L_l; one warp per target.
 template <class C>
 __global__ void l2p_apply_t_kernel(const int* __restrict__ ne, const int* __restrict__ bb,
-                                   const int* __restrict__ be, int P, const C* __restrict__ coef,
+                                   const int* __restrict__ be, int P, int E, const C* __restrict__ coef,
                                    const C* __restrict__ L, C* __restrict__ U) {
   const int box = ne[blockIdx.x];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const C* Lb = L + (size_t)box * P;
   for (int s = bb[box] + warp; s < be[box]; s += nw) {
-    const C* cs = coef + (size_t)s * 2 * P;
+    // coefficient-major cache: entry (q, l) of element s at (q P + l) E + s
+    const C* cs = coef + s;
     C u{0, 0}, du{0, 0};
     for (int l = lane; l < P; l += 32) {
       const C Ll = Lb[l];
-      u += cs[l] * Ll;
-      du += cs[P + l] * Ll;
+      u += cs[(size_t)l * E] * Ll;
+      du += cs[(size_t)(P + l) * E] * Ll;
     }
     for (int o = 16; o > 0; o >>= 1) {
       u.re += __shfl_down_sync(0xffffffffu, u.re, o);
@@ -1845,7 +1851,8 @@ static cudaError_t matvec_cached(pfmbem* h, const cplx* x, cplx* y, const Ops<C>
     prof_end(h, PH_LOCAL + po);
   }
   prof_begin(h, PH_L2P + po);
-  l2p_apply_t_kernel<C><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P, o.l2p, o.L[D], o.U);
+  l2p_apply_t_kernel<C><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P, h->E, o.l2p, o.L[D],
+                                                  o.U);
   prof_end(h, PH_L2P + po);
   prof_begin(h, PH_NEAR + po);
   near_apply_t_kernel<C><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,

@@ -82,7 +82,7 @@ struct FusedArgs {
   const C* m2m31;                    // [n < P_1][u < 16 P_3], T_1 T_2
   const C* root1;                    // [q][n < P_1][u < 4 P_1], L2L_q R T_0: L(1) from the level-1 multipoles
   const C* p2m;                      // [E][2][P_D]
-  const C* l2p;                      // [E][2][P_D]
+  const C* l2p;                      // [2][P_D][E], coefficient-major
   const int64_t* nc_base;
   const int* nc_sbase;
   const int* nc_src;
@@ -105,6 +105,7 @@ struct FusedArgs {
   int* err;
   unsigned long long* stamp;         // optional stage end times (ns), written by block 0
   const int* done;                   // optional: the product is skipped when *done != 0
+  int tws_off;                       // shared-memory offset (in C) of the twiddle copy of the fiber part
 };
 
 __device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k) {
@@ -547,10 +548,15 @@ template <class C>
 __global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const int64_t* __restrict__ fh_base,
                                      const C* __restrict__ pc, const C* __restrict__ tw,
                                      const int64_t* __restrict__ pr_base, const C* __restrict__ pr,
-                                     const cplx* __restrict__ x, cplx* __restrict__ y, const int* done) {
+                                     const cplx* __restrict__ x, cplx* __restrict__ y, const int* done,
+                                     int tws_off) {
   if (done && *(volatile const int*)done != 0) return;
   extern __shared__ unsigned char smraw[];
-  precond_fiber<C>(blockIdx.x, foff, fh_base, pc, tw, pr_base, pr, x, y, reinterpret_cast<C*>(smraw));
+  C* xs = reinterpret_cast<C*>(smraw);
+  C* tws = xs + tws_off;                          // twiddles in shared memory
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) tws[i] = tw[i];
+  __syncthreads();
+  precond_fiber<C>(blockIdx.x, foff, fh_base, pc, tws, pr_base, pr, x, y, xs);
 }
 
 // ------------------------------------------------------------ device-side GMRES step
@@ -587,6 +593,7 @@ struct ArnArgs {
   const void* tw;
   const int64_t* pr_base;            // circulant inverse row pairs (the other regular polygons)
   const void* pr;
+  int tws_off;                       // shared-memory offset (in C) of the twiddle copy
 };
 
 constexpr int ARN_MAXC = 256;        // columns of the basis the kernel can hold (restart length <= 250)
@@ -660,12 +667,17 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
   const double inv = hn > 0 ? 1.0 / hn : 0.0;
   cplx* vn = a.V + (size_t)(a.j + 1) * a.n;
   if (a.Zn) {
+    C* xs = reinterpret_cast<C*>(smraw);
+    C* tws = xs + a.tws_off;                        // twiddles in shared memory
+    if (b < a.M) {
+      for (int i = threadIdx.x; i < 512; i += FB) tws[i] = static_cast<const C*>(a.tw)[i];
+    }
     for (int fb = b; fb < a.M; fb += G) {
       __syncthreads();
       for (int t = 2 * a.foff[fb] + threadIdx.x; t < 2 * a.foff[fb + 1]; t += FB) vn[t] = inv * a.w[t];
       __syncthreads();
-      precond_fiber<C>(fb, a.foff, a.fh_base, static_cast<const C*>(a.pc), static_cast<const C*>(a.tw), a.pr_base,
-                       static_cast<const C*>(a.pr), vn, a.Zn, reinterpret_cast<C*>(smraw));
+      precond_fiber<C>(fb, a.foff, a.fh_base, static_cast<const C*>(a.pc), tws, a.pr_base,
+                       static_cast<const C*>(a.pr), vn, a.Zn, xs);
     }
   } else {
     for (int t = t0 + threadIdx.x; t < t1; t += FB) vn[t] = inv * a.w[t];
@@ -772,6 +784,11 @@ __device__ __forceinline__ int warp_first(int b, int w, int nb) {
 template <class C>
 __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int warp, int lane) {
   using R = decltype(C{}.re);
+  // the twiddle table in shared memory: the FFT passes then wait on no global load
+  C* tws = xs + a.tws_off;
+  if (b0 < a.nfft) {
+    for (int i = threadIdx.x; i < 512; i += FB) tws[i] = a.tw[i];
+  }
   for (int b = b0; b < a.nfft; b += nb) {
     const int fb = a.fft_fib[b];
     const int f0 = a.foff[fb], N = a.foff[fb + 1] - f0, lg = __ffs(N) - 1;
@@ -780,7 +797,7 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
       const int q = t >> lg, f = t & (N - 1);
       xs[t] = from_d<C>(a.x[2 * (f0 + f) + q]);
     }
-    block_fft(xs, 2, lg, -1, a.tw);
+    block_fft(xs, 2, lg, -1, tws);
     const C* Bh = a.fh_val + 4 * a.fh_base[fb];
     for (int k = threadIdx.x; k < N; k += FB) {
       const C x0 = xs[k], x1 = xs[N + k];
@@ -788,7 +805,7 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
       xs[k] = bk[0] * x0 + bk[1] * x1;
       xs[N + k] = bk[2] * x0 + bk[3] * x1;
     }
-    block_fft(xs, 2, lg, +1, a.tw);
+    block_fft(xs, 2, lg, +1, tws);
     const R inv = (R)1 / (R)N;
     for (int t = threadIdx.x; t < 2 * N; t += FB) {
       const int rr = t >> lg, e = f0 + (t & (N - 1));
@@ -1087,30 +1104,33 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   }
 
   // ------------------------------------------------------------ E: L2P + near field, combination of eq. 9
+  // one lane per element (32 consecutive sorted elements per warp item): the
+  // coefficients lie coefficient-major, so the lanes' loads are contiguous, and
+  // no lane sums need a reduction
   {
     const int PD = a.P[D];
     const C c2 = from_d<C>(a.c2);
-    for (int s = wfirst; s < a.E; s += wstride) {
+    const int nit = (a.E + 31) >> 5;
+    for (int it = wfirst; it < nit; it += wstride) {
+      const int s = (it << 5) + lane;
+      if (s >= a.E) continue;
       const int box = a.ne[D][a.s_li[s]];
       const C* Lb = a.L[D] + (size_t)box * PD;
-      const C* cs = a.l2p + (size_t)s * 2 * PD;
+      const C* cs = a.l2p + s;
       C uf{0, 0}, df{0, 0};
-      for (int t = lane; t < PD; t += 32) {
+#pragma unroll 4
+      for (int t = 0; t < PD; ++t) {
         const C Lt = ldcg(Lb + t);
-        uf += cs[t] * Lt;
-        df += cs[PD + t] * Lt;
+        uf += cs[(size_t)t * a.E] * Lt;
+        df += cs[(size_t)(PD + t) * a.E] * Lt;
       }
-      uf = wsum(uf);
-      df = wsum(df);
-      if (lane == 0) {
-        // back to the element's true position: times alpha^{m0} = conj(alpha^{-m0})
-        const int e = a.perm[s];
-        const C po = from_d<C>(conj(a.ph[s]));
-        const C u = po * (uf + ldcg(a.Un + 2 * s));
-        const C du = c2 * (po * (df + ldcg(a.Un + 2 * s + 1)));
-        a.y[2 * e] = ldcg(a.y + 2 * e) + to_d(u);
-        a.y[2 * e + 1] = ldcg(a.y + 2 * e + 1) + to_d(du);
-      }
+      // back to the element's true position: times alpha^{m0} = conj(alpha^{-m0})
+      const int e = a.perm[s];
+      const C po = from_d<C>(conj(a.ph[s]));
+      const C u = po * (uf + ldcg(a.Un + 2 * s));
+      const C du = c2 * (po * (df + ldcg(a.Un + 2 * s + 1)));
+      a.y[2 * e] = ldcg(a.y + 2 * e) + to_d(u);
+      a.y[2 * e + 1] = ldcg(a.y + 2 * e + 1) + to_d(du);
     }
   }
   __syncthreads();
@@ -1120,7 +1140,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
 template <class C>
 size_t fused_smem(int maxfiber) {
   const size_t a = (size_t)TSIZE + (size_t)FW * PF_NCOEF;   // stages B, D
-  const size_t f = 2 * (size_t)maxfiber;                    // fiber part of stage A
+  const size_t f = 2 * (size_t)maxfiber + 512;              // fiber part of stage A, with its twiddles
   return sizeof(C) * std::max(a, f);
 }
 
@@ -1128,6 +1148,7 @@ template <class C>
 cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int* done) {
   FusedArgs<C> a{};
   a.done = done;
+  a.tws_off = 2 * h->max_fiber;
   a.E = h->E;
   a.D = h->D;
   a.perm = h->s_perm;
@@ -1296,7 +1317,7 @@ cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
     int dev = 0, nsm = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const size_t smem = 2 * (size_t)h->max_fiber * sizeof(cplx);
+    const size_t smem = (2 * (size_t)h->max_fiber + 512) * sizeof(cplx);
     int per32 = 0;
     if (smem > 48 * 1024) {
       cudaFuncSetAttribute(arnoldi_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1358,18 +1379,20 @@ cudaError_t k_precond_rows(pfmbem* h) {
 
 cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done) {
   const bool f32 = precision == PFMBEM_MIXED;
-  const size_t smem = 2 * (size_t)h->max_fiber * (f32 ? sizeof(cplxf) : sizeof(cplx));
+  const size_t smem = (2 * (size_t)h->max_fiber + 512) * (f32 ? sizeof(cplxf) : sizeof(cplx));
   prof_begin(h, PH_BLAS);
   if (f32) {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(precond_apply_kernel<cplxf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     precond_apply_kernel<cplxf><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_valf, h->twf,
-                                                                h->pr_base, h->pr_valf, x, y, done);
+                                                                h->pr_base, h->pr_valf, x, y, done,
+                                                                2 * h->max_fiber);
   } else {
     if (smem > 48 * 1024)
       cudaFuncSetAttribute(precond_apply_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     precond_apply_kernel<cplx><<<h->M, 256, smem, h->stream>>>(h->M, h->fib_off, h->fh_base, h->pc_val, h->tw,
-                                                               h->pr_base, h->pr_val, x, y, done);
+                                                               h->pr_base, h->pr_val, x, y, done,
+                                                               2 * h->max_fiber);
   }
   prof_end(h, PH_BLAS);
   return cudaGetLastError();
@@ -1391,6 +1414,7 @@ cudaError_t k_arnoldi_step(pfmbem* h, int j, int precision) {
     a.tw = f32 ? (const void*)h->twf : (const void*)h->tw;
     a.pr_base = h->pr_base;
     a.pr = f32 ? (const void*)h->pr_valf : (const void*)h->pr_val;
+    a.tws_off = 2 * h->max_fiber;
   }
   a.n = g.n;
   a.m = g.m;
@@ -1407,7 +1431,7 @@ cudaError_t k_arnoldi_step(pfmbem* h, int j, int precision) {
   a.bar = h->arn_bar;
   a.err = h->fz_err;
   void* args[] = {&a};
-  const size_t smem = a.Zn ? 2 * (size_t)h->max_fiber * (f32 ? sizeof(cplxf) : sizeof(cplx)) : 0;
+  const size_t smem = a.Zn ? (2 * (size_t)h->max_fiber + 512) * (f32 ? sizeof(cplxf) : sizeof(cplx)) : 0;
   const void* fn = f32 ? (const void*)arnoldi_kernel<cplxf> : (const void*)arnoldi_kernel<cplx>;
   if (smem > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
