@@ -49,6 +49,12 @@ PF_HD cplxf mul_i(cplxf a) { return cplxf{-a.im, a.re}; }
 PF_HD cplxf to_f(cplx a) { return cplxf{(float)a.re, (float)a.im}; }
 PF_HD cplx to_d(cplxf a) { return cplx{(double)a.re, (double)a.im}; }
 PF_HD cplx to_d(cplx a) { return a; }
+// The FP32 pair (hi, lo) of an FP64 complex value: hi = fl32(a), lo = fl32(a - hi);
+// hi + lo carries about 48 bits of a.
+PF_HD cplxf split_lo(cplx a) {
+  const float hr = (float)a.re, hi = (float)a.im;
+  return cplxf{(float)(a.re - (double)hr), (float)(a.im - (double)hi)};
+}
 template <class C> PF_HD C from_d(cplx a);
 template <> PF_HD cplx from_d<cplx>(cplx a) { return a; }
 template <> PF_HD cplxf from_d<cplxf>(cplx a) { return to_f(a); }

@@ -461,7 +461,9 @@ static pfmbem_status build_pair_tables(pfmbem* h, const double* nodes, const std
   if ((st = upload(h, &h->pl_tab, plt)) != PFMBEM_OK) return st;
   h->tab_val = dalloc<cplx>(h, (size_t)4 * h->tab_entries);
   h->tab_valf = dalloc<cplxf>(h, (size_t)4 * h->tab_entries);
-  if (!h->tab_val || !h->tab_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber-pair tables)");
+  h->tab_vall = dalloc<cplxf>(h, (size_t)4 * h->tab_entries);
+  if (!h->tab_val || !h->tab_valf || !h->tab_vall)
+    return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber-pair tables)");
   return PFMBEM_OK;
 }
 
@@ -1100,7 +1102,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       h->kt_val = dalloc<cplx>(h, (size_t)4 * kacc);
       h->kt_sval = dalloc<cplx>(h, (size_t)4 * kacc);
       h->kt_svalf = dalloc<cplxf>(h, (size_t)4 * kacc);
-      if (!h->kt_sval || !h->kt_svalf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
+      h->kt_svall = dalloc<cplxf>(h, (size_t)4 * kacc);
+      if (!h->kt_sval || !h->kt_svalf || !h->kt_svall)
+        return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
       if (!h->kt_val) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber k tables)");
       h->nchunk = (int)chunks.size() / 3;
       // queue of the near pairs integrated directly: every block in the worst case
@@ -1110,6 +1114,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if (!h->nq || !h->nq_len) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near queue)");
       h->nc_val = dalloc<cplx>(h, (size_t)(4 * h->nc_blocks));
       h->nc_valf = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
+      h->nc_vall = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
+      h->dens_dd = dalloc<cplxf>(h, (size_t)4 * E);
+      if (!h->nc_vall || !h->dens_dd) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near-field caches)");
       h->fb_val = dalloc<cplx>(h, (size_t)acc);
       h->fb_valf = dalloc<cplxf>(h, (size_t)acc);
       h->stat_dev = dalloc<unsigned long long>(h, 4);

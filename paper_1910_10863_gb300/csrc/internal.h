@@ -184,6 +184,7 @@ struct pfmbem {
   int* nc_img = nullptr;         // image m per list entry
   cplx* nc_val = nullptr;        // [blocks][4]
   cplxf* nc_valf = nullptr;
+  cplxf* nc_vall = nullptr;      // lo parts: nc_val = nc_valf + nc_vall to ~48 bits (double-float)
   int64_t nc_blocks = 0;
   int nc_maxns = 0;              // longest source list of a leaf
   int leaf_maxn = 0;             // most elements in a leaf
@@ -204,6 +205,7 @@ struct pfmbem {
   int* tab_nb = nullptr;         // [ntab] elements of the source fiber
   cplx* tab_val = nullptr;       // as near-field blocks: (i/4) D, (eta/4) S, (i/4) T, (eta/4) K
   cplxf* tab_valf = nullptr;
+  cplxf* tab_vall = nullptr;
   unsigned long long* nq = nullptr;   // near pairs left to integrate directly (leaf, row, column)
   unsigned* nq_len = nullptr;
   unsigned nq_cap = 0;
@@ -217,6 +219,8 @@ struct pfmbem {
   cplx* kt_val = nullptr;        // [sum N over regular fibers][4]: S, D, K, T at k of (f0, f0 + dl)
   cplx* kt_sval = nullptr;       // the same as near-field blocks: (i/4) D, (eta/4) S, (i/4) T, (eta/4) K
   cplxf* kt_svalf = nullptr;
+  cplxf* kt_svall = nullptr;
+  cplxf* dens_dd = nullptr;      // [2][2E] hi and lo parts of the sorted FP64 densities
   int nchunk = 0;
   cplx* fb_val = nullptr;
   cplxf* fb_valf = nullptr;

@@ -570,13 +570,15 @@ __device__ __forceinline__ void pair4_f64(double kap, double2 x, double2 nx, dou
 // A near-field block from S, D, K, T (without i/4) at the matrix wavenumber:
 // (i/4) {D, -i eta S, T, -i eta K} = {(i/4) D, (eta/4) S, (i/4) T, (eta/4) K},
 // the form in which the tables keep them (FP64 and FP32).
-__device__ __forceinline__ void near_block_form(double eta, cplx S, cplx D, cplx K, cplx T, cplx* o, cplxf* of) {
+__device__ __forceinline__ void near_block_form(double eta, cplx S, cplx D, cplx K, cplx T, cplx* o, cplxf* of,
+                                                cplxf* ol) {
   const double e4 = 0.25 * eta;
   const cplx b[4] = {cplx{-0.25 * D.im, 0.25 * D.re}, cplx{e4 * S.re, e4 * S.im}, cplx{-0.25 * T.im, 0.25 * T.re},
                      cplx{e4 * K.re, e4 * K.im}};
   for (int q = 0; q < 4; ++q) {
     o[q] = b[q];
     of[q] = cplxf{(float)b[q].re, (float)b[q].im};
+    ol[q] = split_lo(b[q]);
   }
 }
 
@@ -889,7 +891,7 @@ __global__ void pair_table_kernel(int ntab, const int* __restrict__ tA, const in
                                   const int64_t* __restrict__ tstart, const int* __restrict__ foff, double k,
                                   double H, const double2* __restrict__ oc, const double2* __restrict__ ot,
                                   const double2* __restrict__ onu, const double* __restrict__ oh, double eta,
-                                  cplx* __restrict__ tval, cplxf* __restrict__ tvalf,
+                                  cplx* __restrict__ tval, cplxf* __restrict__ tvalf, cplxf* __restrict__ tvall,
                                   unsigned long long* __restrict__ stat) {
   const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned long long np = 0, nq = 0;
@@ -913,7 +915,8 @@ __global__ void pair_table_kernel(int ntab, const int* __restrict__ tA, const in
     const int g = gl_order(q, 0);
     cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
     pair4_f64(k, x, nx, c, ot[f], onu[f], hh, g, S, Dv, K, T);
-    near_block_form(eta, S, Dv, K, T, tval + 4 * (tbase[t] + local), tvalf + 4 * (tbase[t] + local));
+    near_block_form(eta, S, Dv, K, T, tval + 4 * (tbase[t] + local), tvalf + 4 * (tbase[t] + local),
+                    tvall + 4 * (tbase[t] + local));
     np = 1;
     nq = g;
   }
@@ -955,13 +958,15 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
                                   const int* __restrict__ perm, const int* __restrict__ ofib,
                                   const int* __restrict__ foff, const int* __restrict__ sm0,
                                   const int64_t* __restrict__ kbase, const cplx* __restrict__ kval,
-                                  const cplxf* __restrict__ kvalf, const int* __restrict__ pl_ptr,
-                                  const int* __restrict__ pl_fib, const int* __restrict__ pl_img,
-                                  const int* __restrict__ pl_tab, const int64_t* __restrict__ tab_base,
-                                  const int* __restrict__ tab_nb, const cplx* __restrict__ tab_val,
-                                  const cplxf* __restrict__ tab_valf, cplx* __restrict__ val,
-                                  cplxf* __restrict__ valf, unsigned long long* __restrict__ queue,
-                                  unsigned* __restrict__ qlen, unsigned qcap) {
+                                  const cplxf* __restrict__ kvalf, const cplxf* __restrict__ kvall,
+                                  const int* __restrict__ pl_ptr, const int* __restrict__ pl_fib,
+                                  const int* __restrict__ pl_img, const int* __restrict__ pl_tab,
+                                  const int64_t* __restrict__ tab_base, const int* __restrict__ tab_nb,
+                                  const cplx* __restrict__ tab_val, const cplxf* __restrict__ tab_valf,
+                                  const cplxf* __restrict__ tab_vall, cplx* __restrict__ val,
+                                  cplxf* __restrict__ valf, cplxf* __restrict__ vall,
+                                  unsigned long long* __restrict__ queue, unsigned* __restrict__ qlen,
+                                  unsigned qcap) {
   extern __shared__ int nbs[];
   const int li = blockIdx.x;
   const int box = ne[li];
@@ -1029,6 +1034,7 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
     const int r = t_run[t];
     cplx* row = val + base[li] + (int64_t)t * ns * 4;
     cplxf* rowf = valf ? valf + base[li] + (int64_t)t * ns * 4 : nullptr;
+    cplxf* rowl = vall + base[li] + (int64_t)t * ns * 4;
     // four lanes per source j, one complex value each, so that a warp writes
     // 8 whole blocks (512 contiguous bytes in FP64) per store
     const int q = lane & 3;
@@ -1037,6 +1043,7 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
       if (s_f[j] == s && m == 0) {
         row[4 * j + q] = cplx{0, 0};
         if (rowf) rowf[4 * j + q] = cplxf{0.f, 0.f};
+        rowl[4 * j + q] = cplxf{0.f, 0.f};
         continue;
       }
       const int ef = s_ef[j], ff = s_ff[j];
@@ -1044,6 +1051,7 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
       int64_t at;
       const cplx* tv;
       const cplxf* tvf;
+      const cplxf* tvl;
       if (tab == -2) {
         // same fiber and, in true coordinates, the same image: a rotation of the k table
         int dl = ef - es;
@@ -1051,11 +1059,13 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
         at = 4 * (kb + dl);
         tv = kval;
         tvf = kvalf;
+        tvl = kvall;
       } else if (tab >= 0) {
         // a translated copy of a fiber pair whose integrals are tabulated
         at = 4 * (tab_base[tab] + (int64_t)(es - fo) * tab_nb[tab] + (ef - foff[ff]));
         tv = tab_val;
         tvf = tab_valf;
+        tvl = tab_vall;
       } else {
         if (q == 0) {
           const unsigned at2 = atomicAdd(qlen, 1u);
@@ -1068,10 +1078,12 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
       if (m == 0) {
         row[4 * j + q] = tv[at + q];
         if (rowf) rowf[4 * j + q] = tvf[at + q];
+        rowl[4 * j + q] = tvl[at + q];
       } else {
         const cplx b = ipow_phase(alpha, m) * tv[at + q];
         row[4 * j + q] = b;
         if (rowf) rowf[4 * j + q] = cplxf{(float)b.re, (float)b.im};
+        rowl[4 * j + q] = split_lo(b);
       }
     }
   }
@@ -1086,7 +1098,7 @@ __global__ void near_direct_kernel(const unsigned long long* __restrict__ queue,
                                    double H, cplx alpha, const double2* __restrict__ sc,
                                    const double2* __restrict__ st, const double2* __restrict__ snu,
                                    const double* __restrict__ sh, cplx* __restrict__ val, cplxf* __restrict__ valf,
-                                   unsigned long long* __restrict__ stat) {
+                                   cplxf* __restrict__ vall, unsigned long long* __restrict__ stat) {
   const unsigned n = min(*qlen, qcap);
   unsigned long long npair = 0, nquad = 0;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -1111,6 +1123,7 @@ __global__ void near_direct_kernel(const unsigned long long* __restrict__ queue,
     for (int q2 = 0; q2 < 4; ++q2) {
       val[o + q2] = b[q2];
       if (valf) valf[o + q2] = cplxf{(float)b[q2].re, (float)b[q2].im};
+      vall[o + q2] = split_lo(b[q2]);
     }
   }
   if (stat) {
@@ -1154,7 +1167,7 @@ __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __re
                                    const double2* __restrict__ ot, const double2* __restrict__ onu,
                                    const double* __restrict__ oh, const cplx* __restrict__ self4,
                                    const int64_t* __restrict__ kbase, cplx* __restrict__ kval,
-                                   cplx* __restrict__ ksval, cplxf* __restrict__ ksvalf,
+                                   cplx* __restrict__ ksval, cplxf* __restrict__ ksvalf, cplxf* __restrict__ ksvall,
                                    cplx* __restrict__ val, cplxf* __restrict__ valf,
                                    unsigned long long* __restrict__ stat) {
   const int e = rows[blockIdx.x];
@@ -1193,7 +1206,7 @@ __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __re
       tv[1] = Dv;
       tv[2] = K;
       tv[3] = T;
-      near_block_form(eta, S, Dv, K, T, ksval + 4 * (kb + fl), ksvalf + 4 * (kb + fl));
+      near_block_form(eta, S, Dv, K, T, ksval + 4 * (kb + fl), ksvalf + 4 * (kb + fl), ksvall + 4 * (kb + fl));
     } else {
       const int64_t r0 = fbase[fb] + (int64_t)(2 * el) * (2 * N), r1 = r0 + 2 * N;
       const cplx c2r = rho * c2;
@@ -1297,13 +1310,14 @@ cudaError_t k_build_caches(pfmbem* h) {
   prof_begin(h, PH_BUILD);
   fiber_build_kernel<<<dim3(h->nfb_rows, (h->max_fiber + 128 / FB_SPLIT - 1) / (128 / FB_SPLIT), 2), 128, 0, st>>>(
       h->fb_rows, h->o_fiber, h->fib_off, h->fb_base, h->k, h->k1, h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu,
-      h->o_h, h->self4, h->kt_base, h->kt_val, h->kt_sval, h->kt_svalf, h->fb_val, h->fb_valf, h->stat_dev);
+      h->o_h, h->self4, h->kt_base, h->kt_val, h->kt_sval, h->kt_svalf, h->kt_svall, h->fb_val, h->fb_valf,
+      h->stat_dev);
   prof_end(h, PH_BUILD);
   if (h->ntab > 0) {
     prof_begin(h, PH_BUILD);
     pair_table_kernel<<<(unsigned)((h->tab_entries + 255) / 256), 256, 0, st>>>(
         h->ntab, h->tab_A, h->tab_B, h->tab_m, h->tab_start, h->tab_start, h->fib_off, h->k, h->H, h->o_c, h->o_t,
-        h->o_nu, h->o_h, h->eta, h->tab_val, h->tab_valf, h->stat_dev);
+        h->o_nu, h->o_h, h->eta, h->tab_val, h->tab_valf, h->tab_vall, h->stat_dev);
     prof_end(h, PH_BUILD);
   }
   cudaMemsetAsync(h->nq_len, 0, sizeof(unsigned), st);
@@ -1319,15 +1333,17 @@ cudaError_t k_build_caches(pfmbem* h) {
     near_build_kernel<<<leaf.nne, 256, smem, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
                                                    h->nc_src, h->nc_img, h->eta, h->alpha, h->s_perm, h->o_fiber,
                                                    h->fib_off, h->s_m0, h->kt_base, h->kt_sval, h->kt_svalf,
-                                                   h->ntab > 0 ? h->pl_ptr : nullptr, h->pl_fib, h->pl_img, h->pl_tab,
-                                                   h->tab_start, h->tab_nb, h->tab_val, h->tab_valf, h->nc_val,
-                                                   h->nc_valf, h->nq, h->nq_len, h->nq_cap);
+                                                   h->kt_svall, h->ntab > 0 ? h->pl_ptr : nullptr, h->pl_fib,
+                                                   h->pl_img, h->pl_tab, h->tab_start, h->tab_nb, h->tab_val,
+                                                   h->tab_valf, h->tab_vall, h->nc_val, h->nc_valf, h->nc_vall, h->nq,
+                                                   h->nq_len, h->nq_cap);
   }
   prof_end(h, PH_BUILD);
   prof_begin(h, PH_BUILD);
   near_direct_kernel<<<1216, 128, 0, st>>>(h->nq, h->nq_len, h->nq_cap, leaf.ne, leaf.box_begin, h->nc_base,
                                            h->nc_sbase, h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c,
-                                           h->s_t, h->s_nu, h->s_h, h->nc_val, h->nc_valf, h->stat_dev);
+                                           h->s_t, h->s_nu, h->s_h, h->nc_val, h->nc_valf, h->nc_vall,
+                                           h->stat_dev);
   prof_end(h, PH_BUILD);
   return cudaGetLastError();
 }

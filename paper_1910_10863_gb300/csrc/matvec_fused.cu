@@ -106,6 +106,11 @@ struct FusedArgs {
   unsigned long long* stamp;         // optional stage end times (ns), written by block 0
   const int* done;                   // optional: the product is skipped when *done != 0
   int tws_off;                       // shared-memory offset (in C) of the twiddle copy of the fiber part
+  // FP64 product only: the near-field sums in double-float arithmetic (FP32
+  // hi + lo pairs), on the FP32 pipes, from these lo parts
+  const cplxf* nc_lo;                // lo parts of the near blocks (hi parts: the FP32 copy)
+  cplxf* dens_dd;                    // [2][2E] hi and lo parts of the sorted densities
+  const cplxf* nc_hi;
 };
 
 __device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k) {
@@ -333,11 +338,95 @@ __global__ void root1_kernel(int P0, int P1, const cplx* __restrict__ l2l0, cons
   r1f[i] = to_f(s);
 }
 
+// ------------------------------------------------------------ double-float sums
+// A value h + l held as two FP32 numbers (about 48 bits).  acc += a b with
+// a = ah + al, b = bh + bl: the product ah bh exactly as p + e (one rounding,
+// its error by a fused multiply-add), the cross terms ah bl + al bh into e, and
+// p added to acc.h by the two-sum of Knuth, whose error goes to acc.l with e.
+// Explicitly rounded intrinsics keep the compiler from contracting the steps.
+struct dflt {
+  float h, l;
+};
+
+__device__ __forceinline__ void dd_mac(dflt& acc, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  float e = __fmaf_rn(ah, bh, -p);
+  e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+  const float s = __fadd_rn(acc.h, p);
+  const float v = __fsub_rn(s, acc.h);
+  const float err = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, v)), __fsub_rn(p, v));
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(err, e));
+}
+
+// acc += a b for complex a, b given as hi and lo parts
+__device__ __forceinline__ void dd_cmac(dflt& re, dflt& im, cplxf ah, cplxf al, cplxf bh, cplxf bl) {
+  dd_mac(re, ah.re, al.re, bh.re, bl.re);
+  dd_mac(re, -ah.im, -al.im, bh.im, bl.im);
+  dd_mac(im, ah.re, al.re, bh.im, bl.im);
+  dd_mac(im, ah.im, al.im, bh.re, bl.re);
+}
+
+__device__ __forceinline__ dflt dd_add(dflt a, dflt b) {
+  const float s = __fadd_rn(a.h, b.h);
+  const float v = __fsub_rn(s, a.h);
+  const float err = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, v)), __fsub_rn(b.h, v));
+  return dflt{s, __fadd_rn(__fadd_rn(a.l, b.l), err)};
+}
+
+__device__ __forceinline__ dflt dd_wsum(dflt v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const dflt w{__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+    v = dd_add(v, w);
+  }
+  return v;
+}
+
+__device__ __forceinline__ double dd_value(dflt v) { return (double)v.h + (double)v.l; }
+
+// Near-field sum of one target (sorted element s) in double-float arithmetic:
+// the FP64 product's near field with FP32 instructions (GB300 issues FP64 at
+// 1/64 of the FP32 rate) and FP64-level accuracy.  Writes the FP64 Un of s.
+template <class C>
+__device__ __forceinline__ void near_row_dd(const FusedArgs<C>& a, int s, int lane) {
+  const int D = a.D, li = a.s_li[s];
+  const int t = s - a.bb[D][a.ne[D][li]];
+  const int j0 = a.nc_sbase[li], ns = a.nc_sbase[li + 1] - j0;
+  const int64_t r = a.nc_base[li] + (int64_t)t * ns * 4;
+  const cplxf* qh = a.nc_hi + r;
+  const cplxf* ql = a.nc_lo + r;
+  const cplxf* dh = a.dens_dd;
+  const cplxf* dl = a.dens_dd + 2 * a.E;
+  const int* src = a.nc_src + j0;
+  dflt ur{0, 0}, ui{0, 0}, dr{0, 0}, di{0, 0};
+  for (int j = lane; j < ns; j += 32) {
+    const int f = src[j];
+    const cplxf ph = ldcg(dh + 2 * f), pl = ldcg(dl + 2 * f), vh = ldcg(dh + 2 * f + 1), vl = ldcg(dl + 2 * f + 1);
+    dd_cmac(ur, ui, qh[4 * j], ql[4 * j], ph, pl);
+    dd_cmac(ur, ui, qh[4 * j + 1], ql[4 * j + 1], vh, vl);
+    dd_cmac(dr, di, qh[4 * j + 2], ql[4 * j + 2], ph, pl);
+    dd_cmac(dr, di, qh[4 * j + 3], ql[4 * j + 3], vh, vl);
+  }
+  ur = dd_wsum(ur);
+  ui = dd_wsum(ui);
+  dr = dd_wsum(dr);
+  di = dd_wsum(di);
+  if (lane == 0) {
+    reinterpret_cast<cplx*>(a.Un)[2 * s] = cplx{dd_value(ur), dd_value(ui)};
+    reinterpret_cast<cplx*>(a.Un)[2 * s + 1] = cplx{dd_value(dr), dd_value(di)};
+  }
+}
+
 // Near-field sum of one target (sorted element s) from its leaf's cached
 // [targets][sources] 2x2 blocks; lanes over the sources, two independent
 // accumulator pairs.  Writes (U'_near, dU'_near) of s.
 template <class C>
 __device__ __forceinline__ void near_row(const FusedArgs<C>& a, int s, int lane) {
+  if (a.nc_lo) {
+    near_row_dd(a, s, lane);
+    return;
+  }
   const int D = a.D, li = a.s_li[s];
   const int t = s - a.bb[D][a.ne[D][li]];
   const int j0 = a.nc_sbase[li], ns = a.nc_sbase[li + 1] - j0;
@@ -887,8 +976,16 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
           if (s < s1) {
             const int e = a.perm[s];
             const C p = from_d<C>(a.ph[s]);
-            a.dens[2 * s] = p * from_d<C>(a.x[2 * e]);
-            a.dens[2 * s + 1] = p * from_d<C>(a.x[2 * e + 1]);
+            const C d0 = p * from_d<C>(a.x[2 * e]), d1 = p * from_d<C>(a.x[2 * e + 1]);
+            a.dens[2 * s] = d0;
+            a.dens[2 * s + 1] = d1;
+            if (a.dens_dd) {
+              const cplx e0 = to_d(d0), e1 = to_d(d1);
+              a.dens_dd[2 * s] = cplxf{(float)e0.re, (float)e0.im};
+              a.dens_dd[2 * s + 1] = cplxf{(float)e1.re, (float)e1.im};
+              a.dens_dd[2 * a.E + 2 * s] = split_lo(e0);
+              a.dens_dd[2 * a.E + 2 * s + 1] = split_lo(e1);
+            }
           }
         }
         __syncwarp();
@@ -1188,6 +1285,13 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
   } else {
     a.Un = h->Un;
     a.dens = h->dens; a.root = h->root; a.rootc = h->rootc; a.p2m = h->p2m_c; a.l2p = h->l2p_c;
+    // (PFMBEM_NEAR_FP64 selects FP64 near sums instead, for measurement)
+    static const bool near64 = std::getenv("PFMBEM_NEAR_FP64") != nullptr;
+    if (h->nc_vall && h->dens_dd && !near64) {
+      a.nc_lo = h->nc_vall;
+      a.nc_hi = h->nc_valf;
+      a.dens_dd = h->dens_dd;
+    }
     a.m2m31 = h->m2m31; a.root1 = h->root1;
     a.nc_val = h->nc_val; a.fb_val = h->fb_val; a.fh_val = h->fh_val; a.tw = h->tw;
   }
