@@ -966,7 +966,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       const size_t tm = l >= 1 ? up16((size_t)49 * L.P * L.P) : 0;
       const size_t mm = l < D ? up16((size_t)4 * L.P * h->lev[l + 1].P) : 0;
       n64 += 2 * ex + 2 * tm + 2 * mm;
-      n32 += 2 * up16(ex) + 2 * up16(tm) + 2 * up16(mm);
+      n32 += 2 * up16(ex) + 3 * up16(tm) + 2 * up16(mm);
     }
     cplx* a64 = dalloc<cplx>(h, n64);
     cplxf* a32 = dalloc<cplxf>(h, n32);
@@ -989,7 +989,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         L.m2lt = a64; a64 += tm;
         L.m2lf = a32; a32 += tm;
         L.m2ltf = a32; a32 += tm;
-        tl.T[l] = L.m2l; tl.Tt[l] = L.m2lt; tl.Tf[l] = L.m2lf; tl.Ttf[l] = L.m2ltf;
+        L.m2ltl = a32; a32 += tm;
+        tl.T[l] = L.m2l; tl.Tt[l] = L.m2lt; tl.Tf[l] = L.m2lf; tl.Ttf[l] = L.m2ltf; tl.Ttl[l] = L.m2ltl;
         if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2) {
           const int kp = tc_kpad(P);
           L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);

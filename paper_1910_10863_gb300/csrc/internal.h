@@ -78,6 +78,7 @@ struct Level {
   cplx* m2l = nullptr;       // [49][P][P]: row = target coefficient, col = source coefficient
   cplx* m2lt = nullptr;      // the same operators transposed, [49][P source][P target]
   cplxf* m2ltf = nullptr;
+  cplxf* m2ltl = nullptr;    // lo parts of m2lt: m2lt = m2ltf + m2ltl to ~48 bits (double-float M2L)
   cplx* m2m = nullptr;       // children (level l+1) -> this level: [4][P][P_child]
   cplx* l2l = nullptr;       // this level -> children: [4][P_child][P]
   // FP32 copies for the mixed path
@@ -342,6 +343,7 @@ struct TableLevels {
   cplxf* Tf[PF_MAXLEVEL + 1];
   cplx* Tt[PF_MAXLEVEL + 1];
   cplxf* Ttf[PF_MAXLEVEL + 1];
+  cplxf* Ttl[PF_MAXLEVEL + 1];
   cplx* A[PF_MAXLEVEL + 1];
   cplxf* Af[PF_MAXLEVEL + 1];
   cplx* B[PF_MAXLEVEL + 1];

@@ -139,10 +139,11 @@ __global__ void m2l_tables_kernel(TableLevels tl, double k, int* __restrict__ ba
   cplxf* Tf = tl.Tf[l] + (size_t)o * P * P;
   cplx* Tt = tl.Tt[l] + (size_t)o * P * P;
   cplxf* Ttf = tl.Ttf[l] + (size_t)o * P * P;
+  cplxf* Ttl = tl.Ttl[l] + (size_t)o * P * P;
   if (abs(dx) <= 1 && abs(dy) <= 1) {
     for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
       T[t] = Tt[t] = cplx{0, 0};
-      Tf[t] = Ttf[t] = cplxf{0, 0};
+      Tf[t] = Ttf[t] = Ttl[t] = cplxf{0, 0};
     }
     return;
   }
@@ -170,6 +171,7 @@ __global__ void m2l_tables_kernel(TableLevels tl, double k, int* __restrict__ ba
     Tf[t] = to_f(v);
     Tt[(size_t)n * P + a] = v;
     Ttf[(size_t)n * P + a] = to_f(v);
+    Ttl[(size_t)n * P + a] = split_lo(v);
   }
 }
 

@@ -111,6 +111,8 @@ struct FusedArgs {
   const cplxf* nc_lo;                // lo parts of the near blocks (hi parts: the FP32 copy)
   cplxf* dens_dd;                    // [2][2E] hi and lo parts of the sorted densities
   const cplxf* nc_hi;
+  const cplxf* m2lth[PF_MAXLEVEL + 1];   // FP64 product, double-float M2L: hi and lo parts of m2lt
+  const cplxf* m2ltl[PF_MAXLEVEL + 1];
 };
 
 __device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k) {
@@ -1155,6 +1157,30 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       const int pi = i - nl2l;
       const int src = a.pr_src[l][pi], tgt = a.pr_tgt[l][pi];
       const C phs = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
+      if (a.m2ltl[l]) {
+        // the FP64 product in double-float arithmetic on the FP32 pipes: the
+        // phased source multipole split into hi and lo parts, the operator
+        // read from its hi and lo tables
+        cplxf* wh = reinterpret_cast<cplxf*>(wsm);
+        cplxf* wl = wh + PF_NCOEF;
+        __syncwarp();
+        for (int m = lane; m < P; m += 32) {
+          const cplx v = to_d(phs * ldcg(a.M[l] + (size_t)src * P + m));
+          wh[m] = cplxf{(float)v.re, (float)v.im};
+          wl[m] = split_lo(v);
+        }
+        __syncwarp();
+        const size_t ob = (size_t)a.pr_off[l][pi] * P * P;
+        const cplxf* Th = a.m2lth[l] + ob;
+        const cplxf* Tl = a.m2ltl[l] + ob;
+        for (int n = lane; n < P; n += 32) {
+          dflt re{0, 0}, im{0, 0};
+#pragma unroll 4
+          for (int m = 0; m < P; ++m) dd_cmac(re, im, Th[(size_t)m * P + n], Tl[(size_t)m * P + n], wh[m], wl[m]);
+          atomic_add(a.L[l] + (size_t)tgt * P + n, from_d<C>(cplx{dd_value(re), dd_value(im)}));
+        }
+        continue;
+      }
       const C* To = a.m2lt[l] + (size_t)a.pr_off[l][pi] * P * P;
       __syncwarp();
       for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * P + m);
@@ -1285,12 +1311,16 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
   } else {
     a.Un = h->Un;
     a.dens = h->dens; a.root = h->root; a.rootc = h->rootc; a.p2m = h->p2m_c; a.l2p = h->l2p_c;
-    // (PFMBEM_NEAR_FP64 selects FP64 near sums instead, for measurement)
+    // (PFMBEM_NEAR_FP64 selects FP64 near sums and M2L instead, for measurement)
     static const bool near64 = std::getenv("PFMBEM_NEAR_FP64") != nullptr;
     if (h->nc_vall && h->dens_dd && !near64) {
       a.nc_lo = h->nc_vall;
       a.nc_hi = h->nc_valf;
       a.dens_dd = h->dens_dd;
+      for (int l = 1; l <= h->D; ++l) {
+        a.m2lth[l] = h->lev[l].m2ltf;
+        a.m2ltl[l] = h->lev[l].m2ltl;
+      }
     }
     a.m2m31 = h->m2m31; a.root1 = h->root1;
     a.nc_val = h->nc_val; a.fb_val = h->fb_val; a.fh_val = h->fh_val; a.tw = h->tw;
