@@ -966,7 +966,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       const size_t tm = l >= 1 ? up16((size_t)49 * L.P * L.P) : 0;
       const size_t mm = l < D ? up16((size_t)4 * L.P * h->lev[l + 1].P) : 0;
       n64 += 2 * ex + 2 * tm + 2 * mm;
-      n32 += 2 * up16(ex) + 3 * up16(tm) + 2 * up16(mm);
+      n32 += 2 * up16(ex) + 3 * up16(tm) + 3 * up16(mm);
     }
     cplx* a64 = dalloc<cplx>(h, n64);
     cplxf* a32 = dalloc<cplxf>(h, n32);
@@ -1004,8 +1004,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         L.m2m = a64; a64 += mm;
         L.l2l = a64; a64 += mm;
         L.m2mf = a32; a32 += mm;
+        L.m2ml = a32; a32 += mm;
         L.l2lf = a32; a32 += mm;
-        tl.A[l] = L.m2m; tl.B[l] = L.l2l; tl.Af[l] = L.m2mf; tl.Bf[l] = L.l2lf;
+        tl.A[l] = L.m2m; tl.B[l] = L.l2l; tl.Af[l] = L.m2mf; tl.Bf[l] = L.l2lf; tl.Al[l] = L.m2ml;
       }
     }
     CK(k_tables(h, tl, h->astream ? h->astream : h->stream));
@@ -1068,6 +1069,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         h->p2m_c = dalloc<cplx>(h, nc);
         h->l2p_c = dalloc<cplx>(h, nc);
         h->p2m_cf = dalloc<cplxf>(h, nc);
+        h->p2m_cl = dalloc<cplxf>(h, nc);
+        if (!h->p2m_cl) return fail(h, PFMBEM_ENOMEM, "device allocation failed (P2M/L2P caches)");
         h->l2p_cf = dalloc<cplxf>(h, nc);
         h->densf = dalloc<cplxf>(h, (size_t)2 * E);
         h->Uf = dalloc<cplxf>(h, (size_t)2 * E);

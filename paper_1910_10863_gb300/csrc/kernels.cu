@@ -192,6 +192,7 @@ __global__ void m2m_tables_kernel(TableLevels tl, double k) {
   bessel_jy_block(k * r, p + pc, J, Y);
   cplx* A = tl.A[l] + (size_t)q * Pc * P;
   cplxf* Af = tl.Af[l] + (size_t)q * Pc * P;
+  cplxf* Al = tl.Al[l] + (size_t)q * Pc * P;
   cplx* B = tl.B[l] + (size_t)q * P * Pc;
   cplxf* Bf = tl.Bf[l] + (size_t)q * P * Pc;
   for (int t = threadIdx.x; t < P * Pc; t += blockDim.x) {
@@ -205,6 +206,7 @@ __global__ void m2m_tables_kernel(TableLevels tl, double k) {
       const cplx v{sc * Jj * cs, -sc * Jj * sn};
       A[t] = v;
       Af[t] = to_f(v);
+      Al[t] = split_lo(v);
     }
     {
       const int m = t / Pc - p, n = t % Pc - pc;     // B: [q][m + p][n + pc]
@@ -1406,9 +1408,12 @@ __global__ void p2m_coef_kernel(int E, const int* __restrict__ sleaf, int D, dou
   }
 }
 
-__global__ void to_f32_kernel(size_t n, const cplx* __restrict__ a, cplxf* __restrict__ b) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+// FP32 copy (the hi part) and, with lo, the lo part of each value.
+__global__ void to_f32_kernel(size_t n, const cplx* __restrict__ a, cplxf* __restrict__ b, cplxf* __restrict__ lo) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     b[i] = to_f(a[i]);
+    if (lo) lo[i] = split_lo(a[i]);
+  }
 }
 
 // L2P coefficients of target s (stored coefficient-major: [2][P][E]):
@@ -1895,7 +1900,8 @@ cudaError_t k_build_fmm_caches(pfmbem* h) {
       h->s_nu, h->s_h, h->p2m_c);
   prof_end(h, PH_SETUP);
   prof_begin(h, PH_SETUP);
-  to_f32_kernel<<<std::min<size_t>((nc + 255) / 256, 4096), 256, 0, h->stream>>>(nc, h->p2m_c, h->p2m_cf);
+  to_f32_kernel<<<std::min<size_t>((nc + 255) / 256, 4096), 256, 0, h->stream>>>(nc, h->p2m_c, h->p2m_cf,
+                                                                                 h->p2m_cl);
   prof_end(h, PH_SETUP);
   prof_begin(h, PH_SETUP);
   l2p_coef_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.iw_dev, h->k,

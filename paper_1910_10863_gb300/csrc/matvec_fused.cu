@@ -113,6 +113,10 @@ struct FusedArgs {
   const cplxf* nc_hi;
   const cplxf* m2lth[PF_MAXLEVEL + 1];   // FP64 product, double-float M2L: hi and lo parts of m2lt
   const cplxf* m2ltl[PF_MAXLEVEL + 1];
+  const cplxf* m2mh[PF_MAXLEVEL + 1];    // FP64 product, double-float M2M: hi and lo parts of m2m
+  const cplxf* m2ml[PF_MAXLEVEL + 1];
+  const cplxf* p2mh;                     // FP64 product, double-float P2M: hi and lo parts of p2m
+  const cplxf* p2ml;
 };
 
 __device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k) {
@@ -991,6 +995,22 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
           }
         }
         __syncwarp();
+        if (a.p2ml) {
+          // FP64 product in double-float arithmetic, from the densities' hi and
+          // lo parts just written by this warp
+          const cplxf* dh = a.dens_dd;
+          const cplxf* dl = a.dens_dd + 2 * a.E;
+          for (int n = lane; n < PD; n += 32) {
+            dflt re{0, 0}, im{0, 0};
+            for (int f = s0; f < s1; ++f) {
+              const size_t c0 = (size_t)f * 2 * PD + n, c1 = c0 + PD;
+              dd_cmac(re, im, a.p2mh[c0], a.p2ml[c0], dh[2 * f], dl[2 * f]);
+              dd_cmac(re, im, a.p2mh[c1], a.p2ml[c1], dh[2 * f + 1], dl[2 * f + 1]);
+            }
+            a.M[D][(size_t)box * PD + n] = from_d<C>(cplx{dd_value(re), dd_value(im)});
+          }
+          continue;
+        }
         for (int n0 = 0; n0 < PD; n0 += 32) {
           const int n = n0 + lane;
           if (n < PD) {
@@ -1070,7 +1090,28 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
         continue;
       }
       const int box = a.ne[l][i];
-      if (4 * Pc <= PF_NCOEF) {
+      if (a.m2ml[l] && 4 * Pc <= PF_NCOEF) {
+        // FP64 product in double-float arithmetic: the four children's
+        // multipoles split into hi and lo parts, the operator from its tables
+        cplxf* wh = reinterpret_cast<cplxf*>(wsm);
+        cplxf* wl = wh + PF_NCOEF;
+        __syncwarp();
+        for (int t = lane; t < 4 * Pc; t += 32) {
+          const int q = t / Pc, ch = 4 * box + q;
+          const cplx v = a.bb[l + 1][ch] < a.be[l + 1][ch] ? to_d(ldcg(a.M[l + 1] + (size_t)ch * Pc + (t - q * Pc)))
+                                                           : cplx{0, 0};
+          wh[t] = cplxf{(float)v.re, (float)v.im};
+          wl[t] = split_lo(v);
+        }
+        __syncwarp();
+        for (int n = lane; n < P; n += 32) {
+          dflt re{0, 0}, im{0, 0};
+#pragma unroll 4
+          for (int u = 0; u < 4 * Pc; ++u)
+            dd_cmac(re, im, a.m2mh[l][(size_t)u * P + n], a.m2ml[l][(size_t)u * P + n], wh[u], wl[u]);
+          a.M[l][(size_t)box * P + n] = from_d<C>(cplx{dd_value(re), dd_value(im)});
+        }
+      } else if (4 * Pc <= PF_NCOEF) {
         // all four children at once (an empty child contributes zeros): the
         // quadrant operators are stored one after another, so one column walk
         // over 4 Pc terms applies them all
@@ -1321,6 +1362,12 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
         a.m2lth[l] = h->lev[l].m2ltf;
         a.m2ltl[l] = h->lev[l].m2ltl;
       }
+      for (int l = 0; l < h->D; ++l) {
+        a.m2mh[l] = h->lev[l].m2mf;
+        a.m2ml[l] = h->lev[l].m2ml;
+      }
+      a.p2mh = h->p2m_cf;
+      a.p2ml = h->p2m_cl;
     }
     a.m2m31 = h->m2m31; a.root1 = h->root1;
     a.nc_val = h->nc_val; a.fb_val = h->fb_val; a.fh_val = h->fh_val; a.tw = h->tw;
