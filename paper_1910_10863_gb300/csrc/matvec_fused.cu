@@ -1035,13 +1035,14 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   stage_stamp(a.stamp, ks++);
 
   // ------------------------------------------------------------ B: M2M (+ root)
-  // the last B stage: level 2 when it also forms M(1) and L(0), else the root;
-  // the near-field rows are spread evenly over all B stages
-  const int lstop = a.top3 ? 2 : 0, nbst = D - lstop;
+  // the last B stage: level 2 when it also forms M(1), else the root
+  // the near-field rows need only the densities of stage A: they are spread
+  // evenly over all B and D stages, whose FMM work leaves most warps idle
+  const int lstop = a.top3 ? 2 : 0, nbst = D - lstop, nst = nbst + D;
   for (int l = D - 1; l >= lstop; --l) {
     const int P = a.P[l], Pc = a.P[l + 1];
     const int jst = D - 1 - l;
-    const int r0 = (int)((int64_t)a.E * jst / nbst), r1 = (int)((int64_t)a.E * (jst + 1) / nbst);
+    const int r0 = (int)((int64_t)a.E * jst / nst), r1 = (int)((int64_t)a.E * (jst + 1) / nst);
     // near the top of the tree the boxes are too few to occupy the grid: one
     // warp per output coefficient, lanes over the 4 Pc child coefficients.  The
     // root then forms L(0) = (R T_0) [M(1) of its four children] at once.
@@ -1164,8 +1165,51 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     // M2L one warp per pair (operator rows through L1/L2), or one block per
     // chunk of pairs sharing the offset (operator staged in shared memory)
     const bool wpair = a.m2l_warp || P > TSP;
-    const int nitem = nl2l + (wpair ? a.npair[l] : 0);
+    // block chunks of the staged M2L first, then the warp items
+    if (!wpair) {
+      for (int b = blockIdx.x; b < a.nch[l]; b += G) {
+        const int o = a.ch_off[l][b], pb = a.ch_beg[l][b], pe = a.ch_end[l][b];
+        const C* To = a.m2lt[l] + (size_t)o * P * P;          // [n source][l target]
+        __syncthreads();                                      // sT of the previous chunk is done
+        for (int t = threadIdx.x; t < P * P; t += FB) sT[(t % P) * P + t / P] = To[t];
+        __syncthreads();
+        // two pairs per warp pass, sharing the operator rows read from shared memory
+        for (int pi = pb + 2 * warp; pi < pe; pi += 2 * FW) {
+          const bool two = pi + 1 < pe;
+          const int srcA = a.pr_src[l][pi], tgtA = a.pr_tgt[l][pi];
+          const int srcB = two ? a.pr_src[l][pi + 1] : srcA, tgtB = two ? a.pr_tgt[l][pi + 1] : tgtA;
+          const C phA = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
+          const C phB = two ? from_d<C>(phase_m(a.alpha, a.pr_img[l][pi + 1])) : C{0, 0};
+          __syncwarp();
+          for (int m = lane; m < P; m += 32) {
+            wsm[m] = phA * ldcg(a.M[l] + (size_t)srcA * P + m);
+            wsm[P + m] = phB * ldcg(a.M[l] + (size_t)srcB * P + m);
+          }
+          __syncwarp();
+          for (int n = lane; n < P; n += 32) {
+            const C* row = sT + (size_t)n * P;
+            C rA{0, 0}, rB{0, 0};
+#pragma unroll 4
+            for (int m = 0; m < P; ++m) {
+              const C t = row[m];
+              rA += t * wsm[m];
+              rB += t * wsm[P + m];
+            }
+            atomic_add(a.L[l] + (size_t)tgtA * P + n, rA);
+            if (two) atomic_add(a.L[l] + (size_t)tgtB * P + n, rB);
+          }
+        }
+      }
+    }
+    const int nm2l = wpair ? a.npair[l] : 0;
+    const int jst = nbst + l - 1;
+    const int r0 = (int)((int64_t)a.E * jst / nst), r1 = (int)((int64_t)a.E * (jst + 1) / nst);
+    const int nitem = nl2l + nm2l + (r1 - r0);
     for (int i = wfirst; i < nitem; i += wstride) {
+      if (i >= nl2l + nm2l) {
+        near_row(a, r0 + (i - nl2l - nm2l), lane);
+        continue;
+      }
       if (i < nl2l) {
         if (top && a.top3 && l == 1) {
           // the root's part of L(1) straight from the four level-1 multipoles
@@ -1227,41 +1271,6 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * P + m);
       __syncwarp();
       for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * P + n, colmv(To + n, P, wsm, P));
-    }
-    if (!wpair) {
-      for (int b = blockIdx.x; b < a.nch[l]; b += G) {
-        const int o = a.ch_off[l][b], pb = a.ch_beg[l][b], pe = a.ch_end[l][b];
-        const C* To = a.m2lt[l] + (size_t)o * P * P;          // [n source][l target]
-        __syncthreads();                                      // sT of the previous chunk is done
-        for (int t = threadIdx.x; t < P * P; t += FB) sT[(t % P) * P + t / P] = To[t];
-        __syncthreads();
-        // two pairs per warp pass, sharing the operator rows read from shared memory
-        for (int pi = pb + 2 * warp; pi < pe; pi += 2 * FW) {
-          const bool two = pi + 1 < pe;
-          const int srcA = a.pr_src[l][pi], tgtA = a.pr_tgt[l][pi];
-          const int srcB = two ? a.pr_src[l][pi + 1] : srcA, tgtB = two ? a.pr_tgt[l][pi + 1] : tgtA;
-          const C phA = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
-          const C phB = two ? from_d<C>(phase_m(a.alpha, a.pr_img[l][pi + 1])) : C{0, 0};
-          __syncwarp();
-          for (int m = lane; m < P; m += 32) {
-            wsm[m] = phA * ldcg(a.M[l] + (size_t)srcA * P + m);
-            wsm[P + m] = phB * ldcg(a.M[l] + (size_t)srcB * P + m);
-          }
-          __syncwarp();
-          for (int n = lane; n < P; n += 32) {
-            const C* row = sT + (size_t)n * P;
-            C rA{0, 0}, rB{0, 0};
-#pragma unroll 4
-            for (int m = 0; m < P; ++m) {
-              const C t = row[m];
-              rA += t * wsm[m];
-              rB += t * wsm[P + m];
-            }
-            atomic_add(a.L[l] + (size_t)tgtA * P + n, rA);
-            if (two) atomic_add(a.L[l] + (size_t)tgtB * P + n, rB);
-          }
-        }
-      }
     }
     if (!grid_barrier(a.bar, a.err)) return;
     stage_stamp(a.stamp, ks++);
