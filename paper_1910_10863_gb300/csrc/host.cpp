@@ -104,6 +104,61 @@ void pin_release(pfmbem* h) {
   h->pin_user = false;
 }
 
+// Set-up streams and events are kept in a process-wide pool per device and
+// handed from one create to the next: creating and destroying them costs more
+// than a small create's host work.  A handle holds its streams exclusively
+// between create and destroy; destroy synchronises them before it returns them.
+struct StreamPool {
+  std::mutex mu;
+  std::vector<cudaStream_t> streams[64];
+  std::vector<cudaEvent_t> events[64];
+};
+StreamPool g_sp;
+
+cudaError_t pool_stream(int dev, cudaStream_t* s) {
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lk(g_sp.mu);
+    if (!g_sp.streams[dev].empty()) {
+      *s = g_sp.streams[dev].back();
+      g_sp.streams[dev].pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
+}
+
+cudaError_t pool_event(int dev, cudaEvent_t* e) {
+  if (dev >= 0 && dev < 64) {
+    std::lock_guard<std::mutex> lk(g_sp.mu);
+    if (!g_sp.events[dev].empty()) {
+      *e = g_sp.events[dev].back();
+      g_sp.events[dev].pop_back();
+      return cudaSuccess;
+    }
+  }
+  return cudaEventCreateWithFlags(e, cudaEventDisableTiming);
+}
+
+void pool_put(int dev, cudaStream_t s) {
+  if (!s) return;
+  if (dev < 0 || dev >= 64) {
+    cudaStreamDestroy(s);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_sp.mu);
+  g_sp.streams[dev].push_back(s);
+}
+
+void pool_put(int dev, cudaEvent_t e) {
+  if (!e) return;
+  if (dev < 0 || dev >= 64) {
+    cudaEventDestroy(e);
+    return;
+  }
+  std::lock_guard<std::mutex> lk(g_sp.mu);
+  g_sp.events[dev].push_back(e);
+}
+
 // Host-to-device copy of a table.  While a batch is open (h->ub_on) the data is
 // appended to the batch (in the page-locked arena when this create holds it)
 // and the destination pointer is set at the next flush_uploads, which makes
@@ -581,9 +636,9 @@ static void build_m2l_lists(const Level& L, int l, bool tc, M2LLists& o) {
 // launchers, allocations and profiling events of f go there.
 template <class F>
 static pfmbem_status on_aux(pfmbem* h, int i, F&& f) {
-  if (!h->aux[i]) CK(cudaStreamCreateWithFlags(&h->aux[i], cudaStreamNonBlocking));
-  if (!h->aux_ev[i]) CK(cudaEventCreateWithFlags(&h->aux_ev[i], cudaEventDisableTiming));
-  if (!h->fork_ev) CK(cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming));
+  if (!h->aux[i]) CK(pool_stream(h->dev, &h->aux[i]));
+  if (!h->aux_ev[i]) CK(pool_event(h->dev, &h->aux_ev[i]));
+  if (!h->fork_ev) CK(pool_event(h->dev, &h->fork_ev));
   CK(cudaEventRecord(h->fork_ev, h->stream));
   CK(cudaStreamWaitEvent(h->aux[i], h->fork_ev, 0));
   cudaStream_t main_stream = h->stream;
@@ -929,7 +984,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   CK(k_self_terms(h));
   mark("element arrays, self terms");
   // ---------------------------------------------------- lattice sums + root operator
-  if (!h->side_ev) CK(cudaEventCreateWithFlags(&h->side_ev, cudaEventDisableTiming));
+  if (!h->side_ev) CK(pool_event(h->dev, &h->side_ev));
   {
     // on their own stream: nothing else of the set-up waits for them until the join
     pfmbem_status st = on_aux(h, 0, [&]() -> pfmbem_status {
@@ -948,13 +1003,13 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   }
   mark("lattice sums, root");
   // the second stream starts after everything uploaded so far (level weights)
-  if (!h->pre_ev) CK(cudaEventCreateWithFlags(&h->pre_ev, cudaEventDisableTiming));
+  if (!h->pre_ev) CK(pool_event(h->dev, &h->pre_ev));
   CK(cudaEventRecord(h->pre_ev, h->stream));
   // ---------------------------------------------------- translation tables
   // One FP64 and one FP32 arena hold every level's expansions and operators
   // (sub-arrays aligned to 256 bytes); the operators are built on the device,
   // on the second stream as soon as the level weights are up.
-  if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+  if (!h->side) CK(pool_stream(h->dev, &h->side));
   CK(cudaStreamWaitEvent(h->side, h->pre_ev, 0));
   h->astream = h->side;
   {
@@ -1205,8 +1260,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       }
     }
   }
-  if (!h->side) CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
-  if (!h->side_ev) CK(cudaEventCreateWithFlags(&h->side_ev, cudaEventDisableTiming));
+  if (!h->side) CK(pool_stream(h->dev, &h->side));
+  if (!h->side_ev) CK(pool_event(h->dev, &h->side_ev));
   CK(cudaStreamWaitEvent(h->side, h->pre_ev, 0));
   h->astream = h->side;
   int64_t m2l_pairs = 0;
@@ -1858,6 +1913,7 @@ pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nod
   }
   ensure_gauss();
   ensure_pool();
+  cudaGetDevice(&h->dev);
   h->prof.on = h->opt.profile != 0;
   // host copies of the inputs
   std::vector<int> npf(M);
@@ -1894,14 +1950,14 @@ void pfmbem_destroy(pfmbem_t h) {
   else cudaDeviceSynchronize();
   pin_release(h);                  // a create that failed part-way
   pinned_small_put(h->gw.hhost);
-  if (h->side_ev) cudaEventDestroy(h->side_ev);
-  if (h->pre_ev) cudaEventDestroy(h->pre_ev);
-  if (h->side) cudaStreamDestroy(h->side);
+  pool_put(h->dev, h->side_ev);
+  pool_put(h->dev, h->pre_ev);
+  pool_put(h->dev, h->side);
   for (int i = 0; i < 2; ++i) {
-    if (h->aux_ev[i]) cudaEventDestroy(h->aux_ev[i]);
-    if (h->aux[i]) cudaStreamDestroy(h->aux[i]);
+    pool_put(h->dev, h->aux_ev[i]);
+    pool_put(h->dev, h->aux[i]);
   }
-  if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+  pool_put(h->dev, h->fork_ev);
   prof_release(h);
   delete h;
 }

@@ -135,6 +135,7 @@ struct pfmbem {
   double c2re = 0, c2im = 0;     // c2 = 2 / (i eta (1 + rho))
   pfmbem_options opt{};
   cudaStream_t stream = nullptr;
+  int dev = -1;                  // device current at create (its streams come from that device's pool)
   cudaStream_t side = nullptr;   // second stream of the set-up: host planning overlaps the cache build
   cudaEvent_t side_ev = nullptr;
   cudaEvent_t pre_ev = nullptr;    // main-stream point the second stream waits for
