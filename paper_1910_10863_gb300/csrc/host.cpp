@@ -1540,17 +1540,22 @@ static pfmbem_status gmres_cycle_device(pfmbem* h, cplx* x, double beta, double 
 // trust_estimate the solve ends as
 // soon as the Arnoldi residual estimate falls below tol/2, without recomputing
 // the true residual (inner solves of the refinement, whose outer loop computes
-// the FP64 residual anyway).
+// the FP64 residual anyway).  A caller that already holds ||b|| passes it as
+// known_bnorm (> 0), which saves a device-to-host round trip; on a zero start
+// the first residual is b itself and its norm is not recomputed either.
 static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int maxit, int precision,
                            int* iters_out, int* restarts_out, double* relres_out, bool zero_start = false,
-                           bool trust_estimate = false) {
+                           bool trust_estimate = false, double known_bnorm = 0) {
   GmresWork& g = h->gw;
   const int n = g.n, m = g.m;
   double* hn = reinterpret_cast<double*>(g.hhost);
-  CK(k_norm2(h, b, n, g.nrm));
-  CK(cudaMemcpyAsync(hn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  const double bnorm = std::sqrt(hn[0]);
+  double bnorm = known_bnorm;
+  if (!(bnorm > 0)) {
+    CK(k_norm2(h, b, n, g.nrm));
+    CK(cudaMemcpyAsync(hn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    bnorm = std::sqrt(hn[0]);
+  }
   if (bnorm == 0) {
     CK(cudaMemsetAsync(x, 0, sizeof(cplx) * n, h->stream));
     *iters_out = 0;
@@ -1563,16 +1568,17 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
   std::vector<std::complex<double>> Hm((size_t)(m + 1) * m), cs(m), sn(m), gvec(m + 1);
   while (!done) {
     // r = b - A x (x = 0 on a zero start)
+    double beta = bnorm;
     if (zero_start && restarts == 0) {
       CK(cudaMemcpyAsync(g.r, b, sizeof(cplx) * n, cudaMemcpyDeviceToDevice, h->stream));
     } else {
       CK(k_matvec(h, x, g.w, precision));
       CK(k_sub(h, b, g.w, g.r, n));
+      CK(k_norm2(h, g.r, n, g.nrm));
+      CK(cudaMemcpyAsync(hn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      beta = std::sqrt(hn[0]);
     }
-    CK(k_norm2(h, g.r, n, g.nrm));
-    CK(cudaMemcpyAsync(hn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    double beta = std::sqrt(hn[0]);
     relres = beta / bnorm;
     if (!std::isfinite(relres)) return fail(h, PFMBEM_ENUMERIC, "non-finite residual");
     if (relres <= tol || iters >= maxit) break;
@@ -2086,10 +2092,12 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
         CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
         CK(k_sub(h, g.b, g.w, g.d, (int)n));
       }
-      double rn = 0;
-      CK(k_norm2(h, g.d, (int)n, g.nrm));
-      CK(cudaMemcpyAsync(&rn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-      CK(cudaStreamSynchronize(h->stream));
+      double rn = bn * bn;             // d = B at a zero start
+      if (refinements > 0 || use_guess) {
+        CK(k_norm2(h, g.d, (int)n, g.nrm));
+        CK(cudaMemcpyAsync(&rn, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+      }
       relres = bn > 0 ? std::sqrt(rn) / bn : 0.0;
       if (!std::isfinite(relres)) return fail(h, PFMBEM_ENUMERIC, "non-finite residual");
       if (relres <= tol) { st = PFMBEM_OK; break; }
@@ -2109,7 +2117,7 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
       int it = 0, rs = 0;
       double rr = 1;
       CK(cudaMemsetAsync(g.c, 0, n * sizeof(cplx), h->stream));
-      pfmbem_status si = gmres(h, g.d, g.c, inner_tol, cap, PFMBEM_MIXED, &it, &rs, &rr, true, true);
+      pfmbem_status si = gmres(h, g.d, g.c, inner_tol, cap, PFMBEM_MIXED, &it, &rs, &rr, true, true, std::sqrt(rn));
       if (si != PFMBEM_OK && si != PFMBEM_ENOCONV) return si;
       iters += it;
       CK(k_axpy(h, cplx{1, 0}, g.c, g.x, (int)n));
@@ -2128,7 +2136,7 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
       relres = rr;
     }
   } else {
-    st = gmres(h, g.b, g.x, tol, maxit, PFMBEM_FP64, &iters, &restarts, &relres);
+    st = gmres(h, g.b, g.x, tol, maxit, PFMBEM_FP64, &iters, &restarts, &relres, !use_guess);
   }
   CK(cudaMemcpyAsync(psi, g.x, n * sizeof(cplx), pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));

@@ -655,9 +655,10 @@ __global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const 
 }
 
 // ------------------------------------------------------------ device-side GMRES step
-// One Arnoldi step of GMRES after w = A z_j, as one cooperative launch:
-// classical Gram-Schmidt applied twice (h1 = V^H w, w -= V h1, h2 = V^H w,
-// w -= V h2), v_{j+1} = w / ||w||, and then, by one thread, the Givens rotations
+// One Arnoldi step of GMRES after w = A z_j, as one cooperative launch with two
+// device-wide barriers: classical Gram-Schmidt applied twice (h1 = V^H w,
+// w -= V h1, h2 = V^H w, w -= V h2), v_{j+1} = w / ||w||, and then, by one
+// thread, the Givens rotations
 // of the new Hessenberg column h1 + h2 (+ ||w|| below the diagonal), the
 // rotated right-hand side g and the residual estimate |g_{j+1}| / ||b||.  The
 // step raises the cycle's done flag when the estimate reaches the threshold,
@@ -666,6 +667,11 @@ __global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const 
 // contiguous slice of the n entries; the dot products go one warp per basis
 // column over the slice and meet by atomic adds.  The sums of step j live in
 // accumulator set j mod 2, and step j clears the other set for step j + 1.
+// The norm of the final w comes from the second pass: with V orthonormal,
+// ||w - V h2||^2 = ||w||^2 - ||h2||^2, and after the first pass h2 is of the
+// order of the rounding error, so the difference loses no accuracy.  The last
+// update w -= V h2 is then done where v_{j+1} is written (fiber by fiber with
+// the preconditioner) and needs no barrier of its own.
 struct ArnArgs {
   int n, m, j;
   cplx* V;                           // [(m+1)][n] orthonormal basis
@@ -724,20 +730,8 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
   // h1 = V^H w
   arn_dots(a, nc, t0, t1, h1, warp, lane);
   if (!grid_barrier(a.bar, a.err)) return;
-  // w -= V h1; h2 = V^H w
+  // w -= V h1; ||w||^2; h2 = V^H w
   for (int i = threadIdx.x; i < nc; i += FB) sh[i] = ldcg(h1 + i);
-  __syncthreads();
-  for (int t = t0 + threadIdx.x; t < t1; t += FB) {
-    cplx v = a.w[t];
-#pragma unroll 4
-    for (int c = 0; c < nc; ++c) v -= a.V[(size_t)c * a.n + t] * sh[c];
-    a.w[t] = v;
-  }
-  __syncthreads();
-  arn_dots(a, nc, t0, t1, h2, warp, lane);
-  if (!grid_barrier(a.bar, a.err)) return;
-  // w -= V h2; ||w||^2
-  for (int i = threadIdx.x; i < nc; i += FB) sh[i] = ldcg(h2 + i);
   __syncthreads();
   double part = 0;
   for (int t = t0 + threadIdx.x; t < t1; t += FB) {
@@ -755,10 +749,17 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
     for (int i = 0; i < FW; ++i) tot += red[i];
     atomicAdd(nrm, tot);
   }
+  arn_dots(a, nc, t0, t1, h2, warp, lane);
   if (!grid_barrier(a.bar, a.err)) return;
-  // v_{j+1} = w / ||w|| and, with the preconditioner, z_{j+1} = P^-1 v_{j+1}
-  // (one block per fiber: a fiber's block of P^-1 reads only its own entries)
-  const double hn = sqrt(*(volatile double*)nrm);
+  // ||w - V h2||^2 = ||w||^2 - ||h2||^2; v_{j+1} = (w - V h2) / ||w - V h2|| and,
+  // with the preconditioner, z_{j+1} = P^-1 v_{j+1} (one block per fiber: a
+  // fiber's block of P^-1 reads only its own entries)
+  __syncthreads();
+  for (int i = threadIdx.x; i < nc; i += FB) sh[i] = ldcg(h2 + i);
+  __syncthreads();
+  double s2 = 0;
+  for (int c = 0; c < nc; ++c) s2 += sh[c].re * sh[c].re + sh[c].im * sh[c].im;
+  const double hn = sqrt(fmax(*(volatile double*)nrm - s2, 0.0));
   const double inv = hn > 0 ? 1.0 / hn : 0.0;
   cplx* vn = a.V + (size_t)(a.j + 1) * a.n;
   if (a.Zn) {
@@ -769,13 +770,23 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
     }
     for (int fb = b; fb < a.M; fb += G) {
       __syncthreads();
-      for (int t = 2 * a.foff[fb] + threadIdx.x; t < 2 * a.foff[fb + 1]; t += FB) vn[t] = inv * a.w[t];
+      for (int t = 2 * a.foff[fb] + threadIdx.x; t < 2 * a.foff[fb + 1]; t += FB) {
+        cplx v = a.w[t];
+#pragma unroll 4
+        for (int c = 0; c < nc; ++c) v -= a.V[(size_t)c * a.n + t] * sh[c];
+        vn[t] = inv * v;
+      }
       __syncthreads();
       precond_fiber<C>(fb, a.foff, a.fh_base, static_cast<const C*>(a.pc), tws, a.pr_base,
                        static_cast<const C*>(a.pr), vn, a.Zn, xs);
     }
   } else {
-    for (int t = t0 + threadIdx.x; t < t1; t += FB) vn[t] = inv * a.w[t];
+    for (int t = t0 + threadIdx.x; t < t1; t += FB) {
+      cplx v = a.w[t];
+#pragma unroll 4
+      for (int c = 0; c < nc; ++c) v -= a.V[(size_t)c * a.n + t] * sh[c];
+      vn[t] = inv * v;
+    }
   }
   if (b == G - 1) {
     // the new column of H and its Givens rotations (by the last block, which
