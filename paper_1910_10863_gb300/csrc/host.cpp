@@ -50,16 +50,64 @@ void ensure_pool() {
   done[dev] = true;
 }
 
-template <class T>
-T* dalloc(pfmbem* h, size_t n) {
+// Small arrays are carved from per-stream chunks of the handle, so that a
+// create makes a handful of pool allocations instead of about a hundred: the
+// pool's allocation call slows down by an order of magnitude once many
+// handles have come and gone (its free lists grow), and every create and solve
+// paid for each call.  A carve is ordered on the stream its chunk was
+// allocated on, as the allocation itself was; chunks and the arrays too large
+// to carve are released together at destroy.
+constexpr size_t kCarveMax = (size_t)256 << 10;     // largest carved array
+constexpr size_t kChunkMin = (size_t)512 << 10;
+constexpr size_t kChunkMax = (size_t)8 << 20;
+
+void* dalloc_bytes(pfmbem* h, size_t bytes, bool carve) {
+  cudaStream_t st = h->astream ? h->astream : h->stream;
+  bytes = (std::max<size_t>(bytes, 1) + 255) & ~(size_t)255;
+  if (carve && bytes <= kCarveMax) {
+    pfmbem::Carve* c = nullptr;
+    for (auto& x : h->carves)
+      if (x.stream == st) c = &x;
+    if (c && c->used + bytes <= c->cap) {
+      void* p = c->base + c->used;
+      c->used += bytes;
+      return p;
+    }
+    const size_t cap = std::min(kChunkMax, std::max(kChunkMin, c ? 2 * c->cap : kChunkMin));
+    void* base = nullptr;
+    if (cudaMallocAsync(&base, cap, st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    h->allocs.push_back(base);
+    if (!c) {
+      h->carves.push_back({});
+      c = &h->carves.back();
+      c->stream = st;
+    }
+    c->base = static_cast<unsigned char*>(base);
+    c->cap = cap;
+    c->used = bytes;
+    return base;
+  }
   void* p = nullptr;
-  if (n == 0) n = 1;
-  if (cudaMallocAsync(&p, n * sizeof(T), h->astream ? h->astream : h->stream) != cudaSuccess) {
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return nullptr;
   }
   h->allocs.push_back(p);
-  return static_cast<T*>(p);
+  return p;
+}
+
+template <class T>
+T* dalloc(pfmbem* h, size_t n) {
+  return static_cast<T*>(dalloc_bytes(h, n * sizeof(T), true));
+}
+
+// A temporary released on its own before destroy (never carved).
+template <class T>
+T* dalloc_tmp(pfmbem* h, size_t n) {
+  return static_cast<T*>(dalloc_bytes(h, n * sizeof(T), false));
 }
 
 // Page-locked staging for the batched set-up copies: one process-wide arena,
@@ -2217,8 +2265,8 @@ pfmbem_status field_points(pfmbem* h, const double* psi, int npts, const double*
   const cplx* psid;
   pfmbem_status st = stage_input(h, psi, n, h->stage_in, &psid);
   if (st != PFMBEM_OK) return st;
-  double2* pd = dalloc<double2>(h, npts);
-  cplx* ud = dalloc<cplx>(h, 2 * (size_t)npts);
+  double2* pd = dalloc_tmp<double2>(h, npts);
+  cplx* ud = dalloc_tmp<cplx>(h, 2 * (size_t)npts);
   if (!pd || !ud) return fail(h, PFMBEM_ENOMEM, "field buffers");
   CK(cudaMemcpyAsync(pd, hp.data(), sizeof(double2) * npts, cudaMemcpyHostToDevice, h->stream));
   CK(k_field_prepare(h, psid));
@@ -2336,7 +2384,7 @@ pfmbem_status pfmbem_warm_features_local(pfmbem_t h, int K, float* x) {
   if (!h || !x || K < 0 || K > 32) return PFMBEM_EINVAL;
   const size_t nx = (size_t)h->M * (5 + 3 * K);
   const bool dev = is_device_ptr(x);
-  float* xd = dev ? x : dalloc<float>(h, nx);
+  float* xd = dev ? x : dalloc_tmp<float>(h, nx);
   if (!xd) return fail(h, PFMBEM_ENOMEM, "warm-start buffer");
   CK(k_warm_features_local(h, K, xd));
   if (!dev) {
@@ -2355,7 +2403,7 @@ pfmbem_status pfmbem_warm_targets(pfmbem_t h, int nmodes, const double* psi, flo
   pfmbem_status st = stage_input(h, psi, n, h->stage_in, &pd);
   if (st != PFMBEM_OK) return st;
   const bool dev = is_device_ptr(t);
-  float* td = dev ? t : dalloc<float>(h, nt);
+  float* td = dev ? t : dalloc_tmp<float>(h, nt);
   if (!td) return fail(h, PFMBEM_ENOMEM, "warm-start buffer");
   CK(k_warm_targets(h, nmodes, pd, td));
   if (!dev) {
@@ -2373,7 +2421,7 @@ pfmbem_status pfmbem_warm_decode(pfmbem_t h, int nmodes, const float* y, double*
   const bool ydev = is_device_ptr(y);
   float* yd = const_cast<float*>(y);
   if (!ydev) {
-    yd = dalloc<float>(h, ny);
+    yd = dalloc_tmp<float>(h, ny);
     if (!yd) return fail(h, PFMBEM_ENOMEM, "warm-start buffer");
     CK(cudaMemcpyAsync(yd, y, ny * sizeof(float), cudaMemcpyHostToDevice, h->stream));
   }

@@ -287,6 +287,12 @@ struct pfmbem {
   GmresWork gw;
   Prof prof;
   std::vector<void*> allocs;
+  struct Carve {                 // the current chunk small arrays are carved from, per stream
+    cudaStream_t stream = nullptr;
+    unsigned char* base = nullptr;
+    size_t used = 0, cap = 0;
+  };
+  std::vector<Carve> carves;
   // batched table uploads during set-up (host.cpp upload / flush_uploads):
   // the open batch is written straight into the page-locked staging arena
   // when this create holds it, else (or once it overflows) into ub_buf
