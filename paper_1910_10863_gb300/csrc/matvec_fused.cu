@@ -663,7 +663,7 @@ __global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const 
 // rotated right-hand side g and the residual estimate |g_{j+1}| / ||b||.  The
 // step raises the cycle's done flag when the estimate reaches the threshold,
 // on breakdown (||w|| = 0) or at the restart length; every kernel of the
-// cycle queued after that returns at once.  All FP64.  Each block owns one
+// cycle queued after that returns at once.  Each block owns one
 // contiguous slice of the n entries; the dot products go one warp per basis
 // column over the slice and meet by atomic adds.  The sums of step j live in
 // accumulator set j mod 2, and step j clears the other set for step j + 1.
@@ -671,7 +671,12 @@ __global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const 
 // ||w - V h2||^2 = ||w||^2 - ||h2||^2, and after the first pass h2 is of the
 // order of the rounding error, so the difference loses no accuracy.  The last
 // update w -= V h2 is then done where v_{j+1} is written (fiber by fiber with
-// the preconditioner) and needs no barrier of its own.
+// the preconditioner) and needs no barrier of its own.  The dot products and
+// the updates run in C, the precision of the products: FP32 for the inner
+// solves of the mixed-precision refinement, whose tolerance (never below 1e-4
+// relative) lies far above FP32 rounding, so the FP64 pipe (1/64 of the FP32 rate
+// on this GPU) carries none of them; the basis, the Hessenberg matrix, the
+// rotations and the sums across blocks stay FP64.
 struct ArnArgs {
   int n, m, j;
   cplx* V;                           // [(m+1)][n] orthonormal basis
@@ -699,14 +704,15 @@ struct ArnArgs {
 
 constexpr int ARN_MAXC = 256;        // columns of the basis the kernel can hold (restart length <= 250)
 
+template <class C>
 __device__ __forceinline__ void arn_dots(const ArnArgs& a, int nc, int t0, int t1, cplx* out, int warp, int lane) {
   for (int c = warp; c < nc; c += FW) {
     const cplx* v = a.V + (size_t)c * a.n;
-    cplx s{0, 0};
+    C s{0, 0};
 #pragma unroll 4
-    for (int t = t0 + lane; t < t1; t += 32) s += conj(v[t]) * a.w[t];
+    for (int t = t0 + lane; t < t1; t += 32) s += conj(from_d<C>(v[t])) * from_d<C>(a.w[t]);
     s = wsum(s);
-    if (lane == 0) atomic_add(out + c, s);
+    if (lane == 0) atomic_add(out + c, to_d(s));
   }
 }
 
@@ -715,6 +721,7 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
   if (*(volatile const int*)a.ictl != 0) return;
   extern __shared__ unsigned char smraw[];
   __shared__ cplx sh[ARN_MAXC];
+  __shared__ C shc[ARN_MAXC];                       // sh in the precision of the updates
   __shared__ double red[FW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x, b = blockIdx.x;
@@ -728,18 +735,19 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
     for (int i = threadIdx.x; i < S; i += FB) other[i] = cplx{0, 0};
   }
   // h1 = V^H w
-  arn_dots(a, nc, t0, t1, h1, warp, lane);
+  arn_dots<C>(a, nc, t0, t1, h1, warp, lane);
   if (!grid_barrier(a.bar, a.err)) return;
   // w -= V h1; ||w||^2; h2 = V^H w
-  for (int i = threadIdx.x; i < nc; i += FB) sh[i] = ldcg(h1 + i);
+  for (int i = threadIdx.x; i < nc; i += FB) shc[i] = from_d<C>(ldcg(h1 + i));
   __syncthreads();
   double part = 0;
   for (int t = t0 + threadIdx.x; t < t1; t += FB) {
-    cplx v = a.w[t];
+    C v = from_d<C>(a.w[t]);
 #pragma unroll 4
-    for (int c = 0; c < nc; ++c) v -= a.V[(size_t)c * a.n + t] * sh[c];
-    a.w[t] = v;
-    part += v.re * v.re + v.im * v.im;
+    for (int c = 0; c < nc; ++c) v -= from_d<C>(a.V[(size_t)c * a.n + t]) * shc[c];
+    const cplx vd = to_d(v);
+    a.w[t] = vd;
+    part += vd.re * vd.re + vd.im * vd.im;
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xffffffffu, part, o);
   if (lane == 0) red[warp] = part;
@@ -749,13 +757,16 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
     for (int i = 0; i < FW; ++i) tot += red[i];
     atomicAdd(nrm, tot);
   }
-  arn_dots(a, nc, t0, t1, h2, warp, lane);
+  arn_dots<C>(a, nc, t0, t1, h2, warp, lane);
   if (!grid_barrier(a.bar, a.err)) return;
   // ||w - V h2||^2 = ||w||^2 - ||h2||^2; v_{j+1} = (w - V h2) / ||w - V h2|| and,
   // with the preconditioner, z_{j+1} = P^-1 v_{j+1} (one block per fiber: a
   // fiber's block of P^-1 reads only its own entries)
   __syncthreads();
-  for (int i = threadIdx.x; i < nc; i += FB) sh[i] = ldcg(h2 + i);
+  for (int i = threadIdx.x; i < nc; i += FB) {
+    sh[i] = ldcg(h2 + i);
+    shc[i] = from_d<C>(sh[i]);
+  }
   __syncthreads();
   double s2 = 0;
   for (int c = 0; c < nc; ++c) s2 += sh[c].re * sh[c].re + sh[c].im * sh[c].im;
@@ -771,10 +782,10 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
     for (int fb = b; fb < a.M; fb += G) {
       __syncthreads();
       for (int t = 2 * a.foff[fb] + threadIdx.x; t < 2 * a.foff[fb + 1]; t += FB) {
-        cplx v = a.w[t];
+        C v = from_d<C>(a.w[t]);
 #pragma unroll 4
-        for (int c = 0; c < nc; ++c) v -= a.V[(size_t)c * a.n + t] * sh[c];
-        vn[t] = inv * v;
+        for (int c = 0; c < nc; ++c) v -= from_d<C>(a.V[(size_t)c * a.n + t]) * shc[c];
+        vn[t] = inv * to_d(v);
       }
       __syncthreads();
       precond_fiber<C>(fb, a.foff, a.fh_base, static_cast<const C*>(a.pc), tws, a.pr_base,
@@ -782,10 +793,10 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
     }
   } else {
     for (int t = t0 + threadIdx.x; t < t1; t += FB) {
-      cplx v = a.w[t];
+      C v = from_d<C>(a.w[t]);
 #pragma unroll 4
-      for (int c = 0; c < nc; ++c) v -= a.V[(size_t)c * a.n + t] * sh[c];
-      vn[t] = inv * v;
+      for (int c = 0; c < nc; ++c) v -= from_d<C>(a.V[(size_t)c * a.n + t]) * shc[c];
+      vn[t] = inv * to_d(v);
     }
   }
   if (b == G - 1) {
