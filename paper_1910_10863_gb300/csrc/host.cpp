@@ -158,19 +158,26 @@ void pin_release(pfmbem* h) {
 // between create and destroy; destroy synchronises them before it returns them.
 struct StreamPool {
   std::mutex mu;
-  std::vector<cudaStream_t> streams[64];
+  std::vector<cudaStream_t> streams[64], hstreams[64];   // default / highest priority
   std::vector<cudaEvent_t> events[64];
 };
 StreamPool g_sp;
 
-cudaError_t pool_stream(int dev, cudaStream_t* s) {
+cudaError_t pool_stream(int dev, cudaStream_t* s, bool hi = false) {
   if (dev >= 0 && dev < 64) {
     std::lock_guard<std::mutex> lk(g_sp.mu);
-    if (!g_sp.streams[dev].empty()) {
-      *s = g_sp.streams[dev].back();
-      g_sp.streams[dev].pop_back();
+    auto& v = hi ? g_sp.hstreams[dev] : g_sp.streams[dev];
+    if (!v.empty()) {
+      *s = v.back();
+      v.pop_back();
       return cudaSuccess;
     }
+  }
+  if (hi) {
+    int least = 0, greatest = 0;
+    cudaError_t e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e != cudaSuccess) return e;
+    return cudaStreamCreateWithPriority(s, cudaStreamNonBlocking, greatest);
   }
   return cudaStreamCreateWithFlags(s, cudaStreamNonBlocking);
 }
@@ -187,14 +194,14 @@ cudaError_t pool_event(int dev, cudaEvent_t* e) {
   return cudaEventCreateWithFlags(e, cudaEventDisableTiming);
 }
 
-void pool_put(int dev, cudaStream_t s) {
+void pool_put(int dev, cudaStream_t s, bool hi = false) {
   if (!s) return;
   if (dev < 0 || dev >= 64) {
     cudaStreamDestroy(s);
     return;
   }
   std::lock_guard<std::mutex> lk(g_sp.mu);
-  g_sp.streams[dev].push_back(s);
+  (hi ? g_sp.hstreams[dev] : g_sp.streams[dev]).push_back(s);
 }
 
 void pool_put(int dev, cudaEvent_t e) {
@@ -272,6 +279,39 @@ std::vector<cplxf> to_float(const std::vector<cplx>& v) {
 
 double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace
+
+void trace(pfmbem* h, cudaStream_t st, const char* label) {
+  if (!h->trace_on) return;
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess || cudaEventRecord(e, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (e) cudaEventDestroy(e);
+    return;
+  }
+  h->trace_lbl.push_back(label);
+  h->trace_ev.push_back(e);
+  h->trace_host.push_back(now_ms());
+}
+
+namespace {
+
+// Prints the set-up trace (GPU time of each event and host time of its record,
+// both from the first) once the streams have completed, and releases it.
+static void trace_report(pfmbem* h) {
+  if (h->trace_ev.empty()) return;
+  for (size_t i = 0; i < h->trace_ev.size(); ++i) {
+    float ms = 0;
+    cudaEventElapsedTime(&ms, h->trace_ev[0], h->trace_ev[i]);
+    std::fprintf(stderr, "pfmbem trace %-34s gpu %7.3f ms  host %7.3f ms\n", h->trace_lbl[i], ms,
+                 h->trace_host[i] - h->trace_host[0]);
+  }
+  for (cudaEvent_t e : h->trace_ev) cudaEventDestroy(e);
+  h->trace_ev.clear();
+  h->trace_lbl.clear();
+  h->trace_host.clear();
 }
 
 // Spreads the low 16 bits of v to the even bit positions.
@@ -684,7 +724,7 @@ static void build_m2l_lists(const Level& L, int l, bool tc, M2LLists& o) {
 // launchers, allocations and profiling events of f go there.
 template <class F>
 static pfmbem_status on_aux(pfmbem* h, int i, F&& f) {
-  if (!h->aux[i]) CK(pool_stream(h->dev, &h->aux[i]));
+  if (!h->aux[i]) CK(pool_stream(h->dev, &h->aux[i], i == 2));
   if (!h->aux_ev[i]) CK(pool_event(h->dev, &h->aux_ev[i]));
   if (!h->fork_ev) CK(pool_event(h->dev, &h->fork_ev));
   CK(cudaEventRecord(h->fork_ev, h->stream));
@@ -772,12 +812,15 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     cw[e] = double2{c[e].x, c[e].y - m * H};
   }
   // optional set-up timing on stderr: PFMBEM_TIMING=1 wall time per section
-  // (the stream is synchronised at every mark), =2 host time only (no sync)
+  // (the stream is synchronised at every mark), =2 host time only (no sync),
+  // =3 trace: timing events on the set-up streams, reported at the end
   const char* tenv = std::getenv("PFMBEM_TIMING");
-  const bool timing = tenv != nullptr;
+  h->trace_on = tenv != nullptr && std::strcmp(tenv, "3") == 0;
+  const bool timing = tenv != nullptr && !h->trace_on;
   const bool tsync = timing && std::strcmp(tenv, "2") != 0;
   double tmark = now_ms();
   auto mark = [&](const char* what) {
+    trace(h, h->astream ? h->astream : h->stream, what);
     if (!timing) return;
     if (tsync) cudaStreamSynchronize(h->astream ? h->astream : h->stream);
     const double t = now_ms();
@@ -1045,6 +1088,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       CK(k_lattice_sums(h, jmax, h->lattice_q, Sd));
       // root translation R[a][n] = w_a S_{|n-a|} w_n, built on the device
       CK(k_root_operator(h, p0, R.w_dev, Sd));
+      trace(h, h->stream, "aux0: lattice sums, root done");
       return PFMBEM_OK;
     });
     if (st != PFMBEM_OK) return st;
@@ -1113,6 +1157,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       }
     }
     CK(k_tables(h, tl, h->astream ? h->astream : h->stream));
+    trace(h, h->astream ? h->astream : h->stream, "side: translation tables done");
   }
   h->astream = nullptr;
 
@@ -1179,7 +1224,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         h->Uf = dalloc<cplxf>(h, (size_t)2 * E);
         if (!h->p2m_c || !h->l2p_c || !h->p2m_cf || !h->l2p_cf || !h->densf || !h->Uf)
           return fail(h, PFMBEM_ENOMEM, "device allocation failed (P2M/L2P caches)");
+        trace(h, h->stream, "aux1: P2M/L2P caches start");
         CK(k_build_fmm_caches(h));
+        trace(h, h->stream, "aux1: P2M/L2P caches done");
         return PFMBEM_OK;
       });
       if (st != PFMBEM_OK) return st;
@@ -1219,7 +1266,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       h->nq = dalloc<unsigned long long>(h, std::max<size_t>(h->nq_cap, 1));
       h->nq_len = dalloc<unsigned>(h, 1);
       if (!h->nq || !h->nq_len) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near queue)");
-      h->nc_val = dalloc<cplx>(h, (size_t)(4 * h->nc_blocks));
+      // (FP64 near blocks: formed from the double-float pair on first use, k_near64)
       h->nc_valf = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
       h->nc_vall = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
       h->dens_dd = dalloc<cplxf>(h, (size_t)4 * E);
@@ -1230,12 +1277,20 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       h->tc_err = dalloc<int>(h, 1);
       if (!h->tc_err) return fail(h, PFMBEM_ENOMEM, "device allocation failed");
       CK(cudaMemsetAsync(h->tc_err, 0, sizeof(int), h->stream));
-      if (!h->nc_val || !h->nc_valf || !h->fb_val || !h->fb_valf || !h->stat_dev)
+      if (!h->nc_valf || !h->fb_val || !h->fb_valf || !h->stat_dev)
         return fail(h, PFMBEM_ENOMEM, "device allocation failed (near-field caches)");
       CK(cudaMemsetAsync(h->stat_dev, 0, 4 * sizeof(unsigned long long), h->stream));
       if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
       mark("cache allocation");
-      CK(k_build_caches(h));
+      // the near-field chain (the longest of the set-up) on its own stream of
+      // the highest priority; the same-fiber blocks here beside it
+      if (!h->ktab_ev) CK(pool_event(h->dev, &h->ktab_ev));
+      st = on_aux(h, 2, [&]() -> pfmbem_status {
+        CK(k_build_caches(h, h->ktab_ev));
+        return PFMBEM_OK;
+      });
+      if (st != PFMBEM_OK) return st;
+      CK(k_build_fiber_blocks(h));
       cache = true;
       // the fiber symbols and the preconditioner go to the GPU now, ahead of
       // the host's M2L lists
@@ -1275,6 +1330,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         h->fh_valf = dalloc<cplxf>(h, (size_t)4 * fa);
         if (!h->fh_val || !h->fh_valf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber symbols)");
         CK(k_fiber_symbols(h));
+        CK(cudaStreamWaitEvent(h->stream, h->ktab_ev, 0));   // the preconditioner reads the k tables
         if (h->opt.precond == 0 && h->fz_nfft > 0) {
           h->pc_val = dalloc<cplx>(h, (size_t)4 * fa);
           h->pc_valf = dalloc<cplxf>(h, (size_t)4 * fa);
@@ -1360,6 +1416,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
     if (h->aux[0]) CK(cudaStreamWaitEvent(h->side, h->aux_ev[0], 0));
     CK(k_top_operators(h, h->side));
+    trace(h, h->side, "side: top operators done");
   }
   {
     pfmbem_status st;
@@ -1369,9 +1426,10 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // join: later work on the main stream sees every upload of the second stream
   CK(cudaEventRecord(h->side_ev, h->side));
   CK(cudaStreamWaitEvent(h->stream, h->side_ev, 0));
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 3; ++i)
     if (h->aux[i]) CK(cudaStreamWaitEvent(h->stream, h->aux_ev[i], 0));
   h->astream = nullptr;
+  trace(h, h->stream, "main: streams joined");
   for (int l = 1; l <= D; ++l)
     if (h->lev[l].tc_B) CK(k_tc_build_operator(h, l));
   if (cache) {
@@ -1415,6 +1473,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   }
   h->ub_on = false;
   CK(cudaStreamSynchronize(h->stream));
+  trace_report(h);
   pin_release(h);                  // every staged copy of this create has completed
   {
     int bad = 0;
@@ -1997,7 +2056,7 @@ pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nod
 void pfmbem_destroy(pfmbem_t h) {
   if (!h) return;
   if (h->side) cudaStreamSynchronize(h->side);
-  for (int i = 0; i < 2; ++i)
+  for (int i = 0; i < 3; ++i)
     if (h->aux[i]) cudaStreamSynchronize(h->aux[i]);
   for (void* p : h->allocs) cudaFreeAsync(p, h->stream);
   if (h->stream) cudaStreamSynchronize(h->stream);
@@ -2007,12 +2066,14 @@ void pfmbem_destroy(pfmbem_t h) {
   pool_put(h->dev, h->side_ev);
   pool_put(h->dev, h->pre_ev);
   pool_put(h->dev, h->side);
-  for (int i = 0; i < 2; ++i) {
+  for (int i = 0; i < 3; ++i) {
     pool_put(h->dev, h->aux_ev[i]);
-    pool_put(h->dev, h->aux[i]);
+    pool_put(h->dev, h->aux[i], i == 2);
   }
   pool_put(h->dev, h->fork_ev);
+  pool_put(h->dev, h->ktab_ev);
   prof_release(h);
+  for (cudaEvent_t e : h->trace_ev) cudaEventDestroy(e);
   delete h;
 }
 

@@ -139,8 +139,10 @@ struct pfmbem {
   cudaStream_t side = nullptr;   // second stream of the set-up: host planning overlaps the cache build
   cudaEvent_t side_ev = nullptr;
   cudaEvent_t pre_ev = nullptr;    // main-stream point the second stream waits for
-  cudaStream_t aux[2] = {nullptr, nullptr};   // set-up streams: lattice sums / P2M-L2P caches
-  cudaEvent_t aux_ev[2] = {nullptr, nullptr};
+  // set-up streams: lattice sums / P2M-L2P caches / near-field chain (high priority)
+  cudaStream_t aux[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t aux_ev[3] = {nullptr, nullptr, nullptr};
+  cudaEvent_t ktab_ev = nullptr;  // the fiber k tables are built (near-field chain)
   cudaEvent_t fork_ev = nullptr;
   cudaStream_t astream = nullptr;  // stream of allocations and uploads while set-up runs on `side`
   std::string err;
@@ -185,7 +187,7 @@ struct pfmbem {
   int* nc_sbase = nullptr;       // [nleaf + 1] offset of the leaf's source list
   int* nc_src = nullptr;         // source element (sorted index) per list entry
   int* nc_img = nullptr;         // image m per list entry
-  cplx* nc_val = nullptr;        // [blocks][4]
+  cplx* nc_val = nullptr;        // [blocks][4] FP64, formed on first use (k_near64)
   cplxf* nc_valf = nullptr;
   cplxf* nc_vall = nullptr;      // lo parts: nc_val = nc_valf + nc_vall to ~48 bits (double-float)
   int64_t nc_blocks = 0;
@@ -293,6 +295,11 @@ struct pfmbem {
     size_t used = 0, cap = 0;
   };
   std::vector<Carve> carves;
+  // set-up trace (PFMBEM_TIMING=3): timing events recorded on the set-up streams
+  bool trace_on = false;
+  std::vector<const char*> trace_lbl;
+  std::vector<cudaEvent_t> trace_ev;
+  std::vector<double> trace_host;
   // batched table uploads during set-up (host.cpp upload / flush_uploads):
   // the open batch is written straight into the page-locked staging arena
   // when this create holds it, else (or once it overflows) into ub_buf
@@ -318,7 +325,11 @@ void prof_release(pfmbem* h);
 int tc_kpad(int P);
 cudaError_t k_tc_build_operator(pfmbem* h, int level);
 cudaError_t k_m2l_tc(pfmbem* h, int level, const cplxf* M, cplxf* L);
-cudaError_t k_build_caches(pfmbem* h);
+cudaError_t k_build_caches(pfmbem* h, cudaEvent_t ktab_done = nullptr);
+cudaError_t k_build_fiber_blocks(pfmbem* h);
+cudaError_t k_near64(pfmbem* h);   // FP64 near blocks (hi + lo), formed on first use
+// Diagnostic: records a timing event on st under label when the set-up trace is on.
+void trace(pfmbem* h, cudaStream_t st, const char* label);
 cudaError_t k_sort_elements(pfmbem* h);
 // single-launch cached matvec (matvec_fused.cu)
 cudaError_t k_fused_prepare(pfmbem* h, bool* ok);

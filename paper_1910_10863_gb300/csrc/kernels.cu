@@ -1036,7 +1036,7 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
     const int64_t kb = kbase[fs];
     const int fN = foff[fs + 1] - foff[fs], fo = foff[fs];
     const int r = t_run[t];
-    cplx* row = val + base[li] + (int64_t)t * ns * 4;
+    cplx* row = val ? val + base[li] + (int64_t)t * ns * 4 : nullptr;
     cplxf* rowf = valf ? valf + base[li] + (int64_t)t * ns * 4 : nullptr;
     cplxf* rowl = vall + base[li] + (int64_t)t * ns * 4;
     // four lanes per source j, one complex value each, so that a warp writes
@@ -1045,7 +1045,7 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
     for (int j = lane >> 2; j < ns; j += 8) {
       const int m = s_m[j];
       if (s_f[j] == s && m == 0) {
-        row[4 * j + q] = cplx{0, 0};
+        if (row) row[4 * j + q] = cplx{0, 0};
         if (rowf) rowf[4 * j + q] = cplxf{0.f, 0.f};
         rowl[4 * j + q] = cplxf{0.f, 0.f};
         continue;
@@ -1080,12 +1080,12 @@ __global__ void near_build_kernel(const int* __restrict__ ne, const int* __restr
       }
       // the tables hold the blocks of image 0; image m adds the factor alpha^m
       if (m == 0) {
-        row[4 * j + q] = tv[at + q];
+        if (row) row[4 * j + q] = tv[at + q];
         if (rowf) rowf[4 * j + q] = tvf[at + q];
         rowl[4 * j + q] = tvl[at + q];
       } else {
         const cplx b = ipow_phase(alpha, m) * tv[at + q];
-        row[4 * j + q] = b;
+        if (row) row[4 * j + q] = b;
         if (rowf) rowf[4 * j + q] = cplxf{(float)b.re, (float)b.im};
         rowl[4 * j + q] = split_lo(b);
       }
@@ -1125,7 +1125,7 @@ __global__ void near_direct_kernel(const unsigned long long* __restrict__ queue,
     const cplx b[4] = {ph * Dv, (-eta) * mul_i(ph * S), ph * T, (-eta) * mul_i(ph * K)};
     const int64_t o = base[li] + ((int64_t)t * ns + j) * 4;
     for (int q2 = 0; q2 < 4; ++q2) {
-      val[o + q2] = b[q2];
+      if (val) val[o + q2] = b[q2];
       if (valf) valf[o + q2] = cplxf{(float)b[q2].re, (float)b[q2].im};
       vall[o + q2] = split_lo(b[q2]);
     }
@@ -1155,6 +1155,11 @@ __global__ void near_direct_kernel(const unsigned long long* __restrict__ queue,
 // near-field build reads same-fiber pairs from this table.
 // FB_SPLIT consecutive lanes share one (row element e, source f) pair and take
 // every FB_SPLIT-th Gauss node; the partial sums meet by shuffles.
+// A regular polygon is also symmetric under the reflection through the
+// midpoint of its first element and the centre: it maps source f0 + dl onto
+// f0 + N - dl and keeps both normals outward, and the Gauss rule is symmetric,
+// so the first element's row (both planes) takes the integrals of dl <= N/2
+// and writes each also at N - dl.
 constexpr int FB_SPLIT = 4;
 
 __device__ __forceinline__ void group_sum(cplx& v) {
@@ -1173,17 +1178,20 @@ __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __re
                                    const int64_t* __restrict__ kbase, cplx* __restrict__ kval,
                                    cplx* __restrict__ ksval, cplxf* __restrict__ ksvalf, cplxf* __restrict__ ksvall,
                                    cplx* __restrict__ val, cplxf* __restrict__ valf,
-                                   unsigned long long* __restrict__ stat) {
+                                   unsigned long long* __restrict__ stat, int zoff) {
   const int e = rows[blockIdx.x];
   const int fb = fib[e], f0 = foff[fb], N = foff[fb + 1] - f0, el = e - f0;
-  const bool ktab = blockIdx.z == 1;
+  const bool ktab = blockIdx.z + zoff == 1;
   const int64_t kb = kbase[fb];
   if (ktab && kb < 0) return;                      // uniform over the block
+  const bool mir = kb >= 0 && el == 0;             // mirrored half row (regular polygon)
+  if (mir && (int)blockIdx.y * (int)(blockDim.x / FB_SPLIT) > N / 2) return;   // uniform over the block
   const int part = threadIdx.x % FB_SPLIT;
   const int fl = blockIdx.y * (blockDim.x / FB_SPLIT) + threadIdx.x / FB_SPLIT;
   const bool lead = part == 0;
   unsigned long long np = 0, nq = 0;
-  const bool on = fl < N;
+  const bool on = fl < N && !(mir && fl > N / 2);
+  const int fm = mir && fl > 0 && 2 * fl != N ? N - fl : -1;   // mirror entry, if any
   const int f = f0 + (on ? fl : 0);
   const bool self = on && f == e;
   cplx S{0, 0}, Dv{0, 0}, K{0, 0}, T{0, 0};
@@ -1194,8 +1202,8 @@ __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __re
     const double q = sqrt((xe.x - c.x) * (xe.x - c.x) + (xe.y - c.y) * (xe.y - c.y)) / hh;
     const int g = gl_order(q, 0);
     if (lead) {
-      np = 1;
-      nq = g;
+      np = fm >= 0 ? 2 : 1;
+      nq = fm >= 0 ? 2 * g : g;
     }
     pair4_f64(ktab ? k : k1, xe, nxe, c, tf, nf, hh, g, S, Dv, K, T, part, FB_SPLIT);
   }
@@ -1211,6 +1219,14 @@ __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __re
       tv[2] = K;
       tv[3] = T;
       near_block_form(eta, S, Dv, K, T, ksval + 4 * (kb + fl), ksvalf + 4 * (kb + fl), ksvall + 4 * (kb + fl));
+      if (fm >= 0) {
+        cplx* tm = kval + 4 * (kb + fm);
+        tm[0] = S;
+        tm[1] = Dv;
+        tm[2] = K;
+        tm[3] = T;
+        near_block_form(eta, S, Dv, K, T, ksval + 4 * (kb + fm), ksvalf + 4 * (kb + fm), ksvall + 4 * (kb + fm));
+      }
     } else {
       const int64_t r0 = fbase[fb] + (int64_t)(2 * el) * (2 * N), r1 = r0 + 2 * N;
       const cplx c2r = rho * c2;
@@ -1231,15 +1247,19 @@ __global__ void fiber_build_kernel(const int* __restrict__ rows, const int* __re
         a10 = -(c2r * T);
         a11 = eta * mul_i(c2r * K);
       }
-      val[r0 + 2 * fl] = a00;
-      val[r0 + 2 * fl + 1] = a01;
-      val[r1 + 2 * fl] = a10;
-      val[r1 + 2 * fl + 1] = a11;
-      if (valf) {
-        valf[r0 + 2 * fl] = cplxf{(float)a00.re, (float)a00.im};
-        valf[r0 + 2 * fl + 1] = cplxf{(float)a01.re, (float)a01.im};
-        valf[r1 + 2 * fl] = cplxf{(float)a10.re, (float)a10.im};
-        valf[r1 + 2 * fl + 1] = cplxf{(float)a11.re, (float)a11.im};
+      for (int w = 0; w < 2; ++w) {
+        const int q = w == 0 ? fl : fm;
+        if (q < 0) break;
+        val[r0 + 2 * q] = a00;
+        val[r0 + 2 * q + 1] = a01;
+        val[r1 + 2 * q] = a10;
+        val[r1 + 2 * q + 1] = a11;
+        if (valf) {
+          valf[r0 + 2 * q] = cplxf{(float)a00.re, (float)a00.im};
+          valf[r0 + 2 * q + 1] = cplxf{(float)a01.re, (float)a01.im};
+          valf[r1 + 2 * q] = cplxf{(float)a10.re, (float)a10.im};
+          valf[r1 + 2 * q + 1] = cplxf{(float)a11.re, (float)a11.im};
+        }
       }
     }
   }
@@ -1304,19 +1324,38 @@ __global__ void near_sources_kernel(const int* __restrict__ nl_ptr, const int* _
   }
 }
 
-cudaError_t k_build_caches(pfmbem* h) {
-  cudaStream_t st = h->stream;
-  Level& leaf = h->lev[h->D];
+// Launches one plane of fiber_build_kernel: the k tables (ktab) or the same-fiber blocks.
+static void fiber_build_plane(pfmbem* h, bool ktab, cudaStream_t st) {
   cplx c2{h->c2re, h->c2im};
-  near_sources_kernel<<<leaf.nne, 128, 0, st>>>(h->nl_ptr, h->nl_src, h->nl_img, leaf.box_begin, leaf.box_end,
-                                                h->nc_sbase, h->nc_src, h->nc_img);
-  // same-fiber blocks and k tables first: the near-field build reads the k tables
   prof_begin(h, PH_BUILD);
-  fiber_build_kernel<<<dim3(h->nfb_rows, (h->max_fiber + 128 / FB_SPLIT - 1) / (128 / FB_SPLIT), 2), 128, 0, st>>>(
+  fiber_build_kernel<<<dim3(h->nfb_rows, (h->max_fiber + 128 / FB_SPLIT - 1) / (128 / FB_SPLIT), 1), 128, 0, st>>>(
       h->fb_rows, h->o_fiber, h->fib_off, h->fb_base, h->k, h->k1, h->eta, h->rho, c2, h->o_c, h->o_t, h->o_nu,
       h->o_h, h->self4, h->kt_base, h->kt_val, h->kt_sval, h->kt_svalf, h->kt_svall, h->fb_val, h->fb_valf,
-      h->stat_dev);
+      h->stat_dev, ktab ? 1 : 0);
   prof_end(h, PH_BUILD);
+}
+
+// The same-fiber blocks (fiber_build_kernel's first plane), apart from the
+// near-field chain, which needs only the k tables.
+cudaError_t k_build_fiber_blocks(pfmbem* h) {
+  fiber_build_plane(h, false, h->stream);
+  return cudaGetLastError();
+}
+
+// The near-field chain: near sources, the fibers' k tables (recorded in
+// ktab_done when given), the pair tables and the near-field blocks.
+cudaError_t k_build_caches(pfmbem* h, cudaEvent_t ktab_done) {
+  cudaStream_t st = h->stream;
+  Level& leaf = h->lev[h->D];
+  near_sources_kernel<<<leaf.nne, 128, 0, st>>>(h->nl_ptr, h->nl_src, h->nl_img, leaf.box_begin, leaf.box_end,
+                                                h->nc_sbase, h->nc_src, h->nc_img);
+  // the near-field build reads the k tables
+  fiber_build_plane(h, true, st);
+  if (ktab_done) {
+    cudaError_t e = cudaEventRecord(ktab_done, st);
+    if (e != cudaSuccess) return e;
+  }
+  trace(h, st, "near: k tables done");
   if (h->ntab > 0) {
     prof_begin(h, PH_BUILD);
     pair_table_kernel<<<(unsigned)((h->tab_entries + 255) / 256), 256, 0, st>>>(
@@ -1343,12 +1382,14 @@ cudaError_t k_build_caches(pfmbem* h) {
                                                    h->nq_len, h->nq_cap);
   }
   prof_end(h, PH_BUILD);
+  trace(h, st, "near: near_build done");
   prof_begin(h, PH_BUILD);
   near_direct_kernel<<<1216, 128, 0, st>>>(h->nq, h->nq_len, h->nq_cap, leaf.ne, leaf.box_begin, h->nc_base,
                                            h->nc_sbase, h->nc_src, h->nc_img, h->k, h->eta, h->H, h->alpha, h->s_c,
                                            h->s_t, h->s_nu, h->s_h, h->nc_val, h->nc_valf, h->nc_vall,
                                            h->stat_dev);
   prof_end(h, PH_BUILD);
+  trace(h, st, "near: near_direct done");
   return cudaGetLastError();
 }
 
@@ -1943,10 +1984,37 @@ static void upward_f64(pfmbem* h, const cplx* x) {
   }
 }
 
+// FP64 near-field blocks as hi + lo of the double-float pair: the set-up keeps
+// only the pair (the single-launch FP64 product works on it directly), and the
+// paths that read FP64 blocks form them here once, on first use.
+__global__ void near64_kernel(size_t n, const cplxf* __restrict__ hi, const cplxf* __restrict__ lo,
+                              cplx* __restrict__ out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const cplxf a = hi[i], b = lo[i];
+    out[i] = cplx{(double)a.re + (double)b.re, (double)a.im + (double)b.im};
+  }
+}
+
+cudaError_t k_near64(pfmbem* h) {
+  if (h->nc_val || !h->nc_valf || !h->nc_vall) return cudaSuccess;
+  const size_t n = 4 * (size_t)h->nc_blocks;
+  void* p = nullptr;
+  cudaError_t e = cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(cplx), h->stream);
+  if (e != cudaSuccess) return e;
+  h->allocs.push_back(p);
+  h->nc_val = static_cast<cplx*>(p);
+  if (n > 0)
+    near64_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(n, h->nc_valf, h->nc_vall,
+                                                                                           h->nc_val);
+  return cudaGetLastError();
+}
+
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision) {
   if (h->cached && h->fused) return k_matvec_fused(h, x, y, precision);
   if (h->cached) {
     if (precision == PFMBEM_MIXED) return matvec_cached(h, x, y, ops32(h));
+    cudaError_t e = k_near64(h);
+    if (e != cudaSuccess) return e;
     return matvec_cached(h, x, y, ops64(h));
   }
   // on-the-fly path (no cached operators): FP64 element integrals in every product

@@ -1385,6 +1385,10 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
     a.dens = h->dens; a.root = h->root; a.rootc = h->rootc; a.p2m = h->p2m_c; a.l2p = h->l2p_c;
     // (PFMBEM_NEAR_FP64 selects FP64 near sums and M2L instead, for measurement)
     static const bool near64 = std::getenv("PFMBEM_NEAR_FP64") != nullptr;
+    if (near64 || !h->dens_dd) {
+      cudaError_t e = k_near64(h);                  // FP64 blocks, formed on first use
+      if (e != cudaSuccess) return e;
+    }
     if (h->nc_vall && h->dens_dd && !near64) {
       a.nc_lo = h->nc_vall;
       a.nc_hi = h->nc_valf;
