@@ -105,7 +105,7 @@ typedef struct {
   int p2m_nodes;          /* Gauss nodes per element in P2M */
   int lattice_q;          /* directly summed image rows in the lattice sums */
   double root_x0, root_y0;/* lower-left corner of the root box (side H) */
-  double setup_ms;        /* wall time of pfmbem_create */
+  double setup_ms;        /* host wall time of pfmbem_create (the device part may still run) */
   int64_t near_blocks;    /* cached near-field 2x2 complex blocks (0 when not cached) */
   int64_t fiber_entries;  /* cached fiber-block complex entries (0 when not cached) */
   int cached;             /* 1 when the element integrals are cached in device memory */
@@ -127,7 +127,11 @@ typedef struct {
  *   cuda_stream       cudaStream_t to order all work on (NULL = legacy stream)
  *   out               receives the handle; the handle owns all device state
  * Builds the quadtree (Sec. 3.1), self-element integrals, lattice sums
- * (Sec. 3.3) and translation tables.  Returns EGEOM/EWOOD/EINVAL/ENOMEM/ECUDA. */
+ * (Sec. 3.3) and translation tables.  Returns EGEOM/EWOOD/EINVAL/ENOMEM/ECUDA.
+ * The device part of the set-up is queued on cuda_stream and the call returns
+ * without waiting for it; the first later call on the handle that waits for
+ * the stream (pfmbem_solve at its end, every other call at its start) returns
+ * ENUMERIC if the set-up found a non-finite translation operator. */
 pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nodes_xy,
                             double H, int lattice, double k, double k1, double rho_ratio,
                             double theta, const pfmbem_options* opt, void* cuda_stream,

@@ -111,15 +111,19 @@ T* dalloc_tmp(pfmbem* h, size_t n) {
 }
 
 // Page-locked staging for the batched set-up copies: one process-wide arena,
-// held by one create at a time (pin_acquire to pin_release; that create
-// synchronises its stream before it lets go, so no copy from the arena is in
-// flight when the next create writes into it).  A create that finds the arena
-// held by another, or whose batches outgrow it, stages in pageable memory.
+// held by one create at a time (pin_acquire to pin_release).  A create that
+// ends without waiting for its stream lets go with pin_release_async, which
+// records an event after its last copy; the next holder waits for that event
+// before it writes into the arena.  A create that finds the arena held by
+// another, or whose batches outgrow it, stages in pageable memory.
 struct PinnedArena {
   std::mutex mu;
   unsigned char* buf = nullptr;
   size_t cap = 0;
   pfmbem* owner = nullptr;
+  cudaEvent_t done = nullptr;      // after the last copy of the previous holder
+  int done_dev = -1;
+  bool pending = false;
 };
 PinnedArena g_pin;
 
@@ -136,6 +140,11 @@ void pin_acquire(pfmbem* h) {
     }
   }
   if (g_pin.buf && !g_pin.owner) {
+    if (g_pin.pending) {
+      cudaEventSynchronize(g_pin.done);
+      cudaGetLastError();
+      g_pin.pending = false;
+    }
     g_pin.owner = h;
     h->ub_pin = g_pin.buf;
     h->ub_pin_cap = g_pin.cap;
@@ -148,6 +157,26 @@ void pin_release(pfmbem* h) {
   if (!h->pin_user) return;
   std::lock_guard<std::mutex> lk(g_pin.mu);
   if (g_pin.owner == h) g_pin.owner = nullptr;
+  h->ub_pin = nullptr;
+  h->pin_user = false;
+}
+
+// Lets go of the arena without waiting: the next holder waits for the event
+// recorded here (or, on another device, this create waits now).
+void pin_release_async(pfmbem* h) {
+  if (!h->pin_user) return;
+  std::lock_guard<std::mutex> lk(g_pin.mu);
+  if (g_pin.owner == h) {
+    bool queued = false;
+    if (!g_pin.done && cudaEventCreateWithFlags(&g_pin.done, cudaEventDisableTiming) == cudaSuccess)
+      g_pin.done_dev = h->dev;
+    if (g_pin.done && g_pin.done_dev == h->dev && cudaEventRecord(g_pin.done, h->stream) == cudaSuccess)
+      queued = true;
+    cudaGetLastError();
+    if (!queued) cudaStreamSynchronize(h->stream);
+    g_pin.pending = queued;
+    g_pin.owner = nullptr;
+  }
   h->ub_pin = nullptr;
   h->pin_user = false;
 }
@@ -1472,15 +1501,16 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
   }
   h->ub_on = false;
-  CK(cudaStreamSynchronize(h->stream));
-  trace_report(h);
-  pin_release(h);                  // every staged copy of this create has completed
-  {
-    int bad = 0;
-    CK(cudaMemcpy(&bad, h->tab_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (bad) return fail(h, PFMBEM_ENUMERIC, "non-finite M2L operator; lower p or change depth");
+  // The create returns without waiting for the device: the caller's next work
+  // queues behind the set-up on the same stream.  The operator check is read
+  // back asynchronously and reported by the first call that waits
+  // (check_ready).  With a timing mode on, the create waits here.
+  if (h->trace_on || timing) {
+    CK(cudaStreamSynchronize(h->stream));
+    trace_report(h);
+    mark("end of set-up");
   }
-  mark("end of set-up");
+  pin_release_async(h);
   h->info.E = E;
   h->info.M = M;
   h->info.depth = D;
@@ -1536,6 +1566,23 @@ static cplx* pinned_small_get() {
     return nullptr;
   }
   return static_cast<cplx*>(p);
+}
+
+// The first call after create that waits for the handle's stream reports the
+// set-up's operator check (non-finite M2L or root operator).
+static pfmbem_status ready_checked(pfmbem* h) {
+  if (h->ready) return PFMBEM_OK;
+  h->ready = true;
+  if (h->hstat && h->hstat[0])
+    return fail(h, PFMBEM_ENUMERIC, "non-finite M2L operator; lower p or change depth");
+  return PFMBEM_OK;
+}
+
+// Waits for the set-up of h once, then reports its operator check.
+static pfmbem_status check_ready(pfmbem* h) {
+  if (h->ready) return PFMBEM_OK;
+  CK(cudaStreamSynchronize(h->stream));
+  return ready_checked(h);
 }
 
 static void pinned_small_put(cplx* p) {
@@ -1914,6 +1961,11 @@ extern "C" {
 pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* psis, double tol, int maxit,
                                  pfmbem_info* infos) {
   if (ninst < 0 || (ninst > 0 && (!hs || !psis)) || !(tol > 0) || maxit < 1) return PFMBEM_EINVAL;
+  for (int i = 0; i < ninst; ++i)
+    if (hs[i] && !hs[i]->ready) {
+      const pfmbem_status rs = check_ready(hs[i]);
+      if (rs != PFMBEM_OK) return rs;
+    }
   std::vector<BInst> inst(ninst);
   const double t0 = now_ms();
   for (int i = 0; i < ninst; ++i) {
@@ -2050,8 +2102,16 @@ pfmbem_status pfmbem_create(int M, const int* nodes_per_fiber, const double* nod
     std::memcpy(nodes.data(), nodes_xy, sizeof(double) * 2 * tot);
   }
   *out = h;
-  return build_plan(h, npf.data(), nodes.data());
+  pfmbem_status st = build_plan(h, npf.data(), nodes.data());
+  if (st != PFMBEM_OK) return st;
+  h->hstat = reinterpret_cast<int*>(pinned_small_get());
+  if (!h->hstat) return fail(h, PFMBEM_ENOMEM, "pinned host buffer");
+  h->hstat[0] = 0;
+  CK(cudaMemcpyAsync(h->hstat, h->tab_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  h->ready = false;
+  return PFMBEM_OK;
 }
+
 
 void pfmbem_destroy(pfmbem_t h) {
   if (!h) return;
@@ -2063,6 +2123,7 @@ void pfmbem_destroy(pfmbem_t h) {
   else cudaDeviceSynchronize();
   pin_release(h);                  // a create that failed part-way
   pinned_small_put(h->gw.hhost);
+  pinned_small_put(reinterpret_cast<cplx*>(h->hstat));
   pool_put(h->dev, h->side_ev);
   pool_put(h->dev, h->pre_ev);
   pool_put(h->dev, h->side);
@@ -2081,6 +2142,7 @@ const char* pfmbem_last_error(pfmbem_t h) { return h ? h->err.c_str() : "null ha
 
 pfmbem_status pfmbem_plan(pfmbem_t h, pfmbem_plan_info* info) {
   if (!h || !info) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   if (h->cached && h->stat_dev) {
     unsigned long long c[4];
     CK(cudaMemcpyAsync(c, h->stat_dev, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
@@ -2099,6 +2161,7 @@ pfmbem_status pfmbem_plan(pfmbem_t h, pfmbem_plan_info* info) {
 
 pfmbem_status pfmbem_rhs(pfmbem_t h, double* B) {
   if (!h || !B) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   const size_t n = 2 * (size_t)h->E;
   if (is_device_ptr(B)) {
     CK(k_rhs(h, reinterpret_cast<cplx*>(B)));
@@ -2112,6 +2175,7 @@ pfmbem_status pfmbem_rhs(pfmbem_t h, double* B) {
 
 pfmbem_status pfmbem_matvec(pfmbem_t h, const double* x, double* y, int precision) {
   if (!h || !x || !y) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   if (precision != PFMBEM_FP64 && precision != PFMBEM_MIXED) return fail(h, PFMBEM_EINVAL, "precision");
   const size_t n = 2 * (size_t)h->E;
   const cplx* xd;
@@ -2247,23 +2311,34 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
   } else {
     st = gmres(h, g.b, g.x, tol, maxit, PFMBEM_FP64, &iters, &restarts, &relres, !use_guess);
   }
+  // the result and the device error flags come back in one wait
+  int* flags = h->hstat;            // [1] tensor-core M2L, [2] device-wide barrier
+  if (flags) {
+    flags[1] = flags[2] = 0;
+    if (h->tc_err) CK(cudaMemcpyAsync(flags + 1, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    if (h->fz_err) CK(cudaMemcpyAsync(flags + 2, h->fz_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  }
   CK(cudaMemcpyAsync(psi, g.x, n * sizeof(cplx), pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
-  if (h->tc_err) {
-    int e = 0;
-    CK(cudaMemcpy(&e, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) {
-      st = PFMBEM_ETIMEOUT;
-      h->err = "tensor-core M2L: a bounded wait for the MMA completion gave up";
-    }
+  {
+    const pfmbem_status rs = ready_checked(h);
+    if (rs != PFMBEM_OK) return rs;
   }
-  if (h->fz_err) {
-    int e = 0;
-    CK(cudaMemcpy(&e, h->fz_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) {
-      st = PFMBEM_ETIMEOUT;
-      h->err = "single-launch matvec: a bounded device-wide barrier wait gave up";
-    }
+  int tce = 0, fze = 0;
+  if (flags) {
+    tce = flags[1];
+    fze = flags[2];
+  } else {
+    if (h->tc_err) CK(cudaMemcpy(&tce, h->tc_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h->fz_err) CK(cudaMemcpy(&fze, h->fz_err, sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  if (tce) {
+    st = PFMBEM_ETIMEOUT;
+    h->err = "tensor-core M2L: a bounded wait for the MMA completion gave up";
+  }
+  if (fze) {
+    st = PFMBEM_ETIMEOUT;
+    h->err = "single-launch matvec: a bounded device-wide barrier wait gave up";
   }
   if (info) {
     info->iters = iters;
@@ -2278,6 +2353,7 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
 
 pfmbem_status pfmbem_lattice_sums(pfmbem_t h, int jmax, double* S) {
   if (!h || !S || jmax < 0 || jmax > 2 * PF_PMAX) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   cplx* Sd = h->stage_out;
   if ((size_t)(jmax + 1) > 2 * (size_t)h->E) return fail(h, PFMBEM_EINVAL, "jmax too large for the work buffer");
   CK(k_lattice_sums(h, jmax, h->lattice_q, Sd));
@@ -2300,6 +2376,7 @@ pfmbem_status pfmbem_lattice_sums(pfmbem_t h, int jmax, double* S) {
 
 pfmbem_status pfmbem_self_terms(pfmbem_t h, double* out) {
   if (!h || !out) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   const size_t n = 4 * (size_t)h->E;
   CK(cudaMemcpyAsync(out, h->self4, n * sizeof(cplx), is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                      h->stream));
@@ -2350,18 +2427,21 @@ pfmbem_status field_points(pfmbem* h, const double* psi, int npts, const double*
 
 pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double* pts, double* u) {
   if (!h || !psi || npts < 0 || (npts > 0 && (!pts || !u))) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   if (npts == 0) return PFMBEM_OK;
   return field_points(h, psi, npts, pts, u, nullptr);
 }
 
 pfmbem_status pfmbem_field_dx1(pfmbem_t h, const double* psi, int npts, const double* pts, double* u, double* dudx1) {
   if (!h || !psi || npts < 0 || (npts > 0 && (!pts || (!u && !dudx1)))) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   if (npts == 0) return PFMBEM_OK;
   return field_points(h, psi, npts, pts, u, dudx1);
 }
 
 pfmbem_status pfmbem_etc(pfmbem_t h, const double* psi, double x1, int npts, double* etc) {
   if (!h || !psi || !etc || npts < 1 || !std::isfinite(x1)) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   // midpoint rule over one period; |du/dx1| is periodic along x2
   std::vector<double> pts(2 * (size_t)npts);
   for (int i = 0; i < npts; ++i) {
@@ -2386,6 +2466,7 @@ pfmbem_status pfmbem_etc(pfmbem_t h, const double* psi, double x1, int npts, dou
 pfmbem_status pfmbem_coefficients(pfmbem_t h, const double* psi, int max_orders, int* norders, int* orders, double* R,
                                   double* T, double* energy) {
   if (!h || !psi || !norders || max_orders < 0) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   const double ks = h->k * std::sin(h->theta);
   std::vector<int> ord;
   int nlo = (int)std::floor((-h->k - ks) * h->H / (2 * M_PI)) - 1;
@@ -2429,6 +2510,7 @@ pfmbem_status pfmbem_coefficients(pfmbem_t h, const double* psi, int max_orders,
 
 pfmbem_status pfmbem_warm_features(pfmbem_t h, float* x) {
   if (!h || !x) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   const size_t nx = 2 + 3 * (size_t)h->M;
   const bool dev = is_device_ptr(x);
   float* xd = dev ? x : reinterpret_cast<float*>(h->stage_out);
@@ -2443,6 +2525,7 @@ pfmbem_status pfmbem_warm_features(pfmbem_t h, float* x) {
 
 pfmbem_status pfmbem_warm_features_local(pfmbem_t h, int K, float* x) {
   if (!h || !x || K < 0 || K > 32) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   const size_t nx = (size_t)h->M * (5 + 3 * K);
   const bool dev = is_device_ptr(x);
   float* xd = dev ? x : dalloc_tmp<float>(h, nx);
@@ -2459,6 +2542,7 @@ pfmbem_status pfmbem_warm_features_local(pfmbem_t h, int K, float* x) {
 
 pfmbem_status pfmbem_warm_targets(pfmbem_t h, int nmodes, const double* psi, float* t) {
   if (!h || !psi || !t || nmodes < 0 || nmodes > 64) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   const size_t n = 2 * (size_t)h->E, nt = (size_t)h->M * 2 * (2 * nmodes + 1) * 2;
   const cplx* pd;
   pfmbem_status st = stage_input(h, psi, n, h->stage_in, &pd);
@@ -2478,6 +2562,7 @@ pfmbem_status pfmbem_warm_targets(pfmbem_t h, int nmodes, const double* psi, flo
 
 pfmbem_status pfmbem_warm_decode(pfmbem_t h, int nmodes, const float* y, double* psi0) {
   if (!h || !y || !psi0 || nmodes < 0 || nmodes > 64) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   const size_t n = 2 * (size_t)h->E, ny = (size_t)h->M * 2 * (2 * nmodes + 1) * 2;
   const bool ydev = is_device_ptr(y);
   float* yd = const_cast<float*>(y);
@@ -2500,6 +2585,7 @@ pfmbem_status pfmbem_warm_decode(pfmbem_t h, int nmodes, const float* y, double*
 
 pfmbem_status pfmbem_profile(pfmbem_t h, int enable_timing, int reset) {
   if (!h) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   CK(prof_fold(h));
   if (reset) {
     for (int i = 0; i < 32; ++i) {
@@ -2513,6 +2599,7 @@ pfmbem_status pfmbem_profile(pfmbem_t h, int enable_timing, int reset) {
 
 pfmbem_status pfmbem_profile_read(pfmbem_t h, pfmbem_profile_info* out) {
   if (!h || !out) return PFMBEM_EINVAL;
+  if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
   CK(cudaStreamSynchronize(h->stream));
   CK(prof_fold(h));
   int64_t tot = 0;

@@ -295,6 +295,8 @@ struct pfmbem {
     size_t used = 0, cap = 0;
   };
   std::vector<Carve> carves;
+  int* hstat = nullptr;          // page-locked: the set-up's operator check, read back at create
+  bool ready = true;             // the set-up has been waited for and its check reported
   // set-up trace (PFMBEM_TIMING=3): timing events recorded on the set-up streams
   bool trace_on = false;
   std::vector<const char*> trace_lbl;
