@@ -283,7 +283,7 @@ pfmbem_status pfmbem_profile_read(pfmbem_t h, pfmbem_profile_info* out);
  * that is being recorded into a CUDA graph by stream capture (allocation calls
  * are not allowed while a stream is capturing), code that runs under another
  * framework's fixed memory pool or budget, and latency-critical loops that must
- * not enter the driver's allocator.  This entry point computes the same S_j as
+ * not enter the CUDA allocator.  This entry point computes the same S_j as
  * pfmbem_lattice_sums for (k, H, theta) without a handle and without allocating:
  * its device results go to one fixed array of 129 complex numbers that is part
  * of the library itself (every GPU that loads the library holds it, 2 KiB,

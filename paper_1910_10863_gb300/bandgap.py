@@ -1,7 +1,7 @@
 """Band-gap sweep of Sec. 4: energy transmission coefficient against frequency.
 
 For the water/mercury square-lattice crystal of Table 3 (workloads.table3_square)
-the driver solves one block per normalised frequency ka/2pi (mixed precision,
+this script solves one block per normalised frequency ka/2pi (mixed precision,
 FP64 residual 1e-6), evaluates ETC on the block's right edge x1 = 4a with
 pfmbem_etc, and reports the frequency intervals where ETC < 3 %, the stop-band
 criterion of Sec. 4.  Frequencies within 1e-3 of a Wood anomaly (ka/2pi = n/6 at
