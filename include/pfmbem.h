@@ -279,24 +279,29 @@ pfmbem_status pfmbem_profile(pfmbem_t h, int enable_timing, int reset);
 pfmbem_status pfmbem_profile_read(pfmbem_t h, pfmbem_profile_info* out);
 
 /* Lattice sums without any device allocation (the paper has no counterpart;
- * this is a library convenience).  Some callers cannot call cudaMalloc: code
- * that is being recorded into a CUDA graph by stream capture (allocation calls
- * are not allowed while a stream is capturing), code that runs under another
- * framework's fixed memory pool or budget, and latency-critical loops that must
- * not enter the CUDA allocator.  This entry point computes the same S_j as
- * pfmbem_lattice_sums for (k, H, theta) without a handle and without allocating:
- * its device results go to one fixed array of 129 complex numbers that is part
- * of the library itself (every GPU that loads the library holds it, 2 KiB,
- * until the process exits).
+ * this is a library convenience).  Some callers cannot call cudaMalloc:
+ * plug-ins that run inside a host application which has already reserved the
+ * device memory for its own pool or budget (a cudaMalloc there fails, or makes
+ * the host release cached memory behind its back), and latency-critical loops
+ * that must not enter the CUDA allocator, whose calls may synchronise the
+ * device.  This entry point computes the same S_j as pfmbem_lattice_sums for
+ * (k, H, theta) without a handle and without allocating: its device results go
+ * to one fixed array of 129 complex numbers that is part of the library itself
+ * (every GPU that loads the library holds it, 2 KiB, until the process exits).
  *   jmax    0 .. 128; larger values return PFMBEM_EINVAL
- *   S       complex [2 jmax + 1], index j + jmax, host or device memory; with a
- *           device pointer the call only enqueues work on cuda_stream, with a
- *           host pointer it waits for the result
- * The first call on each device performs a one-time set-up there (copies the
- * Gauss rules to the library's constant memory and looks up the array's device
- * address); make that first call before any stream capture begins.  All calls
- * share the one array, so calls whose GPU work overlaps (different streams or
- * host threads on the same device) race with each other: serialise them.
+ *   S       complex [2 jmax + 1], index j + jmax, host or device memory; a
+ *           device buffer must belong to the current device (PFMBEM_EINVAL
+ *           otherwise, before any GPU work); with a device pointer the call
+ *           only enqueues work on cuda_stream, with a host pointer it waits for
+ *           the result
+ * The first call on each device performs a one-time set-up there, with that
+ * device current (copies the Gauss rules to the library's constant memory and
+ * looks up the array's device address with cudaGetSymbolAddress); make that
+ * first call before any stream capture begins.  Host threads that make their
+ * first calls together run the set-up once.  All calls share the one array and
+ * it keeps the last call's contents (each call clears what it accumulates into
+ * before use), so calls whose GPU work overlaps (different streams or host
+ * threads on the same device) race with each other: serialise them.
  * Returns EWOOD/EINVAL/ECUDA as pfmbem_create does. */
 pfmbem_status pfmbem_lattice_sums_noalloc(double k, double H, double theta, int jmax, void* cuda_stream,
                                           double* S);

@@ -40,11 +40,15 @@ def image_field_coeffs(k, beta, H, rho, lmax, npts=None):
     return ls, c[ls % npts]
 
 
-def lattice_sums(k, beta, H, jmax, rho=None):
-    """S_j for j in [-jmax, jmax] from the Fourier coefficients of the image field."""
+def lattice_sums(k, beta, H, jmax, rho=None, npts=None):
+    """S_j for j in [-jmax, jmax] from the Fourier coefficients of the image field.
+
+    The nearest excluded images sit at distance 2H, so the coefficients decay
+    like (rho / 2H)^|l|: a circle close to that limit (rho = 1.9 H with a few
+    thousand points) keeps the high orders (|j| ~ 100) accurate."""
     if rho is None:
         rho = 0.75 * H
-    ls, c = image_field_coeffs(k, beta, H, rho, jmax)
+    ls, c = image_field_coeffs(k, beta, H, rho, jmax, npts)
     Jl = sp.jv(ls, k * rho)
     S_minus_l = 4.0 * c / (1j * Jl)
     # S_j with j = -l

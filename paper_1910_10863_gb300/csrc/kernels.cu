@@ -8,7 +8,9 @@
 // K2b varphi (all fibers and their images, wavenumber k, eqs. 7-8).  U and dU
 // come from the periodic FMM of Sec. 3 (near field + P2M/M2M/M2L/L2L/L2P +
 // lattice-sum root translation), V and dV from a fiber-local direct sum.
+#include <atomic>
 #include <cstdio>
+#include <mutex>
 
 #include "internal.h"
 
@@ -424,8 +426,11 @@ cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev) {
 // allocates.  Every GPU that loads the library holds the array until exit.
 #define PF_NOALLOC_JMAX 128
 static __device__ __align__(256) cplx g_lattice_scratch[PF_NOALLOC_JMAX + 1];
-static cplx* g_lattice_scratch_dev[64];    // device address of the array, per device ordinal
-static bool g_lattice_scratch_ready[64];
+// Device address of the array per device ordinal, published with release order
+// once that device's set-up is complete (null until then); the mutex makes two
+// host threads that call first on one device run the set-up once.
+static std::atomic<cplx*> g_lattice_scratch_dev[64];
+static std::mutex g_lattice_scratch_mutex;
 
 __global__ void symmetric_expand_kernel(const cplx* __restrict__ half, int jmax, cplx* __restrict__ full) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -445,29 +450,35 @@ extern "C" pfmbem_status pfmbem_lattice_sums_noalloc(double k, double H, double 
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return PFMBEM_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
-  if (!g_lattice_scratch_ready[dev]) {
+  // A device output must live on the current device: the kernels below run there.
+  cudaPointerAttributes a;
+  const bool attr_ok = cudaPointerGetAttributes(&a, S) == cudaSuccess;
+  cudaGetLastError();
+  const bool sdev = attr_ok && (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
+  if (attr_ok && a.type == cudaMemoryTypeDevice && a.device != dev) return PFMBEM_EINVAL;
+  cplx* scratch = g_lattice_scratch_dev[dev].load(std::memory_order_acquire);
+  if (!scratch) {
     // one-time set-up on this device: Gauss rules for the contour integral and
     // the device address of the fixed array (host code may not use its name)
-    double x[PF_GLMAX * PF_GLMAX] = {0}, w[PF_GLMAX * PF_GLMAX] = {0};
-    for (int g = 1; g <= PF_GLMAX; ++g) gauss_legendre(g, &x[(g - 1) * PF_GLMAX], &w[(g - 1) * PF_GLMAX]);
-    if (cudaMemcpyToSymbol(c_glx, x, sizeof(x)) != cudaSuccess) return PFMBEM_ECUDA;
-    if (cudaMemcpyToSymbol(c_glw, w, sizeof(w)) != cudaSuccess) return PFMBEM_ECUDA;
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_lattice_scratch) != cudaSuccess) return PFMBEM_ECUDA;
-    g_lattice_scratch_dev[dev] = static_cast<cplx*>(p);
-    g_lattice_scratch_ready[dev] = true;
+    std::lock_guard<std::mutex> lock(g_lattice_scratch_mutex);
+    scratch = g_lattice_scratch_dev[dev].load(std::memory_order_acquire);
+    if (!scratch) {
+      double x[PF_GLMAX * PF_GLMAX] = {0}, w[PF_GLMAX * PF_GLMAX] = {0};
+      for (int g = 1; g <= PF_GLMAX; ++g) gauss_legendre(g, &x[(g - 1) * PF_GLMAX], &w[(g - 1) * PF_GLMAX]);
+      if (cudaMemcpyToSymbol(c_glx, x, sizeof(x)) != cudaSuccess) return PFMBEM_ECUDA;
+      if (cudaMemcpyToSymbol(c_glw, w, sizeof(w)) != cudaSuccess) return PFMBEM_ECUDA;
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_lattice_scratch) != cudaSuccess || !p) return PFMBEM_ECUDA;
+      scratch = static_cast<cplx*>(p);
+      g_lattice_scratch_dev[dev].store(scratch, std::memory_order_release);
+    }
   }
-  cplx* scratch = g_lattice_scratch_dev[dev];
   const int q = 8;
   const double beta = k * H * sin(theta);
   const double V = lattice_vmax(jmax, q, k, H);
   if (cudaMemsetAsync(scratch, 0, sizeof(cplx) * (jmax + 1), st) != cudaSuccess) return PFMBEM_ECUDA;
   lattice_sum_kernel<<<jmax + 1, 256, 0, st>>>(jmax, q, k, H, beta, V, scratch);
   if (cudaGetLastError() != cudaSuccess) return PFMBEM_ECUDA;
-  cudaPointerAttributes a;
-  bool sdev = cudaPointerGetAttributes(&a, S) == cudaSuccess &&
-              (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged);
-  cudaGetLastError();
   if (sdev) {
     symmetric_expand_kernel<<<(2 * jmax + 1 + 127) / 128, 128, 0, st>>>(scratch, jmax, reinterpret_cast<cplx*>(S));
     if (cudaGetLastError() != cudaSuccess) return PFMBEM_ECUDA;

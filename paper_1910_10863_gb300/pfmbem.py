@@ -169,7 +169,19 @@ def pfmbem_lattice_sums(h, jmax, S):
 
 
 def pfmbem_lattice_sums_noalloc(k, H, theta, jmax, S, stream=None):
-    """Lattice sums without a handle or any device allocation (see include/pfmbem.h)."""
+    """Lattice sums without a handle or any device allocation (see include/pfmbem.h).
+
+    S must be a contiguous complex128 torch tensor or numpy array with at least
+    2 jmax + 1 entries: the library writes that many values unconditionally."""
+    if isinstance(S, np.ndarray):
+        ok = S.dtype == np.complex128 and S.flags.c_contiguous and S.size >= 2 * int(jmax) + 1
+    elif hasattr(S, "data_ptr"):
+        import torch
+        ok = S.dtype == torch.complex128 and S.is_contiguous() and S.numel() >= 2 * int(jmax) + 1
+    else:
+        ok = False
+    if not ok:
+        raise ValueError("S must be a contiguous complex128 buffer of at least 2*jmax+1 entries")
     st = lib().pfmbem_lattice_sums_noalloc(float(k), float(H), float(theta), int(jmax), stream, addr(S))
     if st != 0:
         raise PfmbemError(st, "pfmbem_lattice_sums_noalloc failed")

@@ -52,18 +52,24 @@ def test_self_terms(pf, make):
         assert np.max(np.abs(got[:, col] - ref) / np.abs(ref)) < 1e-12
 
 
-@pytest.mark.parametrize("kH,theta", [(2.0, math.radians(30)), (5.0, 0.3), (20.0, math.radians(30))])
-def test_lattice_sums(pf, kH, theta):
+@pytest.mark.parametrize("kH,theta,jmax,rho", [(2.0, math.radians(30), 24, 0.75), (5.0, 0.3, 24, 0.75),
+                                                (20.0, math.radians(30), 24, 0.75),
+                                                (20.0, math.radians(30), 108, 1.9),
+                                                (5.0, 0.3, 64, 1.9)])
+def test_lattice_sums(pf, kH, theta, jmax, rho):
+    """jmax = 108 is the largest order the 32x32 block's root translation uses
+    (2 p0 at kH = 20); on the circle rho = 1.9 H every order up to it carries
+    weight, so each one is checked, not only the low ones."""
     w = W.square_2x2_n64()
     w.k = kH / w.H
     w.k1 = w.k * 1490 / 1450
     w.theta = theta
     s = pf.Solver(w, p=12, depth=2)
-    jmax = 24
     S = np.zeros(2 * jmax + 1, dtype=np.complex128)
     pf.pfmbem_lattice_sums(s.h, jmax, S)
-    js, ref = lattice.lattice_sums(w.k, w.k * w.H * math.sin(theta), w.H, jmax, rho=0.75 * w.H)
-    wgt = np.abs(sp.jv(js, w.k * 0.75 * w.H))
+    js, ref = lattice.lattice_sums(w.k, w.k * w.H * math.sin(theta), w.H, jmax, rho=rho * w.H,
+                                   npts=8192 if rho > 1 else None)
+    wgt = np.abs(sp.jv(js, w.k * rho * w.H))
     err = np.max(np.abs(S - ref) * wgt) / np.max(np.abs(ref) * wgt)
     assert err < 1e-10, err
 

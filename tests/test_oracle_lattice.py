@@ -38,3 +38,23 @@ def test_lattice_sums_independent_of_circle_radius():
         js, a = lattice.lattice_sums(k, beta, H, 16, rho=0.6 * H)
         _, b = lattice.lattice_sums(k, beta, H, 16, rho=0.9 * H)
         assert _weighted(js, a, b, k, 0.6 * H) < 1e-11
+
+
+def test_high_orders_match_direct_sum_in_absorbing_medium():
+    """Orders up to 108 (twice the root order of the 32x32 block at kH = 20), each
+    on its own: the circle at 1.9 H keeps every coefficient well above rounding."""
+    H = 1.0
+    k = 20.0 + 0.5j
+    beta = k * H * math.sin(math.radians(30))
+    js, S = lattice.lattice_sums(k, beta, H, 108, rho=1.9 * H, npts=8192)
+    _, D = lattice.direct_sum(k, beta, H, 108, 300)
+    assert np.max(np.abs(S - D) / np.abs(D)) < 1e-11
+
+
+def test_high_orders_independent_of_circle_radius():
+    H = 1.0
+    k = 20.0
+    beta = k * H * math.sin(math.radians(30))
+    js, a = lattice.lattice_sums(k, beta, H, 108, rho=1.9 * H, npts=8192)
+    _, b = lattice.lattice_sums(k, beta, H, 108, rho=1.75 * H, npts=8192)
+    assert _weighted(js, a, b, k, 1.75 * H) < 1e-11
