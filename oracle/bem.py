@@ -267,13 +267,27 @@ def operator_rows(pb: Problem, rows_e=None):
     s1, d1, kk1, t1 = pair_integrals(k1k, el, ti[idx], sj[idx])
     S1[idx], D1[idx], K1[idx], T1[idx] = s1, d1, kk1, t1
     S1, D1, K1, T1 = [a.reshape(R, E) for a in (S1, D1, K1, T1)]
+    return assemble(pb, rows_e, dict(S1=S1, D1=D1, K1=K1, T1=T1, S2=S2, D2=D2, K2=K2, T2=T2))
+
+
+def assemble(pb: Problem, rows_e, ops):
+    """The rows of (I - A) of eq. 9 from the discrete layer operators.
+
+    ops holds [R, E] arrays: S1, D1, K1, T1 (wavenumber k1, same fiber only, zero
+    elsewhere) and S2, D2, K2, T2 (the barred quasi-periodic operators at k, or
+    free-space ones when the problem is not periodic); entry [r, e] is the
+    operator's weight of unknown e at collocation point rows_e[r].  Row 2r carries
+    the first equation of eq. 8, row 2r+1 the second scaled by
+    c2 = 2 / (i eta (1 + rho)), so that both have the identity on the diagonal."""
+    E = pb.el.E
+    R = len(rows_e)
     ie = 1j * pb.eta
     c2 = pb.c2
     M = np.zeros((2 * R, 2 * E), dtype=np.complex128)
-    M[0::2, 0::2] = -D1 + D2
-    M[0::2, 1::2] = ie * S1 - ie * S2
-    M[1::2, 0::2] = c2 * (T2 - pb.rho * T1)
-    M[1::2, 1::2] = c2 * (-ie * K2 + pb.rho * ie * K1)
+    M[0::2, 0::2] = -ops["D1"] + ops["D2"]
+    M[0::2, 1::2] = ie * ops["S1"] - ie * ops["S2"]
+    M[1::2, 0::2] = c2 * (ops["T2"] - pb.rho * ops["T1"])
+    M[1::2, 1::2] = c2 * (-ie * ops["K2"] + pb.rho * ie * ops["K1"])
     for r, e in enumerate(rows_e):
         M[2 * r, 2 * e] += 1.0
         M[2 * r + 1, 2 * e + 1] += 1.0
@@ -301,36 +315,57 @@ def solve(pb: Problem, M=None, B=None):
     return sla.lu_solve(lu, B)
 
 
-def potential(pb: Problem, psi, pts, interior_fiber=None):
+def quadrature(pb: Problem, nq=16):
+    """Source points of the boundary integrals: points y [Q, 2], normals [Q, 2],
+    weights [Q] and the unknown (element or node) each point carries.
+
+    Constant elements: nq Gauss-Legendre nodes per element.  A discretisation
+    whose unknowns are point values with their own weights (the Nystrom mode of
+    ``nystrom``) brings them along as el.w."""
+    el = pb.el
+    if hasattr(el, "w"):
+        return el.c, el.nu, el.w, np.arange(el.E)
+    u, w = np.polynomial.legendre.leggauss(nq)
+    s = 0.5 * u[None, :] * el.h[:, None]
+    y = np.stack([(el.c[:, 0][:, None] + s * el.t[:, 0][:, None]).ravel(),
+                  (el.c[:, 1][:, None] + s * el.t[:, 1][:, None]).ravel()], axis=1)
+    nu = np.repeat(el.nu, nq, axis=0)
+    wq = (0.5 * w[None, :] * el.h[:, None]).ravel()
+    return y, nu, wq, np.repeat(np.arange(el.E), nq)
+
+
+def potential(pb: Problem, psi, pts, interior_fiber=None, grad=False, nq=32):
     """Scattered field u^s (eq. 4/7) at points pts [P,2] outside all fibers, or the
-    interior field u_i (eq. 5) of fiber ``interior_fiber`` at points inside it."""
+    interior field u_i (eq. 5) of fiber ``interior_fiber`` at points inside it.
+
+    With grad=True also returns du/dx1 at the points (the x1-derivative of the
+    layer kernels: d/dx1 of Phi is g1, of its nu_y-derivative -(g11 nu1 + g12 nu2))."""
     el = pb.el
     pts = np.asarray(pts, dtype=np.float64)
     phi = psi[0::2]
     vphi = psi[1::2]
+    y, nu, wq, idx = quadrature(pb, nq)
     if interior_fiber is None:
         ker = Kernel(pb.k, periodic=pb.periodic, beta=pb.beta, H=pb.H)
-        src = np.arange(el.E)
     else:
         ker = Kernel(pb.k1, periodic=False)
-        src = np.nonzero(el.fiber == interior_fiber)[0]
-    u, w = np.polynomial.legendre.leggauss(32)
+        keep = el.fiber[idx] == interior_fiber
+        y, nu, wq, idx = y[keep], nu[keep], wq[keep], idx[keep]
     out = np.zeros(len(pts), dtype=np.complex128)
+    dout = np.zeros(len(pts), dtype=np.complex128)
     for p, x in enumerate(pts):
-        s = 0.5 * u[None, :] * el.h[src][:, None]
-        y1 = el.c[src, 0][:, None] + s * el.t[src, 0][:, None]
-        y2 = el.c[src, 1][:, None] + s * el.t[src, 1][:, None]
-        z1 = (x[0] - y1).ravel()
-        z2 = (x[1] - y2).ravel()
+        z1 = x[0] - y[:, 0]
+        z2 = x[1] - y[:, 1]
         if ker.periodic:
             d = greens.qp_ewald(ker.kappa, ker.beta, pb.H, z1, z2)
         else:
             d = greens.free_space(ker.kappa, z1, z2)
-        nyr = (np.repeat(el.nu[src, 0], u.size), np.repeat(el.nu[src, 1], u.size))
-        Sk, Dk, _, _ = greens.layer_kernels(d, nyr, nyr)
-        wq = (0.5 * w[None, :] * el.h[src][:, None]).ravel()
-        out[p] = np.sum(wq * (Dk * np.repeat(phi[src], u.size) - 1j * pb.eta * Sk * np.repeat(vphi[src], u.size)))
-    return out
+        Dk = -(d["g1"] * nu[:, 0] + d["g2"] * nu[:, 1])
+        out[p] = np.sum(wq * (Dk * phi[idx] - 1j * pb.eta * d["g"] * vphi[idx]))
+        if grad:
+            dD = -(d["g11"] * nu[:, 0] + d["g12"] * nu[:, 1])
+            dout[p] = np.sum(wq * (dD * phi[idx] - 1j * pb.eta * d["g1"] * vphi[idx]))
+    return (out, dout) if grad else out
 
 
 def bragg_orders(pb: Problem):
@@ -343,17 +378,15 @@ def bragg_orders(pb: Problem):
 
 def rayleigh(pb: Problem, psi, orders=None):
     """Reflection R_n and transmission T_n of the Bragg orders n (plane-wave amplitudes of
-    the total field left and right of the block), from the spectral form of G_qp."""
-    el = pb.el
+    the total field left and right of the block), from the spectral form of G_qp:
+    right of every source u^s = sum_n (T_n - delta_n0) e^{i(kx_n x1 + ky_n x2)}, left of
+    them u^s = sum_n R_n e^{i(-kx_n x1 + ky_n x2)}, with ky_n = k sin(theta) + 2 pi n / H and
+    kx_n = sqrt(k^2 - ky_n^2) (Im kx_n >= 0 for the evanescent orders)."""
     if orders is None:
         orders = bragg_orders(pb)
     phi = psi[0::2]
     vphi = psi[1::2]
-    u, w = _GL16
-    s = 0.5 * u[None, :] * el.h[:, None]
-    y1 = el.c[:, 0][:, None] + s * el.t[:, 0][:, None]
-    y2 = el.c[:, 1][:, None] + s * el.t[:, 1][:, None]
-    wq = 0.5 * w[None, :] * el.h[:, None]
+    y, nu, wq, idx = quadrature(pb, 16)
     R = []
     T = []
     for n in orders:
@@ -362,9 +395,9 @@ def rayleigh(pb: Problem, psi, orders=None):
         pref = 1j / (2 * pb.H * kx)
         out = []
         for sgn in (+1, -1):
-            e = np.exp(-1j * (sgn * kx * y1 + ky * y2))
-            dn = -1j * (sgn * kx * el.nu[:, 0][:, None] + ky * el.nu[:, 1][:, None]) * e
-            out.append(pref * np.sum(wq * (dn * phi[:, None] - 1j * pb.eta * e * vphi[:, None])))
+            e = np.exp(-1j * (sgn * kx * y[:, 0] + ky * y[:, 1]))
+            dn = -1j * (sgn * kx * nu[:, 0] + ky * nu[:, 1]) * e
+            out.append(pref * np.sum(wq * (dn * phi[idx] - 1j * pb.eta * e * vphi[idx])))
         T.append((1.0 if n == 0 else 0.0) + out[0])
         R.append(out[1])
     return np.asarray(orders), np.array(R), np.array(T)
@@ -381,15 +414,24 @@ def energy(pb: Problem, orders, R, T):
     return tot
 
 
+def etc_points(pb: Problem, npts):
+    """Midpoints x2 = H (j + 1/2) / npts of the ETC line integral over one period."""
+    return pb.H * (np.arange(npts) + 0.5) / npts
+
+
 def etc(pb: Problem, psi, nmax=20, npts=512, x1=None):
     """Energy transmission coefficient (Sec. 4): (1/kH) int_0^H |du/dx1(L, x2)| dx2 with
-    L the right edge of the block (x1, default the right-most node), from the
-    Rayleigh expansion to the right."""
+    L the right edge of the block (x1, default the right-most node) and u the total
+    field, from the Rayleigh expansion to the right (orders -nmax..nmax), by the
+    midpoint rule with npts points."""
     el = pb.el
-    L = float(np.max(np.concatenate([el.a[:, 0], el.b[:, 0]]))) if x1 is None else float(x1)
+    if x1 is None:
+        L = float(np.max(el.b[:, 0])) if hasattr(el, "b") else float(np.max(el.c[:, 0]))
+    else:
+        L = float(x1)
     orders = np.arange(-nmax, nmax + 1)
     ordr, _, T = rayleigh(pb, psi, orders)
-    x2 = pb.H * (np.arange(npts) + 0.5) / npts
+    x2 = etc_points(pb, npts)
     du = np.zeros(npts, dtype=np.complex128)
     for n, t in zip(ordr, T):
         ky = pb.k * math.sin(pb.theta) + 2 * math.pi * n / pb.H

@@ -177,3 +177,33 @@ def layer_kernels(d, nx, ny):
     K = d["g1"] * nx[0] + d["g2"] * nx[1]
     T = -(nx[0] * (d["g11"] * ny[0] + d["g12"] * ny[1]) + nx[1] * (d["g12"] * ny[0] + d["g22"] * ny[1]))
     return S, D, K, T
+
+
+def qp_remainder_at_origin(k, beta, H, npts=256):
+    """R = G_qp - Phi (all images m != 0) and its z-derivatives at z = 0.
+
+    R is smooth in |z| < H and solves the Helmholtz equation there, so by Graf's
+    theorem (eq. 10) it has the local expansion R(z) = (i/4) sum_l S'_{-l}
+    J_l(k|z|) e^{i l psi} with S'_j = sum_{m != 0} alpha^m H_j(k|m|H) e^{i j theta_{-mh}}.
+    The coefficients S'_l for |l| <= 2 come from the Fourier coefficients of R on a
+    circle of radius rho < H (chosen away from the zeros of J_0, J_1, J_2), and the
+    value, gradient and Hessian at 0 follow from J_0 = 1 - (kr)^2/4, J_{+-1} e^{+-i psi}
+    = +-(k/2)(z1 +- i z2), J_{+-2} e^{+-2i psi} = (k^2/8)(z1 +- i z2)^2 to second order."""
+    cands = H * np.linspace(0.25, 0.6, 15)
+    score = [min(abs(sp.jv(l, k * r)) for l in (0, 1, 2)) for r in cands]
+    rho = float(cands[int(np.argmax(score))])
+    psi = 2 * math.pi * np.arange(npts) / npts
+    z1 = rho * np.cos(psi)
+    z2 = rho * np.sin(psi)
+    Rz = qp_ewald(k, beta, H, z1, z2)["g"] - free_space(k, z1, z2)["g"]
+    c = np.fft.fft(Rz) / npts
+    # S'_{-l} = 4 c_l / (i J_l(k rho))
+    Sp = {-l: 4.0 * c[l % npts] / (1j * sp.jv(l, k * rho)) for l in (-2, -1, 0, 1, 2)}
+    q = 0.25j
+    g = q * Sp[0]
+    g1 = q * 0.5 * k * (Sp[-1] - Sp[1])
+    g2 = q * 0.5j * k * (Sp[-1] + Sp[1])
+    g11 = q * (-0.5 * k * k * Sp[0] + 0.25 * k * k * (Sp[-2] + Sp[2]))
+    g22 = q * (-0.5 * k * k * Sp[0] - 0.25 * k * k * (Sp[-2] + Sp[2]))
+    g12 = q * 0.25j * k * k * (Sp[-2] - Sp[2])
+    return dict(g=g, g1=g1, g2=g2, g11=g11, g12=g12, g22=g22)

@@ -12,7 +12,7 @@
   fiber with period H/2 and Bloch phase exp(i k (H/2) sin theta) -- an exact
   identity of the discrete systems;
 * no contrast (k1 = k, rho = 1): no reflection up to discretisation error;
-* Table 1 (Sec. 3.2): gamma and lambda of the square tree.
+* the Mie series itself: the transmission conditions of eq. 2 on the circle.
 """
 import math
 
@@ -118,30 +118,26 @@ def test_no_contrast_no_reflection():
     assert abs(abs(T[list(o).index(0)]) - 1.0) < 5e-3
 
 
-def _gamma_lambda(offset, size_c, d=1.0):
-    """gamma, lambda of Theorems 1-2 for a target cell D (side d) whose centre is at
-    `offset` from the centre of a source cell C of side size_c."""
-    rC = size_c / math.sqrt(2.0)
-    rD = d / math.sqrt(2.0)
-    ox, oy = offset
-    # nearest point of D to O_C (axis-aligned cells)
-    nx = max(abs(ox) - d / 2, 0.0)
-    ny = max(abs(oy) - d / 2, 0.0)
-    gamma = rC / math.hypot(nx, ny)
-    R = math.hypot(ox, oy)
-    lam = rD / R * math.exp(1.5 * rC / R)
-    return gamma, lam
+def test_mie_series_satisfies_the_transmission_conditions():
+    """u_inc + u^s = u_i and d/dr (u_inc + u^s) = rho d/dr u_i on r = R (eq. 2,
+    rho = rho_matrix / rho_fiber), by central differences across the circle."""
+    k, th, R = 3.0, 0.4, 0.5
+    k1, rho = k * 1490 / 1450, 1000 / 13600
+    ang = np.linspace(0, 2 * math.pi, 11, endpoint=False)
 
+    def total(r):
+        p = np.stack([r * np.cos(ang), r * np.sin(ang)], axis=1)
+        return np.exp(1j * k * (p @ np.array([math.cos(th), math.sin(th)]))) + mie.scattered(k, k1, rho, R, th, p)
 
-@pytest.mark.parametrize("L,offset,size_c,gamma,lam", [
-    (0, (2.0, 0.0), 1.0, 0.4714, 0.6009),
-    (1, (2.5, 0.5), 2.0, 0.7071, 0.6374),
-    (2, (3.5, 0.5), 4.0, 0.9428, 0.6640),
-])
-def test_table1_square_tree(L, offset, size_c, gamma, lam):
-    g, l = _gamma_lambda(offset, size_c)
-    assert round(g, 4) == gamma
-    assert round(l, 4) == lam
+    def inner(r):
+        p = np.stack([r * np.cos(ang), r * np.sin(ang)], axis=1)
+        return mie.interior(k, k1, rho, R, th, p)
+
+    assert np.max(np.abs(total(R) - inner(R))) < 1e-12
+    e = 1e-5
+    dout = (total(R + e) - total(R - e)) / (2 * e)
+    din = (inner(R + e) - inner(R - e)) / (2 * e)
+    assert np.max(np.abs(dout - rho * din)) < 1e-7 * np.max(np.abs(dout))
 
 
 def test_mlp_oracle_gradient_matches_finite_differences():
