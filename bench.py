@@ -39,13 +39,17 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="own", choices=["own", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
-    ap.add_argument("--fp64-steps", type=int, default=2, help="steps of the plain FP64 comparator arm")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="steps of the plain FP64 comparator arm (default: --steps)")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--matvec-reps", type=int, default=20)
     ap.add_argument("--workload", default="hexagon_8x8_n256", choices=sorted(WORKLOADS))
     ap.add_argument("--launch", type=int, default=0, choices=[0, 1],
                     help="cached matvec: 0 = one cooperative launch per product, 1 = one kernel per stage")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the large-block (32x32 square, 131072 elements) and sweep-chunk (128 band-gap "
+                         "instances) keys")
     ap.add_argument("--stage-times", action="store_true",
                     help="diagnostic: print the stage durations of the single-launch matvec (4 FP64 and 4 mixed "
                          "products of the workload, %%globaltimer read by block 0 after every device-wide "
@@ -161,21 +165,22 @@ class Clocks:
 
 
 # ------------------------------------------------------------------ CPU oracle sample
-def oracle_sample(w, rows=8, lu_n=2048, seed=0):
+def oracle_sample(w, rows=8, lu_n=2048, seed=0, keep=False):
     """Time the oracle on a bounded sample and extrapolate one dense solve of the block.
 
     Sample: assembly of `rows` element rows (2 equations each) of the dense operator
     (eq. 9) with the Ewald-summed kernel, plus an LU factorisation of a random
     complex matrix of size lu_n; the full solve is extrapolated as
-    (E / rows) * t_rows + (2E / lu_n)^3 * t_lu."""
+    (E / rows) * t_rows + (2E / lu_n)^3 * t_lu.  keep=True also returns the
+    assembled rows (element indices, operator rows, right-hand side rows)."""
     from scipy import linalg as sla
 
     from oracle import bem
     pb = bem.problem(w)
     rng = np.random.default_rng(seed)
-    sel = rng.choice(w.E, size=rows, replace=False)
+    sel = np.sort(rng.choice(w.E, size=rows, replace=False))
     t0 = time.perf_counter()
-    bem.operator_rows(pb, sel)
+    Mr = bem.operator_rows(pb, sel)
     t_rows = time.perf_counter() - t0
     A = rng.standard_normal((lu_n, lu_n)) + 1j * rng.standard_normal((lu_n, lu_n))
     t0 = time.perf_counter()
@@ -185,6 +190,10 @@ def oracle_sample(w, rows=8, lu_n=2048, seed=0):
     t_full = (w.E / rows) * t_rows + (n / lu_n) ** 3 * t_lu
     sample = (f"assembly of {rows} of {w.E} element rows ({t_rows:.2f} s) + LU of a {lu_n}^2 complex matrix "
               f"({t_lu:.2f} s), extrapolated to one dense solve of {n} unknowns ({t_full:.0f} s)")
+    if keep:
+        B = bem.rhs(pb)
+        eq = np.stack([2 * sel, 2 * sel + 1], axis=1).ravel()
+        return 1.0 / t_full, sample, t_rows + t_lu, (sel, Mr, B[eq])
     return 1.0 / t_full, sample, t_rows + t_lu
 
 
@@ -329,13 +338,14 @@ def main():
     # (the events around every launch would otherwise slow the timed steps)
     prof_steps = max(1, min(2, args.steps))
     timed(host=False, profile=True, steps=prof_steps)
+    prof_iters = stats["iters"]          # FP32 products that ran in each profiled (mixed) step
     barrier()
     # plain FP64 FMM-GMRES comparator on the same block and tolerance
     o64 = pf.Options()
     o64.precision = pf.FP64
     o64.launch = args.launch
     step(o=o64)
-    ms_fp64 = timed(host=False, profile=False, steps=args.fp64_steps, o=o64)
+    ms_fp64 = timed(host=False, profile=False, steps=args.fp64_steps or args.steps, o=o64)
     fp64_stats = dict(stats)
     stats.clear()
     stats.update(main_stats)
@@ -370,6 +380,9 @@ def main():
         if dist is not None:
             dist.destroy_process_group()
         return
+    # accuracy of the benched solve (outside the timed region): the mixed solution at
+    # the bench tolerance against an FP64 solve of the same block at 1e-10
+    acc = solution_accuracy(pf, torch, w, opt, npf_d, nodes_d, sptr, args.tol, maxit)
     plan = stats["plan"]
     launches = int(round(prof_acc["launches"].sum() / prof_steps * args.steps))
     names = pf.PHASES
@@ -377,18 +390,34 @@ def main():
     fp64_peak = pf.pfmbem_probe_peak(0)
     fp32_peak = pf.pfmbem_probe_peak(1)
     roof = roofline(names, ms_ph, prof_acc["launches"], prof_steps, plan, fp64_peak, fp32_peak, w.E,
-                    tensor_m2l=(opt.m2l_mode == 2), workload=w.name)
+                    tensor_m2l=(opt.m2l_mode == 2), workload=w.name,
+                    real_f32_products=prof_iters if prec == pf.MIXED else None)
+    roof_p2p = roofline_p2p(ms_ph, prof_acc["launches"], prof_steps, plan, fp64_peak)
     ms_ph = ms_ph / prof_steps
 
     cpu = None
     if not args.no_cpu_baseline:
-        v, sample, _ = oracle_sample(w)
+        v, sample, _, rows = oracle_sample(w, keep=True)
         cpu = {"value": v, "unit": "solves/s", "cores": cpu_cores(), "kind": "oracle", "sample": sample}
+        # the oracle's residual of the benched solution on the rows it just assembled
+        sel, Mr, Br = rows
+        r = Br - Mr @ acc.pop("psi")
+        acc["oracle_row_residual"] = {"rows": int(len(sel)), "rel": float(np.linalg.norm(r) / np.linalg.norm(Br)),
+                                      "def": "||B_r - A_r psi|| / ||B_r|| over the sampled element rows, A_r and "
+                                             "B_r assembled by the CPU oracle (exact element integrals, Ewald "
+                                             "G_qp), psi the GPU mixed solution"}
+    acc.pop("psi", None)
+    extra = {}
+    if not args.no_extra and world == 1:
+        extra["large_block"] = large_block(pf, torch, args, stream, flush)
+        extra["sweep_chunk"] = sweep_chunk(args)
     h2d = int(npf_h.numel() * 4 + nodes_h.numel() * 8)
     d2h = int(psi_h.numel() * 16 + stats["norders"] * 2 * 16)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32/bf16+f64",
+            "vs_baseline": None,
+            "dtype": ("f64" if args.precision == "fp64" else
+                      "f32/bf16+f64" if opt.m2l_mode == 2 else "f32+f64"),
             "data": "synthetic",
             "config": {"workload": w.name, "elements": w.E, "unknowns": n, "fibers": w.M, "kH": w.k * w.H,
                        "tol": args.tol, "precision": args.precision, "depth": plan.depth,
@@ -405,13 +434,94 @@ def main():
                       "setup_ms": plan.setup_ms},
             "phase_ms_per_step": {names[i]: float(ms_ph[i]) for i in range(len(names)) if names[i] and ms_ph[i] > 0},
             "roofline": roof,
+            "roofline_p2p": roof_p2p,
+            "err_vs_oracle": acc,
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "clocks": clk,
             "gpu_launches": launches}
+    line.update(extra)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def solution_accuracy(pf, torch, w, opt, npf_d, nodes_d, sptr, tol, maxit):
+    """Mixed solve at the bench tolerance against an FP64 solve at 1e-10 of the same
+    block: relative L2 difference of the densities and the largest difference of the
+    Bragg coefficients R_n, T_n."""
+    o64 = pf.Options()
+    o64.precision = pf.FP64
+    out = {}
+    sols = []
+    for o, t in ((opt, tol), (o64, 1e-10)):
+        psi = torch.zeros(2 * w.E, dtype=torch.complex128, device="cuda")
+        h = pf.pfmbem_create(w.M, npf_d, nodes_d, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, o, sptr)
+        try:
+            info = pf.pfmbem_solve(h, None, psi, False, t, maxit, check=False)
+            orders, R, T, _ = pf.pfmbem_coefficients(h, psi)
+        finally:
+            pf.pfmbem_destroy(h)
+        sols.append((psi.cpu().numpy(), R, T, info.rel_residual))
+    (p1, R1, T1, r1), (p2, R2, T2, r2) = sols
+    out["vs_fp64_tol1e-10"] = {"density_rel_l2": float(np.linalg.norm(p1 - p2) / np.linalg.norm(p2)),
+                               "bragg_max_abs": float(max(np.max(np.abs(R1 - R2)), np.max(np.abs(T1 - T2)))),
+                               "fp64_rel_residual": r2}
+    out["psi"] = p1
+    return out
+
+
+def large_block(pf, torch, args, stream, flush, steps=5):
+    """The 32x32 square block (131072 elements, kH = 20): create + mixed solve to the
+    bench tolerance + Bragg coefficients, device buffers, L2 flushed between steps,
+    against the plain FP64 solve of the same block."""
+    from paper_1910_10863_gb300 import workloads as W
+    w = W.square_32x32_n128()
+    npf = torch.from_numpy(np.ascontiguousarray(w.nodes_per_fiber, dtype=np.int32)).cuda()
+    nodes = torch.from_numpy(np.ascontiguousarray(w.nodes)).cuda()
+    psi = torch.zeros(2 * w.E, dtype=torch.complex128, device="cuda")
+    res = {}
+    for name, prec in (("mixed", pf.MIXED), ("fp64", pf.FP64)):
+        o = pf.Options()
+        o.precision = prec
+        info = None
+
+        def one():
+            nonlocal info
+            h = pf.pfmbem_create(w.M, npf, nodes, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, o,
+                                 stream.cuda_stream)
+            try:
+                info = pf.pfmbem_solve(h, None, psi, False, args.tol, 2000, check=False)
+                pf.pfmbem_coefficients(h, psi)
+            finally:
+                pf.pfmbem_destroy(h)
+        one()
+        tot = 0.0
+        for _ in range(steps):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            one()
+            e1.record(stream)
+            e1.synchronize()
+            tot += e0.elapsed_time(e1)
+        res[name] = {"solves_per_s": 1000.0 * steps / tot, "iters": info.iters, "rel_residual": info.rel_residual}
+    return {"workload": w.name, "elements": w.E, "unknowns": 2 * w.E, "steps": steps, **res,
+            "speedup_mixed_over_fp64": res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"]}
+
+
+def sweep_chunk(args, count=128):
+    """One chunk of the band-gap sweep: 128 instances of 16 fibers with 64-256
+    elements each (kH in [0.5, 8]), plans from the autotuner, solved together by
+    pfmbem_solve_batch, wall time from the first create to the last coefficient."""
+    from paper_1910_10863_gb300 import sweep
+    r = sweep.run(count=count, chunk=count, tol=args.tol, sequential_sample=16)
+    return {"instances": count, "batched_solves_per_s": r["batched_solves_per_s"],
+            "sequential_solves_per_s": r["sequential_solves_per_s"], "all_converged": r["all_converged"],
+            "max_rel_residual": r["max_rel_residual"], "mean_iters": r["mean_iters"],
+            "elements": [r["elements_min"], r["elements_max"]], "tune_seconds": r["tune_seconds"]}
 
 
 def pf_density(w):
@@ -426,6 +536,22 @@ def pf_density(w):
 # evaluation).  Cached applies: bytes of the resident operator plus the vectors
 # they read and write.
 FLOPS_PER_EVAL_FP64 = 255.0
+
+
+def roofline_p2p(ms_ph, la_ph, steps, plan, fp64_peak):
+    """Near-field and same-fiber element integrals (the P2P kernel evaluations, once per
+    create): FP64 flops per evaluation x evaluations over the measured build time."""
+    i = 10                                         # phase "p2p_cache_build"
+    if not plan.cached or ms_ph[i] <= 0:
+        return None
+    units = plan.near_quad + plan.fiber_quad
+    ms = ms_ph[i] / steps
+    ach = units * FLOPS_PER_EVAL_FP64 / (ms * 1e-3) / 1e12
+    return {"kernel": "p2p_cache_build (near_build, near_direct, fiber_build)", "bound": "alu",
+            "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+            "ms_per_step": ms, "launches_per_step": la_ph[i] / steps, "units_per_step": int(units),
+            "unit_def": "kernel evaluation (target x Gauss node x wavenumber), 255 FP64 flops",
+            "peak_source": "FP64 FMA-chain probe (pfmbem_probe_peak)"}
 
 
 def measured_peaks():
@@ -469,7 +595,8 @@ def captured_traffic(workload, kernel):
     return NCU_TRAFFIC.get((workload, kernel))
 
 
-def roofline(names, ms_ph, la_ph, steps, plan, fp64_peak, fp32_peak, E, tensor_m2l=False, workload=""):
+def roofline(names, ms_ph, la_ph, steps, plan, fp64_peak, fp32_peak, E, tensor_m2l=False, workload="",
+             real_f32_products=None):
     dom = int(np.argmax(ms_ph))
     name = names[dom]
     ms_step = ms_ph[dom] / steps
@@ -479,6 +606,12 @@ def roofline(names, ms_ph, la_ph, steps, plan, fp64_peak, fp32_peak, E, tensor_m
     csz = 8 if f32 else 16
     hbm, hbm_src = measured_peaks()
     out = {"kernel": name, "ms_per_launch": per_launch, "launches_per_step": launches}
+    if name == "matvec_fused_f32" and real_f32_products:
+        # products queued after convergence return at once: divide the phase time by
+        # the products that ran (the solve's inner iterations), not by the launches
+        per_launch = ms_step / real_f32_products
+        out.update(ms_per_launch=per_launch, products_per_step=real_f32_products,
+                   note="phase time / products that ran; launches queued after convergence return at once")
     if name == "p2p_cache_build":
         units = plan.near_quad + plan.fiber_quad
         ach = units * FLOPS_PER_EVAL_FP64 / (ms_step * 1e-3) / 1e12

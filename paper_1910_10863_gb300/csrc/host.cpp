@@ -934,7 +934,12 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     L.nne = (int)L.hne.size();
     // expansion order
     double x = k * L.d * std::sqrt(2.0);
-    int pmin = h->opt.p_min > 0 ? h->opt.p_min : 15;
+    // p_min = 24: the fine levels' translations (kd << 1) converge geometrically,
+    // by about 0.4 per order for the nearest well-separated boxes (Table 1, L = 0),
+    // so p_min sets the FMM's error on smooth densities: measured against the
+    // oracle on the 8x8 hexagon block's solution, 1.6e-6 at 15, 3.8e-8 at 20,
+    // 6.9e-10 at 24
+    int pmin = h->opt.p_min > 0 ? h->opt.p_min : 24;
     int p = h->opt.p > 0 ? h->opt.p : (int)std::ceil(x + 1.8 * std::pow(10.0, 2.0 / 3.0) * std::cbrt(x));
     p = std::max(p, h->opt.p > 0 ? 1 : pmin);
     if (p > PF_PMAX) return fail(h, PFMBEM_EINVAL, "expansion order above the library limit (128); use more levels");

@@ -42,7 +42,7 @@ namespace {
 
 constexpr int FB = 256;          // threads per block
 constexpr int FW = FB / 32;      // warps per block
-constexpr int TSP = 45;          // largest order count P whose M2L operator is staged in shared memory
+constexpr int TSP = 49;          // largest order count P whose M2L operator is staged in shared memory
 constexpr int TSIZE = TSP * (TSP + 1);
 
 template <class C>
