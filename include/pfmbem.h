@@ -79,7 +79,11 @@ typedef struct {
                        terms) inverted exactly by FFT where the fiber is a regular
                        polygon with 2^j elements, identity elsewhere; flexible GMRES.
                        1 = none */
-  int reserved[3];
+  int wait_us;      /* bound of every device-side wait of the single-launch product, in
+                       microseconds; 0 = one second.  A wait that runs out stops the
+                       product, and the call that reads its result returns
+                       PFMBEM_ETIMEOUT (the next product starts afresh) */
+  int reserved[2];
 } pfmbem_options;
 
 /* Outcome of a solve. */

@@ -1497,6 +1497,71 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         CK(cudaMemsetAsync(h->fz_err, 0, sizeof(int), h->stream));
         h->fused = true;
         h->pc = h->pc_val != nullptr || h->pr_val != nullptr;
+        // the FP32 product's near sums in differences: lo parts of the densities and
+        // the near blocks' FP64 row sums (built once the uploads below have landed)
+        if (h->nc_vall) {
+          h->fz_dlo = dalloc<cplxf>(h, 2 * (size_t)E);
+          h->fz_rsum = dalloc<cplx>(h, 4 * (size_t)E);
+          if (!h->fz_dlo || !h->fz_rsum) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near row sums)");
+        }
+        // the dataflow form of the product (no device-wide barrier), when the
+        // tree has levels 1..3 and the near blocks are cached
+        bool fok = false;
+        CK(k_flow_grids(h, &fok));
+        if (fok) {
+          auto& F = h->flow;
+          size_t off = 0;
+          for (int pi = 0; pi < 2; ++pi) {
+            for (int l = 1; l <= D; ++l) {
+              F.mo[pi][l] = off;
+              off += h->lev[l].nbox;
+              F.lo[pi][l] = off;
+              off += h->lev[l].nbox;
+            }
+            F.go[pi] = off;
+            off += 8;
+          }
+          F.ncnt = off;
+          size_t eoff = 0, loff = 0;
+          for (int l = 1; l <= D; ++l) {
+            F.eo[l] = eoff;
+            eoff += h->lev[l].nbox;
+            F.Lo[l] = loff;
+            loff += (size_t)h->lev[l].nbox * h->lev[l].P;
+          }
+          F.Lo[D + 1] = loff;
+          F.cnt = dalloc<unsigned>(h, F.ncnt);
+          F.expL = dalloc<unsigned>(h, eoff);
+          for (int p = 0; p < 2; ++p) {
+            F.L64[p] = dalloc<cplx>(h, loff);
+            F.L32[p] = dalloc<cplxf>(h, loff);
+          }
+          if (!F.cnt || !F.expL || !F.L64[0] || !F.L64[1] || !F.L32[0] || !F.L32[1])
+            return fail(h, PFMBEM_ENOMEM, "device allocation failed (dataflow product)");
+          CK(cudaMemsetAsync(F.cnt, 0, F.ncnt * sizeof(unsigned), h->stream));
+          CK(cudaMemsetAsync(F.expL, 0, eoff * sizeof(unsigned), h->stream));
+          for (int p = 0; p < 2; ++p) {
+            CK(cudaMemsetAsync(F.L64[p], 0, loff * sizeof(cplx), h->stream));
+            CK(cudaMemsetAsync(F.L32[p], 0, loff * sizeof(cplxf), h->stream));
+          }
+          // near-field items: (leaf index, first target), 4 targets each for the
+          // FP64 product and 8 for the FP32 one
+          const Level& Lf = h->lev[D];
+          for (int pi = 0; pi < 2; ++pi) {
+            const int nt = pi ? 8 : 4;
+            std::vector<int> it;
+            for (size_t li = 0; li < Lf.hne.size(); ++li) {
+              const int b = Lf.hne[li], cnt = Lf.hend[b] - Lf.hbegin[b];
+              for (int t0 = 0; t0 < cnt; t0 += nt) {
+                it.push_back((int)li);
+                it.push_back(t0);
+              }
+            }
+            F.nnear[pi] = (int)(it.size() / 2);
+            if ((st = upload(h, &F.near_item[pi], it)) != PFMBEM_OK) return st;
+          }
+          F.on = true;            // its tables are built once the uploads below have landed
+        }
       }
     }
   }
@@ -1506,6 +1571,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = flush_uploads(h)) != PFMBEM_OK) return st;
   }
   h->ub_on = false;
+  // tables of the single-launch product that read uploaded lists (s_li, the M2L pairs)
+  if (h->fused) CK(k_fused_tables(h));
   // The create returns without waiting for the device: the caller's next work
   // queues behind the set-up on the same stream.  The operator check is read
   // back asynchronously and reported by the first call that waits
@@ -1674,8 +1741,15 @@ static pfmbem_status gmres_cycle_device(pfmbem* h, cplx* x, double beta, double 
     }
     CK(cudaMemcpyAsync(hictl, g.ictl, sizeof(int) * 4, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaMemcpyAsync(hctl + 3, g.ctl, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (h->fz_err) CK(cudaMemcpyAsync(hictl + 4, h->fz_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     done_steps = hictl[1];
+    if (h->fz_err && hictl[4]) {
+      // a bounded device-side wait gave up: the products and steps queued since
+      // returned early, so the cycle stops here
+      h->fz_dirty = true;
+      return fail(h, PFMBEM_ETIMEOUT, "single-launch matvec: a bounded device-side wait gave up");
+    }
     if (hictl[0]) {
       *reason = hictl[2];
       break;
@@ -1750,6 +1824,7 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
       if (sc != PFMBEM_OK) return sc;
       iters += steps;
       ++restarts;
+      if (steps == 0) break;            // no progress (the cycle stopped at once): leave with the current residual
       if (reason != 3 && trust_estimate) {
         relres = est;
         done = true;
@@ -2190,8 +2265,19 @@ pfmbem_status pfmbem_matvec(pfmbem_t h, const double* x, double* y, int precisio
   cplx* yd = ydev ? reinterpret_cast<cplx*>(y) : h->stage_out;
   CK(k_matvec(h, xd, yd, precision));
   if (!ydev) {
+    // a host result waits for the product, so a device-side wait that gave up is reported here
+    int fze = 0;
     CK(cudaMemcpyAsync(y, yd, n * sizeof(cplx), cudaMemcpyDeviceToHost, h->stream));
+    if (h->fused && h->fz_err && h->hstat) {
+      h->hstat[2] = 0;
+      CK(cudaMemcpyAsync(h->hstat + 2, h->fz_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    }
     CK(cudaStreamSynchronize(h->stream));
+    if (h->fused && h->fz_err && h->hstat) fze = h->hstat[2];
+    if (fze) {
+      h->fz_dirty = true;
+      return fail(h, PFMBEM_ETIMEOUT, "single-launch matvec: a bounded device-side wait gave up");
+    }
   }
   return PFMBEM_OK;
 }
@@ -2343,7 +2429,9 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
   }
   if (fze) {
     st = PFMBEM_ETIMEOUT;
-    h->err = "single-launch matvec: a bounded device-wide barrier wait gave up";
+    h->err = "single-launch matvec: a bounded device-side wait gave up";
+    // the next launch clears the barrier words, the dataflow counters and this flag first
+    h->fz_dirty = true;
   }
   if (info) {
     info->iters = iters;

@@ -234,3 +234,49 @@ def table3_square(ka2pi: float, f: float = 0.35, n: int = 256, c_water: float = 
                     k1=k * C_MERCURY / c_water, rho_ratio=RHO_MERCURY / RHO_WATER, theta=0.0,
                     nodes_per_fiber=np.full(len(centres), n, dtype=np.int32), nodes=nodes,
                     centres=np.asarray(centres), radii=np.full(len(centres), r))
+
+
+def round_square_area(r: float = 1.0, n: int = 4096) -> float:
+    """Area enclosed by the round-square curve of Sec. 4 at scale r (shoelace
+    formula on n points; the curve is smooth, so this converges spectrally)."""
+    p = round_square_nodes(0.0, 0.0, r, n)
+    return 0.5 * abs(float(np.sum(p[:, 0] * np.roll(p[:, 1], -1) - np.roll(p[:, 0], -1) * p[:, 1])))
+
+
+def table3_block(ka2pi: float, f: float = 0.35, lattice: str = "square", scatterer: str = "circular",
+                 n: int = 256, c_water: float = 1500.0, name: str | None = None) -> Workload:
+    """The water/mercury crystals of Table 3 (Sec. 4): water scatterers in a mercury
+    matrix, lattice constant a = 0.5 (nearest-neighbour spacing), M_H = 6 scatterers
+    per column along y (period H = 3) and M_L = 4 columns, normal incidence.
+    square: columns at x = (i + 1/2) a; hexagon: columns a sqrt(3)/2 apart, every
+    other column shifted by a/2 along y.  The scatterer's area is f times the unit
+    cell's (a^2, or a^2 sqrt(3)/2 for the hexagon lattice): a circle of radius r, or
+    the round-square curve scaled to that area."""
+    a = 0.5
+    H = 6 * a
+    k = 2.0 * math.pi * ka2pi / a
+    if lattice == "square":
+        cell = a * a
+        centres = [((ix + 0.5) * a, (iy + 0.5) * a) for ix in range(4) for iy in range(6)]
+    elif lattice == "hexagon":
+        cell = a * a * math.sqrt(3.0) / 2.0
+        dx = a * math.sqrt(3.0) / 2.0
+        centres = [((ix + 0.5) * dx, (iy + 0.25 + 0.5 * (ix % 2)) * a) for ix in range(4) for iy in range(6)]
+    else:
+        raise ValueError(lattice)
+    if scatterer == "circular":
+        r = math.sqrt(f * cell / math.pi)
+        nodes = np.concatenate([circle_nodes(c[0], c[1], r, n) for c in centres])
+        radius = r
+    elif scatterer == "roundsquare":
+        r = math.sqrt(f * cell / round_square_area(1.0))
+        nodes = np.concatenate([round_square_nodes(c[0], c[1], r, n) for c in centres])
+        radius = 3.0 * r
+    else:
+        raise ValueError(scatterer)
+    return Workload(name=name or f"table3_{scatterer}_{lattice}_f{f:g}_ka{ka2pi:g}", H=H,
+                    lattice=0 if lattice == "square" else 1, k=k, k1=k * C_MERCURY / c_water,
+                    rho_ratio=RHO_MERCURY / RHO_WATER, theta=0.0,
+                    nodes_per_fiber=np.full(len(centres), n, dtype=np.int32), nodes=nodes,
+                    centres=np.asarray(centres), radii=np.full(len(centres), radius))
+

@@ -9,10 +9,10 @@ Matvecs are checked on two kinds of density: seeded random vectors, whose
 products are dominated by the near-field and same-fiber blocks, and smooth
 physical densities (the incident right-hand side, the solution), whose products
 also expose the far field's truncation.  The mixed (FP32) product is held to
-2e-6 on random vectors; on smooth densities the hypersingular same-fiber
-operator sums terms of size ~1/h that cancel to O(1), so FP32 rounding leaves
-~ eps_32 * max|T h| ~ 3e-5 (MIXED_SMOOTH); the FP64 refinement of the mixed solve
-removes it from the solution.
+2e-6 on both.  On smooth densities the hypersingular same-fiber operator sums
+terms of size ~1/h that cancel to O(1); the product therefore sums the near
+field in differences psi_j - psi_t of hi + lo densities (row sums in FP64) and
+runs the same-fiber FFTs in FP64 (plain FP32 sums left ~5e-5 there).
 """
 import math
 
@@ -45,7 +45,7 @@ def oracle_system(w):
 
 
 SMALL = [W.square_2x2_n64, hexagon_4x4_ragged]
-MIXED_SMOOTH = 5e-5
+MIXED_SMOOTH = 2e-6
 
 
 @pytest.mark.parametrize("make", SMALL)
