@@ -1504,64 +1504,6 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
           h->fz_rsum = dalloc<cplx>(h, 4 * (size_t)E);
           if (!h->fz_dlo || !h->fz_rsum) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near row sums)");
         }
-        // the dataflow form of the product (no device-wide barrier), when the
-        // tree has levels 1..3 and the near blocks are cached
-        bool fok = false;
-        CK(k_flow_grids(h, &fok));
-        if (fok) {
-          auto& F = h->flow;
-          size_t off = 0;
-          for (int pi = 0; pi < 2; ++pi) {
-            for (int l = 1; l <= D; ++l) {
-              F.mo[pi][l] = off;
-              off += h->lev[l].nbox;
-              F.lo[pi][l] = off;
-              off += h->lev[l].nbox;
-            }
-            F.go[pi] = off;
-            off += 8;
-          }
-          F.ncnt = off;
-          size_t eoff = 0, loff = 0;
-          for (int l = 1; l <= D; ++l) {
-            F.eo[l] = eoff;
-            eoff += h->lev[l].nbox;
-            F.Lo[l] = loff;
-            loff += (size_t)h->lev[l].nbox * h->lev[l].P;
-          }
-          F.Lo[D + 1] = loff;
-          F.cnt = dalloc<unsigned>(h, F.ncnt);
-          F.expL = dalloc<unsigned>(h, eoff);
-          for (int p = 0; p < 2; ++p) {
-            F.L64[p] = dalloc<cplx>(h, loff);
-            F.L32[p] = dalloc<cplxf>(h, loff);
-          }
-          if (!F.cnt || !F.expL || !F.L64[0] || !F.L64[1] || !F.L32[0] || !F.L32[1])
-            return fail(h, PFMBEM_ENOMEM, "device allocation failed (dataflow product)");
-          CK(cudaMemsetAsync(F.cnt, 0, F.ncnt * sizeof(unsigned), h->stream));
-          CK(cudaMemsetAsync(F.expL, 0, eoff * sizeof(unsigned), h->stream));
-          for (int p = 0; p < 2; ++p) {
-            CK(cudaMemsetAsync(F.L64[p], 0, loff * sizeof(cplx), h->stream));
-            CK(cudaMemsetAsync(F.L32[p], 0, loff * sizeof(cplxf), h->stream));
-          }
-          // near-field items: (leaf index, first target), 4 targets each for the
-          // FP64 product and 8 for the FP32 one
-          const Level& Lf = h->lev[D];
-          for (int pi = 0; pi < 2; ++pi) {
-            const int nt = pi ? 8 : 4;
-            std::vector<int> it;
-            for (size_t li = 0; li < Lf.hne.size(); ++li) {
-              const int b = Lf.hne[li], cnt = Lf.hend[b] - Lf.hbegin[b];
-              for (int t0 = 0; t0 < cnt; t0 += nt) {
-                it.push_back((int)li);
-                it.push_back(t0);
-              }
-            }
-            F.nnear[pi] = (int)(it.size() / 2);
-            if ((st = upload(h, &F.near_item[pi], it)) != PFMBEM_OK) return st;
-          }
-          F.on = true;            // its tables are built once the uploads below have landed
-        }
       }
     }
   }
@@ -2430,7 +2372,7 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
   if (fze) {
     st = PFMBEM_ETIMEOUT;
     h->err = "single-launch matvec: a bounded device-side wait gave up";
-    // the next launch clears the barrier words, the dataflow counters and this flag first
+    // the next launch clears the barrier words and this flag first
     h->fz_dirty = true;
   }
   if (info) {

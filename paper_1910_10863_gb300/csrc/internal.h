@@ -275,25 +275,6 @@ struct pfmbem {
   cplx* Un = nullptr;            // [E][2] near-field part of (U', dU'), FP64 and FP32
   cplxf* Unf = nullptr;
   unsigned long long* fz_stamp = nullptr;   // [32] stage end times (diagnostic)
-  // dataflow form of the single-launch product (no device-wide barrier): per-box
-  // completion counters instead of stages; see matvec_fused.cu
-  struct Flow {
-    bool on = false;
-    int grid[2] = {0, 0};        // [0] FP64 product, [1] FP32 product
-    int fblk[2] = {0, 0};        // blocks of the grid that apply the same-fiber blocks
-    unsigned* cnt = nullptr;     // all counters of both precisions (one allocation)
-    size_t ncnt = 0;
-    size_t mo[2][PF_MAXLEVEL + 1] = {};   // offset of the M counters of level l in cnt
-    size_t lo[2][PF_MAXLEVEL + 1] = {};   // offset of the L counters
-    size_t go[2] = {0, 0};                // offset of the global counters
-    unsigned* expL = nullptr;    // [sum nbox] contributions to L(l)[box] per product
-    size_t eo[PF_MAXLEVEL + 1] = {};
-    int* near_item[2] = {nullptr, nullptr};   // (leaf index, first target) per near-field item
-    int nnear[2] = {0, 0};
-    cplx* L64[2] = {nullptr, nullptr};    // local expansions of levels 1..D, two parities
-    cplxf* L32[2] = {nullptr, nullptr};
-    size_t Lo[PF_MAXLEVEL + 1] = {};      // offset of level l in those buffers
-  } flow;
   cplx* root = nullptr;          // [P0][P0] periodic root translation
   cplxf* rootf = nullptr;
   cplx* rootc = nullptr;         // [4 P1][P0] root translation times the level-1 -> root M2M
@@ -358,7 +339,6 @@ cudaError_t k_sort_elements(pfmbem* h);
 // single-launch cached matvec (matvec_fused.cu)
 cudaError_t k_fused_prepare(pfmbem* h, bool* ok);
 cudaError_t k_top_operators(pfmbem* h, cudaStream_t st);
-cudaError_t k_flow_grids(pfmbem* h, bool* ok);
 cudaError_t k_fused_tables(pfmbem* h);
 cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done = nullptr);
 cudaError_t k_arnoldi_step(pfmbem* h, int j, int precision);

@@ -1580,29 +1580,20 @@ size_t fused_smem(int maxfiber) {
   return std::max(sizeof(C) * a, sizeof(cplx) * f);
 }
 
-// After a bounded device-side wait gave up, the barrier words, the error flag
-// and the dataflow counters are in an unknown state: clear them (on the
-// handle's stream) before the next launch that uses them.
+// After a bounded device-side wait gave up, the barrier words and the error
+// flag are in an unknown state: clear them (on the handle's stream) before the
+// next launch that uses them.
 cudaError_t reset_device_waits(pfmbem* h) {
   if (!h->fz_dirty) return cudaSuccess;
-  auto& F = h->flow;
   cudaError_t e = cudaSuccess;
   if (h->fz_bar) e = cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned), h->stream);
   if (e == cudaSuccess && h->arn_bar) e = cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->stream);
-  if (e == cudaSuccess && F.on) {
-    e = cudaMemsetAsync(F.cnt, 0, F.ncnt * sizeof(unsigned), h->stream);
-    for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
-      e = cudaMemsetAsync(F.L64[p], 0, F.Lo[h->D + 1] * sizeof(cplx), h->stream);
-      if (e == cudaSuccess) e = cudaMemsetAsync(F.L32[p], 0, F.Lo[h->D + 1] * sizeof(cplxf), h->stream);
-    }
-  }
   if (e == cudaSuccess && h->fz_err) e = cudaMemsetAsync(h->fz_err, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) h->fz_dirty = false;
   return e;
 }
 
-// Operators, vectors and work lists of one product, shared by the barrier and
-// the dataflow forms of the single-launch kernel.
+// Operators, vectors and work lists of one product of the single-launch kernel.
 template <class C>
 cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedArgs<C>& a) {
   a = FusedArgs<C>{};
@@ -1781,618 +1772,10 @@ int fused_grid(int maxfiber) {
 }
 
 
-// ============================================================ dataflow product
-// The same product without device-wide barriers.  Every piece of work is an
-// item of one list in an order where each item depends only on items before
-// it; warp w of the worker blocks takes items w, w + W, w + 2W, ... (W warps
-// in all).  An item waits (bounded) until the items it reads from have
-// signalled completion on per-box counters, and signals its own completion
-// with a release add once its stores and atomics are done:
-//
-//   P2M(leaf)                 gather + P2M             -> cntM[D][leaf], gather
-//   M2M(l, box | coefficient) waits for the children    -> cntM[l][box]
-//   M(1) from level 3 (coefficient items)               -> cntM[1][box]
-//   M2L(l, chunk | pair)      waits for each source's M -> cntL[l][target] per pair
-//   root part of L(1)         waits for M(1)            -> cntL[1][box]
-//   near field (leaf, targets) waits for the gather    -> near
-//   L2L(l, box | coefficient) waits for L(l-1) of the parent being final
-//                                                       -> cntL[l][box]
-//   L2P + combination (32 elements) waits for L(D) of their leaves, every
-//                             near item and every fiber item
-//
-// L(l)[box] is final when cntL reaches expL[l][box], the number of M2L pairs
-// into the box plus its L2L (or root) contributions.  Counters only grow:
-// product number e (read from a device word at the start, so that a product
-// skipped by the done flag leaves everything as it was) waits for (e + 1) x
-// the per-product count.  Items are dealt in list order to warps that are all
-// resident (cooperative launch), so the smallest unfinished item never waits
-// on anything unfinished and the list always progresses; every wait is still
-// bounded by a time limit, after which the warp sets the error flag and stops.
-// The blocks [G - fblk, G) apply the same-fiber blocks (block-level FFT items)
-// and count them on the fiber counter; they take no list items.  L is double
-// buffered by the parity of e: a product accumulates into one buffer and
-// clears the other for the next product.
-//
-// The FP32 product's near-field sums use differences: with the cached blocks
-// B_tj of target t, sum_j B_tj psi_j = sum_j B_tj (psi_j - psi_t) + R_t psi_t,
-// R_t = sum_j B_tj in FP64 (at create).  The densities are kept as FP32 hi +
-// lo pairs, so psi_j - psi_t is formed to FP32 relative accuracy; the
-// hypersingular same-fiber blocks, whose entries grow like 1/h and cancel on
-// smooth densities, then lose no digits to the FP32 sums.
-enum { FG_GATHER = 0, FG_NEAR, FG_FIBER, FG_EDONE, FG_EPOCH, FG_ARRIVE, FG_N = 8 };
-enum { FS_P2M = 0, FS_M2M, FS_M1, FS_M2L, FS_ROOT1, FS_NEAR, FS_L2L, FS_E };
-constexpr int FLOW_MAXSEG = 4 * (PF_MAXLEVEL + 1) + 8;
-// a level whose nne * P is at most this runs its M2M and L2L one warp per
-// coefficient (PFMBEM_FLOW_TOPW overrides, for measurement)
-int flow_topw() {
-  static const char* v = std::getenv("PFMBEM_FLOW_TOPW");
-  static const int w = v ? std::atoi(v) : 2048;
-  return w;
-}
+}  // namespace
 
-template <class C>
-struct FlowArgs {
-  FusedArgs<C> f;
-  unsigned* cntM[PF_MAXLEVEL + 1];
-  unsigned* cntL[PF_MAXLEVEL + 1];
-  const unsigned* expL[PF_MAXLEVEL + 1];
-  unsigned kM[PF_MAXLEVEL + 1];      // M signals per box per product (1, or P for coefficient items)
-  int top[PF_MAXLEVEL + 1];          // 1: the level's M2M / L2L run one warp per coefficient
-  unsigned* gc;                      // [FG_N] global counters
-  C* Lb[2][PF_MAXLEVEL + 1];         // L buffers of both parities
-  size_t Ltot;                       // C entries of one parity (levels 1..D, contiguous)
-  const int* near_item;              // [nnear][2] (leaf index, first target)
-  int nnear, nt;                     // near items, targets per near item
-  cplxf* dlo;                        // FP32 product: lo parts of the sorted densities
-  const cplx* rsum;                  // FP32 product: [E][4] row sums of the near blocks
-  int nE;                            // L2P items (32 elements each)
-  int nfib;                          // fiber items (FFT fibers + row chunks)
-  int gw;                            // worker blocks
-  int nseg, nitem;
-  int seg_kind[FLOW_MAXSEG], seg_lev[FLOW_MAXSEG], seg_end[FLOW_MAXSEG];
-  unsigned long long limit_ns;       // bound of every wait
-  unsigned long long* trace;         // optional: completion time of every item, [nitem] start, [nitem + 1] fiber end
-};
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Bounded wait until *p - target >= 0 (wrap-safe); false when it gave up
-// (the error flag is then set) or another warp already failed.
-__device__ bool wait_ge(const unsigned* p, unsigned target, int* err, unsigned long long limit) {
-  if ((int)(ld_acquire(p) - target) >= 0) return true;
-  const unsigned long long t0 = gtimer();
-  for (unsigned it = 1;; ++it) {
-    if ((int)(ld_acquire(p) - target) >= 0) return true;
-    if ((it & 31u) == 0) {
-      if (*(volatile int*)err != 0) return false;
-      if (gtimer() - t0 > limit) {
-        atomicExch(err, 1);
-        return false;
-      }
-    }
-  }
-}
-
-// lane 0 waits; the verdict and the acquired order reach the whole warp
-__device__ __forceinline__ bool warp_wait(const unsigned* p, unsigned target, int* err, unsigned long long limit,
-                                          int lane) {
-  int ok = 1;
-  if (lane == 0) ok = wait_ge(p, target, err, limit) ? 1 : 0;
-  ok = __shfl_sync(0xffffffffu, ok, 0);
-  __syncwarp();
-  return ok != 0;
-}
-
-// read-only loads of the translation operators through the non-coherent cache
-__device__ __forceinline__ cplxf ldg_c(const cplxf* p) {
-  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
-  return cplxf{v.x, v.y};
-}
-__device__ __forceinline__ cplx ldg_c(const cplx* p) {
-  const double2 v = __ldg(reinterpret_cast<const double2*>(p));
-  return cplx{v.x, v.y};
-}
-
-// The waits of a warp spread over its lanes: lane q < n waits on p[q]; true
-// when all of them were met.
-__device__ __forceinline__ bool lanes_wait(bool mine, const unsigned* p, unsigned target, int* err,
-                                           unsigned long long limit) {
-  const bool ok = !mine || wait_ge(p, target, err, limit);
-  const bool all = __all_sync(0xffffffffu, ok);
-  __syncwarp();
-  return all;
-}
-
-// gather + P2M of one leaf
-template <class C>
-__device__ bool flow_p2m(const FlowArgs<C>& g, int i, int lane) {
-  const FusedArgs<C>& a = g.f;
-  const int D = a.D, PD = a.P[D];
-  const int box = a.ne[D][i], s0 = a.bb[D][box], s1 = a.be[D][box];
-  for (int sb = s0; sb < s1; sb += 32) {
-    const int s = sb + lane;
-    if (s < s1) {
-      const int e = a.perm[s];
-      const cplx p = a.ph[s];
-      const cplx v0 = p * a.x[2 * e], v1 = p * a.x[2 * e + 1];
-      a.dens[2 * s] = from_d<C>(v0);
-      a.dens[2 * s + 1] = from_d<C>(v1);
-      if (a.dens_dd) {
-        a.dens_dd[2 * s] = cplxf{(float)v0.re, (float)v0.im};
-        a.dens_dd[2 * s + 1] = cplxf{(float)v1.re, (float)v1.im};
-        a.dens_dd[2 * a.E + 2 * s] = split_lo(v0);
-        a.dens_dd[2 * a.E + 2 * s + 1] = split_lo(v1);
-      }
-      if (g.dlo) {
-        g.dlo[2 * s] = split_lo(v0);
-        g.dlo[2 * s + 1] = split_lo(v1);
-      }
-    }
-  }
-  __syncwarp();
-  if (a.p2ml) {
-    const cplxf* dh = a.dens_dd;
-    const cplxf* dl = a.dens_dd + 2 * a.E;
-    for (int n = lane; n < PD; n += 32) {
-      dflt re{0, 0}, im{0, 0};
-      for (int f = s0; f < s1; ++f) {
-        const size_t c0 = (size_t)f * 2 * PD + n, c1 = c0 + PD;
-        dd_cmac(re, im, a.p2mh[c0], a.p2ml[c0], dh[2 * f], dl[2 * f]);
-        dd_cmac(re, im, a.p2mh[c1], a.p2ml[c1], dh[2 * f + 1], dl[2 * f + 1]);
-      }
-      a.M[D][(size_t)box * PD + n] = from_d<C>(cplx{dd_value(re), dd_value(im)});
-    }
-  } else {
-    for (int n = lane; n < PD; n += 32) {
-      C acc0{0, 0}, acc1{0, 0};
-#pragma unroll 4
-      for (int f = s0; f < s1; ++f) {
-        const C* cf = a.p2m + (size_t)f * 2 * PD;
-        acc0 += cf[n] * a.dens[2 * f];
-        acc1 += cf[PD + n] * a.dens[2 * f + 1];
-      }
-      a.M[D][(size_t)box * PD + n] = acc0 + acc1;
-    }
-  }
-  __syncwarp();
-  if (lane == 0) {
-    red_add_release(g.cntM[D] + box, 1u);
-    red_add_release(g.gc + FG_GATHER, 1u);
-  }
-  return true;
-}
-
-// M2M into level l (2 <= l < D): one warp per box, or per output coefficient
-template <class C>
-__device__ bool flow_m2m(const FlowArgs<C>& g, int l, int i, unsigned e1, C* wsm, int lane) {
-  const FusedArgs<C>& a = g.f;
-  const int P = a.P[l], Pc = a.P[l + 1];
-  const bool top = g.top[l] != 0;
-  const int bi = top ? i / P : i, n0 = top ? i - bi * P : 0;
-  const int box = a.ne[l][bi];
-  {
-    const int ch = 4 * box + (lane & 3);
-    const bool mine = lane < 4 && a.bb[l + 1][ch] < a.be[l + 1][ch];
-    if (!lanes_wait(mine, g.cntM[l + 1] + ch, e1 * g.kM[l + 1], a.err, g.limit_ns)) return false;
-  }
-  if (top) {
-    const C* A = a.m2m[l] + n0;
-    C acc{0, 0};
-    for (int u = lane; u < 4 * Pc; u += 32) {
-      const int q = u / Pc, ch = 4 * box + q;
-      if (a.bb[l + 1][ch] < a.be[l + 1][ch]) acc += A[(size_t)u * P] * ldcg(a.M[l + 1] + (size_t)ch * Pc + (u - q * Pc));
-    }
-    acc = wsum(acc);
-    if (lane == 0) a.M[l][(size_t)box * P + n0] = acc;
-  } else if (a.m2ml[l] && 4 * Pc <= PF_NCOEF) {
-    cplxf* wh = reinterpret_cast<cplxf*>(wsm);
-    cplxf* wl = wh + PF_NCOEF;
-    for (int t = lane; t < 4 * Pc; t += 32) {
-      const int q = t / Pc, ch = 4 * box + q;
-      const cplx v = a.bb[l + 1][ch] < a.be[l + 1][ch] ? to_d(ldcg(a.M[l + 1] + (size_t)ch * Pc + (t - q * Pc)))
-                                                       : cplx{0, 0};
-      wh[t] = cplxf{(float)v.re, (float)v.im};
-      wl[t] = split_lo(v);
-    }
-    __syncwarp();
-    for (int n = lane; n < P; n += 32) {
-      dflt re{0, 0}, im{0, 0};
-#pragma unroll 4
-      for (int u = 0; u < 4 * Pc; ++u)
-        dd_cmac(re, im, a.m2mh[l][(size_t)u * P + n], a.m2ml[l][(size_t)u * P + n], wh[u], wl[u]);
-      a.M[l][(size_t)box * P + n] = from_d<C>(cplx{dd_value(re), dd_value(im)});
-    }
-  } else if (4 * Pc <= PF_NCOEF) {
-    for (int t = lane; t < 4 * Pc; t += 32) {
-      const int q = t / Pc, ch = 4 * box + q;
-      wsm[t] = a.bb[l + 1][ch] < a.be[l + 1][ch] ? ldcg(a.M[l + 1] + (size_t)ch * Pc + (t - q * Pc)) : C{0, 0};
-    }
-    __syncwarp();
-    for (int n = lane; n < P; n += 32) a.M[l][(size_t)box * P + n] = colmv(a.m2m[l] + n, P, wsm, 4 * Pc);
-  } else {
-    for (int nb = 0; nb < P; nb += 32) {
-      const int n = nb + lane;
-      C acc{0, 0};
-      for (int q = 0; q < 4; ++q) {
-        const int ch = 4 * box + q;
-        if (a.bb[l + 1][ch] >= a.be[l + 1][ch]) continue;
-        __syncwarp();
-        for (int m = lane; m < Pc; m += 32) wsm[m] = ldcg(a.M[l + 1] + (size_t)ch * Pc + m);
-        __syncwarp();
-        if (n < P) acc += colmv(a.m2m[l] + (size_t)q * Pc * P + n, P, wsm, Pc);
-      }
-      if (n < P) a.M[l][(size_t)box * P + n] = acc;
-    }
-  }
-  __syncwarp();
-  if (lane == 0) red_add_release(g.cntM[l] + box, 1u);
-  return true;
-}
-
-// M(1) of a level-1 box from its 16 level-3 boxes (T_1 T_2), one warp per coefficient
-template <class C>
-__device__ bool flow_m1(const FlowArgs<C>& g, int k, unsigned e1, int lane) {
-  const FusedArgs<C>& a = g.f;
-  const int P1 = a.P[1], U1 = 16 * a.P[3];
-  const int b1 = a.ne[1][k / P1], n = k % P1;
-  {
-    const int b3 = 16 * b1 + (lane & 15);
-    const bool mine = lane < 16 && a.bb[3][b3] < a.be[3][b3];
-    if (!lanes_wait(mine, g.cntM[3] + b3, e1 * g.kM[3], a.err, g.limit_ns)) return false;
-  }
-  const C* A = a.m2m31 + (size_t)n * U1;
-  const C* M3 = a.M[3] + (size_t)b1 * U1;
-  C acc{0, 0};
-#pragma unroll 4
-  for (int u = lane; u < U1; u += 32) acc += A[u] * ldcg(M3 + u);
-  acc = wsum(acc);
-  if (lane == 0) {
-    a.M[1][(size_t)b1 * P1 + n] = acc;
-    __threadfence_block();
-    red_add_release(g.cntM[1] + b1, 1u);
-  }
-  return true;
-}
-
-// M2L at level l: a chunk of pairs sharing one offset (FP32 product, operator
-// rows read through L1) or one pair (FP64 product)
-template <class C>
-__device__ bool flow_m2l(const FlowArgs<C>& g, int l, int i, unsigned e1, C* Ll, C* wsm, int lane) {
-  const FusedArgs<C>& a = g.f;
-  const int P = a.P[l];
-  const unsigned tM = e1 * g.kM[l];
-  if (!a.m2l_warp) {
-    const int o = a.ch_off[l][i], pb = a.ch_beg[l][i], pe = a.ch_end[l][i];
-    const C* To = a.m2lt[l] + (size_t)o * P * P;          // [m source][n target]
-    const int step = 2 * P <= PF_NCOEF ? 2 : 1;           // two pairs per pass when both fit the scratch
-    for (int pi = pb; pi < pe; pi += step) {
-      const bool two = step == 2 && pi + 1 < pe;
-      const int srcA = a.pr_src[l][pi], tgtA = a.pr_tgt[l][pi];
-      const int srcB = two ? a.pr_src[l][pi + 1] : srcA, tgtB = two ? a.pr_tgt[l][pi + 1] : tgtA;
-      if (!lanes_wait(lane < (two ? 2 : 1), g.cntM[l] + (lane == 0 ? srcA : srcB), tM, a.err, g.limit_ns))
-        return false;
-      const C phA = from_d<C>(phase_m(a.alpha, a.pr_img[l][pi]));
-      const C phB = two ? from_d<C>(phase_m(a.alpha, a.pr_img[l][pi + 1])) : C{0, 0};
-      for (int m = lane; m < P; m += 32) {
-        wsm[m] = phA * ldcg(a.M[l] + (size_t)srcA * P + m);
-        wsm[P + m] = phB * ldcg(a.M[l] + (size_t)srcB * P + m);
-      }
-      __syncwarp();
-      for (int n = lane; n < P; n += 32) {
-        C rA{0, 0}, rB{0, 0};
-#pragma unroll 4
-        for (int m = 0; m < P; ++m) {
-          const C t = ldg_c(To + (size_t)m * P + n);
-          rA += t * wsm[m];
-          rB += t * wsm[P + m];
-        }
-        atomic_add(Ll + (size_t)tgtA * P + n, rA);
-        if (two) atomic_add(Ll + (size_t)tgtB * P + n, rB);
-      }
-      __syncwarp();
-      if (lane == 0) {
-        red_add_release(g.cntL[l] + tgtA, 1u);
-        if (two) red_add_release(g.cntL[l] + tgtB, 1u);
-      }
-    }
-    return true;
-  }
-  const int src = a.pr_src[l][i], tgt = a.pr_tgt[l][i];
-  if (!warp_wait(g.cntM[l] + src, tM, a.err, g.limit_ns, lane)) return false;
-  const C phs = from_d<C>(phase_m(a.alpha, a.pr_img[l][i]));
-  if (a.m2ltl[l]) {
-    cplxf* wh = reinterpret_cast<cplxf*>(wsm);
-    cplxf* wl = wh + PF_NCOEF;
-    for (int m = lane; m < P; m += 32) {
-      const cplx v = to_d(phs * ldcg(a.M[l] + (size_t)src * P + m));
-      wh[m] = cplxf{(float)v.re, (float)v.im};
-      wl[m] = split_lo(v);
-    }
-    __syncwarp();
-    const size_t ob = (size_t)a.pr_off[l][i] * P * P;
-    const cplxf* Th = a.m2lth[l] + ob;
-    const cplxf* Tl = a.m2ltl[l] + ob;
-    for (int n = lane; n < P; n += 32) {
-      dflt re{0, 0}, im{0, 0};
-#pragma unroll 4
-      for (int m = 0; m < P; ++m) dd_cmac(re, im, Th[(size_t)m * P + n], Tl[(size_t)m * P + n], wh[m], wl[m]);
-      atomic_add(Ll + (size_t)tgt * P + n, from_d<C>(cplx{dd_value(re), dd_value(im)}));
-    }
-  } else {
-    const C* To = a.m2lt[l] + (size_t)a.pr_off[l][i] * P * P;
-    for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * P + m);
-    __syncwarp();
-    for (int n = lane; n < P; n += 32) atomic_add(Ll + (size_t)tgt * P + n, colmv(To + n, P, wsm, P));
-  }
-  __syncwarp();
-  if (lane == 0) red_add_release(g.cntL[l] + tgt, 1u);
-  return true;
-}
-
-// the root's part of L(1) from the four level-1 multipoles (L2L_q R T_0), one
-// warp per coefficient
-template <class C>
-__device__ bool flow_root1(const FlowArgs<C>& g, int k, unsigned e1, C* L1, int lane) {
-  const FusedArgs<C>& a = g.f;
-  const int P = a.P[1];
-  const int bi = k / P, n = k - bi * P;
-  const int box = a.ne[1][bi];
-  {
-    const bool mine = lane < 4 && a.bb[1][lane & 3] < a.be[1][lane & 3];
-    if (!lanes_wait(mine, g.cntM[1] + (lane & 3), e1 * g.kM[1], a.err, g.limit_ns)) return false;
-  }
-  const C* A = a.root1 + ((size_t)box * P + n) * 4 * P;
-  C acc{0, 0};
-  for (int u = lane; u < 4 * P; u += 32) acc += A[u] * ldcg(a.M[1] + u);
-  acc = wsum(acc);
-  if (lane == 0) {
-    atomic_add(L1 + (size_t)box * P + n, acc);
-    __threadfence_block();
-    red_add_release(g.cntL[1] + box, 1u);
-  }
-  return true;
-}
-
-// near-field sums of up to NT targets of one leaf, FP32 product, in differences
-// (see the head of this section): lanes over the leaf's sources, the targets'
-// densities (hi, lo) in the warp's scratch
-template <int NT>
-__device__ void flow_near_diff(const FlowArgs<cplxf>& g, int li, int t0, cplxf* wt, int lane) {
-  const FusedArgs<cplxf>& a = g.f;
-  const int D = a.D, box = a.ne[D][li];
-  const int sb = a.bb[D][box], nt = a.be[D][box] - sb;
-  const int tn = min(NT, nt - t0);
-  const int j0 = a.nc_sbase[li], ns = a.nc_sbase[li + 1] - j0;
-  const cplxf* blk = a.nc_val + a.nc_base[li] + (int64_t)t0 * ns * 4;
-  if (lane < 4 * tn) {
-    const int t = lane >> 2, q = lane & 3, s = sb + t0 + t, c = q >> 1;
-    wt[lane] = (q & 1) ? ldcg(g.dlo + 2 * s + c) : ldcg(a.dens + 2 * s + c);
-  }
-  __syncwarp();
-  cplxf u[NT], du[NT];
-#pragma unroll
-  for (int t = 0; t < NT; ++t) u[t] = du[t] = cplxf{0, 0};
-  for (int j = lane; j < ns; j += 32) {
-    const int f = __ldg(a.nc_src + j0 + j);
-    const cplxf ph = ldcg(a.dens + 2 * f), vh = ldcg(a.dens + 2 * f + 1);
-    const cplxf pl = ldcg(g.dlo + 2 * f), vl = ldcg(g.dlo + 2 * f + 1);
-#pragma unroll
-    for (int t = 0; t < NT; ++t) {
-      if (t < tn) {
-        const cplxf dp = (ph - wt[4 * t]) + (pl - wt[4 * t + 1]);
-        const cplxf dv = (vh - wt[4 * t + 2]) + (vl - wt[4 * t + 3]);
-        const cplxf* q = blk + ((int64_t)t * ns + j) * 4;
-        u[t] += q[0] * dp + q[1] * dv;
-        du[t] += q[2] * dp + q[3] * dv;
-      }
-    }
-  }
-#pragma unroll
-  for (int t = 0; t < NT; ++t) {
-    if (t < tn) {
-      const cplxf U = wsum(u[t]), dU = wsum(du[t]);
-      if (lane == 0) {
-        const int s = sb + t0 + t;
-        a.Un[2 * s] = U;
-        a.Un[2 * s + 1] = dU;
-      }
-    }
-  }
-}
-
-template <class C>
-__device__ bool flow_near(const FlowArgs<C>& g, int k, unsigned e1, C* wsm, int lane) {
-  const FusedArgs<C>& a = g.f;
-  if (!warp_wait(g.gc + FG_GATHER, e1 * (unsigned)a.nne[a.D], a.err, g.limit_ns, lane)) return false;
-  const int li = g.near_item[2 * k], t0 = g.near_item[2 * k + 1];
-  if constexpr (sizeof(C) == sizeof(cplxf)) {
-    if (g.dlo) {
-      flow_near_diff<8>(g, li, t0, reinterpret_cast<cplxf*>(wsm), lane);
-      __syncwarp();
-      if (lane == 0) red_add_release(g.gc + FG_NEAR, 1u);
-      return true;
-    }
-  }
-  const int D = a.D, box = a.ne[D][li];
-  const int sb = a.bb[D][box], te = min(a.be[D][box], sb + t0 + g.nt);
-  for (int s = sb + t0; s < te; ++s) near_row(a, s, lane);
-  __syncwarp();
-  if (lane == 0) red_add_release(g.gc + FG_NEAR, 1u);
-  return true;
-}
-
-// L2L into level l >= 2 from the parent, once the parent's L is final
-template <class C>
-__device__ bool flow_l2l(const FlowArgs<C>& g, int l, int i, unsigned e1, C* const* Lb, C* wsm, int lane) {
-  const FusedArgs<C>& a = g.f;
-  const int P = a.P[l], Pp = a.P[l - 1];
-  const bool top = g.top[l] != 0;
-  const int bi = top ? i / P : i, n0 = top ? i - bi * P : 0;
-  const int box = a.ne[l][bi], par = box >> 2, q = box & 3;
-  if (!warp_wait(g.cntL[l - 1] + par, e1 * g.expL[l - 1][par], a.err, g.limit_ns, lane)) return false;
-  const C* Lp = Lb[l - 1] + (size_t)par * Pp;
-  C* Lc = Lb[l] + (size_t)box * P;
-  if (top) {
-    const C* A = a.l2l[l - 1] + (size_t)q * Pp * P + n0;
-    C acc{0, 0};
-    for (int m = lane; m < Pp; m += 32) acc += A[(size_t)m * P] * ldcg(Lp + m);
-    acc = wsum(acc);
-    if (lane == 0) atomic_add(Lc + n0, acc);
-  } else {
-    for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(Lp + m);
-    __syncwarp();
-    for (int n = lane; n < P; n += 32) atomic_add(Lc + n, colmv(a.l2l[l - 1] + (size_t)q * Pp * P + n, P, wsm, Pp));
-  }
-  __syncwarp();
-  if (lane == 0) red_add_release(g.cntL[l] + box, 1u);
-  return true;
-}
-
-// L2P of 32 consecutive sorted elements and the combination of eq. 9, added to
-// the fiber part in y; the last such item of the product advances the epoch
-template <class C>
-__device__ bool flow_e(const FlowArgs<C>& g, int it, unsigned e1, C* const* Lb, int lane) {
-  const FusedArgs<C>& a = g.f;
-  if (!warp_wait(g.gc + FG_NEAR, e1 * (unsigned)g.nnear, a.err, g.limit_ns, lane)) return false;
-  if (!warp_wait(g.gc + FG_FIBER, e1 * (unsigned)g.nfib, a.err, g.limit_ns, lane)) return false;
-  const int D = a.D, PD = a.P[D];
-  const int s = (it << 5) + lane;
-  const bool live = s < a.E;
-  const int box = live ? a.ne[D][a.s_li[s]] : 0;
-  if (!lanes_wait(live, g.cntL[D] + box, live ? e1 * g.expL[D][box] : 0u, a.err, g.limit_ns)) return false;
-  if (live) {
-    const C* Lbx = Lb[D] + (size_t)box * PD;
-    const C* cs = a.l2p + s;
-    C uf{0, 0}, df{0, 0};
-#pragma unroll 4
-    for (int t = 0; t < PD; ++t) {
-      const C Lt = ldcg(Lbx + t);
-      uf += cs[(size_t)t * a.E] * Lt;
-      df += cs[(size_t)(PD + t) * a.E] * Lt;
-    }
-    const int e = a.perm[s];
-    cplx u = to_d(uf + ldcg(a.Un + 2 * s));
-    cplx du = to_d(df + ldcg(a.Un + 2 * s + 1));
-    if (g.rsum) {
-      // FP32 product: the row-sum part of the near field, in FP64
-      const cplx p0 = a.ph[s] * a.x[2 * e], p1 = a.ph[s] * a.x[2 * e + 1];
-      const cplx* R = g.rsum + 4 * (size_t)s;
-      u += R[0] * p0 + R[1] * p1;
-      du += R[2] * p0 + R[3] * p1;
-    }
-    const cplx po = conj(a.ph[s]);
-    a.y[2 * e] = ldcg(a.y + 2 * e) + po * u;
-    a.y[2 * e + 1] = ldcg(a.y + 2 * e + 1) + a.c2 * (po * du);
-  }
-  __syncwarp();
-  bool ok = true;
-  if (lane == 0) {
-    const unsigned old = atom_add_acq_rel(g.gc + FG_EDONE, 1u);
-    if (old == e1 * (unsigned)g.nE - 1u) {
-      // every block has read this product's epoch: advance it for the next product
-      ok = wait_ge(g.gc + FG_ARRIVE, e1 * gridDim.x, a.err, g.limit_ns);
-      if (ok) red_add_release(g.gc + FG_EPOCH, 1u);
-    }
-  }
-  return __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
-}
-
-template <class C>
-__global__ void __launch_bounds__(FB, 3) matvec_flow_kernel(const __grid_constant__ FlowArgs<C> g) {
-  const FusedArgs<C>& a = g.f;
-  // a GMRES cycle that has already converged skips the products queued after it
-  if (a.done && *(volatile const int*)a.done != 0) return;
-  extern __shared__ unsigned char smraw[];
-  C* sm = reinterpret_cast<C*>(smraw);
-  __shared__ unsigned s_epoch;
-  if (threadIdx.x == 0) {
-    s_epoch = ld_acquire(g.gc + FG_EPOCH);
-    atomicAdd(g.gc + FG_ARRIVE, 1u);
-  }
-  __syncthreads();
-  const unsigned e1 = s_epoch + 1u;
-  const int par = (int)(s_epoch & 1u);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  if (g.trace && blockIdx.x == 0 && threadIdx.x == 0) g.trace[g.nitem] = gtimer();
-  if ((int)blockIdx.x >= g.gw) {
-    // the same-fiber blocks of eq. 9, counted on the fiber counter once written
-    const int b0 = blockIdx.x - g.gw, nb = gridDim.x - g.gw;
-    fiber_part(a, sm, b0, nb, warp, lane);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      unsigned n = 0;
-      if (b0 < a.nfft) n += (unsigned)((a.nfft - b0 + nb - 1) / nb);
-      if (b0 < a.nchunk) n += (unsigned)((a.nchunk - b0 + nb - 1) / nb);
-      if (n) red_add_release(g.gc + FG_FIBER, n);
-      if (g.trace) atomicMax(g.trace + g.nitem + 1, gtimer());
-    }
-    return;
-  }
-  // clear the other parity's local expansions for the next product
-  {
-    C* z = g.Lb[par ^ 1][1];
-    for (size_t t = (size_t)blockIdx.x * FB + threadIdx.x; t < g.Ltot; t += (size_t)g.gw * FB) z[t] = C{0, 0};
-  }
-  C* const* Lb = g.Lb[par];
-  C* wsm = sm + (size_t)warp * PF_NCOEF;
-  const int W = g.gw * FW;
-  int sg = 0, sbeg = 0;
-  for (int i = warp_first(blockIdx.x, warp, g.gw); i < g.nitem; i += W) {
-    while (i >= g.seg_end[sg]) sbeg = g.seg_end[sg++];
-    const int k = i - sbeg, l = g.seg_lev[sg];
-    bool ok = true;
-    switch (g.seg_kind[sg]) {
-      case FS_P2M: ok = flow_p2m(g, k, lane); break;
-      case FS_M2M: ok = flow_m2m(g, l, k, e1, wsm, lane); break;
-      case FS_M1: ok = flow_m1(g, k, e1, lane); break;
-      case FS_M2L: ok = flow_m2l(g, l, k, e1, Lb[l], wsm, lane); break;
-      case FS_ROOT1: ok = flow_root1(g, k, e1, Lb[1], lane); break;
-      case FS_NEAR: ok = flow_near(g, k, e1, wsm, lane); break;
-      case FS_L2L: ok = flow_l2l(g, l, k, e1, Lb, wsm, lane); break;
-      case FS_E: ok = flow_e(g, k, e1, Lb, lane); break;
-      default: break;
-    }
-    if (!ok) return;
-    if (g.trace && lane == 0) g.trace[i] = gtimer();
-    __syncwarp();
-  }
-}
-
-template <class C>
-size_t flow_smem(int maxfiber) {
-  const size_t w = (size_t)FW * PF_NCOEF;                   // per-warp scratch
-  const size_t f = 2 * (size_t)maxfiber + 512;              // fiber part, with its twiddles (FP64 FFTs)
-  return std::max(sizeof(C) * w, sizeof(cplx) * f);
-}
-
-template <class C>
-int flow_grid(int maxfiber) {
-  const size_t smem = flow_smem<C>(maxfiber);
-  if (cudaFuncSetAttribute(matvec_flow_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  int dev = 0, nsm = 0, per = 0, coop = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, matvec_flow_kernel<C>, FB, smem) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  // resident blocks per SM (PFMBEM_FLOW_BLOCKS_PER_SM overrides, for measurement)
-  static const char* bps = std::getenv("PFMBEM_FLOW_BLOCKS_PER_SM");
-  const int cap = bps ? std::max(1, std::atoi(bps)) : 3;
-  return nsm * std::min(per, cap);
-}
-
-// row sums R_s = sum_j B_sj of the cached near blocks (hi + lo, FP64): warp per
-// sorted element
+// Row sums R_s = sum_j B_sj of the cached near blocks (hi + lo, in FP64) for the
+// FP32 product's near sums in differences: one warp per sorted element.
 __global__ void near_rowsum_kernel(int E, int D, const int* __restrict__ s_li, const int* __restrict__ ne,
                                    const int* __restrict__ bb, const int* __restrict__ nc_sbase,
                                    const int64_t* __restrict__ nc_base, const cplxf* __restrict__ hi,
@@ -2412,164 +1795,10 @@ __global__ void near_rowsum_kernel(int E, int D, const int* __restrict__ s_li, c
   }
 }
 
-// expected contributions to L(l)[box] per product: the M2L pairs into the box
-// plus its L2L (or, at level 1, root) items
-__global__ void flow_expl_kernel(int npair, const int* __restrict__ pr_tgt, unsigned* __restrict__ expL) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p < npair) atomicAdd(expL + pr_tgt[p], 1u);
-}
-__global__ void flow_expl_add_kernel(int nne, const int* __restrict__ ne, unsigned add, unsigned* __restrict__ expL) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < nne) expL[ne[i]] += add;
-}
-
-template <class C>
-cudaError_t launch_flow(pfmbem* h, const cplx* x, cplx* y, bool f32, const int* done) {
-  auto& F = h->flow;
-  const int pi = f32 ? 1 : 0;
-  {
-    cudaError_t e = reset_device_waits(h);
-    if (e != cudaSuccess) return e;
-  }
-  FlowArgs<C> g{};
-  {
-    cudaError_t e = fill_args<C>(h, x, y, done, g.f);
-    if (e != cudaSuccess) return e;
-  }
-  FusedArgs<C>& a = g.f;
-  const int D = h->D;
-  static const char* mw = std::getenv("PFMBEM_M2L_WARP");
-  a.m2l_warp = mw ? std::atoi(mw) != 0 : !f32;
-  for (int l = 1; l <= D; ++l) {
-    g.cntM[l] = F.cnt + F.mo[pi][l];
-    g.cntL[l] = F.cnt + F.lo[pi][l];
-    g.expL[l] = F.expL + F.eo[l];
-    g.top[l] = (l >= 2 && (int64_t)h->lev[l].nne * h->lev[l].P <= flow_topw()) ? 1 : 0;
-    for (int p = 0; p < 2; ++p)
-      g.Lb[p][l] = f32 ? (C*)(void*)(F.L32[p] + F.Lo[l]) : (C*)(void*)(F.L64[p] + F.Lo[l]);
-  }
-  for (int l = 1; l <= D; ++l) g.kM[l] = (l == D) ? 1u : (l == 1 ? (unsigned)h->lev[1].P : (g.top[l] ? (unsigned)h->lev[l].P : 1u));
-  g.gc = F.cnt + F.go[pi];
-  g.Ltot = F.Lo[D + 1] - F.Lo[1];
-  g.near_item = F.near_item[pi];
-  g.nnear = F.nnear[pi];
-  g.nt = f32 ? 8 : 4;
-  g.dlo = f32 ? h->fz_dlo : nullptr;
-  g.rsum = f32 ? h->fz_rsum : nullptr;
-  g.nE = (h->E + 31) / 32;
-  g.nfib = h->fz_nfft + h->fz_nchunk;
-  const int grid = F.grid[pi];
-  g.gw = grid - F.fblk[pi];
-  g.limit_ns = h->opt.wait_us > 0 ? 1000ull * (unsigned long long)h->opt.wait_us : 1000000000ull;
-  // the item list
-  int ns = 0, acc = 0;
-  auto seg = [&](int kind, int lev, int n) {
-    if (n <= 0) return;
-    g.seg_kind[ns] = kind;
-    g.seg_lev[ns] = lev;
-    acc += n;
-    g.seg_end[ns++] = acc;
-  };
-  auto nm2l = [&](int l) { return a.m2l_warp ? (int)h->lev[l].nil : h->lev[l].nchunk; };
-  seg(FS_P2M, D, h->lev[D].nne);
-  for (int l = D - 1; l >= 2; --l) {
-    seg(FS_M2M, l, g.top[l] ? h->lev[l].nne * h->lev[l].P : h->lev[l].nne);
-    seg(FS_M2L, l + 1, nm2l(l + 1));
-  }
-  seg(FS_M1, 1, h->lev[1].nne * h->lev[1].P);
-  seg(FS_M2L, 2, nm2l(2));
-  seg(FS_M2L, 1, nm2l(1));
-  seg(FS_ROOT1, 1, h->lev[1].nne * h->lev[1].P);
-  seg(FS_NEAR, 0, g.nnear);
-  for (int l = 2; l <= D; ++l) seg(FS_L2L, l, g.top[l] ? h->lev[l].nne * h->lev[l].P : h->lev[l].nne);
-  seg(FS_E, 0, g.nE);
-  g.nseg = ns;
-  g.nitem = acc;
-  const size_t smem = flow_smem<C>(h->max_fiber);
-  // diagnostic (PFMBEM_FLOW_TRACE set): item completion times of this launch,
-  // summarised per segment on stderr
-  static const bool tracing = std::getenv("PFMBEM_FLOW_TRACE") != nullptr;
-  unsigned long long* tr = nullptr;
-  if (tracing && cudaMalloc(&tr, (g.nitem + 2) * sizeof(unsigned long long)) == cudaSuccess) {
-    cudaMemsetAsync(tr, 0, (g.nitem + 2) * sizeof(unsigned long long), h->stream);
-    g.trace = tr;
-  }
-  void* args[] = {&g};
-  const int ph = PH_FUSED + (f32 ? 16 : 0);
-  prof_begin(h, ph);
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)matvec_flow_kernel<C>, dim3(grid), dim3(FB), args, smem,
-                                              h->stream);
-  prof_end(h, ph);
-  if (tr) {
-    std::vector<unsigned long long> t(g.nitem + 2);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(t.data(), tr, t.size() * sizeof(unsigned long long),
-                                              cudaMemcpyDeviceToHost, h->stream);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
-    cudaFree(tr);
-    if (e == cudaSuccess) {
-      static const char* kn[] = {"P2M", "M2M", "M1", "M2L", "ROOT1", "NEAR", "L2L", "E"};
-      const unsigned long long t0 = t[g.nitem];
-      std::fprintf(stderr, "pfmbem flow %s (grid %d, workers %d):", f32 ? "f32" : "f64", grid, g.gw * FW);
-      int b = 0;
-      for (int q = 0; q < g.nseg; ++q) {
-        unsigned long long lo = ~0ull, hi = 0;
-        for (int i = b; i < g.seg_end[q]; ++i) {
-          lo = std::min(lo, t[i]);
-          hi = std::max(hi, t[i]);
-        }
-        std::fprintf(stderr, " %s%d[%d]:%.1f-%.1f", kn[g.seg_kind[q]], g.seg_lev[q], g.seg_end[q] - b,
-                     1e-3 * (double)(lo - t0), 1e-3 * (double)(hi - t0));
-        b = g.seg_end[q];
-      }
-      std::fprintf(stderr, " fiber-end:%.1f\n", 1e-3 * (double)(t[g.nitem + 1] - t0));
-    }
-  }
-  return e;
-}
-
-}  // namespace
-
-// Grid and fiber-block share of the dataflow product for both precisions; ok
-// is false when the tree or the device does not allow the dataflow form (the
-// barrier form then runs).
-cudaError_t k_flow_grids(pfmbem* h, bool* ok) {
-  auto& F = h->flow;
-  *ok = false;
-  const int D = h->D;
-  // off unless PFMBEM_FLOW=1 (measured slower than the barrier form at p_min = 24:
-  // single warps streaming translation tables from L2 set its critical path)
-  const char* fl = std::getenv("PFMBEM_FLOW");
-  if (!fl || std::atoi(fl) == 0 || D < 3 || D > PF_MAXLEVEL - 1 || !h->m2m31 || !h->root1 || !h->nc_vall)
-    return cudaSuccess;
-  const int nf = h->fz_nfft + h->fz_nchunk;
-  for (int pi = 0; pi < 2; ++pi) {
-    const int G = pi ? flow_grid<cplxf>(h->max_fiber) : flow_grid<cplx>(h->max_fiber);
-    if (G < 16) return cudaGetLastError();
-    static const char* fb = std::getenv("PFMBEM_FLOW_FBLK");
-    int fblk = fb ? std::atoi(fb) : std::max(1, G / 8);
-    fblk = std::max(1, std::min(fblk, std::max(nf, 1)));
-    fblk = std::min(fblk, G / 2);
-    F.grid[pi] = G;
-    F.fblk[pi] = fblk;
-  }
-  *ok = true;
-  return cudaGetLastError();
-}
-
 // Device tables of the single-launch product that read uploaded lists (buffers
-// allocated by the caller): the near blocks' row sums and, for the dataflow
-// form, the expected contributions to every L(l)[box].
+// allocated by the caller): the near blocks' row sums.
 cudaError_t k_fused_tables(pfmbem* h) {
-  auto& F = h->flow;
   const int D = h->D;
-  for (int l = 1; l <= D && F.on; ++l) {
-    const Level& L = h->lev[l];
-    unsigned* ex = F.expL + F.eo[l];
-    if (L.nil > 0) flow_expl_kernel<<<(int)((L.nil + 255) / 256), 256, 0, h->stream>>>((int)L.nil, L.pr_tgt, ex);
-    const bool top = l >= 2 && (int64_t)L.nne * L.P <= flow_topw();
-    const unsigned add = (l == 1 || top) ? (unsigned)L.P : 1u;
-    if (L.nne > 0) flow_expl_add_kernel<<<(L.nne + 255) / 256, 256, 0, h->stream>>>(L.nne, L.ne, add, ex);
-  }
   const Level& Lf = h->lev[D];
   if (h->fz_rsum)
     near_rowsum_kernel<<<(h->E * 32 + 255) / 256, 256, 0, h->stream>>>(h->E, D, h->s_li, Lf.ne, Lf.box_begin,
@@ -2761,10 +1990,6 @@ cudaError_t k_arnoldi_solve(pfmbem* h, cplx* y) {
 }
 
 cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done) {
-  if (h->flow.on) {
-    if (precision == PFMBEM_MIXED) return launch_flow<cplxf>(h, x, y, true, done);
-    return launch_flow<cplx>(h, x, y, false, done);
-  }
   if (precision == PFMBEM_MIXED) return launch_fused<cplxf>(h, x, y, true, done);
   return launch_fused<cplx>(h, x, y, false, done);
 }

@@ -4,7 +4,7 @@
   best iterate (its residual is below that of the zero start).
 * ENUMERIC: a right-hand side with a NaN entry makes the residual non-finite.
 * The handle stays usable after either: the next solve succeeds.
-(ETIMEOUT, a device-side wait that runs out, is in test_gpu_flow.py.)
+* ETIMEOUT: a device-wide barrier wait bounded by 1 us runs out.
 """
 import numpy as np
 import pytest
@@ -48,3 +48,32 @@ def test_enumeric_on_non_finite_rhs(pf):
     psi2 = np.zeros_like(B)
     ok = s.solve(psi2, tol=1e-8, maxit=300)
     assert ok.rel_residual <= 1e-8
+
+
+def test_device_wait_that_runs_out_returns_etimeout(pf):
+    """Every device-wide barrier wait of the single-launch product is bounded by
+    options.wait_us; a 1 us bound runs out on the 8x8 hexagon block.  The call that
+    reads the result returns PFMBEM_ETIMEOUT (no trap, no unbounded wait), the next
+    product on the handle starts from cleared barrier words, and a handle with the
+    default bound gives the per-stage kernels' product."""
+    from tests.gpu_common import rel
+    w = W.hexagon_8x8_n256()
+    s = pf.Solver(w, wait_us=1)
+    x = W.density_vector(w.E, 2)
+    y = np.zeros_like(x)
+    for _ in range(2):
+        with pytest.raises(pf.PfmbemError) as e:
+            s.matvec(x, y, pf.MIXED)
+        assert e.value.status == 7                # PFMBEM_ETIMEOUT
+    psi = np.zeros_like(x)
+    with pytest.raises(pf.PfmbemError) as e:
+        s.solve(psi, tol=1e-6, maxit=50)
+    assert e.value.status == 7
+    s.close()
+    ok = pf.Solver(w)
+    y2 = np.zeros_like(x)
+    ok.matvec(x, y2, pf.FP64)
+    ref = pf.Solver(w, launch=1)                  # per-stage kernels: no device-wide waits
+    y3 = np.zeros_like(x)
+    ref.matvec(x, y3, pf.FP64)
+    assert rel(y2, y3) < 1e-12
