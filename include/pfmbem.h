@@ -83,7 +83,11 @@ typedef struct {
                        microseconds; 0 = one second.  A wait that runs out stops the
                        product, and the call that reads its result returns
                        PFMBEM_ETIMEOUT (the next product starts afresh) */
-  int reserved[2];
+  int p_min_mixed;  /* lower bound of the per-level rule for the FP32 (mixed) product,
+                       which uses the central sub-blocks of the FP64 tables; 0 = 18.
+                       At most the FP64 order; the FP64 refinement of a mixed solve
+                       keeps the solution at the FP64 product's accuracy */
+  int reserved[1];
 } pfmbem_options;
 
 /* Outcome of a solve. */

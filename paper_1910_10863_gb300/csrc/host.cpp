@@ -945,6 +945,13 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if (p > PF_PMAX) return fail(h, PFMBEM_EINVAL, "expansion order above the library limit (128); use more levels");
     L.p = p;
     L.P = 2 * p + 1;
+    // the FP32 product's order: the same rule with the lower bound p_min_mixed
+    // (0 = 18: its truncation, ~0.4^p as for p_min, stays near the FP32 rounding)
+    {
+      const int pm32 = h->opt.p_min_mixed > 0 ? h->opt.p_min_mixed : 18;
+      const int rule = (int)std::ceil(x + 1.8 * std::pow(10.0, 2.0 / 3.0) * std::cbrt(x));
+      L.p32 = h->opt.p > 0 ? p : std::min(p, std::max(rule, pm32));
+    }
     L.sigma = k * L.d / std::sqrt(2.0);
     L.w.assign(L.P, 1.0);
     double wn = 1.0;
@@ -1354,6 +1361,17 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         h->fz_nchunk = (int)zchunk.size() / 3;
         if ((st = upload(h, &h->fz_fft, fft)) != PFMBEM_OK) return st;
         if ((st = upload(h, &h->fz_chunk, zchunk)) != PFMBEM_OK) return st;
+        {
+          // (fiber, row) of every row applied by rows, for the FP32 product's row sums
+          std::vector<int> rf;
+          for (size_t c = 0; c + 2 < zchunk.size(); c += 3)
+            for (int r = zchunk[c + 1]; r < zchunk[c + 2]; ++r) {
+              rf.push_back(zchunk[c]);
+              rf.push_back(r);
+            }
+          h->fz_nrowsum = (int)(rf.size() / 2);
+          if (h->fz_nrowsum > 0 && (st = upload(h, &h->fz_rowfib, rf)) != PFMBEM_OK) return st;
+        }
         if ((st = upload(h, &h->fh_base, fhb)) != PFMBEM_OK) return st;
         std::vector<cplx> twh(512);
         for (int j = 0; j < 512; ++j) twh[j] = cplx{std::cos(2.0 * M_PI * j / 1024.0), std::sin(2.0 * M_PI * j / 1024.0)};
@@ -1503,6 +1521,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
           h->fz_dlo = dalloc<cplxf>(h, 2 * (size_t)E);
           h->fz_rsum = dalloc<cplx>(h, 4 * (size_t)E);
           if (!h->fz_dlo || !h->fz_rsum) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near row sums)");
+        }
+        // rows of the fibers applied by rows (not by FFT), for their FP64 row sums
+        if (h->fz_nrowsum > 0 && h->fb_val) {
+          h->fz_frs = dalloc<cplx>(h, 4 * (size_t)E);
+          if (!h->fz_frs) return fail(h, PFMBEM_ENOMEM, "device allocation failed (fiber row sums)");
         }
       }
     }

@@ -36,6 +36,7 @@ struct NoInitAlloc : std::allocator<T> {
 // One level of the uniform quadtree (level 0 = root box of side H).
 struct Level {
   int p = 0, P = 0;          // order and coefficient count 2p+1
+  int p32 = 0;               // order of the FP32 product's expansions (<= p; the central sub-blocks)
   double d = 0;              // box side
   double sigma = 0;          // expansion scale k * d / sqrt(2)
   std::vector<double> w;     // w_n = sigma^|n| / |n|!, n = -p..p (index n + p)
@@ -271,6 +272,9 @@ struct pfmbem {
   bool fz_dirty = false;         // fz_err was found set: clear the wait state before the next launch
   cplxf* fz_dlo = nullptr;       // [2E] lo parts of the FP32 product's sorted densities
   cplx* fz_rsum = nullptr;       // [E][4] FP64 row sums of the cached near blocks
+  cplx* fz_frs = nullptr;        // [2E][2] FP64 row sums of the same-fiber rows applied by rows
+  int* fz_rowfib = nullptr;      // [nrowsum][2] (fiber, row) of those rows
+  int fz_nrowsum = 0;
   int* s_li = nullptr;           // sorted element -> index of its leaf among the non-empty leaves
   cplx* Un = nullptr;            // [E][2] near-field part of (U', dU'), FP64 and FP32
   cplxf* Unf = nullptr;

@@ -58,7 +58,12 @@ struct FusedArgs {
   const int* s_li;               // sorted element -> index of its leaf among the non-empty leaves
   int nne[PF_MAXLEVEL + 1];
   int nbox[PF_MAXLEVEL + 1];
+  // expansions of level l: P[l] coefficients used, stored in rows of S[l] from
+  // offset O[l] on (the FP32 product may run at a lower order than its tables:
+  // it then uses their central S-by-S sub-blocks; P = S and O = 0 otherwise)
   int P[PF_MAXLEVEL + 1];
+  int S[PF_MAXLEVEL + 1];
+  int O[PF_MAXLEVEL + 1];
   int nch[PF_MAXLEVEL + 1];      // M2L chunks (pairs of one offset) per level
   const int* ne[PF_MAXLEVEL + 1];
   const int* bb[PF_MAXLEVEL + 1];
@@ -126,6 +131,9 @@ struct FusedArgs {
   const cplx* rsum;
   const cplx* fh64;
   const cplx* tw64;
+  // FP32 product: row sums of the same-fiber rows applied by rows, split by the
+  // parity of the column ([2E rows][2], FP64), for their sums in differences
+  const cplx* frs;
 };
 
 __device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k) {
@@ -257,6 +265,57 @@ struct IdxTranspose {          // [n][l] -> [l][n], P x P
   int P;
   __device__ int operator()(int t) const { return (t % P) * P + t / P; }
 };
+// The used block of a table with rows of stride S: compact index t (row t / P,
+// column t % P) of the staged copy reads src[(t / P) S + t % P].
+struct IdxBlock {
+  int P, S;
+};
+
+template <class C>
+__device__ __forceinline__ void stage_copy(C* dst, const C* __restrict__ src, int n, IdxBlock b) {
+  constexpr int U = 8;
+  int t = threadIdx.x;
+  for (; t + (U - 1) * FB < n; t += U * FB) {
+    C v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int w = t + u * FB, r = w / b.P;
+      v[u] = src[(size_t)r * b.S + (w - r * b.P)];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) dst[t + u * FB] = v[u];
+  }
+  for (; t < n; t += FB) {
+    const int r = t / b.P;
+    dst[t] = src[(size_t)r * b.S + (t - r * b.P)];
+  }
+}
+
+// The used P x P block of a [P source][P target] operator with rows of stride S,
+// staged transposed ([target][source]) with batched loads.
+template <class C>
+__device__ __forceinline__ void stage_copy_bt(C* dst, const C* __restrict__ src, int P, int S) {
+  constexpr int U = 8;
+  const int n = P * P;
+  int t = threadIdx.x;
+  for (; t + (U - 1) * FB < n; t += U * FB) {
+    C v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int w = t + u * FB, r = w / P;
+      v[u] = src[(size_t)r * S + (w - r * P)];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int w = t + u * FB, r = w / P;
+      dst[(w - r * P) * P + r] = v[u];
+    }
+  }
+  for (; t < n; t += FB) {
+    const int r = t / P;
+    dst[(t - r * P) * P + r] = src[(size_t)r * S + (t - r * P)];
+  }
+}
 
 // In-place radix-2 FFTs of nseq sequences of length N = 2^lg (N <= 1024)
 // held one after another in shared memory, by the whole block:
@@ -972,6 +1031,49 @@ __device__ __forceinline__ int warp_first(int b, int w, int nb) {
   return b + nb * ((w - b % FW + FW) % FW);
 }
 
+// Rows rb..re of one fiber's same-fiber block (FP32 product) in differences:
+// with the element t of rows (r, r+1) and x_t its two unknowns,
+//   y_r = sum_c R_r[c] (x_c - x_t^(c mod 2)) + sum_{c even} R_r[c] x_t^(0) + sum_{c odd} R_r[c] x_t^(1),
+// the first sum in FP32 on hi + lo copies of x (differences to FP32 relative
+// accuracy, no cancellation of the hypersingular entries), the row sums
+// (FP64, from frs) times x_t in FP64.  xs holds the hi parts [n2] and the lo
+// parts [n2].
+__device__ void fiber_rows_diff(const FusedArgs<cplxf>& a, cplxf* xs, int fb, int rb, int re, int f0, int n2,
+                                bool cir, int warp, int lane) {
+  cplxf* xl = xs + n2;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n2; i += FB) {
+    const cplx v = a.x[2 * f0 + i];
+    xs[i] = to_f(v);
+    xl[i] = split_lo(v);
+  }
+  __syncthreads();
+  for (int r = rb + 2 * warp; r < re; r += 2 * FW) {
+    const cplxf* row0 = a.fb_val + a.fb_base[fb] + (cir ? 0 : (int64_t)r * n2);
+    const cplxf* row1 = row0 + n2;
+    const int sh = cir ? r : 0;
+    const bool two = r + 1 < re;
+    // every column this lane visits has the lane's parity
+    const cplxf th = xs[r + (lane & 1)], tl = xl[r + (lane & 1)];
+    cplxf a0{0, 0}, b0v{0, 0};
+    for (int c = lane; c < n2; c += 32) {
+      int i0 = c + sh;
+      if (i0 >= n2) i0 -= n2;
+      const cplxf d = (xs[i0] - th) + (xl[i0] - tl);
+      a0 += row0[c] * d;
+      if (two) b0v += row1[c] * d;
+    }
+    const cplxf s0 = wsum(a0);
+    const cplxf s1 = wsum(b0v);
+    if (lane == 0) {
+      const cplx x0 = a.x[2 * f0 + r], x1 = a.x[2 * f0 + r + 1];
+      const cplx* R = a.frs + 2 * (size_t)(2 * f0 + r);
+      a.y[2 * f0 + r] = to_d(s0) + R[0] * x0 + R[1] * x1;
+      if (two) a.y[2 * f0 + r + 1] = to_d(s1) + R[2] * x0 + R[3] * x1;
+    }
+  }
+}
+
 // The FFT-applied fibers of the same-fiber part (block b0 of nb), in the
 // arithmetic of F: y^(r) = IFFT(sum_s B^(r,s) FFT(x^(s))), one block per fiber;
 // xs holds [2N] values of F and, from tws_off on, the twiddle table.
@@ -1035,6 +1137,12 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
     const int fb = a.fb_chunk[3 * b], rb = a.fb_chunk[3 * b + 1], re = a.fb_chunk[3 * b + 2];
     const int f0 = a.foff[fb], n2 = 2 * (a.foff[fb + 1] - f0);
     const bool cir = a.circ[fb] != 0;
+    if constexpr (sizeof(C) == sizeof(cplxf)) {
+      if (a.frs) {
+        fiber_rows_diff(a, xs, fb, rb, re, f0, n2, cir, warp, lane);
+        continue;
+      }
+    }
     __syncthreads();
     for (int i = threadIdx.x; i < n2; i += FB) xs[i] = from_d<C>(a.x[2 * f0 + i]);
     __syncthreads();
@@ -1081,6 +1189,7 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
 template <class C>
 __device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, int wstride, C* sT, C* wsm, int lane) {
   const int P = a.P[l], Pc = a.P[l + 1], PP = Pc * P;
+  const int S = a.S[l], O = a.O[l], Sc = a.S[l + 1], Oc = a.O[l + 1];
   const bool dd = a.m2ml[l] != nullptr;
   const int rounds = (nbi + wstride - 1) / wstride;
   for (int rd = 0; rd < rounds; ++rd) {
@@ -1094,7 +1203,8 @@ __device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, in
     if (mine) {
       for (int t = lane; t < 4 * Pc; t += 32) {
         const int q = t / Pc, ch = 4 * box + q;
-        const C v = a.bb[l + 1][ch] < a.be[l + 1][ch] ? ldcg(a.M[l + 1] + (size_t)ch * Pc + (t - q * Pc)) : C{0, 0};
+        const C v = a.bb[l + 1][ch] < a.be[l + 1][ch] ? ldcg(a.M[l + 1] + (size_t)ch * Sc + Oc + (t - q * Pc))
+                                                      : C{0, 0};
         if (dd) {
           const cplx d = to_d(v);
           wh[t] = cplxf{(float)d.re, (float)d.im};
@@ -1108,12 +1218,13 @@ __device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, in
     dflt re[2] = {{0, 0}, {0, 0}}, im[2] = {{0, 0}, {0, 0}};
     for (int q = 0; q < 4; ++q) {
       __syncthreads();
+      // the used [Pc][P] block of T_q: source rows q Sc + Oc + m, target columns O + n
       if (dd) {
         cplxf* th = reinterpret_cast<cplxf*>(sT);
-        stage_copy(th, a.m2mh[l] + (size_t)q * PP, PP, IdxSame{});
-        stage_copy(th + PP, a.m2ml[l] + (size_t)q * PP, PP, IdxSame{});
+        stage_copy(th, a.m2mh[l] + (size_t)(q * Sc + Oc) * S + O, PP, IdxBlock{P, S});
+        stage_copy(th + PP, a.m2ml[l] + (size_t)(q * Sc + Oc) * S + O, PP, IdxBlock{P, S});
       } else {
-        stage_copy(sT, a.m2m[l] + (size_t)q * PP, PP, IdxSame{});
+        stage_copy(sT, a.m2m[l] + (size_t)(q * Sc + Oc) * S + O, PP, IdxBlock{P, S});
       }
       __syncthreads();
       if (!mine) continue;
@@ -1142,7 +1253,7 @@ __device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, in
       for (int h = 0; h < 2; ++h) {
         const int n = lane + 32 * h;
         if (n >= P) break;
-        a.M[l][(size_t)box * P + n] = dd ? from_d<C>(cplx{dd_value(re[h]), dd_value(im[h])}) : acc[h];
+        a.M[l][(size_t)box * S + O + n] = dd ? from_d<C>(cplx{dd_value(re[h]), dd_value(im[h])}) : acc[h];
       }
     }
   }
@@ -1155,6 +1266,7 @@ __device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, in
 template <class C>
 __device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, int wstride, C* sT, C* wsm, int lane) {
   const int P = a.P[l], Pp = a.P[l - 1], PP = Pp * P;
+  const int S = a.S[l], O = a.O[l], Sp = a.S[l - 1], Op = a.O[l - 1];
   const int rounds = (nl2l + wstride - 1) / wstride;
   for (int rd = 0; rd < rounds; ++rd) {
     if ((int)blockIdx.x + rd * wstride >= nl2l) break;
@@ -1163,10 +1275,11 @@ __device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, i
     const int box = mine ? a.ne[l][i] : 0, par = box >> 2, qb = box & 3;
     __syncwarp();
     if (mine)
-      for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Pp + m);
+      for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Sp + Op + m);
     for (int q = 0; q < 4; ++q) {
       __syncthreads();
-      stage_copy(sT, a.l2l[l - 1] + (size_t)q * PP, PP, IdxSame{});
+      // the used [Pp][P] block of T_q: source rows q Sp + Op + m, target columns O + n
+      stage_copy(sT, a.l2l[l - 1] + (size_t)(q * Sp + Op) * S + O, PP, IdxBlock{P, S});
       __syncthreads();
       if (!mine || qb != q) continue;
       for (int n = lane; n < P; n += 32) {
@@ -1178,7 +1291,7 @@ __device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, i
           s1 += sT[(m + 1) * P + n] * wsm[m + 1];
         }
         if (m < Pp) s0 += sT[m * P + n] * wsm[m];
-        atomic_add(a.L[l] + (size_t)box * P + n, s0 + s1);
+        atomic_add(a.L[l] + (size_t)box * S + O + n, s0 + s1);
       }
     }
   }
@@ -1204,7 +1317,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   {
     for (int l = 1; l <= D; ++l) {
       C* Lz = a.L[l];
-      const size_t nz = (size_t)a.nbox[l] * a.P[l];
+      const size_t nz = (size_t)a.nbox[l] * a.S[l];
       for (size_t t = (size_t)blockIdx.x * FB + threadIdx.x; t < nz; t += (size_t)G * FB) Lz[t] = C{0, 0};
     }
     // blocks [gA, G) apply the same-fiber blocks while the others run P2M
@@ -1250,17 +1363,18 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
           }
           continue;
         }
+        const int SD = a.S[D], OD = a.O[D];
         for (int n0 = 0; n0 < PD; n0 += 32) {
           const int n = n0 + lane;
           if (n < PD) {
             C acc0{0, 0}, acc1{0, 0};
 #pragma unroll 8
             for (int f = s0; f < s1; ++f) {
-              const C* cf = a.p2m + (size_t)f * 2 * PD;
+              const C* cf = a.p2m + (size_t)f * 2 * SD + OD;
               acc0 += cf[n] * a.dens[2 * f];
-              acc1 += cf[PD + n] * a.dens[2 * f + 1];
+              acc1 += cf[SD + n] * a.dens[2 * f + 1];
             }
-            a.M[D][(size_t)box * PD + n] = acc0 + acc1;
+            a.M[D][(size_t)box * SD + OD + n] = acc0 + acc1;
           }
         }
       }
@@ -1282,7 +1396,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     const int P = a.P[l], Pc = a.P[l + 1];
     const int jst = D - 1 - l;
     const int r0 = a.near_first ? (jst == 0 ? 0 : a.E) : (int)((int64_t)a.E * jst / nst);
-    const int r1 = a.near_first ? (jst == 0 ? a.E : a.E) : (int)((int64_t)a.E * (jst + 1) / nst);
+    const int r1 = a.near_first ? a.E : (int)((int64_t)a.E * (jst + 1) / nst);
     // near the top of the tree the boxes are too few to occupy the grid: one
     // warp per output coefficient, lanes over the 4 Pc child coefficients.  The
     // root then forms L(0) = (R T_0) [M(1) of its four children] at once.
@@ -1306,33 +1420,38 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       if (i >= nbi) {
         // M(1) of a level-1 box from its 16 level-3 boxes; the multipoles of
         // empty level-3 boxes are kept at zero, so the sum runs without branches
-        const int k = i - nbi, P1 = a.P[1], U1 = 16 * a.P[3];
+        const int k = i - nbi, P1 = a.P[1], P3 = a.P[3], S3 = a.S[3], O3 = a.O[3];
+        const int U1 = 16 * S3;
         const int b1 = a.ne[1][k / P1], n = k % P1;
-        const C* A = a.m2m31 + (size_t)n * U1;
-        const C* M3 = a.M[3] + (size_t)b1 * U1;
+        const C* A = a.m2m31 + (size_t)(a.O[1] + n) * U1 + O3;
+        const C* M3 = a.M[3] + (size_t)b1 * U1 + O3;
         C acc{0, 0};
 #pragma unroll 4
-        for (int u = lane; u < U1; u += 32) acc += A[u] * ldcg(M3 + u);
+        for (int u = lane; u < 16 * P3; u += 32) {
+          const int r = u / P3, v = r * S3 + (u - r * P3);
+          acc += A[v] * ldcg(M3 + v);
+        }
         acc = wsum(acc);
-        if (lane == 0) a.M[1][(size_t)b1 * P1 + n] = acc;
+        if (lane == 0) a.M[1][(size_t)b1 * a.S[1] + a.O[1] + n] = acc;
         continue;
       }
       if (top) {
         const int bi = i / P, n = i - bi * P;
         const int box = a.ne[l][bi];
-        const C* A = (l == 0 ? a.rootc : a.m2m[l]) + n;
+        const int S = a.S[l], Sc = a.S[l + 1], Oc = a.O[l + 1];
+        const C* A = (l == 0 ? a.rootc : a.m2m[l]) + a.O[l] + n;
         C acc{0, 0};
         for (int u = lane; u < 4 * Pc; u += 32) {
-          const int q = u / Pc, ch = 4 * box + q;
+          const int q = u / Pc, m = u - q * Pc, ch = 4 * box + q;
           if (a.bb[l + 1][ch] < a.be[l + 1][ch])
-            acc += A[(size_t)u * P] * ldcg(a.M[l + 1] + (size_t)ch * Pc + (u - q * Pc));
+            acc += A[(size_t)(q * Sc + Oc + m) * S] * ldcg(a.M[l + 1] + (size_t)ch * Sc + Oc + m);
         }
         acc = wsum(acc);
         if (lane == 0) {
           if (l == 0)
-            a.L[0][n] = acc;
+            a.L[0][a.O[0] + n] = acc;
           else
-            a.M[l][(size_t)box * P + n] = acc;
+            a.M[l][(size_t)box * S + a.O[l] + n] = acc;
         }
         continue;
       }
@@ -1415,9 +1534,13 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     if (!wpair) {
       for (int b = blockIdx.x; b < a.nch[l]; b += G) {
         const int o = a.ch_off[l][b], pb = a.ch_beg[l][b], pe = a.ch_end[l][b];
-        const C* To = a.m2lt[l] + (size_t)o * P * P;          // [n source][l target]
+        const int S = a.S[l], O = a.O[l];
+        const C* To = a.m2lt[l] + (size_t)o * S * S + (size_t)O * S + O;   // [n source][l target], used block
         __syncthreads();                                      // sT of the previous chunk is done
-        stage_copy(sT, To, P * P, IdxTranspose{P});
+        if (S == P)
+          stage_copy(sT, To, P * P, IdxTranspose{P});
+        else
+          stage_copy_bt(sT, To, P, S);
         __syncthreads();
         // two pairs per warp pass, sharing the operator rows read from shared memory
         for (int pi = pb + 2 * warp; pi < pe; pi += 2 * FW) {
@@ -1428,8 +1551,8 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
           const C phB = two ? from_d<C>(phase_m(a.alpha, a.pr_img[l][pi + 1])) : C{0, 0};
           __syncwarp();
           for (int m = lane; m < P; m += 32) {
-            wsm[m] = phA * ldcg(a.M[l] + (size_t)srcA * P + m);
-            wsm[P + m] = phB * ldcg(a.M[l] + (size_t)srcB * P + m);
+            wsm[m] = phA * ldcg(a.M[l] + (size_t)srcA * S + O + m);
+            wsm[P + m] = phB * ldcg(a.M[l] + (size_t)srcB * S + O + m);
           }
           __syncwarp();
           for (int n = lane; n < P; n += 32) {
@@ -1441,8 +1564,8 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
               rA += t * wsm[m];
               rB += t * wsm[P + m];
             }
-            atomic_add(a.L[l] + (size_t)tgtA * P + n, rA);
-            if (two) atomic_add(a.L[l] + (size_t)tgtB * P + n, rB);
+            atomic_add(a.L[l] + (size_t)tgtA * S + O + n, rA);
+            if (two) atomic_add(a.L[l] + (size_t)tgtB * S + O + n, rB);
           }
         }
       }
@@ -1453,7 +1576,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     const int nm2l = wpair ? a.npair[l] : 0;
     const int jst = nbst + l - 1;
     const int r0 = a.near_first ? (jst == 0 ? 0 : a.E) : (int)((int64_t)a.E * jst / nst);
-    const int r1 = a.near_first ? (jst == 0 ? a.E : a.E) : (int)((int64_t)a.E * (jst + 1) / nst);
+    const int r1 = a.near_first ? a.E : (int)((int64_t)a.E * (jst + 1) / nst);
     const int nitem = nl2l + nm2l + (r1 - r0);
     for (int i = wfirst; i < nitem; i += wstride) {
       if (i >= nl2l + nm2l) {
@@ -1466,20 +1589,25 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
           // the root's part of L(1) straight from the four level-1 multipoles
           // (those of empty level-1 boxes are kept at zero)
           const int bi = i / P, n = i - bi * P;
-          const int box = a.ne[1][bi];
-          const C* A = a.root1 + ((size_t)box * P + n) * 4 * P;
+          const int box = a.ne[1][bi], S1 = a.S[1], O1 = a.O[1];
+          const C* A = a.root1 + ((size_t)box * S1 + O1 + n) * 4 * S1;
           C acc{0, 0};
-          for (int u = lane; u < 4 * P; u += 32) acc += A[u] * ldcg(a.M[1] + u);
+          for (int u = lane; u < 4 * P; u += 32) {
+            const int q = u / P, v = q * S1 + O1 + (u - q * P);
+            acc += A[v] * ldcg(a.M[1] + v);
+          }
           acc = wsum(acc);
-          if (lane == 0) atomic_add(a.L[1] + (size_t)box * P + n, acc);
+          if (lane == 0) atomic_add(a.L[1] + (size_t)box * S1 + O1 + n, acc);
         } else if (top) {
           const int bi = i / P, n = i - bi * P;
           const int box = a.ne[l][bi], par = box >> 2, q = box & 3;
-          const C* A = a.l2l[l - 1] + (size_t)q * Pp * P + n;
+          const int S = a.S[l], O = a.O[l], Sp = a.S[l - 1], Op = a.O[l - 1];
+          const C* A = a.l2l[l - 1] + (size_t)(q * Sp + Op) * S + O + n;
           C acc{0, 0};
-          for (int m = lane; m < Pp; m += 32) acc += A[(size_t)m * P] * ldcg(a.L[l - 1] + (size_t)par * Pp + m);
+          for (int m = lane; m < Pp; m += 32)
+            acc += A[(size_t)m * S] * ldcg(a.L[l - 1] + (size_t)par * Sp + Op + m);
           acc = wsum(acc);
-          if (lane == 0) atomic_add(a.L[l] + (size_t)box * P + n, acc);
+          if (lane == 0) atomic_add(a.L[l] + (size_t)box * S + O + n, acc);
         } else {
           const int box = a.ne[l][i], par = box >> 2, q = box & 3;
           __syncwarp();
@@ -1517,11 +1645,12 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
         }
         continue;
       }
-      const C* To = a.m2lt[l] + (size_t)a.pr_off[l][pi] * P * P;
+      const int S = a.S[l], O = a.O[l];
+      const C* To = a.m2lt[l] + (size_t)a.pr_off[l][pi] * S * S + (size_t)O * S + O;
       __syncwarp();
-      for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * P + m);
+      for (int m = lane; m < P; m += 32) wsm[m] = phs * ldcg(a.M[l] + (size_t)src * S + O + m);
       __syncwarp();
-      for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * P + n, colmv(To + n, P, wsm, P));
+      for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * S + O + n, colmv(To + n, S, wsm, P));
     }
     if (!grid_barrier(a.bar, a.err, a.wait_ns)) return;
     stage_stamp(a.stamp, ks++);
@@ -1532,21 +1661,21 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   // coefficients lie coefficient-major, so the lanes' loads are contiguous, and
   // no lane sums need a reduction
   {
-    const int PD = a.P[D];
+    const int PD = a.P[D], SD = a.S[D], OD = a.O[D];
     const C c2 = from_d<C>(a.c2);
     const int nit = (a.E + 31) >> 5;
     for (int it = wfirst; it < nit; it += wstride) {
       const int s = (it << 5) + lane;
       if (s >= a.E) continue;
       const int box = a.ne[D][a.s_li[s]];
-      const C* Lb = a.L[D] + (size_t)box * PD;
-      const C* cs = a.l2p + s;
+      const C* Lb = a.L[D] + (size_t)box * SD + OD;
+      const C* cs = a.l2p + s + (size_t)OD * a.E;
       C uf{0, 0}, df{0, 0};
 #pragma unroll 16
       for (int t = 0; t < PD; ++t) {
         const C Lt = ldcg(Lb + t);
         uf += cs[(size_t)t * a.E] * Lt;
-        df += cs[(size_t)(PD + t) * a.E] * Lt;
+        df += cs[(size_t)(SD + t) * a.E] * Lt;
       }
       // back to the element's true position: times alpha^{m0} = conj(alpha^{-m0})
       const int e = a.perm[s];
@@ -1606,10 +1735,17 @@ cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedA
   a.opos = h->o_pos;
   a.x = x;
   a.y = y;
+  // the FP32 product may run at a lower order than the FP64 one (the central
+  // sub-blocks of the same tables); only with the folded top of the tree (level 3
+  // present), whose paths all take the strides
+  const bool reduce = sizeof(C) == sizeof(cplxf) && h->m2m31 != nullptr && h->D >= 3;
   for (int l = 0; l <= h->D; ++l) {
     const Level& L = h->lev[l];
     a.nne[l] = L.nne;
-    a.P[l] = L.P;
+    const int pu = reduce ? std::min(L.p, std::max(1, L.p32)) : L.p;
+    a.P[l] = 2 * pu + 1;
+    a.S[l] = L.P;
+    a.O[l] = L.p - pu;
     a.ne[l] = L.ne;
     a.bb[l] = L.box_begin;
     a.be[l] = L.box_end;
@@ -1644,6 +1780,7 @@ cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedA
       a.fh64 = h->fh_val;
       a.tw64 = h->tw;
     }
+    if (!plain && h->fz_frs) a.frs = h->fz_frs;
     a.m2m31 = h->m2m31f; a.root1 = h->root1f;
     a.nc_val = h->nc_valf; a.fb_val = h->fb_valf; a.fh_val = h->fh_valf; a.tw = h->twf;
   } else {
@@ -1795,10 +1932,38 @@ __global__ void near_rowsum_kernel(int E, int D, const int* __restrict__ s_li, c
   }
 }
 
+// Row sums of the same-fiber rows split by column parity: frs[row][q] = sum over
+// the columns c = q mod 2 of the FP64 row (a circulant fiber's rows are
+// rotations of its first row pair by whole elements, so they share its sums).
+// One warp per row of a fiber applied by rows.
+__global__ void fiber_rowsum_kernel(int nrow, const int* __restrict__ row_fiber, const int* __restrict__ foff,
+                                    const int64_t* __restrict__ fb_base, const int* __restrict__ circ,
+                                    const cplx* __restrict__ fb_val, cplx* __restrict__ frs) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= nrow) return;
+  const int fb = row_fiber[2 * i], r = row_fiber[2 * i + 1];
+  const int f0 = foff[fb], n2 = 2 * (foff[fb + 1] - f0);
+  const cplx* row = fb_val + fb_base[fb] + (int64_t)(circ[fb] ? (r & 1) : r) * n2;
+  cplx e{0, 0}, o{0, 0};
+  for (int c = lane; c < n2; c += 32) {
+    if (c & 1) o += row[c];
+    else e += row[c];
+  }
+  e = wsum(e);
+  o = wsum(o);
+  if (lane == 0) {
+    frs[2 * (size_t)(2 * f0 + r)] = e;
+    frs[2 * (size_t)(2 * f0 + r) + 1] = o;
+  }
+}
+
 // Device tables of the single-launch product that read uploaded lists (buffers
 // allocated by the caller): the near blocks' row sums.
 cudaError_t k_fused_tables(pfmbem* h) {
   const int D = h->D;
+  if (h->fz_frs && h->fz_nrowsum > 0)
+    fiber_rowsum_kernel<<<(h->fz_nrowsum * 32 + 255) / 256, 256, 0, h->stream>>>(
+        h->fz_nrowsum, h->fz_rowfib, h->fib_off, h->fb_base, h->fb_circ, h->fb_val, h->fz_frs);
   const Level& Lf = h->lev[D];
   if (h->fz_rsum)
     near_rowsum_kernel<<<(h->E * 32 + 255) / 256, 256, 0, h->stream>>>(h->E, D, h->s_li, Lf.ne, Lf.box_begin,

@@ -25,7 +25,7 @@ class Options(ctypes.Structure):
                 ("leaf_max", ctypes.c_int), ("depth", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("precision", ctypes.c_int), ("near_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int),
                 ("profile", ctypes.c_int), ("launch", ctypes.c_int), ("precond", ctypes.c_int),
-                ("wait_us", ctypes.c_int), ("reserved", ctypes.c_int * 2)]
+                ("wait_us", ctypes.c_int), ("p_min_mixed", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 class Info(ctypes.Structure):

@@ -236,11 +236,9 @@ def table3_square(ka2pi: float, f: float = 0.35, n: int = 256, c_water: float = 
                     centres=np.asarray(centres), radii=np.full(len(centres), r))
 
 
-def round_square_area(r: float = 1.0, n: int = 4096) -> float:
-    """Area enclosed by the round-square curve of Sec. 4 at scale r (shoelace
-    formula on n points; the curve is smooth, so this converges spectrally)."""
-    p = round_square_nodes(0.0, 0.0, r, n)
-    return 0.5 * abs(float(np.sum(p[:, 0] * np.roll(p[:, 1], -1) - np.roll(p[:, 0], -1) * p[:, 1])))
+def round_square_area(r: float = 1.0) -> float:
+    """Area enclosed by the round-square curve of Sec. 4 at scale r: 23 pi r^2 / 2 (Sec. 4)."""
+    return 23.0 * math.pi * r * r / 2.0
 
 
 def table3_block(ka2pi: float, f: float = 0.35, lattice: str = "square", scatterer: str = "circular",

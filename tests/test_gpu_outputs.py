@@ -1,8 +1,6 @@
 """Outputs of Sec. 4 through the C ABI: the x1-derivative of the scattered field
-and the energy transmission coefficient ETC against the oracle, and the stop
-band of the water/mercury crystal of Table 3."""
-import os
-
+and the energy transmission coefficient ETC against the oracle (the stop bands
+of Table 3 are in test_gpu_table3.py)."""
 import numpy as np
 import pytest
 
@@ -43,33 +41,3 @@ def test_field_x1_derivative_and_etc_match_oracle(pf):
     etc = pf.pfmbem_etc(s.h, psi, 1.0, 512)
     etc_ref = bem.etc(pb, psi, nmax=60, npts=512, x1=1.0)
     assert abs(etc - etc_ref) < 1e-6 * etc_ref
-
-
-def _golden_gap(scatterer, lattice, fill):
-    path = os.path.join(os.path.dirname(__file__), "golden", "table3_band_gaps.txt")
-    for line in open(path):
-        if line.startswith("#") or not line.strip():
-            continue
-        f = line.split()
-        if f[0] == scatterer and f[1] == lattice and abs(float(f[2]) - fill) < 1e-9:
-            return [float(x) for x in f[3:]]
-    raise KeyError((scatterer, lattice, fill))
-
-
-def test_table3_first_stop_band_circles_in_square_lattice(pf):
-    """Table 3, circular scatterers in a square lattice, filling fraction 35 %:
-    ETC < 3 % inside the printed first gap and above it below the gap."""
-    lo, hi, _, _ = _golden_gap("circular", "square", 0.35)
-    inside = [lo + 0.25 * (hi - lo), 0.5 * (lo + hi), lo + 0.7 * (hi - lo)]
-    outside = [0.1, 0.14]
-    for ka in inside + outside:
-        # stay away from the Wood anomalies ka/2pi = n/6 of normal incidence
-        assert min(abs(ka - n / 6) for n in range(1, 10)) > 0.01
-    for ka, expect_gap in [(k, True) for k in inside] + [(k, False) for k in outside]:
-        w = W.table3_square(ka, f=0.35)
-        s = pf.Solver(w, precision=pf.MIXED)
-        psi = np.zeros(2 * s.E, dtype=np.complex128)
-        info = s.solve(psi, tol=1e-6, check=False)
-        assert info.rel_residual <= 1e-6
-        etc = pf.pfmbem_etc(s.h, psi, 2.0, 256)
-        assert (etc < 0.03) == expect_gap, (ka, etc)
