@@ -88,6 +88,7 @@ struct Level {
   cplxf* m2lf = nullptr;
   cplxf* m2mf = nullptr;
   cplxf* m2ml = nullptr;     // lo parts of m2m (double-float M2M)
+  cplxf* l2ll = nullptr;     // lo parts of l2l (double-float L2L)
   cplxf* l2lf = nullptr;
 };
 
@@ -239,6 +240,7 @@ struct pfmbem {
   cplx* l2p_c = nullptr;
   cplxf* p2m_cf = nullptr;
   cplxf* p2m_cl = nullptr;       // lo parts of p2m_c (double-float P2M)
+  cplxf* l2p_cl = nullptr;       // lo parts of l2p_c (double-float L2P)
   cplxf* l2p_cf = nullptr;
   // FP32 work buffers of the mixed matvec
   int* tc_err = nullptr;         // set by the tensor-core M2L when a bounded wait gave up
@@ -377,6 +379,7 @@ struct TableLevels {
   cplx* A[PF_MAXLEVEL + 1];
   cplxf* Af[PF_MAXLEVEL + 1];
   cplxf* Al[PF_MAXLEVEL + 1];
+  cplxf* Bl[PF_MAXLEVEL + 1];
   cplx* B[PF_MAXLEVEL + 1];
   cplxf* Bf[PF_MAXLEVEL + 1];
 };

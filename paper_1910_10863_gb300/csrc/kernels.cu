@@ -197,6 +197,7 @@ __global__ void m2m_tables_kernel(TableLevels tl, double k) {
   cplxf* Al = tl.Al[l] + (size_t)q * Pc * P;
   cplx* B = tl.B[l] + (size_t)q * P * Pc;
   cplxf* Bf = tl.Bf[l] + (size_t)q * P * Pc;
+  cplxf* Bl = tl.Bl[l] + (size_t)q * P * Pc;
   for (int t = threadIdx.x; t < P * Pc; t += blockDim.x) {
     {
       const int m = t / P - pc, n = t % P - p;       // A: [q][m + pc][n + p]
@@ -220,6 +221,7 @@ __global__ void m2m_tables_kernel(TableLevels tl, double k) {
       const cplx v{sc * Jj * cs, sc * Jj * sn};
       B[t] = v;
       Bf[t] = to_f(v);
+      Bl[t] = split_lo(v);
     }
   }
 }
@@ -1958,6 +1960,9 @@ cudaError_t k_build_fmm_caches(pfmbem* h) {
   prof_begin(h, PH_SETUP);
   l2p_coef_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.iw_dev, h->k,
                                                              h->x0, h->y0, h->s_c, h->s_nu, h->l2p_c, h->l2p_cf);
+  if (h->l2p_cl)
+    to_f32_kernel<<<std::min<size_t>((nc + 255) / 256, 4096), 256, 0, h->stream>>>(nc, h->l2p_c, h->l2p_cf,
+                                                                                   h->l2p_cl);
   prof_end(h, PH_SETUP);
   return cudaGetLastError();
 }

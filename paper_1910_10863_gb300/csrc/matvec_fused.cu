@@ -124,6 +124,11 @@ struct FusedArgs {
   const cplxf* m2ml[PF_MAXLEVEL + 1];
   const cplxf* p2mh;                     // FP64 product, double-float P2M: hi and lo parts of p2m
   const cplxf* p2ml;
+  const cplxf* l2lh[PF_MAXLEVEL + 1];    // FP64 product, double-float L2L: hi and lo parts of l2l
+  const cplxf* l2ll[PF_MAXLEVEL + 1];
+  const cplxf* l2ph;                     // FP64 product, double-float L2P: hi and lo parts of l2p
+  const cplxf* l2pl;
+  int l2p_dd;                            // measurement (PFMBEM_L2P_DD=1): it measured slower than FP64
   // FP32 product: near-field sums in differences (dlo: lo parts of the sorted
   // densities, rsum: FP64 row sums of the near blocks) and the same-fiber FFTs
   // in FP64 (fh64, tw64: the FP64 block symbols and twiddles)
@@ -1267,7 +1272,11 @@ template <class C>
 __device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, int wstride, C* sT, C* wsm, int lane) {
   const int P = a.P[l], Pp = a.P[l - 1], PP = Pp * P;
   const int S = a.S[l], O = a.O[l], Sp = a.S[l - 1], Op = a.O[l - 1];
+  // FP64 product: double-float arithmetic from the hi and lo tables
+  const bool dd = a.l2ll[l - 1] != nullptr;
   const int rounds = (nl2l + wstride - 1) / wstride;
+  cplxf* wh = reinterpret_cast<cplxf*>(wsm);
+  cplxf* wl = wh + PF_NCOEF;
   for (int rd = 0; rd < rounds; ++rd) {
     if ((int)blockIdx.x + rd * wstride >= nl2l) break;
     const int i = wfirst + rd * wstride;
@@ -1275,14 +1284,37 @@ __device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, i
     const int box = mine ? a.ne[l][i] : 0, par = box >> 2, qb = box & 3;
     __syncwarp();
     if (mine)
-      for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Sp + Op + m);
+      for (int m = lane; m < Pp; m += 32) {
+        const C v = ldcg(a.L[l - 1] + (size_t)par * Sp + Op + m);
+        if (dd) {
+          const cplx d = to_d(v);
+          wh[m] = cplxf{(float)d.re, (float)d.im};
+          wl[m] = split_lo(d);
+        } else {
+          wsm[m] = v;
+        }
+      }
     for (int q = 0; q < 4; ++q) {
       __syncthreads();
       // the used [Pp][P] block of T_q: source rows q Sp + Op + m, target columns O + n
-      stage_copy(sT, a.l2l[l - 1] + (size_t)(q * Sp + Op) * S + O, PP, IdxBlock{P, S});
+      if (dd) {
+        cplxf* th = reinterpret_cast<cplxf*>(sT);
+        stage_copy(th, a.l2lh[l - 1] + (size_t)(q * Sp + Op) * S + O, PP, IdxBlock{P, S});
+        stage_copy(th + PP, a.l2ll[l - 1] + (size_t)(q * Sp + Op) * S + O, PP, IdxBlock{P, S});
+      } else {
+        stage_copy(sT, a.l2l[l - 1] + (size_t)(q * Sp + Op) * S + O, PP, IdxBlock{P, S});
+      }
       __syncthreads();
       if (!mine || qb != q) continue;
       for (int n = lane; n < P; n += 32) {
+        if (dd) {
+          const cplxf* th = reinterpret_cast<const cplxf*>(sT);
+          dflt re{0, 0}, im{0, 0};
+#pragma unroll 4
+          for (int m = 0; m < Pp; ++m) dd_cmac(re, im, th[m * P + n], th[PP + m * P + n], wh[m], wl[m]);
+          atomic_add(a.L[l] + (size_t)box * S + O + n, from_d<C>(cplx{dd_value(re), dd_value(im)}));
+          continue;
+        }
         C s0{0, 0}, s1{0, 0};
         int m = 0;
 #pragma unroll 4
@@ -1671,11 +1703,27 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       const C* Lb = a.L[D] + (size_t)box * SD + OD;
       const C* cs = a.l2p + s + (size_t)OD * a.E;
       C uf{0, 0}, df{0, 0};
+      if (a.l2pl && a.l2p_dd) {
+        // FP64 product: L2P in double-float arithmetic from the caches' hi and lo parts
+        const cplxf* ch = a.l2ph + s + (size_t)OD * a.E;
+        const cplxf* cl = a.l2pl + s + (size_t)OD * a.E;
+        dflt ur{0, 0}, ui{0, 0}, dr{0, 0}, di{0, 0};
+#pragma unroll 8
+        for (int t = 0; t < PD; ++t) {
+          const cplx Lt = to_d(ldcg(Lb + t));
+          const cplxf Lh{(float)Lt.re, (float)Lt.im}, Ll = split_lo(Lt);
+          dd_cmac(ur, ui, ch[(size_t)t * a.E], cl[(size_t)t * a.E], Lh, Ll);
+          dd_cmac(dr, di, ch[(size_t)(SD + t) * a.E], cl[(size_t)(SD + t) * a.E], Lh, Ll);
+        }
+        uf = from_d<C>(cplx{dd_value(ur), dd_value(ui)});
+        df = from_d<C>(cplx{dd_value(dr), dd_value(di)});
+      } else {
 #pragma unroll 16
-      for (int t = 0; t < PD; ++t) {
-        const C Lt = ldcg(Lb + t);
-        uf += cs[(size_t)t * a.E] * Lt;
-        df += cs[(size_t)(SD + t) * a.E] * Lt;
+        for (int t = 0; t < PD; ++t) {
+          const C Lt = ldcg(Lb + t);
+          uf += cs[(size_t)t * a.E] * Lt;
+          df += cs[(size_t)(SD + t) * a.E] * Lt;
+        }
       }
       // back to the element's true position: times alpha^{m0} = conj(alpha^{-m0})
       const int e = a.perm[s];
@@ -1803,9 +1851,19 @@ cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedA
       for (int l = 0; l < h->D; ++l) {
         a.m2mh[l] = h->lev[l].m2mf;
         a.m2ml[l] = h->lev[l].m2ml;
+        if (h->lev[l].l2ll) {
+          a.l2lh[l] = h->lev[l].l2lf;
+          a.l2ll[l] = h->lev[l].l2ll;
+        }
       }
       a.p2mh = h->p2m_cf;
       a.p2ml = h->p2m_cl;
+      if (h->l2p_cl) {
+        a.l2ph = h->l2p_cf;
+        a.l2pl = h->l2p_cl;
+        static const bool l2pdd = std::getenv("PFMBEM_L2P_DD") != nullptr;
+        a.l2p_dd = l2pdd ? 1 : 0;
+      }
     }
     a.m2m31 = h->m2m31; a.root1 = h->root1;
     a.nc_val = h->nc_val; a.fb_val = h->fb_val; a.fh_val = h->fh_val; a.tw = h->tw;
@@ -1923,12 +1981,20 @@ __global__ void near_rowsum_kernel(int E, int D, const int* __restrict__ s_li, c
   const int t = s - bb[ne[li]];
   const int ns = nc_sbase[li + 1] - nc_sbase[li];
   const int64_t r = nc_base[li] + (int64_t)t * ns * 4;
-  cplx acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  // double-float sums (about 48 bits) on the FP32 pipes; FP64 adds would run at
+  // 1/64 of their rate
+  dflt ar[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}}, ai[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
   for (int j = lane; j < ns; j += 32)
-    for (int q = 0; q < 4; ++q) acc[q] += to_d(hi[r + 4 * j + q]) + to_d(lo[r + 4 * j + q]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const cplxf h = hi[r + 4 * j + q], l = lo[r + 4 * j + q];
+      ar[q] = dd_add(ar[q], dflt{h.re, l.re});
+      ai[q] = dd_add(ai[q], dflt{h.im, l.im});
+    }
+#pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const cplx v = wsum(acc[q]);
-    if (lane == 0) rsum[4 * (size_t)s + q] = v;
+    const dflt vr = dd_wsum(ar[q]), vi = dd_wsum(ai[q]);
+    if (lane == 0) rsum[4 * (size_t)s + q] = cplx{dd_value(vr), dd_value(vi)};
   }
 }
 
