@@ -965,9 +965,26 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   mark("depth, sort, levels");
   // the M2L lists depend on the tree alone: a worker thread builds them while
   // the set-up below goes on (they are uploaded where the second stream starts)
+  // M2L on the tensor cores in the single-launch FP32 product: by default at
+  // the levels with at least tc_min_boxes non-empty boxes (below that the
+  // tiles of 128 targets run mostly empty); m2l_mode 2: every level, 1: none.
+  // Only where the product's order there gives 2P <= 80 (the operands' shared
+  // memory).  PFMBEM_TC_MIN_BOXES overrides the threshold, for measurement.
+  {
+    static const char* tmb = std::getenv("PFMBEM_TC_MIN_BOXES");
+    const int tc_min_boxes = tmb ? std::max(1, std::atoi(tmb)) : 1024;
+    const bool fusable = h->opt.near_mode == 0 && h->max_fiber <= 1024 && h->opt.launch == 0;
+    for (int l = 1; l <= D; ++l) {
+      Level& L = h->lev[l];
+      const int pu = D >= 3 ? std::min(L.p, std::max(1, L.p32)) : L.p;
+      L.tc_fused = fusable && h->opt.m2l_mode != 1 && tc_kpad(2 * pu + 1) <= 80 &&
+                   (h->opt.m2l_mode == 2 ? L.nne > 0 : L.nne >= tc_min_boxes);
+    }
+  }
   std::vector<M2LLists> m2l(D + 1);
   std::future<void> m2l_lists = std::async(std::launch::async, [h, D, &m2l]() {
-    for (int l = 1; l <= D; ++l) build_m2l_lists(h->lev[l], l, h->opt.m2l_mode == 2, m2l[l]);
+    for (int l = 1; l <= D; ++l)
+      build_m2l_lists(h->lev[l], l, h->opt.m2l_mode == 2 || h->lev[l].tc_fused, m2l[l]);
   });
   // ---------------------------------------------------- lists
   const int nD = 1 << D;
@@ -1179,12 +1196,18 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         L.m2ltf = a32; a32 += tm;
         L.m2ltl = a32; a32 += tm;
         tl.T[l] = L.m2l; tl.Tt[l] = L.m2lt; tl.Tf[l] = L.m2lf; tl.Ttf[l] = L.m2ltf; tl.Ttl[l] = L.m2ltl;
-        if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2) {
+        // tensor-core operators: the per-stage kernels' (full order), the
+        // single-launch FP32 product's (its order, interleaved layout)
+        if (tc_kpad(P) <= 128 && h->opt.m2l_mode == 2 && h->opt.launch == 1) {
           const int kp = tc_kpad(P);
           L.tc_B = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
           if (!L.tc_B) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
-        } else {
-          L.tc_ntile = 0;
+        }
+        if (L.tc_fused) {
+          const int pu = D >= 3 ? std::min(L.p, std::max(1, L.p32)) : L.p;
+          const int kp = tc_kpad(2 * pu + 1);
+          L.tc_Bf = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
+          if (!L.tc_Bf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
         }
       }
       if (l < D) {
@@ -1435,7 +1458,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if ((st = upload(h, &L.il_src, o.src)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.il_off, o.off)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.il_img, o.img)) != PFMBEM_OK) return st;
-    if (h->opt.m2l_mode == 2) {
+    if (h->opt.m2l_mode == 2 || L.tc_fused) {
       L.tc_ntile = o.ntile;
       if ((st = upload(h, &L.tc_box, o.tbox)) != PFMBEM_OK) return st;
       if ((st = upload(h, &L.tc_noff, o.tnoff)) != PFMBEM_OK) return st;
@@ -1485,8 +1508,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     if (h->aux[i]) CK(cudaStreamWaitEvent(h->stream, h->aux_ev[i], 0));
   h->astream = nullptr;
   trace(h, h->stream, "main: streams joined");
-  for (int l = 1; l <= D; ++l)
-    if (h->lev[l].tc_B) CK(k_tc_build_operator(h, l));
+  for (int l = 1; l <= D; ++l) {
+    Level& L = h->lev[l];
+    if (L.tc_B) CK(k_tc_build_operator(h, l));
+    if (L.tc_Bf) CK(k_tc_build_operator_fused(h, l, 2 * (D >= 3 ? std::min(L.p, std::max(1, L.p32)) : L.p) + 1));
+  }
   if (cache) {
     // single-launch matvec unless the tensor-core M2L (its own kernel) is on
     bool tensor = false;
@@ -1504,17 +1530,33 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
             for (int s2 = Lf.hbegin[Lf.hne[li]]; s2 < Lf.hend[Lf.hne[li]]; ++s2) sli[s2] = (int)li;
         }
         if ((st = upload(h, &h->s_li, sli)) != PFMBEM_OK) return st;
+        // per sorted element, where its near-field row lies: (offset of the row's
+        // blocks, first source << 32 | sources), one 16-byte load
+        if (!nc_base.empty()) {
+          std::vector<int64_t> meta(2 * (size_t)E, 0);
+          const Level& Lf = h->lev[D];
+          for (size_t li = 0; li < Lf.hne.size(); ++li) {
+            const int b = Lf.hne[li], j0 = nc_sbase[li], ns = nc_sbase[li + 1] - j0;
+            for (int s2 = Lf.hbegin[b]; s2 < Lf.hend[b]; ++s2) {
+              meta[2 * (size_t)s2] = nc_base[li] + (int64_t)(s2 - Lf.hbegin[b]) * ns * 4;
+              meta[2 * (size_t)s2 + 1] = ((int64_t)j0 << 32) | (int64_t)ns;
+            }
+          }
+          if ((st = upload(h, &h->nr_meta, meta)) != PFMBEM_OK) return st;
+        }
         h->Un = dalloc<cplx>(h, (size_t)2 * E);
         h->Unf = dalloc<cplxf>(h, (size_t)2 * E);
         if (!h->Un || !h->Unf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (near sums)");
-        h->fz_bar = dalloc<unsigned>(h, 2);
-        h->arn_bar = dalloc<unsigned>(h, 2);
+        h->fz_bar = dalloc<unsigned long long>(h, 2);
+        h->arn_bar = dalloc<unsigned long long>(h, 2);
         h->fz_err = dalloc<int>(h, 1);
         h->fz_stamp = dalloc<unsigned long long>(h, 32);
+        // diagnostic: every block's arrival at every barrier (PFMBEM_BLOCK_TIMES)
+        if (std::getenv("PFMBEM_BLOCK_TIMES")) h->fz_arrive = dalloc<unsigned long long>(h, (size_t)32 * 1024);
         if (!h->fz_bar || !h->arn_bar || !h->fz_err || !h->fz_stamp)
           return fail(h, PFMBEM_ENOMEM, "device allocation failed (barrier)");
-        CK(cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned), h->stream));
-        CK(cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->stream));
+        CK(cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned long long), h->stream));
+        CK(cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned long long), h->stream));
         CK(cudaMemsetAsync(h->fz_err, 0, sizeof(int), h->stream));
         h->fused = true;
         h->pc = h->pc_val != nullptr || h->pr_val != nullptr;

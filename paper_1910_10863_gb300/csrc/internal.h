@@ -76,6 +76,8 @@ struct Level {
   int* tc_src = nullptr;     // [ntile][49][128]
   int* tc_img = nullptr;     // [ntile][49][128]
   uint16_t* tc_B = nullptr;  // [49][3][kp][kp] BF16 parts of the real-embedded operators
+  uint16_t* tc_Bf = nullptr; // the same for the single-launch FP32 product's central block (order p32)
+  bool tc_fused = false;     // M2L of this level on tensor cores in the single-launch FP32 product
   cplx* m2l = nullptr;       // [49][P][P]: row = target coefficient, col = source coefficient
   cplx* m2lt = nullptr;      // the same operators transposed, [49][P source][P target]
   cplxf* m2ltf = nullptr;
@@ -251,8 +253,9 @@ struct pfmbem {
   bool fused = false;
   int fz_grid64 = 0, fz_grid32 = 0;
   int arn_grid = 0;              // blocks of the device-side GMRES step (0: host-side steps)
-  unsigned* arn_bar = nullptr;   // [2] its barrier words
-  unsigned* fz_bar = nullptr;    // [2] barrier arrivals and generation
+  unsigned long long* arn_bar = nullptr;   // its barrier's arrival counter
+  unsigned long long* fz_bar = nullptr;    // [2] barrier arrival counters (FP64, FP32 product)
+  unsigned long long* fz_arrive = nullptr; // diagnostic: [barrier][block] arrival times
   int fz_nfft = 0;               // fibers whose block-circulant block is applied by FFT
   int* fz_fft = nullptr;         // their indices
   int64_t* fh_base = nullptr;    // [M] first frequency of the fiber's block symbol (-1: none)
@@ -277,7 +280,10 @@ struct pfmbem {
   cplx* fz_frs = nullptr;        // [2E][2] FP64 row sums of the same-fiber rows applied by rows
   int* fz_rowfib = nullptr;      // [nrowsum][2] (fiber, row) of those rows
   int fz_nrowsum = 0;
+  int fz_treg32 = 0;             // staged-operator region of the FP32 single-launch product (complex values)
+  size_t fz_tcb32 = 0;           // shared memory of the FP32 product's tensor-core M2L operands (0: none)
   int* s_li = nullptr;           // sorted element -> index of its leaf among the non-empty leaves
+  int64_t* nr_meta = nullptr;    // [E][2] near-field row of a sorted element: block offset, (first source << 32) | sources
   cplx* Un = nullptr;            // [E][2] near-field part of (U', dU'), FP64 and FP32
   cplxf* Unf = nullptr;
   unsigned long long* fz_stamp = nullptr;   // [32] stage end times (diagnostic)
@@ -335,6 +341,7 @@ void prof_release(pfmbem* h);
 // tensor-core M2L (m2l_tc.cu)
 int tc_kpad(int P);
 cudaError_t k_tc_build_operator(pfmbem* h, int level);
+cudaError_t k_tc_build_operator_fused(pfmbem* h, int level, int Pu);
 cudaError_t k_m2l_tc(pfmbem* h, int level, const cplxf* M, cplxf* L);
 cudaError_t k_build_caches(pfmbem* h, cudaEvent_t ktab_done = nullptr);
 cudaError_t k_build_fiber_blocks(pfmbem* h);

@@ -14,52 +14,22 @@
 // (A0B0, A0B1, A1B0, A0B2, A1B1, A2B0) accumulate in FP32 in tensor memory
 // across all offsets, which keeps FP32-level accuracy.  The epilogue adds the
 // tile's local expansions into L (which already holds the L2L contribution).
-#include <cuda_bf16.h>
-
 #include <algorithm>
 #include <cstring>
 #include <vector>
 
 #include "internal.h"
 
+#include "tc_common.cuh"
+
 namespace {
 
-constexpr int TILE = 128;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-// Byte offset of element (r, k) in a K-major operand tile without swizzle:
-// 8-row x 16-byte core matrices, consecutive along K (LBO = 128 B), 8-row
-// groups SBO = (kp / 8) * 128 B apart.
-__host__ __device__ __forceinline__ uint32_t canon(int r, int k, int kp) {
-  return (uint32_t)((((r >> 3) * (kp >> 3) + (k >> 3)) << 7) + ((r & 7) << 4) + ((k & 7) << 1));
-}
-
-// Shared-memory matrix descriptor (tcgen05): start >> 4 in bits 0-13, leading
-// byte offset >> 4 in 16-29, stride byte offset >> 4 in 32-45, version 1 in
-// bits 46-47, no swizzle.
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
-
-// Instruction descriptor: FP32 accumulator, BF16 A and B, both K-major, M x N.
-__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void split3(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
-  a = __float2bfloat16_rn(x);
-  float r = x - __bfloat162float(a);
-  b = __float2bfloat16_rn(r);
-  r -= __bfloat162float(b);
-  c = __float2bfloat16_rn(r);
-}
+using tc::TILE;
+using tc::canon;
+using tc::idesc_bf16;
+using tc::sdesc;
+using tc::smem_u32;
+using tc::split3;
 
 template <int KP>
 __global__ void __launch_bounds__(TILE) m2l_tc_kernel(int P, const int* __restrict__ tile_box,
@@ -227,19 +197,55 @@ __global__ void __launch_bounds__(TILE) m2l_tc_kernel(int P, const int* __restri
   }
 }
 
-// Operator tiles of one level in the canonical layout: three BF16 parts split
-// (in FP64) from the FP64 table T [49][P][P] (row = target coefficient) of the
-// real-embedded complex operator.  One thread per (offset, row, column).
-__global__ void tc_split_kernel(int P, int kp, const cplx* __restrict__ T, __nv_bfloat16* __restrict__ out) {
+// x = b0 + b1 + b2 in BF16 parts, split in FP64.
+__device__ __forceinline__ void split3d(double x, __nv_bfloat16& b0, __nv_bfloat16& b1, __nv_bfloat16& b2) {
+  b0 = __float2bfloat16_rn((float)x);
+  const double r1 = x - (double)__bfloat162float(b0);
+  b1 = __float2bfloat16_rn((float)r1);
+  const double r2 = r1 - (double)__bfloat162float(b1);
+  b2 = __float2bfloat16_rn((float)r2);
+}
+
+// The operators of the single-launch FP32 product, for its interleaved layout:
+// K index 2c + 0 / 2c + 1 multiplies the real / imaginary part of source
+// coefficient c; output row n < Pu gives the real part of target coefficient
+// n and row imrow + n its imaginary part:
+//   row n:         [Re T_nc, -Im T_nc],   row imrow + n: [Im T_nc, Re T_nc].
+// Used block of Pu coefficients from offset O of the FP64 table T [49][S][S].
+// One thread per (offset, output, source coefficient).
+__global__ void tc_split_fused_kernel(int Pu, int S, int O, int kp, int imrow, const cplx* __restrict__ T,
+                                      __nv_bfloat16* __restrict__ out) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t n2 = (int64_t)(2 * P) * (2 * P);
+  const int64_t n2 = (int64_t)Pu * Pu;
   if (i >= 49 * n2) return;
-  const int o = (int)(i / n2), rem = (int)(i % n2), c = rem / (2 * P), k = rem % (2 * P);
-  const cplx v = T[((size_t)o * P + (c % P)) * P + (k % P)];
+  const int o = (int)(i / n2), rem = (int)(i % n2), n = rem / Pu, c = rem % Pu;
+  const cplx v = T[((size_t)o * S + O + n) * S + O + c];
+  const size_t base = (size_t)o * 3 * kp * kp;
+  const double val[4] = {v.re, -v.im, v.im, v.re};
+  const int rows[2] = {n, imrow + n};
+  for (int q = 0; q < 4; ++q) {
+    __nv_bfloat16 b[3];
+    split3d(val[q], b[0], b[1], b[2]);
+    const uint32_t off = canon(rows[q >> 1], 2 * c + (q & 1), kp) >> 1;
+    for (int j = 0; j < 3; ++j) out[base + (size_t)j * kp * kp + off] = b[j];
+  }
+}
+
+// Operator tiles of one level in the canonical layout: three BF16 parts split
+// (in FP64) from the FP64 table T [49][S][S] (row = target coefficient) of the
+// real-embedded complex operator, its used block of Pu coefficients from
+// offset O.  One thread per (offset, row, column).
+__global__ void tc_split_kernel(int Pu, int S, int O, int kp, const cplx* __restrict__ T,
+                                __nv_bfloat16* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t n2 = (int64_t)(2 * Pu) * (2 * Pu);
+  if (i >= 49 * n2) return;
+  const int o = (int)(i / n2), rem = (int)(i % n2), c = rem / (2 * Pu), k = rem % (2 * Pu);
+  const cplx v = T[((size_t)o * S + O + (c % Pu)) * S + O + (k % Pu)];
   double x;
-  if (c < P && k < P) x = v.re;
-  else if (c < P) x = -v.im;
-  else if (k < P) x = v.im;
+  if (c < Pu && k < Pu) x = v.re;
+  else if (c < Pu) x = -v.im;
+  else if (k < Pu) x = v.im;
   else x = v.re;
   const __nv_bfloat16 b0 = __float2bfloat16_rn((float)x);
   const double r1 = x - (double)__bfloat162float(b0);
@@ -255,7 +261,7 @@ __global__ void tc_split_kernel(int P, int kp, const cplx* __restrict__ T, __nv_
 
 }  // namespace
 
-int tc_kpad(int P) { return ((2 * P + 15) / 16) * 16; }
+int tc_kpad(int P) { return tc::kpad(P); }
 
 cudaError_t k_tc_build_operator(pfmbem* h, int l) {
   Level& a = h->lev[l];
@@ -264,8 +270,23 @@ cudaError_t k_tc_build_operator(pfmbem* h, int l) {
   if (e != cudaSuccess) return e;
   const int64_t n = 49LL * (2 * a.P) * (2 * a.P);
   prof_begin(h, PH_SETUP);
-  tc_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(a.P, kp, a.m2l,
+  tc_split_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(a.P, a.P, 0, kp, a.m2l,
                                                                       reinterpret_cast<__nv_bfloat16*>(a.tc_B));
+  prof_end(h, PH_SETUP);
+  return cudaGetLastError();
+}
+
+// The central Pu-coefficient block for the single-launch FP32 product, in its
+// interleaved layout.
+cudaError_t k_tc_build_operator_fused(pfmbem* h, int l, int Pu) {
+  Level& a = h->lev[l];
+  const int kp = tc_kpad(Pu);
+  cudaError_t e = cudaMemsetAsync(a.tc_Bf, 0, sizeof(uint16_t) * 49 * 3 * (size_t)kp * kp, h->stream);
+  if (e != cudaSuccess) return e;
+  const int64_t n = 49LL * Pu * Pu;
+  prof_begin(h, PH_SETUP);
+  tc_split_fused_kernel<<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(
+      Pu, a.P, (a.P - Pu) / 2, kp, tc::imrow(Pu), a.m2l, reinterpret_cast<__nv_bfloat16*>(a.tc_Bf));
   prof_end(h, PH_SETUP);
   return cudaGetLastError();
 }

@@ -33,15 +33,22 @@
 // ends; each wait is nevertheless bounded (one second of %globaltimer), after which the
 // block records an error flag and returns, and the host reports
 // PFMBEM_ETIMEOUT instead of a result.
+#include <atomic>
 #include <cstdio>
 #include <cstdlib>
 
 #include "internal.h"
+#include "tc_common.cuh"
 
 namespace {
 
 constexpr int FB = 256;          // threads per block
 constexpr int FW = FB / 32;      // warps per block
+
+// Threads and warps of the running block: the single-launch product runs with
+// 256 threads per block, or 512 in its tensor-core form (one block per SM)
+__device__ __forceinline__ int nt() { return (int)blockDim.x; }
+__device__ __forceinline__ int nw() { return (int)(blockDim.x >> 5); }
 constexpr int TSP = 49;          // largest order count P whose M2L operator is staged in shared memory
 constexpr int TSIZE = TSP * (TSP + 1);
 
@@ -90,6 +97,7 @@ struct FusedArgs {
   const C* l2p;                      // [2][P_D][E], coefficient-major
   const int64_t* nc_base;
   const int* nc_sbase;
+  const longlong2* nr_meta;          // per sorted element: block offset of its near row, (first source << 32) | sources
   const int* nc_src;
   const C* nc_val;
   int nchunk;                        // direct-row chunks (fibers not applied by FFT)
@@ -107,12 +115,27 @@ struct FusedArgs {
   int fblk;                          // blocks applying the same-fiber blocks during stage A (0: all, after P2M)
   int m2l_warp;                      // M2L one warp per pair (1) or one block per staged chunk (0)
   int near_first;                    // measurement: every near-field row in the first B stage
-  unsigned* bar;                     // [0] arrivals, [1] generation
+  unsigned long long* bar;           // arrival counter of the device-wide barriers
   int* err;
   unsigned long long wait_ns;        // bound of every barrier wait
   unsigned long long* stamp;         // optional stage end times (ns), written by block 0
+  unsigned long long* arrive;        // optional [barrier][block] arrival times (ns)
+  unsigned long long* bdone;         // optional [barrier][block] end of the block items (ns)
   const int* done;                   // optional: the product is skipped when *done != 0
   int tws_off;                       // shared-memory offset (in C) of the twiddle copy of the fiber part
+  int treg;                          // shared-memory region (in C) of the staged operators, >= TSIZE
+  // FP32 product, M2L on the tensor cores (tcgen05) at the levels with tc_kp > 0:
+  // tiles of 128 target boxes; block item (tile, group of the tile's offsets)
+  int tc_any;
+  int tc_kp[PF_MAXLEVEL + 1];            // MMA N = K: 2P padded to 16 (0: CUDA cores)
+  int tc_ngrp[PF_MAXLEVEL + 1];          // offset groups per tile
+  int tc_ntile[PF_MAXLEVEL + 1];
+  const int* tc_box[PF_MAXLEVEL + 1];    // [tile][128] target box, -1 padding
+  const int* tc_noff[PF_MAXLEVEL + 1];   // [tile] offsets present
+  const int* tc_offs[PF_MAXLEVEL + 1];   // [tile][49] offset ids
+  const int* tc_src[PF_MAXLEVEL + 1];    // [tile][49][128] source box, -1: none
+  const int* tc_img[PF_MAXLEVEL + 1];    // [tile][49][128] image m of the source
+  const uint16_t* tc_B[PF_MAXLEVEL + 1]; // [49][3][kp][kp] BF16 parts of the operators (canonical layout)
   // FP64 product only: the near-field sums in double-float arithmetic (FP32
   // hi + lo pairs), on the FP32 pipes, from these lo parts
   const cplxf* nc_lo;                // lo parts of the near blocks (hi parts: the FP32 copy)
@@ -170,8 +193,7 @@ __device__ __forceinline__ void atomic_add(cplx* p, cplx v) {
   atomicAdd(&p->im, v.im);
 }
 __device__ __forceinline__ void atomic_add(cplxf* p, cplxf v) {
-  atomicAdd(&p->re, v.re);
-  atomicAdd(&p->im, v.im);
+  atomicAdd(reinterpret_cast<float2*>(p), make_float2(v.re, v.im));   // one 8-byte vector atomic
 }
 
 template <class C>
@@ -184,45 +206,40 @@ __device__ __forceinline__ C wsum(C v) {
   return v;
 }
 
-// Device-wide barrier with a bounded wait; false when any block gave up.  The
-// arrival is an acquire-release add at GPU scope (it publishes this block's
-// writes and, for the last arrival, takes in everyone else's); the last
-// arrival resets the counter and advances the generation word with a release
-// add, and the others poll the generation with acquire loads.
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
-  unsigned old;
-  asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
-__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned ld_acquire(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+// Device-wide barrier with a bounded wait; false when any block gave up.  One
+// 64-bit arrival counter that only grows: a block's arrival is a release add
+// (it publishes the block's writes), whose old value tells the barrier's
+// target, the next multiple of the grid size; the block then polls the counter
+// with acquire loads (taking in everyone else's writes) until it reaches the
+// target.  Each completed launch adds a multiple of the grid size, so the
+// counter stays aligned across launches of one grid size; it is cleared after
+// a wait ran out.  Optionally records the block's arrival time (ns).
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ bool grid_barrier(unsigned* bar, int* err, unsigned long long limit = 1000000000ull) {
+__device__ bool grid_barrier(unsigned long long* bar, int* err, unsigned long long limit = 1000000000ull,
+                             unsigned long long* arrive = nullptr) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
-    const unsigned g = ld_acquire(bar + 1);
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    if (arrive) arrive[blockIdx.x] = t0;
     int ok = 1;
-    if (atom_add_acq_rel(bar, 1u) == gridDim.x - 1) {
-      atomicExch(bar, 0u);
-      red_add_release(bar + 1, 1u);            // release the other blocks
-    } else {
-      // poll the generation word; give up after one second of device time
-      unsigned long long t0, t;
-      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-      while (ld_acquire(bar + 1) == g) {
-        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-        if (t - t0 > limit) {
-          atomicExch(err, 1);
-          ok = 0;
-          break;
-        }
+    const unsigned long long G = gridDim.x;
+    unsigned long long old;
+    asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(bar) : "memory");
+    const unsigned long long target = (old / G + 1) * G;
+    while (ld_acquire64(bar) < target) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      if (t - t0 > limit) {
+        atomicExch(err, 1);
+        ok = 0;
+        break;
       }
     }
     s_ok = ok && *(volatile int*)err == 0;
@@ -246,6 +263,77 @@ __device__ __forceinline__ C colmv(const C* __restrict__ A, int P, const C* w, i
   return a0 + a1;
 }
 
+template <class C>
+__device__ __forceinline__ C shfl_c(C v, int src) {
+  v.re = __shfl_sync(0xffffffffu, v.re, src);
+  v.im = __shfl_sync(0xffffffffu, v.im, src);
+  return v;
+}
+
+// One warp: y[n] = sum_{u < K} A[u P + n] w[u] for every n < P, handed to
+// out(n, y[n]).  Full passes of 32 outputs; the last r = P mod 32 outputs are
+// shared by 32 / r lane groups that split the u range, their partial sums
+// combined by shuffles (P = 37 then costs 1.17 K steps instead of 2 K).
+template <class C, class Out>
+__device__ __forceinline__ void warp_colmv(const C* A, int P, const C* w, int K, int lane, Out out) {
+  const int full = P & ~31;
+  for (int n0 = 0; n0 < full; n0 += 32) out(n0 + lane, colmv(A + n0 + lane, P, w, K));
+  const int r = P - full;
+  if (r == 0) return;
+  const int g = 32 / r, grp = lane / r, nr = lane - grp * r;
+  C acc{0, 0};
+  if (grp < g) {
+    const C* Ar = A + full + nr;
+#pragma unroll 4
+    for (int u = grp; u < K; u += g) acc += Ar[(size_t)u * P] * w[u];
+  }
+  C s = acc;
+  for (int k = 1; k < g; ++k) {
+    const C o = shfl_c(acc, k * r + nr);
+    s += o;
+  }
+  if (lane < r) out(full + lane, s);
+}
+
+// One warp, two vectors sharing the operator rows: yA[n] = sum_{m < P} T[n P + m]
+// wA[m] and yB likewise, handed to out(n, yA[n], yB[n]); the last P mod 32 rows
+// are split over lane groups as in warp_colmv.
+template <class C, class Out>
+__device__ __forceinline__ void warp_rowmv2(const C* T, int P, const C* wA, const C* wB, int lane, Out out) {
+  const int full = P & ~31;
+  for (int n0 = 0; n0 < full; n0 += 32) {
+    const C* row = T + (size_t)(n0 + lane) * P;
+    C rA{0, 0}, rB{0, 0};
+#pragma unroll 4
+    for (int m = 0; m < P; ++m) {
+      const C t = row[m];
+      rA += t * wA[m];
+      rB += t * wB[m];
+    }
+    out(n0 + lane, rA, rB);
+  }
+  const int r = P - full;
+  if (r == 0) return;
+  const int g = 32 / r, grp = lane / r, nr = lane - grp * r;
+  C rA{0, 0}, rB{0, 0};
+  if (grp < g) {
+    const C* row = T + (size_t)(full + nr) * P;
+#pragma unroll 4
+    for (int m = grp; m < P; m += g) {
+      const C t = row[m];
+      rA += t * wA[m];
+      rB += t * wB[m];
+    }
+  }
+  C sA = rA, sB = rB;
+  for (int k = 1; k < g; ++k) {
+    const C oA = shfl_c(rA, k * r + nr), oB = shfl_c(rB, k * r + nr);
+    sA += oA;
+    sB += oB;
+  }
+  if (lane < r) out(full + lane, sA, sB);
+}
+
 // Block-wide copy of n values from global to shared memory with the loads of a
 // thread batched ahead of its stores (eight in flight): the copy then costs
 // about one L2 round trip instead of one per element the thread moves.
@@ -254,14 +342,14 @@ template <class C, class Idx>
 __device__ __forceinline__ void stage_copy(C* dst, const C* __restrict__ src, int n, Idx idx) {
   constexpr int U = 8;
   int t = threadIdx.x;
-  for (; t + (U - 1) * FB < n; t += U * FB) {
+  for (; t + (U - 1) * nt() < n; t += U * nt()) {
     C v[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) v[u] = src[t + u * FB];
+    for (int u = 0; u < U; ++u) v[u] = src[t + u * nt()];
 #pragma unroll
-    for (int u = 0; u < U; ++u) dst[idx(t + u * FB)] = v[u];
+    for (int u = 0; u < U; ++u) dst[idx(t + u * nt())] = v[u];
   }
-  for (; t < n; t += FB) dst[idx(t)] = src[t];
+  for (; t < n; t += nt()) dst[idx(t)] = src[t];
 }
 struct IdxSame {
   __device__ int operator()(int t) const { return t; }
@@ -280,17 +368,17 @@ template <class C>
 __device__ __forceinline__ void stage_copy(C* dst, const C* __restrict__ src, int n, IdxBlock b) {
   constexpr int U = 8;
   int t = threadIdx.x;
-  for (; t + (U - 1) * FB < n; t += U * FB) {
+  for (; t + (U - 1) * nt() < n; t += U * nt()) {
     C v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int w = t + u * FB, r = w / b.P;
+      const int w = t + u * nt(), r = w / b.P;
       v[u] = src[(size_t)r * b.S + (w - r * b.P)];
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u) dst[t + u * FB] = v[u];
+    for (int u = 0; u < U; ++u) dst[t + u * nt()] = v[u];
   }
-  for (; t < n; t += FB) {
+  for (; t < n; t += nt()) {
     const int r = t / b.P;
     dst[t] = src[(size_t)r * b.S + (t - r * b.P)];
   }
@@ -303,22 +391,47 @@ __device__ __forceinline__ void stage_copy_bt(C* dst, const C* __restrict__ src,
   constexpr int U = 8;
   const int n = P * P;
   int t = threadIdx.x;
-  for (; t + (U - 1) * FB < n; t += U * FB) {
+  for (; t + (U - 1) * nt() < n; t += U * nt()) {
     C v[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int w = t + u * FB, r = w / P;
+      const int w = t + u * nt(), r = w / P;
       v[u] = src[(size_t)r * S + (w - r * P)];
     }
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int w = t + u * FB, r = w / P;
+      const int w = t + u * nt(), r = w / P;
       dst[(w - r * P) * P + r] = v[u];
     }
   }
-  for (; t < n; t += FB) {
+  for (; t < n; t += nt()) {
     const int r = t / P;
     dst[(t - r * P) * P + r] = src[(size_t)r * S + (t - r * P)];
+  }
+}
+
+// The four quadrant operators of a translation table, stacked: staged row
+// u = q Pn + m (q < 4, m < Pn) holds the used columns O .. O + P of table row
+// q Sn + On + m (base = table + On S + O; rows of stride S).  Sixteen loads in
+// flight per thread: the whole stack costs about two L2 round trips.
+template <class C>
+__device__ __forceinline__ void stage_copy_quad(C* dst, const C* __restrict__ base, int P, int Pn, int S, int Sn) {
+  constexpr int U = sizeof(C) == sizeof(cplxf) ? 16 : 8;
+  const int n = 4 * Pn * P;
+  int t = threadIdx.x;
+  for (; t < n; t += U * nt()) {
+    C v[U];
+#pragma unroll
+    for (int k = 0; k < U; ++k) {
+      const int w = t + k * nt();
+      if (w < n) {
+        const int u = w / P, q = u / Pn;
+        v[k] = base[(size_t)(q * Sn + (u - q * Pn)) * S + (w - u * P)];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < U; ++k)
+      if (t + k * nt() < n) dst[t + k * nt()] = v[k];
   }
 }
 
@@ -367,7 +480,7 @@ __global__ void fiber_symbol_kernel(const int* __restrict__ fib_list, const int*
                                     const int64_t* __restrict__ fb_base, const cplx* __restrict__ rows,
                                     const int64_t* __restrict__ fh_base, const cplx* __restrict__ tw,
                                     cplx* __restrict__ fh, cplxf* __restrict__ fhf) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   cplx* s = reinterpret_cast<cplx*>(smraw);      // [2][N]
   const int fb = fib_list[blockIdx.x];
   const int N = foff[fb + 1] - foff[fb], lg = __ffs(N) - 1;
@@ -494,10 +607,9 @@ __device__ __forceinline__ double dd_value(dflt v) { return (double)v.h + (doubl
 // 1/64 of the FP32 rate) and FP64-level accuracy.  Writes the FP64 Un of s.
 template <class C>
 __device__ __forceinline__ void near_row_dd(const FusedArgs<C>& a, int s, int lane) {
-  const int D = a.D, li = a.s_li[s];
-  const int t = s - a.bb[D][a.ne[D][li]];
-  const int j0 = a.nc_sbase[li], ns = a.nc_sbase[li + 1] - j0;
-  const int64_t r = a.nc_base[li] + (int64_t)t * ns * 4;
+  const longlong2 mt = __ldg(a.nr_meta + s);
+  const int64_t r = mt.x;
+  const int j0 = (int)(mt.y >> 32), ns = (int)(mt.y & 0xffffffffll);
   const cplxf* qh = a.nc_hi + r;
   const cplxf* ql = a.nc_lo + r;
   const cplxf* dh = a.dens_dd;
@@ -532,32 +644,47 @@ __device__ __forceinline__ void near_row_dd(const FusedArgs<C>& a, int s, int la
 // same-fiber blocks (entries ~1/h that cancel to O(1) on smooth densities) then
 // lose no digits to the FP32 sums.
 __device__ __forceinline__ void near_row_diff(const FusedArgs<cplxf>& a, int s, int lane) {
-  const int D = a.D, li = a.s_li[s];
-  const int t = s - a.bb[D][a.ne[D][li]];
-  const int j0 = a.nc_sbase[li], ns = a.nc_sbase[li + 1] - j0;
-  const cplxf* row = a.nc_val + a.nc_base[li] + (int64_t)t * ns * 4;
-  const int* src = a.nc_src + j0;
+  // where the row lies (one load), the target's own densities, and the first
+  // NJ source indices of every lane, all independent of one another
+  const longlong2 mt = __ldg(a.nr_meta + s);
+  const cplxf* row = a.nc_val + mt.x;
+  const int* src = a.nc_src + (int)(mt.y >> 32);
+  const int ns = (int)(mt.y & 0xffffffffll);
   const cplxf tph = ldcg(a.dens + 2 * s), tpl = ldcg(a.dlo + 2 * s);
   const cplxf tvh = ldcg(a.dens + 2 * s + 1), tvl = ldcg(a.dlo + 2 * s + 1);
-  cplxf u0{0, 0}, d0{0, 0}, u1{0, 0}, d1{0, 0};
-  int j = lane;
-  for (; j + 32 < ns; j += 64) {
-    const int f0 = src[j], f1 = src[j + 32];
-    const cplxf p0 = (ldcg(a.dens + 2 * f0) - tph) + (ldcg(a.dlo + 2 * f0) - tpl);
-    const cplxf v0 = (ldcg(a.dens + 2 * f0 + 1) - tvh) + (ldcg(a.dlo + 2 * f0 + 1) - tvl);
-    const cplxf p1 = (ldcg(a.dens + 2 * f1) - tph) + (ldcg(a.dlo + 2 * f1) - tpl);
-    const cplxf v1 = (ldcg(a.dens + 2 * f1 + 1) - tvh) + (ldcg(a.dlo + 2 * f1 + 1) - tvl);
-    u0 += row[4 * j] * p0 + row[4 * j + 1] * v0;
-    d0 += row[4 * j + 2] * p0 + row[4 * j + 3] * v0;
-    u1 += row[4 * j + 128] * p1 + row[4 * j + 129] * v1;
-    d1 += row[4 * j + 130] * p1 + row[4 * j + 131] * v1;
+  // NJ sources per lane and pass: their blocks and densities loaded together,
+  // the next pass's source indices fetched meanwhile; a lane past the end takes
+  // the target itself as its source, whose difference is zero
+  constexpr int NJ = 4;
+  int f[NJ];
+#pragma unroll
+  for (int k = 0; k < NJ; ++k) {
+    const int jj = lane + 32 * k;
+    f[k] = jj < ns ? __ldg(src + jj) : s;
   }
-  for (; j < ns; j += 32) {
-    const int f = src[j];
-    const cplxf p = (ldcg(a.dens + 2 * f) - tph) + (ldcg(a.dlo + 2 * f) - tpl);
-    const cplxf v = (ldcg(a.dens + 2 * f + 1) - tvh) + (ldcg(a.dlo + 2 * f + 1) - tvl);
-    u0 += row[4 * j] * p + row[4 * j + 1] * v;
-    d0 += row[4 * j + 2] * p + row[4 * j + 3] * v;
+  cplxf u0{0, 0}, d0{0, 0}, u1{0, 0}, d1{0, 0};
+  for (int jb = 0; jb < ns; jb += 32 * NJ) {
+    cplxf p[NJ], v[NJ], q[NJ][4];
+#pragma unroll
+    for (int k = 0; k < NJ; ++k) {
+      const int jj = jb + lane + 32 * k;
+      p[k] = (ldcg(a.dens + 2 * f[k]) - tph) + (ldcg(a.dlo + 2 * f[k]) - tpl);
+      v[k] = (ldcg(a.dens + 2 * f[k] + 1) - tvh) + (ldcg(a.dlo + 2 * f[k] + 1) - tvl);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) q[k][c] = jj < ns ? row[4 * jj + c] : cplxf{0, 0};
+    }
+#pragma unroll
+    for (int k = 0; k < NJ; ++k) {
+      const int jj = jb + 32 * NJ + lane + 32 * k;
+      f[k] = jj < ns ? __ldg(src + jj) : s;
+    }
+#pragma unroll
+    for (int k = 0; k < NJ; k += 2) {
+      u0 += q[k][0] * p[k] + q[k][1] * v[k];
+      d0 += q[k][2] * p[k] + q[k][3] * v[k];
+      u1 += q[k + 1][0] * p[k + 1] + q[k + 1][1] * v[k + 1];
+      d1 += q[k + 1][2] * p[k + 1] + q[k + 1][3] * v[k + 1];
+    }
   }
   const cplxf u = wsum(u0 + u1), du = wsum(d0 + d1);
   if (lane == 0) {
@@ -578,11 +705,10 @@ __device__ __forceinline__ void near_row(const FusedArgs<C>& a, int s, int lane)
       return;
     }
   }
-  const int D = a.D, li = a.s_li[s];
-  const int t = s - a.bb[D][a.ne[D][li]];
-  const int j0 = a.nc_sbase[li], ns = a.nc_sbase[li + 1] - j0;
-  const C* row = a.nc_val + a.nc_base[li] + (int64_t)t * ns * 4;
-  const int* src = a.nc_src + j0;
+  const longlong2 mt = __ldg(a.nr_meta + s);
+  const C* row = a.nc_val + mt.x;
+  const int* src = a.nc_src + (int)(mt.y >> 32);
+  const int ns = (int)(mt.y & 0xffffffffll);
   C u0{0, 0}, d0{0, 0}, u1{0, 0}, d1{0, 0};
   int j = lane;
   for (; j + 32 < ns; j += 64) {
@@ -619,7 +745,7 @@ __global__ void precond_symbol_kernel(const int* __restrict__ fib_list, const in
                                       const int64_t* __restrict__ fh_base, const cplx* __restrict__ fh,
                                       double eta, cplx c2, const cplx* __restrict__ tw, cplx* __restrict__ pc,
                                       cplxf* __restrict__ pcf) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   cplx* sq = reinterpret_cast<cplx*>(smraw);      // [4][N]
   const int fb = fib_list[blockIdx.x];
   const int N = foff[fb + 1] - foff[fb], lg = __ffs(N) - 1;
@@ -661,7 +787,7 @@ __global__ void precond_rows_kernel(const int* __restrict__ fib_list, const int*
                                     const int64_t* __restrict__ kbase, const cplx* __restrict__ kval, double eta,
                                     cplx c2, const int64_t* __restrict__ pr_base, cplx* __restrict__ pr,
                                     cplxf* __restrict__ prf) {
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   const int fb = fib_list[blockIdx.x];
   const int N = foff[fb + 1] - foff[fb];
   cplx* b = reinterpret_cast<cplx*>(smraw);        // [4][N] blocks b_d
@@ -791,7 +917,7 @@ __global__ void precond_apply_kernel(int M, const int* __restrict__ foff, const 
                                      const cplx* __restrict__ x, cplx* __restrict__ y, const int* done,
                                      int tws_off) {
   if (done && *(volatile const int*)done != 0) return;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   C* xs = reinterpret_cast<C*>(smraw);
   C* tws = xs + tws_off;                          // twiddles in shared memory
   for (int i = threadIdx.x; i < 512; i += blockDim.x) tws[i] = tw[i];
@@ -833,7 +959,7 @@ struct ArnArgs {
   cplx* acc;                         // [2][2 (m+1) + 1] CGS2 sums h1, h2 and ||w||^2, by step parity
   double* ctl;                       // [0] estimate (out), [1] ||b||, [2] threshold
   int* ictl;                         // [0] done, [1] steps completed in the cycle, [2] reason (1 est, 2 breakdown, 3 restart)
-  unsigned* bar;
+  unsigned long long* bar;
   int* err;
   // with the block-Jacobi preconditioner, z_{j+1} = P^-1 v_{j+1} fiber by fiber
   cplx* Zn;                          // [n] z_{j+1}, or null (no preconditioner)
@@ -864,7 +990,7 @@ __device__ __forceinline__ void arn_dots(const ArnArgs& a, int nc, int t0, int t
 template <class C>
 __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
   if (*(volatile const int*)a.ictl != 0) return;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ cplx sh[ARN_MAXC];
   __shared__ C shc[ARN_MAXC];                       // sh in the precision of the updates
   __shared__ double red[FW];
@@ -1028,12 +1154,12 @@ __global__ void arnoldi_solve_kernel(const cplx* __restrict__ H, const cplx* __r
 }
 
 // Warp items: item i goes to block i mod nb and, within the block, to warp
-// (i / nb + i mod nb) mod FW, so that a stage whose item count is not a
+// (i / nb + i mod nb) mod nw(), so that a stage whose item count is not a
 // multiple of the grid spreads its extra items over all four sub-partitions
 // of the SMs instead of piling them on warp 0.  Returns the first item of
-// warp w of block b; the stride is nb * FW.
+// warp w of block b; the stride is nb * nw().
 __device__ __forceinline__ int warp_first(int b, int w, int nb) {
-  return b + nb * ((w - b % FW + FW) % FW);
+  return b + nb * ((w - b % nw() + nw()) % nw());
 }
 
 // Rows rb..re of one fiber's same-fiber block (FP32 product) in differences:
@@ -1047,13 +1173,13 @@ __device__ void fiber_rows_diff(const FusedArgs<cplxf>& a, cplxf* xs, int fb, in
                                 bool cir, int warp, int lane) {
   cplxf* xl = xs + n2;
   __syncthreads();
-  for (int i = threadIdx.x; i < n2; i += FB) {
+  for (int i = threadIdx.x; i < n2; i += nt()) {
     const cplx v = a.x[2 * f0 + i];
     xs[i] = to_f(v);
     xl[i] = split_lo(v);
   }
   __syncthreads();
-  for (int r = rb + 2 * warp; r < re; r += 2 * FW) {
+  for (int r = rb + 2 * warp; r < re; r += 2 * nw()) {
     const cplxf* row0 = a.fb_val + a.fb_base[fb] + (cir ? 0 : (int64_t)r * n2);
     const cplxf* row1 = row0 + n2;
     const int sh = cir ? r : 0;
@@ -1089,19 +1215,19 @@ __device__ void fiber_fft(int nfft, const int* fft_fib, const int* foff, const i
   // the twiddle table in shared memory: the FFT passes then wait on no global load
   F* tws = xs + tws_off;
   if (b0 < nfft) {
-    for (int i = threadIdx.x; i < 512; i += FB) tws[i] = tw[i];
+    for (int i = threadIdx.x; i < 512; i += nt()) tws[i] = tw[i];
   }
   for (int b = b0; b < nfft; b += nb) {
     const int fb = fft_fib[b];
     const int f0 = foff[fb], N = foff[fb + 1] - f0, lg = __ffs(N) - 1;
     __syncthreads();
-    for (int t = threadIdx.x; t < 2 * N; t += FB) {
+    for (int t = threadIdx.x; t < 2 * N; t += nt()) {
       const int q = t >> lg, f = t & (N - 1);
       xs[t] = from_d<F>(x[2 * (f0 + f) + q]);
     }
     block_fft(xs, 2, lg, -1, tws);
     const F* Bh = fh_val + 4 * fh_base[fb];
-    for (int k = threadIdx.x; k < N; k += FB) {
+    for (int k = threadIdx.x; k < N; k += nt()) {
       const F x0 = xs[k], x1 = xs[N + k];
       const F* bk = Bh + 4 * k;
       xs[k] = bk[0] * x0 + bk[1] * x1;
@@ -1109,7 +1235,7 @@ __device__ void fiber_fft(int nfft, const int* fft_fib, const int* foff, const i
     }
     block_fft(xs, 2, lg, +1, tws);
     const R inv = (R)1 / (R)N;
-    for (int t = threadIdx.x; t < 2 * N; t += FB) {
+    for (int t = threadIdx.x; t < 2 * N; t += nt()) {
       const int rr = t >> lg, e = f0 + (t & (N - 1));
       y[2 * e + rr] = to_d(inv * xs[t]);
     }
@@ -1149,9 +1275,9 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
       }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < n2; i += FB) xs[i] = from_d<C>(a.x[2 * f0 + i]);
+    for (int i = threadIdx.x; i < n2; i += nt()) xs[i] = from_d<C>(a.x[2 * f0 + i]);
     __syncthreads();
-    for (int r = rb + 2 * warp; r < re; r += 2 * FW) {
+    for (int r = rb + 2 * warp; r < re; r += 2 * nw()) {
       const C* row0 = a.fb_val + a.fb_base[fb] + (cir ? 0 : (int64_t)r * n2);
       const C* row1 = row0 + n2;
       const int sh = cir ? r : 0;
@@ -1186,11 +1312,310 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
   }
 }
 
+// M2M into the nbi boxes of level l as block items: group g of nw() boxes (one
+// per warp) goes to block g mod G, which stages the four stacked quadrant
+// operators [4 Pc][P] once (the same for every box of the level) and applies
+// them to each warp's box in one pass over its 4 Pc child coefficients.  A few
+// blocks then carry the level while the others go on to their warp items.
+// Called by all threads of the block.
+template <class C>
+__device__ void m2m_quad(const FusedArgs<C>& a, int l, int nbi, C* sT, C* wsm, int warp, int lane) {
+  const int ng = (nbi + nw() - 1) / nw();
+  if ((int)blockIdx.x >= ng) return;
+  const int P = a.P[l], Pc = a.P[l + 1], K = 4 * Pc;
+  const int S = a.S[l], O = a.O[l], Sc = a.S[l + 1], Oc = a.O[l + 1];
+  __syncthreads();
+  stage_copy_quad(sT, a.m2m[l] + (size_t)Oc * S + O, P, Pc, S, Sc);
+  __syncthreads();
+  for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+    const int i = g * nw() + warp;
+    if (i >= nbi) continue;
+    const int box = a.ne[l][i];
+    // the four children's multipoles (those of empty boxes are kept at zero),
+    // every load issued before the first store
+    __syncwarp();
+    for (int t0 = 0; t0 < K; t0 += 160) {
+      constexpr int KU = 5;
+      C v[KU];
+#pragma unroll
+      for (int k = 0; k < KU; ++k) {
+        const int t = t0 + lane + 32 * k, q = t / Pc;
+        v[k] = t < K ? ldcg(a.M[l + 1] + (size_t)(4 * box + q) * Sc + Oc + (t - q * Pc)) : C{0, 0};
+      }
+#pragma unroll
+      for (int k = 0; k < KU; ++k)
+        if (t0 + lane + 32 * k < K) wsm[t0 + lane + 32 * k] = v[k];
+    }
+    __syncwarp();
+    C* Mo = a.M[l] + (size_t)box * S + O;
+    warp_colmv(sT, P, wsm, K, lane, [&](int n, C v) { Mo[n] = v; });
+  }
+}
+
+// L2L into group g of nw() boxes of level l (box g nw() + warp), the four stacked
+// quadrant operators [4 Pp][P] already staged in sT; each box applies the block
+// of its own quadrant to its parent's local expansion.
+template <class C>
+__device__ __forceinline__ void l2l_quad_group(const FusedArgs<C>& a, int l, int nl2l, int g, const C* sT, C* wsm,
+                                               int warp, int lane) {
+  const int i = g * nw() + warp;
+  if (i >= nl2l) return;
+  const int P = a.P[l], Pp = a.P[l - 1];
+  const int S = a.S[l], O = a.O[l], Sp = a.S[l - 1], Op = a.O[l - 1];
+  const int box = a.ne[l][i], par = box >> 2, q = box & 3;
+  __syncwarp();
+  for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Sp + Op + m);
+  __syncwarp();
+  C* Lo = a.L[l] + (size_t)box * S + O;
+  warp_colmv(sT + (size_t)q * Pp * P, P, wsm, Pp, lane, [&](int n, C v) { atomic_add(Lo + n, v); });
+}
+
 // M2M into the nbi boxes of level l with the quadrant operators T_q (stored
 // [q][m child][n parent]) staged in shared memory one after another: warp item i
 // (the warp's box) accumulates its four children's contributions over the four
 // quadrant phases.  All threads of the block call this (block-level barriers);
 // a block with no box in a round leaves the loop, which is uniform over it.
+// ---------------------------------------------------------------- tensor-core M2L
+// TMEM columns a block holds while the product runs (>= the largest tc_kp).
+constexpr int TC_NCOL = 128;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait for the completion of the MMAs committed to mbar in phase ph.
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t ph, unsigned long long limit) {
+  const uint32_t addr = tc::smem_u32(mbar);
+  unsigned long long t0 = 0;
+  for (int spin = 0;; ++spin) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(ph)
+        : "memory");
+    if (done) return true;
+    if ((spin & 15) == 15) {
+      const unsigned long long t = gtimer();
+      if (t0 == 0) t0 = t;
+      else if (t - t0 > limit) return false;
+    }
+  }
+}
+
+// Largest MMA N = K of the single-launch product's tensor-core M2L: A and B
+// then take 3 x 128 x 80 + 3 x 80 x 80 BF16 values (97.5 KB of shared memory).
+constexpr int TC_KPMAX = 80;
+
+__host__ __device__ constexpr size_t tc_smem_bytes(int kp) {
+  return (size_t)3 * tc::TILE * kp * 2 + (size_t)3 * kp * kp * 2;
+}
+
+// M2L of one block item at level l: tile = 128 target boxes (rows of the MMA),
+// and a group of the offsets present in the tile.  For each offset o, thread 0
+// starts the bulk copy of B = T_o (three BF16 parts, canonical layout, built at
+// set-up) into shared memory while the block writes A: row t holds
+// alpha^m M(src_t) with K index 2c / 2c + 1 for the real / imaginary part of
+// coefficient c, in three BF16 parts.  Thread 0 then issues the six split
+// products of order <= 2,
+//   A0B0 + A0B1 + A1B0 + A0B2 + A1B1 + A2B0,
+// accumulated in FP32 in tensor memory over the group's offsets (about FP32
+// accuracy).  B's output rows hold the real parts of the target coefficients
+// at 0 .. P - 1 and the imaginary parts from tc::imrow(P) on, so the epilogue
+// reads both in aligned groups of 8 columns and adds them into L (atomically:
+// L2L and the tile's other groups add into the same boxes).  Called by all
+// threads; false when a wait ran out (after a second bounded wait for what was
+// in flight).
+__device__ bool tc_m2l_item(const FusedArgs<cplxf>& a, int l, int item, unsigned char* smraw, uint32_t tmem,
+                            uint64_t* mbar, uint32_t& phase, int warp, int lane) {
+  using bf = __nv_bfloat16;
+  const int kp = a.tc_kp[l], P = a.P[l], S = a.S[l], O = a.O[l];
+  const int ngrp = a.tc_ngrp[l];
+  const int tile = item / ngrp, grp = item - tile * ngrp;
+  const int ntot = a.tc_noff[l][tile];
+  const int og = (ntot + ngrp - 1) / ngrp, o0 = grp * og, o1 = min(ntot, o0 + og);
+  if (o0 >= o1) return true;
+  bf* sA = reinterpret_cast<bf*>(smraw);                 // 3 x 128 x kp
+  bf* sB = sA + 3 * tc::TILE * kp;                        // 3 x kp x kp
+  const uint32_t bbytes = (uint32_t)(3 * kp * kp * 2);
+  // nq threads per row of A (the block's threads over the 128 rows)
+  const int t = threadIdx.x, row = t & (tc::TILE - 1), part = t >> 7, nq = nt() >> 7;
+  const uint32_t idesc = tc::idesc_bf16(tc::TILE, kp), sbo = (uint32_t)(kp / 8) * 128;
+  uint64_t* mb_mma = mbar;
+  uint64_t* mb_b = mbar + 1;
+  __shared__ int s_fail;
+  // each offset's accumulator is read back into registers and summed there in
+  // FP32 (round to nearest), so that the tensor memory accumulates one offset's
+  // split products only: warp w reads TMEM lanes 32 (w mod 4) .. + 31 (rows of
+  // the tile), the warps of one lane quarter taking turns over the groups of 8
+  // coefficients (at most TC_CH groups each; P <= 40)
+  constexpr int TC_CH = 2;
+  const int lq = warp & 3, ch = warp >> 2, nch = nw() >> 2;
+  const int nc8 = (P + 7) / 8, im0 = tc::imrow(P);
+  const uint32_t lane_addr = tmem + ((uint32_t)(lq * 32) << 16);
+  float accr[TC_CH][8], acci[TC_CH][8];
+#pragma unroll
+  for (int k = 0; k < TC_CH; ++k)
+#pragma unroll
+    for (int j = 0; j < 8; ++j) accr[k][j] = acci[k][j] = 0.f;
+  // earlier generic-proxy writes of this shared memory (other items, stages)
+  // are ordered before the bulk copies and MMAs of the async proxy
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  for (int oi = o0; oi < o1; ++oi) {
+    const int o = a.tc_offs[l][tile * 49 + oi];
+    if (t == 0) {
+      const bf* gB = reinterpret_cast<const bf*>(a.tc_B[l]) + (size_t)o * 3 * kp * kp;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_u32(mb_b)), "r"(bbytes)
+                   : "memory");
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       tc::smem_u32(sB)),
+                   "l"(gB), "r"(bbytes), "r"(tc::smem_u32(mb_b))
+                   : "memory");
+    }
+    {
+      const size_t ti = ((size_t)tile * 49 + oi) * tc::TILE + row;
+      const int src = a.tc_src[l][ti];
+      const cplxf ph = from_d<cplxf>(phase_m(a.alpha, src >= 0 ? a.tc_img[l][ti] : 0));
+      const cplxf* Ms = a.M[l] + (size_t)(src >= 0 ? src : 0) * S + O;
+      // this thread's groups g = part + nq j of 8 components (4 coefficients);
+      // all loads first
+      constexpr int GJ = TC_KPMAX / 16;
+      cplxf v[GJ][4];
+#pragma unroll
+      for (int j = 0; j < GJ; ++j)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int g = part + nq * j, c = 4 * g + q;
+          v[j][q] = (src >= 0 && 8 * g < kp && c < P) ? ldcg(Ms + c) : cplxf{0, 0};
+        }
+#pragma unroll
+      for (int j = 0; j < GJ; ++j) {
+        const int g = part + nq * j;
+        if (8 * g < kp) {
+          uint32_t w0[4], w1[4], w2[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const cplxf z = ph * v[j][q];
+            bf a0, a1, a2, b0, b1, b2;
+            tc::split3(z.re, a0, a1, a2);
+            tc::split3(z.im, b0, b1, b2);
+            w0[q] = (uint32_t)__bfloat16_as_ushort(a0) | ((uint32_t)__bfloat16_as_ushort(b0) << 16);
+            w1[q] = (uint32_t)__bfloat16_as_ushort(a1) | ((uint32_t)__bfloat16_as_ushort(b1) << 16);
+            w2[q] = (uint32_t)__bfloat16_as_ushort(a2) | ((uint32_t)__bfloat16_as_ushort(b2) << 16);
+          }
+          const uint32_t off = tc::canon(row, 8 * g, kp) >> 4;    // 16-byte units
+          reinterpret_cast<uint4*>(sA)[off] = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+          reinterpret_cast<uint4*>(sA + tc::TILE * kp)[off] = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+          reinterpret_cast<uint4*>(sA + 2 * tc::TILE * kp)[off] = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+        }
+      }
+    }
+    // the generic-proxy writes of A become visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      int f = 0;
+      if (!mbar_wait(mb_b, phase, a.wait_ns)) {
+        f = 1;
+      } else {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int pa[6] = {0, 0, 1, 0, 1, 2};
+        const int pb[6] = {0, 1, 0, 2, 1, 0};
+        for (int q = 0; q < 6; ++q) {
+          const uint32_t abase = tc::smem_u32(sA + pa[q] * tc::TILE * kp);
+          const uint32_t bbase = tc::smem_u32(sB + pb[q] * kp * kp);
+          for (int kk = 0; kk < kp / 16; ++kk) {
+            const uint64_t ad = tc::sdesc(abase + kk * 256, 128, sbo);
+            const uint64_t bd = tc::sdesc(bbase + kk * 256, 128, sbo);
+            const uint32_t acc = (q > 0 || kk > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         tc::smem_u32(mb_mma))
+                     : "memory");
+      }
+      s_fail = f;
+    }
+    __syncthreads();
+    if (s_fail) {
+      // no MMA was issued; the bulk copy may still be running
+      if (t == 0) {
+        mbar_wait(mb_b, phase, a.wait_ns);
+        atomicExch(a.err, 1);
+      }
+      __syncthreads();
+      return false;
+    }
+    // every thread waits for the MMAs (their operands are overwritten next)
+    const bool ok = mbar_wait(mb_mma, phase, a.wait_ns);
+    if (__syncthreads_or(!ok)) {
+      if (t == 0) {
+        mbar_wait(mb_mma, phase, a.wait_ns);
+        atomicExch(a.err, 1);
+      }
+      __syncthreads();
+      return false;
+    }
+    phase ^= 1u;
+    // this offset's accumulator into the registers (the next offset's first
+    // MMA, issued after a block barrier, overwrites it)
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+    for (int k = 0; k < TC_CH; ++k) {
+      const int c8 = ch + nch * k;
+      if (c8 < nc8) {
+        uint32_t vr[8], vi[8];
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(vr[0]), "=r"(vr[1]), "=r"(vr[2]), "=r"(vr[3]), "=r"(vr[4]), "=r"(vr[5]), "=r"(vr[6]),
+                       "=r"(vr[7])
+                     : "r"(lane_addr + 8 * c8));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                     : "=r"(vi[0]), "=r"(vi[1]), "=r"(vi[2]), "=r"(vi[3]), "=r"(vi[4]), "=r"(vi[5]), "=r"(vi[6]),
+                       "=r"(vi[7])
+                     : "r"(lane_addr + im0 + 8 * c8));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          accr[k][j] += __uint_as_float(vr[j]);
+          acci[k][j] += __uint_as_float(vi[j]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  }
+  // epilogue: the row's sums into L
+  {
+    const int r = lq * 32 + lane;
+    const int tgt = a.tc_box[l][tile * tc::TILE + r];
+    cplxf* Lt = a.L[l] + (size_t)(tgt >= 0 ? tgt : 0) * S + O;
+    if (tgt >= 0) {
+#pragma unroll
+      for (int k = 0; k < TC_CH; ++k) {
+        const int c8 = ch + nch * k;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int c = 8 * c8 + j;
+          if (c8 < nc8 && c < P) atomic_add(Lt + c, cplxf{accr[k][j], acci[k][j]});
+        }
+      }
+    }
+  }
+  // the next item's first MMA overwrites the accumulator: every read is done
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return true;
+}
+
 template <class C>
 __device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, int wstride, C* sT, C* wsm, int lane) {
   const int P = a.P[l], Pc = a.P[l + 1], PP = Pc * P;
@@ -1330,19 +1755,61 @@ __device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, i
   __syncthreads();
 }
 
-template <class C>
-__global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
+// Register budget: three resident blocks of 256 threads per SM for the FP64
+// product, two for the FP32 one (the counts launch_fused runs them at).  The
+// tensor-core form (TC, FP32 only) holds tensor memory, with which the device
+// keeps one block per SM: it runs 512 threads per block instead.
+template <class C, bool TC>
+__global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeof(cplx) ? 3 : 2))
+    matvec_fused_kernel(FusedArgs<C> a) {
   // a GMRES cycle that has already converged skips the products queued after it
   if (a.done && *(volatile const int*)a.done != 0) return;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(128) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x;
-  const int wfirst = warp_first(blockIdx.x, warp, G), wstride = G * FW;
-  C* wsm = sm + TSIZE + (size_t)warp * PF_NCOEF;                // per-warp scratch
+  const int wfirst = warp_first(blockIdx.x, warp, G), wstride = G * nw();
+  C* wsm = sm + a.treg + (size_t)warp * PF_NCOEF;               // per-warp scratch
   C* sT = sm;                                                   // [P][P] staged M2L operator (row stride P, odd)
   const int D = a.D;
   int ks = 0;
+  // FP32 product with tensor-core M2L levels: the block holds TC_NCOL columns
+  // of tensor memory and two mbarriers (MMA completion, operator copy) for the
+  // whole launch; tc_leave gives the columns back on every way out
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_mbar[2];
+  uint32_t tc_phase = 0;
+  bool tc_on = false;
+  if constexpr (TC && sizeof(C) == sizeof(cplxf)) {
+    if (a.tc_any) {
+      if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc::smem_u32(&s_tmem)),
+                     "r"(TC_NCOL)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+      }
+      if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&s_mbar[0])) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc::smem_u32(&s_mbar[1])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      tc_on = true;
+    }
+  }
+  auto tc_leave = [&]() {
+    if constexpr (TC && sizeof(C) == sizeof(cplxf)) {
+      if (tc_on) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (warp == 0)
+          asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s_tmem), "r"(TC_NCOL) : "memory");
+      }
+    }
+  };
   stage_stamp(a.stamp, ks++);
 
   // ------------------------------------------------------------ A: gather + P2M, clear L; fiber part
@@ -1350,20 +1817,37 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     for (int l = 1; l <= D; ++l) {
       C* Lz = a.L[l];
       const size_t nz = (size_t)a.nbox[l] * a.S[l];
-      for (size_t t = (size_t)blockIdx.x * FB + threadIdx.x; t < nz; t += (size_t)G * FB) Lz[t] = C{0, 0};
+      for (size_t t = (size_t)blockIdx.x * nt() + threadIdx.x; t < nz; t += (size_t)G * nt()) Lz[t] = C{0, 0};
     }
     // blocks [gA, G) apply the same-fiber blocks while the others run P2M
     const int gA = G - a.fblk;
     if (blockIdx.x < gA) {
       const int PD = a.P[D];
-      for (int i = warp_first(blockIdx.x, warp, gA); i < a.nne[D]; i += gA * FW) {
+      for (int i = warp_first(blockIdx.x, warp, gA); i < a.nne[D]; i += gA * nw()) {
         const int box = a.ne[D][i], s0 = a.bb[D][box], s1 = a.be[D][box];
-        for (int sb = s0; sb < s1; sb += 32) {
-          const int s = sb + lane;
+        // the leaf's elements GU x 32 at a time: indices and phases, then the
+        // inputs, each batch of loads issued before its first use
+        constexpr int GU = sizeof(C) == sizeof(cplxf) ? 4 : 2;
+        for (int sb = s0; sb < s1; sb += 32 * GU) {
+          int ei[GU];
+          cplx pk[GU], xa[GU], xb[GU];
+#pragma unroll
+          for (int k = 0; k < GU; ++k) {
+            const int s = sb + lane + 32 * k;
+            ei[k] = s < s1 ? a.perm[s] : 0;
+            pk[k] = s < s1 ? a.ph[s] : cplx{0, 0};
+          }
+#pragma unroll
+          for (int k = 0; k < GU; ++k) {
+            xa[k] = a.x[2 * ei[k]];
+            xb[k] = a.x[2 * ei[k] + 1];
+          }
+#pragma unroll
+          for (int k = 0; k < GU; ++k) {
+          const int s = sb + lane + 32 * k;
           if (s < s1) {
-            const int e = a.perm[s];
-            const cplx p = a.ph[s];
-            const cplx e0 = p * a.x[2 * e], e1 = p * a.x[2 * e + 1];     // FP64, then rounded
+            const cplx p = pk[k];
+            const cplx e0 = p * xa[k], e1 = p * xb[k];     // FP64, then rounded
             a.dens[2 * s] = from_d<C>(e0);
             a.dens[2 * s + 1] = from_d<C>(e1);
             if (a.dens_dd) {
@@ -1376,6 +1860,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
               a.dlo[2 * s] = split_lo(e0);
               a.dlo[2 * s + 1] = split_lo(e1);
             }
+          }
           }
         }
         __syncwarp();
@@ -1396,18 +1881,40 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
           continue;
         }
         const int SD = a.S[D], OD = a.O[D];
-        for (int n0 = 0; n0 < PD; n0 += 32) {
+        // coefficients n < 32 (PD & ~31) a lane each over all the leaf's
+        // elements; the last PD mod 32 split over lane groups that share the
+        // elements, their sums combined by shuffles
+        const int full = PD & ~31;
+        for (int n0 = 0; n0 < full; n0 += 32) {
           const int n = n0 + lane;
-          if (n < PD) {
-            C acc0{0, 0}, acc1{0, 0};
+          C acc0{0, 0}, acc1{0, 0};
 #pragma unroll 8
-            for (int f = s0; f < s1; ++f) {
+          for (int f = s0; f < s1; ++f) {
+            const C* cf = a.p2m + (size_t)f * 2 * SD + OD;
+            acc0 += cf[n] * a.dens[2 * f];
+            acc1 += cf[SD + n] * a.dens[2 * f + 1];
+          }
+          a.M[D][(size_t)box * SD + OD + n] = acc0 + acc1;
+        }
+        if (PD > full) {
+          const int r = PD - full, g = 32 / r, grp = lane / r, nr = lane - grp * r;
+          const int n = full + nr;
+          C acc0{0, 0}, acc1{0, 0};
+          if (grp < g) {
+#pragma unroll 4
+            for (int f = s0 + grp; f < s1; f += g) {
               const C* cf = a.p2m + (size_t)f * 2 * SD + OD;
               acc0 += cf[n] * a.dens[2 * f];
               acc1 += cf[SD + n] * a.dens[2 * f + 1];
             }
-            a.M[D][(size_t)box * SD + OD + n] = acc0 + acc1;
           }
+          const C acc = acc0 + acc1;
+          C sum = acc;
+          for (int k = 1; k < g; ++k) {
+            const C o = shfl_c(acc, k * r + nr);
+            sum += o;
+          }
+          if (lane < r) a.M[D][(size_t)box * SD + OD + n] = sum;
         }
       }
     }
@@ -1416,7 +1923,10 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     else if (blockIdx.x >= gA)
       fiber_part(a, sm, blockIdx.x - gA, a.fblk, warp, lane);
   }
-  if (!grid_barrier(a.bar, a.err, a.wait_ns)) return;
+  if (!grid_barrier(a.bar, a.err, a.wait_ns, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
+      tc_leave();
+      return;
+    }
   stage_stamp(a.stamp, ks++);
 
   // ------------------------------------------------------------ B: M2M (+ root)
@@ -1441,8 +1951,13 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     // boxes of the larger levels: the block stages each quadrant operator in
     // shared memory once and applies it to all of its warps' boxes (a warp on
     // its own would stream the whole [4][Pc][P] table from L2 for every box)
-    const bool staged = l >= 1 && !top && 4 * Pc <= PF_NCOEF && Pc * P <= TSIZE && P <= 64;
-    if (staged) m2m_staged(a, l, nbi, wfirst, wstride, sT, wsm, lane);
+    const bool quad = sizeof(C) == sizeof(cplxf) && l >= 1 && !top && 4 * Pc <= PF_NCOEF && 4 * Pc * P <= a.treg;
+    const bool staged = quad || (l >= 1 && !top && 4 * Pc <= PF_NCOEF && Pc * P <= TSIZE && P <= 64);
+    if (quad)
+      m2m_quad(a, l, nbi, sT, wsm, warp, lane);
+    else if (staged)
+      m2m_staged(a, l, nbi, wfirst, wstride, sT, wsm, lane);
+    if (a.bdone && threadIdx.x == 0) a.bdone[(size_t)(ks - 1) * G + blockIdx.x] = gtimer();
     for (int i = wfirst; i < nitem; i += wstride) {
       if (staged && i < nbi) continue;
       if (i >= nbi + nx) {
@@ -1548,7 +2063,10 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
         }
       }
     }
-    if (!grid_barrier(a.bar, a.err, a.wait_ns)) return;
+    if (!grid_barrier(a.bar, a.err, a.wait_ns, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
+      tc_leave();
+      return;
+    }
     stage_stamp(a.stamp, ks++);
   }
 
@@ -1562,9 +2080,38 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
     // M2L one warp per pair (operator rows through L1/L2), or one block per
     // chunk of pairs sharing the offset (operator staged in shared memory)
     const bool wpair = a.m2l_warp || P > TSP;
-    // block chunks of the staged M2L first, then the warp items
-    if (!wpair) {
-      for (int b = blockIdx.x; b < a.nch[l]; b += G) {
+    // L2L as block items (groups of nw() boxes, the stacked quadrant operators
+    // staged once per block) when the FP32 tables fit the staging region
+    const bool ql2l = sizeof(C) == sizeof(cplxf) && !top && Pp <= PF_NCOEF && 4 * Pp * P <= a.treg;
+    // M2L on the tensor cores at this level (FP32 product): block items over
+    // (tile of 128 targets, group of offsets) in place of the chunks
+    const bool tcl = TC && sizeof(C) == sizeof(cplxf) && a.tc_kp[l] > 0;
+    const int ntc = tcl ? a.tc_ntile[l] * a.tc_ngrp[l] : 0;
+    const int nchu = (wpair || tcl) ? 0 : a.nch[l];
+    const int ngl = ql2l ? (nl2l + nw() - 1) / nw() : 0;
+    // block items: the tensor-core tiles or the staged M2L chunks first, then
+    // the L2L groups; then the warp items
+    {
+      bool l2l_ready = false;
+      for (int b0 = blockIdx.x; b0 < ntc + nchu + ngl; b0 += G) {
+        if (b0 < ntc) {
+          if constexpr (TC && sizeof(C) == sizeof(cplxf)) {
+            // a wait that ran out has set the error flag: the next barrier ends the product
+            if (!tc_m2l_item(a, l, b0, smraw, s_tmem, s_mbar, tc_phase, warp, lane)) break;
+          }
+          continue;
+        }
+        const int b = b0 - ntc;
+        if (b >= nchu) {
+          if (!l2l_ready) {
+            __syncthreads();                                  // sT of the last chunk is done
+            stage_copy_quad(sT, a.l2l[l - 1] + (size_t)a.O[l - 1] * a.S[l] + a.O[l], P, Pp, a.S[l], a.S[l - 1]);
+            __syncthreads();
+            l2l_ready = true;
+          }
+          l2l_quad_group(a, l, nl2l, b - nchu, sT, wsm, warp, lane);
+          continue;
+        }
         const int o = a.ch_off[l][b], pb = a.ch_beg[l][b], pe = a.ch_end[l][b];
         const int S = a.S[l], O = a.O[l];
         const C* To = a.m2lt[l] + (size_t)o * S * S + (size_t)O * S + O;   // [n source][l target], used block
@@ -1575,7 +2122,7 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
           stage_copy_bt(sT, To, P, S);
         __syncthreads();
         // two pairs per warp pass, sharing the operator rows read from shared memory
-        for (int pi = pb + 2 * warp; pi < pe; pi += 2 * FW) {
+        for (int pi = pb + 2 * warp; pi < pe; pi += 2 * nw()) {
           const bool two = pi + 1 < pe;
           const int srcA = a.pr_src[l][pi], tgtA = a.pr_tgt[l][pi];
           const int srcB = two ? a.pr_src[l][pi + 1] : srcA, tgtB = two ? a.pr_tgt[l][pi + 1] : tgtA;
@@ -1587,25 +2134,21 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
             wsm[P + m] = phB * ldcg(a.M[l] + (size_t)srcB * S + O + m);
           }
           __syncwarp();
-          for (int n = lane; n < P; n += 32) {
-            const C* row = sT + (size_t)n * P;
-            C rA{0, 0}, rB{0, 0};
-#pragma unroll 4
-            for (int m = 0; m < P; ++m) {
-              const C t = row[m];
-              rA += t * wsm[m];
-              rB += t * wsm[P + m];
-            }
-            atomic_add(a.L[l] + (size_t)tgtA * S + O + n, rA);
-            if (two) atomic_add(a.L[l] + (size_t)tgtB * S + O + n, rB);
-          }
+          C* LA = a.L[l] + (size_t)tgtA * S + O;
+          C* LB = a.L[l] + (size_t)tgtB * S + O;
+          warp_rowmv2(sT, P, wsm, wsm + P, lane, [&](int n, C rA, C rB) {
+            atomic_add(LA + n, rA);
+            if (two) atomic_add(LB + n, rB);
+          });
         }
       }
     }
-    // box-form L2L with the quadrant operators staged in shared memory
-    const bool sl2l = !top && Pp * P <= TSIZE && P <= 64 && Pp <= PF_NCOEF;
-    if (sl2l) l2l_staged(a, l, nl2l, wfirst, wstride, sT, wsm, lane);
-    const int nm2l = wpair ? a.npair[l] : 0;
+    if (a.bdone && threadIdx.x == 0) a.bdone[(size_t)(ks - 1) * G + blockIdx.x] = gtimer();
+    // box-form L2L with the quadrant operators staged in shared memory, one
+    // quadrant at a time (the FP64 product's hi and lo tables)
+    const bool sl2l = ql2l || (!top && Pp * P <= TSIZE && P <= 64 && Pp <= PF_NCOEF);
+    if (sl2l && !ql2l) l2l_staged(a, l, nl2l, wfirst, wstride, sT, wsm, lane);
+    const int nm2l = (wpair && !tcl) ? a.npair[l] : 0;
     const int jst = nbst + l - 1;
     const int r0 = a.near_first ? (jst == 0 ? 0 : a.E) : (int)((int64_t)a.E * jst / nst);
     const int r1 = a.near_first ? a.E : (int)((int64_t)a.E * (jst + 1) / nst);
@@ -1684,7 +2227,10 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
       __syncwarp();
       for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * S + O + n, colmv(To + n, S, wsm, P));
     }
-    if (!grid_barrier(a.bar, a.err, a.wait_ns)) return;
+    if (!grid_barrier(a.bar, a.err, a.wait_ns, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
+      tc_leave();
+      return;
+    }
     stage_stamp(a.stamp, ks++);
   }
 
@@ -1748,13 +2294,17 @@ __global__ void __launch_bounds__(FB, 3) matvec_fused_kernel(FusedArgs<C> a) {
   }
   __syncthreads();
   stage_stamp(a.stamp, ks++);
+  tc_leave();
 }
 
+// Threads per block of a form of the single-launch product.
+constexpr int fused_threads(bool tc) { return tc ? 2 * FB : FB; }
+
 template <class C>
-size_t fused_smem(int maxfiber) {
-  const size_t a = (size_t)TSIZE + (size_t)FW * PF_NCOEF;   // stages B, D
+size_t fused_smem(int maxfiber, int treg, size_t tcb, int nwarp) {
+  const size_t a = (size_t)treg + (size_t)nwarp * PF_NCOEF; // stages B, D
   const size_t f = 2 * (size_t)maxfiber + 512;              // fiber part of stage A, with its twiddles (FP64 FFTs)
-  return std::max(sizeof(C) * a, sizeof(cplx) * f);
+  return std::max({sizeof(C) * a, sizeof(cplx) * f, tcb});  // tcb: tensor-core M2L operands
 }
 
 // After a bounded device-side wait gave up, the barrier words and the error
@@ -1763,19 +2313,54 @@ size_t fused_smem(int maxfiber) {
 cudaError_t reset_device_waits(pfmbem* h) {
   if (!h->fz_dirty) return cudaSuccess;
   cudaError_t e = cudaSuccess;
-  if (h->fz_bar) e = cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned), h->stream);
-  if (e == cudaSuccess && h->arn_bar) e = cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned), h->stream);
+  if (h->fz_bar) e = cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned long long), h->stream);
+  if (e == cudaSuccess && h->arn_bar) e = cudaMemsetAsync(h->arn_bar, 0, 2 * sizeof(unsigned long long), h->stream);
   if (e == cudaSuccess && h->fz_err) e = cudaMemsetAsync(h->fz_err, 0, sizeof(int), h->stream);
   if (e == cudaSuccess) h->fz_dirty = false;
   return e;
 }
 
 // Operators, vectors and work lists of one product of the single-launch kernel.
+// Coefficients per expansion at level l in the single-launch product.  The
+// FP32 product may run at a lower order than the FP64 one (the central
+// sub-blocks of the same tables); only with the folded top of the tree (level 3
+// present), whose paths all take the strides.
+int fused_P(const pfmbem* h, int l, bool f32) {
+  const Level& L = h->lev[l];
+  const bool reduce = f32 && h->m2m31 != nullptr && h->D >= 3;
+  const int pu = reduce ? std::min(L.p, std::max(1, L.p32)) : L.p;
+  return 2 * pu + 1;
+}
+
 template <class C>
 cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedArgs<C>& a) {
   a = FusedArgs<C>{};
   a.done = done;
   a.tws_off = 2 * h->max_fiber;
+  a.treg = sizeof(C) == sizeof(cplxf) ? std::max(TSIZE, h->fz_treg32) : TSIZE;
+  a.nr_meta = reinterpret_cast<const longlong2*>(h->nr_meta);
+  a.tc_any = 0;
+  for (int l = 0; l <= h->D; ++l) {
+    const Level& L = h->lev[l];
+    const int kp = tc::kpad(fused_P(h, l, sizeof(C) == sizeof(cplxf)));
+    const bool on = sizeof(C) == sizeof(cplxf) && l >= 1 && h->fz_tcb32 > 0 && L.tc_fused && L.tc_Bf &&
+                    L.tc_ntile > 0 && kp <= TC_KPMAX;
+    a.tc_kp[l] = on ? kp : 0;
+    a.tc_ntile[l] = on ? L.tc_ntile : 0;
+    // offset groups per tile: about two block items per block of the grid
+    // (PFMBEM_TC_GROUPS overrides, for measurement)
+    static const char* tg = std::getenv("PFMBEM_TC_GROUPS");
+    const int G = h->fz_grid32 > 0 ? h->fz_grid32 : 1;
+    a.tc_ngrp[l] = on ? std::max(1, std::min(49, (2 * G + L.tc_ntile - 1) / L.tc_ntile)) : 1;
+    if (on && tg) a.tc_ngrp[l] = std::max(1, std::min(49, std::atoi(tg)));
+    a.tc_box[l] = L.tc_box;
+    a.tc_noff[l] = L.tc_noff;
+    a.tc_offs[l] = L.tc_offs;
+    a.tc_src[l] = L.tc_src;
+    a.tc_img[l] = L.tc_img;
+    a.tc_B[l] = L.tc_Bf;
+    a.tc_any |= on ? 1 : 0;
+  }
   a.E = h->E;
   a.D = h->D;
   a.perm = h->s_perm;
@@ -1783,14 +2368,10 @@ cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedA
   a.opos = h->o_pos;
   a.x = x;
   a.y = y;
-  // the FP32 product may run at a lower order than the FP64 one (the central
-  // sub-blocks of the same tables); only with the folded top of the tree (level 3
-  // present), whose paths all take the strides
-  const bool reduce = sizeof(C) == sizeof(cplxf) && h->m2m31 != nullptr && h->D >= 3;
   for (int l = 0; l <= h->D; ++l) {
     const Level& L = h->lev[l];
     a.nne[l] = L.nne;
-    const int pu = reduce ? std::min(L.p, std::max(1, L.p32)) : L.p;
+    const int pu = (fused_P(h, l, sizeof(C) == sizeof(cplxf)) - 1) / 2;
     a.P[l] = 2 * pu + 1;
     a.S[l] = L.P;
     a.O[l] = L.p - pu;
@@ -1881,7 +2462,7 @@ cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedA
   a.circ = h->fb_circ;
   a.alpha = h->alpha;
   a.c2 = cplx{h->c2re, h->c2im};
-  a.bar = h->fz_bar;
+  a.bar = h->fz_bar + (sizeof(C) == sizeof(cplxf) ? 1 : 0);   // one counter per grid size
   a.err = h->fz_err;
   a.wait_ns = h->opt.wait_us > 0 ? 1000ull * (unsigned long long)h->opt.wait_us : 1000000000ull;
   return cudaSuccess;
@@ -1897,12 +2478,20 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
   }
   static const bool stamps = std::getenv("PFMBEM_STAGE_TIMES") != nullptr;
   a.stamp = stamps ? h->fz_stamp : nullptr;
+  // diagnostic (PFMBEM_BLOCK_TIMES set, with PFMBEM_STAGE_TIMES): every block's
+  // arrival at every barrier
+  static const bool btimes = std::getenv("PFMBEM_BLOCK_TIMES") != nullptr;
+  a.arrive = stamps && btimes ? h->fz_arrive : nullptr;
+  a.bdone = a.arrive ? h->fz_arrive + (size_t)16 * 1024 : nullptr;
   const int grid = f32 ? h->fz_grid32 : h->fz_grid64;
+  // the tensor-core form: FP32 product with tensor-core M2L levels
+  const bool tc = f32 && h->fz_tcb32 > 0;
+  const int nthr = fused_threads(tc), nwarp = nthr / 32;
   // the fiber part's blocks in stage A, in proportion to its block items
   // against the P2M warp items (one leaf per warp)
   {
     const int nf = h->fz_nfft + h->fz_nchunk;
-    const double wa = (double)h->lev[h->D].nne / FW;
+    const double wa = (double)h->lev[h->D].nne / nwarp;
     const int fb = (int)((double)grid * nf / (nf + wa) + 0.5);
     a.fblk = grid >= 16 ? std::max(1, std::min({fb, nf, grid - grid / 4})) : 0;
   }
@@ -1915,16 +2504,29 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
   // levels 1 and 0 inside the level-2 stage when the tree has level 3 and the
   // three levels' coefficients fit one item per warp
   {
-    const int64_t w = (int64_t)grid * FW;
+    const int64_t w = (int64_t)grid * nwarp;
     a.top3 = h->m2m31 != nullptr &&
              (int64_t)h->lev[2].nne * h->lev[2].P + (int64_t)h->lev[1].nne * h->lev[1].P + 4 * h->lev[0].P <= w;
   }
-  const size_t smem = fused_smem<C>(h->max_fiber);
+  const size_t smem = fused_smem<C>(h->max_fiber, a.treg, tc ? h->fz_tcb32 : 0, nwarp);
+  const void* fn = tc ? (const void*)matvec_fused_kernel<cplxf, true> : (const void*)matvec_fused_kernel<C, false>;
+  {
+    // the kernel's dynamic shared-memory limit is process-wide: raise it to
+    // this launch's need (another handle may have set a smaller one)
+    static std::atomic<size_t> set_max[2]{{0}, {0}};
+    std::atomic<size_t>& sm = set_max[tc ? 1 : 0];
+    size_t cur = sm.load();
+    if (smem > cur) {
+      cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      while (smem > cur && !sm.compare_exchange_weak(cur, smem)) {
+      }
+    }
+  }
   void* args[] = {&a};
   const int ph = PH_FUSED + (f32 ? 16 : 0);
   prof_begin(h, ph);
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)matvec_fused_kernel<C>, dim3(grid), dim3(FB), args, smem,
-                                              h->stream);
+  cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(nthr), args, smem, h->stream);
   prof_end(h, ph);
   if (e == cudaSuccess && a.stamp) {
     // diagnostic (PFMBEM_STAGE_TIMES set): stage durations of this launch on stderr
@@ -1933,19 +2535,56 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e == cudaSuccess) {
       const int n = 2 * h->D + 3 - (a.top3 ? 2 : 0);
-      std::fprintf(stderr, "pfmbem fused %s stages (us):", f32 ? "f32" : "f64");
+      std::fprintf(stderr, "pfmbem fused %s grid %d smem %zu stages (us):", f32 ? "f32" : "f64", grid, smem);
       for (int i = 1; i < n; ++i) std::fprintf(stderr, " %.1f", 1e-3 * (double)(t[i] - t[i - 1]));
       std::fprintf(stderr, "  total %.1f\n", 1e-3 * (double)(t[n - 1] - t[0]));
+      if (a.arrive && grid <= 1024) {
+        // per stage: the blocks' arrivals at its closing barrier after the
+        // stage's start (block 0 leaving the previous barrier): min, median,
+        // 90th percentile, max (us) and the last block
+        std::vector<unsigned long long> arr((size_t)(n - 1) * grid), bd((size_t)(n - 1) * grid, 0);
+        e = cudaMemcpy(arr.data(), a.arrive, sizeof(unsigned long long) * arr.size(), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+          e = cudaMemcpy(bd.data(), a.bdone, sizeof(unsigned long long) * bd.size(), cudaMemcpyDeviceToHost);
+        for (int i = 1; e == cudaSuccess && i < n - 1; ++i) {
+          std::vector<double> d(grid), q;
+          int last = 0;
+          for (int b = 0; b < grid; ++b) {
+            d[b] = 1e-3 * ((double)arr[(size_t)(i - 1) * grid + b] - (double)t[i - 1]);
+            if (d[b] > d[last]) last = b;
+            const unsigned long long x = bd[(size_t)(i - 1) * grid + b];
+            if (x > t[i - 1] && x < t[i]) q.push_back(1e-3 * ((double)x - (double)t[i - 1]));
+          }
+          std::vector<double> srt = d;
+          std::sort(srt.begin(), srt.end());
+          std::sort(q.begin(), q.end());
+          std::fprintf(stderr,
+                       "pfmbem fused %s stage %d arrivals (us): %.1f %.1f %.1f %.1f last block %d, stage %.1f; "
+                       "block items done: median %.1f max %.1f\n",
+                       f32 ? "f32" : "f64", i, srt[0], srt[grid / 2], srt[(9 * grid) / 10], srt[grid - 1], last,
+                       1e-3 * (double)(t[i] - t[i - 1]), q.empty() ? 0.0 : q[q.size() / 2],
+                       q.empty() ? 0.0 : q.back());
+        }
+        cudaMemsetAsync(a.bdone, 0, sizeof(unsigned long long) * bd.size(), h->stream);
+      }
     }
   }
   return e;
 }
 
-template <class C>
-int fused_grid(int maxfiber) {
-  const size_t smem = fused_smem<C>(maxfiber);
-  if (cudaFuncSetAttribute(matvec_fused_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess) {
+template <class C, bool TC>
+int fused_grid(int maxfiber, int treg, size_t tcb) {
+  const void* fn = (const void*)matvec_fused_kernel<C, TC>;
+  const int nthr = fused_threads(TC);
+  const size_t smem = fused_smem<C>(maxfiber, treg, tcb, nthr / 32);
+  // the limit only grows: handles made earlier keep theirs
+  int cur = 0;
+  {
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) == cudaSuccess) cur = fa.maxDynamicSharedSizeBytes;
+    cudaGetLastError();
+  }
+  if ((int)smem > cur && cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -1953,16 +2592,17 @@ int fused_grid(int maxfiber) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, matvec_fused_kernel<C>, FB, smem) != cudaSuccess) {
+  if (!coop || cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, nthr, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
   // resident blocks per SM: three for the FP64 product, whose stages are bound
   // by the FP64 pipes of all sub-partitions; two for the FP32 product, whose
-  // stages are short and pay less for a barrier over fewer blocks
-  // (PFMBEM_FUSED_BLOCKS_PER_SM overrides, for measurement)
+  // stages are short and pay less for a barrier over fewer blocks; one of 512
+  // threads in the tensor-core form (PFMBEM_FUSED_BLOCKS_PER_SM overrides the
+  // first two, for measurement)
   static const char* bps = std::getenv("PFMBEM_FUSED_BLOCKS_PER_SM");
-  const int cap = bps ? std::max(1, std::atoi(bps)) : (sizeof(C) == sizeof(cplx) ? 3 : 2);
+  const int cap = TC ? 1 : bps ? std::max(1, std::atoi(bps)) : (sizeof(C) == sizeof(cplx) ? 3 : 2);
   return nsm * std::min(per, cap);
 }
 
@@ -2051,8 +2691,9 @@ cudaError_t k_top_operators(pfmbem* h, cudaStream_t st) {
     const int P1 = h->lev[1].P, P2 = h->lev[2].P, P3 = h->lev[3].P;
     m2m31_kernel<<<(16 * P3 * P1 + 255) / 256, 256, 0, st>>>(P1, P2, P3, h->lev[1].m2m, h->lev[2].m2m, h->m2m31,
                                                              h->m2m31f);
-    // the level-1 and level-3 multipoles of empty boxes are never written: keep them zero
-    for (int l : {1, 3}) {
+    // the multipoles of empty boxes are never written: keep them zero (the
+    // M2M stages and M(1) read all four children without occupancy tests)
+    for (int l = 1; l <= h->D; ++l) {
       const size_t nz = (size_t)h->lev[l].nbox * h->lev[l].P;
       cudaError_t e = cudaMemsetAsync(h->lev[l].M, 0, nz * sizeof(cplx), st);
       if (e == cudaSuccess) e = cudaMemsetAsync(h->lev[l].Mf, 0, nz * sizeof(cplxf), st);
@@ -2072,8 +2713,39 @@ cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
   int need = std::max(h->lev[h->D].nne, h->fz_nchunk + h->fz_nfft);
   for (int l = 0; l <= h->D; ++l) need = std::max(need, (h->lev[l].nne + FW - 1) / FW);
   need = std::max(need, 1);
-  h->fz_grid64 = std::min(fused_grid<cplx>(h->max_fiber), need);
-  h->fz_grid32 = std::min(fused_grid<cplxf>(h->max_fiber), need);
+  // staging region of the FP32 product: room for the four stacked quadrant
+  // operators of M2M and L2L at the FP32 orders, within about 100 KB per block
+  // (two resident blocks per SM)
+  {
+    // only the levels that run box items (the others take one warp per
+    // coefficient: more warps than boxes x coefficients, for two blocks per SM)
+    int nsm = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t wst = (int64_t)2 * nsm * FW;
+    int need4 = 0;
+    for (int l = 1; l <= h->D; ++l) {
+      const int P = fused_P(h, l, true), Pp = fused_P(h, l - 1, true);
+      if ((int64_t)h->lev[l].nne * P <= wst) continue;
+      if (l < h->D && 4 * fused_P(h, l + 1, true) <= PF_NCOEF) need4 = std::max(need4, 4 * fused_P(h, l + 1, true) * P);
+      if (l >= 2 && Pp <= PF_NCOEF) need4 = std::max(need4, 4 * Pp * P);
+    }
+    const int cap = (int)(100 * 1024 / sizeof(cplxf)) - 2 * FW * PF_NCOEF;   // room for 16 warps' scratch
+    static const bool noquad = std::getenv("PFMBEM_NO_QUAD") != nullptr;   // measurement: per-quadrant staging
+    h->fz_treg32 = noquad ? TSIZE : std::max(TSIZE, std::min(need4, cap));
+  }
+  // tensor-core M2L levels of the FP32 product (their operands need up to
+  // tc_smem_bytes(TC_KPMAX) of shared memory)
+  h->fz_tcb32 = 0;
+  for (int l = 1; l <= h->D; ++l) {
+    const Level& L = h->lev[l];
+    if (L.tc_fused && L.tc_Bf && L.tc_ntile > 0 && tc::kpad(fused_P(h, l, true)) <= TC_KPMAX)
+      h->fz_tcb32 = std::max(h->fz_tcb32, tc_smem_bytes(tc::kpad(fused_P(h, l, true))));
+  }
+  h->fz_grid64 = std::min(fused_grid<cplx, false>(h->max_fiber, TSIZE, 0), need);
+  h->fz_grid32 = std::min(h->fz_tcb32 > 0 ? fused_grid<cplxf, true>(h->max_fiber, h->fz_treg32, h->fz_tcb32)
+                                          : fused_grid<cplxf, false>(h->max_fiber, h->fz_treg32, 0),
+                          need);
   if (h->fz_grid64 <= 0 || h->fz_grid32 <= 0) return cudaSuccess;
   {
     // device-side GMRES steps: one block per SM (the steps are short; fewer
