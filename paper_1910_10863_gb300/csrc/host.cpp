@@ -1552,7 +1552,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
         h->fz_err = dalloc<int>(h, 1);
         h->fz_stamp = dalloc<unsigned long long>(h, 32);
         // diagnostic: every block's arrival at every barrier (PFMBEM_BLOCK_TIMES)
-        if (std::getenv("PFMBEM_BLOCK_TIMES")) h->fz_arrive = dalloc<unsigned long long>(h, (size_t)32 * 1024);
+        if (std::getenv("PFMBEM_BLOCK_TIMES")) h->fz_arrive = dalloc<unsigned long long>(h, (size_t)48 * 1024);
         if (!h->fz_bar || !h->arn_bar || !h->fz_err || !h->fz_stamp)
           return fail(h, PFMBEM_ENOMEM, "device allocation failed (barrier)");
         CK(cudaMemsetAsync(h->fz_bar, 0, 2 * sizeof(unsigned long long), h->stream));

@@ -45,6 +45,13 @@ namespace {
 constexpr int FB = 256;          // threads per block
 constexpr int FW = FB / 32;      // warps per block
 
+// Device time in nanoseconds.
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
 // Threads and warps of the running block: the single-launch product runs with
 // 256 threads per block, or 512 in its tensor-core form (one block per SM)
 __device__ __forceinline__ int nt() { return (int)blockDim.x; }
@@ -1319,7 +1326,8 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
 // blocks then carry the level while the others go on to their warp items.
 // Called by all threads of the block.
 template <class C>
-__device__ void m2m_quad(const FusedArgs<C>& a, int l, int nbi, C* sT, C* wsm, int warp, int lane) {
+__device__ void m2m_quad(const FusedArgs<C>& a, int l, int nbi, C* sT, C* wsm, int warp, int lane,
+                         unsigned long long* dg) {
   const int ng = (nbi + nw() - 1) / nw();
   if ((int)blockIdx.x >= ng) return;
   const int P = a.P[l], Pc = a.P[l + 1], K = 4 * Pc;
@@ -1327,6 +1335,7 @@ __device__ void m2m_quad(const FusedArgs<C>& a, int l, int nbi, C* sT, C* wsm, i
   __syncthreads();
   stage_copy_quad(sT, a.m2m[l] + (size_t)Oc * S + O, P, Pc, S, Sc);
   __syncthreads();
+  if (dg && threadIdx.x == 0) dg[8192] = gtimer();     // diagnostic: operators staged
   for (int g = blockIdx.x; g < ng; g += gridDim.x) {
     const int i = g * nw() + warp;
     if (i >= nbi) continue;
@@ -1347,6 +1356,7 @@ __device__ void m2m_quad(const FusedArgs<C>& a, int l, int nbi, C* sT, C* wsm, i
         if (t0 + lane + 32 * k < K) wsm[t0 + lane + 32 * k] = v[k];
     }
     __syncwarp();
+    if (dg && threadIdx.x == 0) dg[16384] = gtimer();    // diagnostic: children gathered
     C* Mo = a.M[l] + (size_t)box * S + O;
     warp_colmv(sT, P, wsm, K, lane, [&](int n, C v) { Mo[n] = v; });
   }
@@ -1378,12 +1388,6 @@ __device__ __forceinline__ void l2l_quad_group(const FusedArgs<C>& a, int l, int
 // ---------------------------------------------------------------- tensor-core M2L
 // TMEM columns a block holds while the product runs (>= the largest tc_kp).
 constexpr int TC_NCOL = 128;
-
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
 
 // Bounded wait for the completion of the MMAs committed to mbar in phase ph.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t ph, unsigned long long limit) {
@@ -1954,7 +1958,7 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
     const bool quad = sizeof(C) == sizeof(cplxf) && l >= 1 && !top && 4 * Pc <= PF_NCOEF && 4 * Pc * P <= a.treg;
     const bool staged = quad || (l >= 1 && !top && 4 * Pc <= PF_NCOEF && Pc * P <= TSIZE && P <= 64);
     if (quad)
-      m2m_quad(a, l, nbi, sT, wsm, warp, lane);
+      m2m_quad(a, l, nbi, sT, wsm, warp, lane, a.bdone ? a.bdone + (size_t)(ks - 1) * G + blockIdx.x : nullptr);
     else if (staged)
       m2m_staged(a, l, nbi, wfirst, wstride, sT, wsm, lane);
     if (a.bdone && threadIdx.x == 0) a.bdone[(size_t)(ks - 1) * G + blockIdx.x] = gtimer();
@@ -2542,7 +2546,7 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
         // per stage: the blocks' arrivals at its closing barrier after the
         // stage's start (block 0 leaving the previous barrier): min, median,
         // 90th percentile, max (us) and the last block
-        std::vector<unsigned long long> arr((size_t)(n - 1) * grid), bd((size_t)(n - 1) * grid, 0);
+        std::vector<unsigned long long> arr((size_t)(n - 1) * grid), bd((size_t)3 * 8192, 0);
         e = cudaMemcpy(arr.data(), a.arrive, sizeof(unsigned long long) * arr.size(), cudaMemcpyDeviceToHost);
         if (e == cudaSuccess)
           e = cudaMemcpy(bd.data(), a.bdone, sizeof(unsigned long long) * bd.size(), cudaMemcpyDeviceToHost);
@@ -2558,12 +2562,17 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
           std::vector<double> srt = d;
           std::sort(srt.begin(), srt.end());
           std::sort(q.begin(), q.end());
+          // block 'last''s own marks: operators staged, children gathered (M2M), block items done
+          auto mark = [&](size_t slot) {
+            const unsigned long long x = bd[slot + (size_t)(i - 1) * grid + last];
+            return x > t[i - 1] && x < t[i] ? 1e-3 * ((double)x - (double)t[i - 1]) : -1.0;
+          };
           std::fprintf(stderr,
                        "pfmbem fused %s stage %d arrivals (us): %.1f %.1f %.1f %.1f last block %d, stage %.1f; "
-                       "block items done: median %.1f max %.1f\n",
+                       "block items done: median %.1f max %.1f; last block: staged %.1f gathered %.1f items %.1f\n",
                        f32 ? "f32" : "f64", i, srt[0], srt[grid / 2], srt[(9 * grid) / 10], srt[grid - 1], last,
                        1e-3 * (double)(t[i] - t[i - 1]), q.empty() ? 0.0 : q[q.size() / 2],
-                       q.empty() ? 0.0 : q.back());
+                       q.empty() ? 0.0 : q.back(), mark(8192), mark(16384), mark(0));
         }
         cudaMemsetAsync(a.bdone, 0, sizeof(unsigned long long) * bd.size(), h->stream);
       }
