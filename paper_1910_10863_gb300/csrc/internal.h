@@ -281,6 +281,7 @@ struct pfmbem {
   int* fz_rowfib = nullptr;      // [nrowsum][2] (fiber, row) of those rows
   int fz_nrowsum = 0;
   int fz_treg32 = 0;             // staged-operator region of the FP32 single-launch product (complex values)
+  int fz_tregL32 = 0;            // its second region, for the L2L operators (0: none)
   size_t fz_tcb32 = 0;           // shared memory of the FP32 product's tensor-core M2L operands (0: none)
   int* s_li = nullptr;           // sorted element -> index of its leaf among the non-empty leaves
   int64_t* nr_meta = nullptr;    // [E][2] near-field row of a sorted element: block offset, (first source << 32) | sources

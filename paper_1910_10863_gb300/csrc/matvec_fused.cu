@@ -131,6 +131,7 @@ struct FusedArgs {
   const int* done;                   // optional: the product is skipped when *done != 0
   int tws_off;                       // shared-memory offset (in C) of the twiddle copy of the fiber part
   int treg;                          // shared-memory region (in C) of the staged operators, >= TSIZE
+  int tregL;                         // a second region for the L2L operators (0: L2L stages into the first)
   // FP32 product, M2L on the tensor cores (tcgen05) at the levels with tc_kp > 0:
   // tiles of 128 target boxes; block item (tile, group of the tile's offsets)
   int tc_any;
@@ -419,11 +420,12 @@ __device__ __forceinline__ void stage_copy_bt(C* dst, const C* __restrict__ src,
 
 // The four quadrant operators of a translation table, stacked: staged row
 // u = q Pn + m (q < 4, m < Pn) holds the used columns O .. O + P of table row
-// q Sn + On + m (base = table + On S + O; rows of stride S).  Sixteen loads in
-// flight per thread: the whole stack costs about two L2 round trips.
+// q Sn + On + m (base = table + On S + O; rows of stride S).  Eight loads in
+// flight per thread (measured faster than sixteen, 2.1 against 3.1 us for a
+// 4 x 37 x 37 stack over 304 blocks).
 template <class C>
 __device__ __forceinline__ void stage_copy_quad(C* dst, const C* __restrict__ base, int P, int Pn, int S, int Sn) {
-  constexpr int U = sizeof(C) == sizeof(cplxf) ? 16 : 8;
+  constexpr int U = 8;
   const int n = 4 * Pn * P;
   int t = threadIdx.x;
   for (; t < n; t += U * nt()) {
@@ -1320,23 +1322,25 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
 }
 
 // M2M into the nbi boxes of level l as block items: group g of nw() boxes (one
-// per warp) goes to block g mod G, which stages the four stacked quadrant
+// per warp) goes to the block of rank g mod G, which stages the four stacked quadrant
 // operators [4 Pc][P] once (the same for every box of the level) and applies
 // them to each warp's box in one pass over its 4 Pc child coefficients.  A few
 // blocks then carry the level while the others go on to their warp items.
 // Called by all threads of the block.
 template <class C>
-__device__ void m2m_quad(const FusedArgs<C>& a, int l, int nbi, C* sT, C* wsm, int warp, int lane,
-                         unsigned long long* dg) {
+__device__ void m2m_quad(const FusedArgs<C>& a, int l, int nbi, C* sT, C* wsm, int warp, int lane, int rb,
+                         bool have, unsigned long long* dg) {
   const int ng = (nbi + nw() - 1) / nw();
-  if ((int)blockIdx.x >= ng) return;
+  if (rb >= ng) return;
   const int P = a.P[l], Pc = a.P[l + 1], K = 4 * Pc;
   const int S = a.S[l], O = a.O[l], Sc = a.S[l + 1], Oc = a.O[l + 1];
-  __syncthreads();
-  stage_copy_quad(sT, a.m2m[l] + (size_t)Oc * S + O, P, Pc, S, Sc);
+  if (!have) {           // not staged ahead, at the end of the previous stage
+    __syncthreads();
+    stage_copy_quad(sT, a.m2m[l] + (size_t)Oc * S + O, P, Pc, S, Sc);
+  }
   __syncthreads();
   if (dg && threadIdx.x == 0) dg[8192] = gtimer();     // diagnostic: operators staged
-  for (int g = blockIdx.x; g < ng; g += gridDim.x) {
+  for (int g = rb; g < ng; g += gridDim.x) {
     const int i = g * nw() + warp;
     if (i >= nbi) continue;
     const int box = a.ne[l][i];
@@ -1620,6 +1624,51 @@ __device__ bool tc_m2l_item(const FusedArgs<cplxf>& a, int l, int item, unsigned
   return true;
 }
 
+// Block items of the next stage, so that a block can stage their operators in
+// shared memory at the end of the current stage (off the next stage's critical
+// path): the M2M quadrant stack of a B stage, the first M2L chunk's operator and
+// the L2L quadrant stack of a D stage.  The rules are those of the stages.
+template <class C>
+__device__ __forceinline__ bool bstage_quad(const FusedArgs<C>& a, int l, int wstride, int* ng) {
+  const int P = a.P[l], Pc = a.P[l + 1];
+  const bool top = (int64_t)a.nne[l] * P <= wstride;
+  const bool quad = sizeof(C) == sizeof(cplxf) && l >= 1 && !top && 4 * Pc <= PF_NCOEF && 4 * Pc * P <= a.treg;
+  *ng = quad ? (a.nne[l] + nw() - 1) / nw() : 0;
+  return quad;
+}
+struct DItems {
+  bool ql2l;
+  int ntc, nchu, ngl, nl2l;
+};
+template <class C, bool TC>
+__device__ __forceinline__ DItems dstage_items(const FusedArgs<C>& a, int l, int wstride) {
+  const int P = a.P[l], Pp = a.P[l - 1];
+  const bool top = (int64_t)a.nne[l] * P <= wstride;
+  DItems d;
+  d.nl2l = top ? a.nne[l] * P : a.nne[l];
+  const bool wpair = a.m2l_warp || P > TSP;
+  d.ql2l = sizeof(C) == sizeof(cplxf) && !top && Pp <= PF_NCOEF && 4 * Pp * P <= (a.tregL > 0 ? a.tregL : a.treg);
+  const bool tcl = TC && sizeof(C) == sizeof(cplxf) && a.tc_kp[l] > 0;
+  d.ntc = tcl ? a.tc_ntile[l] * a.tc_ngrp[l] : 0;
+  d.nchu = (wpair || tcl) ? 0 : a.nch[l];
+  d.ngl = d.ql2l ? (d.nl2l + nw() - 1) / nw() : 0;
+  return d;
+}
+// The M2L chunk b's operator of level l, staged transposed ([target][source]).
+template <class C>
+__device__ __forceinline__ void stage_chunk(const FusedArgs<C>& a, int l, int b, C* sT) {
+  const int P = a.P[l], S = a.S[l], O = a.O[l];
+  const C* To = a.m2lt[l] + (size_t)a.ch_off[l][b] * S * S + (size_t)O * S + O;   // [n source][l target]
+  if (S == P)
+    stage_copy(sT, To, P * P, IdxTranspose{P});
+  else
+    stage_copy_bt(sT, To, P, S);
+}
+template <class C>
+__device__ __forceinline__ void stage_l2l_quad(const FusedArgs<C>& a, int l, C* dst) {
+  stage_copy_quad(dst, a.l2l[l - 1] + (size_t)a.O[l - 1] * a.S[l] + a.O[l], a.P[l], a.P[l - 1], a.S[l], a.S[l - 1]);
+}
+
 template <class C>
 __device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, int wstride, C* sT, C* wsm, int lane) {
   const int P = a.P[l], Pc = a.P[l + 1], PP = Pc * P;
@@ -1773,10 +1822,49 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int G = gridDim.x;
   const int wfirst = warp_first(blockIdx.x, warp, G), wstride = G * nw();
-  C* wsm = sm + a.treg + (size_t)warp * PF_NCOEF;               // per-warp scratch
+  C* wsm = sm + a.treg + a.tregL + (size_t)warp * PF_NCOEF;     // per-warp scratch
   C* sT = sm;                                                   // [P][P] staged M2L operator (row stride P, odd)
+  C* sL = sm + a.treg;                                          // staged L2L quadrant stack (when tregL > 0)
   const int D = a.D;
   int ks = 0;
+  // block items of consecutive stages start at blocks half a grid apart, so the
+  // blocks that stage the next stage's operators at the end of this one are not
+  // the ones carrying this stage's block items; rank(stage) is the block's rank
+  // in a stage's block-item order
+  auto rank = [&](int stage) { return (int)((blockIdx.x + G - ((stage & 1) ? G / 2 : 0)) % G); };
+  int pf_b = -1, pf_c = -1, pf_cl = -1, pf_l = -1;   // what is staged ahead: B level, chunk (level), L2L level
+  // at the end of a stage, before its barrier: stage the operators of this
+  // block's first block items of the next stage (index sn), a B stage of level
+  // lb or a D stage of level ld (-1: none)
+  auto prefetch = [&](int sn, int lb, int ld) {
+    const int rb = rank(sn);
+    if (lb >= 1) {
+      int ng = 0;
+      if (bstage_quad(a, lb, wstride, &ng) && rb < ng) {
+        __syncthreads();
+        stage_copy_quad(sT, a.m2m[lb] + (size_t)a.O[lb + 1] * a.S[lb] + a.O[lb], a.P[lb], a.P[lb + 1], a.S[lb],
+                        a.S[lb + 1]);
+        pf_b = lb;
+      }
+    } else if (ld >= 1) {
+      const DItems d = dstage_items<C, TC>(a, ld, wstride);
+      if (d.ntc > 0) return;                    // tensor-core items take the whole shared memory
+      bool synced = false;
+      if (rb < d.nchu) {
+        __syncthreads();
+        synced = true;
+        stage_chunk(a, ld, rb, sT);
+        pf_c = rb;
+        pf_cl = ld;
+      }
+      const int first = d.nchu, b0 = rb >= first ? rb : rb + ((first - rb + G - 1) / G) * G;
+      if (a.tregL > 0 && d.ngl > 0 && b0 < first + d.ngl) {
+        if (!synced) __syncthreads();
+        stage_l2l_quad(a, ld, sL);
+        pf_l = ld;
+      }
+    }
+  };
   // FP32 product with tensor-core M2L levels: the block holds TC_NCOL columns
   // of tensor memory and two mbarriers (MMA completion, operator copy) for the
   // whole launch; tc_leave gives the columns back on every way out
@@ -1926,6 +2014,16 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
       fiber_part(a, sm, blockIdx.x, G, warp, lane);
     else if (blockIdx.x >= gA)
       fiber_part(a, sm, blockIdx.x - gA, a.fblk, warp, lane);
+    // the first B stage's (or D_1's) operators, staged ahead; the fiber part
+    // is done with the shared memory
+    {
+      const int lst = a.top3 ? 2 : 0;
+      __syncthreads();
+      if (D - 1 >= lst)
+        prefetch(ks, D - 1, -1);
+      else
+        prefetch(ks, -1, 1);
+    }
   }
   if (!grid_barrier(a.bar, a.err, a.wait_ns, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
       tc_leave();
@@ -1957,8 +2055,11 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
     // its own would stream the whole [4][Pc][P] table from L2 for every box)
     const bool quad = sizeof(C) == sizeof(cplxf) && l >= 1 && !top && 4 * Pc <= PF_NCOEF && 4 * Pc * P <= a.treg;
     const bool staged = quad || (l >= 1 && !top && 4 * Pc <= PF_NCOEF && Pc * P <= TSIZE && P <= 64);
-    if (quad)
-      m2m_quad(a, l, nbi, sT, wsm, warp, lane, a.bdone ? a.bdone + (size_t)(ks - 1) * G + blockIdx.x : nullptr);
+    if (quad) {
+      m2m_quad(a, l, nbi, sT, wsm, warp, lane, rank(ks - 1), pf_b == l,
+               a.bdone ? a.bdone + (size_t)(ks - 1) * G + blockIdx.x : nullptr);
+      pf_b = -1;
+    }
     else if (staged)
       m2m_staged(a, l, nbi, wfirst, wstride, sT, wsm, lane);
     if (a.bdone && threadIdx.x == 0) a.bdone[(size_t)(ks - 1) * G + blockIdx.x] = gtimer();
@@ -2067,6 +2168,12 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
         }
       }
     }
+    // the next stage's operators, staged ahead (this stage's items are done
+    // with the shared memory once the block has passed this point)
+    if (l - 1 >= lstop)
+      prefetch(ks, l - 1, -1);
+    else
+      prefetch(ks, -1, 1);
     if (!grid_barrier(a.bar, a.err, a.wait_ns, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
       tc_leave();
       return;
@@ -2086,18 +2193,18 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
     const bool wpair = a.m2l_warp || P > TSP;
     // L2L as block items (groups of nw() boxes, the stacked quadrant operators
     // staged once per block) when the FP32 tables fit the staging region
-    const bool ql2l = sizeof(C) == sizeof(cplxf) && !top && Pp <= PF_NCOEF && 4 * Pp * P <= a.treg;
     // M2L on the tensor cores at this level (FP32 product): block items over
     // (tile of 128 targets, group of offsets) in place of the chunks
-    const bool tcl = TC && sizeof(C) == sizeof(cplxf) && a.tc_kp[l] > 0;
-    const int ntc = tcl ? a.tc_ntile[l] * a.tc_ngrp[l] : 0;
-    const int nchu = (wpair || tcl) ? 0 : a.nch[l];
-    const int ngl = ql2l ? (nl2l + nw() - 1) / nw() : 0;
+    const DItems di = dstage_items<C, TC>(a, l, wstride);
+    const bool ql2l = di.ql2l, tcl = di.ntc > 0;
+    const int ntc = di.ntc, nchu = di.nchu, ngl = di.ngl;
     // block items: the tensor-core tiles or the staged M2L chunks first, then
-    // the L2L groups; then the warp items
+    // the L2L groups (in their own region when there is one); then the warp items
     {
-      bool l2l_ready = false;
-      for (int b0 = blockIdx.x; b0 < ntc + nchu + ngl; b0 += G) {
+      C* sLL = a.tregL > 0 ? sL : sT;
+      bool l2l_ready = pf_l == l;
+      const int rb = rank(ks - 1);
+      for (int b0 = rb; b0 < ntc + nchu + ngl; b0 += G) {
         if (b0 < ntc) {
           if constexpr (TC && sizeof(C) == sizeof(cplxf)) {
             // a wait that ran out has set the error flag: the next barrier ends the product
@@ -2109,21 +2216,17 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
         if (b >= nchu) {
           if (!l2l_ready) {
             __syncthreads();                                  // sT of the last chunk is done
-            stage_copy_quad(sT, a.l2l[l - 1] + (size_t)a.O[l - 1] * a.S[l] + a.O[l], P, Pp, a.S[l], a.S[l - 1]);
-            __syncthreads();
+            stage_l2l_quad(a, l, sLL);
             l2l_ready = true;
           }
-          l2l_quad_group(a, l, nl2l, b - nchu, sT, wsm, warp, lane);
+          __syncthreads();
+          l2l_quad_group(a, l, nl2l, b - nchu, sLL, wsm, warp, lane);
           continue;
         }
-        const int o = a.ch_off[l][b], pb = a.ch_beg[l][b], pe = a.ch_end[l][b];
+        const int pb = a.ch_beg[l][b], pe = a.ch_end[l][b];
         const int S = a.S[l], O = a.O[l];
-        const C* To = a.m2lt[l] + (size_t)o * S * S + (size_t)O * S + O;   // [n source][l target], used block
         __syncthreads();                                      // sT of the previous chunk is done
-        if (S == P)
-          stage_copy(sT, To, P * P, IdxTranspose{P});
-        else
-          stage_copy_bt(sT, To, P, S);
+        if (!(b0 == rb && pf_c == b && pf_cl == l)) stage_chunk(a, l, b, sT);
         __syncthreads();
         // two pairs per warp pass, sharing the operator rows read from shared memory
         for (int pi = pb + 2 * warp; pi < pe; pi += 2 * nw()) {
@@ -2231,6 +2334,7 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
       __syncwarp();
       for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * S + O + n, colmv(To + n, S, wsm, P));
     }
+    if (l < D) prefetch(ks, -1, l + 1);     // the next D stage's operators, staged ahead
     if (!grid_barrier(a.bar, a.err, a.wait_ns, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
       tc_leave();
       return;
@@ -2342,6 +2446,7 @@ cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedA
   a.done = done;
   a.tws_off = 2 * h->max_fiber;
   a.treg = sizeof(C) == sizeof(cplxf) ? std::max(TSIZE, h->fz_treg32) : TSIZE;
+  a.tregL = sizeof(C) == sizeof(cplxf) && h->fz_tcb32 == 0 ? h->fz_tregL32 : 0;
   a.nr_meta = reinterpret_cast<const longlong2*>(h->nr_meta);
   a.tc_any = 0;
   for (int l = 0; l <= h->D; ++l) {
@@ -2512,7 +2617,7 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
     a.top3 = h->m2m31 != nullptr &&
              (int64_t)h->lev[2].nne * h->lev[2].P + (int64_t)h->lev[1].nne * h->lev[1].P + 4 * h->lev[0].P <= w;
   }
-  const size_t smem = fused_smem<C>(h->max_fiber, a.treg, tc ? h->fz_tcb32 : 0, nwarp);
+  const size_t smem = fused_smem<C>(h->max_fiber, a.treg + a.tregL, tc ? h->fz_tcb32 : 0, nwarp);
   const void* fn = tc ? (const void*)matvec_fused_kernel<cplxf, true> : (const void*)matvec_fused_kernel<C, false>;
   {
     // the kernel's dynamic shared-memory limit is process-wide: raise it to
@@ -2732,16 +2837,20 @@ cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int64_t wst = (int64_t)2 * nsm * FW;
-    int need4 = 0;
+    int needm = 0, needl = 0;
     for (int l = 1; l <= h->D; ++l) {
       const int P = fused_P(h, l, true), Pp = fused_P(h, l - 1, true);
       if ((int64_t)h->lev[l].nne * P <= wst) continue;
-      if (l < h->D && 4 * fused_P(h, l + 1, true) <= PF_NCOEF) need4 = std::max(need4, 4 * fused_P(h, l + 1, true) * P);
-      if (l >= 2 && Pp <= PF_NCOEF) need4 = std::max(need4, 4 * Pp * P);
+      if (l < h->D && 4 * fused_P(h, l + 1, true) <= PF_NCOEF) needm = std::max(needm, 4 * fused_P(h, l + 1, true) * P);
+      if (l >= 2 && Pp <= PF_NCOEF) needl = std::max(needl, 4 * Pp * P);
     }
     const int cap = (int)(100 * 1024 / sizeof(cplxf)) - 2 * FW * PF_NCOEF;   // room for 16 warps' scratch
     static const bool noquad = std::getenv("PFMBEM_NO_QUAD") != nullptr;   // measurement: per-quadrant staging
-    h->fz_treg32 = noquad ? TSIZE : std::max(TSIZE, std::min(need4, cap));
+    h->fz_treg32 = noquad ? TSIZE : std::max(TSIZE, std::min(std::max(needm, needl), cap));
+    // the plain form also keeps the L2L stack in a region of its own (staged
+    // ahead beside the first M2L chunk's operator), within about 112 KB per block
+    const int capL = (int)(112 * 1024 / sizeof(cplxf)) - FW * PF_NCOEF - h->fz_treg32;
+    h->fz_tregL32 = !noquad && needl > 0 && needl <= capL ? needl : 0;
   }
   // tensor-core M2L levels of the FP32 product (their operands need up to
   // tc_smem_bytes(TC_KPMAX) of shared memory)
@@ -2753,7 +2862,7 @@ cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
   }
   h->fz_grid64 = std::min(fused_grid<cplx, false>(h->max_fiber, TSIZE, 0), need);
   h->fz_grid32 = std::min(h->fz_tcb32 > 0 ? fused_grid<cplxf, true>(h->max_fiber, h->fz_treg32, h->fz_tcb32)
-                                          : fused_grid<cplxf, false>(h->max_fiber, h->fz_treg32, 0),
+                                          : fused_grid<cplxf, false>(h->max_fiber, h->fz_treg32 + h->fz_tregL32, 0),
                           need);
   if (h->fz_grid64 <= 0 || h->fz_grid32 <= 0) return cudaSuccess;
   {
