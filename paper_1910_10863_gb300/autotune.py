@@ -2,8 +2,8 @@
 
 The leaf occupancy (how many elements a leaf box may hold, which sets the
 quadtree depth and so the balance between the cached near-field blocks and the
-M2L translations) and the M2L engine (CUDA cores or tcgen05 tensor cores) are
-chosen per instance class by timing candidate plans on a representative block:
+M2L translations) is chosen per instance class by timing candidate plans on a
+representative block:
 
     cost = create + solve,
 
@@ -24,7 +24,11 @@ import time
 
 from . import pfmbem as pf
 
-CANDIDATES = [dict(leaf_max=lm, m2l_mode=mm) for lm in (32, 64, 128) for mm in (1, 2)]
+# The M2L engine is left to the library's own rule (tensor cores from 1024 boxes
+# a level up, which no instance of a sweep reaches): forcing the tensor-core form
+# on small blocks puts one 512-thread block per SM under every product, which
+# keeps concurrent instances of a batch from sharing the GPU.
+CANDIDATES = [dict(leaf_max=lm) for lm in (32, 64, 128)]
 
 
 def instance_key(w) -> str:

@@ -1543,6 +1543,15 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
             }
           }
           if ((st = upload(h, &h->nr_meta, meta)) != PFMBEM_OK) return st;
+          // the rows cut into pieces of at most 128 sources: (piece << 24) | element
+          std::vector<unsigned> pieces;
+          pieces.reserve((size_t)E + E / 2);
+          for (int s2 = 0; s2 < E && E < (1 << 24); ++s2) {
+            const int ns = (int)(meta[2 * (size_t)s2 + 1] & 0xffffffffll);
+            for (int pc = 0; pc * 128 < std::max(ns, 1) && pc < 256; ++pc) pieces.push_back(((unsigned)pc << 24) | (unsigned)s2);
+          }
+          h->nr_npiece = (int)pieces.size();
+          if ((st = upload(h, &h->nr_piece, pieces)) != PFMBEM_OK) return st;
         }
         h->Un = dalloc<cplx>(h, (size_t)2 * E);
         h->Unf = dalloc<cplxf>(h, (size_t)2 * E);

@@ -105,6 +105,11 @@ struct FusedArgs {
   const int64_t* nc_base;
   const int* nc_sbase;
   const longlong2* nr_meta;          // per sorted element: block offset of its near row, (first source << 32) | sources
+  // FP32 product: the near rows cut into pieces of at most NR_PIECE sources
+  // ((piece << 24) | sorted element), summed atomically into Un (zeroed in
+  // stage A); 0 pieces: whole rows
+  const unsigned* nr_piece;
+  int npiece;
   const int* nc_src;
   const C* nc_val;
   int nchunk;                        // direct-row chunks (fibers not applied by FFT)
@@ -742,6 +747,61 @@ __device__ __forceinline__ void near_row(const FusedArgs<C>& a, int s, int lane)
     a.Un[2 * s] = u;
     a.Un[2 * s + 1] = du;
   }
+}
+
+// One piece of a near-field row in differences (FP32 product): sources
+// [NR_PIECE p, NR_PIECE (p + 1)) of target s, one pass of four sources per lane,
+// added atomically into Un.  Pieces bound every near item's latency to one
+// pass, whatever the row's length (crowded leaves give rows of ~600 sources).
+constexpr int NR_PIECE = 128;
+__device__ __forceinline__ void near_piece_diff(const FusedArgs<cplxf>& a, unsigned code, int lane) {
+  const int s = (int)(code & 0xffffffu), jb = (int)(code >> 24) * NR_PIECE;
+  const longlong2 mt = __ldg(a.nr_meta + s);
+  const cplxf* row = a.nc_val + mt.x;
+  const int* src = a.nc_src + (int)(mt.y >> 32);
+  const int ns = (int)(mt.y & 0xffffffffll);
+  const cplxf tph = ldcg(a.dens + 2 * s), tpl = ldcg(a.dlo + 2 * s);
+  const cplxf tvh = ldcg(a.dens + 2 * s + 1), tvl = ldcg(a.dlo + 2 * s + 1);
+  constexpr int NJ = NR_PIECE / 32;
+  int f[NJ];
+  cplxf q[NJ][4];
+#pragma unroll
+  for (int k = 0; k < NJ; ++k) {
+    const int jj = jb + lane + 32 * k;
+    f[k] = jj < ns ? __ldg(src + jj) : s;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[k][c] = jj < ns ? row[4 * jj + c] : cplxf{0, 0};
+  }
+  cplxf u0{0, 0}, d0{0, 0}, u1{0, 0}, d1{0, 0};
+#pragma unroll
+  for (int k = 0; k < NJ; k += 2) {
+    const cplxf p0 = (ldcg(a.dens + 2 * f[k]) - tph) + (ldcg(a.dlo + 2 * f[k]) - tpl);
+    const cplxf v0 = (ldcg(a.dens + 2 * f[k] + 1) - tvh) + (ldcg(a.dlo + 2 * f[k] + 1) - tvl);
+    const cplxf p1 = (ldcg(a.dens + 2 * f[k + 1]) - tph) + (ldcg(a.dlo + 2 * f[k + 1]) - tpl);
+    const cplxf v1 = (ldcg(a.dens + 2 * f[k + 1] + 1) - tvh) + (ldcg(a.dlo + 2 * f[k + 1] + 1) - tvl);
+    u0 += q[k][0] * p0 + q[k][1] * v0;
+    d0 += q[k][2] * p0 + q[k][3] * v0;
+    u1 += q[k + 1][0] * p1 + q[k + 1][1] * v1;
+    d1 += q[k + 1][2] * p1 + q[k + 1][3] * v1;
+  }
+  const cplxf u = wsum(u0 + u1), du = wsum(d0 + d1);
+  if (lane == 0) {
+    atomic_add(a.Un + 2 * s, u);
+    atomic_add(a.Un + 2 * s + 1, du);
+  }
+}
+
+// Near item i of a stage: a piece (FP32 product in differences, when the pieces
+// are set up) or a whole row.
+template <class C>
+__device__ __forceinline__ void near_item(const FusedArgs<C>& a, int i, int lane) {
+  if constexpr (sizeof(C) == sizeof(cplxf)) {
+    if (a.npiece > 0) {
+      near_piece_diff(a, __ldg(a.nr_piece + i), lane);
+      return;
+    }
+  }
+  near_row(a, i, lane);
 }
 
 // Inverse block symbol of a regular-polygon fiber's whole same-fiber block of
@@ -1911,6 +1971,9 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
       const size_t nz = (size_t)a.nbox[l] * a.S[l];
       for (size_t t = (size_t)blockIdx.x * nt() + threadIdx.x; t < nz; t += (size_t)G * nt()) Lz[t] = C{0, 0};
     }
+    if (sizeof(C) == sizeof(cplxf) && a.npiece > 0)      // the near pieces add into Un
+      for (size_t t = (size_t)blockIdx.x * nt() + threadIdx.x; t < 2 * (size_t)a.E; t += (size_t)G * nt())
+        a.Un[t] = C{0, 0};
     // blocks [gA, G) apply the same-fiber blocks while the others run P2M
     const int gA = G - a.fblk;
     if (blockIdx.x < gA) {
@@ -2036,11 +2099,13 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
   // the near-field rows need only the densities of stage A: they are spread
   // evenly over all B and D stages, whose FMM work leaves most warps idle
   const int lstop = a.top3 ? 2 : 0, nbst = D - lstop, nst = nbst + D;
+  // near items: pieces of rows (FP32 product) or whole rows
+  const int NI = (sizeof(C) == sizeof(cplxf) && a.npiece > 0) ? a.npiece : a.E;
   for (int l = D - 1; l >= lstop; --l) {
     const int P = a.P[l], Pc = a.P[l + 1];
     const int jst = D - 1 - l;
-    const int r0 = a.near_first ? (jst == 0 ? 0 : a.E) : (int)((int64_t)a.E * jst / nst);
-    const int r1 = a.near_first ? a.E : (int)((int64_t)a.E * (jst + 1) / nst);
+    const int r0 = a.near_first ? (jst == 0 ? 0 : NI) : (int)((int64_t)NI * jst / nst);
+    const int r1 = a.near_first ? NI : (int)((int64_t)NI * (jst + 1) / nst);
     // near the top of the tree the boxes are too few to occupy the grid: one
     // warp per output coefficient, lanes over the 4 Pc child coefficients.  The
     // root then forms L(0) = (R T_0) [M(1) of its four children] at once.
@@ -2066,7 +2131,7 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
     for (int i = wfirst; i < nitem; i += wstride) {
       if (staged && i < nbi) continue;
       if (i >= nbi + nx) {
-        near_row(a, r0 + (i - nbi - nx), lane);
+        near_item(a, r0 + (i - nbi - nx), lane);
         continue;
       }
       if (i >= nbi) {
@@ -2257,12 +2322,12 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
     if (sl2l && !ql2l) l2l_staged(a, l, nl2l, wfirst, wstride, sT, wsm, lane);
     const int nm2l = (wpair && !tcl) ? a.npair[l] : 0;
     const int jst = nbst + l - 1;
-    const int r0 = a.near_first ? (jst == 0 ? 0 : a.E) : (int)((int64_t)a.E * jst / nst);
-    const int r1 = a.near_first ? a.E : (int)((int64_t)a.E * (jst + 1) / nst);
+    const int r0 = a.near_first ? (jst == 0 ? 0 : NI) : (int)((int64_t)NI * jst / nst);
+    const int r1 = a.near_first ? NI : (int)((int64_t)NI * (jst + 1) / nst);
     const int nitem = nl2l + nm2l + (r1 - r0);
     for (int i = wfirst; i < nitem; i += wstride) {
       if (i >= nl2l + nm2l) {
-        near_row(a, r0 + (i - nl2l - nm2l), lane);
+        near_item(a, r0 + (i - nl2l - nm2l), lane);
         continue;
       }
       if (i < nl2l) {
@@ -2448,6 +2513,9 @@ cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedA
   a.treg = sizeof(C) == sizeof(cplxf) ? std::max(TSIZE, h->fz_treg32) : TSIZE;
   a.tregL = sizeof(C) == sizeof(cplxf) && h->fz_tcb32 == 0 ? h->fz_tregL32 : 0;
   a.nr_meta = reinterpret_cast<const longlong2*>(h->nr_meta);
+  static const bool rows = std::getenv("PFMBEM_NEAR_ROWS") != nullptr;   // measurement: whole rows
+  a.nr_piece = reinterpret_cast<const unsigned*>(h->nr_piece);
+  a.npiece = (sizeof(C) == sizeof(cplxf) && h->fz_dlo && h->nr_piece && !rows) ? h->nr_npiece : 0;
   a.tc_any = 0;
   for (int l = 0; l <= h->D; ++l) {
     const Level& L = h->lev[l];
