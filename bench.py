@@ -417,7 +417,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": ("f64" if args.precision == "fp64" else
-                      "f32/bf16+f64" if opt.m2l_mode == 2 else "f32+f64"),
+                      "f32/bf16x3+f64" if (opt.m2l_mode == 2 or plan.tc_levels) else "f32+f64"),
             "data": "synthetic",
             "config": {"workload": w.name, "elements": w.E, "unknowns": n, "fibers": w.M, "kH": w.k * w.H,
                        "tol": args.tol, "precision": args.precision, "depth": plan.depth,

@@ -87,7 +87,8 @@ typedef struct {
                        which uses the central sub-blocks of the FP64 tables; 0 = 18.
                        At most the FP64 order; the FP64 refinement of a mixed solve
                        keeps the solution at the FP64 product's accuracy */
-  int reserved[1];
+  int batch_group;  /* blocks per instance group of pfmbem_solve_batch's persistent launch;
+                       0 = 16.  A batch uses the largest value among its handles */
 } pfmbem_options;
 
 /* Outcome of a solve. */
@@ -118,6 +119,10 @@ typedef struct {
   int64_t near_blocks;    /* cached near-field 2x2 complex blocks (0 when not cached) */
   int64_t fiber_entries;  /* cached fiber-block complex entries (0 when not cached) */
   int cached;             /* 1 when the element integrals are cached in device memory */
+  int tc_levels;          /* bit l set: the FP32 product runs level l's M2L on the tensor cores
+                             (tcgen05, BF16x3 split products accumulated in FP32) */
+  int p32[16];            /* expansion order per level of the FP32 product (<= p) */
+  int64_t m2l_pairs_level[16];  /* M2L translations per matvec at each level 0..depth */
 } pfmbem_plan_info;
 
 /* Create a solver for one fundamental block (paper Sec. 2-3).
@@ -180,13 +185,23 @@ pfmbem_status pfmbem_matvec(pfmbem_t h, const double* x, double* y, int precisio
 pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_guess,
                            double tol, int maxit, pfmbem_info* info);
 
-/* Solve many blocks together (band-gap sweeps): the incident-wave systems of
- * ninst handles are solved in lockstep, one unit of GMRES work per instance per
- * phase, each instance's kernels on its own handle's stream, so that the GPU
- * overlaps the work of many small blocks.  Each handle uses its own precision:
- * FP64, or mixed (FP32 operator in the inner GMRES, FP64 residuals for the
- * refinement).  psis[i] complex [2 E_i] receive the solutions; infos may be
- * NULL.  Returns the first non-OK instance status (others are still solved). */
+/* Solve many blocks together (band-gap sweeps, Sec. 4): the incident-wave
+ * systems of ninst handles, each with its own geometry, size, frequency and
+ * angle.  All instances are solved inside ONE persistent cooperative launch on
+ * the first handle's stream (ordered after every handle's pending work): the
+ * grid is cut into groups of blocks, and each group takes the next instance
+ * from a device-side queue ordered by element count, longest first, and runs
+ * its whole solve (refinement, GMRES cycles, products, Arnoldi steps) with
+ * barriers over the group only.  The host waits once, at the end.  Handles
+ * that cannot run in it (the tensor-core or per-stage product, restart length
+ * above 250) make the whole batch run in host-driven lockstep instead, one unit
+ * of GMRES work per instance per phase on the handles' own streams.  Each
+ * handle uses its own precision: FP64, or mixed (FP32 operator in the inner
+ * GMRES, FP64 residuals for the refinement).  psis[i] complex [2 E_i] (host or
+ * device) receive the solutions; infos may be NULL (info.ms is the batch's
+ * time).  Returns the first non-OK instance status (others are still solved);
+ * ETIMEOUT for every instance when a bounded device wait of the launch gave up
+ * (options.wait_us of the handles, 1 s by default). */
 pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* psis, double tol, int maxit,
                                  pfmbem_info* infos);
 

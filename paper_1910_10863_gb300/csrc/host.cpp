@@ -1720,6 +1720,9 @@ static pfmbem_status gmres_alloc(pfmbem* h, int m) {
 
 static inline std::complex<double> toz(cplx a) { return {a.re, a.im}; }
 
+// Estimate threshold (times tol) that ends an inner GMRES cycle of the refinement.
+constexpr double kTrustThr = 0.5;
+
 // Arnoldi steps enqueued per host check of the device-side GMRES cycle.
 constexpr int kArnBatch = 4;
 
@@ -1784,6 +1787,19 @@ static pfmbem_status gmres_cycle_device(pfmbem* h, cplx* x, double beta, double 
   return PFMBEM_OK;
 }
 
+// A GMRES cycle ends once its Arnoldi residual estimate falls below f tol: f =
+// 1/2 where the true residual is checked after the cycle (a margin against an
+// optimistic estimate); for the inner solves of the refinement, which trust the
+// estimate and whose error the FP64 residual of the next refinement step
+// corrects, f = trust_thr() (PFMBEM_INNER_THR overrides, for measurement).
+static double trust_thr() {
+  static const double f = [] {
+    const char* v = std::getenv("PFMBEM_INNER_THR");
+    return v ? std::atof(v) : kTrustThr;
+  }();
+  return f;
+}
+
 // Restarted GMRES(m) with classical Gram-Schmidt applied twice; A is applied by
 // the FMM matvec in the given precision.  Solves A x = b in place of x (device).
 // Restarted GMRES(m) with CGS2 Arnoldi, flexibly right-preconditioned by the
@@ -1838,8 +1854,8 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
     if (h->arn_grid > 0 && h->fused && h->cached && m < 256) {
       int steps = 0, reason = 0;
       double est = 1;
-      pfmbem_status sc = gmres_cycle_device(h, x, beta, bnorm, 0.5 * tol, maxit - iters, precision, &steps, &est,
-                                            &reason);
+      pfmbem_status sc = gmres_cycle_device(h, x, beta, bnorm, (trust_estimate ? trust_thr() : 0.5) * tol,
+                                            maxit - iters, precision, &steps, &est, &reason);
       if (sc != PFMBEM_OK) return sc;
       iters += steps;
       ++restarts;
@@ -1894,7 +1910,7 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
       gvec[j] = std::conj(cs[j]) * gj;
       gvec[j + 1] = -sn[j] * gj;
       double est = std::abs(gvec[j + 1]) / bnorm;
-      if (est <= 0.5 * tol || hnext == 0) {
+      if (est <= (trust_estimate ? trust_thr() : 0.5) * tol || hnext == 0) {
         ++j;
         if (trust_estimate) {
           relres = est;
@@ -1922,6 +1938,9 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
 }
 
 // ============================================================== batched solve
+// Blocks per instance group of the persistent batched launch.
+constexpr int kBatchGroup = 16;
+
 // Lockstep iterative refinement over many handles: every instance is a small
 // state machine (outer FP64 residual, then Arnoldi steps of an inner GMRES on
 // the handle's operator precision); each lockstep phase enqueues one unit of
@@ -2084,6 +2103,59 @@ pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* p
     b.gv.assign(g.m + 1, 0.0);
     CK(k_rhs(h, g.b));
     CK(cudaMemsetAsync(g.x, 0, sizeof(cplx) * g.n, h->stream));
+  }
+  // One persistent launch over all instances when every handle can run in it
+  // (PFMBEM_BATCH_LOCKSTEP=1 keeps the host-driven lockstep below, for
+  // measurement); PFMBEM_BATCH_GROUP sets the blocks per instance group.
+  static const bool lockstep = std::getenv("PFMBEM_BATCH_LOCKSTEP") != nullptr;
+  bool persist = !lockstep && ninst > 0;
+  for (int i = 0; persist && i < ninst; ++i) persist = batch_eligible(hs[i]);
+  if (persist) {
+    static const char* gsenv = std::getenv("PFMBEM_BATCH_GROUP");
+    int GS = 0;
+    for (int i = 0; i < ninst; ++i) GS = std::max(GS, hs[i]->opt.batch_group);
+    if (GS <= 0) GS = kBatchGroup;
+    if (gsenv) GS = std::max(1, std::atoi(gsenv));
+    // longest first (LPT): the instances by element count, descending
+    std::vector<int> order(ninst);
+    for (int i = 0; i < ninst; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return hs[a]->E > hs[b]->E; });
+    pfmbem* h = hs[0];                 // errors are reported on the first handle
+    cudaStream_t st = h->stream;
+    // the launch runs on the first handle's stream, after every handle's
+    // pending work (set-up tails, right-hand sides)
+    std::vector<BatchResult> res(ninst);
+    int timed_out = 0;
+    const cudaError_t e = k_batch_solve(ninst, hs, order.data(), GS, tol, maxit, trust_thr(), st, res.data(),
+                                        &timed_out);
+    if (e == cudaErrorNotSupported) {
+      cudaGetLastError();
+      persist = false;                 // the lockstep below
+    } else if (e != cudaSuccess) {
+      return fail_cuda(h, e, "batched solve");
+    } else {
+      pfmbem_status worst = PFMBEM_OK;
+      for (int i = 0; i < ninst; ++i) {
+        const bool pdev = is_device_ptr(psis[i]);
+        CK(cudaMemcpyAsync(psis[i], hs[i]->gw.x, sizeof(cplx) * hs[i]->gw.n,
+                           pdev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+      }
+      CK(cudaStreamSynchronize(st));
+      const double ms = now_ms() - t0;
+      for (int i = 0; i < ninst; ++i) {
+        pfmbem_status si = timed_out ? PFMBEM_ETIMEOUT : (pfmbem_status)res[i].status;
+        if (timed_out) hs[i]->err = "batched solve: a bounded device-side wait gave up";
+        if (infos) {
+          infos[i].iters = res[i].iters;
+          infos[i].restarts = res[i].refinements;
+          infos[i].rel_residual = res[i].relres;
+          infos[i].ms = ms;
+          infos[i].status = si;
+        }
+        if (si != PFMBEM_OK && worst == PFMBEM_OK) worst = si;
+      }
+      return worst;
+    }
   }
   int active = ninst;
   while (active > 0) {
@@ -2252,6 +2324,11 @@ pfmbem_status pfmbem_plan(pfmbem_t h, pfmbem_plan_info* info) {
     h->info.fiber_quad = (int64_t)c[3];
   }
   h->info.cached = h->cached ? 1 : 0;
+  h->info.tc_levels = h->fused ? k_fused_tc_levels(h) : 0;
+  for (int l = 0; l < 16; ++l) {
+    h->info.p32[l] = l <= h->D ? (h->fused ? (k_fused_order(h, l, true) - 1) / 2 : h->lev[l].p) : 0;
+    h->info.m2l_pairs_level[l] = l <= h->D ? (int64_t)h->lev[l].nil : 0;
+  }
   h->info.near_blocks = h->cached ? h->nc_blocks : 0;
   h->info.fiber_entries = h->cached ? h->fb_entries : 0;
   *info = h->info;

@@ -359,6 +359,20 @@ cudaError_t k_fused_tables(pfmbem* h);
 cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done = nullptr);
 cudaError_t k_arnoldi_step(pfmbem* h, int j, int precision);
 cudaError_t k_arnoldi_solve(pfmbem* h, cplx* y);
+// Persistent batched solve: every instance solved inside one cooperative launch
+// by groups of GS blocks, instances taken in the given order (longest first).
+// cudaErrorNotSupported when an instance cannot run in it (see batch_eligible).
+struct BatchResult {
+  int iters, refinements, status;
+  double relres;
+};
+bool batch_eligible(const pfmbem* h);
+// Coefficients 2p + 1 of level l in the single-launch product of the given
+// precision, and the levels (bit mask) whose FP32 M2L runs on the tensor cores.
+int k_fused_order(const pfmbem* h, int l, bool f32);
+int k_fused_tc_levels(const pfmbem* h);
+cudaError_t k_batch_solve(int ninst, pfmbem* const* hs, const int* order, int GS, double tol, int maxit,
+                          double trust_thr, cudaStream_t st, BatchResult* out, int* timed_out);
 cudaError_t k_fiber_symbols(pfmbem* h);
 cudaError_t k_precond_symbols(pfmbem* h);
 cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done = nullptr);

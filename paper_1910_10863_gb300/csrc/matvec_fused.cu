@@ -36,6 +36,8 @@
 #include <atomic>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
+#include <vector>
 
 #include "internal.h"
 #include "tc_common.cuh"
@@ -177,8 +179,8 @@ struct FusedArgs {
   const cplx* frs;
 };
 
-__device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k) {
-  if (stamp && blockIdx.x == 0 && threadIdx.x == 0) {
+__device__ __forceinline__ void stage_stamp(unsigned long long* stamp, int k, int bid) {
+  if (stamp && bid == 0 && threadIdx.x == 0) {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     stamp[k] = t;
@@ -219,30 +221,31 @@ __device__ __forceinline__ C wsum(C v) {
   return v;
 }
 
-// Device-wide barrier with a bounded wait; false when any block gave up.  One
-// 64-bit arrival counter that only grows: a block's arrival is a release add
-// (it publishes the block's writes), whose old value tells the barrier's
-// target, the next multiple of the grid size; the block then polls the counter
-// with acquire loads (taking in everyone else's writes) until it reaches the
-// target.  Each completed launch adds a multiple of the grid size, so the
-// counter stays aligned across launches of one grid size; it is cleared after
-// a wait ran out.  Optionally records the block's arrival time (ns).
+// Barrier over the nb blocks that share the counter bar (the whole grid, or
+// one group of blocks of a persistent launch), with a bounded wait; false when
+// any block gave up.  One 64-bit arrival counter that only grows: a block's
+// arrival is a release add (it publishes the block's writes), whose old value
+// tells the barrier's target, the next multiple of nb; the block then polls the
+// counter with acquire loads (taking in everyone else's writes) until it
+// reaches the target.  Each completed pass adds a multiple of nb, so the
+// counter stays aligned as long as only those nb blocks use it; it is cleared
+// after a wait ran out.  Optionally records the arrival time (ns) of block bid.
 __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long* p) {
   unsigned long long v;
   asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
-__device__ bool grid_barrier(unsigned long long* bar, int* err, unsigned long long limit = 1000000000ull,
-                             unsigned long long* arrive = nullptr) {
+__device__ bool group_barrier(unsigned long long* bar, int* err, unsigned long long limit, int nb, int bid,
+                              unsigned long long* arrive = nullptr) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned long long t0;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    if (arrive) arrive[blockIdx.x] = t0;
+    if (arrive) arrive[bid] = t0;
     int ok = 1;
-    const unsigned long long G = gridDim.x;
+    const unsigned long long G = (unsigned long long)nb;
     unsigned long long old;
     asm volatile("atom.release.gpu.global.add.u64 %0, [%1], 1;" : "=l"(old) : "l"(bar) : "memory");
     const unsigned long long target = (old / G + 1) * G;
@@ -259,6 +262,12 @@ __device__ bool grid_barrier(unsigned long long* bar, int* err, unsigned long lo
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// The barrier over the whole grid.
+__device__ __forceinline__ bool grid_barrier(unsigned long long* bar, int* err, unsigned long long limit = 1000000000ull,
+                                             unsigned long long* arrive = nullptr) {
+  return group_barrier(bar, err, limit, (int)gridDim.x, (int)blockIdx.x, arrive);
 }
 
 // acc += sum_m A[m * P] * w[m], m < K (A already offset to the output column),
@@ -1056,15 +1065,15 @@ __device__ __forceinline__ void arn_dots(const ArnArgs& a, int nc, int t0, int t
   }
 }
 
-template <class C>
-__global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
-  if (*(volatile const int*)a.ictl != 0) return;
+// EXT: the rotations of the serial part are staged in the dynamic shared memory
+// (at least 2 ARN_MAXC complex values) instead of a static array of their own.
+template <class C, bool EXT>
+__device__ __forceinline__ bool arnoldi_body(const ArnArgs& a, const int b, const int G, unsigned long long limit) {
   extern __shared__ __align__(128) unsigned char smraw[];
   __shared__ cplx sh[ARN_MAXC];
   __shared__ C shc[ARN_MAXC];                       // sh in the precision of the updates
   __shared__ double red[FW];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int G = gridDim.x, b = blockIdx.x;
   const int t0 = (int)((int64_t)a.n * b / G), t1 = (int)((int64_t)a.n * (b + 1) / G);
   const int nc = a.j + 1, S = 2 * (a.m + 1) + 1;
   cplx* h1 = a.acc + (size_t)(a.j & 1) * S;
@@ -1076,7 +1085,7 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
   }
   // h1 = V^H w
   arn_dots<C>(a, nc, t0, t1, h1, warp, lane);
-  if (!grid_barrier(a.bar, a.err)) return;
+  if (!group_barrier(a.bar, a.err, limit, G, b)) return false;
   // w -= V h1; ||w||^2; h2 = V^H w
   for (int i = threadIdx.x; i < nc; i += FB) shc[i] = from_d<C>(ldcg(h1 + i));
   __syncthreads();
@@ -1098,7 +1107,7 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
     atomicAdd(nrm, tot);
   }
   arn_dots<C>(a, nc, t0, t1, h2, warp, lane);
-  if (!grid_barrier(a.bar, a.err)) return;
+  if (!group_barrier(a.bar, a.err, limit, G, b)) return false;
   // ||w - V h2||^2 = ||w||^2 - ||h2||^2; v_{j+1} = (w - V h2) / ||w - V h2|| and,
   // with the preconditioner, z_{j+1} = P^-1 v_{j+1} (one block per fiber: a
   // fiber's block of P^-1 reads only its own entries)
@@ -1146,7 +1155,13 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
     // runs without global-memory latency
     const int j = a.j, m = a.m;
     cplx* col = sh;                                   // [j + 2]
-    __shared__ cplx rot[2 * ARN_MAXC];                // cs, sn of the earlier steps
+    cplx* rot;                                        // cs, sn of the earlier steps
+    if constexpr (EXT) {
+      rot = reinterpret_cast<cplx*>(smraw);
+    } else {
+      __shared__ cplx rot_s[2 * ARN_MAXC];
+      rot = rot_s;
+    }
     __syncthreads();
     for (int i = threadIdx.x; i <= j; i += FB) col[i] = ldcg(h1 + i) + ldcg(h2 + i);
     for (int i = threadIdx.x; i < j; i += FB) {
@@ -1188,17 +1203,36 @@ __global__ void __launch_bounds__(FB) arnoldi_kernel(ArnArgs a) {
     __syncthreads();
     for (int i = threadIdx.x; i <= j + 1; i += FB) a.H[(size_t)i * m + j] = col[i];
   }
+  return true;
+}
+
+template <class C>
+__global__ void __launch_bounds__(FB) arnoldi_kernel(const __grid_constant__ ArnArgs a) {
+  if (*(volatile const int*)a.ictl != 0) return;
+  arnoldi_body<C, false>(a, (int)blockIdx.x, (int)gridDim.x, 1000000000ull);
 }
 
 // y = R^{-1} g over the steps completed in the cycle (R: the rotated H) by
 // back substitution: R (up to 32 steps) is staged in shared memory by the
-// block, then one thread solves.
-__global__ void arnoldi_solve_kernel(const cplx* __restrict__ H, const cplx* __restrict__ g, int m,
-                                     const int* __restrict__ ictl, cplx* __restrict__ y) {
+// block, then one thread solves.  Called by all threads of one block.
+// EXT: R and g staged in the dynamic shared memory (at least 1056 complex
+// values) instead of static arrays of their own.
+template <bool EXT>
+__device__ void arn_backsolve(const cplx* __restrict__ H, const cplx* __restrict__ g, int m, int jf,
+                              cplx* __restrict__ y) {
   constexpr int RS = 32;
-  __shared__ cplx R[RS * RS], gs[RS];
-  const int jf = ictl[1];
+  cplx *R, *gs;
+  if constexpr (EXT) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    R = reinterpret_cast<cplx*>(smraw);
+    gs = R + RS * RS;
+  } else {
+    __shared__ cplx R_s[RS * RS], gs_s[RS];
+    R = R_s;
+    gs = gs_s;
+  }
   const bool staged = jf <= RS;
+  __syncthreads();
   if (staged) {
     for (int t = threadIdx.x; t < jf * jf; t += blockDim.x) {
       const int i = t / jf, q = t - i * jf;
@@ -1207,19 +1241,26 @@ __global__ void arnoldi_solve_kernel(const cplx* __restrict__ H, const cplx* __r
     for (int t = threadIdx.x; t < jf; t += blockDim.x) gs[t] = g[t];
   }
   __syncthreads();
-  if (threadIdx.x != 0) return;
-  cplx ys[RS];
-  for (int i = jf - 1; i >= 0; --i) {
-    cplx v = staged ? gs[i] : g[i];
-    if (staged) {
-      for (int q = i + 1; q < jf; ++q) v -= R[i * RS + q] * ys[q];
-      ys[i] = cdiv(v, R[i * RS + i]);
-      y[i] = ys[i];
-    } else {
-      for (int q = i + 1; q < jf; ++q) v -= H[(size_t)i * m + q] * y[q];
-      y[i] = cdiv(v, H[(size_t)i * m + i]);
+  if (threadIdx.x == 0) {
+    cplx ys[RS];
+    for (int i = jf - 1; i >= 0; --i) {
+      cplx v = staged ? gs[i] : g[i];
+      if (staged) {
+        for (int q = i + 1; q < jf; ++q) v -= R[i * RS + q] * ys[q];
+        ys[i] = cdiv(v, R[i * RS + i]);
+        y[i] = ys[i];
+      } else {
+        for (int q = i + 1; q < jf; ++q) v -= H[(size_t)i * m + q] * y[q];
+        y[i] = cdiv(v, H[(size_t)i * m + i]);
+      }
     }
   }
+  __syncthreads();
+}
+
+__global__ void arnoldi_solve_kernel(const cplx* __restrict__ H, const cplx* __restrict__ g, int m,
+                                     const int* __restrict__ ictl, cplx* __restrict__ y) {
+  arn_backsolve<false>(H, g, m, ictl[1], y);
 }
 
 // Warp items: item i goes to block i mod nb and, within the block, to warp
@@ -1389,7 +1430,7 @@ __device__ void fiber_part(const FusedArgs<C>& a, C* xs, int b0, int nb, int war
 // Called by all threads of the block.
 template <class C>
 __device__ void m2m_quad(const FusedArgs<C>& a, int l, int nbi, C* sT, C* wsm, int warp, int lane, int rb,
-                         bool have, unsigned long long* dg) {
+                         bool have, unsigned long long* dg, int G) {
   const int ng = (nbi + nw() - 1) / nw();
   if (rb >= ng) return;
   const int P = a.P[l], Pc = a.P[l + 1], K = 4 * Pc;
@@ -1400,7 +1441,7 @@ __device__ void m2m_quad(const FusedArgs<C>& a, int l, int nbi, C* sT, C* wsm, i
   }
   __syncthreads();
   if (dg && threadIdx.x == 0) dg[8192] = gtimer();     // diagnostic: operators staged
-  for (int g = rb; g < ng; g += gridDim.x) {
+  for (int g = rb; g < ng; g += G) {
     const int i = g * nw() + warp;
     if (i >= nbi) continue;
     const int box = a.ne[l][i];
@@ -1730,13 +1771,14 @@ __device__ __forceinline__ void stage_l2l_quad(const FusedArgs<C>& a, int l, C* 
 }
 
 template <class C>
-__device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, int wstride, C* sT, C* wsm, int lane) {
+__device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, int wstride, C* sT, C* wsm, int lane,
+                           int bid) {
   const int P = a.P[l], Pc = a.P[l + 1], PP = Pc * P;
   const int S = a.S[l], O = a.O[l], Sc = a.S[l + 1], Oc = a.O[l + 1];
   const bool dd = a.m2ml[l] != nullptr;
   const int rounds = (nbi + wstride - 1) / wstride;
   for (int rd = 0; rd < rounds; ++rd) {
-    if ((int)blockIdx.x + rd * wstride >= nbi) break;
+    if (bid + rd * wstride >= nbi) break;
     const int i = wfirst + rd * wstride;
     const bool mine = i < nbi;
     const int box = mine ? a.ne[l][i] : 0;
@@ -1807,7 +1849,8 @@ __device__ void m2m_staged(const FusedArgs<C>& a, int l, int nbi, int wfirst, in
 // [n child]) staged in shared memory; each warp's box takes the phase of its
 // own quadrant.  Called by all threads of the block, like m2m_staged.
 template <class C>
-__device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, int wstride, C* sT, C* wsm, int lane) {
+__device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, int wstride, C* sT, C* wsm, int lane,
+                           int bid) {
   const int P = a.P[l], Pp = a.P[l - 1], PP = Pp * P;
   const int S = a.S[l], O = a.O[l], Sp = a.S[l - 1], Op = a.O[l - 1];
   // FP64 product: double-float arithmetic from the hi and lo tables
@@ -1816,7 +1859,7 @@ __device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, i
   cplxf* wh = reinterpret_cast<cplxf*>(wsm);
   cplxf* wl = wh + PF_NCOEF;
   for (int rd = 0; rd < rounds; ++rd) {
-    if ((int)blockIdx.x + rd * wstride >= nl2l) break;
+    if (bid + rd * wstride >= nl2l) break;
     const int i = wfirst + rd * wstride;
     const bool mine = i < nl2l;
     const int box = mine ? a.ne[l][i] : 0, par = box >> 2, qb = box & 3;
@@ -1873,15 +1916,11 @@ __device__ void l2l_staged(const FusedArgs<C>& a, int l, int nl2l, int wfirst, i
 // tensor-core form (TC, FP32 only) holds tensor memory, with which the device
 // keeps one block per SM: it runs 512 threads per block instead.
 template <class C, bool TC>
-__global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeof(cplx) ? 3 : 2))
-    matvec_fused_kernel(FusedArgs<C> a) {
-  // a GMRES cycle that has already converged skips the products queued after it
-  if (a.done && *(volatile const int*)a.done != 0) return;
+__device__ __forceinline__ bool fused_body(const FusedArgs<C>& a, const int bid, const int G) {
   extern __shared__ __align__(128) unsigned char smraw[];
   C* sm = reinterpret_cast<C*>(smraw);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int G = gridDim.x;
-  const int wfirst = warp_first(blockIdx.x, warp, G), wstride = G * nw();
+  const int wfirst = warp_first(bid, warp, G), wstride = G * nw();
   C* wsm = sm + a.treg + a.tregL + (size_t)warp * PF_NCOEF;     // per-warp scratch
   C* sT = sm;                                                   // [P][P] staged M2L operator (row stride P, odd)
   C* sL = sm + a.treg;                                          // staged L2L quadrant stack (when tregL > 0)
@@ -1891,7 +1930,7 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
   // blocks that stage the next stage's operators at the end of this one are not
   // the ones carrying this stage's block items; rank(stage) is the block's rank
   // in a stage's block-item order
-  auto rank = [&](int stage) { return (int)((blockIdx.x + G - ((stage & 1) ? G / 2 : 0)) % G); };
+  auto rank = [&](int stage) { return (int)((bid + G - ((stage & 1) ? G / 2 : 0)) % G); };
   int pf_b = -1, pf_c = -1, pf_cl = -1, pf_l = -1;   // what is staged ahead: B level, chunk (level), L2L level
   // at the end of a stage, before its barrier: stage the operators of this
   // block's first block items of the next stage (index sn), a B stage of level
@@ -1962,23 +2001,23 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
       }
     }
   };
-  stage_stamp(a.stamp, ks++);
+  stage_stamp(a.stamp, ks++, bid);
 
   // ------------------------------------------------------------ A: gather + P2M, clear L; fiber part
   {
     for (int l = 1; l <= D; ++l) {
       C* Lz = a.L[l];
       const size_t nz = (size_t)a.nbox[l] * a.S[l];
-      for (size_t t = (size_t)blockIdx.x * nt() + threadIdx.x; t < nz; t += (size_t)G * nt()) Lz[t] = C{0, 0};
+      for (size_t t = (size_t)bid * nt() + threadIdx.x; t < nz; t += (size_t)G * nt()) Lz[t] = C{0, 0};
     }
     if (sizeof(C) == sizeof(cplxf) && a.npiece > 0)      // the near pieces add into Un
-      for (size_t t = (size_t)blockIdx.x * nt() + threadIdx.x; t < 2 * (size_t)a.E; t += (size_t)G * nt())
+      for (size_t t = (size_t)bid * nt() + threadIdx.x; t < 2 * (size_t)a.E; t += (size_t)G * nt())
         a.Un[t] = C{0, 0};
     // blocks [gA, G) apply the same-fiber blocks while the others run P2M
     const int gA = G - a.fblk;
-    if (blockIdx.x < gA) {
+    if (bid < gA) {
       const int PD = a.P[D];
-      for (int i = warp_first(blockIdx.x, warp, gA); i < a.nne[D]; i += gA * nw()) {
+      for (int i = warp_first(bid, warp, gA); i < a.nne[D]; i += gA * nw()) {
         const int box = a.ne[D][i], s0 = a.bb[D][box], s1 = a.be[D][box];
         // the leaf's elements GU x 32 at a time: indices and phases, then the
         // inputs, each batch of loads issued before its first use
@@ -2074,9 +2113,9 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
       }
     }
     if (a.fblk == 0)
-      fiber_part(a, sm, blockIdx.x, G, warp, lane);
-    else if (blockIdx.x >= gA)
-      fiber_part(a, sm, blockIdx.x - gA, a.fblk, warp, lane);
+      fiber_part(a, sm, bid, G, warp, lane);
+    else if (bid >= gA)
+      fiber_part(a, sm, bid - gA, a.fblk, warp, lane);
     // the first B stage's (or D_1's) operators, staged ahead; the fiber part
     // is done with the shared memory
     {
@@ -2088,11 +2127,11 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
         prefetch(ks, -1, 1);
     }
   }
-  if (!grid_barrier(a.bar, a.err, a.wait_ns, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
+  if (!group_barrier(a.bar, a.err, a.wait_ns, G, bid, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
       tc_leave();
-      return;
+      return false;
     }
-  stage_stamp(a.stamp, ks++);
+  stage_stamp(a.stamp, ks++, bid);
 
   // ------------------------------------------------------------ B: M2M (+ root)
   // the last B stage: level 2 when it also forms M(1), else the root
@@ -2122,12 +2161,12 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
     const bool staged = quad || (l >= 1 && !top && 4 * Pc <= PF_NCOEF && Pc * P <= TSIZE && P <= 64);
     if (quad) {
       m2m_quad(a, l, nbi, sT, wsm, warp, lane, rank(ks - 1), pf_b == l,
-               a.bdone ? a.bdone + (size_t)(ks - 1) * G + blockIdx.x : nullptr);
+               a.bdone ? a.bdone + (size_t)(ks - 1) * G + bid : nullptr, G);
       pf_b = -1;
     }
     else if (staged)
-      m2m_staged(a, l, nbi, wfirst, wstride, sT, wsm, lane);
-    if (a.bdone && threadIdx.x == 0) a.bdone[(size_t)(ks - 1) * G + blockIdx.x] = gtimer();
+      m2m_staged(a, l, nbi, wfirst, wstride, sT, wsm, lane, bid);
+    if (a.bdone && threadIdx.x == 0) a.bdone[(size_t)(ks - 1) * G + bid] = gtimer();
     for (int i = wfirst; i < nitem; i += wstride) {
       if (staged && i < nbi) continue;
       if (i >= nbi + nx) {
@@ -2239,11 +2278,11 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
       prefetch(ks, l - 1, -1);
     else
       prefetch(ks, -1, 1);
-    if (!grid_barrier(a.bar, a.err, a.wait_ns, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
+    if (!group_barrier(a.bar, a.err, a.wait_ns, G, bid, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
       tc_leave();
-      return;
+      return false;
     }
-    stage_stamp(a.stamp, ks++);
+    stage_stamp(a.stamp, ks++, bid);
   }
 
   // ------------------------------------------------------------ D: L2L + M2L
@@ -2315,11 +2354,11 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
         }
       }
     }
-    if (a.bdone && threadIdx.x == 0) a.bdone[(size_t)(ks - 1) * G + blockIdx.x] = gtimer();
+    if (a.bdone && threadIdx.x == 0) a.bdone[(size_t)(ks - 1) * G + bid] = gtimer();
     // box-form L2L with the quadrant operators staged in shared memory, one
     // quadrant at a time (the FP64 product's hi and lo tables)
     const bool sl2l = ql2l || (!top && Pp * P <= TSIZE && P <= 64 && Pp <= PF_NCOEF);
-    if (sl2l && !ql2l) l2l_staged(a, l, nl2l, wfirst, wstride, sT, wsm, lane);
+    if (sl2l && !ql2l) l2l_staged(a, l, nl2l, wfirst, wstride, sT, wsm, lane, bid);
     const int nm2l = (wpair && !tcl) ? a.npair[l] : 0;
     const int jst = nbst + l - 1;
     const int r0 = a.near_first ? (jst == 0 ? 0 : NI) : (int)((int64_t)NI * jst / nst);
@@ -2400,11 +2439,11 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
       for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * S + O + n, colmv(To + n, S, wsm, P));
     }
     if (l < D) prefetch(ks, -1, l + 1);     // the next D stage's operators, staged ahead
-    if (!grid_barrier(a.bar, a.err, a.wait_ns, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
+    if (!group_barrier(a.bar, a.err, a.wait_ns, G, bid, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
       tc_leave();
-      return;
+      return false;
     }
-    stage_stamp(a.stamp, ks++);
+    stage_stamp(a.stamp, ks++, bid);
   }
 
   // ------------------------------------------------------------ E: L2P + near field, combination of eq. 9
@@ -2466,8 +2505,18 @@ __global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeo
     }
   }
   __syncthreads();
-  stage_stamp(a.stamp, ks++);
+  stage_stamp(a.stamp, ks++, bid);
   tc_leave();
+  return true;
+}
+
+// The single-launch product over the whole grid (a cooperative launch).
+template <class C, bool TC>
+__global__ void __launch_bounds__(TC ? 2 * FB : FB, TC ? 1 : (sizeof(C) == sizeof(cplx) ? 3 : 2))
+    matvec_fused_kernel(const __grid_constant__ FusedArgs<C> a) {
+  // a GMRES cycle that has already converged skips the products queued after it
+  if (a.done && *(volatile const int*)a.done != 0) return;
+  fused_body<C, TC>(a, (int)blockIdx.x, (int)gridDim.x);
 }
 
 // Threads per block of a form of the single-launch product.
@@ -3082,3 +3131,5 @@ cudaError_t k_matvec_fused(pfmbem* h, const cplx* x, cplx* y, int precision, con
   if (precision == PFMBEM_MIXED) return launch_fused<cplxf>(h, x, y, true, done);
   return launch_fused<cplx>(h, x, y, false, done);
 }
+
+#include "batch_solve.cuh"

@@ -25,7 +25,7 @@ class Options(ctypes.Structure):
                 ("leaf_max", ctypes.c_int), ("depth", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("precision", ctypes.c_int), ("near_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int),
                 ("profile", ctypes.c_int), ("launch", ctypes.c_int), ("precond", ctypes.c_int),
-                ("wait_us", ctypes.c_int), ("p_min_mixed", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
+                ("wait_us", ctypes.c_int), ("p_min_mixed", ctypes.c_int), ("batch_group", ctypes.c_int)]
 
 
 class Info(ctypes.Structure):
@@ -39,7 +39,8 @@ class PlanInfo(ctypes.Structure):
                 ("near_quad", ctypes.c_int64), ("fiber_pairs", ctypes.c_int64), ("fiber_quad", ctypes.c_int64),
                 ("p2m_nodes", ctypes.c_int), ("lattice_q", ctypes.c_int), ("root_x0", ctypes.c_double),
                 ("root_y0", ctypes.c_double), ("setup_ms", ctypes.c_double), ("near_blocks", ctypes.c_int64),
-                ("fiber_entries", ctypes.c_int64), ("cached", ctypes.c_int)]
+                ("fiber_entries", ctypes.c_int64), ("cached", ctypes.c_int), ("tc_levels", ctypes.c_int),
+                ("p32", ctypes.c_int * 16), ("m2l_pairs_level", ctypes.c_int64 * 16)]
 
 
 _lib = None
@@ -155,7 +156,8 @@ def pfmbem_solve(h, B, psi, use_guess=False, tol=1e-8, maxit=1000, check=True) -
 
 
 def pfmbem_solve_batch(handles, psis, tol=1e-6, maxit=2000):
-    """Lockstep solve of many handles; psis are complex128 buffers (host or device)."""
+    """Solve of many handles in one persistent launch (host-driven lockstep when a
+    handle cannot run in it); psis are complex128 buffers (host or device)."""
     n = len(handles)
     hs = (ctypes.c_void_p * n)(*handles)
     ps = (ctypes.c_void_p * n)(*[addr(p) for p in psis])
