@@ -88,7 +88,8 @@ typedef struct {
                        At most the FP64 order; the FP64 refinement of a mixed solve
                        keeps the solution at the FP64 product's accuracy */
   int batch_group;  /* blocks per instance group of pfmbem_solve_batch's persistent launch;
-                       0 = 16.  A batch uses the largest value among its handles */
+                       0 = 8 (raised to fit the coefficients of the tree's top level, one
+                       warp each).  A batch uses the largest value among its handles */
 } pfmbem_options;
 
 /* Outcome of a solve. */

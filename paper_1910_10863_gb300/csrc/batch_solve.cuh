@@ -529,10 +529,8 @@ cudaError_t k_batch_solve(int ninst, pfmbem* const* hs, const int* order, int GS
   if (GS < 1) return cudaErrorInvalidValue;
   for (int i = 0; i < ninst; ++i)
     if (!batch_eligible(hs[i])) return cudaErrorNotSupported;
-  // the top of every instance's tree must run in the coefficient-per-warp form
-  // on a group (level 0 always: its box form assumes unreduced orders)
-  for (int i = 0; i < ninst; ++i)
-    if (hs[i]->lev[0].P > GS * FW) return cudaErrorNotSupported;
+  // groups large enough for the root's coefficients, one warp each
+  for (int i = 0; i < ninst; ++i) GS = std::max(GS, (hs[i]->lev[0].P + FW - 1) / FW);
   size_t smem = 0;
   for (int i = 0; i < ninst; ++i) smem = std::max(smem, batch_smem(hs[i]));
   const void* fn = (const void*)batch_solve_kernel;

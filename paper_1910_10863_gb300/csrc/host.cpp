@@ -1939,7 +1939,7 @@ static pfmbem_status gmres(pfmbem* h, const cplx* b, cplx* x, double tol, int ma
 
 // ============================================================== batched solve
 // Blocks per instance group of the persistent batched launch.
-constexpr int kBatchGroup = 16;
+constexpr int kBatchGroup = 8;
 
 // Lockstep iterative refinement over many handles: every instance is a small
 // state machine (outer FP64 residual, then Arnoldi steps of an inner GMRES on

@@ -2233,18 +2233,11 @@ __device__ __forceinline__ bool fused_body(const FusedArgs<C>& a, const int bid,
             dd_cmac(re, im, a.m2mh[l][(size_t)u * P + n], a.m2ml[l][(size_t)u * P + n], wh[u], wl[u]);
           a.M[l][(size_t)box * P + n] = from_d<C>(cplx{dd_value(re), dd_value(im)});
         }
-      } else if (4 * Pc <= PF_NCOEF) {
-        // all four children at once (an empty child contributes zeros): the
-        // quadrant operators are stored one after another, so one column walk
-        // over 4 Pc terms applies them all
-        __syncwarp();
-        for (int t = lane; t < 4 * Pc; t += 32) {
-          const int q = t / Pc, ch = 4 * box + q;
-          wsm[t] = a.bb[l + 1][ch] < a.be[l + 1][ch] ? ldcg(a.M[l + 1] + (size_t)ch * Pc + (t - q * Pc)) : C{0, 0};
-        }
-        __syncwarp();
-        for (int n = lane; n < P; n += 32) a.M[l][(size_t)box * P + n] = colmv(a.m2m[l] + n, P, wsm, 4 * Pc);
       } else {
+        // the generic form (the FP32 product may run at orders below its
+        // tables': the used coefficients and operator blocks sit at offsets O
+        // in rows of S): the children one quadrant at a time
+        const int S = a.S[l], O = a.O[l], Sc = a.S[l + 1], Oc = a.O[l + 1];
         for (int n0 = 0; n0 < P; n0 += 32) {
           const int n = n0 + lane;
           C acc{0, 0};
@@ -2252,23 +2245,24 @@ __device__ __forceinline__ bool fused_body(const FusedArgs<C>& a, const int bid,
             const int ch = 4 * box + q;
             if (a.bb[l + 1][ch] >= a.be[l + 1][ch]) continue;
             __syncwarp();
-            for (int m = lane; m < Pc; m += 32) wsm[m] = ldcg(a.M[l + 1] + (size_t)ch * Pc + m);
+            for (int m = lane; m < Pc; m += 32) wsm[m] = ldcg(a.M[l + 1] + (size_t)ch * Sc + Oc + m);
             __syncwarp();
-            if (n < P) acc += colmv(a.m2m[l] + (size_t)q * Pc * P + n, P, wsm, Pc);
+            if (n < P) acc += colmv(a.m2m[l] + (size_t)(q * Sc + Oc) * S + O + n, S, wsm, Pc);
           }
-          if (n < P) a.M[l][(size_t)box * P + n] = acc;
+          if (n < P) a.M[l][(size_t)box * S + O + n] = acc;
         }
       }
       if (l == 0) {
         // root: L(0) = R M(0), the images |m| >= 2 through the lattice sums
         // (only on a grid too small for the coefficient-per-warp form above)
+        const int S = a.S[0], O = a.O[0];
         __syncwarp();
-        for (int m = lane; m < P; m += 32) wsm[m] = ldcg(a.M[0] + m);
+        for (int m = lane; m < P; m += 32) wsm[m] = ldcg(a.M[0] + O + m);
         __syncwarp();
         for (int t = lane; t < P; t += 32) {
           C r{0, 0};
-          for (int m = 0; m < P; ++m) r += a.root[(size_t)t * P + m] * wsm[m];
-          a.L[0][t] = r;
+          for (int m = 0; m < P; ++m) r += a.root[(size_t)(O + t) * S + O + m] * wsm[m];
+          a.L[0][O + t] = r;
         }
       }
     }
@@ -2395,12 +2389,15 @@ __device__ __forceinline__ bool fused_body(const FusedArgs<C>& a, const int bid,
           acc = wsum(acc);
           if (lane == 0) atomic_add(a.L[l] + (size_t)box * S + O + n, acc);
         } else {
+          // the generic form, with the offsets of the used coefficients (see M2M)
           const int box = a.ne[l][i], par = box >> 2, q = box & 3;
+          const int S = a.S[l], O = a.O[l], Sp = a.S[l - 1], Op = a.O[l - 1];
           __syncwarp();
-          for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Pp + m);
+          for (int m = lane; m < Pp; m += 32) wsm[m] = ldcg(a.L[l - 1] + (size_t)par * Sp + Op + m);
           __syncwarp();
           for (int n = lane; n < P; n += 32)
-            atomic_add(a.L[l] + (size_t)box * P + n, colmv(a.l2l[l - 1] + (size_t)q * Pp * P + n, P, wsm, Pp));
+            atomic_add(a.L[l] + (size_t)box * S + O + n,
+                       colmv(a.l2l[l - 1] + (size_t)(q * Sp + Op) * S + O + n, S, wsm, Pp));
         }
         continue;
       }
@@ -2981,6 +2978,15 @@ cudaError_t k_fused_prepare(pfmbem* h, bool* ok) {
   h->fz_grid32 = std::min(h->fz_tcb32 > 0 ? fused_grid<cplxf, true>(h->max_fiber, h->fz_treg32, h->fz_tcb32)
                                           : fused_grid<cplxf, false>(h->max_fiber, h->fz_treg32 + h->fz_tregL32, 0),
                           need);
+  {
+    // PFMBEM_FUSED_GRID caps both grids (a test of the products on few blocks,
+    // the group sizes of the batched launch; the cap is kept a multiple of 1)
+    static const char* fg = std::getenv("PFMBEM_FUSED_GRID");
+    if (fg && std::atoi(fg) > 0) {
+      h->fz_grid64 = std::min(h->fz_grid64, std::atoi(fg));
+      h->fz_grid32 = std::min(h->fz_grid32, std::atoi(fg));
+    }
+  }
   if (h->fz_grid64 <= 0 || h->fz_grid32 <= 0) return cudaSuccess;
   {
     // device-side GMRES steps: one block per SM (the steps are short; fewer
