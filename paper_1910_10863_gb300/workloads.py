@@ -236,6 +236,32 @@ def table3_square(ka2pi: float, f: float = 0.35, n: int = 256, c_water: float = 
                     centres=np.asarray(centres), radii=np.full(len(centres), r))
 
 
+def mercury_water_block(ka2pi: float, f: float = 0.35, ml: int = 4, n: int = 256, c_water: float = 1500.0,
+                        rows: int = 12, name: str | None = None) -> Workload:
+    """The mercury/water crystal of Sec. 4 (the last experiment): mercury cylinders in a
+    water matrix, square lattice of constant a = 0.5, M_L = ml columns, circles of
+    radius r = a sqrt(f / pi), n elements each, normal incidence, normalised frequency
+    ka/2pi.  k = omega / c_water (matrix) and k1 = omega / c_mercury (fibers);
+    varrho = rho_water / rho_mercury.  The crystal repeats along y with period 6a
+    (M_H = 6); the fundamental block is taken two periods tall (12 rows, H = 6a), which
+    describes the same crystal (at normal incidence the field is 6a-periodic, hence
+    also 12a-periodic) and keeps the block's width ml a within H for ml <= 12 (Wood
+    anomalies of the taller period: ka/2pi = n/12).  rows = 6 gives the one-period
+    block (ml <= 6)."""
+    a = 0.5
+    H = rows * a
+    if ml * a > H:
+        raise ValueError("block wider than its period")
+    k = 2.0 * math.pi * ka2pi / a
+    r = a * math.sqrt(f / math.pi)
+    centres = [((ix + 0.5) * a, (iy + 0.5) * a) for ix in range(ml) for iy in range(rows)]
+    nodes = np.concatenate([circle_nodes(c[0], c[1], r, n) for c in centres])
+    return Workload(name=name or f"mercury_water_ml{ml}_rows{rows}_f{f:g}_ka{ka2pi:g}", H=H, lattice=0, k=k,
+                    k1=k * c_water / C_MERCURY, rho_ratio=RHO_WATER / RHO_MERCURY, theta=0.0,
+                    nodes_per_fiber=np.full(len(centres), n, dtype=np.int32), nodes=nodes,
+                    centres=np.asarray(centres), radii=np.full(len(centres), r))
+
+
 def round_square_area(r: float = 1.0) -> float:
     """Area enclosed by the round-square curve of Sec. 4 at scale r: 23 pi r^2 / 2 (Sec. 4)."""
     return 23.0 * math.pi * r * r / 2.0

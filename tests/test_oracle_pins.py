@@ -190,3 +190,36 @@ def test_interaction_list_counts():
     assert len(tree.interaction_list(4, 7, 0)) == 27
     assert len(tree.interaction_list(4, 0, 7)) == 18
     assert all(m in (-1, 0, 1) for _, _, m in tree.interaction_list(4, 5, 15))
+
+
+def test_triangle_tree_geometry():
+    """The regular-triangle tree of Sec. 3.1 (Fig. 5): each cell of side 2 holds
+    exactly four cells of side 1 (its three corner children and the inverted
+    middle one), which cover its area; the circumradius is s / sqrt(3)."""
+    from collections import Counter
+    cells = [(i, j, up) for i in range(-4, 4) for j in range(-4, 4) for up in (True, False)]
+    kids = Counter(tree.triangle_parent(c) for c in cells)
+    inner = [p for p in kids if all(-1 <= x <= 0 for x in p[:2])]
+    assert inner and all(kids[p] == 4 for p in inner)
+    v = tree.triangle_vertices(0, 0, True, 1.0)
+    o = tree.triangle_centre(v)
+    assert all(abs(math.hypot(p[0] - o[0], p[1] - o[1]) - 1 / math.sqrt(3)) < 1e-14 for p in v)
+    assert tree.triangle_parent((0, 0, False)) == (0, 0, True)        # the middle child
+
+
+def test_table1_triangular_tree():
+    """Table 1, triangular tree columns.  L = 0: lambda 0.6663 is the worst of the
+    interaction list (the opposite-orientation sources whose centres lie sqrt(7/3)
+    sides away); gamma 0.4000 is that of the nearest same-orientation source of
+    the list (centres sqrt(3) sides apart).  L = 1: a source one level up, touching
+    the target's parent, and the parent's middle child as the target: gamma
+    0.7559 and lambda 0.6863."""
+    for D in [(0, 0, True), (0, 0, False)]:
+        lst = tree.triangle_interaction_list(D)
+        lam = max(tree.triangle_gamma_lambda(c, 1.0, D, 1.0)[1] for c in lst)
+        assert round(lam, 4) == 0.6663
+    assert (1, 1, True) in tree.triangle_interaction_list((0, 0, True))
+    g, _ = tree.triangle_gamma_lambda((1, 1, True), 1.0, (0, 0, True), 1.0)
+    assert round(g, 4) == 0.4000
+    g, lam = tree.triangle_gamma_lambda((1, 0, True), 2.0, (0, 0, False), 1.0)
+    assert (round(g, 4), round(lam, 4)) == (0.7559, 0.6863)
