@@ -124,6 +124,8 @@ typedef struct {
                              (tcgen05, BF16x3 split products accumulated in FP32) */
   int p32[16];            /* expansion order per level of the FP32 product (<= p) */
   int64_t m2l_pairs_level[16];  /* M2L translations per matvec at each level 0..depth */
+  int nroot;              /* root squares of side H in a row along x (1 unless the block is wider than H) */
+  int super_p;            /* with nroot > 1: order of the super root over the row (0 otherwise) */
 } pfmbem_plan_info;
 
 /* Create a solver for one fundamental block (paper Sec. 2-3).
@@ -133,7 +135,11 @@ typedef struct {
  *                     (outward normal = tangent turned clockwise, Sec. 2),
  *                     host or device, float64
  *   H                 period along y (paper H; "period L" elsewhere), > 0;
- *                     the block's extent along x must not exceed H
+ *                     a block wider than H along x (up to 4 H) is covered by a
+ *                     row of root squares of side H whose top operator couples
+ *                     them (explicit root-to-root M2L for the near images, a
+ *                     super root with the lattice sums for the far ones); such
+ *                     blocks need the default product options (EINVAL otherwise)
  *   lattice           informational (square / hexagon; the quadtree is square)
  *   k, k1             matrix and fiber wavenumbers (> 0), k = omega/c_matrix
  *   rho_ratio         varrho = rho_matrix / rho_fiber of eq. 6 (> 0)
@@ -212,8 +218,8 @@ pfmbem_status pfmbem_field(pfmbem_t h, const double* psi, int npts, const double
 
 /* Scattered field u^s (eq. 7) and its derivative du^s/dx1 at npts points
  * outside the fibers (either output may be NULL, not both): pts [npts][2]
- * float64, u and dudx1 complex [npts].  Points must lie within 0.7 H of the
- * block centre along x (PFMBEM_EINVAL otherwise). */
+ * float64, u and dudx1 complex [npts].  Points must lie within (nroot/2 + 0.2) H
+ * of the block centre along x, 0.7 H for one root (PFMBEM_EINVAL otherwise). */
 pfmbem_status pfmbem_field_dx1(pfmbem_t h, const double* psi, int npts, const double* pts, double* u,
                                double* dudx1);
 

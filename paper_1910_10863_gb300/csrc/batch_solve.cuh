@@ -530,7 +530,7 @@ cudaError_t k_batch_solve(int ninst, pfmbem* const* hs, const int* order, int GS
   for (int i = 0; i < ninst; ++i)
     if (!batch_eligible(hs[i])) return cudaErrorNotSupported;
   // groups large enough for the root's coefficients, one warp each
-  for (int i = 0; i < ninst; ++i) GS = std::max(GS, (hs[i]->lev[0].P + FW - 1) / FW);
+  for (int i = 0; i < ninst; ++i) GS = std::max(GS, (hs[i]->lev[0].nne * hs[i]->lev[0].P + FW - 1) / FW);
   size_t smem = 0;
   for (int i = 0; i < ninst; ++i) smem = std::max(smem, batch_smem(hs[i]));
   const void* fn = (const void*)batch_solve_kernel;

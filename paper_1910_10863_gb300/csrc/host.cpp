@@ -369,6 +369,18 @@ inline int morton(int ix, int iy, int D) {
   return (int)(spread_bits((unsigned)ix & m) | (spread_bits((unsigned)iy & m) << 1));
 }
 
+// Root squares of side H along x (at most kMaxRoots): box (ix, iy) of level l,
+// ix < nroot 2^l, is numbered root-major, root (ix >> l) first and the Morton code
+// inside it after, so that a box's children are 4 b .. 4 b + 3 and its parent b >> 2
+// as in one root, and the level's boxes of one root are consecutive.
+constexpr int kMaxRoots = 4;
+inline int box_id(int ix, int iy, int l) { return ((ix >> l) << (2 * l)) | morton(ix & ((1 << l) - 1), iy, l); }
+inline void box_xy(int b, int l, int* ix, int* iy) {
+  const unsigned m = (unsigned)b & ((1u << (2 * l)) - 1u);
+  *ix = ((b >> (2 * l)) << l) | (int)unspread_bits(m);
+  *iy = (int)unspread_bits(m >> 1);
+}
+
 // Gauss-Legendre thresholds: rule g meets tolerance tol for a source element
 // whose midpoint is q element lengths away when its Bernstein ellipse
 // parameter 2q + sqrt(4q^2 - 1) >= tol^(-1/(2g)); i.e. q >= (R + 1/R)/4.
@@ -650,12 +662,16 @@ struct M2LLists {
   int ntile = 0;
 };
 
-static void build_m2l_lists(const Level& L, int l, bool tc, M2LLists& o) {
-  const int nl = 1 << l, np = 1 << (l - 1);
+static void build_m2l_lists(const Level& L, int l, int nr, bool tc, M2LLists& o) {
+  const int nl = 1 << l, nlx = nr << l, np = nr << (l - 1);
   const int nne = (int)L.hne.size();
   // occupancy of the level's boxes on the (x, y) grid
-  std::vector<unsigned char> occ((size_t)nl * nl, 0);
-  for (int b : L.hne) occ[(size_t)unspread_bits((unsigned)b >> 1) * nl + unspread_bits((unsigned)b)] = 1;
+  std::vector<unsigned char> occ((size_t)nlx * nl, 0);
+  for (int b : L.hne) {
+    int bx, by;
+    box_xy(b, l, &bx, &by);
+    occ[(size_t)by * nlx + bx] = 1;
+  }
   std::vector<int>& ptr = o.ptr;
   std::vector<int>& src = o.src;
   std::vector<int>& off = o.off;
@@ -666,7 +682,8 @@ static void build_m2l_lists(const Level& L, int l, bool tc, M2LLists& o) {
   img.reserve((size_t)27 * nne);
   for (int ti = 0; ti < nne; ++ti) {
     const int b = L.hne[ti];
-    const int ix = (int)unspread_bits((unsigned)b), iy = (int)unspread_bits((unsigned)b >> 1);
+    int ix, iy;
+    box_xy(b, l, &ix, &iy);
     const int px = ix >> 1, py = iy >> 1;
     for (int pdx = -1; pdx <= 1; ++pdx) {
       const int qx = px + pdx;
@@ -679,8 +696,8 @@ static void build_m2l_lists(const Level& L, int l, bool tc, M2LLists& o) {
             const int dx = ix - sx, dy = iy - sy;
             if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1) continue;
             const int syw = sy & (nl - 1);            // nl is a power of two
-            if (!occ[(size_t)syw * nl + sx]) continue;
-            src.push_back(morton(sx, syw, l));
+            if (!occ[(size_t)syw * nlx + sx]) continue;
+            src.push_back(box_id(sx, syw, l));
             off.push_back((dx + 3) * 7 + (dy + 3));
             img.push_back((sy - syw) >> l);
           }
@@ -809,7 +826,13 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
     if (!(area > 0)) return fail(h, PFMBEM_EGEOM, "fiber " + std::to_string(i) + " is not counter-clockwise");
   }
-  if (xmax - xmin > H) return fail(h, PFMBEM_EGEOM, "block wider than the period H along x");
+  // a block wider than H along x takes a row of root squares of side H (Sec. 2
+  // allows any width L; the y-period H sets the root's side)
+  {
+    const int nr = std::max(1, (int)std::ceil((xmax - xmin) / H - 1e-12));
+    if (nr > kMaxRoots) return fail(h, PFMBEM_EGEOM, "block wider than 4 H along x");
+    h->nroot = nr;
+  }
   // fiber centre (mean of the nodes) and mean radius, for the learned warm start
   h->hfib_geo.assign(3 * (size_t)M, 0.0);
   for (int i = 0; i < M; ++i) {
@@ -831,8 +854,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   }
   if (0.5 * k * hmax > 4.0) return fail(h, PFMBEM_EINVAL, "elements longer than 8/k");
   // ---------------------------------------------------- root box and wrapping
-  h->x0 = 0.5 * (xmin + xmax) - 0.5 * H;
+  h->x0 = 0.5 * (xmin + xmax) - 0.5 * h->nroot * H;
   h->y0 = 0.5 * (ymin + ymax) - 0.5 * H;
+  const int NR = h->nroot;
   std::vector<int> m0(E);
   std::vector<double2> cw(E);
   for (int e = 0; e < E; ++e) {
@@ -870,19 +894,19 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     // (a value below 0 truncates to 0 like its floor clamps to 0)
     const double r10 = 1024.0 / H;
     for (int e = 0; e < E; ++e) {
-      const int ix = std::min(std::max((int)((cw[e].x - h->x0) * r10), 0), 1023);
+      const int ix = std::min(std::max((int)((cw[e].x - h->x0) * r10), 0), 1024 * NR - 1);
       const int iy = std::min(std::max((int)((cw[e].y - h->y0) * r10), 0), 1023);
-      m10[e] = morton(ix, iy, 10);
+      m10[e] = box_id(ix, iy, 10);
     }
   }
   // box occupancy at depth 8 in one pass, then at every coarser depth by
   // summing the four Morton-consecutive children: cnt[l][b], l <= 8
   constexpr int DH = 8;
   std::vector<std::vector<int>> cnt(DH + 1);
-  cnt[DH].assign((size_t)1 << (2 * DH), 0);
+  cnt[DH].assign((size_t)NR << (2 * DH), 0);
   for (int e = 0; e < E; ++e) cnt[DH][m10[e] >> (2 * (10 - DH))]++;
   for (int l = DH - 1; l >= 0; --l) {
-    cnt[l].resize((size_t)1 << (2 * l));
+    cnt[l].resize((size_t)NR << (2 * l));
     const int* c1 = cnt[l + 1].data();
     for (size_t b = 0; b < cnt[l].size(); ++b) cnt[l][b] = c1[4 * b] + c1[4 * b + 1] + c1[4 * b + 2] + c1[4 * b + 3];
   }
@@ -892,7 +916,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       if (D <= DH) {
         for (int v : cnt[D]) mx = std::max(mx, v);
       } else {
-        std::vector<int> c((size_t)1 << (2 * D), 0);
+        std::vector<int> c((size_t)NR << (2 * D), 0);
         for (int e = 0; e < E; ++e) mx = std::max(mx, ++c[m10[e] >> (2 * (10 - D))]);
       }
       if (mx <= leaf_max) break;
@@ -906,12 +930,12 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   if (D > DH) {
     cnt.resize(D + 1);
     for (int l = DH + 1; l <= D; ++l) {
-      cnt[l].assign((size_t)1 << (2 * l), 0);
+      cnt[l].assign((size_t)NR << (2 * l), 0);
       for (int e = 0; e < E; ++e) cnt[l][m10[e] >> (2 * (10 - l))]++;
     }
   }
   {
-    std::vector<int> start(((size_t)1 << (2 * D)) + 1, 0);
+    std::vector<int> start(((size_t)NR << (2 * D)) + 1, 0);
     for (size_t b = 0; b + 1 < start.size(); ++b) start[b + 1] = start[b] + cnt[D][b];
     for (int e = 0; e < E; ++e) perm[start[key[e]]++] = e;
   }
@@ -919,7 +943,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // ---------------------------------------------------- levels
   for (int l = 0; l <= D; ++l) {
     Level& L = h->lev[l];
-    L.nbox = 1 << (2 * l);
+    L.nbox = NR << (2 * l);
     L.d = H / (1 << l);
     L.hbegin.resize(L.nbox);
     L.hend.resize(L.nbox);
@@ -962,6 +986,25 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     }
     h->info.p[l] = p;
   }
+  if (NR > 1) {
+    // the super root over the row: its centre C, radius R_s (the half-diagonal of
+    // the nr H x H row), the first image row m0 it takes (m0 H >= 3 R_s: the super
+    // M2L's ratio 2 R_s / (m0 H) stays at or below 2/3) and its order (the levels'
+    // rule for a box of diagonal 2 R_s)
+    if (h->opt.launch != 0 || h->opt.near_mode != 0 || h->opt.m2l_mode == 2)
+      return fail(h, PFMBEM_EINVAL, "blocks wider than H need the cached single-launch product (default options)");
+    h->wide_cx = h->x0 + 0.5 * NR * H;
+    h->wide_cy = h->y0 + 0.5 * H;
+    h->wide_rs = 0.5 * H * std::sqrt((double)NR * NR + 1.0);
+    h->wide_m0 = (int)std::ceil(3.0 * h->wide_rs / H - 1e-12);
+    const double x = 2.0 * k * h->wide_rs;
+    // at least the order at which the super M2L's ratio 2 R_s / (m0 H), to that
+    // power, falls to 1e-11
+    const int pratio = (int)std::ceil(std::log(1e-11) / std::log(2.0 * h->wide_rs / (h->wide_m0 * H)));
+    const int ps = std::max({(int)std::ceil(x + 1.8 * std::pow(10.0, 2.0 / 3.0) * std::cbrt(x)), h->lev[0].p, pratio});
+    if (ps > PF_PMAX) return fail(h, PFMBEM_EINVAL, "block too wide for this frequency (super-root order above 128)");
+    h->wide_ps = ps;
+  }
   mark("depth, sort, levels");
   // the M2L lists depend on the tree alone: a worker thread builds them while
   // the set-up below goes on (they are uploaded where the second stream starts)
@@ -976,7 +1019,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     const bool fusable = h->opt.near_mode == 0 && h->max_fiber <= 1024 && h->opt.launch == 0;
     for (int l = 1; l <= D; ++l) {
       Level& L = h->lev[l];
-      const int pu = D >= 3 ? std::min(L.p, std::max(1, L.p32)) : L.p;
+      const int pu = D >= 3 && NR == 1 ? std::min(L.p, std::max(1, L.p32)) : L.p;
       L.tc_fused = fusable && h->opt.m2l_mode != 1 && tc_kpad(2 * pu + 1) <= 80 &&
                    (h->opt.m2l_mode == 2 ? L.nne > 0 : L.nne >= tc_min_boxes);
     }
@@ -984,10 +1027,10 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   std::vector<M2LLists> m2l(D + 1);
   std::future<void> m2l_lists = std::async(std::launch::async, [h, D, &m2l]() {
     for (int l = 1; l <= D; ++l)
-      build_m2l_lists(h->lev[l], l, h->opt.m2l_mode == 2 || h->lev[l].tc_fused, m2l[l]);
+      build_m2l_lists(h->lev[l], l, h->nroot, h->opt.m2l_mode == 2 || h->lev[l].tc_fused, m2l[l]);
   });
   // ---------------------------------------------------- lists
-  const int nD = 1 << D;
+  const int nD = 1 << D, nDx = NR << D;
   std::vector<int64_t> nc_base;
   std::vector<int> nc_sbase(1, 0);
   std::vector<int> nl_ptr(1, 0), nl_src, nl_img;      // near lists of the leaves: source leaf, image m
@@ -997,15 +1040,15 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     std::vector<int>& src = nl_src;
     std::vector<int>& img = nl_img;
     for (int b : Lf.hne) {
-      int ix = 0, iy = 0;
-      for (int bb = 0; bb < D; ++bb) { ix |= ((b >> (2 * bb)) & 1) << bb; iy |= ((b >> (2 * bb + 1)) & 1) << bb; }
+      int ix, iy;
+      box_xy(b, D, &ix, &iy);
       for (int dx = -1; dx <= 1; ++dx)
         for (int dy = -1; dy <= 1; ++dy) {
           int sx = ix + dx, sy = iy + dy;
-          if (sx < 0 || sx >= nD) continue;
+          if (sx < 0 || sx >= nDx) continue;
           int syw = ((sy % nD) + nD) % nD;
           int m = (sy - syw) / nD;
-          int sb = morton(sx, syw, D);
+          int sb = box_id(sx, syw, D);
           if (Lf.hend[sb] > Lf.hbegin[sb]) { src.push_back(sb); img.push_back(m); }
         }
       ptr.push_back((int)src.size());
@@ -1139,6 +1182,42 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     pfmbem_status st = on_aux(h, 0, [&]() -> pfmbem_status {
       Level& R = h->lev[0];
       const int p0 = R.p, P0 = R.P, jmax = 2 * p0;
+      if (h->nroot > 1) {
+        // a row of root squares: the operator between all roots (k_wide_top)
+        const int nr = h->nroot, ps = h->wide_ps, Ps = 2 * ps + 1;
+        h->root = dalloc<cplx>(h, (size_t)nr * P0 * nr * P0);
+        h->rootf = dalloc<cplxf>(h, (size_t)P0 * P0);
+        double2* dv = dalloc<double2>(h, 2 * nr);
+        h->wide_w = dalloc<double>(h, Ps);
+        h->wide_A = dalloc<cplx>(h, (size_t)nr * P0 * Ps);
+        h->wide_B = dalloc<cplx>(h, (size_t)nr * Ps * P0);
+        h->wide_Rs = dalloc<cplx>(h, (size_t)Ps * Ps);
+        h->wide_ML = dalloc<cplx>(h, 2 * (size_t)Ps);
+        cplx* S = dalloc<cplx>(h, (size_t)2 * ps + 1);
+        cplx* X = dalloc<cplx>(h, (size_t)nr * Ps * P0);
+        if (!h->root || !h->rootf || !dv || !h->wide_w || !h->wide_A || !h->wide_B || !h->wide_Rs || !h->wide_ML ||
+            !S || !X)
+          return fail(h, PFMBEM_ENOMEM, "device allocation failed (root row)");
+        std::vector<double2> hv(2 * nr);
+        for (int i = 0; i < nr; ++i) {
+          const double cx = h->x0 + (i + 0.5) * H, cy = h->y0 + 0.5 * H;
+          hv[i] = double2{cx, cy};
+          hv[nr + i] = double2{cx - h->wide_cx, cy - h->wide_cy};
+        }
+        // the super root's weights w_n = sigma^|n| / |n|!, sigma = k R_s, as the levels'
+        std::vector<double> w(Ps, 1.0);
+        double wn = 1.0;
+        for (int n = 1; n <= ps; ++n) {
+          wn *= k * h->wide_rs / n;
+          w[ps + n] = w[ps - n] = wn;
+        }
+        // (pageable sources: the copies have left the vectors when the calls return)
+        CK(cudaMemcpyAsync(dv, hv.data(), sizeof(double2) * 2 * nr, cudaMemcpyHostToDevice, h->stream));
+        CK(cudaMemcpyAsync(h->wide_w, w.data(), sizeof(double) * Ps, cudaMemcpyHostToDevice, h->stream));
+        CK(k_wide_top(h, dv, S, X));
+        trace(h, h->stream, "aux0: root row operators done");
+        return PFMBEM_OK;
+      }
       cplx* Sd = dalloc<cplx>(h, jmax + 1);
       h->root = dalloc<cplx>(h, (size_t)P0 * P0);
       h->rootf = dalloc<cplxf>(h, (size_t)P0 * P0);
@@ -1204,7 +1283,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
           if (!L.tc_B) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
         }
         if (L.tc_fused) {
-          const int pu = D >= 3 ? std::min(L.p, std::max(1, L.p32)) : L.p;
+          const int pu = D >= 3 && NR == 1 ? std::min(L.p, std::max(1, L.p32)) : L.p;
           const int kp = tc_kpad(2 * pu + 1);
           L.tc_Bf = dalloc<uint16_t>(h, (size_t)49 * 3 * kp * kp);
           if (!L.tc_Bf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (tensor-core operators)");
@@ -1480,10 +1559,11 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   if (cache && h->opt.launch == 0) {
     // top operators of the single-launch product, on the second stream once the
     // root operator (first set-up stream) and the M2M tables are there
-    h->rootc = dalloc<cplx>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
-    h->rootcf = dalloc<cplxf>(h, (size_t)h->lev[0].P * 4 * h->lev[1].P);
+    const size_t nrc = (size_t)NR * h->lev[0].P * 4 * NR * h->lev[1].P;   // [4 nr P1][nr P0]
+    h->rootc = dalloc<cplx>(h, nrc);
+    h->rootcf = dalloc<cplxf>(h, nrc);
     if (!h->rootc || !h->rootcf) return fail(h, PFMBEM_ENOMEM, "device allocation failed (root operator)");
-    if (D >= 3) {
+    if (D >= 3 && NR == 1) {
       const size_t P1 = h->lev[1].P, P3 = h->lev[3].P;
       h->m2m31 = dalloc<cplx>(h, 16 * P3 * P1);
       h->m2m31f = dalloc<cplxf>(h, 16 * P3 * P1);
@@ -1511,7 +1591,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   for (int l = 1; l <= D; ++l) {
     Level& L = h->lev[l];
     if (L.tc_B) CK(k_tc_build_operator(h, l));
-    if (L.tc_Bf) CK(k_tc_build_operator_fused(h, l, 2 * (D >= 3 ? std::min(L.p, std::max(1, L.p32)) : L.p) + 1));
+    if (L.tc_Bf)
+      CK(k_tc_build_operator_fused(h, l, 2 * (D >= 3 && NR == 1 ? std::min(L.p, std::max(1, L.p32)) : L.p) + 1));
   }
   if (cache) {
     // single-launch matvec unless the tensor-core M2L (its own kernel) is on
@@ -1522,6 +1603,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
       bool ok = false;
       if (!h->rootc) return fail(h, PFMBEM_ENOMEM, "single-launch product without its top operators");
       CK(k_fused_prepare(h, &ok));
+      if (!ok && NR > 1) return fail(h, PFMBEM_EINVAL, "blocks wider than H need the single-launch product");
       if (ok) {
         std::vector<int> sli(E);
         {
@@ -1610,6 +1692,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   h->info.lattice_q = h->lattice_q;
   h->info.root_x0 = h->x0;
   h->info.root_y0 = h->y0;
+  h->info.nroot = h->nroot;
+  h->info.super_p = h->nroot > 1 ? h->wide_ps : 0;
   h->setup_ms = now_ms() - t0;
   h->info.setup_ms = h->setup_ms;
   return PFMBEM_OK;
@@ -2592,12 +2676,13 @@ pfmbem_status field_points(pfmbem* h, const double* psi, int npts, const double*
   std::vector<double> hp(2 * (size_t)npts);
   if (is_device_ptr(pts)) CK(cudaMemcpy(hp.data(), pts, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost));
   else std::memcpy(hp.data(), pts, sizeof(double) * hp.size());
-  const double ox = h->x0 + 0.5 * h->H;
+  const double ox = h->x0 + 0.5 * h->nroot * h->H;
   for (int i = 0; i < npts; ++i) {
     if (!std::isfinite(hp[2 * i]) || !std::isfinite(hp[2 * i + 1])) return fail(h, PFMBEM_EINVAL, "non-finite point");
     // the root local expansion of the images |m| >= 2 converges for |x - O| + H/sqrt(2) < 2H
-    if (std::fabs(hp[2 * i] - ox) > 1.2 * h->H - 0.5 * h->H)
-      return fail(h, PFMBEM_EINVAL, "field point too far from the block along x (|x - centre| > 0.7 H)");
+    // (a row of roots: the super root's, of the images |m| >= m0, for |x - C| < 2 R_s)
+    if (std::fabs(hp[2 * i] - ox) > (0.5 * h->nroot + 0.2) * h->H)
+      return fail(h, PFMBEM_EINVAL, "field point too far from the block along x (|x - centre| > (nroot/2 + 0.2) H)");
   }
   const cplx* psid;
   pfmbem_status st = stage_input(h, psi, n, h->stage_in, &psid);

@@ -152,6 +152,7 @@ struct pfmbem {
   std::string err;
   // plan
   int D = 0;
+  int nroot = 1;                 // root squares of side H in a row along x (block width up to nroot H)
   double x0 = 0, y0 = 0;
   Level lev[PF_MAXLEVEL + 1];
   int g_far = 4, g_far_f = 2;    // Gauss nodes per element in P2M (FP64 / FP32)
@@ -290,7 +291,16 @@ struct pfmbem {
   cplx* Un = nullptr;            // [E][2] near-field part of (U', dU'), FP64 and FP32
   cplxf* Unf = nullptr;
   unsigned long long* fz_stamp = nullptr;   // [32] stage end times (diagnostic)
-  cplx* root = nullptr;          // [P0][P0] periodic root translation
+  cplx* root = nullptr;          // [P0][P0] periodic root translation ([nroot P0]^2 with several roots)
+  // several roots: the super root (centre of the row, radius wide_rs, order
+  // wide_ps) and the image row m0 from which its lattice sums take the images
+  int wide_ps = 0, wide_m0 = 0;
+  double wide_cx = 0, wide_cy = 0, wide_rs = 0;
+  double* wide_w = nullptr;      // [Ps] weights of the super root's expansions
+  cplx* wide_A = nullptr;        // [nroot][P0][Ps] M2M root j -> super root
+  cplx* wide_B = nullptr;        // [nroot][Ps][P0] L2L super root -> root i
+  cplx* wide_Rs = nullptr;       // [Ps][Ps] lattice-sum translation of the super root
+  cplx* wide_ML = nullptr;       // [2][Ps] super multipole and local (field)
   cplxf* rootf = nullptr;
   cplx* rootc = nullptr;         // [4 P1][P0] root translation times the level-1 -> root M2M
   cplxf* rootcf = nullptr;
@@ -409,7 +419,13 @@ struct TableLevels {
 };
 cudaError_t k_tables(pfmbem* h, const TableLevels& tl, cudaStream_t st);
 cudaError_t k_root_operator(pfmbem* h, int p0, const double* w0, const cplx* S);
-cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev);
+cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev, int mlo = 2);
+// Blocks wider than H (a row of nroot root squares): the operator from every root's
+// multipole to every root's local expansion, the images beyond the tree's lists
+// included, into h->root ([nroot P0][nroot P0]), and the super root's operators
+// kept for the field.
+cudaError_t k_wide_top(pfmbem* h, const double2* dv, cplx* S, cplx* X);
+cudaError_t k_wide_local(pfmbem* h);
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_rhs(pfmbem* h, cplx* B);
 cudaError_t k_field(pfmbem* h, const cplx* psi, int npts, const double2* pts, cplx* u, cplx* dudx1);

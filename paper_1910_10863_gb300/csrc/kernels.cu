@@ -72,8 +72,10 @@ __device__ __forceinline__ cplx warp_sum(cplx v) {
   return v;
 }
 __device__ __forceinline__ cplx ipow_phase(cplx alpha, int m) {
-  // alpha^m for m in {-1, 0, 1}; |alpha| = 1, so alpha^{-1} = conj(alpha)
-  return m == 0 ? cplx{1, 0} : (m > 0 ? alpha : conj(alpha));
+  // alpha^m for any image m by |m| products; |alpha| = 1, so alpha^{-1} = conj(alpha)
+  cplx r{1, 0};
+  for (int i = 0; i < (m < 0 ? -m : m); ++i) r = r * alpha;
+  return m < 0 ? conj(r) : r;
 }
 
 // ---------------------------------------------------------------- profiling
@@ -245,7 +247,7 @@ __global__ void root_operator_kernel(int p0, const double* __restrict__ w, const
     const cplx v{sc * sj.re, sc * sj.im};
     if (!isfinite(v.re) || !isfinite(v.im)) atomicExch(bad, 1);
     R[t] = v;
-    Rf[t] = to_f(v);
+    if (Rf) Rf[t] = to_f(v);
   }
 }
 
@@ -254,6 +256,161 @@ cudaError_t k_root_operator(pfmbem* h, int p0, const double* w0, const cplx* S) 
   prof_begin(h, PH_SETUP);
   root_operator_kernel<<<(P * P + 255) / 256, 256, 0, h->stream>>>(p0, w0, S, h->root, h->rootf, h->tab_err);
   prof_end(h, PH_SETUP);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- blocks wider than H
+// A row of nr root squares (centres c_i, level-0 order p0) is closed at the top by a
+// super root: the centre C of the row, radius R_s, order ps.  The images |m| >= m0 of
+// the whole row reach every root through C: M2M from each root to C, the lattice
+// sums of Sec. 3.3 taken from image m0 on, L2L from C back to each root.  The images
+// |m| < m0 of the root pairs that are not neighbours (|i - j| > 1 or |m| > 1) go by
+// explicit root-to-root M2L; the neighbours are the tree lists' (Sec. 3.1).  With
+// the translation tables' conventions (A[child m][parent n], B[parent m][child n],
+// T[target a][source n] = w_a H^+_{n-a}(k v) w_n, v = target - source centre):
+//   TOP[(i,a)][(j,n)] = sum_c B_i[c][a] sum_b R_s[c][b] A_j[n][b]
+//                      + sum_{explicit m} alpha^m w_a H^+_{n-a}(k (c_i - c_j - m h)) w_n.
+// One root (nr = 1, m0 = 2, C = c_0) gives TOP = R.
+
+// A_j and B_j of root j = blockIdx.x, v = c_j - C.
+__global__ void wide_shift_kernel(int p0, int ps, double k, const double2* __restrict__ v, const double* __restrict__ w0,
+                                  const double* __restrict__ ws, cplx* __restrict__ A, cplx* __restrict__ B) {
+  const int j = blockIdx.x, P0 = 2 * p0 + 1, Ps = 2 * ps + 1;
+  __shared__ double J[2 * PF_PMAX + 2], Y[2 * PF_PMAX + 2];
+  const double vx = v[j].x, vy = v[j].y;
+  const double r = sqrt(vx * vx + vy * vy), th = r > 0 ? atan2(vy, vx) : 0.0;
+  bessel_jy_block(k * r, p0 + ps, J, Y);          // r = 0 (a root at C): J_n = delta_n0; Y is not used
+  cplx* Aj = A + (size_t)j * P0 * Ps;
+  cplx* Bj = B + (size_t)j * Ps * P0;
+  for (int t = threadIdx.x; t < P0 * Ps; t += blockDim.x) {
+    {
+      const int m = t / Ps - p0, n = t % Ps - ps;      // A: [m + p0 (root)][n + ps (super)]
+      const int jj = n - m, aj = abs(jj);
+      const double Jj = (jj < 0 && (aj & 1)) ? -J[aj] : J[aj];
+      const double sc = w0[m + p0] / ws[n + ps];
+      double sn, cs;
+      sincos(jj * th, &sn, &cs);
+      Aj[t] = cplx{sc * Jj * cs, -sc * Jj * sn};
+    }
+    {
+      const int m = t / P0 - ps, n = t % P0 - p0;      // B: [m + ps (super)][n + p0 (root)]
+      const int jj = m - n, aj = abs(jj);
+      const double Jj = (jj < 0 && (aj & 1)) ? -J[aj] : J[aj];
+      const double sc = w0[n + p0] / ws[m + ps];
+      double sn, cs;
+      sincos(jj * th, &sn, &cs);
+      Bj[t] = cplx{sc * Jj * cs, sc * Jj * sn};
+    }
+  }
+}
+
+// X_j[c][n] = sum_b R_s[c][b] A_j[n][b], one thread per (j, c, n).
+__global__ void wide_x_kernel(int nr, int P0, int Ps, const cplx* __restrict__ Rs, const cplx* __restrict__ A,
+                              cplx* __restrict__ X) {
+  const size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)nr * Ps * P0) return;
+  const int j = (int)(t / ((size_t)Ps * P0)), c = (int)(t / P0 % Ps), n = (int)(t % P0);
+  const cplx* Ar = A + ((size_t)j * P0 + n) * Ps;
+  const cplx* Rr = Rs + (size_t)c * Ps;
+  cplx acc{0, 0};
+  for (int b = 0; b < Ps; ++b) acc += Rr[b] * Ar[b];
+  X[t] = acc;
+}
+
+// TOP tile (i, j) = blockIdx.x / nr, blockIdx.x % nr.
+__global__ void wide_top_kernel(int nr, int p0, int Ps, int m0, double k, double H, cplx alpha,
+                                const double2* __restrict__ ctr, const double* __restrict__ w0,
+                                const cplx* __restrict__ B, const cplx* __restrict__ X, cplx* __restrict__ TOP,
+                                int* __restrict__ bad) {
+  const int i = blockIdx.x / nr, j = blockIdx.x % nr, P0 = 2 * p0 + 1, RS = nr * P0;
+  const cplx* Bi = B + (size_t)i * Ps * P0;
+  const cplx* Xj = X + (size_t)j * Ps * P0;
+  for (int t = threadIdx.x; t < P0 * P0; t += blockDim.x) {
+    const int a = t / P0, n = t % P0;
+    cplx acc{0, 0};
+    for (int c = 0; c < Ps; ++c) acc += Bi[(size_t)c * P0 + a] * Xj[(size_t)c * P0 + n];
+    TOP[(size_t)(i * P0 + a) * RS + j * P0 + n] = acc;
+  }
+  __shared__ double J[4 * PF_PMAX + 2], Y[4 * PF_PMAX + 2];
+  __shared__ cplx hv[4 * PF_PMAX + 1];
+  for (int m = -(m0 - 1); m <= m0 - 1; ++m) {
+    if (abs(i - j) <= 1 && abs(m) <= 1) continue;      // neighbours: the tree's lists
+    const double vx = ctr[i].x - ctr[j].x, vy = ctr[i].y - ctr[j].y - m * H;
+    const double r = sqrt(vx * vx + vy * vy), th = atan2(vy, vx);
+    __syncthreads();
+    bessel_jy_block(k * r, 2 * p0, J, Y);
+    for (int q = threadIdx.x - 2 * p0; q <= 2 * p0; q += blockDim.x) {
+      const int aq = abs(q);
+      const double sg = (q < 0 && (aq & 1)) ? -1.0 : 1.0;
+      double sn, cs;
+      sincos(q * th, &sn, &cs);
+      const double hr = sg * J[aq], hi = sg * Y[aq];
+      hv[q + 2 * p0] = cplx{hr * cs - hi * sn, hr * sn + hi * cs};
+    }
+    __syncthreads();
+    const cplx am = ipow_phase(alpha, m);
+    for (int t = threadIdx.x; t < P0 * P0; t += blockDim.x) {
+      const int a = t / P0, n = t % P0;
+      const cplx h = am * hv[n - a + 2 * p0];
+      const double sc = w0[a] * w0[n];
+      cplx* o = TOP + (size_t)(i * P0 + a) * RS + j * P0 + n;
+      *o = *o + cplx{sc * h.re, sc * h.im};
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < P0 * P0; t += blockDim.x) {
+    const cplx v = TOP[(size_t)(i * P0 + t / P0) * RS + j * P0 + t % P0];
+    if (!isfinite(v.re) || !isfinite(v.im)) atomicExch(bad, 1);
+  }
+}
+
+// The super root's expansions for the field: M_C = sum_j A_j^T M_j over the
+// non-empty roots, L_C = R_s M_C.  One block.
+__global__ void wide_local_kernel(int nne0, const int* __restrict__ ne0, int P0, int Ps, const cplx* __restrict__ A,
+                                  const cplx* __restrict__ Rs, const cplx* __restrict__ M0, cplx* __restrict__ ML) {
+  cplx* Ms = ML;
+  cplx* Ls = ML + Ps;
+  for (int b = threadIdx.x; b < Ps; b += blockDim.x) {
+    cplx acc{0, 0};
+    for (int r = 0; r < nne0; ++r) {
+      const int j = ne0[r];
+      const cplx* Aj = A + (size_t)j * P0 * Ps;
+      for (int n = 0; n < P0; ++n) acc += Aj[(size_t)n * Ps + b] * M0[(size_t)j * P0 + n];
+    }
+    Ms[b] = acc;
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < Ps; c += blockDim.x) {
+    cplx acc{0, 0};
+    for (int b = 0; b < Ps; ++b) acc += Rs[(size_t)c * Ps + b] * Ms[b];
+    Ls[c] = acc;
+  }
+}
+
+// dv: [2 nr] device: the roots' centres, then their shifts c_j - C; S [2 ps + 1] and
+// X [nr][Ps][P0] device scratch; the super root's weights, A, B, R_s and the
+// expansions' buffer are the handle's (allocated by the caller).
+cudaError_t k_wide_top(pfmbem* h, const double2* dv, cplx* S, cplx* X) {
+  const int nr = h->nroot, p0 = h->lev[0].p, P0 = 2 * p0 + 1, ps = h->wide_ps, Ps = 2 * ps + 1;
+  cudaStream_t st = h->stream;
+  prof_begin(h, PH_SETUP);
+  // lattice sums of the super root from image m0 on
+  cudaError_t e = k_lattice_sums(h, 2 * ps, std::max(h->lattice_q, h->wide_m0 + 4), S, h->wide_m0);
+  if (e != cudaSuccess) return e;
+  root_operator_kernel<<<(Ps * Ps + 255) / 256, 256, 0, st>>>(ps, h->wide_w, S, h->wide_Rs, nullptr, h->tab_err);
+  wide_shift_kernel<<<nr, 256, 0, st>>>(p0, ps, h->k, dv + nr, h->lev[0].w_dev, h->wide_w, h->wide_A, h->wide_B);
+  const size_t nx = (size_t)nr * Ps * P0;
+  wide_x_kernel<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(nr, P0, Ps, h->wide_Rs, h->wide_A, X);
+  wide_top_kernel<<<nr * nr, 256, 0, st>>>(nr, p0, Ps, h->wide_m0, h->k, h->H, h->alpha, dv, h->lev[0].w_dev,
+                                           h->wide_B, X, h->root, h->tab_err);
+  prof_end(h, PH_SETUP);
+  return cudaGetLastError();
+}
+
+cudaError_t k_wide_local(pfmbem* h) {
+  const Level& r = h->lev[0];
+  const int Ps = 2 * h->wide_ps + 1;
+  wide_local_kernel<<<1, 256, 0, h->stream>>>(r.nne, r.ne, r.P, Ps, h->wide_A, h->wide_Rs, r.M, h->wide_ML);
   return cudaGetLastError();
 }
 
@@ -315,7 +472,7 @@ cudaError_t k_self_terms(pfmbem* h) {
 // geometrically graded panels [V 2^-(P-1-i)...], given by the host.
 #define LS_PANELS 12
 __global__ void lattice_sum_kernel(int jmax, int q, double k, double H, double beta, double V,
-                                   cplx* __restrict__ out) {
+                                   cplx* __restrict__ out, int mlo = 2) {
   const int j = blockIdx.x;
   __shared__ double red[2][256];
   cplx acc{0, 0};
@@ -352,8 +509,8 @@ __global__ void lattice_sum_kernel(int jmax, int q, double k, double H, double b
     double n = (double)j;
     acc += cexp_d(n * l1 + lbp) + cexp_d(n * l2 + lbp) + cexp_d(n * l3 + lbm) + cexp_d(n * l4 + lbm);
   }
-  // direct rows 2 <= |m| <= q
-  for (int m = 2 + threadIdx.x; m <= q; m += blockDim.x) {
+  // direct rows mlo <= |m| <= q (mlo = 2: every image beyond the adjacent ones)
+  for (int m = mlo + threadIdx.x; m <= q; m += blockDim.x) {
     double x = k * m * H;
     double Jv[2 * PF_PMAX + 2];
     bessel_j_array(x, j, Jv);
@@ -414,10 +571,10 @@ static double lattice_vmax(int jmax, int q, double k, double H) {
   return V;
 }
 
-cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev) {
+cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev, int mlo) {
   double V = lattice_vmax(jmax, q, h->k, h->H);
   prof_begin(h, PH_SETUP);
-  lattice_sum_kernel<<<jmax + 1, 256, 0, h->stream>>>(jmax, q, h->k, h->H, h->beta, V, out_dev);
+  lattice_sum_kernel<<<jmax + 1, 256, 0, h->stream>>>(jmax, q, h->k, h->H, h->beta, V, out_dev, mlo);
   prof_end(h, PH_SETUP);
   return cudaGetLastError();
 }
@@ -626,7 +783,7 @@ __global__ void p2m_f64_kernel(const int* __restrict__ ne, const int* __restrict
   for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) acc[i] = 0.0;
   __syncthreads();
   // box centre from the Morton code
-  int ix = 0, iy = 0;
+  int ix = (box >> (2 * D)) << D, iy = 0;       // root squares in a row along x, root-major
   for (int b = 0; b < D; ++b) {
     ix |= ((box >> (2 * b)) & 1) << b;
     iy |= ((box >> (2 * b + 1)) & 1) << b;
@@ -751,7 +908,7 @@ __global__ void l2p_f64_kernel(const int* __restrict__ ne, const int* __restrict
   __shared__ cplx sl[PF_NCOEF];
   for (int i = threadIdx.x; i < P; i += blockDim.x) sl[i] = (1.0 / wgt[i]) * L[(size_t)box * P + i];
   __syncthreads();
-  int ix = 0, iy = 0;
+  int ix = (box >> (2 * D)) << D, iy = 0;       // root squares in a row along x, root-major
   for (int b = 0; b < D; ++b) {
     ix |= ((box >> (2 * b)) & 1) << b;
     iy |= ((box >> (2 * b + 1)) & 1) << b;
@@ -1408,7 +1565,7 @@ cudaError_t k_build_caches(pfmbem* h, cudaEvent_t ktab_done) {
 
 // ------------------------------------------------------------ cached P2M / L2P
 __device__ __forceinline__ void morton_centre(int box, int D, double d, double x0, double y0, double& ox, double& oy) {
-  int ix = 0, iy = 0;
+  int ix = (box >> (2 * D)) << D, iy = 0;       // root squares in a row along x, root-major
   for (int b = 0; b < D; ++b) {
     ix |= ((box >> (2 * b)) & 1) << b;
     iy |= ((box >> (2 * b + 1)) & 1) << b;
@@ -1991,6 +2148,13 @@ static void upward_f64(pfmbem* h, const cplx* x) {
     prof_end(h, PH_M2M);
   }
   cplx alpha = h->alpha;
+  if (h->nroot > 1) {
+    // a row of roots: the super root's local expansion of the images |m| >= m0
+    prof_begin(h, PH_LOCAL);
+    k_wide_local(h);
+    prof_end(h, PH_LOCAL);
+    return;
+  }
   {
     Level& r = h->lev[0];
     prof_begin(h, PH_LOCAL);
@@ -2213,8 +2377,10 @@ cudaError_t k_sub(pfmbem* h, const cplx* a, const cplx* b, cplx* out, int n) {
 // double-layer integrals); images |m| >= 2 through the root local expansion
 // sum_n c_n J_n(kr) e^{i n theta}, c_n = L_n / w_n, whose x1-derivative is
 // (k/2) sum_m J_m(kr) e^{i m theta} (c_{m+1} - c_{m-1}).  One warp per point.
+// With a row of roots the direct images are |m| <= mdir = m0 - 1 and the local
+// expansion is the super root's (centre (ox, oy)); one root: mdir = 1, the root's.
 __global__ void field_kernel(int npts, const double2* __restrict__ pts, int E, double k, double eta, double H,
-                             double x0, double y0, cplx alpha, const double2* __restrict__ sc,
+                             double ox, double oy, double y0, int mdir, cplx alpha, const double2* __restrict__ sc,
                              const double2* __restrict__ st, const double2* __restrict__ snu,
                              const double* __restrict__ sh, const cplx* __restrict__ dens, int p0,
                              const double* __restrict__ w0, const cplx* __restrict__ L0, cplx* __restrict__ u,
@@ -2227,8 +2393,9 @@ __global__ void field_kernel(int npts, const double2* __restrict__ pts, int E, d
   x.y -= mp * H;
   const double2 nx{1.0, 0.0};
   cplx acc{0, 0}, dacc{0, 0};
-  for (int t = lane; t < 3 * E; t += 32) {
-    const int f = t / 3, m = t % 3 - 1;
+  const int nim = 2 * mdir + 1;
+  for (int t = lane; t < nim * E; t += 32) {
+    const int f = t / nim, m = t % nim - mdir;
     double2 c = sc[f];
     c.y += m * H;
     const double hh = sh[f];
@@ -2243,7 +2410,6 @@ __global__ void field_kernel(int npts, const double2* __restrict__ pts, int E, d
   acc = warp_sum(acc);
   dacc = warp_sum(dacc);
   if (lane == 0) {
-    const double ox = x0 + 0.5 * H, oy = y0 + 0.5 * H;
     const double vx = x.x - ox, vy = x.y - oy;
     const double r = sqrt(vx * vx + vy * vy);
     cplx z = r > 0 ? cplx{vx / r, vy / r} : cplx{1, 0};
@@ -2283,9 +2449,15 @@ cudaError_t k_field(pfmbem* h, const cplx* psi, int npts, const double2* pts, cp
   (void)psi;
   Level& r = h->lev[0];
   prof_begin(h, PH_OUT);
-  field_kernel<<<(npts * 32 + 127) / 128, 128, 0, h->stream>>>(npts, pts, h->E, h->k, h->eta, h->H, h->x0, h->y0,
-                                                               h->alpha, h->s_c, h->s_t, h->s_nu, h->s_h, h->dens,
-                                                               r.p, r.w_dev, r.L, u, dudx1);
+  if (h->nroot > 1) {
+    field_kernel<<<(npts * 32 + 127) / 128, 128, 0, h->stream>>>(
+        npts, pts, h->E, h->k, h->eta, h->H, h->wide_cx, h->wide_cy, h->y0, h->wide_m0 - 1, h->alpha, h->s_c, h->s_t,
+        h->s_nu, h->s_h, h->dens, h->wide_ps, h->wide_w, h->wide_ML + 2 * h->wide_ps + 1, u, dudx1);
+  } else {
+    field_kernel<<<(npts * 32 + 127) / 128, 128, 0, h->stream>>>(
+        npts, pts, h->E, h->k, h->eta, h->H, h->x0 + 0.5 * h->H, h->y0 + 0.5 * h->H, h->y0, 1, h->alpha, h->s_c,
+        h->s_t, h->s_nu, h->s_h, h->dens, r.p, r.w_dev, r.L, u, dudx1);
+  }
   prof_end(h, PH_OUT);
   return cudaGetLastError();
 }

@@ -64,6 +64,7 @@ constexpr int TSIZE = TSP * (TSP + 1);
 template <class C>
 struct FusedArgs {
   int E, D;
+  int nroot;                     // root squares in a row along x (level 0 has nroot boxes)
   const int* perm;               // sorted -> original element
   const cplx* ph;                // alpha^{-m0} of every sorted element
   const int* opos;               // original -> sorted
@@ -529,13 +530,20 @@ __global__ void fiber_symbol_kernel(const int* __restrict__ fib_list, const int*
 // translation and T_0 the level-1 -> root M2M, stored [u][l] for the 4 P_1
 // child coefficients u, so that the fused product never forms M(0).  One
 // warp per entry (lanes over the P_0 terms), FP64, with an FP32 copy.
-__global__ void root_fold_kernel(int P0, int K, const cplx* __restrict__ R, const cplx* __restrict__ m2m0,
+// With nr roots in a row, R is the operator between all roots ([nr P0][nr P0]) and
+// row u = (level-1 box ch, coefficient m) of the fold, ch = 4 j + q below root j,
+// meets column t = (root i, coefficient a): rc[u][t] = sum_n R[t][j P0 + n] T_0^q[m][n].
+__global__ void root_fold_kernel(int P0, int K, int nr, const cplx* __restrict__ R, const cplx* __restrict__ m2m0,
                                  cplx* __restrict__ rc, cplxf* __restrict__ rcf) {
   const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (i >= P0 * K) return;
-  const int u = i / P0, t = i - u * P0;
+  const int NP = nr * P0, P1 = K / 4;
+  if (i >= NP * nr * K) return;
+  const int u = i / NP, t = i - u * NP;
+  const int ch = u / P1, m = u - ch * P1, j = ch >> 2, q = ch & 3;
+  const cplx* Rr = R + (size_t)t * NP + (size_t)j * P0;
+  const cplx* Tq = m2m0 + (size_t)(q * P1 + m) * P0;
   cplx s{0, 0};
-  for (int n = lane; n < P0; n += 32) s += R[(size_t)t * P0 + n] * m2m0[(size_t)u * P0 + n];
+  for (int n = lane; n < P0; n += 32) s += Rr[n] * Tq[n];
   s = wsum(s);
   if (lane == 0) {
     rc[i] = s;
@@ -2195,17 +2203,29 @@ __device__ __forceinline__ bool fused_body(const FusedArgs<C>& a, const int bid,
         const int bi = i / P, n = i - bi * P;
         const int box = a.ne[l][bi];
         const int S = a.S[l], Sc = a.S[l + 1], Oc = a.O[l + 1];
-        const C* A = (l == 0 ? a.rootc : a.m2m[l]) + a.O[l] + n;
         C acc{0, 0};
-        for (int u = lane; u < 4 * Pc; u += 32) {
-          const int q = u / Pc, m = u - q * Pc, ch = 4 * box + q;
-          if (a.bb[l + 1][ch] < a.be[l + 1][ch])
-            acc += A[(size_t)(q * Sc + Oc + m) * S] * ldcg(a.M[l + 1] + (size_t)ch * Sc + Oc + m);
+        if (l == 0) {
+          // L(0) of root box from the level-1 multipoles of every root (R T_0
+          // folded; rows (level-1 box, coefficient), columns (root, coefficient))
+          const int RS = a.nroot * S;
+          const C* A = a.rootc + (size_t)box * S + a.O[0] + n;
+          for (int u = lane; u < 4 * a.nroot * Pc; u += 32) {
+            const int ch = u / Pc, m = u - ch * Pc;
+            if (a.bb[1][ch] < a.be[1][ch])
+              acc += A[(size_t)(ch * Sc + Oc + m) * RS] * ldcg(a.M[1] + (size_t)ch * Sc + Oc + m);
+          }
+        } else {
+          const C* A = a.m2m[l] + a.O[l] + n;
+          for (int u = lane; u < 4 * Pc; u += 32) {
+            const int q = u / Pc, m = u - q * Pc, ch = 4 * box + q;
+            if (a.bb[l + 1][ch] < a.be[l + 1][ch])
+              acc += A[(size_t)(q * Sc + Oc + m) * S] * ldcg(a.M[l + 1] + (size_t)ch * Sc + Oc + m);
+          }
         }
         acc = wsum(acc);
         if (lane == 0) {
           if (l == 0)
-            a.L[0][a.O[0] + n] = acc;
+            a.L[0][(size_t)box * S + a.O[0] + n] = acc;
           else
             a.M[l][(size_t)box * S + a.O[l] + n] = acc;
         }
@@ -2586,6 +2606,7 @@ cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedA
   }
   a.E = h->E;
   a.D = h->D;
+  a.nroot = h->nroot;
   a.perm = h->s_perm;
   a.ph = h->s_ph;
   a.opos = h->o_pos;
@@ -2710,6 +2731,8 @@ cudaError_t launch_fused(pfmbem* h, const cplx* x, cplx* y, bool f32, const int*
   // the tensor-core form: FP32 product with tensor-core M2L levels
   const bool tc = f32 && h->fz_tcb32 > 0;
   const int nthr = fused_threads(tc), nwarp = nthr / 32;
+  // several roots: L(0) takes one warp per root coefficient (its only form)
+  if (h->nroot > 1 && (int64_t)h->lev[0].nne * h->lev[0].P > (int64_t)grid * nwarp) return cudaErrorInvalidConfiguration;
   // the fiber part's blocks in stage A, in proportion to its block items
   // against the P2M warp items (one leaf per warp)
   {
@@ -2913,20 +2936,21 @@ namespace {
 // with level 3 present, T_1 T_2 and R T_0 T_1 T_2; st must be ordered after the
 // root operator and the M2M tables.
 cudaError_t k_top_operators(pfmbem* h, cudaStream_t st) {
-  const int P0 = h->lev[0].P, K = 4 * h->lev[1].P;
-  root_fold_kernel<<<(P0 * K + 7) / 8, 256, 0, st>>>(P0, K, h->root, h->lev[0].m2m, h->rootc, h->rootcf);
+  const int P0 = h->lev[0].P, K = 4 * h->lev[1].P, nr = h->nroot;
+  root_fold_kernel<<<(nr * nr * P0 * K + 7) / 8, 256, 0, st>>>(P0, K, nr, h->root, h->lev[0].m2m, h->rootc,
+                                                                h->rootcf);
+  // the multipoles of empty boxes are never written: keep them zero (the M2M
+  // stages and M(1) read all four children without occupancy tests)
+  for (int l = 1; l <= h->D; ++l) {
+    const size_t nz = (size_t)h->lev[l].nbox * h->lev[l].P;
+    cudaError_t e = cudaMemsetAsync(h->lev[l].M, 0, nz * sizeof(cplx), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->lev[l].Mf, 0, nz * sizeof(cplxf), st);
+    if (e != cudaSuccess) return e;
+  }
   if (h->m2m31) {
     const int P1 = h->lev[1].P, P2 = h->lev[2].P, P3 = h->lev[3].P;
     m2m31_kernel<<<(16 * P3 * P1 + 255) / 256, 256, 0, st>>>(P1, P2, P3, h->lev[1].m2m, h->lev[2].m2m, h->m2m31,
                                                              h->m2m31f);
-    // the multipoles of empty boxes are never written: keep them zero (the
-    // M2M stages and M(1) read all four children without occupancy tests)
-    for (int l = 1; l <= h->D; ++l) {
-      const size_t nz = (size_t)h->lev[l].nbox * h->lev[l].P;
-      cudaError_t e = cudaMemsetAsync(h->lev[l].M, 0, nz * sizeof(cplx), st);
-      if (e == cudaSuccess) e = cudaMemsetAsync(h->lev[l].Mf, 0, nz * sizeof(cplxf), st);
-      if (e != cudaSuccess) return e;
-    }
     root1_kernel<<<(16 * P1 * P1 + 255) / 256, 256, 0, st>>>(P0, P1, h->lev[0].l2l, h->rootc, h->root1, h->root1f);
   }
   return cudaGetLastError();

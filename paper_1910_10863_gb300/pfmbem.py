@@ -40,7 +40,8 @@ class PlanInfo(ctypes.Structure):
                 ("p2m_nodes", ctypes.c_int), ("lattice_q", ctypes.c_int), ("root_x0", ctypes.c_double),
                 ("root_y0", ctypes.c_double), ("setup_ms", ctypes.c_double), ("near_blocks", ctypes.c_int64),
                 ("fiber_entries", ctypes.c_int64), ("cached", ctypes.c_int), ("tc_levels", ctypes.c_int),
-                ("p32", ctypes.c_int * 16), ("m2l_pairs_level", ctypes.c_int64 * 16)]
+                ("p32", ctypes.c_int * 16), ("m2l_pairs_level", ctypes.c_int64 * 16), ("nroot", ctypes.c_int),
+                ("super_p", ctypes.c_int)]
 
 
 _lib = None

@@ -247,11 +247,9 @@ def mercury_water_block(ka2pi: float, f: float = 0.35, ml: int = 4, n: int = 256
     describes the same crystal (at normal incidence the field is 6a-periodic, hence
     also 12a-periodic) and keeps the block's width ml a within H for ml <= 12 (Wood
     anomalies of the taller period: ka/2pi = n/12).  rows = 6 gives the one-period
-    block (ml <= 6)."""
+    block, which for ml > 6 is wider than its period (a row of root squares)."""
     a = 0.5
     H = rows * a
-    if ml * a > H:
-        raise ValueError("block wider than its period")
     k = 2.0 * math.pi * ka2pi / a
     r = a * math.sqrt(f / math.pi)
     centres = [((ix + 0.5) * a, (iy + 0.5) * a) for ix in range(ml) for iy in range(rows)]

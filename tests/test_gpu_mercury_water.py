@@ -8,7 +8,9 @@ The 10-column block (width 5) is wider than the crystal's period 6a = 3 along y,
 so the fundamental block is taken two periods tall (12 rows, H = 6): the same
 crystal, whose field at normal incidence is 3-periodic and hence 6-periodic.  The
 first test checks that reading: the 4-column crystal's ETC from the one-period
-and the two-period blocks agree."""
+and the two-period blocks agree, and so does the 10-column crystal's from the
+two-period block and from the one-period block, which is wider than its period
+(two root squares)."""
 import numpy as np
 import pytest
 
@@ -40,6 +42,9 @@ def test_one_period_and_two_period_blocks_agree(pf):
     for ka in (0.21, 0.37):
         a, b = etc(pf, ka, 4, rows=6, tol=1e-9), etc(pf, ka, 4, rows=12, tol=1e-9)
         assert abs(a - b) < 1e-7 * max(1.0, abs(a)), (ka, a, b)
+    for ka in (0.34, 0.47):
+        a, b = etc(pf, ka, 10, rows=6, tol=1e-9), etc(pf, ka, 10, rows=12, tol=1e-9)
+        assert abs(a - b) < 1e-6 * max(1.0, abs(a)), (ka, a, b)
 
 
 def test_stop_band_visible_with_ten_columns_only(pf):
