@@ -411,6 +411,7 @@ def main():
     if not args.no_extra and world == 1:
         extra["large_block"] = large_block(pf, torch, args, stream, flush)
         extra["sweep_chunk"] = sweep_chunk(args)
+        extra["warm_start_sweep"] = warm_start_sweep(args)
     h2d = int(npf_h.numel() * 4 + nodes_h.numel() * 8)
     d2h = int(psi_h.numel() * 16 + stats["norders"] * 2 * 16)
     line = {"metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
@@ -527,6 +528,30 @@ def sweep_chunk(args, count=128):
             "max_rel_residual": r["max_rel_residual"], "mean_iters": r["mean_iters"],
             "elements": [r["elements_min"], r["elements_max"]], "tune_seconds": r["tune_seconds"],
             "launch": "one persistent cooperative launch for the whole chunk (groups of blocks per instance)"}
+
+
+def warm_start_sweep(args, train=2048, test=512, epochs=300):
+    """The learned warm start inside the batched sweep: the network (50 -> 3 x 256
+    GELU -> 1088, trained on the GPU by the library's kernels on `train` sweep
+    blocks solved in batched launches) predicts every held-out block's densities;
+    features, one forward pass, decode and one persistent batched solve with the
+    guesses are timed together, against the same blocks in one zero-start batch and
+    against plain FP64 GMRES (pfmbem_solve one block after another).  A reduced
+    form of the 8192 / 1024 training and held-out sets, to keep the bench short."""
+    import time
+
+    from paper_1910_10863_gb300 import warmstart as ws
+    from paper_1910_10863_gb300 import workloads as W
+    t0 = time.perf_counter()
+    X, T, inst, _ = ws.generate_batched(W.batch_instances(train, seed=1912), tol=args.tol)
+    net, hist = ws.train(X, T, epochs=epochs, batch=256, lr=1e-3)
+    t1 = time.perf_counter()
+    r = ws.evaluate_batched(net, W.batch_instances(test, seed=1915), tol=args.tol)
+    r.update({"train_blocks": train, "epochs": epochs, "final_train_loss": hist[-1], "train_seconds": t1 - t0,
+              "speedup_warm_batched_over_plain_fp64": r["batched_warm_start_solves_per_s"] / r["plain_fp64_solves_per_s"],
+              "speedup_warm_over_zero_batched": r["batched_warm_start_solves_per_s"]
+              / r["batched_zero_start_solves_per_s"]})
+    return r
 
 
 def pf_density(w):

@@ -40,12 +40,12 @@ typedef struct pfmbem* pfmbem_t;
 typedef enum {
   PFMBEM_OK = 0,
   PFMBEM_EINVAL = 1,    /* bad argument (null pointer, size, option out of range) */
-  PFMBEM_EGEOM = 2,     /* bad geometry: degenerate element, clockwise fiber, block wider than H */
+  PFMBEM_EGEOM = 2,     /* bad geometry: degenerate element, clockwise fiber, block wider than 4 H */
   PFMBEM_EWOOD = 3,     /* too close to a Wood anomaly: min_n |kH(1 +- sin theta) - 2 pi n| < 1e-3 (Sec. 2) */
   PFMBEM_ENOMEM = 4,    /* device allocation failed */
   PFMBEM_ECUDA = 5,     /* a CUDA runtime call failed */
   PFMBEM_ENOCONV = 6,   /* GMRES stopped at maxit before reaching tol (best iterate is written) */
-  PFMBEM_ETIMEOUT = 7,  /* reserved for bounded device waits */
+  PFMBEM_ETIMEOUT = 7,  /* a bounded device-side wait gave up (options.wait_us) */
   PFMBEM_ENUMERIC = 8   /* non-finite value detected (overflowing expansion tables, NaN residual) */
 } pfmbem_status;
 
@@ -115,7 +115,7 @@ typedef struct {
   int64_t fiber_quad;     /* same-fiber kernel evaluations per matvec */
   int p2m_nodes;          /* Gauss nodes per element in P2M */
   int lattice_q;          /* directly summed image rows in the lattice sums */
-  double root_x0, root_y0;/* lower-left corner of the root box (side H) */
+  double root_x0, root_y0;/* lower-left corner of the (first) root box (side H) */
   double setup_ms;        /* host wall time of pfmbem_create (the device part may still run) */
   int64_t near_blocks;    /* cached near-field 2x2 complex blocks (0 when not cached) */
   int64_t fiber_entries;  /* cached fiber-block complex entries (0 when not cached) */
@@ -184,8 +184,9 @@ pfmbem_status pfmbem_matvec(pfmbem_t h, const double* x, double* y, int precisio
  *   tol   relative residual target (FP64 true residual)
  *   maxit maximum matrix-vector products
  * A guess x is first scaled by the gamma minimising ||B - gamma (I - A) x||
- * (one FP64 matvec) and kept only if that residual is below ||B||; otherwise
- * the solve starts from zero.  In mixed precision the inner GMRES uses the
+ * (one matvec: FP32 in mixed precision, whose residual only starts the
+ * refinement, FP64 otherwise) and kept only if that residual is below ||B||;
+ * otherwise the solve starts from zero.  In mixed precision the inner GMRES uses the
  * mixed matvec and an outer FP64 refinement loop restores FP64 accuracy.
  * Returns ENOCONV if tol is not met (psi still holds the best iterate).
  * info may be NULL. */
@@ -205,12 +206,15 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
  * of GMRES work per instance per phase on the handles' own streams.  Each
  * handle uses its own precision: FP64, or mixed (FP32 operator in the inner
  * GMRES, FP64 residuals for the refinement).  psis[i] complex [2 E_i] (host or
- * device) receive the solutions; infos may be NULL (info.ms is the batch's
- * time).  Returns the first non-OK instance status (others are still solved);
+ * device) receive the solutions; with use_guess != 0 they hold initial guesses
+ * on entry (the learned warm start), each scaled by the gamma minimising
+ * ||B - gamma (I - A) x|| and kept when that residual is below ||B|| (in mixed
+ * precision gamma comes from the FP32 product; convergence is decided on FP64
+ * residuals only).  infos may be NULL (info.ms is the batch's time).  Returns the first non-OK instance status (others are still solved);
  * ETIMEOUT for every instance when a bounded device wait of the launch gave up
  * (options.wait_us of the handles, 1 s by default). */
-pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* psis, double tol, int maxit,
-                                 pfmbem_info* infos);
+pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* psis, int use_guess, double tol,
+                                 int maxit, pfmbem_info* infos);
 
 /* Scattered field u^s (eq. 7) at npts points outside the fibers, from the
  * densities psi: pts [npts][2] float64, u complex [npts]. */

@@ -24,7 +24,7 @@ namespace {
 // Per-instance state (device memory): the handle's GMRES workspace and the
 // results, written by the group that solved the instance.
 struct BatchInst {
-  int n, m, M, pc, mixed, pad0;
+  int n, m, M, pc, mixed, guess;     // guess: x holds an initial guess on entry
   cplx *b, *x, *d, *c, *w, *r, *V, *Z, *yv, *H, *gv, *acc;
   double* ctl;
   int* ictl;
@@ -43,7 +43,7 @@ struct BatchArgs {
   const ArnArgs* arn64;
   unsigned long long* gbar;          // [groups] barrier counters
   int* gslot;                        // [groups] the group's current instance
-  double* gpart;                     // [groups][2][GS] per-block partial sums
+  double* gpart;                     // [groups][2][4][GS] per-block partial sums
   int* err;                          // set when a bounded wait gave up
   unsigned long long wait_ns;
   double tol;
@@ -58,7 +58,7 @@ struct Grp {
   unsigned long long* bar;
   int* err;
   unsigned long long lim;
-  double* part;                      // [2][G]
+  double* part;                      // [2][4][G]
   int par;                           // slot set of the next group sum
 };
 
@@ -76,20 +76,24 @@ __device__ __forceinline__ double block_sum(double v) {
   return t;
 }
 
-// Sum over the group of one value per block, in block order: each block writes
-// its slot, a barrier, then every block adds the G slots.  The two slot sets
-// alternate; a set is written again only two sums later, after a barrier that
-// every block passes only once it has read the set.
-__device__ bool group_sum(Grp& g, double v, double* out) {
-  double* slot = g.part + (size_t)g.par * g.G;
+// Sums over the group of K <= 4 values per block, in block order: each block
+// writes its slots, a barrier, then every block adds the G slots of each value.
+// The two slot sets alternate; a set is written again only two sums later, after
+// a barrier that every block passes only once it has read the set.
+__device__ bool group_sumv(Grp& g, const double* v, int K, double* out) {
+  double* slot = g.part + (size_t)g.par * 4 * g.G;
   g.par ^= 1;
-  if (threadIdx.x == 0) slot[g.b] = v;
+  if (threadIdx.x == 0)
+    for (int q = 0; q < K; ++q) slot[q * g.G + g.b] = v[q];
   if (!gsync(g)) return false;
-  double t = 0;
-  for (int i = 0; i < g.G; ++i) t += __ldcg(slot + i);
-  *out = t;
+  for (int q = 0; q < K; ++q) {
+    double t = 0;
+    for (int i = 0; i < g.G; ++i) t += __ldcg(slot + q * g.G + i);
+    out[q] = t;
+  }
   return true;
 }
+__device__ __forceinline__ bool group_sum(Grp& g, double v, double* out) { return group_sumv(g, &v, 1, out); }
 
 // Vector operations over the n entries, entry t by block (t / blockDim) mod G:
 // every operation of the group gives an entry to the same block, so chains of
@@ -331,12 +335,48 @@ __device__ bool solve_inst(const BatchArgs& A, int ii, Grp& g, unsigned long lon
   const int n = S.n, m = S.m;
   const double tol = A.tol;
   const int maxit = A.maxit;
-  gfill0(g, S.x, n);
+  bool guess = S.guess != 0;
+  if (!guess) gfill0(g, S.x, n);
   double bn2 = 0;
   if (!group_sum(g, gnorm2_part(g, S.b, n), &bn2)) return false;
   const double bn = sqrt(bn2);
   int iters = 0, refinements = 0, st = PFMBEM_ENOCONV;
   double relres = 0;
+  // an initial guess x (the learned warm start): scaled by the gamma minimising
+  // ||b - gamma A x||, kept when the scaled residual d = b - gamma A x is below
+  // ||b||, else a zero start.  In mixed precision A x is the FP32 product: d only
+  // starts the refinement, whose FP64 residuals decide convergence.
+  double rn0 = bn2;
+  bool g32 = false;
+  if (bn > 0 && guess) {
+    const bool ok = S.mixed ? gproduct<cplxf>(A.fa32 + ii, S.x, S.w, g, sargs)
+                            : gproduct<cplx>(A.fa64 + ii, S.x, S.w, g, sargs);
+    if (!ok) return false;
+    double part[3] = {0, 0, 0}, tot[3];
+    GFOR(t, n) {
+      const cplx wv = ldcg(S.w + t), bv = S.b[t];
+      part[0] += abs2(wv);
+      part[1] += wv.re * bv.re + wv.im * bv.im;       // <w, b> = conj(w) b
+      part[2] += wv.re * bv.im - wv.im * bv.re;
+    }
+    for (int q = 0; q < 3; ++q) part[q] = block_sum(part[q]);
+    if (!group_sumv(g, part, 3, tot)) return false;
+    const cplx gam = tot[0] > 0 ? cplx{tot[1] / tot[0], tot[2] / tot[0]} : cplx{0, 0};
+    double dn = 0;
+    GFOR(t, n) {
+      const cplx v = S.b[t] - gam * ldcg(S.w + t);
+      S.d[t] = v;
+      S.x[t] = gam * S.x[t];
+      dn += abs2(v);
+    }
+    if (!group_sum(g, block_sum(dn), &rn0)) return false;
+    if (!(rn0 < bn2) || !isfinite(rn0)) {
+      gfill0(g, S.x, n);
+      guess = false;
+      rn0 = bn2;
+    }
+    g32 = guess && S.mixed;
+  }
   if (bn == 0) {
     st = PFMBEM_OK;
   } else if (S.mixed) {
@@ -346,7 +386,9 @@ __device__ bool solve_inst(const BatchArgs& A, int ii, Grp& g, unsigned long lon
     for (; refinements < 50; ++refinements) {
       const bool r32 = refinements == 1 && A.fast_r1;
       double rn = bn2;
-      if (refinements == 0) {
+      if (refinements == 0 && guess) {
+        rn = rn0;                          // d = b - gamma A x is in place
+      } else if (refinements == 0) {
         gcopy(g, S.d, S.b, n);
       } else {
         const bool ok = r32 ? gproduct<cplxf>(A.fa32 + ii, S.x, S.w, g, sargs)
@@ -359,7 +401,7 @@ __device__ bool solve_inst(const BatchArgs& A, int ii, Grp& g, unsigned long lon
         st = PFMBEM_ENUMERIC;
         break;
       }
-      if (relres <= tol && !r32) {
+      if (relres <= tol && !r32 && !(refinements == 0 && g32)) {
         st = PFMBEM_OK;
         break;
       }
@@ -397,7 +439,7 @@ __device__ bool solve_inst(const BatchArgs& A, int ii, Grp& g, unsigned long lon
     }
   } else {
     GRes r;
-    if (!gmres_dev<cplx>(A, ii, g, S.b, S.x, tol, maxit, true, false, bn, &r, sargs, sarn)) return false;
+    if (!gmres_dev<cplx>(A, ii, g, S.b, S.x, tol, maxit, !guess, false, bn, &r, sargs, sarn)) return false;
     st = r.status;
     iters = r.iters;
     relres = r.relres;
@@ -419,7 +461,7 @@ __global__ void __launch_bounds__(FB, 2) batch_solve_kernel(const __grid_constan
   __shared__ __align__(16) unsigned long long s_args[BATCH_ARGW];
   __shared__ ArnArgs s_arn;
   const int grp = (int)blockIdx.x / A.GS;
-  Grp g{(int)blockIdx.x - grp * A.GS, A.GS, A.gbar + grp, A.err, A.wait_ns, A.gpart + (size_t)grp * 2 * A.GS, 0};
+  Grp g{(int)blockIdx.x - grp * A.GS, A.GS, A.gbar + grp, A.err, A.wait_ns, A.gpart + (size_t)grp * 8 * A.GS, 0};
   for (;;) {
     if (g.b == 0 && threadIdx.x == 0) A.gslot[grp] = atomicAdd(A.next, 1);
     if (!gsync(g)) return;
@@ -523,7 +565,7 @@ static size_t batch_smem(const pfmbem* h) {
 }
 
 cudaError_t k_batch_solve(int ninst, pfmbem* const* hs, const int* order, int GS, double tol, int maxit,
-                          double trust_thr, cudaStream_t st, BatchResult* out, int* timed_out) {
+                          double trust_thr, int use_guess, cudaStream_t st, BatchResult* out, int* timed_out) {
   *timed_out = 0;
   if (ninst <= 0) return cudaSuccess;
   if (GS < 1) return cudaErrorInvalidValue;
@@ -567,7 +609,7 @@ cudaError_t k_batch_solve(int ninst, pfmbem* const* hs, const int* order, int GS
   const size_t o_bar = al(o_ord + sizeof(int) * ninst);
   const size_t o_slot = al(o_bar + sizeof(unsigned long long) * ngroup);
   const size_t o_part = al(o_slot + sizeof(int) * ngroup);
-  const size_t o_next = al(o_part + sizeof(double) * 2 * grid);
+  const size_t o_next = al(o_part + sizeof(double) * 8 * grid);
   const size_t o_err = o_next + 16;
   const size_t total = al(o_err + 16);
   std::vector<unsigned char> hb(total, 0);
@@ -595,6 +637,7 @@ cudaError_t k_batch_solve(int ninst, pfmbem* const* hs, const int* order, int GS
     b.b = gw.b; b.x = gw.x; b.d = gw.d; b.c = gw.c; b.w = gw.w; b.r = gw.r; b.V = gw.V; b.Z = gw.Z;
     b.yv = gw.y; b.H = gw.H; b.gv = gw.gv; b.acc = gw.acc; b.ctl = gw.ctl; b.ictl = gw.ictl;
     b.status = PFMBEM_ENOCONV;
+    b.guess = use_guess ? 1 : 0;
     if (h->opt.wait_us > 0) wait_ns = std::min(wait_ns, 1000ull * (unsigned long long)h->opt.wait_us);
   }
   // the launch is ordered after every handle's pending work on its own stream

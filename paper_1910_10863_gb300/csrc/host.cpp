@@ -2160,8 +2160,8 @@ static pfmbem_status batch_advance(BInst& b, double tol, int maxit) {
 // ============================================================== C ABI
 extern "C" {
 
-pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* psis, double tol, int maxit,
-                                 pfmbem_info* infos) {
+pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* psis, int use_guess, double tol,
+                                 int maxit, pfmbem_info* infos) {
   if (ninst < 0 || (ninst > 0 && (!hs || !psis)) || !(tol > 0) || maxit < 1) return PFMBEM_EINVAL;
   for (int i = 0; i < ninst; ++i)
     if (hs[i] && !hs[i]->ready) {
@@ -2186,7 +2186,20 @@ pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* p
     b.sn.assign(g.m, 0.0);
     b.gv.assign(g.m + 1, 0.0);
     CK(k_rhs(h, g.b));
-    CK(cudaMemsetAsync(g.x, 0, sizeof(cplx) * g.n, h->stream));
+    if (use_guess) {
+      // the initial guess, from host or device memory
+      CK(cudaMemcpyAsync(g.x, psis[i], sizeof(cplx) * g.n,
+                         is_device_ptr(psis[i]) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+      b.zero_x = false;
+      // ||b|| for the lockstep's relative residuals (the persistent launch forms its own)
+      double bn2 = 0;
+      CK(k_norm2(h, g.b, g.n, g.nrm));
+      CK(cudaMemcpyAsync(&bn2, g.nrm, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaStreamSynchronize(h->stream));
+      b.bn = std::sqrt(bn2);
+    } else {
+      CK(cudaMemsetAsync(g.x, 0, sizeof(cplx) * g.n, h->stream));
+    }
   }
   // One persistent launch over all instances when every handle can run in it
   // (PFMBEM_BATCH_LOCKSTEP=1 keeps the host-driven lockstep below, for
@@ -2210,8 +2223,8 @@ pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* p
     // pending work (set-up tails, right-hand sides)
     std::vector<BatchResult> res(ninst);
     int timed_out = 0;
-    const cudaError_t e = k_batch_solve(ninst, hs, order.data(), GS, tol, maxit, trust_thr(), st, res.data(),
-                                        &timed_out);
+    const cudaError_t e = k_batch_solve(ninst, hs, order.data(), GS, tol, maxit, trust_thr(), use_guess, st,
+                                        res.data(), &timed_out);
     if (e == cudaErrorNotSupported) {
       cudaGetLastError();
       persist = false;                 // the lockstep below
@@ -2487,13 +2500,17 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
   }
   int iters = 0, restarts = 0;
   double relres = 1;
+  bool guess32 = false;
   if (use_guess) {
     // Scale the guess x by the gamma minimising ||B - gamma A x|| (w = A x from
     // one FP64 matvec, gamma = <w, B> / <w, w>); the scaled guess is kept when
     // its residual d = B - gamma w is below ||B||, else the solve starts at zero.
+    // (mixed precision: A x is the FP32 product; its residual only starts the
+    // refinement, and convergence is decided on FP64 residuals)
     double nn[2] = {0, 0}, rn = 0;
     cplx wb{0, 0};
-    CK(k_matvec(h, g.x, g.w, PFMBEM_FP64));
+    guess32 = h->opt.precision == PFMBEM_MIXED && h->cached && h->fused;
+    CK(k_matvec(h, g.x, g.w, guess32 ? PFMBEM_MIXED : PFMBEM_FP64));
     CK(k_norm2(h, g.b, (int)n, g.nrm));
     CK(k_norm2(h, g.w, (int)n, g.nrm + 1));
     CK(k_multidot(h, g.w, 1, g.b, (int)n, g.hcol));
@@ -2552,7 +2569,7 @@ pfmbem_status pfmbem_solve(pfmbem_t h, const double* B, double* psi, int use_gue
       }
       relres = bn > 0 ? std::sqrt(rn) / bn : 0.0;
       if (!std::isfinite(relres)) return fail(h, PFMBEM_ENUMERIC, "non-finite residual");
-      if (relres <= tol && !r32) { st = PFMBEM_OK; break; }
+      if (relres <= tol && !r32 && !(refinements == 0 && guess32 && use_guess)) { st = PFMBEM_OK; break; }
       if (iters >= maxit) break;
       // stop when refinement no longer reduces the FP64 residual
       if (!r32) {

@@ -382,7 +382,7 @@ bool batch_eligible(const pfmbem* h);
 int k_fused_order(const pfmbem* h, int l, bool f32);
 int k_fused_tc_levels(const pfmbem* h);
 cudaError_t k_batch_solve(int ninst, pfmbem* const* hs, const int* order, int GS, double tol, int maxit,
-                          double trust_thr, cudaStream_t st, BatchResult* out, int* timed_out);
+                          double trust_thr, int use_guess, cudaStream_t st, BatchResult* out, int* timed_out);
 cudaError_t k_fiber_symbols(pfmbem* h);
 cudaError_t k_precond_symbols(pfmbem* h);
 cudaError_t k_precond_apply(pfmbem* h, const cplx* x, cplx* y, int precision, const int* done = nullptr);

@@ -81,7 +81,7 @@ def lib():
             "pfmbem_warm_features_local": ([vp, i, vp], i),
             "pfmbem_warm_targets": ([vp, i, vp, vp], i),
             "pfmbem_warm_decode": ([vp, i, vp, vp], i),
-            "pfmbem_solve_batch": ([i, vp, vp, d, i, vp], i),
+            "pfmbem_solve_batch": ([i, vp, vp, i, d, i, vp], i),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -156,14 +156,15 @@ def pfmbem_solve(h, B, psi, use_guess=False, tol=1e-8, maxit=1000, check=True) -
     return info
 
 
-def pfmbem_solve_batch(handles, psis, tol=1e-6, maxit=2000):
+def pfmbem_solve_batch(handles, psis, tol=1e-6, maxit=2000, use_guess=False):
     """Solve of many handles in one persistent launch (host-driven lockstep when a
-    handle cannot run in it); psis are complex128 buffers (host or device)."""
+    handle cannot run in it); psis are complex128 buffers (host or device), read
+    as initial guesses with use_guess."""
     n = len(handles)
     hs = (ctypes.c_void_p * n)(*handles)
     ps = (ctypes.c_void_p * n)(*[addr(p) for p in psis])
     infos = (Info * n)()
-    st = lib().pfmbem_solve_batch(n, hs, ps, float(tol), int(maxit), infos)
+    st = lib().pfmbem_solve_batch(n, hs, ps, int(bool(use_guess)), float(tol), int(maxit), infos)
     return st, list(infos)
 
 

@@ -64,6 +64,96 @@ def generate(instances, tol=1e-6, model=None):
             np.array(iters))
 
 
+def _create_all(instances, precision=pf.MIXED, threads=16):
+    """Handles of many blocks, created on a pool of host threads."""
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(threads) as ex:
+        return list(ex.map(lambda w: pf.Solver(w, precision=precision), instances))
+
+
+def generate_batched(instances, tol=1e-6, model=None, chunk=256):
+    """As generate, with the blocks solved in persistent batched launches of
+    chunk blocks (the training data of a sweep come at the batched rate)."""
+    import torch
+    X, T, inst, iters = [], [], [], []
+    for c0 in range(0, len(instances), chunk):
+        part = instances[c0:c0 + chunk]
+        sols = _create_all(part)
+        psis = [torch.zeros(2 * s.E, dtype=torch.complex128, device="cuda") for s in sols]
+        st, infos = pf.pfmbem_solve_batch([s.h for s in sols], psis, tol=tol)
+        for q, (w, s, psi, info) in enumerate(zip(part, sols, psis, infos)):
+            p = psi.cpu().numpy()
+            x = features(s, w.M, model)
+            X.append(x)
+            T.append(targets(s, p, w.M, model))
+            inst.append(np.full(x.shape[0], c0 + q))
+            iters.append(info.iters)
+            s.close()
+    return (np.concatenate(X).astype(np.float32), np.concatenate(T).astype(np.float32), np.concatenate(inst),
+            np.array(iters))
+
+
+def evaluate_batched(net, instances, tol=1e-6, model=None, fp64_sample=32):
+    """The whole warm-start pipeline on many held-out blocks at once: features of
+    every block, one forward pass of the network over all of them, decode, and one
+    persistent batched solve with the guesses; against the same blocks solved in
+    one batch from zero, and against plain FP64 GMRES (one pfmbem_solve after
+    another, FP64 handles, on the first fp64_sample blocks).  Times in seconds,
+    handles created beforehand (outside every timed region)."""
+    import time
+
+    import torch
+    tc = time.perf_counter()
+    sols = _create_all(instances)
+    n = len(sols)
+    torch.cuda.synchronize()
+    t_create = time.perf_counter() - tc
+    # zero start (after one untimed batch: first-launch costs stay out of the timing)
+    psz = [torch.zeros(2 * s.E, dtype=torch.complex128, device="cuda") for s in sols]
+    pf.pfmbem_solve_batch([s.h for s in sols], psz, tol=tol)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st0, iz = pf.pfmbem_solve_batch([s.h for s in sols], psz, tol=tol)
+    t_zero = time.perf_counter() - t0
+    # warm start: features, network, decode and solve, all timed
+    psw = [torch.zeros(2 * s.E, dtype=torch.complex128, device="cuda") for s in sols]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    Xf = np.concatenate([features(s, w.M, model) for s, w in zip(sols, instances)]).astype(np.float32)
+    Y = net.forward(Xf)
+    rows_per = Y.shape[0] // n
+    for q, (s, psi) in enumerate(zip(sols, psw)):
+        pf.pfmbem_warm_decode(s.h, Y[q * rows_per:(q + 1) * rows_per].ravel(), psi.data_ptr(), NMODES)
+    st1, iw = pf.pfmbem_solve_batch([s.h for s in sols], psw, tol=tol, use_guess=True)
+    t_warm = time.perf_counter() - t0
+    # plain FP64 GMRES, one block after another
+    sample = instances[:fp64_sample]
+    s64 = _create_all(sample, precision=pf.FP64)
+    psf = [torch.zeros(2 * s.E, dtype=torch.complex128, device="cuda") for s in s64]
+    s64[0].solve(psf[0].data_ptr(), tol=tol, check=False)           # untimed first solve
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    i64 = [s.solve(p.data_ptr(), tol=tol, check=False) for s, p in zip(s64, psf)]
+    torch.cuda.synchronize()
+    t_fp64 = time.perf_counter() - t0
+    diff = max(float(torch.linalg.norm(a - b) / torch.linalg.norm(b)) for a, b in zip(psw, psz))
+    out = {
+        "blocks": n, "status_zero": st0, "status_warm": st1,
+        "batched_zero_start_solves_per_s": n / t_zero,
+        "batched_warm_start_solves_per_s": n / t_warm,
+        "plain_fp64_solves_per_s": len(sample) / t_fp64, "plain_fp64_sample": len(sample),
+        "mean_iters_zero": float(np.mean([i.iters for i in iz])), "mean_iters_warm": float(np.mean([i.iters for i in iw])),
+        "mean_iters_fp64": float(np.mean([i.iters for i in i64])),
+        "max_rel_residual_warm": float(max(i.rel_residual for i in iw)),
+        "max_rel_residual_fp64": float(max(i.rel_residual for i in i64)),
+        "max_rel_diff_warm_vs_zero": diff, "create_seconds": t_create}
+    tc = time.perf_counter()
+    for s in sols + s64:
+        s.close()
+    out["destroy_seconds"] = time.perf_counter() - tc
+    return out
+
+
 def train(X, T, hidden=256, layers=3, epochs=200, batch=256, lr=1e-3, seed=1913, log_every=0, lr_final=0.05,
           X_val=None, T_val=None):
     """Adam on the mean-squared error with a cosine learning-rate decay from lr
@@ -105,16 +195,27 @@ def main():
     ap.add_argument("--batch", type=int, default=0, help="0: 256 (global) or 512 (local)")
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--batched", action="store_true",
+                    help="training data from batched solves; evaluation as one batched warm-started solve of all "
+                         "held-out blocks against a batched zero start and plain FP64 GMRES")
     a = ap.parse_args()
     a.epochs = a.epochs or (1000 if a.model == "global" else 300)
     a.batch = a.batch or (256 if a.model == "global" else 512)
     t0 = time.perf_counter()
-    X, T, inst, _ = generate(W.batch_instances(a.train, seed=1912), tol=a.tol, model=a.model)
+    gen = generate_batched if a.batched else generate
+    X, T, inst, _ = gen(W.batch_instances(a.train, seed=1912), tol=a.tol, model=a.model)
     nv = max(1, a.train // 16)               # validation split: the first blocks' rows
     val = inst < nv
     t1 = time.perf_counter()
     net, hist = train(X[~val], T[~val], epochs=a.epochs, batch=a.batch, lr=a.lr, X_val=X[val], T_val=T[val])
     t2 = time.perf_counter()
+    if a.batched:
+        r = evaluate_batched(net, W.batch_instances(a.test, seed=1915), tol=a.tol, model=a.model)
+        r.update({"model": a.model, "train_blocks": a.train - nv, "epochs": a.epochs, "final_loss": hist[-1],
+                  "final_validation_loss": net.val_hist[-1],
+                  "seconds": {"data": t1 - t0, "train": t2 - t1, "evaluate": time.perf_counter() - t2}})
+        print(json.dumps(r), flush=True)
+        return
     rows = evaluate(net, W.batch_instances(a.test, seed=1915), tol=a.tol, model=a.model)
     t3 = time.perf_counter()
     iz, iw, r0 = rows[:, 0], rows[:, 1], rows[:, 2]

@@ -130,3 +130,28 @@ def test_batch_wait_that_runs_out_returns_etimeout(pf=None):
     psis = [np.zeros(2 * s.E, dtype=np.complex128) for s in solvers]
     st, infos = pf.pfmbem_solve_batch([s.h for s in solvers], psis, tol=1e-8, maxit=500)
     assert st == 0 and all(i.rel_residual <= 1e-8 for i in infos)
+
+
+def test_batch_with_initial_guesses_matches_dense_lu(sweep):
+    """use_guess: every block starts from a perturbed copy of its dense-LU solution
+    (scaled by the residual-minimising gamma on the device); one of them from
+    large random noise, which the scaling reduces to almost nothing.  All reach
+    the tolerance and the oracle's solution."""
+    import torch
+    from paper_1910_10863_gb300 import pfmbem as pf
+    ws, refs = sweep
+    ws, refs = ws[:6], refs[:6]
+    rng = np.random.default_rng(4)
+    solvers = [pf.Solver(w, precision=pf.FP64 if i == 3 else pf.MIXED) for i, w in enumerate(ws)]
+    guesses = []
+    for i, ref in enumerate(refs):
+        noise = rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape)
+        g = 0.7 * ref + 1e-2 * np.linalg.norm(ref) / math.sqrt(ref.size) * noise
+        if i == 5:
+            g = 1e3 * noise                      # no better than a zero start
+        guesses.append(torch.from_numpy(np.ascontiguousarray(g)).cuda())
+    st, infos = pf.pfmbem_solve_batch([s.h for s in solvers], guesses, tol=1e-9, maxit=2000, use_guess=True)
+    assert st == 0
+    for g, ref, info in zip(guesses, refs, infos):
+        assert info.rel_residual <= 1e-9
+        assert rel(g.cpu().numpy(), ref) < 1e-6
