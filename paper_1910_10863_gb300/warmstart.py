@@ -93,13 +93,14 @@ def generate_batched(instances, tol=1e-6, model=None, chunk=256):
             np.array(iters))
 
 
-def evaluate_batched(net, instances, tol=1e-6, model=None, fp64_sample=32):
+def evaluate_batched(net, instances, tol=1e-6, model=None, fp64_sample=32, keep=0):
     """The whole warm-start pipeline on many held-out blocks at once: features of
     every block, one forward pass of the network over all of them, decode, and one
     persistent batched solve with the guesses; against the same blocks solved in
     one batch from zero, and against plain FP64 GMRES (one pfmbem_solve after
     another, FP64 handles, on the first fp64_sample blocks).  Times in seconds,
-    handles created beforehand (outside every timed region)."""
+    handles created beforehand (outside every timed region).  keep > 0 adds the
+    first keep warm-started solutions (host arrays) under "solutions"."""
     import time
 
     import torch
@@ -147,6 +148,8 @@ def evaluate_batched(net, instances, tol=1e-6, model=None, fp64_sample=32):
         "max_rel_residual_warm": float(max(i.rel_residual for i in iw)),
         "max_rel_residual_fp64": float(max(i.rel_residual for i in i64)),
         "max_rel_diff_warm_vs_zero": diff, "create_seconds": t_create}
+    if keep > 0:
+        out["solutions"] = [p.cpu().numpy() for p in psw[:keep]]
     tc = time.perf_counter()
     for s in sols + s64:
         s.close()

@@ -94,14 +94,26 @@ def test_trained_network_reduces_gmres_iterations_on_held_out_blocks(pf):
 def test_batched_warm_start_on_held_out_blocks(pf):
     """The whole pipeline in one batch: features of every held-out block, one
     forward pass, decode, one persistent solve with the guesses; fewer iterations
-    than the batched zero start, the same solutions, and both converged."""
+    than the batched zero start, the same solutions, both converged, and the
+    warm-started solutions' residual judged by the oracle on sampled rows."""
     from paper_1910_10863_gb300 import warmstart as ws
     train = W.batch_instances(320, seed=101)
     test = W.batch_instances(24, seed=202)
     X, T, _, _ = ws.generate_batched(train)
     net, hist = ws.train(X, T, epochs=150, batch=64, lr=2e-3, seed=3)
-    r = ws.evaluate_batched(net, test, fp64_sample=4)
+    r = ws.evaluate_batched(net, test, fp64_sample=4, keep=2)
     assert r["status_zero"] == 0 and r["status_warm"] == 0
     assert r["max_rel_residual_warm"] <= 1e-6 and r["max_rel_residual_fp64"] <= 1e-6
     assert r["mean_iters_warm"] < r["mean_iters_zero"]
     assert r["max_rel_diff_warm_vs_zero"] < 1e-4
+    # judged by the oracle: its residual of two warm-started solutions on sampled
+    # element rows (exact element integrals, Ewald G_qp), at the solve tolerance
+    from oracle import bem
+    rng = np.random.default_rng(9)
+    for w, psi in zip(test[:2], r["solutions"]):
+        pb = bem.problem(w)
+        sel = np.sort(rng.choice(w.E, size=6, replace=False))
+        rows = bem.operator_rows(pb, sel)
+        eq = np.stack([2 * sel, 2 * sel + 1], axis=1).ravel()
+        B = bem.rhs(pb)[eq]
+        assert np.linalg.norm(B - rows @ psi) / np.linalg.norm(B) < 5e-6
