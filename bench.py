@@ -228,6 +228,19 @@ def run_reference(args, rank, world):
 
 
 # ------------------------------------------------------------------ own arm
+def aggregate_ranks(ms, world, dist=None, device="cpu"):
+    """Replicas: every rank solves its own block (weak scaling, no collective on
+    the data path).  The job's time per step is the slowest rank's (max over
+    ranks of each entry of ms), and its rate the solves of all ranks per second:
+    world * 1000 / ms.  Returns (max times, whole-job rates)."""
+    import torch
+    if dist is not None:
+        t = torch.tensor([float(v) for v in ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = [float(v) for v in t]
+    return list(ms), [world * 1000.0 / v for v in ms]
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -350,12 +363,7 @@ def main():
     stats.clear()
     stats.update(main_stats)
     barrier()
-    if dist is not None:
-        t = torch.tensor([ms_step, ms_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step, ms_e2e = float(t[0]), float(t[1])
-    value = world * 1000.0 / ms_step
-    e2e_value = world * 1000.0 / ms_e2e
+    (ms_step, ms_e2e), (value, e2e_value) = aggregate_ranks([ms_step, ms_e2e], world, dist, "cuda")
 
     # FMM matvec rate (FP64 and mixed) on one handle
     h = pf.pfmbem_create(w.M, npf_d, nodes_d, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, opt, sptr)
