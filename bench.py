@@ -89,21 +89,123 @@ def workload(name="hexagon_8x8_n256"):
 
 
 # ------------------------------------------------------------------ clocks
+CLOCK_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+# bits of NVML's clocks-event-reason mask (nvmlClocksEventReason* in nvml.h)
+_NVML_REASON_BITS = {"sw_power_cap": 0x4, "hw_slowdown": 0x8, "sw_thermal_slowdown": 0x20,
+                     "hw_thermal_slowdown": 0x40}
+
+
+def summarize_clocks(rows, t0, t1, source):
+    """Median SM clock, maximum clock and active slowdown reasons of the samples
+    taken between t0 and t1 (host time, seconds).  rows: (time, sm MHz, max MHz,
+    set of active reasons).  With no sample inside the window the nearest one on
+    either side stands in, and in_window says so."""
+    keep = [r for r in rows if t0 <= r[0] <= t1]
+    if not keep and rows:
+        before = [r for r in rows if r[0] < t0]
+        after = [r for r in rows if r[0] > t1]
+        keep = ([before[-1]] if before else []) + ([after[0]] if after else [])
+    sm = [r[1] for r in keep]
+    mx = [r[2] for r in keep]
+    reasons = sorted({nm for r in keep for nm in r[3]})
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "samples": len(sm), "in_window": bool(keep) and all(t0 <= r[0] <= t1 for r in keep),
+            "reasons": reasons, "source": source}
+
+
+class _Nvml:
+    """Read-only NVML queries through ctypes: SM clock, its maximum and the
+    clocks-event-reason mask of one device.  Raises OSError when the library or
+    the device is missing."""
+
+    def __init__(self, index, pci=None):
+        import ctypes
+        self.c = ctypes
+        lib = None
+        for name in ("libnvidia-ml.so.1", "libnvidia-ml.so"):
+            try:
+                lib = ctypes.CDLL(name)
+                break
+            except OSError:
+                continue
+        if lib is None:
+            raise OSError("libnvidia-ml not found")
+        self.lib = lib
+        if lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        # the CUDA device's PCI address names it whatever the visible-device list
+        if (pci is None or lib.nvmlDeviceGetHandleByPciBusId_v2(pci.encode(), ctypes.byref(self.dev)) != 0) and \
+                lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(index), ctypes.byref(self.dev)) != 0:
+            raise OSError("no NVML device %d" % index)
+        try:
+            self.reason_fn = lib.nvmlDeviceGetCurrentClocksEventReasons
+        except AttributeError:
+            self.reason_fn = lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        self.max_sm = self._clock(lib.nvmlDeviceGetMaxClockInfo)
+        if self.max_sm is None:
+            raise OSError("nvmlDeviceGetMaxClockInfo failed")
+
+    def _clock(self, fn):
+        v = self.c.c_uint()
+        return float(v.value) if fn(self.dev, self.c.c_int(1), self.c.byref(v)) == 0 else None  # 1 = SM
+
+    def sample(self):
+        sm = self._clock(self.lib.nvmlDeviceGetClockInfo)
+        m = self.c.c_ulonglong()
+        mask = m.value if self.reason_fn(self.dev, self.c.byref(m)) == 0 else 0
+        act = {nm for nm, bit in _NVML_REASON_BITS.items() if mask & bit}
+        return sm, self.max_sm, act
+
+    def close(self):
+        self.lib.nvmlShutdown()
+
+
+def pci_address(torch, dev):
+    """domain:bus:device.function of a CUDA device, as NVML spells it, or None."""
+    pr = torch.cuda.get_device_properties(dev)
+    try:
+        return "%08X:%02X:%02X.0" % (pr.pci_domain_id, pr.pci_bus_id, pr.pci_device_id)
+    except AttributeError:
+        return None
+
+
 class Clocks:
-    """nvidia-smi samples every 50 ms, kept for the timed region.
+    """SM clocks and slowdown reasons sampled during the timed region.
 
-    The sampler starts before the warm-up (nvidia-smi takes a while to come up)
-    and the samples are filtered by their timestamps to the window between
-    mark_start() and mark_stop(); a region shorter than the sampling period keeps
-    the nearest sample on either side of it."""
+    A host thread reads NVML every 2 ms from start() to stop(), so a timed
+    region of a few tens of milliseconds still holds samples; the samples are
+    kept for the window between mark_start() and mark_stop().  Where NVML cannot
+    be loaded, nvidia-smi samples every 50 ms instead."""
 
-    def __init__(self, index):
+    def __init__(self, index, pci=None):
         self.index = index
+        self.pci = pci
         self.proc = None
         self.path = None
+        self.nvml = None
+        self.thread = None
+        self.rows = []
         self.t0 = self.t1 = None
 
     def start(self):
+        import threading
+        try:
+            self.nvml = _Nvml(self.index, self.pci)
+        except (OSError, AttributeError):
+            self.nvml = None
+        if self.nvml is not None:
+            self.halt = threading.Event()
+
+            def run():
+                while not self.halt.is_set():
+                    sm, mx, act = self.nvml.sample()
+                    if sm is not None:
+                        self.rows.append((time.time(), sm, mx, act))
+                    time.sleep(0.002)
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            return
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -118,8 +220,11 @@ class Clocks:
 
     def wait_first(self, timeout=10.0):
         t = time.time()
-        while self.proc is not None and time.time() - t < timeout:
-            if os.path.getsize(self.path) > 0 or self.proc.poll() is not None:
+        while time.time() - t < timeout:
+            if self.thread is not None:
+                if self.rows or not self.thread.is_alive():
+                    return
+            elif self.proc is None or os.path.getsize(self.path) > 0 or self.proc.poll() is not None:
                 return
             time.sleep(0.02)
 
@@ -131,6 +236,12 @@ class Clocks:
 
     def stop(self):
         import datetime
+        t0, t1 = self.t0 or 0.0, self.t1 or 1e300
+        if self.thread is not None:
+            self.halt.set()
+            self.thread.join(timeout=5)
+            self.nvml.close()
+            return summarize_clocks(self.rows, t0, t1, "NVML, 2 ms")
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
         self.proc.terminate()
@@ -139,29 +250,18 @@ class Clocks:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         rows = []
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             f = [x.strip() for x in line.split(",")]
             if len(f) < 10:
                 continue
             try:
                 ts = datetime.datetime.strptime(f[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
-                rows.append((ts, float(f[2]), float(f[3]), f[6:10]))
+                act = {nm for nm, v in zip(CLOCK_REASONS, f[6:10]) if v.lower().startswith("active")}
+                rows.append((ts, float(f[2]), float(f[3]), act))
             except ValueError:
                 continue
         os.unlink(self.path)
-        t0, t1 = self.t0 or 0.0, self.t1 or 1e300
-        keep = [r for r in rows if t0 <= r[0] <= t1]
-        if not keep and rows:
-            before = [r for r in rows if r[0] < t0]
-            after = [r for r in rows if r[0] > t1]
-            keep = ([before[-1]] if before else []) + ([after[0]] if after else [])
-        sm = [r[1] for r in keep]
-        mx = [r[2] for r in keep]
-        reasons = sorted({nm for r in keep for nm, v in zip(names, r[3]) if v.lower().startswith("active")})
-        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "samples": len(sm), "in_window": bool(keep) and all(t0 <= r[0] <= t1 for r in keep),
-                "reasons": reasons}
+        return summarize_clocks(rows, t0, t1, "nvidia-smi, 50 ms")
 
 
 # ------------------------------------------------------------------ CPU oracle sample
@@ -328,7 +428,7 @@ def main():
             tot += e0.elapsed_time(e1)
         return tot / steps
 
-    clocks = Clocks(local)
+    clocks = Clocks(local, pci_address(torch, local))
     clocks.start()
     for _ in range(args.warmup):
         step()

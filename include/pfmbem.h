@@ -90,6 +90,19 @@ typedef struct {
   int batch_group;  /* blocks per instance group of pfmbem_solve_batch's persistent launch;
                        0 = 8 (raised to fit the coefficients of the tree's top level, one
                        warp each).  A batch uses the largest value among its handles */
+  int tree;         /* 0 = square quadtree over the block (default); 1 = regular-triangle
+                       quadtree for hexagon lattices (Sec. 3.1, Fig. 5): every fiber in the
+                       hexagonal cell of its lattice point (the lattice below), the cell
+                       split into six equilateral triangles and each triangle into four
+                       down to the leaves; cells and triangles are neighbours when they
+                       touch.  Its product is FP64 with the element integrals computed in
+                       every product (near_mode is ignored, launch and m2l_mode must be 0,
+                       a MIXED precision solves in FP64); pfmbem_solve_batch rejects it.
+                       Default p_min 30.  EGEOM when a fiber leaves its cell, two fibers
+                       share a cell or H is not a multiple (>= 2) of tri_a */
+  double tri_a;     /* tree 1: nearest-neighbour spacing a of the hexagonal lattice, whose
+                       lattice vectors are (0, a) and (a sqrt(3)/2, a/2) */
+  double tri_ox, tri_oy;  /* tree 1: one point of that lattice */
 } pfmbem_options;
 
 /* Outcome of a solve. */

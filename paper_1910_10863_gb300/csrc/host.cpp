@@ -784,6 +784,8 @@ static pfmbem_status on_aux(pfmbem* h, int i, F&& f) {
   return PFMBEM_OK;
 }
 
+#include "tri_plan.h"
+
 static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) {
   const double t0 = now_ms();
   const int M = h->M;
@@ -830,7 +832,7 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
   // allows any width L; the y-period H sets the root's side)
   {
     const int nr = std::max(1, (int)std::ceil((xmax - xmin) / H - 1e-12));
-    if (nr > kMaxRoots) return fail(h, PFMBEM_EGEOM, "block wider than 4 H along x");
+    if (nr > kMaxRoots && h->opt.tree != 1) return fail(h, PFMBEM_EGEOM, "block wider than 4 H along x");
     h->nroot = nr;
   }
   // fiber centre (mean of the nodes) and mean radius, for the learned warm start
@@ -852,6 +854,8 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     h->hfib_geo[3 * i + 1] = sy;
     h->hfib_geo[3 * i + 2] = sr / n;
   }
+  if (h->opt.tree == 1) return build_plan_tri(h, nodes, foff, c, t, nu, len, fib, hmax, t0);
+  if (h->opt.tree != 0) return fail(h, PFMBEM_EINVAL, "tree must be 0 (square) or 1 (triangle)");
   if (0.5 * k * hmax > 4.0) return fail(h, PFMBEM_EINVAL, "elements longer than 8/k");
   // ---------------------------------------------------- root box and wrapping
   h->x0 = 0.5 * (xmin + xmax) - 0.5 * h->nroot * H;
@@ -2173,6 +2177,7 @@ pfmbem_status pfmbem_solve_batch(int ninst, const pfmbem_t* hs, double* const* p
   for (int i = 0; i < ninst; ++i) {
     pfmbem* h = hs[i];
     if (!h || !psis[i]) return PFMBEM_EINVAL;
+    if (h->tree == 1) return fail(h, PFMBEM_EINVAL, "the batched solver takes square-tree handles only");
     BInst& b = inst[i];
     b.h = h;
     b.prec = (h->opt.precision == PFMBEM_MIXED && h->cached) ? PFMBEM_MIXED : PFMBEM_FP64;
@@ -2693,13 +2698,16 @@ pfmbem_status field_points(pfmbem* h, const double* psi, int npts, const double*
   std::vector<double> hp(2 * (size_t)npts);
   if (is_device_ptr(pts)) CK(cudaMemcpy(hp.data(), pts, sizeof(double) * hp.size(), cudaMemcpyDeviceToHost));
   else std::memcpy(hp.data(), pts, sizeof(double) * hp.size());
-  const double ox = h->x0 + 0.5 * h->nroot * h->H;
+  // half the block's width: a row of root squares, or the hexagonal cells' extent
+  const double ox = h->tree == 1 ? h->wide_cx : h->x0 + 0.5 * h->nroot * h->H;
+  const double hw = h->tree == 1 ? h->field_hw : 0.5 * h->nroot * h->H;
   for (int i = 0; i < npts; ++i) {
     if (!std::isfinite(hp[2 * i]) || !std::isfinite(hp[2 * i + 1])) return fail(h, PFMBEM_EINVAL, "non-finite point");
     // the root local expansion of the images |m| >= 2 converges for |x - O| + H/sqrt(2) < 2H
-    // (a row of roots: the super root's, of the images |m| >= m0, for |x - C| < 2 R_s)
-    if (std::fabs(hp[2 * i] - ox) > (0.5 * h->nroot + 0.2) * h->H)
-      return fail(h, PFMBEM_EINVAL, "field point too far from the block along x (|x - centre| > (nroot/2 + 0.2) H)");
+    // (a row of roots or the hexagonal cells: the super root's, of the images
+    // |m| >= m0, for |x - C| < 2 R_s)
+    if (std::fabs(hp[2 * i] - ox) > hw + 0.2 * h->H)
+      return fail(h, PFMBEM_EINVAL, "field point too far from the block along x (|x - centre| > half width + 0.2 H)");
   }
   const cplx* psid;
   pfmbem_status st = stage_input(h, psi, n, h->stage_in, &psid);

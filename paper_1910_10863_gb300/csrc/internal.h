@@ -82,6 +82,10 @@ struct Level {
   cplx* m2lt = nullptr;      // the same operators transposed, [49][P source][P target]
   cplxf* m2ltf = nullptr;
   cplxf* m2ltl = nullptr;    // lo parts of m2lt: m2lt = m2ltf + m2ltl to ~48 bits (double-float M2L)
+  // triangle tree: box centres, and per box the index of its M2M/L2L operator in
+  // the parent level's tables (the children's offsets vary with the orientation)
+  double2* ctr = nullptr;    // [nbox]
+  int* pidx = nullptr;       // [nbox]
   cplx* m2m = nullptr;       // children (level l+1) -> this level: [4][P][P_child]
   cplx* l2l = nullptr;       // this level -> children: [4][P_child][P]
   // FP32 copies for the mixed path
@@ -152,7 +156,10 @@ struct pfmbem {
   std::string err;
   // plan
   int D = 0;
-  int nroot = 1;                 // root squares of side H in a row along x (block width up to nroot H)
+  int nroot = 1;                 // root squares of side H in a row along x (block width up to nroot H);
+                                 // triangle tree: the hexagonal cells, one per fiber
+  int tree = 0;                  // 0 = square quadtree, 1 = regular-triangle quadtree (hexagon lattices)
+  double field_hw = 0;           // triangle tree: half the block's width along x (field point check)
   double x0 = 0, y0 = 0;
   Level lev[PF_MAXLEVEL + 1];
   int g_far = 4, g_far_f = 2;    // Gauss nodes per element in P2M (FP64 / FP32)
@@ -424,7 +431,12 @@ cudaError_t k_lattice_sums(pfmbem* h, int jmax, int q, cplx* out_dev, int mlo = 
 // multipole to every root's local expansion, the images beyond the tree's lists
 // included, into h->root ([nroot P0][nroot P0]), and the super root's operators
 // kept for the field.
-cudaError_t k_wide_top(pfmbem* h, const double2* dv, cplx* S, cplx* X);
+// nbr: optional [nroot][nroot][3] mask of the root pairs (i, j, image m = -1..1)
+// that the tree's lists take (null: a row of squares, adjacent indices).
+cudaError_t k_wide_top(pfmbem* h, const double2* dv, cplx* S, cplx* X, const unsigned char* nbr = nullptr);
+// Triangle tree: level l's M2L operators for nm2l offsets (target - source
+// centre) and its M2M/L2L operators for nshift child offsets (child - parent).
+cudaError_t k_tri_tables(pfmbem* h, int l, const double2* m2l_v, int nm2l, const double2* shift_v, int nshift);
 cudaError_t k_wide_local(pfmbem* h);
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_rhs(pfmbem* h, cplx* B);

@@ -243,6 +243,87 @@ cudaError_t k_tables(pfmbem* h, const TableLevels& tl, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Triangle tree (Sec. 3.1, Fig. 5): the cells' centres are not on one grid, so
+// the operators are built for the list of offsets that occur, per level.
+// M2L, one block per offset v_o = target - source centre:
+//   T[o][a][n] = w_a H^+_{n-a}(k v_o) w_n   (the square tree's formula above).
+__global__ void tri_m2l_tables_kernel(const double2* __restrict__ v, int p, const double* __restrict__ w, double k,
+                                      cplx* __restrict__ T, int* __restrict__ bad) {
+  const int o = blockIdx.x, P = 2 * p + 1;
+  __shared__ double J[4 * PF_PMAX + 2], Y[4 * PF_PMAX + 2];
+  __shared__ cplx hv[4 * PF_PMAX + 1];
+  const double vx = v[o].x, vy = v[o].y;
+  const double r = sqrt(vx * vx + vy * vy), th = atan2(vy, vx);
+  bessel_jy_block(k * r, 2 * p, J, Y);
+  for (int j = threadIdx.x - 2 * p; j <= 2 * p; j += blockDim.x) {
+    const int aj = abs(j);
+    const double sg = (j < 0 && (aj & 1)) ? -1.0 : 1.0;
+    double sn, cs;
+    sincos(j * th, &sn, &cs);
+    const double hr = sg * J[aj], hi = sg * Y[aj];
+    hv[j + 2 * p] = cplx{hr * cs - hi * sn, hr * sn + hi * cs};
+  }
+  __syncthreads();
+  cplx* To = T + (size_t)o * P * P;
+  for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+    const int a = t / P, n = t % P;
+    const cplx hj = hv[n - a + 2 * p];
+    const double sc = w[a] * w[n];
+    const cplx val{sc * hj.re, sc * hj.im};
+    if (!isfinite(val.re) || !isfinite(val.im)) atomicExch(bad, 1);
+    To[t] = val;
+  }
+}
+
+// M2M and L2L, one block per child offset v_q = O_child - O_parent (zero for the
+// middle child of a triangle, whose centroid is its parent's):
+//   A[q][m][n] = J^-_{n-m}(k v) w^c_m / w^p_n,  B[q][m][n] = w^c_n J^+_{m-n}(k v) / w^p_m
+// (m child and n parent coefficient in A, m parent and n child in B).
+__global__ void tri_shift_tables_kernel(const double2* __restrict__ v, int p, int pc, const double* __restrict__ wp,
+                                        const double* __restrict__ wc, double k, cplx* __restrict__ A,
+                                        cplx* __restrict__ B) {
+  const int q = blockIdx.x, P = 2 * p + 1, Pc = 2 * pc + 1;
+  __shared__ double J[2 * PF_PMAX + 2], Y[2 * PF_PMAX + 2];
+  __shared__ cplx ej[4 * PF_PMAX + 3];            // J_j e^{i j theta}, j = -(p + pc) .. p + pc
+  const double vx = v[q].x, vy = v[q].y;
+  const double r = sqrt(vx * vx + vy * vy), th = r > 0 ? atan2(vy, vx) : 0.0;
+  bessel_jy_block(k * r, p + pc, J, Y);          // r = 0: J_n = delta_n0 (Y is not used)
+  const int jm = p + pc;
+  for (int j = (int)threadIdx.x - jm; j <= jm; j += blockDim.x) {
+    const int aj = abs(j);
+    const double Jj = (j < 0 && (aj & 1)) ? -J[aj] : J[aj];
+    double sn, cs;
+    sincos(j * th, &sn, &cs);
+    ej[j + jm] = cplx{Jj * cs, Jj * sn};
+  }
+  __syncthreads();
+  cplx* Aq = A + (size_t)q * Pc * P;
+  cplx* Bq = B + (size_t)q * P * Pc;
+  for (int t = threadIdx.x; t < P * Pc; t += blockDim.x) {
+    {
+      const int m = t / P - pc, n = t % P - p;       // A: [q][m + pc][n + p]
+      const cplx e = ej[n - m + jm];
+      const double sc = wc[m + pc] / wp[n + p];
+      Aq[t] = cplx{sc * e.re, -sc * e.im};
+    }
+    {
+      const int m = t / Pc - p, n = t % Pc - pc;     // B: [q][m + p][n + pc]
+      const cplx e = ej[m - n + jm];
+      const double sc = wc[n + pc] / wp[m + p];
+      Bq[t] = cplx{sc * e.re, sc * e.im};
+    }
+  }
+}
+
+cudaError_t k_tri_tables(pfmbem* h, int l, const double2* m2l_v, int nm2l, const double2* shift_v, int nshift) {
+  Level& L = h->lev[l];
+  if (nm2l > 0) tri_m2l_tables_kernel<<<nm2l, 256, 0, h->stream>>>(m2l_v, L.p, L.w_dev, h->k, L.m2l, h->tab_err);
+  if (nshift > 0)
+    tri_shift_tables_kernel<<<nshift, 256, 0, h->stream>>>(shift_v, L.p, h->lev[l + 1].p, L.w_dev,
+                                                           h->lev[l + 1].w_dev, h->k, L.m2m, L.l2l);
+  return cudaGetLastError();
+}
+
 // Periodic root translation (Sec. 3.3): R[a][n] = w_a S_{|n-a|} w_n, S_{-j} = S_j.
 __global__ void root_operator_kernel(int p0, const double* __restrict__ w, const cplx* __restrict__ S,
                                      cplx* __restrict__ R, cplxf* __restrict__ Rf, int* __restrict__ bad) {
@@ -328,7 +409,7 @@ __global__ void wide_x_kernel(int nr, int P0, int Ps, const cplx* __restrict__ R
 __global__ void wide_top_kernel(int nr, int p0, int Ps, int m0, double k, double H, cplx alpha,
                                 const double2* __restrict__ ctr, const double* __restrict__ w0,
                                 const cplx* __restrict__ B, const cplx* __restrict__ X, cplx* __restrict__ TOP,
-                                int* __restrict__ bad) {
+                                int* __restrict__ bad, const unsigned char* __restrict__ nbr) {
   const int i = blockIdx.x / nr, j = blockIdx.x % nr, P0 = 2 * p0 + 1, RS = nr * P0;
   const cplx* Bi = B + (size_t)i * Ps * P0;
   const cplx* Xj = X + (size_t)j * Ps * P0;
@@ -341,7 +422,9 @@ __global__ void wide_top_kernel(int nr, int p0, int Ps, int m0, double k, double
   __shared__ double J[4 * PF_PMAX + 2], Y[4 * PF_PMAX + 2];
   __shared__ cplx hv[4 * PF_PMAX + 1];
   for (int m = -(m0 - 1); m <= m0 - 1; ++m) {
-    if (abs(i - j) <= 1 && abs(m) <= 1) continue;      // neighbours: the tree's lists
+    // neighbours: the tree's lists (a row of squares: adjacent indices; otherwise
+    // the mask nbr[i][j][m + 1] over the images |m| <= 1)
+    if (abs(m) <= 1 && (nbr ? nbr[((size_t)i * nr + j) * 3 + m + 1] != 0 : abs(i - j) <= 1)) continue;
     const double vx = ctr[i].x - ctr[j].x, vy = ctr[i].y - ctr[j].y - m * H;
     const double r = sqrt(vx * vx + vy * vy), th = atan2(vy, vx);
     __syncthreads();
@@ -397,7 +480,7 @@ __global__ void wide_local_kernel(int nne0, const int* __restrict__ ne0, int P0,
 // dv: [2 nr] device: the roots' centres, then their shifts c_j - C; S [2 ps + 1] and
 // X [nr][Ps][P0] device scratch; the super root's weights, A, B, R_s and the
 // expansions' buffer are the handle's (allocated by the caller).
-cudaError_t k_wide_top(pfmbem* h, const double2* dv, cplx* S, cplx* X) {
+cudaError_t k_wide_top(pfmbem* h, const double2* dv, cplx* S, cplx* X, const unsigned char* nbr) {
   const int nr = h->nroot, p0 = h->lev[0].p, P0 = 2 * p0 + 1, ps = h->wide_ps, Ps = 2 * ps + 1;
   cudaStream_t st = h->stream;
   prof_begin(h, PH_SETUP);
@@ -409,7 +492,7 @@ cudaError_t k_wide_top(pfmbem* h, const double2* dv, cplx* S, cplx* X) {
   const size_t nx = (size_t)nr * Ps * P0;
   wide_x_kernel<<<(unsigned)((nx + 255) / 256), 256, 0, st>>>(nr, P0, Ps, h->wide_Rs, h->wide_A, X);
   wide_top_kernel<<<nr * nr, 256, 0, st>>>(nr, p0, Ps, h->wide_m0, h->k, h->H, h->alpha, dv, h->lev[0].w_dev,
-                                           h->wide_B, X, h->root, h->tab_err);
+                                           h->wide_B, X, h->root, h->tab_err, nbr);
   prof_end(h, PH_SETUP);
   return cudaGetLastError();
 }
@@ -783,19 +866,20 @@ __global__ void p2m_f64_kernel(const int* __restrict__ ne, const int* __restrict
                                double k, double eta, double x0, double y0,
                                const double2* __restrict__ sc, const double2* __restrict__ st,
                                const double2* __restrict__ snu, const double* __restrict__ sh,
-                               const cplx* __restrict__ dens, cplx* __restrict__ Mout) {
+                               const cplx* __restrict__ dens, cplx* __restrict__ Mout,
+                               const double2* __restrict__ ctr) {
   const int box = ne[blockIdx.x];
   const int P = 2 * p + 1;
   __shared__ double acc[2 * PF_NCOEF];
   for (int i = threadIdx.x; i < 2 * P; i += blockDim.x) acc[i] = 0.0;
   __syncthreads();
-  // box centre from the Morton code
+  // box centre: given (triangle tree), else from the Morton code
   int ix = (box >> (2 * D)) << D, iy = 0;       // root squares in a row along x, root-major
   for (int b = 0; b < D; ++b) {
     ix |= ((box >> (2 * b)) & 1) << b;
     iy |= ((box >> (2 * b + 1)) & 1) << b;
   }
-  const double ox = x0 + (ix + 0.5) * d, oy = y0 + (iy + 0.5) * d;
+  const double ox = ctr ? ctr[box].x : x0 + (ix + 0.5) * d, oy = ctr ? ctr[box].y : y0 + (iy + 0.5) * d;
   const int lb = bb[box], le = be[box];
   const int npts = (le - lb) * g;
   for (int t = threadIdx.x; t < npts; t += blockDim.x) {
@@ -834,20 +918,24 @@ __global__ void p2m_f64_kernel(const int* __restrict__ ne, const int* __restrict
 
 // ---------------------------------------------------------------- M2M (FP64)
 // M(parent) = sum_children A_q M(child), A_q[n][m] = J^-_{n-m}(k(O_child - O_parent)) w^c_m / w^p_n.
+// Children nch box + q, q < nch; the child's operator is q, or aidx[child] where
+// the children's offsets vary (triangle tree).
 __global__ void m2m_f64_kernel(const int* __restrict__ ne, int P, int Pc, const cplx* __restrict__ A,
                                const int* __restrict__ cbb, const int* __restrict__ cbe,
-                               const cplx* __restrict__ Mc, cplx* __restrict__ Mp) {
+                               const cplx* __restrict__ Mc, cplx* __restrict__ Mp, int nch,
+                               const int* __restrict__ aidx) {
   const int box = ne[blockIdx.x];
   __shared__ cplx sm[PF_NCOEF];
   cplx acc{0, 0};
-  for (int q = 0; q < 4; ++q) {
-    int ch = 4 * box + q;
+  for (int q = 0; q < nch; ++q) {
+    int ch = nch * box + q;
     if (cbb[ch] >= cbe[ch]) continue;   // empty child (uniform across the block)
     __syncthreads();
     for (int i = threadIdx.x; i < Pc; i += blockDim.x) sm[i] = Mc[(size_t)ch * Pc + i];
     __syncthreads();
     if (threadIdx.x < P) {
-      const cplx* col = A + (size_t)q * Pc * P + threadIdx.x;     // transposed [q][m][n]
+      const int op = aidx ? aidx[ch] : q;
+      const cplx* col = A + (size_t)op * Pc * P + threadIdx.x;    // transposed [op][m][n]
       for (int m = 0; m < Pc; ++m) acc += col[(size_t)m * P] * sm[m];
     }
   }
@@ -864,7 +952,8 @@ __global__ void local_f64_kernel(const int* __restrict__ ne, int D_unused, int P
                                  const int* __restrict__ ilp, const int* __restrict__ ils,
                                  const int* __restrict__ ilo, const int* __restrict__ ilm,
                                  const cplx* __restrict__ T, const cplx* __restrict__ Mlev,
-                                 const cplx* __restrict__ root, cplx alpha, cplx* __restrict__ Lout) {
+                                 const cplx* __restrict__ root, cplx alpha, cplx* __restrict__ Lout,
+                                 int nchp, const int* __restrict__ pidx) {
   const int ti = blockIdx.x;
   const int box = ne[ti];
   __shared__ cplx sm[PF_NCOEF];
@@ -878,9 +967,10 @@ __global__ void local_f64_kernel(const int* __restrict__ ne, int D_unused, int P
     if (l < P) Lout[l] = acc;
     return;
   }
-  // L2L from the parent
+  // L2L from the parent (nchp children per parent; the box's operator q, or
+  // pidx[box] where the children's offsets vary)
   {
-    int par = box >> 2, q = box & 3;
+    int par = box / nchp, q = pidx ? pidx[box] : box % nchp;
     for (int i = threadIdx.x; i < Pp; i += blockDim.x) sm[i] = Lp[(size_t)par * Pp + i];
     __syncthreads();
     if (l < P) {
@@ -909,7 +999,7 @@ __global__ void local_f64_kernel(const int* __restrict__ ne, int D_unused, int P
 __global__ void l2p_f64_kernel(const int* __restrict__ ne, const int* __restrict__ bb, const int* __restrict__ be,
                                int D, double d, int p, const double* __restrict__ wgt, double k,
                                double x0, double y0, const double2* __restrict__ sc, const double2* __restrict__ snu,
-                               const cplx* __restrict__ L, cplx* __restrict__ U) {
+                               const cplx* __restrict__ L, cplx* __restrict__ U, const double2* __restrict__ ctr) {
   const int box = ne[blockIdx.x];
   const int P = 2 * p + 1;
   __shared__ cplx sl[PF_NCOEF];
@@ -920,7 +1010,7 @@ __global__ void l2p_f64_kernel(const int* __restrict__ ne, const int* __restrict
     ix |= ((box >> (2 * b)) & 1) << b;
     iy |= ((box >> (2 * b + 1)) & 1) << b;
   }
-  const double ox = x0 + (ix + 0.5) * d, oy = y0 + (iy + 0.5) * d;
+  const double ox = ctr ? ctr[box].x : x0 + (ix + 0.5) * d, oy = ctr ? ctr[box].y : y0 + (iy + 0.5) * d;
   for (int s = bb[box] + threadIdx.x; s < be[box]; s += blockDim.x) {
     double2 c = sc[s], nu = snu[s];
     double vx = c.x - ox, vy = c.y - oy;
@@ -2176,7 +2266,10 @@ cudaError_t k_build_fmm_caches(pfmbem* h) {
 // ---------------------------------------------------------------- matvec driver
 
 // Gather the densities into tree order and run the upward pass (P2M, M2M)
-// and the periodic root translation.
+// and the periodic root translation.  Triangle tree: P2M at the leaf
+// triangles' centroids and M2M up to the hexagonal cells (six children each at
+// level 0); their local expansions come from the operator between the cells
+// (top_apply_kernel, in the product).
 static void upward_f64(pfmbem* h, const cplx* x) {
   cudaStream_t st = h->stream;
   const int E = h->E, D = h->D;
@@ -2187,15 +2280,17 @@ static void upward_f64(pfmbem* h, const cplx* x) {
   prof_begin(h, PH_P2M);
   p2m_f64_kernel<<<leaf.nne, 128, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, D, leaf.d, leaf.p, leaf.w_dev,
                                             h->g_far, h->k, h->eta, h->x0, h->y0, h->s_c, h->s_t, h->s_nu, h->s_h,
-                                            h->dens, leaf.M);
+                                            h->dens, leaf.M, leaf.ctr);
   prof_end(h, PH_P2M);
   for (int l = D - 1; l >= 0; --l) {
     Level& a = h->lev[l];
     Level& c = h->lev[l + 1];
     prof_begin(h, PH_M2M);
-    m2m_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, c.P, a.m2m, c.box_begin, c.box_end, c.M, a.M);
+    m2m_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, c.P, a.m2m, c.box_begin, c.box_end, c.M, a.M,
+                                                   h->tree == 1 && l == 0 ? 6 : 4, c.pidx);
     prof_end(h, PH_M2M);
   }
+  if (h->tree == 1) return;
   cplx alpha = h->alpha;
   if (h->nroot > 1) {
     // a row of roots: the super root's local expansion of the images |m| >= m0
@@ -2208,9 +2303,24 @@ static void upward_f64(pfmbem* h, const cplx* x) {
     Level& r = h->lev[0];
     prof_begin(h, PH_LOCAL);
     local_f64_kernel<<<1, round32(r.P), 0, st>>>(r.ne, 0, r.P, 0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                                 nullptr, r.M, h->root, alpha, r.L);
+                                                 nullptr, r.M, h->root, alpha, r.L, 4, nullptr);
     prof_end(h, PH_LOCAL);
   }
+}
+
+// Local expansions of all top cells at once: L0 = TOP M0, TOP [n P0][n P0] the
+// operator between every pair of top cells (explicit M2L of the images the
+// tree's lists leave out, and the super root's lattice sums for the rest).
+// One warp per row.
+__global__ void top_apply_kernel(int rows, const cplx* __restrict__ TOP, const cplx* __restrict__ M0,
+                                 cplx* __restrict__ L0) {
+  const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= rows) return;
+  const cplx* t = TOP + (size_t)row * rows;
+  cplx acc{0, 0};
+  for (int c = lane; c < rows; c += 32) acc += t[c] * M0[c];
+  acc = warp_sum(acc);
+  if (lane == 0) L0[row] = acc;
 }
 
 // FP64 near-field blocks as hi + lo of the double-float pair: the set-up keeps
@@ -2252,17 +2362,25 @@ cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision) {
   Level& leaf = h->lev[D];
   const cplx alpha = h->alpha;
   upward_f64(h, x);
+  if (h->tree == 1) {
+    // the hexagonal cells' local expansions from all cells' multipoles
+    const int rows = h->nroot * h->lev[0].P;
+    prof_begin(h, PH_LOCAL);
+    top_apply_kernel<<<(rows * 32 + 255) / 256, 256, 0, st>>>(rows, h->root, h->lev[0].M, h->lev[0].L);
+    prof_end(h, PH_LOCAL);
+  }
   for (int l = 1; l <= D; ++l) {
     Level& a = h->lev[l];
     Level& pa = h->lev[l - 1];
     prof_begin(h, PH_LOCAL);
     local_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, 0, a.P, pa.P, pa.l2l, pa.L, a.il_ptr, a.il_src, a.il_off,
-                                                     a.il_img, a.m2l, a.M, nullptr, alpha, a.L);
+                                                     a.il_img, a.m2l, a.M, nullptr, alpha, a.L,
+                                                     h->tree == 1 && l == 1 ? 6 : 4, a.pidx);
     prof_end(h, PH_LOCAL);
   }
   prof_begin(h, PH_L2P);
   l2p_f64_kernel<<<leaf.nne, 64, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, D, leaf.d, leaf.p, leaf.w_dev, h->k,
-                                          h->x0, h->y0, h->s_c, h->s_nu, leaf.L, h->U);
+                                          h->x0, h->y0, h->s_c, h->s_nu, leaf.L, h->U, leaf.ctr);
   prof_end(h, PH_L2P);
   cplx c2{h->c2re, h->c2im};
   prof_begin(h, PH_NEAR);
@@ -2491,6 +2609,12 @@ __global__ void field_kernel(int npts, const double2* __restrict__ pts, int E, d
 
 cudaError_t k_field_prepare(pfmbem* h, const cplx* psi) {
   upward_f64(h, psi);
+  if (h->tree == 1) {
+    // the super root's local expansion of the images |m| >= m0
+    prof_begin(h, PH_LOCAL);
+    k_wide_local(h);
+    prof_end(h, PH_LOCAL);
+  }
   return cudaGetLastError();
 }
 

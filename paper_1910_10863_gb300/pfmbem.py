@@ -25,7 +25,9 @@ class Options(ctypes.Structure):
                 ("leaf_max", ctypes.c_int), ("depth", ctypes.c_int), ("gmres_m", ctypes.c_int),
                 ("precision", ctypes.c_int), ("near_mode", ctypes.c_int), ("m2l_mode", ctypes.c_int),
                 ("profile", ctypes.c_int), ("launch", ctypes.c_int), ("precond", ctypes.c_int),
-                ("wait_us", ctypes.c_int), ("p_min_mixed", ctypes.c_int), ("batch_group", ctypes.c_int)]
+                ("wait_us", ctypes.c_int), ("p_min_mixed", ctypes.c_int), ("batch_group", ctypes.c_int),
+                ("tree", ctypes.c_int), ("tri_a", ctypes.c_double), ("tri_ox", ctypes.c_double),
+                ("tri_oy", ctypes.c_double)]
 
 
 class Info(ctypes.Structure):

@@ -2,6 +2,7 @@
 
     python -m paper_1910_10863_gb300.profile_products --workload hexagon_8x8_n256 --reps 3
     python -m paper_1910_10863_gb300.profile_products --sweep 32
+    python -m paper_1910_10863_gb300.profile_products --trees
 
 The first form creates the block's handle and runs --reps pairs of products
 (FP32 mixed, then FP64) on a device vector; the second solves a chunk of
@@ -41,6 +42,60 @@ def products(workload: str, reps: int) -> dict:
     return out
 
 
+def trees(reps: int, solve: bool = True) -> dict:
+    """The square and the regular-triangle tree on the 8x8 hexagon block: the FP64
+    product with the element integrals computed in every product (the form the
+    triangle tree runs), its difference from the square tree's cached FP64
+    product, and each tree's FP64 solve to 1e-6."""
+    import time
+
+    import torch
+    w = W.hexagon_8x8_n256()
+    lat = W.hexagon_block_lattice(w.H, 8)
+    n = 2 * w.E
+    x = torch.randn(n, dtype=torch.complex128, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    ref = torch.zeros_like(x)
+    cached = pf.Solver(w)
+    pf.pfmbem_matvec(cached.h, x.data_ptr(), ref.data_ptr(), pf.FP64)
+    torch.cuda.synchronize()
+    out = {"workload": w.name, "elements": int(w.E)}
+    for name, opts in (("square", {"near_mode": 1}), ("triangle", dict(tree=1, leaf_max=16, **lat))):
+        t0 = time.perf_counter()
+        s = pf.Solver(w, **opts)
+        torch.cuda.synchronize()
+        create_s = time.perf_counter() - t0
+        pl = s.plan()
+        y = torch.zeros_like(x)
+        times = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            a.record()
+            pf.pfmbem_matvec(s.h, x.data_ptr(), y.data_ptr(), pf.FP64)
+            b.record()
+            torch.cuda.synchronize()
+            times.append(a.elapsed_time(b))
+        r = {"create_s": create_s, "depth": pl.depth, "p": list(pl.p)[:pl.depth + 1], "m2l_pairs": pl.m2l_pairs,
+             "near_pairs": pl.near_pairs, "near_quad": pl.near_quad, "fp64_onthefly_ms": times,
+             "rel_diff_vs_cached_square": float(torch.linalg.vector_norm(y - ref) / torch.linalg.vector_norm(ref))}
+        if name == "triangle":
+            r["cells"] = pl.nroot
+            r["super_p"] = pl.super_p
+        if solve:
+            psi = torch.zeros_like(x)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            info = s.solve(psi, tol=1e-6, maxit=2000)
+            torch.cuda.synchronize()
+            r["solve_s"] = time.perf_counter() - t0
+            r["solve_iters"] = info.iters
+            r["solve_rel_residual"] = info.rel_residual
+        out[name] = r
+        s.close()
+    cached.close()
+    return out
+
+
 def sweep(count: int) -> dict:
     import time
 
@@ -62,7 +117,12 @@ def main():
                                                                        "square_2x2_n64"])
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--sweep", type=int, default=0, help="solve this many sweep instances in one batched launch")
+    ap.add_argument("--trees", action="store_true",
+                    help="square against regular-triangle tree on the 8x8 hexagon block (FP64 products and solves)")
     a = ap.parse_args()
+    if a.trees:
+        print(json.dumps(trees(a.reps)), flush=True)
+        return
     print(json.dumps(sweep(a.sweep) if a.sweep > 0 else products(a.workload, a.reps)), flush=True)
 
 

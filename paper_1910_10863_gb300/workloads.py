@@ -158,6 +158,13 @@ def hexagon_block(ncol: int, nrow: int, H: float, n: int, kH: float, theta: floa
     return _from_fibers(name or f"hexagon_{ncol}x{nrow}_n{n}_kH{kH:g}", H, 1, kH, theta, centres, radii, npf)
 
 
+def hexagon_block_lattice(H: float, nrow: int) -> dict:
+    """The hexagonal lattice of hexagon_block (spacing a = H/nrow, one lattice vector
+    along y, the point of column 0, row 0), as the triangle tree's options."""
+    a = H / nrow
+    return {"tri_a": a, "tri_ox": 0.5 * a * math.sqrt(3.0) / 2.0, "tri_oy": 0.5 * a}
+
+
 def hexagon_8x8_n256(seed: int = 1911) -> Workload:
     """Hexagon lattice, 8x8 = 64 fibers, radii in [0.1,0.3]*spacing with jitter, 256
     elements each (16384 elements, 32768 unknowns), kH = 5, theta uniform in

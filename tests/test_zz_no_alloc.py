@@ -90,3 +90,38 @@ def test_noalloc_largest_order_and_rejections():
             with pytest.raises(pf.PfmbemError) as e:
                 pf.pfmbem_lattice_sums_noalloc(2.0, 1.0, 0.5, 10, other)
         assert e.value.status == 1
+
+
+def test_noalloc_in_a_captured_graph():
+    """After a first call on the device, a device-output call can be captured into
+    a CUDA graph; its replays reproduce the handle path and take no device memory."""
+    ensure_built()
+    import torch
+
+    from paper_1910_10863_gb300 import pfmbem as pf
+    kH, theta, jmax = 5.0, 0.3, 40
+    k, H, ref = _handle_sums(pf, kH, theta, jmax)
+    dev = torch.zeros(2 * jmax + 1, dtype=torch.complex128, device="cuda")
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):                     # first call, outside the capture
+        pf.pfmbem_lattice_sums_noalloc(k, H, theta, jmax, dev, stream=side.cuda_stream)
+    torch.cuda.synchronize()
+    dev.zero_()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        pf.pfmbem_lattice_sums_noalloc(k, H, theta, jmax, dev, stream=torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    assert not bool(dev.abs().max() > 0)              # captured, not run
+    scale = np.max(np.abs(ref))
+    g.replay()
+    torch.cuda.synchronize()
+    assert np.max(np.abs(dev.cpu().numpy() - ref)) <= 1e-10 * scale
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(3):
+        dev.zero_()
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert np.max(np.abs(dev.cpu().numpy() - ref)) <= 1e-10 * scale
+    del g
