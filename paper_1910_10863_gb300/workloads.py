@@ -165,6 +165,13 @@ def hexagon_block_lattice(H: float, nrow: int) -> dict:
     return {"tri_a": a, "tri_ox": 0.5 * a * math.sqrt(3.0) / 2.0, "tri_oy": 0.5 * a}
 
 
+def table3_hexagon_lattice() -> dict:
+    """The hexagonal lattice of table3_block(lattice="hexagon") (a = 0.5, the point
+    of column 0, row 0), as the triangle tree's options."""
+    a = 0.5
+    return {"tri_a": a, "tri_ox": 0.5 * a * math.sqrt(3.0) / 2.0, "tri_oy": 0.25 * a}
+
+
 def hexagon_8x8_n256(seed: int = 1911) -> Workload:
     """Hexagon lattice, 8x8 = 64 fibers, radii in [0.1,0.3]*spacing with jitter, 256
     elements each (16384 elements, 32768 unknowns), kH = 5, theta uniform in

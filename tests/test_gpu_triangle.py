@@ -136,3 +136,23 @@ def test_triangle_tree_rejections(pf):
     st, _ = pf.pfmbem_solve_batch([s.h], [psi], 1e-6, 100)
     assert st == 1
     s.close()
+
+
+@pytest.mark.parametrize("fill,ka,stop", [(0.35, 0.45, True), (0.35, 0.12, False), (0.50, 0.52, True),
+                                          (0.50, 0.12, False)])
+def test_triangle_tree_table3_hexagon_rows(pf, fill, ka, stop):
+    """Table 3's circular scatterers in the hexagon lattice, solved on the tree the
+    paper builds for that lattice: ETC on the block's right edge equals the square
+    tree's to 1e-6, below 3 % inside the first stop band and above it below."""
+    w = W.table3_block(ka, fill, "hexagon", "circular")
+    x1 = 4 * 0.5 * 3 ** 0.5 / 2
+    etc = []
+    for opts in (dict(tree=1, **W.table3_hexagon_lattice()), {}):
+        s = pf.Solver(w, **opts)
+        psi = np.zeros(2 * s.E, dtype=np.complex128)
+        info = s.solve(psi, tol=1e-9, maxit=3000)
+        assert info.rel_residual <= 1e-9
+        etc.append(pf.pfmbem_etc(s.h, psi, x1, 256))
+        s.close()
+    assert abs(etc[0] - etc[1]) < 1e-6, etc
+    assert (etc[0] < 0.03) == stop, etc
