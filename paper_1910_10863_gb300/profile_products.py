@@ -42,7 +42,7 @@ def products(workload: str, reps: int) -> dict:
     return out
 
 
-def trees(reps: int, solve: bool = True) -> dict:
+def trees(reps: int, solve: bool = True, only: str | None = None) -> dict:
     """The square and the regular-triangle tree on the 8x8 hexagon block: the FP64
     product with the element integrals computed in every product (the form the
     triangle tree runs), its difference from the square tree's cached FP64
@@ -60,6 +60,8 @@ def trees(reps: int, solve: bool = True) -> dict:
     torch.cuda.synchronize()
     out = {"workload": w.name, "elements": int(w.E)}
     for name, opts in (("square", {"near_mode": 1}), ("triangle", dict(tree=1, leaf_max=16, **lat))):
+        if only is not None and name != only:
+            continue
         t0 = time.perf_counter()
         s = pf.Solver(w, **opts)
         torch.cuda.synchronize()
@@ -119,9 +121,11 @@ def main():
     ap.add_argument("--sweep", type=int, default=0, help="solve this many sweep instances in one batched launch")
     ap.add_argument("--trees", action="store_true",
                     help="square against regular-triangle tree on the 8x8 hexagon block (FP64 products and solves)")
+    ap.add_argument("--only", choices=["square", "triangle"], help="with --trees: one tree")
+    ap.add_argument("--no-solve", action="store_true", help="with --trees: products only")
     a = ap.parse_args()
     if a.trees:
-        print(json.dumps(trees(a.reps)), flush=True)
+        print(json.dumps(trees(a.reps, solve=not a.no_solve, only=a.only)), flush=True)
         return
     print(json.dumps(sweep(a.sweep) if a.sweep > 0 else products(a.workload, a.reps)), flush=True)
 
