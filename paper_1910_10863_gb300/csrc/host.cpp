@@ -784,6 +784,28 @@ static pfmbem_status on_aux(pfmbem* h, int i, F&& f) {
   return PFMBEM_OK;
 }
 
+// Regular polygon (equal chords, equal turning angles) of n elements from f0:
+// rotating by one element maps the fiber onto itself.
+static bool regular_polygon(const std::vector<double>& len, const std::vector<double2>& t, int f0, int n) {
+  double hm = 0;
+  for (int e = f0; e < f0 + n; ++e) hm += len[e];
+  hm /= n;
+  // the turn between consecutive unit tangents, as its (sine, cosine)
+  double sn0 = 0, cs0 = 0;
+  for (int q = 0; q < n; ++q) {
+    const int e = f0 + q, e1 = q + 1 < n ? e + 1 : f0;
+    if (std::fabs(len[e] - hm) > 1e-12 * hm) return false;
+    const double sn = t[e].x * t[e1].y - t[e].y * t[e1].x, cs = t[e].x * t[e1].x + t[e].y * t[e1].y;
+    if (q == 0) {
+      sn0 = sn;
+      cs0 = cs;
+    } else if (std::fabs(sn - sn0) > 1e-12 || std::fabs(cs - cs0) > 1e-12) {
+      return false;
+    }
+  }
+  return true;
+}
+
 #include "tri_plan.h"
 
 static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) {
@@ -1320,30 +1342,9 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
     std::vector<int> chunks, circ(M, 0);
     int64_t acc = 0;
     for (int i = 0; i < M; ++i) {
-      // regular polygon (equal chords, equal turning angles): rotating by one
-      // element maps the fiber onto itself, so its block is circulant and is
-      // stored as the row pair of its first element
-      {
-        const int f0 = foff[i], n = foff[i + 1] - f0;
-        double hm = 0;
-        for (int e = f0; e < f0 + n; ++e) hm += len[e];
-        hm /= n;
-        // the turn between consecutive unit tangents, as its (sine, cosine)
-        bool reg = true;
-        double sn0 = 0, cs0 = 0;
-        for (int q = 0; q < n && reg; ++q) {
-          const int e = f0 + q, e1 = q + 1 < n ? e + 1 : f0;
-          if (std::fabs(len[e] - hm) > 1e-12 * hm) reg = false;
-          const double sn = t[e].x * t[e1].y - t[e].y * t[e1].x, cs = t[e].x * t[e1].x + t[e].y * t[e1].y;
-          if (q == 0) {
-            sn0 = sn;
-            cs0 = cs;
-          } else if (std::fabs(sn - sn0) > 1e-12 || std::fabs(cs - cs0) > 1e-12) {
-            reg = false;
-          }
-        }
-        circ[i] = reg ? 1 : 0;
-      }
+      // regular polygon: its block is circulant and is stored as the row pair of
+      // its first element
+      circ[i] = regular_polygon(len, t, foff[i], foff[i + 1] - foff[i]) ? 1 : 0;
       fbase[i] = acc;
       const int n2 = 2 * (foff[i + 1] - foff[i]);
       acc += circ[i] ? (int64_t)2 * n2 : (int64_t)n2 * n2;

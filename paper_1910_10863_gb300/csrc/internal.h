@@ -159,6 +159,7 @@ struct pfmbem {
   int nroot = 1;                 // root squares of side H in a row along x (block width up to nroot H);
                                  // triangle tree: the hexagonal cells, one per fiber
   int tree = 0;                  // 0 = square quadtree, 1 = regular-triangle quadtree (hexagon lattices)
+  bool tri_cache = false;        // triangle tree: element integrals and P2M/L2P coefficients cached
   double field_hw = 0;           // triangle tree: half the block's width along x (field point check)
   double x0 = 0, y0 = 0;
   Level lev[PF_MAXLEVEL + 1];
@@ -437,6 +438,9 @@ cudaError_t k_wide_top(pfmbem* h, const double2* dv, cplx* S, cplx* X, const uns
 // Triangle tree: level l's M2L operators for nm2l offsets (target - source
 // centre) and its M2M/L2L operators for nshift child offsets (child - parent).
 cudaError_t k_tri_tables(pfmbem* h, int l, const double2* m2l_v, int nm2l, const double2* shift_v, int nshift);
+// Triangle tree: the cached FP64 product's tables (P2M/L2P coefficients at the
+// leaves' centroids, near-field and same-fiber blocks).
+cudaError_t k_tri_caches(pfmbem* h);
 cudaError_t k_wide_local(pfmbem* h);
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_rhs(pfmbem* h, cplx* B);

@@ -978,8 +978,8 @@ __global__ void local_f64_kernel(const int* __restrict__ ne, int D_unused, int P
       for (int m = 0; m < Pp; ++m) acc += col[(size_t)m * P] * sm[m];
     }
   }
-  // M2L
-  for (int e = ilp[ti]; e < ilp[ti + 1]; ++e) {
+  // M2L (none without lists: the caller adds it by offset groups)
+  for (int e = ilp ? ilp[ti] : 0; ilp && e < ilp[ti + 1]; ++e) {
     int src = ils[e], off = ilo[e];
     cplx ph = ipow_phase(alpha, ilm[e]);
     __syncthreads();
@@ -1680,7 +1680,7 @@ __global__ void p2m_coef_kernel(int E, const int* __restrict__ sleaf, int D, dou
                                 const double* __restrict__ iwgt, int g, double k, double eta, double x0, double y0,
                                 const double2* __restrict__ sc, const double2* __restrict__ st,
                                 const double2* __restrict__ snu, const double* __restrict__ sh,
-                                cplx* __restrict__ out) {
+                                cplx* __restrict__ out, const double2* __restrict__ ctr) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   // g a power of two: the g nodes of an element are g consecutive lanes of one
   // warp, whose sums meet by shuffles (every lane takes part; lanes past the end
@@ -1693,6 +1693,10 @@ __global__ void p2m_coef_kernel(int E, const int* __restrict__ sleaf, int D, dou
   const int P = 2 * p + 1;
   double ox, oy;
   morton_centre(sleaf[s], D, d, x0, y0, ox, oy);
+  if (ctr) {                                       // leaf centres given (triangle tree)
+    ox = ctr[sleaf[s]].x;
+    oy = ctr[sleaf[s]].y;
+  }
   const double2 c = sc[s], tt = st[s], nu = snu[s];
   const double hh = sh[s];
   const cplx nuc{nu.x, nu.y};
@@ -1761,12 +1765,16 @@ __global__ void to_f32_kernel(size_t n, const cplx* __restrict__ a, cplxf* __res
 __global__ void l2p_coef_kernel(int E, const int* __restrict__ sleaf, int D, double d, int p,
                                 const double* __restrict__ iwgt, double k, double x0, double y0,
                                 const double2* __restrict__ sc, const double2* __restrict__ snu,
-                                cplx* __restrict__ out, cplxf* __restrict__ outf) {
+                                cplx* __restrict__ out, cplxf* __restrict__ outf, const double2* __restrict__ ctr) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= E) return;
   const int P = 2 * p + 1;
   double ox, oy;
   morton_centre(sleaf[s], D, d, x0, y0, ox, oy);
+  if (ctr) {                                       // leaf centres given (triangle tree)
+    ox = ctr[sleaf[s]].x;
+    oy = ctr[sleaf[s]].y;
+  }
   const double2 c = sc[s], nu = snu[s];
   const double vx = c.x - ox, vy = c.y - oy;
   const double r = sqrt(vx * vx + vy * vy);
@@ -2247,7 +2255,7 @@ cudaError_t k_build_fmm_caches(pfmbem* h) {
   prof_begin(h, PH_SETUP);
   p2m_coef_kernel<<<(h->E * h->g_far + 127) / 128, 128, 0, h->stream>>>(
       h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.iw_dev, h->g_far, h->k, h->eta, h->x0, h->y0, h->s_c, h->s_t,
-      h->s_nu, h->s_h, h->p2m_c);
+      h->s_nu, h->s_h, h->p2m_c, nullptr);
   prof_end(h, PH_SETUP);
   prof_begin(h, PH_SETUP);
   to_f32_kernel<<<std::min<size_t>((nc + 255) / 256, 4096), 256, 0, h->stream>>>(nc, h->p2m_c, h->p2m_cf,
@@ -2255,7 +2263,8 @@ cudaError_t k_build_fmm_caches(pfmbem* h) {
   prof_end(h, PH_SETUP);
   prof_begin(h, PH_SETUP);
   l2p_coef_kernel<<<(h->E + 127) / 128, 128, 0, h->stream>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.iw_dev, h->k,
-                                                             h->x0, h->y0, h->s_c, h->s_nu, h->l2p_c, h->l2p_cf);
+                                                             h->x0, h->y0, h->s_c, h->s_nu, h->l2p_c, h->l2p_cf,
+                                                             nullptr);
   if (h->l2p_cl)
     to_f32_kernel<<<std::min<size_t>((nc + 255) / 256, 4096), 256, 0, h->stream>>>(nc, h->l2p_c, h->l2p_cf,
                                                                                    h->l2p_cl);
@@ -2348,7 +2357,89 @@ cudaError_t k_near64(pfmbem* h) {
   return cudaGetLastError();
 }
 
+// Triangle tree, cached FP64 product: the square tree's cached tables where they
+// are tree-independent (P2M/L2P coefficients at the leaves' centroids, near-field
+// and same-fiber blocks, M2L by offset groups), and M2M/L2L with the per-box
+// operators of the triangles.
+static cudaError_t matvec_tri_cached(pfmbem* h, const cplx* x, cplx* y) {
+  cudaStream_t st = h->stream;
+  const int E = h->E, D = h->D;
+  Level& leaf = h->lev[D];
+  const cplx alpha = h->alpha;
+  cudaError_t e = k_near64(h);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, PH_GATHER);
+  gather_dens_kernel<<<(E + 255) / 256, 256, 0, st>>>(E, h->s_perm, h->s_ph, x, h->dens);
+  prof_end(h, PH_GATHER);
+  prof_begin(h, PH_P2M);
+  p2m_apply_t_kernel<cplx><<<leaf.nne, round32(leaf.P), 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P,
+                                                                 h->p2m_c, h->dens, leaf.M);
+  prof_end(h, PH_P2M);
+  for (int l = D - 1; l >= 0; --l) {
+    Level& a = h->lev[l];
+    Level& c = h->lev[l + 1];
+    prof_begin(h, PH_M2M);
+    m2m_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, c.P, a.m2m, c.box_begin, c.box_end, c.M, a.M,
+                                                   l == 0 ? 6 : 4, c.pidx);
+    prof_end(h, PH_M2M);
+  }
+  const int rows = h->nroot * h->lev[0].P;
+  prof_begin(h, PH_LOCAL);
+  top_apply_kernel<<<(rows * 32 + 255) / 256, 256, 0, st>>>(rows, h->root, h->lev[0].M, h->lev[0].L);
+  prof_end(h, PH_LOCAL);
+  for (int l = 1; l <= D; ++l) {
+    Level& a = h->lev[l];
+    Level& pa = h->lev[l - 1];
+    prof_begin(h, PH_LOCAL);
+    local_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, 0, a.P, pa.P, pa.l2l, pa.L, nullptr, nullptr, nullptr,
+                                                     nullptr, nullptr, a.M, nullptr, alpha, a.L, l == 1 ? 6 : 4,
+                                                     a.pidx);
+    if (a.nchunk > 0) {
+      const int nwarp = 8;
+      const size_t smem = sizeof(cplx) * ((size_t)a.P * (a.P + 1) + (size_t)nwarp * a.P);
+      if (smem > 48 * 1024)
+        cudaFuncSetAttribute(m2l_offset_t_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      m2l_offset_t_kernel<cplx><<<a.nchunk, 32 * nwarp, smem, st>>>(a.P, a.ch_off, a.ch_beg, a.ch_end, a.pr_tgt,
+                                                                     a.pr_src, a.pr_img, a.m2l, a.M, alpha, a.L);
+    }
+    prof_end(h, PH_LOCAL);
+  }
+  prof_begin(h, PH_L2P);
+  l2p_apply_t_kernel<cplx><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P, E, h->l2p_c,
+                                                     leaf.L, h->U);
+  prof_end(h, PH_L2P);
+  prof_begin(h, PH_NEAR);
+  near_apply_t_kernel<cplx><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, h->nc_base, h->nc_sbase,
+                                                      h->nc_src, h->nc_val, h->dens, h->U);
+  prof_end(h, PH_NEAR);
+  cplx c2{h->c2re, h->c2im};
+  prof_begin(h, PH_FIBER);
+  fiber_apply_t_kernel<cplx><<<h->nchunk, 256, 0, st>>>(h->fb_chunk, h->fib_off, h->fb_base, h->fb_val, h->o_pos,
+                                                        h->s_ph, c2, x, h->U, y, h->fb_circ);
+  prof_end(h, PH_FIBER);
+  return cudaGetLastError();
+}
+
+cudaError_t k_tri_caches(pfmbem* h) {
+  cudaStream_t st = h->stream;
+  Level& leaf = h->lev[h->D];
+  const size_t nc = (size_t)h->E * 2 * leaf.P;
+  cudaError_t e = cudaMemsetAsync(h->p2m_c, 0, nc * sizeof(cplx), st);
+  if (e != cudaSuccess) return e;
+  prof_begin(h, PH_SETUP);
+  p2m_coef_kernel<<<(h->E * h->g_far + 127) / 128, 128, 0, st>>>(
+      h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.iw_dev, h->g_far, h->k, h->eta, h->x0, h->y0, h->s_c, h->s_t,
+      h->s_nu, h->s_h, h->p2m_c, leaf.ctr);
+  l2p_coef_kernel<<<(h->E + 127) / 128, 128, 0, st>>>(h->E, h->s_leaf, h->D, leaf.d, leaf.p, leaf.iw_dev, h->k, h->x0,
+                                                      h->y0, h->s_c, h->s_nu, h->l2p_c, nullptr, leaf.ctr);
+  prof_end(h, PH_SETUP);
+  e = k_build_caches(h, nullptr);
+  if (e != cudaSuccess) return e;
+  return k_build_fiber_blocks(h);
+}
+
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision) {
+  if (h->tree == 1 && h->tri_cache) return matvec_tri_cached(h, x, y);
   if (h->cached && h->fused) return k_matvec_fused(h, x, y, precision);
   if (h->cached) {
     if (precision == PFMBEM_MIXED) return matvec_cached(h, x, y, ops32(h));

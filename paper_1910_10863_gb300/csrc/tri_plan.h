@@ -18,9 +18,12 @@
 // |m| < m0 and a super root over the block whose lattice sums (Sec. 3.3) take
 // the images |m| >= m0 (the operator of the blocks wider than H, k_wide_top).
 //
-// The tree drives the FP64 product computed in every matrix-vector product
-// (the element integrals of the near field included), the single solve and the
-// outputs; the cached products and the batched solver stay with the square tree.
+// The tree drives an FP64 product, the single solve and the outputs.  The
+// product applies tables built once here where they do not depend on the tree's
+// shape (near-field and same-fiber blocks, P2M/L2P coefficients at the leaves'
+// centroids, M2L by offset groups); with near_mode 1 it integrates the element
+// integrals in every product instead.  The mixed-precision single-launch
+// products and the batched solver stay with the square tree.
 
 struct TriBox {
   double2 v[3];
@@ -267,7 +270,7 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
     const double tol = 1e-6 * side;
     m2l_off[l].quantum = 1e-7 * side;
     std::vector<std::vector<std::pair<int, int>>> nb(L.nbox);
-    std::vector<int> ptr(1, 0), src, off, img;
+    std::vector<int> ptr(1, 0), src, off, img, tgt;
     for (int b : L.hne) {
       const int par = b / nch;
       for (const auto& pm : nb_prev[par]) {
@@ -281,6 +284,7 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
           } else {
             src.push_back(cb);
             img.push_back(m);
+            tgt.push_back(b);
             off.push_back(m2l_off[l].get(double2{ctr[l][b].x - ctr[l][cb].x, ctr[l][b].y - ctr[l][cb].y - m * H}));
           }
         }
@@ -302,6 +306,33 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
     if ((st = upload(h, &L.il_src, src)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.il_off, off)) != PFMBEM_OK) return st;
     if ((st = upload(h, &L.il_img, img)) != PFMBEM_OK) return st;
+    {
+      // the same pairs grouped by offset, in chunks of at most 16 pairs (the
+      // cached product stages one operator per chunk)
+      std::vector<int> order(src.size());
+      for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+      std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return off[x] < off[y]; });
+      std::vector<int> ptg, psr, pim, cof, cbg, cen;
+      for (size_t i = 0; i < order.size(); ++i) {
+        const int q = order[i];
+        if (cof.empty() || cof.back() != off[q] || (int)ptg.size() - cbg.back() >= 16) {
+          if (!cof.empty()) cen.push_back((int)ptg.size());
+          cof.push_back(off[q]);
+          cbg.push_back((int)ptg.size());
+        }
+        ptg.push_back(tgt[q]);
+        psr.push_back(src[q]);
+        pim.push_back(img[q]);
+      }
+      if (!cof.empty()) cen.push_back((int)ptg.size());
+      L.nchunk = (int)cof.size();
+      if ((st = upload(h, &L.pr_tgt, ptg)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.pr_src, psr)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.pr_img, pim)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.ch_off, cof)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.ch_beg, cbg)) != PFMBEM_OK) return st;
+      if ((st = upload(h, &L.ch_end, cen)) != PFMBEM_OK) return st;
+    }
     nb_prev.swap(nb);
   }
   h->info.m2l_pairs = m2l_pairs;
@@ -339,6 +370,94 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
         }
     h->info.fiber_pairs = pairs;
     h->info.fiber_quad = quad;
+  }
+  // ---------------------------------------------------- cached element integrals
+  // As the square tree's: per leaf its concatenated near sources and a dense
+  // [targets][sources] array of 2x2 blocks; the same-fiber blocks (a row pair
+  // for a regular polygon, whose block is circulant); P2M/L2P coefficients.
+  // Without room (or with near_mode 1) the product integrates them every time.
+  std::vector<int64_t> nc_base, fbase(M, 0), kbase(M, -1);
+  std::vector<int> nc_sbase(1, 0), chunks, circ(M, 0), rows;
+  int64_t fb_acc = 0, kacc = 0;
+  {
+    const Level& Lf = h->lev[D];
+    int64_t acc = 0;
+    for (size_t li = 0; li < Lf.hne.size(); ++li) {
+      const int b = Lf.hne[li];
+      int ns = 0;
+      for (int e = nl_ptr[li]; e < nl_ptr[li + 1]; ++e) ns += Lf.hend[nl_src[e]] - Lf.hbegin[nl_src[e]];
+      nc_sbase.push_back(nc_sbase.back() + ns);
+      h->nc_maxns = std::max(h->nc_maxns, ns);
+      h->leaf_maxn = std::max(h->leaf_maxn, Lf.hend[b] - Lf.hbegin[b]);
+      nc_base.push_back(acc);
+      acc += 4 * (int64_t)(Lf.hend[b] - Lf.hbegin[b]) * ns;
+    }
+    h->nc_blocks = acc / 4;
+    for (int i = 0; i < M; ++i) {
+      const int n = foff[i + 1] - foff[i], n2 = 2 * n;
+      circ[i] = regular_polygon(len, t, foff[i], n) ? 1 : 0;
+      fbase[i] = fb_acc;
+      fb_acc += circ[i] ? (int64_t)2 * n2 : (int64_t)n2 * n2;
+      for (int r = 0; r < n2; r += 32) {
+        chunks.push_back(i);
+        chunks.push_back(r);
+        chunks.push_back(std::min(r + 32, n2));
+      }
+      for (int e = foff[i]; e < (circ[i] ? foff[i] + 1 : foff[i + 1]); ++e) rows.push_back(e);
+      if (circ[i]) {
+        kbase[i] = kacc;
+        kacc += n;
+      }
+    }
+  }
+  {
+    size_t freeb = 0, totb = 0;
+    CK(cudaMemGetInfo(&freeb, &totb));
+    const double bytes = (double)(4 * h->nc_blocks + fb_acc) * (sizeof(cplx) + 2 * sizeof(cplxf)) +
+                         2.0 * E * 2 * h->lev[D].P * sizeof(cplx);
+    // (the near-field build's shared memory: per-source and per-target arrays)
+    const size_t nb_smem = sizeof(int) * (13 * (size_t)h->nc_maxns + 4 * (size_t)h->leaf_maxn + 16);
+    h->tri_cache = h->opt.near_mode == 0 && h->max_fiber <= 1024 && bytes < 0.5 * (double)freeb &&
+                   nb_smem <= 200 * 1024;
+  }
+  if (h->tri_cache) {
+    h->fb_entries = fb_acc;
+    h->hcirc = circ;
+    h->nfb_rows = (int)rows.size();
+    h->nchunk = (int)chunks.size() / 3;
+    pfmbem_status st;
+    if ((st = upload(h, &h->nc_base, nc_base)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->nc_sbase, nc_sbase)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->fb_base, fbase)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->fb_circ, circ)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->fb_chunk, chunks)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->fb_rows, rows)) != PFMBEM_OK) return st;
+    if ((st = upload(h, &h->kt_base, kbase)) != PFMBEM_OK) return st;
+    if ((st = build_pair_tables(h, nodes, foff, fib, std::vector<int>(E, 0), perm, nl_ptr, nl_src, nl_img)) !=
+        PFMBEM_OK)
+      return st;
+    h->nc_src = dalloc<int>(h, (size_t)std::max(nc_sbase.back(), 1));
+    h->nc_img = dalloc<int>(h, (size_t)std::max(nc_sbase.back(), 1));
+    h->kt_val = dalloc<cplx>(h, (size_t)4 * kacc);
+    h->kt_sval = dalloc<cplx>(h, (size_t)4 * kacc);
+    h->kt_svalf = dalloc<cplxf>(h, (size_t)4 * kacc);
+    h->kt_svall = dalloc<cplxf>(h, (size_t)4 * kacc);
+    h->nq_cap = (unsigned)std::min<int64_t>(h->nc_blocks, (int64_t)0xFFFFFFFFu);
+    h->nq = dalloc<unsigned long long>(h, std::max<size_t>(h->nq_cap, 1));
+    h->nq_len = dalloc<unsigned>(h, 1);
+    h->nc_valf = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
+    h->nc_vall = dalloc<cplxf>(h, (size_t)(4 * h->nc_blocks));
+    h->fb_val = dalloc<cplx>(h, (size_t)fb_acc);
+    h->fb_valf = dalloc<cplxf>(h, (size_t)fb_acc);
+    h->stat_dev = dalloc<unsigned long long>(h, 4);
+    const size_t ncoef = (size_t)E * 2 * h->lev[D].P;
+    h->p2m_c = dalloc<cplx>(h, ncoef);
+    h->l2p_c = dalloc<cplx>(h, ncoef);
+    if (!h->nc_src || !h->nc_img || !h->kt_val || !h->kt_sval || !h->kt_svalf || !h->kt_svall || !h->nq ||
+        !h->nq_len || !h->nc_valf || !h->nc_vall || !h->fb_val || !h->fb_valf || !h->stat_dev || !h->p2m_c ||
+        !h->l2p_c)
+      return fail(h, PFMBEM_ENOMEM, "device allocation failed (triangle tree caches)");
+    CK(cudaMemsetAsync(h->stat_dev, 0, 4 * sizeof(unsigned long long), h->stream));
   }
   // P2M Gauss nodes: a leaf's M2L sources are at least the leaf triangle's height
   // (side sqrt(3) / 2) away
@@ -497,6 +616,7 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
     CK(k_tri_tables(h, l, l >= 1 ? m2l_v[l] : nullptr, l >= 1 ? (int)m2l_off[l].v.size() : 0,
                     l < D ? sh_v[l] : nullptr, l < D ? (int)sh_off[l].v.size() : 0));
   CK(k_wide_top(h, dv, S, X, nbr_dev));
+  if (h->tri_cache) CK(k_tri_caches(h));
   h->ub_on = false;
   pin_release_async(h);
   h->info.E = E;

@@ -1,10 +1,11 @@
 """The regular-triangle quadtree for hexagon lattices (Sec. 3.1, Fig. 5): every
 fiber in the hexagonal cell of its lattice point, the cell split into six
 triangles and each triangle into four, neighbours where cells or triangles
-touch.  Against the dense CPU oracle, which has no tree: the FP64 product on
-random and smooth densities at several depths, the solution, the Bragg
-coefficients and ETC; on a larger hexagon block against the square tree's
-solution; and the geometry the tree rejects."""
+touch.  Against the dense CPU oracle, which has no tree: the FP64 product (with
+cached element integrals, and with the integrals in every product) on random and
+smooth densities at several depths, the solution, the Bragg coefficients and
+ETC; on a larger hexagon block and on Table 3's hexagon rows against the square
+tree; and the geometry the tree rejects."""
 import math
 
 import numpy as np
@@ -25,10 +26,11 @@ def hexagon(ncol, nrow, n, kH, theta_deg, seed, H=1.0):
 
 
 CASES = [
-    # (workload args, extra options)
+    # (workload args, extra options); near_mode 1: the element integrals in every product
     ((3, 2, 32, 3.0, 20.0, 5), {}),
     ((3, 2, 32, 3.0, 20.0, 5), {"depth": 2}),
     ((2, 3, 40, 4.5, 35.0, 6), {"depth": 3}),
+    ((2, 3, 40, 4.5, 35.0, 6), {"depth": 3, "near_mode": 1}),
 ]
 _cache = {}
 
