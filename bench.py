@@ -518,6 +518,7 @@ def main():
     extra = {}
     if not args.no_extra and world == 1:
         extra["large_block"] = large_block(pf, torch, args, stream, flush)
+        extra["triangle_tree"] = triangle_tree(pf, torch, args, stream, flush, fp64_peak)
         extra["sweep_chunk"] = sweep_chunk(args)
         extra["warm_start_sweep"] = warm_start_sweep(args)
     h2d = int(npf_h.numel() * 4 + nodes_h.numel() * 8)
@@ -619,6 +620,76 @@ def large_block(pf, torch, args, stream, flush, steps=5):
         res[name] = {"solves_per_s": 1000.0 * steps / tot, "iters": info.iters, "rel_residual": info.rel_residual}
     return {"workload": w.name, "elements": w.E, "unknowns": 2 * w.E, "steps": steps, **res,
             "speedup_mixed_over_fp64": res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"]}
+
+
+def triangle_tree(pf, torch, args, stream, flush, fp64_peak, steps=5, products=5):
+    """The paper's regular-triangle tree (Sec. 3.1, Fig. 5) on the 8x8 hexagon block:
+    create + FP64 solve to the bench tolerance + Bragg coefficients per step (device
+    buffers, L2 flushed between steps), and the roofline of its dominant kernel, the
+    FP64 M2L by offset groups (phase "m2l" of the library's profile over a few
+    products): flops = sum over levels of pairs x P^2 x 8."""
+    from paper_1910_10863_gb300 import workloads as W
+    w = W.hexagon_8x8_n256()
+    npf = torch.from_numpy(np.ascontiguousarray(w.nodes_per_fiber, dtype=np.int32)).cuda()
+    nodes = torch.from_numpy(np.ascontiguousarray(w.nodes)).cuda()
+    psi = torch.zeros(2 * w.E, dtype=torch.complex128, device="cuda")
+    o = pf.Options()
+    o.tree = 1
+    o.leaf_max = 16
+    for key, val in W.hexagon_block_lattice(w.H, 8).items():
+        setattr(o, key, val)
+    info = None
+
+    def one():
+        nonlocal info
+        h = pf.pfmbem_create(w.M, npf, nodes, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, o, stream.cuda_stream)
+        try:
+            info = pf.pfmbem_solve(h, None, psi, False, args.tol, 2000, check=False)
+            pf.pfmbem_coefficients(h, psi)
+        finally:
+            pf.pfmbem_destroy(h)
+    one()
+    tot = 0.0
+    for _ in range(steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    # products under the library's profile
+    h = pf.pfmbem_create(w.M, npf, nodes, w.H, w.lattice, w.k, w.k1, w.rho_ratio, w.theta, o, stream.cuda_stream)
+    try:
+        plan = pf.pfmbem_plan(h)
+        x = torch.ones(2 * w.E, dtype=torch.complex128, device="cuda")
+        y = torch.zeros_like(x)
+        pf.pfmbem_matvec(h, x.data_ptr(), y.data_ptr(), pf.FP64)
+        torch.cuda.synchronize()
+        pf.pfmbem_profile(h, True, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(products):
+            pf.pfmbem_matvec(h, x.data_ptr(), y.data_ptr(), pf.FP64)
+        e1.record(stream)
+        e1.synchronize()
+        prod_ms = e0.elapsed_time(e1) / products
+        prof = pf.pfmbem_profile_read(h)
+        m2l_ms = prof.ms[pf.PHASES.index("m2l")] / products
+    finally:
+        pf.pfmbem_destroy(h)
+    flops = sum(plan.m2l_pairs_level[l] * (2 * plan.p[l] + 1) ** 2 * 8 for l in range(1, plan.depth + 1))
+    ach = flops / (m2l_ms * 1e-3) / 1e12
+    return {"workload": w.name, "tree": "regular triangles (64 hexagonal cells)", "elements": w.E, "steps": steps,
+            "depth": plan.depth, "p": list(plan.p)[:plan.depth + 1], "precision": "fp64",
+            "solves_per_s": 1000.0 * steps / tot, "iters": info.iters, "rel_residual": info.rel_residual,
+            "product_ms": prod_ms,
+            "roofline": {"kernel": "m2l_offset_t_kernel<cplx> (triangle tree)", "bound": "alu", "achieved": ach,
+                         "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "ms_per_product": m2l_ms,
+                         "flops_per_product": flops, "peak_source": "FP64 FMA-chain probe (pfmbem_probe_peak)"}}
 
 
 def sweep_chunk(args, count=128):

@@ -312,8 +312,10 @@ pfmbem_status pfmbem_warm_decode(pfmbem_t h, int nmodes, const float* y, double*
  * kernels, 8 set-up kernels, 9 output kernels (field, coefficients),
  * 10 element-integral cache build (the near-field and same-fiber Hankel
  * quadrature, once per create), 11 the single-launch matrix-vector product
- * (all of phases 0-6 in one cooperative kernel); phases 0-6 and 11 of the
- * FP32 (mixed) matrix-vector product are counted at index + 16.
+ * (all of phases 0-6 in one cooperative kernel), 12 M2L where it runs apart
+ * from L2L (the triangle tree's offset groups; phase 3 then holds L2L and the
+ * operator between the cells); phases 0-6 and 11 of the FP32 (mixed)
+ * matrix-vector product are counted at index + 16.
  * launches[] always counts the library's kernel launches; ms[] accumulates
  * CUDA-event device time per phase on the handle's stream while timing is on. */
 typedef struct {

@@ -123,7 +123,7 @@ struct GmresWork {
 };
 
 enum Phase { PH_GATHER = 0, PH_P2M, PH_M2M, PH_LOCAL, PH_L2P, PH_NEAR, PH_FIBER, PH_BLAS, PH_SETUP, PH_OUT, PH_BUILD,
-             PH_FUSED, PH_COUNT };
+             PH_FUSED, PH_M2L, PH_COUNT };
 
 // Launch counters and optional CUDA-event timing per phase.
 struct Prof {

@@ -2394,6 +2394,8 @@ static cudaError_t matvec_tri_cached(pfmbem* h, const cplx* x, cplx* y) {
     local_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, 0, a.P, pa.P, pa.l2l, pa.L, nullptr, nullptr, nullptr,
                                                      nullptr, nullptr, a.M, nullptr, alpha, a.L, l == 1 ? 6 : 4,
                                                      a.pidx);
+    prof_end(h, PH_LOCAL);
+    prof_begin(h, PH_M2L);
     if (a.nchunk > 0) {
       const int nwarp = 8;
       const size_t smem = sizeof(cplx) * ((size_t)a.P * (a.P + 1) + (size_t)nwarp * a.P);
@@ -2402,7 +2404,7 @@ static cudaError_t matvec_tri_cached(pfmbem* h, const cplx* x, cplx* y) {
       m2l_offset_t_kernel<cplx><<<a.nchunk, 32 * nwarp, smem, st>>>(a.P, a.ch_off, a.ch_beg, a.ch_end, a.pr_tgt,
                                                                      a.pr_src, a.pr_img, a.m2l, a.M, alpha, a.L);
     }
-    prof_end(h, PH_LOCAL);
+    prof_end(h, PH_M2L);
   }
   prof_begin(h, PH_L2P);
   l2p_apply_t_kernel<cplx><<<leaf.nne, 256, 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P, E, h->l2p_c,

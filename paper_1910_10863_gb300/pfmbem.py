@@ -214,7 +214,7 @@ def pfmbem_coefficients(h, psi, max_orders=64):
 
 
 PHASES = ["gather", "p2m", "m2m", "m2l_l2l", "l2p", "near_p2p", "fiber_p2p_combine", "gmres_blas", "setup",
-          "outputs", "p2p_cache_build", "matvec_fused", "", "", "", "",
+          "outputs", "p2p_cache_build", "matvec_fused", "m2l", "", "", "",
           "gather_f32", "p2m_f32", "m2m_f32", "m2l_l2l_f32", "l2p_f32", "near_p2p_f32", "fiber_p2p_combine_f32",
           "", "", "", "", "matvec_fused_f32", "", "", "", ""]
 
