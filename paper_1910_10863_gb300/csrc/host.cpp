@@ -2417,7 +2417,7 @@ const char* pfmbem_last_error(pfmbem_t h) { return h ? h->err.c_str() : "null ha
 pfmbem_status pfmbem_plan(pfmbem_t h, pfmbem_plan_info* info) {
   if (!h || !info) return PFMBEM_EINVAL;
   if (!h->ready) { const pfmbem_status rs = check_ready(h); if (rs != PFMBEM_OK) return rs; }
-  if (h->cached && h->stat_dev) {
+  if ((h->cached || h->tri_cache) && h->stat_dev) {
     unsigned long long c[4];
     CK(cudaMemcpyAsync(c, h->stat_dev, sizeof(c), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
@@ -2432,8 +2432,8 @@ pfmbem_status pfmbem_plan(pfmbem_t h, pfmbem_plan_info* info) {
     h->info.p32[l] = l <= h->D ? (h->fused ? (k_fused_order(h, l, true) - 1) / 2 : h->lev[l].p) : 0;
     h->info.m2l_pairs_level[l] = l <= h->D ? (int64_t)h->lev[l].nil : 0;
   }
-  h->info.near_blocks = h->cached ? h->nc_blocks : 0;
-  h->info.fiber_entries = h->cached ? h->fb_entries : 0;
+  h->info.near_blocks = h->cached || h->tri_cache ? h->nc_blocks : 0;
+  h->info.fiber_entries = h->cached || h->tri_cache ? h->fb_entries : 0;
   *info = h->info;
   return PFMBEM_OK;
 }

@@ -342,35 +342,6 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
     if ((st = upload(h, &h->nl_src, nl_src)) != PFMBEM_OK) return st;
     if ((st = upload(h, &h->nl_img, nl_img)) != PFMBEM_OK) return st;
   }
-  // near-field and same-fiber pair statistics (the product integrates them every time)
-  {
-    const Level& Lf = h->lev[D];
-    int64_t pairs = 0, quad = 0;
-    for (size_t li = 0; li < Lf.hne.size(); ++li) {
-      const int b = Lf.hne[li];
-      for (int s = Lf.hbegin[b]; s < Lf.hend[b]; ++s)
-        for (int e = nl_ptr[li]; e < nl_ptr[li + 1]; ++e)
-          for (int f = Lf.hbegin[nl_src[e]]; f < Lf.hend[nl_src[e]]; ++f) {
-            if (f == s && nl_img[e] == 0) continue;
-            const int eo = perm[f], so = perm[s];
-            const double q = std::hypot(c[so].x - c[eo].x, c[so].y - (c[eo].y + nl_img[e] * H)) / len[eo];
-            pairs++;
-            quad += gl_order_host(q, g_thr64);
-          }
-    }
-    h->info.near_pairs = pairs;
-    h->info.near_quad = quad;
-    pairs = quad = 0;
-    for (int i = 0; i < M; ++i)
-      for (int e = foff[i]; e < foff[i + 1]; ++e)
-        for (int f = foff[i]; f < foff[i + 1]; ++f) {
-          if (f == e) continue;
-          pairs++;
-          quad += gl_order_host(std::hypot(c[e].x - c[f].x, c[e].y - c[f].y) / len[f], g_thr64);
-        }
-    h->info.fiber_pairs = pairs;
-    h->info.fiber_quad = quad;
-  }
   // ---------------------------------------------------- cached element integrals
   // As the square tree's: per leaf its concatenated near sources and a dense
   // [targets][sources] array of 2x2 blocks; the same-fiber blocks (a row pair
@@ -458,6 +429,36 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
         !h->l2p_c)
       return fail(h, PFMBEM_ENOMEM, "device allocation failed (triangle tree caches)");
     CK(cudaMemsetAsync(h->stat_dev, 0, 4 * sizeof(unsigned long long), h->stream));
+  }
+  // near-field and same-fiber pair statistics on the host when the product
+  // integrates them every time (the cache build counts them on the GPU)
+  if (!h->tri_cache) {
+    const Level& Lf = h->lev[D];
+    int64_t pairs = 0, quad = 0;
+    for (size_t li = 0; li < Lf.hne.size(); ++li) {
+      const int b = Lf.hne[li];
+      for (int s = Lf.hbegin[b]; s < Lf.hend[b]; ++s)
+        for (int e = nl_ptr[li]; e < nl_ptr[li + 1]; ++e)
+          for (int f = Lf.hbegin[nl_src[e]]; f < Lf.hend[nl_src[e]]; ++f) {
+            if (f == s && nl_img[e] == 0) continue;
+            const int eo = perm[f], so = perm[s];
+            const double q = std::hypot(c[so].x - c[eo].x, c[so].y - (c[eo].y + nl_img[e] * H)) / len[eo];
+            pairs++;
+            quad += gl_order_host(q, g_thr64);
+          }
+    }
+    h->info.near_pairs = pairs;
+    h->info.near_quad = quad;
+    pairs = quad = 0;
+    for (int i = 0; i < M; ++i)
+      for (int e = foff[i]; e < foff[i + 1]; ++e)
+        for (int f = foff[i]; f < foff[i + 1]; ++f) {
+          if (f == e) continue;
+          pairs++;
+          quad += gl_order_host(std::hypot(c[e].x - c[f].x, c[e].y - c[f].y) / len[f], g_thr64);
+        }
+    h->info.fiber_pairs = pairs;
+    h->info.fiber_quad = quad;
   }
   // P2M Gauss nodes: a leaf's M2L sources are at least the leaf triangle's height
   // (side sqrt(3) / 2) away
