@@ -179,7 +179,9 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
     }
   }
   if (D < 1 || D > kDmax) return fail(h, PFMBEM_EINVAL, "triangle tree: depth must be in [1, 8]");
-  if (nbox_at(D) > ((size_t)1 << 26)) return fail(h, PFMBEM_EINVAL, "triangle tree: too many boxes at this depth");
+  // (every level keeps expansions for all its boxes: at most 4 M leaves, about
+  // 4 GB of FP64 multipoles and locals at p 30)
+  if (nbox_at(D) > ((size_t)1 << 22)) return fail(h, PFMBEM_EINVAL, "triangle tree: too many boxes at this depth");
   h->D = D;
   // ---------------------------------------------------- sort by leaf (stable counting sort)
   std::vector<int> key(E), perm(E), pos(E);
