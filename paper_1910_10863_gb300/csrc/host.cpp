@@ -1630,12 +1630,20 @@ static pfmbem_status build_plan(pfmbem* h, const int* npf, const double* nodes) 
             }
           }
           if ((st = upload(h, &h->nr_meta, meta)) != PFMBEM_OK) return st;
-          // the rows cut into pieces of at most 128 sources: (piece << 24) | element
-          std::vector<unsigned> pieces;
+          // the rows cut into pieces of at most 128 sources, each described in one
+          // 16-byte load: offset of its first block (low, high word), its first
+          // source in the concatenated list, (sources << 24) | element
+          std::vector<int4> pieces;
           pieces.reserve((size_t)E + E / 2);
           for (int s2 = 0; s2 < E && E < (1 << 24); ++s2) {
-            const int ns = (int)(meta[2 * (size_t)s2 + 1] & 0xffffffffll);
-            for (int pc = 0; pc * 128 < std::max(ns, 1) && pc < 256; ++pc) pieces.push_back(((unsigned)pc << 24) | (unsigned)s2);
+            const int64_t r = meta[2 * (size_t)s2];
+            const int j0 = (int)(meta[2 * (size_t)s2 + 1] >> 32), ns = (int)(meta[2 * (size_t)s2 + 1] & 0xffffffffll);
+            for (int jb = 0; jb < std::max(ns, 1); jb += 128) {
+              const int cnt = std::max(0, std::min(128, ns - jb));
+              const uint64_t rp = (uint64_t)(r + 4 * (int64_t)jb);
+              pieces.push_back(int4{(int)(uint32_t)(rp & 0xffffffffu), (int)(uint32_t)(rp >> 32), j0 + jb,
+                                    (int)(((uint32_t)cnt << 24) | (uint32_t)s2)});
+            }
           }
           h->nr_npiece = (int)pieces.size();
           if ((st = upload(h, &h->nr_piece, pieces)) != PFMBEM_OK) return st;

@@ -294,7 +294,8 @@ struct pfmbem {
   size_t fz_tcb32 = 0;           // shared memory of the FP32 product's tensor-core M2L operands (0: none)
   int* s_li = nullptr;           // sorted element -> index of its leaf among the non-empty leaves
   int64_t* nr_meta = nullptr;    // [E][2] near-field row of a sorted element: block offset, (first source << 32) | sources
-  unsigned* nr_piece = nullptr;  // near rows cut into pieces of <= 128 sources: (piece << 24) | element
+  int4* nr_piece = nullptr;      // near rows cut into pieces of <= 128 sources: first block offset (low,
+                                 // high word), first source, (sources << 24) | element
   int nr_npiece = 0;
   cplx* Un = nullptr;            // [E][2] near-field part of (U', dU'), FP64 and FP32
   cplxf* Unf = nullptr;

@@ -108,10 +108,11 @@ struct FusedArgs {
   const int64_t* nc_base;
   const int* nc_sbase;
   const longlong2* nr_meta;          // per sorted element: block offset of its near row, (first source << 32) | sources
-  // FP32 product: the near rows cut into pieces of at most NR_PIECE sources
-  // ((piece << 24) | sorted element), summed atomically into Un (zeroed in
-  // stage A); 0 pieces: whole rows
-  const unsigned* nr_piece;
+  // FP32 product: the near rows cut into pieces of at most NR_PIECE sources,
+  // each one 16-byte descriptor (offset of its first block, low and high word;
+  // its first source in nc_src; (sources << 24) | sorted element), summed
+  // atomically into Un (zeroed in stage A); 0 pieces: whole rows
+  const int4* nr_piece;
   int npiece;
   const int* nc_src;
   const C* nc_val;
@@ -766,17 +767,18 @@ __device__ __forceinline__ void near_row(const FusedArgs<C>& a, int s, int lane)
   }
 }
 
-// One piece of a near-field row in differences (FP32 product): sources
-// [NR_PIECE p, NR_PIECE (p + 1)) of target s, one pass of four sources per lane,
+// One piece of a near-field row in differences (FP32 product): at most
+// NR_PIECE consecutive sources of target s, one pass of four sources per lane,
 // added atomically into Un.  Pieces bound every near item's latency to one
 // pass, whatever the row's length (crowded leaves give rows of ~600 sources).
+// The descriptor d (read ahead by the stage loops) holds everything the piece
+// needs to start: its block offset, its first source and (count, target).
 constexpr int NR_PIECE = 128;
-__device__ __forceinline__ void near_piece_diff(const FusedArgs<cplxf>& a, unsigned code, int lane) {
-  const int s = (int)(code & 0xffffffu), jb = (int)(code >> 24) * NR_PIECE;
-  const longlong2 mt = __ldg(a.nr_meta + s);
-  const cplxf* row = a.nc_val + mt.x;
-  const int* src = a.nc_src + (int)(mt.y >> 32);
-  const int ns = (int)(mt.y & 0xffffffffll);
+__device__ __forceinline__ void near_piece_diff(const FusedArgs<cplxf>& a, int4 d, int lane) {
+  const int64_t r = (int64_t)(((unsigned long long)(unsigned)d.y << 32) | (unsigned)d.x);
+  const int cnt = (int)((unsigned)d.w >> 24), s = (int)((unsigned)d.w & 0xffffffu);
+  const cplxf* row = a.nc_val + r;
+  const int* src = a.nc_src + d.z;
   const cplxf tph = ldcg(a.dens + 2 * s), tpl = ldcg(a.dlo + 2 * s);
   const cplxf tvh = ldcg(a.dens + 2 * s + 1), tvl = ldcg(a.dlo + 2 * s + 1);
   constexpr int NJ = NR_PIECE / 32;
@@ -784,10 +786,10 @@ __device__ __forceinline__ void near_piece_diff(const FusedArgs<cplxf>& a, unsig
   cplxf q[NJ][4];
 #pragma unroll
   for (int k = 0; k < NJ; ++k) {
-    const int jj = jb + lane + 32 * k;
-    f[k] = jj < ns ? __ldg(src + jj) : s;
+    const int jj = lane + 32 * k;
+    f[k] = jj < cnt ? __ldg(src + jj) : s;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) q[k][c] = jj < ns ? row[4 * jj + c] : cplxf{0, 0};
+    for (int c = 0; c < 4; ++c) q[k][c] = jj < cnt ? row[4 * jj + c] : cplxf{0, 0};
   }
   cplxf u0{0, 0}, d0{0, 0}, u1{0, 0}, d1{0, 0};
 #pragma unroll
@@ -802,23 +804,44 @@ __device__ __forceinline__ void near_piece_diff(const FusedArgs<cplxf>& a, unsig
     d1 += q[k + 1][2] * p1 + q[k + 1][3] * v1;
   }
   const cplxf u = wsum(u0 + u1), du = wsum(d0 + d1);
-  if (lane == 0) {
+  if (lane == 0 && cnt > 0) {
     atomic_add(a.Un + 2 * s, u);
     atomic_add(a.Un + 2 * s + 1, du);
   }
 }
 
-// Near item i of a stage: a piece (FP32 product in differences, when the pieces
-// are set up) or a whole row.
+// The near items [ifirst, nitem) of a stage that fall to one warp (every
+// wstride-th from its first), item i being near item r0 + i - base: pieces
+// (FP32 product in differences) with the next descriptor read while the current
+// piece runs, so that a piece costs about two dependent loads instead of four;
+// else whole rows.  nd: the warp's first descriptor, read by the caller before
+// the stage's box items.
 template <class C>
-__device__ __forceinline__ void near_item(const FusedArgs<C>& a, int i, int lane) {
+__device__ __forceinline__ void near_items(const FusedArgs<C>& a, int ifirst, int nitem, int wstride, int r0,
+                                           int base, int4 nd, int lane) {
   if constexpr (sizeof(C) == sizeof(cplxf)) {
     if (a.npiece > 0) {
-      near_piece_diff(a, __ldg(a.nr_piece + i), lane);
+      for (int i = ifirst; i < nitem; i += wstride) {
+        const int in = i + wstride;
+        const int4 dn = in < nitem ? __ldg(a.nr_piece + r0 + (in - base)) : nd;
+        near_piece_diff(a, nd, lane);
+        nd = dn;
+      }
       return;
     }
   }
-  near_row(a, i, lane);
+  for (int i = ifirst; i < nitem; i += wstride) near_row(a, r0 + (i - base), lane);
+}
+
+// A warp's first near item of a stage (items from base on) and its descriptor.
+template <class C>
+__device__ __forceinline__ int first_near(const FusedArgs<C>& a, int wfirst, int wstride, int base, int nitem,
+                                          int r0, int4* nd) {
+  const int i0 = wfirst >= base ? wfirst : wfirst + ((base - wfirst + wstride - 1) / wstride) * wstride;
+  *nd = int4{0, 0, 0, 0};
+  if constexpr (sizeof(C) == sizeof(cplxf))
+    if (a.npiece > 0 && i0 < nitem) *nd = __ldg(a.nr_piece + r0 + (i0 - base));
+  return i0;
 }
 
 // Inverse block symbol of a regular-polygon fiber's whole same-fiber block of
@@ -2175,12 +2198,10 @@ __device__ __forceinline__ bool fused_body(const FusedArgs<C>& a, const int bid,
     else if (staged)
       m2m_staged(a, l, nbi, wfirst, wstride, sT, wsm, lane, bid);
     if (a.bdone && threadIdx.x == 0) a.bdone[(size_t)(ks - 1) * G + bid] = gtimer();
-    for (int i = wfirst; i < nitem; i += wstride) {
+    int4 nd;
+    const int inear = first_near(a, wfirst, wstride, nbi + nx, nitem, r0, &nd);
+    for (int i = wfirst; i < nbi + nx; i += wstride) {
       if (staged && i < nbi) continue;
-      if (i >= nbi + nx) {
-        near_item(a, r0 + (i - nbi - nx), lane);
-        continue;
-      }
       if (i >= nbi) {
         // M(1) of a level-1 box from its 16 level-3 boxes; the multipoles of
         // empty level-3 boxes are kept at zero, so the sum runs without branches
@@ -2286,6 +2307,7 @@ __device__ __forceinline__ bool fused_body(const FusedArgs<C>& a, const int bid,
         }
       }
     }
+    near_items(a, inear, nitem, wstride, r0, nbi + nx, nd, lane);
     // the next stage's operators, staged ahead (this stage's items are done
     // with the shared memory once the block has passed this point)
     if (l - 1 >= lstop)
@@ -2378,11 +2400,9 @@ __device__ __forceinline__ bool fused_body(const FusedArgs<C>& a, const int bid,
     const int r0 = a.near_first ? (jst == 0 ? 0 : NI) : (int)((int64_t)NI * jst / nst);
     const int r1 = a.near_first ? NI : (int)((int64_t)NI * (jst + 1) / nst);
     const int nitem = nl2l + nm2l + (r1 - r0);
-    for (int i = wfirst; i < nitem; i += wstride) {
-      if (i >= nl2l + nm2l) {
-        near_item(a, r0 + (i - nl2l - nm2l), lane);
-        continue;
-      }
+    int4 nd;
+    const int inear = first_near(a, wfirst, wstride, nl2l + nm2l, nitem, r0, &nd);
+    for (int i = wfirst; i < nl2l + nm2l; i += wstride) {
       if (i < nl2l) {
         if (sl2l) continue;
         if (top && a.top3 && l == 1) {
@@ -2455,6 +2475,7 @@ __device__ __forceinline__ bool fused_body(const FusedArgs<C>& a, const int bid,
       __syncwarp();
       for (int n = lane; n < P; n += 32) atomic_add(a.L[l] + (size_t)tgt * S + O + n, colmv(To + n, S, wsm, P));
     }
+    near_items(a, inear, nitem, wstride, r0, nl2l + nm2l, nd, lane);
     if (l < D) prefetch(ks, -1, l + 1);     // the next D stage's operators, staged ahead
     if (!group_barrier(a.bar, a.err, a.wait_ns, G, bid, a.arrive ? a.arrive + (size_t)(ks - 1) * G : nullptr)) {
       tc_leave();
@@ -2580,7 +2601,7 @@ cudaError_t fill_args(pfmbem* h, const cplx* x, cplx* y, const int* done, FusedA
   a.tregL = sizeof(C) == sizeof(cplxf) && h->fz_tcb32 == 0 ? h->fz_tregL32 : 0;
   a.nr_meta = reinterpret_cast<const longlong2*>(h->nr_meta);
   static const bool rows = std::getenv("PFMBEM_NEAR_ROWS") != nullptr;   // measurement: whole rows
-  a.nr_piece = reinterpret_cast<const unsigned*>(h->nr_piece);
+  a.nr_piece = h->nr_piece;
   a.npiece = (sizeof(C) == sizeof(cplxf) && h->fz_dlo && h->nr_piece && !rows) ? h->nr_npiece : 0;
   a.tc_any = 0;
   for (int l = 0; l <= h->D; ++l) {
