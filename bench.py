@@ -518,7 +518,7 @@ def main():
     extra = {}
     if not args.no_extra and world == 1:
         extra["large_block"] = large_block(pf, torch, args, stream, flush)
-        extra["triangle_tree"] = triangle_tree(pf, torch, args, stream, flush, fp64_peak)
+        extra["triangle_tree"] = triangle_tree(pf, torch, args, stream, flush, fp32_peak)
         extra["sweep_chunk"] = sweep_chunk(args)
         extra["warm_start_sweep"] = warm_start_sweep(args)
     h2d = int(npf_h.numel() * 4 + nodes_h.numel() * 8)
@@ -622,12 +622,14 @@ def large_block(pf, torch, args, stream, flush, steps=5):
             "speedup_mixed_over_fp64": res["mixed"]["solves_per_s"] / res["fp64"]["solves_per_s"]}
 
 
-def triangle_tree(pf, torch, args, stream, flush, fp64_peak, steps=5, products=5):
+def triangle_tree(pf, torch, args, stream, flush, fp32_peak, steps=5, products=5):
     """The paper's regular-triangle tree (Sec. 3.1, Fig. 5) on the 8x8 hexagon block:
     create + FP64 solve to the bench tolerance + Bragg coefficients per step (device
     buffers, L2 flushed between steps), and the roofline of its dominant kernel, the
-    FP64 M2L by offset groups (phase "m2l" of the library's profile over a few
-    products): flops = sum over levels of pairs x P^2 x 8."""
+    M2L by offset groups in double-float arithmetic (phase "m2l" of the library's
+    profile over a few products) on the FP32 pipes: flops = sum over levels of pairs
+    x P^2 x 60 (four double-float multiply-adds of 15 FP32 flops per complex
+    multiply-add)."""
     from paper_1910_10863_gb300 import workloads as W
     w = W.hexagon_8x8_n256()
     npf = torch.from_numpy(np.ascontiguousarray(w.nodes_per_fiber, dtype=np.int32)).cuda()
@@ -681,15 +683,16 @@ def triangle_tree(pf, torch, args, stream, flush, fp64_peak, steps=5, products=5
         m2l_ms = prof.ms[pf.PHASES.index("m2l")] / products
     finally:
         pf.pfmbem_destroy(h)
-    flops = sum(plan.m2l_pairs_level[l] * (2 * plan.p[l] + 1) ** 2 * 8 for l in range(1, plan.depth + 1))
+    flops = sum(plan.m2l_pairs_level[l] * (2 * plan.p[l] + 1) ** 2 * 60 for l in range(1, plan.depth + 1))
     ach = flops / (m2l_ms * 1e-3) / 1e12
     return {"workload": w.name, "tree": "regular triangles (64 hexagonal cells)", "elements": w.E, "steps": steps,
             "depth": plan.depth, "p": list(plan.p)[:plan.depth + 1], "precision": "fp64",
             "solves_per_s": 1000.0 * steps / tot, "iters": info.iters, "rel_residual": info.rel_residual,
             "product_ms": prod_ms,
-            "roofline": {"kernel": "m2l_offset_t_kernel<cplx> (triangle tree)", "bound": "alu", "achieved": ach,
-                         "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak, "ms_per_product": m2l_ms,
-                         "flops_per_product": flops, "peak_source": "FP64 FMA-chain probe (pfmbem_probe_peak)"}}
+            "roofline": {"kernel": "tri_m2l_dd_kernel (triangle tree, double-float M2L)", "bound": "alu",
+                         "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s", "frac": ach / fp32_peak,
+                         "ms_per_product": m2l_ms, "flops_per_product": flops,
+                         "peak_source": "FP32 FMA-chain probe (pfmbem_probe_peak)"}}
 
 
 def sweep_chunk(args, count=128):

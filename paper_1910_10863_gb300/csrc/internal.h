@@ -86,6 +86,8 @@ struct Level {
   // the parent level's tables (the children's offsets vary with the orientation)
   double2* ctr = nullptr;    // [nbox]
   int* pidx = nullptr;       // [nbox]
+  int tri_noff = 0;          // distinct M2L offsets of the level
+  cplxf* tri_m2l_hl = nullptr;   // hi, then lo parts of m2l ([2][tri_noff][P][P]) for the double-float M2L
   cplx* m2m = nullptr;       // children (level l+1) -> this level: [4][P][P_child]
   cplx* l2l = nullptr;       // this level -> children: [4][P_child][P]
   // FP32 copies for the mixed path
@@ -442,6 +444,10 @@ cudaError_t k_tri_tables(pfmbem* h, int l, const double2* m2l_v, int nm2l, const
 // Triangle tree: the cached FP64 product's tables (P2M/L2P coefficients at the
 // leaves' centroids, near-field and same-fiber blocks).
 cudaError_t k_tri_caches(pfmbem* h);
+// Triangle tree: level l's M2L operator as hi and lo parts, and its M2L by
+// offset groups in double-float arithmetic (matvec_fused.cu).
+cudaError_t k_tri_m2l_split(pfmbem* h, int l);
+cudaError_t k_tri_m2l_dd(pfmbem* h, int l);
 cudaError_t k_wide_local(pfmbem* h);
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_rhs(pfmbem* h, cplx* B);

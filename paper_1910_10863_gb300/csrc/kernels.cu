@@ -10,6 +10,7 @@
 // lattice-sum root translation), V and dV from a fiber-local direct sum.
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <mutex>
 
 #include "internal.h"
@@ -2348,18 +2349,29 @@ static cudaError_t matvec_tri_cached(pfmbem* h, const cplx* x, cplx* y) {
   prof_begin(h, PH_LOCAL);
   top_apply_kernel<<<(rows * 32 + 255) / 256, 256, 0, st>>>(rows, h->root, h->lev[0].M, h->lev[0].L);
   prof_end(h, PH_LOCAL);
+  // M2L by offset groups in double-float arithmetic on the FP32 pipes
+  // (PFMBEM_TRI_M2L64=1: FP64 instructions, for measurement); where a group's
+  // operator does not fit shared memory, per target over its list, with L2L
+  static const bool m2l64 = std::getenv("PFMBEM_TRI_M2L64") != nullptr;
   for (int l = 1; l <= D; ++l) {
     Level& a = h->lev[l];
     Level& pa = h->lev[l - 1];
+    const int nwarp = 8;
+    const size_t smem = m2l64 || !a.tri_m2l_hl
+                            ? sizeof(cplx) * ((size_t)a.P * (a.P + 1) + (size_t)nwarp * a.P)
+                            : sizeof(cplxf) * (2 * (size_t)a.P * (a.P + 1) + 2 * (size_t)nwarp * a.P);
+    const bool lists = smem > 200 * 1024;
     prof_begin(h, PH_LOCAL);
-    local_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, 0, a.P, pa.P, pa.l2l, pa.L, nullptr, nullptr, nullptr,
-                                                     nullptr, nullptr, a.M, nullptr, alpha, a.L, l == 1 ? 6 : 4,
-                                                     a.pidx);
+    local_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, 0, a.P, pa.P, pa.l2l, pa.L, lists ? a.il_ptr : nullptr,
+                                                     a.il_src, a.il_off, a.il_img, a.m2l, a.M, nullptr, alpha, a.L,
+                                                     l == 1 ? 6 : 4, a.pidx);
     prof_end(h, PH_LOCAL);
+    if (lists) continue;
     prof_begin(h, PH_M2L);
-    if (a.nchunk > 0) {
-      const int nwarp = 8;
-      const size_t smem = sizeof(cplx) * ((size_t)a.P * (a.P + 1) + (size_t)nwarp * a.P);
+    if (a.tri_m2l_hl && !m2l64) {
+      e = k_tri_m2l_dd(h, l);
+      if (e != cudaSuccess) return e;
+    } else if (a.nchunk > 0) {
       if (smem > 48 * 1024)
         cudaFuncSetAttribute(m2l_offset_t_kernel<cplx>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       m2l_offset_t_kernel<cplx><<<a.nchunk, 32 * nwarp, smem, st>>>(a.P, a.ch_off, a.ch_beg, a.ch_end, a.pr_tgt,

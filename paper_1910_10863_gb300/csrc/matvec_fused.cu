@@ -2950,6 +2950,90 @@ cudaError_t k_fused_tables(pfmbem* h) {
   return cudaGetLastError();
 }
 
+// ------------------------------------------------ triangle tree: double-float M2L
+// hi and lo FP32 parts of n FP64 values: out[i] = hi, out[n + i] = lo.
+__global__ void split_hl_kernel(size_t n, const cplx* __restrict__ a, cplxf* __restrict__ out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    out[i] = cplxf{(float)a[i].re, (float)a[i].im};
+    out[n + i] = split_lo(a[i]);
+  }
+}
+
+// M2L of the triangle tree's offset groups (chunks of at most 16 pairs of one
+// offset) in double-float arithmetic: the FP64 result on the FP32 pipes, which
+// GB300 issues at 64 times its FP64 rate.  One block per chunk stages the
+// offset's operator as hi and lo parts ([P][P+1] each, padded rows); a warp per
+// pair splits its phased source multipole alpha^m M(src) into hi and lo, sums
+// each target coefficient with error-free products and sums (about 48 bits)
+// and adds it to L(tgt) in FP64.  L(tgt) holds the L2L part already.
+__global__ void tri_m2l_dd_kernel(int P, int noff, const int* __restrict__ chunk_off, const int* __restrict__ chunk_beg,
+                                  const int* __restrict__ chunk_end, const int* __restrict__ ptgt,
+                                  const int* __restrict__ psrc, const int* __restrict__ pimg,
+                                  const cplxf* __restrict__ Thl, const cplx* __restrict__ M, cplx alpha,
+                                  cplx* __restrict__ L) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  cplxf* sh = reinterpret_cast<cplxf*>(smraw);          // [P][P+1] hi
+  cplxf* sl = sh + (size_t)P * (P + 1);                  // [P][P+1] lo
+  cplxf* sm = sl + (size_t)P * (P + 1);                  // [warps][2][P] source hi, lo
+  const int o = chunk_off[blockIdx.x];
+  const int pb = chunk_beg[blockIdx.x], pe = chunk_end[blockIdx.x];
+  const size_t PP = (size_t)P * P;
+  const cplxf* Th = Thl + (size_t)o * PP;
+  const cplxf* Tl = Thl + (size_t)noff * PP + (size_t)o * PP;
+  for (int i = threadIdx.x; i < P * P; i += blockDim.x) {
+    const int r = i / P, c = i - r * P;
+    sh[r * (P + 1) + c] = Th[i];
+    sl[r * (P + 1) + c] = Tl[i];
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  cplxf* wh = sm + (size_t)warp * 2 * P;
+  cplxf* wl = wh + P;
+  __syncthreads();
+  for (int pi = pb + warp; pi < pe; pi += nw) {
+    const int src = psrc[pi], tgt = ptgt[pi];
+    const cplx ph = phase_m(alpha, pimg[pi]);
+    __syncwarp();
+    for (int n = lane; n < P; n += 32) {
+      const cplx v = ph * M[(size_t)src * P + n];
+      wh[n] = cplxf{(float)v.re, (float)v.im};
+      wl[n] = split_lo(v);
+    }
+    __syncwarp();
+    for (int l = lane; l < P; l += 32) {
+      const cplxf* rh = sh + (size_t)l * (P + 1);
+      const cplxf* rl = sl + (size_t)l * (P + 1);
+      dflt re{0, 0}, im{0, 0};
+      for (int n = 0; n < P; ++n) dd_cmac(re, im, rh[n], rl[n], wh[n], wl[n]);
+      atomic_add(L + (size_t)tgt * P + l, cplx{dd_value(re), dd_value(im)});
+    }
+  }
+}
+
+// Level l's hi and lo operator parts from its FP64 M2L table.
+cudaError_t k_tri_m2l_split(pfmbem* h, int l) {
+  const Level& L = h->lev[l];
+  const size_t n = (size_t)L.tri_noff * L.P * L.P;
+  if (n == 0 || !L.tri_m2l_hl) return cudaSuccess;
+  split_hl_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(n, L.m2l, L.tri_m2l_hl);
+  return cudaGetLastError();
+}
+
+// Level l's M2L by offset groups in double-float arithmetic (after its L2L).
+cudaError_t k_tri_m2l_dd(pfmbem* h, int l) {
+  const Level& L = h->lev[l];
+  if (L.nchunk == 0) return cudaSuccess;
+  const int nwarp = 8;
+  const size_t smem = sizeof(cplxf) * (2 * (size_t)L.P * (L.P + 1) + 2 * (size_t)nwarp * L.P);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(tri_m2l_dd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  tri_m2l_dd_kernel<<<L.nchunk, 32 * nwarp, smem, h->stream>>>(L.P, L.tri_noff, L.ch_off, L.ch_beg, L.ch_end,
+                                                                L.pr_tgt, L.pr_src, L.pr_img, L.tri_m2l_hl, L.M,
+                                                                h->alpha, L.L);
+  return cudaGetLastError();
+}
+
 namespace {
 }  // namespace
 

@@ -505,8 +505,14 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
     L.L = dalloc<cplx>(h, (size_t)L.nbox * L.P);
     if (!L.M || !L.L) return fail(h, PFMBEM_ENOMEM, "device allocation failed (expansions)");
     if (l >= 1) {
+      L.tri_noff = (int)m2l_off[l].v.size();
       L.m2l = dalloc<cplx>(h, std::max<size_t>(m2l_off[l].v.size(), 1) * L.P * L.P);
       if (!L.m2l) return fail(h, PFMBEM_ENOMEM, "device allocation failed (M2L operators)");
+      if (h->tri_cache && L.tri_noff > 0) {
+        // hi and lo parts for the double-float M2L of the cached product
+        L.tri_m2l_hl = dalloc<cplxf>(h, 2 * (size_t)L.tri_noff * L.P * L.P);
+        if (!L.tri_m2l_hl) return fail(h, PFMBEM_ENOMEM, "device allocation failed (M2L operators)");
+      }
     }
     if (l < D) {
       const size_t n = sh_off[l].v.size() * L.P * h->lev[l + 1].P;
@@ -619,7 +625,10 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
     CK(k_tri_tables(h, l, l >= 1 ? m2l_v[l] : nullptr, l >= 1 ? (int)m2l_off[l].v.size() : 0,
                     l < D ? sh_v[l] : nullptr, l < D ? (int)sh_off[l].v.size() : 0));
   CK(k_wide_top(h, dv, S, X, nbr_dev));
-  if (h->tri_cache) CK(k_tri_caches(h));
+  if (h->tri_cache) {
+    CK(k_tri_caches(h));
+    for (int l = 1; l <= D; ++l) CK(k_tri_m2l_split(h, l));
+  }
   h->ub_on = false;
   pin_release_async(h);
   h->info.E = E;
