@@ -88,6 +88,9 @@ struct Level {
   int* pidx = nullptr;       // [nbox]
   int tri_noff = 0;          // distinct M2L offsets of the level
   cplxf* tri_m2l_hl = nullptr;   // hi, then lo parts of m2l ([2][tri_noff][P][P]) for the double-float M2L
+  int tri_nop = 0;           // distinct child offsets below the level (M2M/L2L operators)
+  cplxf* tri_m2m_hl = nullptr;   // hi, then lo parts of m2m and l2l ([2][tri_nop][P][P_child] each)
+  cplxf* tri_l2l_hl = nullptr;
   cplx* m2m = nullptr;       // children (level l+1) -> this level: [4][P][P_child]
   cplx* l2l = nullptr;       // this level -> children: [4][P_child][P]
   // FP32 copies for the mixed path
@@ -448,6 +451,10 @@ cudaError_t k_tri_caches(pfmbem* h);
 // offset groups in double-float arithmetic (matvec_fused.cu).
 cudaError_t k_tri_m2l_split(pfmbem* h, int l);
 cudaError_t k_tri_m2l_dd(pfmbem* h, int l);
+// Triangle tree: M2M of level l from level l + 1, and L2L of level l from l - 1,
+// in double-float arithmetic.
+cudaError_t k_tri_m2m_dd(pfmbem* h, int l);
+cudaError_t k_tri_l2l_dd(pfmbem* h, int l);
 cudaError_t k_wide_local(pfmbem* h);
 cudaError_t k_matvec(pfmbem* h, const cplx* x, cplx* y, int precision);
 cudaError_t k_rhs(pfmbem* h, cplx* B);

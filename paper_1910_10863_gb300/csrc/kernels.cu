@@ -2337,22 +2337,28 @@ static cudaError_t matvec_tri_cached(pfmbem* h, const cplx* x, cplx* y) {
   p2m_apply_t_kernel<cplx><<<leaf.nne, round32(leaf.P), 0, st>>>(leaf.ne, leaf.box_begin, leaf.box_end, leaf.P,
                                                                  h->p2m_c, h->dens, leaf.M);
   prof_end(h, PH_P2M);
+  // M2M, L2L and M2L in double-float arithmetic on the FP32 pipes
+  // (PFMBEM_TRI_M2L64=1: FP64 instructions, for measurement)
+  static const bool m2l64 = std::getenv("PFMBEM_TRI_M2L64") != nullptr;
   for (int l = D - 1; l >= 0; --l) {
     Level& a = h->lev[l];
     Level& c = h->lev[l + 1];
     prof_begin(h, PH_M2M);
-    m2m_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, c.P, a.m2m, c.box_begin, c.box_end, c.M, a.M,
-                                                   l == 0 ? 6 : 4, c.pidx);
+    if (a.tri_m2m_hl && !m2l64) {
+      e = k_tri_m2m_dd(h, l);
+      if (e != cudaSuccess) return e;
+    } else {
+      m2m_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, a.P, c.P, a.m2m, c.box_begin, c.box_end, c.M, a.M,
+                                                     l == 0 ? 6 : 4, c.pidx);
+    }
     prof_end(h, PH_M2M);
   }
   const int rows = h->nroot * h->lev[0].P;
   prof_begin(h, PH_LOCAL);
   top_apply_kernel<<<(rows * 32 + 255) / 256, 256, 0, st>>>(rows, h->root, h->lev[0].M, h->lev[0].L);
   prof_end(h, PH_LOCAL);
-  // M2L by offset groups in double-float arithmetic on the FP32 pipes
-  // (PFMBEM_TRI_M2L64=1: FP64 instructions, for measurement); where a group's
-  // operator does not fit shared memory, per target over its list, with L2L
-  static const bool m2l64 = std::getenv("PFMBEM_TRI_M2L64") != nullptr;
+  // M2L by offset groups; where a group's operator does not fit shared memory,
+  // per target over its list, with L2L
   for (int l = 1; l <= D; ++l) {
     Level& a = h->lev[l];
     Level& pa = h->lev[l - 1];
@@ -2362,9 +2368,14 @@ static cudaError_t matvec_tri_cached(pfmbem* h, const cplx* x, cplx* y) {
                             : sizeof(cplxf) * (2 * (size_t)a.P * (a.P + 1) + 2 * (size_t)nwarp * a.P);
     const bool lists = smem > 200 * 1024;
     prof_begin(h, PH_LOCAL);
-    local_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, 0, a.P, pa.P, pa.l2l, pa.L, lists ? a.il_ptr : nullptr,
-                                                     a.il_src, a.il_off, a.il_img, a.m2l, a.M, nullptr, alpha, a.L,
-                                                     l == 1 ? 6 : 4, a.pidx);
+    if (!lists && pa.tri_l2l_hl && !m2l64) {
+      e = k_tri_l2l_dd(h, l);
+      if (e != cudaSuccess) return e;
+    } else {
+      local_f64_kernel<<<a.nne, round32(a.P), 0, st>>>(a.ne, 0, a.P, pa.P, pa.l2l, pa.L, lists ? a.il_ptr : nullptr,
+                                                       a.il_src, a.il_off, a.il_img, a.m2l, a.M, nullptr, alpha, a.L,
+                                                       l == 1 ? 6 : 4, a.pidx);
+    }
     prof_end(h, PH_LOCAL);
     if (lists) continue;
     prof_begin(h, PH_M2L);

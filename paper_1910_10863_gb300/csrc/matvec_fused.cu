@@ -3009,12 +3009,91 @@ __global__ void tri_m2l_dd_kernel(int P, int noff, const int* __restrict__ chunk
   }
 }
 
+// M2M and L2L of the triangle tree in double-float arithmetic, one block per
+// box and a thread per output coefficient; the operators' hi parts first, then
+// their lo parts (nop operators of [Pc][P] for M2M, [Pp][P] for L2L, rows of the
+// input coefficient, as the FP64 tables).  M2M: M(box) = sum over the non-empty
+// children ch (nch per box) of A_aidx[ch] M(ch).
+__global__ void tri_m2m_dd_kernel(const int* __restrict__ ne, int P, int Pc, int nop, const cplxf* __restrict__ Ahl,
+                                  const int* __restrict__ cbb, const int* __restrict__ cbe,
+                                  const cplx* __restrict__ Mc, cplx* __restrict__ Mp, int nch,
+                                  const int* __restrict__ aidx) {
+  const int box = ne[blockIdx.x];
+  __shared__ cplxf sh[PF_NCOEF], sl[PF_NCOEF];
+  const size_t lo = (size_t)nop * Pc * P;
+  dflt re{0, 0}, im{0, 0};
+  for (int q = 0; q < nch; ++q) {
+    const int ch = nch * box + q;
+    if (cbb[ch] >= cbe[ch]) continue;   // empty child (uniform across the block)
+    __syncthreads();
+    for (int i = threadIdx.x; i < Pc; i += blockDim.x) {
+      const cplx v = Mc[(size_t)ch * Pc + i];
+      sh[i] = cplxf{(float)v.re, (float)v.im};
+      sl[i] = split_lo(v);
+    }
+    __syncthreads();
+    if (threadIdx.x < P) {
+      const cplxf* ah = Ahl + (size_t)aidx[ch] * Pc * P + threadIdx.x;
+      for (int m = 0; m < Pc; ++m) dd_cmac(re, im, ah[(size_t)m * P], ah[lo + (size_t)m * P], sh[m], sl[m]);
+    }
+  }
+  if (threadIdx.x < P) Mp[(size_t)box * P + threadIdx.x] = cplx{dd_value(re), dd_value(im)};
+}
+
+// L2L: L(box) = B_pidx[box] L(parent), the parent box / nchp.
+__global__ void tri_l2l_dd_kernel(const int* __restrict__ ne, int P, int Pp, int nop, const cplxf* __restrict__ Bhl,
+                                  const cplx* __restrict__ Lp, cplx* __restrict__ L, int nchp,
+                                  const int* __restrict__ pidx) {
+  const int box = ne[blockIdx.x];
+  __shared__ cplxf sh[PF_NCOEF], sl[PF_NCOEF];
+  const int par = box / nchp;
+  for (int i = threadIdx.x; i < Pp; i += blockDim.x) {
+    const cplx v = Lp[(size_t)par * Pp + i];
+    sh[i] = cplxf{(float)v.re, (float)v.im};
+    sl[i] = split_lo(v);
+  }
+  __syncthreads();
+  if (threadIdx.x < P) {
+    const size_t lo = (size_t)nop * Pp * P;
+    const cplxf* bh = Bhl + (size_t)pidx[box] * Pp * P + threadIdx.x;
+    dflt re{0, 0}, im{0, 0};
+    for (int m = 0; m < Pp; ++m) dd_cmac(re, im, bh[(size_t)m * P], bh[lo + (size_t)m * P], sh[m], sl[m]);
+    L[(size_t)box * P + threadIdx.x] = cplx{dd_value(re), dd_value(im)};
+  }
+}
+
+cudaError_t k_tri_m2m_dd(pfmbem* h, int l) {
+  const Level& a = h->lev[l];
+  const Level& c = h->lev[l + 1];
+  tri_m2m_dd_kernel<<<a.nne, ((a.P + 31) / 32) * 32, 0, h->stream>>>(a.ne, a.P, c.P, a.tri_nop, a.tri_m2m_hl,
+                                                                     c.box_begin, c.box_end, c.M, a.M,
+                                                                     l == 0 ? 6 : 4, c.pidx);
+  return cudaGetLastError();
+}
+
+cudaError_t k_tri_l2l_dd(pfmbem* h, int l) {
+  const Level& a = h->lev[l];
+  const Level& pa = h->lev[l - 1];
+  tri_l2l_dd_kernel<<<a.nne, ((a.P + 31) / 32) * 32, 0, h->stream>>>(a.ne, a.P, pa.P, pa.tri_nop, pa.tri_l2l_hl,
+                                                                     pa.L, a.L, l == 1 ? 6 : 4, a.pidx);
+  return cudaGetLastError();
+}
+
 // Level l's hi and lo operator parts from its FP64 M2L table.
+// (and its M2M/L2L tables' parts, when the level has children)
 cudaError_t k_tri_m2l_split(pfmbem* h, int l) {
   const Level& L = h->lev[l];
   const size_t n = (size_t)L.tri_noff * L.P * L.P;
-  if (n == 0 || !L.tri_m2l_hl) return cudaSuccess;
-  split_hl_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(n, L.m2l, L.tri_m2l_hl);
+  if (n > 0 && L.tri_m2l_hl)
+    split_hl_kernel<<<(unsigned)std::min<size_t>((n + 255) / 256, 4096), 256, 0, h->stream>>>(n, L.m2l,
+                                                                                               L.tri_m2l_hl);
+  if (l < h->D && L.tri_m2m_hl && L.tri_l2l_hl) {
+    const size_t ns = (size_t)L.tri_nop * L.P * h->lev[l + 1].P;
+    split_hl_kernel<<<(unsigned)std::min<size_t>((ns + 255) / 256, 4096), 256, 0, h->stream>>>(ns, L.m2m,
+                                                                                                L.tri_m2m_hl);
+    split_hl_kernel<<<(unsigned)std::min<size_t>((ns + 255) / 256, 4096), 256, 0, h->stream>>>(ns, L.l2l,
+                                                                                                L.tri_l2l_hl);
+  }
   return cudaGetLastError();
 }
 

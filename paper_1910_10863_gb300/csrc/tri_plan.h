@@ -515,10 +515,17 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
       }
     }
     if (l < D) {
+      L.tri_nop = (int)sh_off[l].v.size();
       const size_t n = sh_off[l].v.size() * L.P * h->lev[l + 1].P;
       L.m2m = dalloc<cplx>(h, n);
       L.l2l = dalloc<cplx>(h, n);
       if (!L.m2m || !L.l2l) return fail(h, PFMBEM_ENOMEM, "device allocation failed (M2M/L2L operators)");
+      if (h->tri_cache) {
+        // hi and lo parts for the double-float M2M and L2L of the cached product
+        L.tri_m2m_hl = dalloc<cplxf>(h, 2 * n);
+        L.tri_l2l_hl = dalloc<cplxf>(h, 2 * n);
+        if (!L.tri_m2m_hl || !L.tri_l2l_hl) return fail(h, PFMBEM_ENOMEM, "device allocation failed (M2M/L2L operators)");
+      }
     }
   }
   // ---------------------------------------------------- element arrays (no wrapping: m0 = 0)
@@ -627,7 +634,7 @@ static pfmbem_status build_plan_tri(pfmbem* h, const double* nodes, const std::v
   CK(k_wide_top(h, dv, S, X, nbr_dev));
   if (h->tri_cache) {
     CK(k_tri_caches(h));
-    for (int l = 1; l <= D; ++l) CK(k_tri_m2l_split(h, l));
+    for (int l = 0; l <= D; ++l) CK(k_tri_m2l_split(h, l));
   }
   h->ub_on = false;
   pin_release_async(h);
