@@ -2288,9 +2288,18 @@ __global__ void top_apply_kernel(int rows, const cplx* __restrict__ TOP, const c
   const int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (row >= rows) return;
   const cplx* t = TOP + (size_t)row * rows;
-  cplx acc{0, 0};
-  for (int c = lane; c < rows; c += 32) acc += t[c] * M0[c];
-  acc = warp_sum(acc);
+  // four independent sums per lane: four loads of the row in flight at a time
+  cplx a0{0, 0}, a1{0, 0}, a2{0, 0}, a3{0, 0};
+  int c = lane;
+  for (; c + 96 < rows; c += 128) {
+    const cplx t0 = t[c], t1 = t[c + 32], t2 = t[c + 64], t3 = t[c + 96];
+    a0 += t0 * M0[c];
+    a1 += t1 * M0[c + 32];
+    a2 += t2 * M0[c + 64];
+    a3 += t3 * M0[c + 96];
+  }
+  for (; c < rows; c += 32) a0 += t[c] * M0[c];
+  cplx acc = warp_sum((a0 + a1) + (a2 + a3));
   if (lane == 0) L0[row] = acc;
 }
 
