@@ -96,9 +96,11 @@ typedef struct {
                        split into six equilateral triangles and each triangle into four
                        down to the leaves; cells and triangles are neighbours when they
                        touch.  Its product is FP64, one kernel per stage, with the element
-                       integrals cached at create (near_mode 0) or computed in every
-                       product (near_mode 1); launch and m2l_mode must be 0, a MIXED
-                       precision solves in FP64, and pfmbem_solve_batch rejects it.
+                       integrals cached at create (near_mode 0; M2M, M2L and L2L then in
+                       double-float arithmetic, about 48 bits, on the FP32 pipes) or
+                       computed in every product (near_mode 1); launch and m2l_mode must
+                       be 0, a MIXED precision solves in FP64, and pfmbem_solve_batch
+                       rejects it.
                        Default p_min 30.  EGEOM when a fiber leaves its cell, two fibers
                        share a cell or H is not a multiple (>= 2) of tri_a */
   double tri_a;     /* tree 1: nearest-neighbour spacing a of the hexagonal lattice, whose
